@@ -1,0 +1,208 @@
+/*
+ * skconv.h -- C ABI of the B300 real-space spherical convolution library.
+ *
+ * The operation (Sutter, Wandelt & Elsner, "Accelerating convolutions on the
+ * sphere with hybrid GPU/CPU kernel splitting", Sec. 2, Eq. 1): a radially
+ * symmetric kernel is split into a harmonic part K^_l (l <= l_cut) and a
+ * compact real-space part K^_theta supported on [0, theta_cut].  This library
+ * applies the real-space part to pixelised maps:
+ *
+ *   y_o = dOmega * sum_{i : gamma(o,i) <= theta_cut} K_lin(gamma(o,i)) * x_i,
+ *   dOmega = 4 pi / Npix,  gamma(o,i) = angle between pixel centres,
+ *
+ * where K_lin interpolates the tabulated kernel linearly in theta between
+ * nodes (Sec. 3: the tabulated real-space kernel, optionally with half of the
+ * nodes in the first 1/16 of the support).  Maps are HEALPix RING-ordered
+ * (the paper's pixelisation, Sec. 2), FP32, with the HEALPix library's pixel
+ * numbering (the first pixel of an unshifted ring at phi = 0).
+ *
+ * Conventions for every entry point:
+ *  - Return value: SK_OK (0) or a negative SK_E* code.  No exception crosses
+ *    the ABI.  sk_last_error() gives a message for the calling thread.
+ *  - Device pointers (d_*) are CUDA device addresses on the context's device,
+ *    owned by the caller.  Map buffers are contiguous FP32 [batch][map_stride]
+ *    with map_stride >= Npix; the first Npix entries of each row are the map in
+ *    RING order.  Map pointers must be 16-byte aligned and map_stride a
+ *    multiple of 4 (SK_EINVAL otherwise).  Input and output must not overlap
+ *    (SK_EINVAL).
+ *  - Host pointers (h_*) are ordinary host memory; page-locked memory gives the
+ *    fastest copies.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Launches
+ *    are asynchronous on it; device-side failures are recorded in the
+ *    context's status word and reported by sk_get_status().
+ *  - Handles (sk_ctx, sk_geom, sk_kern) are owned by the library and are
+ *    immutable after creation apart from sk_kernel_set_tiles.  Calls that use
+ *    the context's internal workspace (noted below) must not overlap on the
+ *    GPU: issue them on one stream, or synchronise between streams.
+ */
+#ifndef SKCONV_H
+#define SKCONV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SK_OK            0
+#define SK_EINVAL       -1   /* bad argument: size, alignment, aliasing, NULL   */
+#define SK_ENOMEM       -2   /* a device or host allocation failed              */
+#define SK_ECUDA        -3   /* a CUDA runtime call failed                       */
+#define SK_ETIMEOUT     -4   /* a bounded device-side wait gave up               */
+#define SK_EUNSUPPORTED -5   /* valid but outside what this build supports       */
+
+/* Node layouts of the tabulated kernel (Sec. 3). */
+#define SK_NODES_UNIFORM   0  /* n nodes theta_k = k theta_cut / (n-1)                      */
+#define SK_NODES_BIASED    1  /* nodes 0..n/2 uniform on [0, theta_cut/16], the rest uniform */
+                              /* on [theta_cut/16, theta_cut]: half the nodes in 1/16 of the  */
+                              /* support, the bias the paper uses for the oscillating kernel  */
+
+/* Path selection for sk_convolve_path / sk_convolve_jobs / sk_graph_capture. */
+#define SK_PATH_AUTO       0   /* belt Toeplitz + symmetric caps where they apply   */
+#define SK_PATH_GENERAL    1   /* per-pair evaluation for every output ring        */
+
+typedef struct sk_ctx  sk_ctx;
+typedef struct sk_geom sk_geom;
+typedef struct sk_kern sk_kern;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Bind a context to CUDA device `device` (makes it current on this thread).
+ * The context owns a device status word and a reusable workspace.
+ * Errors: SK_EINVAL (bad device), SK_ENOMEM, SK_ECUDA. */
+int sk_create(sk_ctx **out, int device);
+int sk_destroy(sk_ctx *ctx);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char *sk_last_error(void);
+
+/* Synchronise `stream` and return the device status word (SK_OK, or e.g.
+ * SK_ETIMEOUT recorded by a kernel), then clear it. */
+int sk_get_status(sk_ctx *ctx, void *stream);
+
+/* ---- geometry: HEALPix RING pixelisation (Sec. 2) ------------------------- */
+
+/* 12 * nside^2; -1 if nside is not a power of two in [1, 8192]. */
+int64_t sk_npix(int64_t nside);
+
+/* Per-ring tables for `nside` (power of two, 1..8192), computed on the device
+ * in FP64: pixel count, first pixel, phi shift, z = cos(theta), sin(theta).
+ * Errors: SK_EINVAL (bad nside), SK_ENOMEM, SK_ECUDA. */
+int sk_geometry_create(sk_ctx *ctx, int64_t nside, sk_geom **out);
+int sk_geometry_destroy(sk_geom *g);
+
+/* Copy the per-ring tables to the host (each array has 4*nside-1 entries;
+ * any pointer may be NULL).  For tests and tooling. */
+int sk_geometry_rings(const sk_geom *g, int32_t *h_n, int64_t *h_start, int32_t *h_shift,
+                      double *h_z, double *h_sinth);
+
+/* ---- tabulated real-space kernel K^_theta (Sec. 2 Eq. 1, Sec. 3) --------- */
+
+/* Build the operator for geometry `g` from a kernel table: n_nodes FP64 node
+ * values `h_values` (host; copied) on [0, theta_cut] in the given node layout.
+ * theta_cut in radians, 0 < theta_cut <= pi.  Computes on the device the
+ * per-ring-pair window bounds (which input rings and phi ranges can hold
+ * pixels within theta_cut of each output ring) and the work plan.  The
+ * geometry must outlive the operator.
+ * Errors: SK_EINVAL (n_nodes < 2, or < 4 for the biased layout, bad
+ * theta_cut or layout), SK_EUNSUPPORTED (n_nodes > 16384), SK_ENOMEM, SK_ECUDA. */
+int sk_kernel_create(sk_ctx *ctx, const sk_geom *g, const double *h_values, int64_t n_nodes,
+                     double theta_cut, int layout, sk_kern **out);
+
+/* Tabulate the real-space part of the split of a kernel given by its Legendre
+ * coefficients (Sec. 2, Eq. 1: K^_theta = the part of sum_l (2l+1)/(4pi) K_l
+ * P_l(cos theta) above l_cut, truncated at theta_cut), on the device in FP64:
+ *   V_k = taper(theta_k) * sum_{l=lmin}^{lmax} (2l+1)/(4 pi) h_kl[l] P_l(cos theta_k)
+ * with taper = 1 for theta <= taper_start*theta_cut and a raised cosine down to
+ * 0 at theta_cut (taper_start >= 1: no taper).  h_kl has lmax+1 entries (host).
+ * Writes the n_nodes FP64 values to h_values_out (host) if it is not NULL and,
+ * if `out` is not NULL, builds the operator as sk_kernel_create would.
+ * Errors as sk_kernel_create, plus SK_EINVAL for lmin > lmax or lmax < 0. */
+int sk_kernel_from_legendre(sk_ctx *ctx, const sk_geom *g, const double *h_kl, int64_t lmin,
+                            int64_t lmax, int64_t n_nodes, double theta_cut, int layout,
+                            double taper_start, double *h_values_out, sk_kern **out);
+int sk_kernel_destroy(sk_kern *k);
+
+/* Replace the node values of an operator (same count, cut and layout), e.g.
+ * between training steps; the window tables are kept.  h_values: n_nodes FP64
+ * (host; copied).  Synchronises the device.  Errors: SK_EINVAL, SK_ECUDA. */
+int sk_kernel_update_values(sk_kern *k, const double *h_values);
+
+/* Number of ordered pixel pairs (o, i) with gamma(o,i) <= theta_cut, counted on
+ * the device in FP64 from the per-ring-pair phi windows.  Blocks until done. */
+int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out);
+
+/* ---- convolution --------------------------------------------------------- */
+
+/* y = A x for `batch` maps (the real-space convolution above).
+ * d_in, d_out: [batch][map_stride] FP32 device buffers.  batch >= 0 (0 is a
+ * no-op).  Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_convolve(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
+                int64_t batch, int64_t map_stride, void *stream);
+
+/* Same, forcing a path (SK_PATH_AUTO or SK_PATH_GENERAL). */
+int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
+                     int64_t batch, int64_t map_stride, int path, void *stream);
+
+/* x_bar = A^T y_bar.  The kernel is radial, so A_oi = dOmega K_lin(gamma(o,i))
+ * is symmetric and the transpose, written as a gather over the inputs of each
+ * output, is the forward gather.  Same arguments and errors as sk_convolve. */
+int sk_convolve_adjoint(sk_ctx *ctx, const sk_kern *k, const float *d_gy, float *d_gx,
+                        int64_t batch, int64_t map_stride, void *stream);
+
+/* Gradient of a loss with respect to the table nodes, given the input maps x
+ * and dL/dy:  d_gtable[n] = dOmega sum_b sum_o gy_bo sum_{i in cut} x_bi dK_lin/dV_n,
+ * dK_lin/dV_k = 1 - f, dK_lin/dV_{k+1} = f (linear interpolation, Sec. 3).
+ * d_gtable: n_nodes FP32 device buffer (overwritten).  Partial sums are FP32
+ * per block and reduced in FP64.  Uses the context workspace.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, const float *d_gy,
+                  int64_t batch, int64_t map_stride, float *d_gtable, void *stream);
+
+/* End-to-end convolution from and to host memory: copies `batch` maps from
+ * h_in to the context workspace, convolves, copies the result to h_out, and
+ * synchronises `stream`.  h_in/h_out: [batch][map_stride] FP32 host buffers.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in, float *h_out,
+                     int64_t batch, int64_t map_stride, void *stream);
+
+/* ---- many jobs in one launch, CUDA graphs -------------------------------- */
+
+typedef struct {
+    const sk_kern *k;      /* operator (its geometry decides Npix)             */
+    const float *d_in;     /* [batch][map_stride] FP32 device                   */
+    float *d_out;          /* [batch][map_stride] FP32 device                   */
+    int64_t batch;
+    int64_t map_stride;
+} sk_job;
+
+/* Convolve several jobs (mixed Nside, kernels, batch sizes) with one
+ * persistent launch per path family that pulls (job, tile) items from a
+ * device work queue, largest items first.  flags: SK_PATH_AUTO or
+ * SK_PATH_GENERAL.  Uses the context workspace.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_convolve_jobs(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int flags, void *stream);
+
+/* Capture the launches of sk_convolve_jobs(jobs) into a CUDA graph and
+ * instantiate it; *graph_exec receives an opaque handle.  Replaying it with
+ * sk_graph_launch runs the same jobs on the same buffers.  The work list the
+ * graph reads is owned by the handle; free it with sk_graph_destroy. */
+int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int flags, void *stream,
+                     void **graph_exec);
+int sk_graph_launch(void *graph_exec, void *stream);
+int sk_graph_destroy(void *graph_exec);
+
+/* ---- tuning -------------------------------------------------------------- */
+
+/* Set the tile parameters of operator k: belt_p = outputs per thread along a
+ * belt ring (one of 5, 7, 9, 11, 13, 15, 17), cap_t = output pixels per cap tile
+ * (64 or 128).  0 keeps the current value.  Used by the autotuner; not safe
+ * while a launch with k is being issued from another thread.
+ * Errors: SK_EINVAL. */
+int sk_kernel_set_tiles(sk_kern *k, int belt_p, int cap_t);
+int sk_kernel_get_tiles(const sk_kern *k, int *belt_p, int *cap_t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKCONV_H */

@@ -1,0 +1,391 @@
+"""Python binding of libskconv (include/skconv.h): argument marshalling only.
+
+Every step of the convolution runs in the library's CUDA kernels; this module
+turns torch CUDA tensors into pointers and streams and raises on error codes.
+There is no CPU fallback: without the compiled library (or a GPU) every call
+raises.
+
+The operation is the real-space part of the split convolution of Sutter,
+Wandelt & Elsner (Sec. 2, Eq. 1): y_o = dOmega sum_{gamma(o,i) <= theta_cut}
+K_lin(gamma(o,i)) x_i on HEALPix RING maps, with K_lin the linearly interpolated
+kernel table of Sec. 3.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libskconv.so")
+
+SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+NODES_UNIFORM, NODES_BIASED = 0, 1
+PATH_AUTO, PATH_GENERAL = 0, 1
+
+_ERRNAMES = {SK_EINVAL: "SK_EINVAL", SK_ENOMEM: "SK_ENOMEM", SK_ECUDA: "SK_ECUDA",
+             SK_ETIMEOUT: "SK_ETIMEOUT", SK_EUNSUPPORTED: "SK_EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sk_job(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("batch", ctypes.c_int64), ("map_stride", ctypes.c_int64)]
+
+
+def _declare(L):
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "sk_create": (I, [PP, I]),
+        "sk_destroy": (I, [P]),
+        "sk_last_error": (ctypes.c_char_p, []),
+        "sk_get_status": (I, [P, P]),
+        "sk_npix": (I64, [I64]),
+        "sk_geometry_create": (I, [P, I64, PP]),
+        "sk_geometry_destroy": (I, [P]),
+        "sk_geometry_rings": (I, [P, P, P, P, P, P]),
+        "sk_kernel_create": (I, [P, P, P, I64, D, I, PP]),
+        "sk_kernel_from_legendre": (I, [P, P, P, I64, I64, I64, D, I, D, P, PP]),
+        "sk_kernel_update_values": (I, [P, P]),
+        "sk_kernel_destroy": (I, [P]),
+        "sk_count_pairs": (I, [P, P, ctypes.POINTER(I64)]),
+        "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
+        "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
+        "sk_convolve_adjoint": (I, [P, P, P, P, I64, I64, P]),
+        "sk_grad_table": (I, [P, P, P, P, I64, I64, P, P]),
+        "sk_convolve_host": (I, [P, P, P, P, I64, I64, P]),
+        "sk_convolve_jobs": (I, [P, ctypes.POINTER(sk_job), I, I, P]),
+        "sk_graph_capture": (I, [P, ctypes.POINTER(sk_job), I, I, P, PP]),
+        "sk_graph_launch": (I, [P, P]),
+        "sk_graph_destroy": (I, [P]),
+        "sk_kernel_set_tiles": (I, [P, I, I]),
+        "sk_kernel_get_tiles": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def lib():
+    """Load libskconv.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+            if not _build.up_to_date():
+                _build.build()
+            _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def _check(rc):
+    if rc != SK_OK:
+        raise SkError(rc, lib().sk_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _map_args(t, npix):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+        raise TypeError("maps must be float32 CUDA tensors")
+    if t.dim() == 1:
+        t = t.view(1, -1)
+    if t.dim() != 2 or t.shape[1] < npix or t.stride(1) != 1:
+        raise ValueError(f"maps must be [batch, >= {npix}] with unit inner stride")
+    return t, t.shape[0], t.stride(0) if t.shape[0] > 1 else max(t.shape[1], npix)
+
+
+class Context:
+    """A library context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_create(ctypes.byref(self._h), device))
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().sk_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None):
+        _check(lib().sk_get_status(self._h, _stream_ptr(stream)))
+
+
+class Geometry:
+    """HEALPix RING geometry for one Nside, on the device."""
+
+    def __init__(self, ctx: Context, nside: int):
+        self.ctx = ctx
+        self.nside = int(nside)
+        self.npix = 12 * self.nside * self.nside
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_geometry_create(ctx._h, self.nside, ctypes.byref(self._h)))
+
+    def rings(self):
+        nr = 4 * self.nside - 1
+        n = np.empty(nr, np.int32); st = np.empty(nr, np.int64); s = np.empty(nr, np.int32)
+        z = np.empty(nr); sn = np.empty(nr)
+        _check(lib().sk_geometry_rings(self._h, n.ctypes.data, st.ctypes.data, s.ctypes.data,
+                                       z.ctypes.data, sn.ctypes.data))
+        return n, st, s, z, sn
+
+    def close(self):
+        if self._h:
+            lib().sk_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Kernel:
+    """The operator: a tabulated real-space kernel on [0, theta_cut] for a geometry."""
+
+    def __init__(self, geom: Geometry, values=None, theta_cut: float = None, layout: int = NODES_UNIFORM,
+                 _handle=None):
+        self.geom = geom
+        self.ctx = geom.ctx
+        self.theta_cut = float(theta_cut)
+        self.layout = int(layout)
+        if _handle is not None:
+            self._h = _handle
+            self.values = None
+            return
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self.values = v.copy()
+        self.n_nodes = len(v)
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_kernel_create(self.ctx._h, geom._h, v.ctypes.data, len(v), self.theta_cut,
+                                      self.layout, ctypes.byref(self._h)))
+
+    @classmethod
+    def from_legendre(cls, geom: Geometry, k_ell, lmin: int, lmax: int, n_nodes: int, theta_cut: float,
+                      layout: int = NODES_UNIFORM, taper_start: float = 0.9):
+        """Tabulate on the device the l in [lmin, lmax] part of sum (2l+1)/(4pi) K_l P_l(cos theta),
+        tapered to 0 at theta_cut, and build the operator.  Returns (Kernel, FP64 node values)."""
+        kl = np.ascontiguousarray(k_ell, dtype=np.float64)
+        if len(kl) < lmax + 1:
+            raise ValueError("k_ell shorter than lmax + 1")
+        vals = np.empty(n_nodes, np.float64)
+        h = ctypes.c_void_p()
+        _check(lib().sk_kernel_from_legendre(geom.ctx._h, geom._h, kl.ctypes.data, lmin, lmax, n_nodes,
+                                             float(theta_cut), layout, float(taper_start),
+                                             vals.ctypes.data, ctypes.byref(h)))
+        k = cls(geom, theta_cut=theta_cut, layout=layout, _handle=h)
+        k.values = vals
+        k.n_nodes = n_nodes
+        return k, vals
+
+    @staticmethod
+    def tabulate(geom: Geometry, k_ell, lmin, lmax, n_nodes, theta_cut, layout=NODES_UNIFORM,
+                 taper_start=0.9):
+        """Only the FP64 node values of from_legendre (no operator)."""
+        kl = np.ascontiguousarray(k_ell, dtype=np.float64)
+        vals = np.empty(n_nodes, np.float64)
+        _check(lib().sk_kernel_from_legendre(geom.ctx._h, geom._h, kl.ctypes.data, lmin, lmax, n_nodes,
+                                             float(theta_cut), layout, float(taper_start),
+                                             vals.ctypes.data, None))
+        return vals
+
+    def update_values(self, values):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        if len(v) != self.n_nodes:
+            raise ValueError("node count differs")
+        _check(lib().sk_kernel_update_values(self._h, v.ctypes.data))
+        self.values = v.copy()
+
+    def count_pairs(self) -> int:
+        c = ctypes.c_int64()
+        _check(lib().sk_count_pairs(self.ctx._h, self._h, ctypes.byref(c)))
+        return c.value
+
+    def set_tiles(self, belt_p=0, cap_t=0):
+        _check(lib().sk_kernel_set_tiles(self._h, belt_p, cap_t))
+
+    def tiles(self):
+        p = ctypes.c_int(); t = ctypes.c_int()
+        _check(lib().sk_kernel_get_tiles(self._h, ctypes.byref(p), ctypes.byref(t)))
+        return p.value, t.value
+
+    def close(self):
+        if self._h:
+            lib().sk_kernel_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def convolve(kern: Kernel, x, out=None, path: int = PATH_AUTO, stream=None):
+    """y = A x for maps x [batch, npix] (float32 CUDA)."""
+    import torch
+    x2, b, stride = _map_args(x, kern.geom.npix)
+    if out is None:
+        out = torch.empty_like(x2)
+    o2, b2, stride2 = _map_args(out, kern.geom.npix)
+    if b2 != b or stride2 != stride:
+        raise ValueError("out must match x in shape and strides")
+    _check(lib().sk_convolve_path(kern.ctx._h, kern._h, ctypes.c_void_p(x2.data_ptr()),
+                                  ctypes.c_void_p(o2.data_ptr()), b, stride, path, _stream_ptr(stream)))
+    return out
+
+
+def convolve_adjoint(kern: Kernel, gy, out=None, stream=None):
+    """x_bar = A^T y_bar (the same gather: the operator is symmetric)."""
+    import torch
+    g2, b, stride = _map_args(gy, kern.geom.npix)
+    if out is None:
+        out = torch.empty_like(g2)
+    o2, _, _ = _map_args(out, kern.geom.npix)
+    _check(lib().sk_convolve_adjoint(kern.ctx._h, kern._h, ctypes.c_void_p(g2.data_ptr()),
+                                     ctypes.c_void_p(o2.data_ptr()), b, stride, _stream_ptr(stream)))
+    return out
+
+
+def grad_table(kern: Kernel, x, gy, out=None, stream=None):
+    """dL/dV_n for the table nodes given maps x and dL/dy (float32 [n_nodes])."""
+    import torch
+    x2, b, stride = _map_args(x, kern.geom.npix)
+    g2, b2, stride2 = _map_args(gy, kern.geom.npix)
+    if b2 != b or stride2 != stride:
+        raise ValueError("x and gy must match")
+    if out is None:
+        out = torch.empty(kern.n_nodes, dtype=torch.float32, device=x2.device)
+    _check(lib().sk_grad_table(kern.ctx._h, kern._h, ctypes.c_void_p(x2.data_ptr()),
+                               ctypes.c_void_p(g2.data_ptr()), b, stride,
+                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def convolve_host(kern: Kernel, x: np.ndarray, out: np.ndarray = None, stream=None) -> np.ndarray:
+    """End to end from host memory: copies in, convolves, copies out (synchronises)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if x.ndim == 1:
+        x = x[None]
+    if out is None:
+        out = np.empty_like(x)
+    _check(lib().sk_convolve_host(kern.ctx._h, kern._h, x.ctypes.data, out.ctypes.data, x.shape[0],
+                                  x.shape[1], _stream_ptr(stream)))
+    return out
+
+
+def _jobs_array(jobs):
+    arr = (sk_job * len(jobs))()
+    keep = []
+    for i, (kern, x, y) in enumerate(jobs):
+        x2, b, stride = _map_args(x, kern.geom.npix)
+        y2, _, _ = _map_args(y, kern.geom.npix)
+        keep.append((x2, y2))
+        arr[i] = sk_job(kern._h.value, x2.data_ptr(), y2.data_ptr(), b, stride)
+    return arr, keep
+
+
+def convolve_jobs(ctx: Context, jobs, path: int = PATH_AUTO, stream=None):
+    """Several (kernel, x, y) jobs with mixed Nside/kernels/batch in one launch per path family."""
+    arr, _keep = _jobs_array(jobs)
+    _check(lib().sk_convolve_jobs(ctx._h, arr, len(jobs), path, _stream_ptr(stream)))
+
+
+class Graph:
+    """A CUDA graph of convolve_jobs(jobs) on fixed buffers."""
+
+    def __init__(self, ctx: Context, jobs, path: int = PATH_AUTO, stream=None):
+        import torch
+        self.ctx = ctx
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        arr, self._keep = _jobs_array(jobs)
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_graph_capture(ctx._h, arr, len(jobs), path, _stream_ptr(self._stream),
+                                      ctypes.byref(self._h)))
+
+    def launch(self, stream=None):
+        _check(lib().sk_graph_launch(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if self._h:
+            lib().sk_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sph_conv(x, table, kern: Kernel):
+    """Differentiable y = A(table) x: gradients for the maps (adjoint gather) and for the
+    table nodes (binned scatter-add).  `table` is a float64 or float32 tensor of the
+    node values; the operator's table is refreshed when the values change."""
+    return _SphConv.apply(x, table, kern)
+
+
+def _make_autograd():
+    import torch
+
+    class SphConv(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, table, kern):
+            v = table.detach().to(torch.float64).cpu().numpy()
+            if kern.values is None or not np.array_equal(v, kern.values):
+                kern.update_values(v)
+            ctx.kern = kern
+            ctx.table_dtype = table.dtype
+            ctx.save_for_backward(x)
+            return convolve(kern, x.contiguous())
+
+        @staticmethod
+        def backward(ctx, gy):
+            (x,) = ctx.saved_tensors
+            gy = gy.contiguous()
+            gx = convolve_adjoint(ctx.kern, gy) if ctx.needs_input_grad[0] else None
+            gt = None
+            if ctx.needs_input_grad[1]:
+                gt = grad_table(ctx.kern, x.contiguous(), gy).to(ctx.table_dtype)
+            return gx, gt, None
+
+    return SphConv
+
+
+class _Lazy:
+    _cls = None
+
+    def apply(self, *a):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_autograd()
+        return _Lazy._cls.apply(*a)
+
+
+_SphConv = _Lazy()

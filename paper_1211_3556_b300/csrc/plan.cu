@@ -1,0 +1,389 @@
+// plan.cu -- which path covers which output ring, the work items of each path,
+// and the launch sequences of the forward operator and of the table gradient.
+//
+// Rings are split three ways when a kernel handle is built:
+//  * belt: a symmetric range of equatorial rings whose whole window lies in the
+//    belt (all rings of 4 Nside pixels), computed as ring-wise Toeplitz sums;
+//  * caps: the remaining northern rings (not the equator ring) with their
+//    southern mirrors, evaluated per pair and shared by the 8 symmetric images;
+//  * general: whatever neither covers (e.g. the equator ring when no belt
+//    exists at a small Nside and a wide cut), evaluated per pair.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "skconv_host.h"
+
+namespace {
+
+template <typename T>
+int upload(const std::vector<T> &h, T **d) {
+    *d = nullptr;
+    if (h.empty()) return SK_OK;
+    SK_CU(cudaMalloc(d, sizeof(T) * h.size()));
+    SK_CU(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    return SK_OK;
+}
+
+int centre(int jo, int n_o, int s_o, const PairInfo &P) {
+    long long num = (long long)(2 * jo + s_o) * P.n_i + (long long)(1 - P.s_i) * n_o;
+    return (int)(num / (2LL * n_o));
+}
+
+// Strip length a cap item needs for input ring P, and the largest |q| of its windows.
+void cap_needs(int j0, int jlast, int n_o, int s_o, const PairInfo &P, int &L, long long &qmax) {
+    int cnt = P.W < 0 ? P.n_i : 2 * P.W + 1;
+    L = centre(jlast, n_o, s_o, P) - centre(j0, n_o, s_o, P) + cnt;
+    // q at the window centre is below n_o + n_i in magnitude; each step adds 2 n_o
+    qmax = (long long)n_o + P.n_i + (long long)cnt * 2 * n_o;
+}
+
+int belt_cost_p(int n4) {
+    // choose the outputs-per-thread P: tail waste of the last segment against the
+    // per-chunk overhead of reloading P + 3 strip values for 4P FFMAs
+    const int Ps[] = {5, 7, 9, 11, 13, 15, 17};
+    int best = 13;
+    double bc = 1e300;
+    for (int P : Ps) {
+        int ts = 32 * P;
+        int nseg = (n4 + ts - 1) / ts;
+        double c = (double)nseg * ts * (1.0 + 3.0 / P);
+        if (c < bc - 1e-9) { bc = c; best = P; }
+    }
+    return best;
+}
+
+}  // namespace
+
+void sk_plan_free(sk_kern *k) {
+    cudaFree(k->d_items_gen); k->d_items_gen = nullptr;
+    cudaFree(k->d_brng); k->d_brng = nullptr;
+    cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
+    cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c) { cudaFree(k->d_items_cap[c]); k->d_items_cap[c] = nullptr; }
+    k->plan_ok = false;
+}
+
+int sk_plan_rebuild_belt_items(sk_kern *k) {
+    cudaFree(k->d_items_belt);
+    k->d_items_belt = nullptr;
+    k->n_items_belt = 0;
+    if (k->nb == 0) return SK_OK;
+    const int n4 = (int)(4 * k->g->nside);
+    const int ts = 32 * k->belt_P;
+    const int nseg = (n4 + ts - 1) / ts;
+    std::vector<int4> it;
+    for (int g = 0; g < k->ngroups; ++g)
+        for (int s = 0; s < nseg; ++s) it.push_back(make_int4(g, s, 0, 0));
+    k->n_items_belt = (int)it.size();
+    return upload(it, &k->d_items_belt);
+}
+
+int sk_plan_build(sk_kern *k) {
+    const sk_geom *g = k->g;
+    const int nr = g->nr;
+    const long long N = g->nside;
+    const int n4 = (int)(4 * N);
+    const int eq = (int)(2 * N - 1);           // equator ring (0-based)
+    const auto &R = g->h_rings;
+    const auto &off = k->h_pair_off;
+    const auto &pairs = k->h_pairs;
+
+    // ---- belt: rings whose whole window has 4N pixels per ring and narrow windows
+    auto belt_ok = [&](int r) {
+        if (R[r].n != n4) return false;
+        for (int p = off[r]; p < off[r + 1]; ++p) {
+            const PairInfo &P = pairs[p];
+            if (P.n_i != n4 || P.W < 0) return false;
+            int nch = (2 * P.W + 1 + 3) / 4;
+            if (4 * nch > n4) return false;
+        }
+        return true;
+    };
+    int b_lo = eq, b_hi = eq;
+    if (belt_ok(eq)) {
+        while (b_lo - 1 >= 0 && belt_ok(b_lo - 1) && belt_ok(nr - 1 - (b_lo - 1))) --b_lo;
+        b_hi = nr - 1 - b_lo;
+        k->b_lo = b_lo;
+        k->nb = b_hi - b_lo + 1;
+    } else {
+        k->b_lo = eq;
+        k->nb = 0;
+    }
+
+    std::vector<char> covered(nr, 0);
+    if (k->nb > 0) {
+        int HM = 0;
+        for (int r = b_lo; r <= b_hi; ++r) HM = std::max(HM, std::max(r - k->h_lo[r], k->h_hi[r] - r));
+        k->HM = HM;
+        const int R2 = 2 * HM + 1;
+        k->ngroups = (k->nb + SK_BELT_G - 1) / SK_BELT_G;
+        const int nb_pad = k->ngroups * SK_BELT_G;
+        std::vector<int2> rng((size_t)nb_pad * R2, make_int2(0, 0));
+        int EMIN = 1 << 30, EMAX = -(1 << 30), WPM = 4;
+        for (int rb = 0; rb < k->nb; ++rb) {
+            const int r = b_lo + rb;
+            covered[r] = 1;
+            for (int p = off[r]; p < off[r + 1]; ++p) {
+                const PairInfo &P = pairs[p];
+                const int d = P.ri - r;
+                const int ec = (R[r].s + 1 - P.s_i) >> 1;     // offset of the nearest input pixel
+                const int elo = ec - P.W;
+                const int nch = (2 * P.W + 1 + 3) / 4;
+                rng[(size_t)rb * R2 + d + HM] = make_int2(elo, nch);
+                EMIN = std::min(EMIN, elo);
+                EMAX = std::max(EMAX, elo + 4 * nch - 1);
+                WPM = std::max(WPM, 4 * nch);
+            }
+        }
+        k->EMIN = EMIN; k->EMAX = EMAX; k->WPM = WPM;
+        std::vector<int2> grp(k->ngroups);
+        for (int gi = 0; gi < k->ngroups; ++gi) {
+            int lo = 1 << 30, hi = -1;
+            for (int w = 0; w < SK_BELT_G; ++w) {
+                int rb = gi * SK_BELT_G + w;
+                if (rb >= k->nb) break;
+                lo = std::min(lo, k->h_lo[b_lo + rb]);
+                hi = std::max(hi, k->h_hi[b_lo + rb]);
+            }
+            grp[gi] = make_int2(lo, hi);
+        }
+        int rc;
+        if ((rc = upload(rng, &k->d_brng))) return rc;
+        if ((rc = upload(grp, &k->d_bgrp))) return rc;
+        k->belt_P = belt_cost_p(n4);
+        if ((rc = sk_plan_rebuild_belt_items(k))) return rc;
+    }
+
+    // ---- caps: northern rings below the belt (never the equator ring) and mirrors
+    std::vector<int4> cap_items[SK_CAP_LS_CLASSES];
+    const int cap_end = k->nb > 0 ? b_lo : eq;
+    k->n_cap_rings = 0;
+    for (int r = 0; r < cap_end; ++r) {
+        const int Q = R[r].n / 4;
+        int need = 0;
+        bool ok = (nr - 1 - r) != r;
+        for (int j0 = 0; j0 < Q && ok; j0 += 128) {
+            const int jl = std::min(j0 + 127, Q - 1);
+            for (int p = off[r]; p < off[r + 1]; ++p) {
+                int L; long long qm;
+                cap_needs(j0, jl, R[r].n, R[r].s, pairs[p], L, qm);
+                need = std::max(need, L);
+                if (qm >= (1LL << 24)) ok = false;
+            }
+        }
+        int cls = -1;
+        for (int c = 0; c < SK_CAP_LS_CLASSES && ok; ++c)
+            if (need <= SK_CAP_LS[c]) { cls = c; break; }
+        if (!ok || cls < 0) continue;
+        covered[r] = covered[nr - 1 - r] = 1;
+        ++k->n_cap_rings;
+        for (int j0 = 0; j0 < Q; j0 += 128) cap_items[cls].push_back(make_int4(r, j0, 0, 0));
+    }
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c) {
+        // heavier rings first: per-item cost grows with the number of window pixels
+        std::stable_sort(cap_items[c].begin(), cap_items[c].end(), [&](const int4 &a, const int4 &b) {
+            return (off[a.x + 1] - off[a.x]) > (off[b.x + 1] - off[b.x]);
+        });
+        k->n_items_cap[c] = (int)cap_items[c].size();
+        int rc = upload(cap_items[c], &k->d_items_cap[c]);
+        if (rc) return rc;
+    }
+
+    // ---- general: the rest
+    std::vector<int4> gen;
+    for (int r = 0; r < nr; ++r)
+        if (!covered[r])
+            for (int j = 0; j < R[r].n; j += 128) gen.push_back(make_int4(r, j, 0, 0));
+    k->n_items_gen = (int)gen.size();
+    int rc = upload(gen, &k->d_items_gen);
+    if (rc) return rc;
+    k->plan_ok = true;
+    return SK_OK;
+}
+
+size_t sk_plan_workspace_bytes(const sk_kern *k) {
+    if (!k->plan_ok || k->nb == 0) return 0;
+    size_t rows = (size_t)k->ngroups * SK_BELT_G * (2 * k->HM + 1);
+    return (rows * k->WPM * sizeof(float) + 255) & ~(size_t)255;
+}
+
+size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n) {
+    size_t b = 0;
+    for (int i = 0; i < n; ++i) b += sk_plan_workspace_bytes(jobs[i].k);
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// launch sequences
+// ---------------------------------------------------------------------------
+
+namespace {
+
+JobDesc base_desc(const SkJob &jb) {
+    const sk_kern *k = jb.k;
+    JobDesc d;
+    memset(&d, 0, sizeof d);
+    d.rings = k->g->d_rings;
+    d.pair_off = k->d_pair_off;
+    d.pairs = k->d_pairs;
+    d.tab = k->d_tab;
+    d.kp = k->kp;
+    d.nr = k->g->nr;
+    d.x = jb.x;
+    d.y = jb.y;
+    d.stride = jb.stride;
+    d.batch = (int)jb.batch;
+    d.n4 = (int)(4 * k->g->nside);
+    return d;
+}
+
+// Collects jobs for one kernel family and launches them SK_MAXJ at a time.
+struct Batcher {
+    JobsArg a;
+    Batcher() { reset(); }
+    void reset() { memset(&a, 0, sizeof a); }
+    bool full() const { return a.n_jobs == SK_MAXJ; }
+    void add(JobDesc d, const int4 *items, int n_items) {
+        d.items = items;
+        d.n_items = n_items;
+        d.flat_base = a.total;
+        a.j[a.n_jobs++] = d;
+        a.total += n_items * d.batch;
+    }
+};
+
+int grid_for(int total, int per_sm, int sms) {
+    int g = std::max(1, per_sm) * sms;
+    return std::min(total, g);
+}
+
+}  // namespace
+
+int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
+    // belt weight rows first (one pre-pass per job, shared by all its maps)
+    std::vector<float *> wrows(n, nullptr);
+    char *wp = (char *)ws;
+    if (path == SK_PATH_AUTO) {
+        for (int i = 0; i < n; ++i) {
+            const sk_kern *k = jobs[i].k;
+            if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
+            wrows[i] = (float *)wp;
+            wp += sk_plan_workspace_bytes(k);
+            JobDesc d = base_desc(jobs[i]);
+            d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
+            d.brng = k->d_brng;
+            SK_CU(sk_launch_belt_weights(d, wrows[i], st));
+        }
+    }
+
+    if (path == SK_PATH_GENERAL) {
+        Batcher b;
+        auto flush = [&]() -> int {
+            if (b.a.total > 0) {
+                b.a.status = ctx->d_status;
+                SK_CU(sk_launch_conv_general(b.a, grid_for(b.a.total, 16, ctx->num_sms), st));
+            }
+            b.reset();
+            return SK_OK;
+        };
+        for (int i = 0; i < n; ++i) {
+            if (jobs[i].batch == 0) continue;
+            b.add(base_desc(jobs[i]), jobs[i].k->d_items_all, jobs[i].k->n_items_all);
+            if (b.full()) { int rc = flush(); if (rc) return rc; }
+        }
+        return flush();
+    }
+
+    // belt: one launch family per tile width P
+    const int Ps[] = {5, 7, 9, 11, 13, 15, 17};
+    for (int P : Ps) {
+        Batcher b;
+        auto flush = [&]() -> int {
+            if (b.a.total > 0) {
+                b.a.status = ctx->d_status;
+                int per = sk_belt_blocks_per_sm(b.a, P);
+                SK_CU(sk_launch_conv_belt(b.a, P, grid_for(b.a.total, per, ctx->num_sms), st));
+            }
+            b.reset();
+            return SK_OK;
+        };
+        for (int i = 0; i < n; ++i) {
+            const sk_kern *k = jobs[i].k;
+            if (!k->plan_ok || k->nb == 0 || k->belt_P != P || jobs[i].batch == 0) continue;
+            JobDesc d = base_desc(jobs[i]);
+            d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
+            d.EMIN = k->EMIN; d.EMAX = k->EMAX;
+            d.brng = k->d_brng; d.bw = wrows[i]; d.bgrp = k->d_bgrp;
+            b.add(d, k->d_items_belt, k->n_items_belt);
+            if (b.full()) { int rc = flush(); if (rc) return rc; }
+        }
+        int rc = flush();
+        if (rc) return rc;
+    }
+
+    // caps: one launch family per strip class
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c) {
+        Batcher b;
+        auto flush = [&]() -> int {
+            if (b.a.total > 0) {
+                b.a.status = ctx->d_status;
+                int per = sk_cap_blocks_per_sm(SK_CAP_LS[c]);
+                SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], grid_for(b.a.total, per, ctx->num_sms), st));
+            }
+            b.reset();
+            return SK_OK;
+        };
+        for (int i = 0; i < n; ++i) {
+            const sk_kern *k = jobs[i].k;
+            if (!k->plan_ok || k->n_items_cap[c] == 0 || jobs[i].batch == 0) continue;
+            JobDesc d = base_desc(jobs[i]);
+            d.cap_ls = SK_CAP_LS[c];
+            b.add(d, k->d_items_cap[c], k->n_items_cap[c]);
+            if (b.full()) { int rc = flush(); if (rc) return rc; }
+        }
+        int rc = flush();
+        if (rc) return rc;
+    }
+
+    // general fallback rings
+    {
+        Batcher b;
+        auto flush = [&]() -> int {
+            if (b.a.total > 0) {
+                b.a.status = ctx->d_status;
+                SK_CU(sk_launch_conv_general(b.a, grid_for(b.a.total, 16, ctx->num_sms), st));
+            }
+            b.reset();
+            return SK_OK;
+        };
+        for (int i = 0; i < n; ++i) {
+            const sk_kern *k = jobs[i].k;
+            if (jobs[i].batch == 0) continue;
+            const int4 *items = k->plan_ok ? k->d_items_gen : k->d_items_all;
+            const int ni = k->plan_ok ? k->n_items_gen : k->n_items_all;
+            if (ni == 0) continue;
+            b.add(base_desc(jobs[i]), items, ni);
+            if (b.full()) { int rc = flush(); if (rc) return rc; }
+        }
+        int rc = flush();
+        if (rc) return rc;
+    }
+    return SK_OK;
+}
+
+int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,
+                long long stride, float *out, double *acc, cudaStream_t st) {
+    SK_CU(cudaMemsetAsync(acc, 0, sizeof(double) * k->nt, st));
+    if (batch > 0) {
+        SkJob jb{k, x, nullptr, batch, stride};
+        Batcher b;
+        b.add(base_desc(jb), k->d_items_all, k->n_items_all);
+        b.a.status = ctx->d_status;
+        SK_CU(sk_launch_grad_general(b.a, gy, acc, grid_for(b.a.total, 8, ctx->num_sms), st));
+    }
+    SK_CU(sk_launch_grad_finish(acc, k->nt, 4.0 * SK_PI / (double)k->g->npix, out, st));
+    return SK_OK;
+}

@@ -1,0 +1,96 @@
+// skconv_host.h -- host-side handle structures and planner interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdarg.h>
+
+#include <string>
+#include <vector>
+
+#include "skconv.h"
+#include "skconv_internal.cuh"
+#include "skconv_launch.h"
+
+struct sk_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int *d_status = nullptr;       // device status word
+    void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
+    size_t ws_bytes = 0;
+    int occ_general = 0;           // cached blocks per SM
+};
+
+struct sk_geom {
+    sk_ctx *ctx = nullptr;
+    long long nside = 0, npix = 0;
+    int nr = 0;
+    RingDev *d_rings = nullptr;
+    double *d_z = nullptr, *d_rho = nullptr, *d_theta = nullptr;
+    std::vector<RingDev> h_rings;
+};
+
+struct sk_kern {
+    sk_ctx *ctx = nullptr;
+    const sk_geom *g = nullptr;
+    int nt = 0, layout = 0;
+    double tc = 0.0;
+    KernParams kp{};
+    double *d_V = nullptr;                 // FP64 node values
+    float2 *d_tab = nullptr;               // FP32 (value, slope) * dOmega
+    int *d_pair_off = nullptr;
+    PairInfo *d_pairs = nullptr;
+    double *d_dphimax = nullptr;
+    int n_pairs = 0;
+    std::vector<int> h_pair_off, h_lo, h_hi;
+    std::vector<PairInfo> h_pairs;
+
+    // every ring, 128 outputs per item: the per-pair path and the table gradient
+    int4 *d_items_all = nullptr;
+    int n_items_all = 0;
+
+    // plan of the specialised paths
+    bool plan_ok = false;
+    int4 *d_items_gen = nullptr;           // rings neither belt nor cap covers
+    int n_items_gen = 0;
+    // belt
+    int b_lo = 0, nb = 0, HM = 0, WPM = 0, EMIN = 0, EMAX = 0, ngroups = 0;
+    int belt_P = 13;
+    int2 *d_brng = nullptr, *d_bgrp = nullptr;
+    int4 *d_items_belt = nullptr;
+    int n_items_belt = 0;
+    // caps (one item list per strip class)
+    int4 *d_items_cap[SK_CAP_LS_CLASSES] = {nullptr, nullptr, nullptr};
+    int n_items_cap[SK_CAP_LS_CLASSES] = {0, 0, 0};
+    int n_cap_rings = 0;
+};
+
+// api.cu
+int sk_fail(int code, const char *fmt, ...);
+int sk_ctx_workspace(sk_ctx *ctx, size_t bytes, void **out);
+
+// plan.cu
+int sk_plan_build(sk_kern *k);
+void sk_plan_free(sk_kern *k);
+int sk_plan_rebuild_belt_items(sk_kern *k);
+size_t sk_plan_workspace_bytes(const sk_kern *k);
+
+// One job of a launch sequence.
+struct SkJob {
+    const sk_kern *k;
+    const float *x;
+    float *y;
+    long long batch, stride;
+};
+// Launch sequence of the forward operator for a set of jobs.  `ws` must hold
+// sk_jobs_workspace_bytes(jobs) bytes (belt weight rows).
+size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n);
+int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st);
+int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,
+                long long stride, float *out, double *acc, cudaStream_t st);
+
+#define SK_CU(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return sk_fail(e_ == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA,           \
+                           "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)

@@ -1,0 +1,90 @@
+// skconv_launch.h -- declarations shared by the library's .cu files: the job
+// table every convolution kernel receives by value, and the launchers.
+//
+// A launch processes a flat list of work items.  Items of job j occupy flat
+// indices [flat_base_j, flat_base_j + n_items_j * batch_j): map b of job j uses
+// the job's per-map item list again.  Blocks stride over the flat list, so a
+// launch is persistent (a grid sized to the GPU) and may mix jobs of different
+// Nside, kernels and batch sizes.
+#pragma once
+#include <cuda_runtime.h>
+#include "skconv_internal.cuh"
+
+constexpr int SK_MAXJ = 16;            // jobs per launch (more: several launches)
+constexpr int SK_MAX_NODES = 16384;    // largest kernel table
+constexpr int SK_BELT_G = 8;           // output rings per belt block (one warp each)
+constexpr int SK_BELT_STAGES = 4;      // input-ring strips in flight per belt block
+
+struct JobDesc {
+    // operator
+    const RingDev *rings;
+    const int *pair_off;
+    const PairInfo *pairs;
+    const float2 *tab;
+    KernParams kp;
+    int nr;
+    // maps
+    const float *x;
+    float *y;
+    long long stride;
+    int batch;
+    // this launch's items of the job (one map's worth) and their flat range
+    const int4 *items;
+    int n_items;
+    int flat_base;
+    // belt (Toeplitz) path
+    int b_lo;             // first belt output ring
+    int nb;               // belt output rings
+    int HM;               // max |input ring - output ring| over the belt
+    int WPM;              // weights per (output ring, input ring) row, multiple of 4
+    int EMIN, EMAX;       // pixel offset range of all belt windows
+    int n4;               // pixels per belt ring (4 Nside)
+    const int2 *brng;     // [nb_pad][2HM+1] (first offset, number of 4-chunks)
+    const float *bw;      // [nb_pad][2HM+1][WPM] weights (workspace, per call)
+    const int2 *bgrp;     // [groups] first and last input ring of each group
+    // cap path
+    int cap_ls;           // strip stride class
+};
+
+struct JobsArg {
+    int n_jobs;
+    int total;            // flat items over all jobs
+    int *status;          // device status word
+    JobDesc j[SK_MAXJ];
+};
+
+__device__ __forceinline__ int sk_find_job(const JobsArg &a, int f) {
+    int j = 0;
+    while (j + 1 < a.n_jobs && f >= a.j[j + 1].flat_base) ++j;
+    return j;
+}
+
+// set-up kernels (geometry.cu)
+cudaError_t sk_launch_ring_geom(long long nside, RingDev *rings, double *z, double *rho,
+                                double *theta, cudaStream_t st);
+cudaError_t sk_launch_pair_ranges(int nr, const double *theta, double tc, int *lo, int *hi,
+                                  cudaStream_t st);
+cudaError_t sk_launch_pair_info(int nr, const RingDev *rings, const double *z, const double *rho,
+                                const double *theta, const int *off, const int *lo, double tc,
+                                PairInfo *pairs, double *dphimax, cudaStream_t st);
+cudaError_t sk_launch_tabulate(const double *kl, int lmin, int lmax, int nt, double tc, int layout,
+                               double taper_start, double *V, cudaStream_t st);
+cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 *tab, cudaStream_t st);
+cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const int *off,
+                                  const PairInfo *pairs, const double *dphimax,
+                                  unsigned long long *total, cudaStream_t st);
+
+// convolution kernels; grid = number of blocks (persistent)
+cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);
+cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st);
+cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st);
+cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int grid, cudaStream_t st);
+int sk_belt_blocks_per_sm(const JobsArg &a, int P);
+int sk_cap_blocks_per_sm(int ls);
+constexpr int SK_CAP_LS_CLASSES = 3;
+constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {256, 512, 1024};   // strip strides of the cap path
+
+// table gradient (grad.cu)
+cudaError_t sk_launch_grad_general(const JobsArg &a, const float *gy, double *acc, int grid,
+                                   cudaStream_t st);
+cudaError_t sk_launch_grad_finish(const double *acc, int nt, double scale, float *out, cudaStream_t st);

@@ -1,0 +1,278 @@
+"""CUDA path against the FP64 oracle, through the C ABI (via the thin binding).
+
+Bar: rms relative error <= 1e-6 against the oracle on the same FP32 input
+promoted to FP64 and the same FP64 table (error budget: FP32 chord, asin
+series and table coordinate, each ~1e-7 relative; FP32 accumulation over a few
+hundred terms).  Integer results (ring tables, pair counts) are bit-exact.
+Inputs are seeded and synthetic (white-noise maps, Gaussian-beam kernels split
+at l_cut, point sources).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from inputs import (ARCMIN, WORKLOADS, add_point_sources, gaussian_beam, sample_indices,
+                    white_noise_maps)
+
+pytestmark = pytest.mark.gpu
+
+RMS_BOUND = 1e-6
+
+
+@pytest.fixture(scope="module")
+def sk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1211_3556_b300 as sk
+    sk._ctx = sk.Context(0)
+    yield sk
+    torch.cuda.synchronize()
+
+
+def rms_rel(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_conv(sk, kern, x, path=0):
+    import torch
+    xt = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    y = sk.convolve(kern, xt, path=path)
+    torch.cuda.synchronize()
+    sk._ctx.status()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def oracle_table(nside, fwhm, lmax, lcut, tc, nt, layout=0):
+    return O.tabulate_real_kernel(gaussian_beam(fwhm, lmax), lcut, lmax, tc, nt, layout)
+
+
+# ------------------------------------------------------------------ geometry
+
+@pytest.mark.parametrize("nside", [1, 2, 16, 64, 2048])
+def test_ring_tables_match_oracle(sk, nside):
+    g = sk.Geometry(sk._ctx, nside)
+    n, st, s, z, sn = g.rings()
+    for r in range(1, 4 * nside, max(1, (4 * nside) // 97)):
+        on, ost, os_, oz, osn = O.ring_info(nside, r)
+        assert (n[r - 1], st[r - 1], s[r - 1]) == (on, ost, os_)
+        assert z[r - 1] == pytest.approx(oz, abs=2e-16)
+        assert sn[r - 1] == pytest.approx(osn, abs=2e-16)
+
+
+# ------------------------------------------------------------------ tabulation
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_legendre_tabulation_matches_oracle(sk, layout):
+    g = sk.Geometry(sk._ctx, 64)
+    b = gaussian_beam(60.0, 192)
+    tc = 180 * ARCMIN
+    v_gpu = sk.Kernel.tabulate(g, b, 97, 192, 4096, tc, layout)
+    v_or = O.tabulate_real_kernel(b, 96, 192, tc, 4096, layout)
+    assert np.abs(v_gpu - v_or).max() <= 1e-11 * np.abs(v_or).max()
+
+
+def test_legendre_tabulation_high_l(sk):
+    g = sk.Geometry(sk._ctx, 64)
+    b = gaussian_beam(7.1, 4096)
+    tc = 20 * ARCMIN
+    v_gpu = sk.Kernel.tabulate(g, b, 1025, 4096, 512, tc, 0)
+    v_or = O.tabulate_real_kernel(b, 1024, 4096, tc, 512, 0)
+    assert np.abs(v_gpu - v_or).max() <= 1e-9 * np.abs(v_or).max()
+
+
+# ------------------------------------------------------------------ pair counts
+
+@pytest.mark.parametrize("nside,tc", [(4, 0.9), (8, 0.3), (16, 0.15), (64, 180 * ARCMIN), (32, 2.5)])
+def test_pair_count_exact(sk, nside, tc):
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, np.ones(16), tc)
+    assert k.count_pairs() == O.count_pairs(nside, tc)
+
+
+# ------------------------------------------------------------------ forward parity
+
+CASES = [
+    # nside, theta_cut, n_nodes, layout, path
+    (8, 0.35, 256, 0, 0), (8, 0.35, 256, 0, 1),
+    (16, 0.2, 512, 1, 0), (16, 1.2, 512, 0, 0),      # wide cut: whole-ring windows, no belt
+    (32, 0.08, 1024, 0, 0), (32, 0.08, 1024, 1, 1),
+    (64, 180 * ARCMIN, 4096, 0, 0), (64, 180 * ARCMIN, 4096, 0, 1),
+    (128, 0.03, 2048, 0, 0), (128, 0.03, 2048, 1, 0),
+    (256, 0.02, 4096, 0, 0),
+]
+
+
+@pytest.mark.parametrize("nside,tc,nt,layout,path", CASES)
+def test_forward_matches_oracle(sk, nside, tc, nt, layout, path):
+    lmax = 3 * nside
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, lmax, lmax // 4, tc, nt, layout)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc, layout)
+    x = white_noise_maps(nside, 1, 1000 + nside)
+    y = gpu_conv(sk, k, x, path)[0]
+    yo = O.conv_window(nside, V, tc, layout, x[0].astype(np.float64))
+    assert rms_rel(y, yo) <= RMS_BOUND
+    assert np.abs(y - yo).max() <= 1e-5 * np.abs(yo).max()
+
+
+def test_config_n64_full_map(sk):
+    wl = WORKLOADS["n64_plain"].groups[0]
+    ks = wl.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    g = sk.Geometry(sk._ctx, wl.nside)
+    k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+    x = white_noise_maps(wl.nside, 1, wl.seed)
+    y = gpu_conv(sk, k, x)[0]
+    yo = O.conv_window(wl.nside, V, ks.theta_cut, ks.layout, x[0].astype(np.float64))
+    assert rms_rel(y, yo) <= RMS_BOUND
+
+
+def _special_pixels(nside):
+    """Pole rings, the first pixel of rings (phi = 0 wrap), the z = +-2/3 rings, the equator."""
+    N = nside
+    rings = [1, 2, N - 1, N, N + 1, 2 * N - 1, 2 * N, 3 * N, 3 * N + 1, 4 * N - 2, 4 * N - 1]
+    pix = []
+    for r in rings:
+        n, st, *_ = O.ring_info(N, r)
+        pix += [st, st + n - 1, st + n // 4, st + n // 2 - 1]
+    return np.unique(np.array(pix, dtype=np.int64))
+
+
+@pytest.mark.parametrize("nside,tc", [(32, 0.12), (128, 0.04)])
+def test_delta_maps_at_special_pixels(sk, nside, tc):
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, 1024)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc)
+    pix = _special_pixels(nside)
+    x = np.zeros((len(pix), 12 * nside * nside), np.float32)
+    x[np.arange(len(pix)), pix] = 1.0
+    y = gpu_conv(sk, k, x)
+    for b, p in enumerate(pix):
+        yo = O.conv_window(nside, V, tc, 0, x[b].astype(np.float64))
+        assert rms_rel(y[b], yo) <= RMS_BOUND, (p, rms_rel(y[b], yo))
+
+
+def test_config_n2048_sampled_outputs(sk):
+    wl = WORKLOADS["n2048_plain"]
+    grp = wl.groups[0]
+    ks = grp.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    g = sk.Geometry(sk._ctx, grp.nside)
+    k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+    x = white_noise_maps(grp.nside, 1, grp.seed)
+    add_point_sources(x, *wl.sources[0])
+    y = gpu_conv(sk, k, x)[0]
+    outs = np.concatenate([sample_indices(x.shape[1], 20000, 203), _special_pixels(grp.nside)])
+    yo = O.conv_window(grp.nside, V, ks.theta_cut, ks.layout, x[0].astype(np.float64), outs)
+    assert rms_rel(y[outs], yo) <= RMS_BOUND
+
+
+# ------------------------------------------------------------------ batch, adjoint
+
+def test_batch_equals_single_maps(sk):
+    nside, tc = 128, 0.03
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 384, 96, tc, 2048)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc)
+    x = white_noise_maps(nside, 5, 77)
+    yb = gpu_conv(sk, k, x)
+    for b in range(5):
+        assert np.array_equal(yb[b], gpu_conv(sk, k, x[b:b + 1])[0])
+
+
+def test_adjoint_dot_product(sk):
+    import torch
+    nside, tc = 64, 0.06
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 192, 48, tc, 1024)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc)
+    x = torch.from_numpy(white_noise_maps(nside, 1, 5)).cuda()
+    yb = torch.from_numpy(white_noise_maps(nside, 1, 6)).cuda()
+    Ax = sk.convolve(k, x)
+    ATy = sk.convolve_adjoint(k, yb)
+    lhs = float((Ax.double() * yb.double()).sum())
+    rhs = float((x.double() * ATy.double()).sum())
+    assert abs(lhs - rhs) <= 1e-6 * float((Ax.double().abs() * yb.double().abs()).sum())
+
+
+# ------------------------------------------------------------------ table gradient
+
+@pytest.mark.parametrize("nside,tc,layout", [(16, 0.25, 0), (32, 0.1, 1)])
+def test_grad_table_matches_oracle(sk, nside, tc, layout):
+    import torch
+    nt = 64
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, nt, layout)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc, layout)
+    x = white_noise_maps(nside, 2, 21)
+    gy = white_noise_maps(nside, 2, 22)
+    gt = sk.grad_table(k, torch.from_numpy(x).cuda(), torch.from_numpy(gy).cuda())
+    torch.cuda.synchronize()
+    go = sum(O.grad_table(nside, nt, tc, layout, x[b].astype(np.float64), gy[b].astype(np.float64))
+             for b in range(2))
+    got = gt.cpu().numpy().astype(np.float64)
+    assert np.abs(got - go).max() <= 1e-5 * np.abs(go).max()
+
+
+# ------------------------------------------------------------------ jobs and graphs
+
+def _mixed_jobs(sk):
+    import torch
+    jobs, refs = [], []
+    for nside, tc, batch, seed in [(32, 0.1, 3, 31), (64, 0.05, 2, 32), (128, 0.03, 1, 33)]:
+        V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, 1024)
+        g = sk.Geometry(sk._ctx, nside)
+        k = sk.Kernel(g, V, tc)
+        x = torch.from_numpy(white_noise_maps(nside, batch, seed)).cuda()
+        y = torch.zeros_like(x)
+        jobs.append((k, x, y))
+        refs.append(sk.convolve(k, x))
+    return jobs, refs
+
+
+def test_jobs_equal_single_calls(sk):
+    import torch
+    jobs, refs = _mixed_jobs(sk)
+    sk.convolve_jobs(sk._ctx, jobs)
+    torch.cuda.synchronize()
+    for (k, x, y), r in zip(jobs, refs):
+        assert torch.equal(y, r)
+
+
+def test_graph_replay_equals_eager(sk):
+    import torch
+    jobs, refs = _mixed_jobs(sk)
+    gr = sk.Graph(sk._ctx, jobs)
+    for _ in range(2):
+        for (_, _, y) in jobs:
+            y.zero_()
+        gr.launch()
+        torch.cuda.synchronize()
+        for (k, x, y), r in zip(jobs, refs):
+            assert torch.equal(y, r)
+    gr.close()
+
+
+# ------------------------------------------------------------------ errors
+
+def test_argument_errors(sk):
+    import torch
+    g = sk.Geometry(sk._ctx, 16)
+    with pytest.raises(sk.SkError):
+        sk.Geometry(sk._ctx, 24)
+    with pytest.raises(sk.SkError):
+        sk.Kernel(g, np.ones(1), 0.1)
+    with pytest.raises(sk.SkError):
+        sk.Kernel(g, np.ones(8), -0.1)
+    k = sk.Kernel(g, np.ones(8), 0.1)
+    x = torch.zeros(1, 12 * 16 * 16, device="cuda")
+    with pytest.raises(sk.SkError):
+        sk.convolve(k, x, out=x)                          # aliasing
+    big = torch.zeros(1, 12 * 16 * 16 + 4, device="cuda")
+    with pytest.raises(sk.SkError):
+        sk.convolve(k, big[:, 1:1 + 12 * 16 * 16])        # misaligned map pointer
+    sk._ctx.status()
