@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the real-space HEALPix convolution (pixel pairs per second).
+
+One step = one pass of the whole forward operator (belt weight rows, belt
+Toeplitz sums, symmetric cap sums, any per-pair rings) over one batch of
+synthetic maps that are already resident in HBM.  The default workload is a
+single Planck-like map: Nside 2048 (50.3 M pixels), white noise plus 1000
+point sources of amplitude 100, Gaussian beam FWHM 7.1', l_max 4096, split at
+l_cut 1024, theta_cut 20', 8192-node table.  The map (201 MB) is larger than
+the 126 MB L2, so consecutive steps read it from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME]
+Under torchrun (N > 1) every rank convolves its own maps (weak scaling, no
+collective on the data path); the step time is the max over ranks.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from inputs import ARCMIN, WORKLOADS, make_maps, npix_of, sample_indices  # noqa: E402
+
+METRIC = "pixel-pairs/s and ms/map at Nside 2048, plain vs batched, rms err vs FP64"
+UNIT = "pixel-pairs/s"
+
+# FP32 issue peak of the B300 derived from its unit counts and clock: 148 SMs x
+# 128 FP32 lanes x 2 flop per FFMA x 2.032 GHz (maximum SM clock).
+SMS, LANES, MAX_GHZ = 148, 128, 2.032
+FP32_PEAK_TFLOPS = SMS * LANES * 2 * MAX_GHZ / 1e3
+# Algorithmic flops per in-cut pixel pair and map: the multiply-accumulate every
+# direct sum must do (the table lerp and chord are amortised by the belt and cap
+# paths, so they are not counted).
+FLOP_PER_PAIR = 2.0
+# Per-pair flops of a plain per-pair evaluation (chord 8, table coordinate 2,
+# lerp 2, multiply-accumulate 2), reported as f_eval for context.
+FLOP_PER_PAIR_EVAL = 14.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n2048_plain", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1])); smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def build_operator(sk, ctx, group):
+    ks = group.kernel
+    g = sk.Geometry(ctx, group.nside)
+    k, _ = sk.Kernel.from_legendre(g, ks.beam(), ks.lcut + 1, ks.lmax, ks.n_nodes, ks.theta_cut, ks.layout)
+    return g, k
+
+
+def time_steps(torch, fn, steps, warmup, barrier):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline_leg(wl, group, y_gpu_first_map, target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded random sample of output pixels of
+    the same workload (all host cores); also the rms error of the GPU result on
+    that sample against it."""
+    import oracle as O
+    ks = group.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    x = make_maps(group, wl.sources[0] if wl.sources else None)[0].astype(np.float64)
+    npx = npix_of(group.nside)
+    probe = sample_indices(npx, 2000, 9001)
+    t0 = time.perf_counter()
+    O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(npx, max(2000, 2000 * target_s / dt)))
+    outs = sample_indices(npx, n, 9002)
+    t0 = time.perf_counter()
+    yo = O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, outs)
+    dt = time.perf_counter() - t0
+    pairs = O.count_pairs(group.nside, ks.theta_cut, outs)
+    yg = y_gpu_first_map[outs].astype(np.float64)
+    rms = float(np.linalg.norm(yg - yo) / np.linalg.norm(yo))
+    return {"value": pairs / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} random output pixels of map 0 ({pairs} pairs), FP64 windowed direct sum, "
+                      f"{dt:.1f} s"}, rms
+
+
+def run_ours(args):
+    import torch
+    import paper_1211_3556_b300 as sk
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+
+    wl = WORKLOADS[args.workload]
+    ctx = sk.Context(local)
+    ops = []
+    for gi, group in enumerate(wl.groups):
+        g, k = build_operator(sk, ctx, group)
+        src = wl.sources[gi] if wl.sources and gi < len(wl.sources) else None
+        maps = make_maps(group, src)
+        if world > 1:                 # every rank convolves its own maps (weak scaling)
+            maps = np.ascontiguousarray(np.roll(maps, rank, axis=1))
+        x = torch.from_numpy(maps).cuda()
+        y = torch.empty_like(x)
+        pairs = k.count_pairs()
+        by_path = k.count_pairs_by_path()
+        ops.append(dict(group=group, geom=g, kern=k, x=x, y=y, maps=maps, pairs=pairs, by_path=by_path))
+    pairs_step = sum(o["pairs"] * o["group"].batch for o in ops)
+    maps_step = sum(o["group"].batch for o in ops)
+
+    if len(ops) == 1:
+        o = ops[0]
+
+        def step():
+            sk.convolve(o["kern"], o["x"], out=o["y"])
+    else:
+        jobs = [(o["kern"], o["x"], o["y"]) for o in ops]
+
+        def step():
+            sk.convolve_jobs(ctx, jobs)
+
+    # timed region: clocks sampled throughout, per-launch events recorded by the library
+    step()
+    torch.cuda.synchronize()
+    ctx.status()
+    for _ in range(args.warmup):
+        step()
+    ctx.profile(True)
+    ctx.profile_read()
+    sampler = ClockSampler(local)
+    ms = time_steps(torch, step, args.steps, 0, barrier)
+    clocks = sampler.stop()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ctx.status()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = pairs_step * world / (ms * 1e-3)
+    launches = sum(c for _, c in prof.values())
+
+    # roofline of the dominant kernel: F_mac flops per pair of the outputs it evaluates
+    dom = max(prof, key=lambda n: prof[n][0]) if prof else None
+    path_idx = {"conv_belt": 0, "conv_cap": 1, "conv_general": 2}
+    roofline = None
+    if dom in path_idx:
+        dom_pairs = sum(o["by_path"][path_idx[dom]] * o["group"].batch for o in ops)
+        launch_ms = prof[dom][0] / prof[dom][1]
+        per_launch_pairs = dom_pairs * args.steps / prof[dom][1]
+        achieved = FLOP_PER_PAIR * per_launch_pairs / (launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": None,
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                    "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if len(ops) == 1:
+        o = ops[0]
+        hx = torch.from_numpy(o["maps"]).pin_memory()
+        hy = torch.empty_like(hx).pin_memory()
+        hxn, hyn = hx.numpy(), hy.numpy()
+        sk.convolve_host(o["kern"], hxn, hyn)
+        k_e2e = max(3, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            sk.convolve_host(o["kern"], hxn, hyn)
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        nbytes = int(o["maps"].nbytes)
+        e2e = {"value": pairs_step * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
+               "api": "sk_convolve_host (pinned host buffers)"}
+        del hx, hy
+
+    # the batched form beside the plain one (64 maps at Nside 1024 sharing one kernel)
+    batched = None
+    if not args.no_batched and args.workload == "n2048_plain":
+        grp = WORKLOADS["n1024x64_batched"].groups[0]
+        gb, kb = build_operator(sk, ctx, grp)
+        xb = torch.from_numpy(make_maps(grp)).cuda()
+        yb = torch.empty_like(xb)
+        pb = kb.count_pairs()
+        msb = time_steps(torch, lambda: sk.convolve(kb, xb, out=yb), max(3, args.steps // 4), 2, barrier)
+        batched = {"workload": "n1024x64_batched", "value": pb * grp.batch / (msb * 1e-3), "unit": UNIT,
+                   "ms_per_map": msb / grp.batch, "ms_per_step": msb, "form": "fp32 belt+cap, weights shared by the batch"}
+        del xb, yb
+
+    o0 = ops[0]
+    y0 = o0["y"][0].cpu().numpy()
+    cpu_baseline, rms = None, None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu_baseline, rms = cpu_baseline_leg(wl, o0["group"], y0)
+
+    if rank == 0:
+        ks = o0["group"].kernel
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "ms_per_map": ms / maps_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "nside": [o["group"].nside for o in ops],
+                       "maps_per_gpu": maps_step, "theta_cut_arcmin": ks.theta_cut_arcmin,
+                       "n_nodes": ks.n_nodes, "fwhm_arcmin": ks.fwhm_arcmin, "lmax": ks.lmax, "lcut": ks.lcut,
+                       "pairs_per_step_per_gpu": pairs_step,
+                       "l2": "inputs larger than L2 (map bytes %d > 126 MB)" % int(sum(o["maps"].nbytes for o in ops)),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "rms_rel_vs_fp64": rms,
+            "f_eval": value / world * FLOP_PER_PAIR_EVAL / (FP32_PEAK_TFLOPS * 1e12),
+            "f_mac": value / world * FLOP_PER_PAIR / (FP32_PEAK_TFLOPS * 1e12),
+            "roofline": roofline,
+            "kernels": {n: {"ms_total": t, "launches": c, "ms_per_launch": t / c} for n, (t, c) in prof.items()},
+            "gpu_launches": launches,
+            "pairs_by_path": {"belt": o0["by_path"][0], "cap": o0["by_path"][1], "general": o0["by_path"][2]},
+            "clocks": clocks,
+            "e2e": e2e,
+            "batched": batched,
+            "cpu_baseline": cpu_baseline,
+            "context": "paper: GTX 480 + 1 Core2 core, split convolution >10x faster than a full "
+                       "single-core SHT convolution (eq. 3 model: 2.89 s at theta_cut 20')",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    wl = WORKLOADS[args.workload]
+    group = wl.groups[0]
+    ks = group.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    x = make_maps(group, wl.sources[0] if wl.sources else None)[0].astype(np.float64)
+    npx = npix_of(group.nside)
+    probe = sample_indices(npx, 1000, 8001)
+    t0 = time.perf_counter()
+    O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_step_s = max(1.0, 150.0 / (args.steps + args.warmup))
+    n = int(min(npx, max(1000, 1000 * per_step_s / dt)))
+    samples = [sample_indices(npx, n, 8100 + s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, samples[s])
+    pairs = 0
+    tt = 0.0
+    for s in range(args.warmup, args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, samples[s])
+        tt += time.perf_counter() - t0
+        pairs += O.count_pairs(group.nside, ks.theta_cut, samples[s])
+    value = pairs / tt
+    cores = O.num_threads()
+    sample = f"{n} random output pixels per step of map 0, FP64 windowed direct sum"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nside": [group.nside], "theta_cut_arcmin": ks.theta_cut_arcmin,
+                   "n_nodes": ks.n_nodes},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

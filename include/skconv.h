@@ -132,6 +132,12 @@ int sk_kernel_update_values(sk_kern *k, const double *h_values);
  * the device in FP64 from the per-ring-pair phi windows.  Blocks until done. */
 int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out);
 
+/* Pair counts split by the path that evaluates each output ring:
+ * out3[0] belt (ring-wise Toeplitz sums), out3[1] polar caps (8-fold
+ * symmetric per-pair evaluation), out3[2] per-pair general path.  Their sum is
+ * sk_count_pairs.  Blocks until done.  Errors: SK_EINVAL, SK_ECUDA. */
+int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3);
+
 /* ---- convolution --------------------------------------------------------- */
 
 /* y = A x for `batch` maps (the real-space convolution above).
@@ -191,6 +197,19 @@ int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int flags, voi
                      void **graph_exec);
 int sk_graph_launch(void *graph_exec, void *stream);
 int sk_graph_destroy(void *graph_exec);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Turn per-launch timing on or off for the context.  While on, every kernel the
+ * library launches is bracketed by CUDA events on its stream (no work changes). */
+int sk_profile_enable(sk_ctx *ctx, int on);
+
+/* Collect the recorded launches (synchronising on their events) and clear
+ * them: per kernel name, total milliseconds and launch count.  names receives
+ * up to max_kernels NUL-terminated names of 32 bytes each.  *n_kernels is the
+ * number of distinct kernels seen. */
+int sk_profile_read(sk_ctx *ctx, int max_kernels, char *names, double *ms, int *launches,
+                    int *n_kernels);
 
 /* ---- tuning -------------------------------------------------------------- */
 

@@ -60,6 +60,9 @@ def _declare(L):
         "sk_kernel_update_values": (I, [P, P]),
         "sk_kernel_destroy": (I, [P]),
         "sk_count_pairs": (I, [P, P, ctypes.POINTER(I64)]),
+        "sk_count_pairs_by_path": (I, [P, P, ctypes.POINTER(I64)]),
+        "sk_profile_enable": (I, [P, I]),
+        "sk_profile_read": (I, [P, I, P, P, P, ctypes.POINTER(I)]),
         "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
         "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
         "sk_convolve_adjoint": (I, [P, P, P, P, I64, I64, P]),
@@ -135,6 +138,21 @@ class Context:
 
     def status(self, stream=None):
         _check(lib().sk_get_status(self._h, _stream_ptr(stream)))
+
+    def profile(self, on: bool):
+        _check(lib().sk_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} of the launches recorded since the last read."""
+        m = 32
+        names = ctypes.create_string_buffer(32 * m)
+        ms = np.zeros(m); cnt = np.zeros(m, np.int32); n = ctypes.c_int()
+        _check(lib().sk_profile_read(self._h, m, names, ms.ctypes.data, cnt.ctypes.data, ctypes.byref(n)))
+        out = {}
+        for i in range(min(n.value, m)):
+            nm = names.raw[32 * i: 32 * i + 32].split(b"\0")[0].decode()
+            out[nm] = (float(ms[i]), int(cnt[i]))
+        return out
 
 
 class Geometry:
@@ -227,6 +245,12 @@ class Kernel:
         c = ctypes.c_int64()
         _check(lib().sk_count_pairs(self.ctx._h, self._h, ctypes.byref(c)))
         return c.value
+
+    def count_pairs_by_path(self):
+        """(belt, cap, general) in-cut pair counts of the outputs each path evaluates."""
+        c = (ctypes.c_int64 * 3)()
+        _check(lib().sk_count_pairs_by_path(self.ctx._h, self._h, c))
+        return int(c[0]), int(c[1]), int(c[2])
 
     def set_tiles(self, belt_p=0, cap_t=0):
         _check(lib().sk_kernel_set_tiles(self._h, belt_p, cap_t))
@@ -363,6 +387,7 @@ def _make_autograd():
                 kern.update_values(v)
             ctx.kern = kern
             ctx.table_dtype = table.dtype
+            ctx.table_device = table.device
             ctx.save_for_backward(x)
             return convolve(kern, x.contiguous())
 
@@ -373,7 +398,8 @@ def _make_autograd():
             gx = convolve_adjoint(ctx.kern, gy) if ctx.needs_input_grad[0] else None
             gt = None
             if ctx.needs_input_grad[1]:
-                gt = grad_table(ctx.kern, x.contiguous(), gy).to(ctx.table_dtype)
+                gt = grad_table(ctx.kern, x.contiguous(), gy).to(device=ctx.table_device,
+                                                                  dtype=ctx.table_dtype)
             return gx, gt, None
 
     return SphConv

@@ -78,6 +78,59 @@ extern "C" int sk_destroy(sk_ctx *ctx) {
     return SK_OK;
 }
 
+cudaEvent_t sk_prof_begin(sk_ctx *ctx, cudaStream_t st) {
+    if (!ctx->prof) return nullptr;
+    cudaEvent_t a = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+    cudaEventRecord(a, st);
+    return a;
+}
+
+void sk_prof_end(sk_ctx *ctx, const char *name, cudaEvent_t a, cudaStream_t st) {
+    if (!ctx->prof || !a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    cudaEventRecord(b, st);
+    ctx->prof_recs.push_back({name, a, b});
+}
+
+extern "C" int sk_profile_enable(sk_ctx *ctx, int on) {
+    if (!ctx) return sk_fail(SK_EINVAL, "sk_profile_enable: NULL context");
+    ctx->prof = on != 0;
+    return SK_OK;
+}
+
+extern "C" int sk_profile_read(sk_ctx *ctx, int max_kernels, char *names, double *ms, int *launches,
+                               int *n_kernels) {
+    if (!ctx || !n_kernels) return sk_fail(SK_EINVAL, "sk_profile_read: NULL argument");
+    SK_CU(cudaSetDevice(ctx->device));
+    std::vector<std::string> nm;
+    std::vector<double> tot;
+    std::vector<int> cnt;
+    int rc = SK_OK;
+    for (auto &r : ctx->prof_recs) {
+        float t = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            rc = sk_fail(SK_ECUDA, "sk_profile_read: event failed");
+        size_t i = 0;
+        while (i < nm.size() && nm[i] != r.name) ++i;
+        if (i == nm.size()) { nm.push_back(r.name); tot.push_back(0.0); cnt.push_back(0); }
+        tot[i] += t;
+        cnt[i] += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    ctx->prof_recs.clear();
+    int n = (int)nm.size();
+    *n_kernels = n;
+    for (int i = 0; i < n && i < max_kernels; ++i) {
+        if (names) { strncpy(names + 32 * i, nm[i].c_str(), 31); names[32 * i + 31] = 0; }
+        if (ms) ms[i] = tot[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    return rc;
+}
+
 extern "C" int sk_get_status(sk_ctx *ctx, void *stream) {
     if (!ctx) return sk_fail(SK_EINVAL, "sk_get_status: NULL context");
     SK_CU(cudaSetDevice(ctx->device));
@@ -155,7 +208,7 @@ extern "C" int sk_geometry_rings(const sk_geom *g, int32_t *h_n, int64_t *h_star
 static void free_kern(sk_kern *k) {
     if (!k) return;
     cudaFree(k->d_V); cudaFree(k->d_tab); cudaFree(k->d_pair_off); cudaFree(k->d_pairs);
-    cudaFree(k->d_dphimax); cudaFree(k->d_items_all);
+    cudaFree(k->d_dphimax); cudaFree(k->d_items_all); cudaFree(k->d_ab64);
     sk_plan_free(k);
     delete k;
 }
@@ -205,6 +258,18 @@ static int finish_kernel(sk_kern *k) {
         kp.Mf = (float)M;
     }
     kp.small_angle = tc <= 0.25 ? 1 : 0;
+    KernParams64 &kd = k->kd;
+    kd.tcut = 4.0 * sh * sh;
+    if (k->layout == SK_NODES_UNIFORM) {
+        kd.inv_h = (double)(nt - 1) / tc;
+        kd.t1 = 0.0; kd.inv_h2 = 0.0; kd.Mf = 0.0;
+    } else {
+        const int M = nt / 2;
+        kd.t1 = tc / 16.0;
+        kd.inv_h = (double)M / kd.t1;
+        kd.inv_h2 = (double)(nt - 1 - M) / (tc - kd.t1);
+        kd.Mf = (double)M;
+    }
 
     int *d_lo = nullptr, *d_hi = nullptr;
     SK_CU(cudaMalloc(&d_lo, sizeof(int) * nr));
@@ -222,10 +287,11 @@ static int finish_kernel(sk_kern *k) {
     }
     if (e == cudaSuccess) e = cudaMalloc(&k->d_pairs, sizeof(PairInfo) * k->n_pairs);
     if (e == cudaSuccess) e = cudaMalloc(&k->d_dphimax, sizeof(double) * k->n_pairs);
+    if (e == cudaSuccess) e = cudaMalloc(&k->d_ab64, sizeof(double2) * k->n_pairs);
     if (e == cudaSuccess) e = cudaMemcpy(k->d_pair_off, k->h_pair_off.data(), sizeof(int) * (nr + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = sk_launch_pair_info(nr, g->d_rings, g->d_z, g->d_rho, g->d_theta, k->d_pair_off, d_lo, tc,
-                                k->d_pairs, k->d_dphimax, 0);
+                                k->d_pairs, k->d_dphimax, k->d_ab64, 0);
     if (e == cudaSuccess) {
         k->h_pairs.resize(k->n_pairs);
         e = cudaMemcpy(k->h_pairs.data(), k->d_pairs, sizeof(PairInfo) * k->n_pairs, cudaMemcpyDeviceToHost);
@@ -328,12 +394,30 @@ extern "C" int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out) {
     cudaError_t e = cudaMemset(d_total, 0, sizeof(unsigned long long));
     if (e == cudaSuccess)
         e = sk_launch_count_pairs(k->g->nr, (int)(4 * k->g->nside), k->g->d_rings, k->d_pair_off, k->d_pairs,
-                                  k->d_dphimax, d_total, 0);
+                                  k->d_dphimax, nullptr, d_total, 0);
     unsigned long long h = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h, d_total, sizeof h, cudaMemcpyDeviceToHost);
     cudaFree(d_total);
     if (e != cudaSuccess) return sk_fail(SK_ECUDA, "sk_count_pairs: %s", cudaGetErrorString(e));
     *out = (int64_t)h;
+    return SK_OK;
+}
+
+extern "C" int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3) {
+    if (!ctx || !k || !out3) return sk_fail(SK_EINVAL, "sk_count_pairs_by_path: NULL argument");
+    if (!k->plan_ok) return sk_fail(SK_EUNSUPPORTED, "operator has no plan");
+    SK_CU(cudaSetDevice(ctx->device));
+    unsigned long long *d_total = nullptr;
+    SK_CU(cudaMalloc(&d_total, 3 * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemset(d_total, 0, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = sk_launch_count_pairs(k->g->nr, (int)(4 * k->g->nside), k->g->d_rings, k->d_pair_off, k->d_pairs,
+                                  k->d_dphimax, k->d_ring_path, d_total, 0);
+    unsigned long long h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d_total, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d_total);
+    if (e != cudaSuccess) return sk_fail(SK_ECUDA, "sk_count_pairs_by_path: %s", cudaGetErrorString(e));
+    for (int i = 0; i < 3; ++i) out3[i] = (int64_t)h[i];
     return SK_OK;
 }
 

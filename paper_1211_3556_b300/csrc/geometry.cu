@@ -62,7 +62,7 @@ __device__ double window_hav(double tc, double tho, double thi, double ro, doubl
 
 __global__ void k_pair_info(int nr, const RingDev *rings, const double *z, const double *rho,
                             const double *theta, const int *off, const int *lo, double tc,
-                            PairInfo *pairs, double *dphimax) {
+                            PairInfo *pairs, double *dphimax, double2 *ab64) {
     int o = blockIdx.x;
     if (o >= nr) return;
     int cnt = off[o + 1] - off[o];
@@ -72,8 +72,10 @@ __global__ void k_pair_info(int nr, const RingDev *rings, const double *z, const
         P.ri = i;
         P.n_i = rings[i].n; P.s_i = rings[i].s; P.pad = 0;
         double dz = z[o] - z[i], dr = rho[o] - rho[i];
-        P.A = (float)(dz * dz + dr * dr);
-        P.B = (float)(4.0 * rho[o] * rho[i]);
+        const double A = dz * dz + dr * dr, B = 4.0 * rho[o] * rho[i];
+        P.A = (float)A;
+        P.B = (float)B;
+        if (ab64) ab64[off[o] + t] = make_double2(A, B);
         P.c0 = (float)(SK_PI / (2.0 * (double)rings[i].n * (double)rings[o].n));
         double h = window_hav(tc, theta[o], theta[i], rho[o], rho[i]);
         double dpm;
@@ -134,7 +136,7 @@ __global__ void k_make_table(const double *V, int nt, double dOmega, float2 *tab
 // Exact pair count: on ring i the in-cut pixels of output (o, jo) are those with
 // |phi_j - phi_o| <= dphi_max (gamma grows with |dphi|), an integer interval.
 __global__ void k_count_pairs(int nr, const RingDev *rings, const int *off, const PairInfo *pairs,
-                              const double *dphimax, unsigned long long *total) {
+                              const double *dphimax, const unsigned char *cls, unsigned long long *total) {
     int o = blockIdx.y;
     int jo = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long c = 0;
@@ -161,7 +163,7 @@ __global__ void k_count_pairs(int nr, const RingDev *rings, const int *off, cons
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && red[0]) atomicAdd(total, red[0]);
+    if (threadIdx.x == 0 && red[0]) atomicAdd(total + (cls && o < nr ? cls[o] : 0), red[0]);
 }
 
 }  // namespace
@@ -181,8 +183,8 @@ cudaError_t sk_launch_pair_ranges(int nr, const double *theta, double tc, int *l
 
 cudaError_t sk_launch_pair_info(int nr, const RingDev *rings, const double *z, const double *rho,
                                 const double *theta, const int *off, const int *lo, double tc,
-                                PairInfo *pairs, double *dphimax, cudaStream_t st) {
-    k_pair_info<<<nr, 64, 0, st>>>(nr, rings, z, rho, theta, off, lo, tc, pairs, dphimax);
+                                PairInfo *pairs, double *dphimax, double2 *ab64, cudaStream_t st) {
+    k_pair_info<<<nr, 64, 0, st>>>(nr, rings, z, rho, theta, off, lo, tc, pairs, dphimax, ab64);
     return cudaGetLastError();
 }
 
@@ -198,9 +200,9 @@ cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 
 }
 
 cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const int *off,
-                                  const PairInfo *pairs, const double *dphimax,
+                                  const PairInfo *pairs, const double *dphimax, const unsigned char *cls,
                                   unsigned long long *total, cudaStream_t st) {
     dim3 grid((max_n + 255) / 256, nr);
-    k_count_pairs<<<grid, 256, 0, st>>>(nr, rings, off, pairs, dphimax, total);
+    k_count_pairs<<<grid, 256, 0, st>>>(nr, rings, off, pairs, dphimax, cls, total);
     return cudaGetLastError();
 }

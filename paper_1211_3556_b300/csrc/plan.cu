@@ -59,6 +59,7 @@ int belt_cost_p(int n4) {
 
 void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_items_gen); k->d_items_gen = nullptr;
+    cudaFree(k->d_ring_path); k->d_ring_path = nullptr;
     cudaFree(k->d_brng); k->d_brng = nullptr;
     cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
     cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
@@ -194,9 +195,14 @@ int sk_plan_build(sk_kern *k) {
 
     // ---- general: the rest
     std::vector<int4> gen;
+    std::vector<unsigned char> path(nr, 1);
+    for (int r = b_lo; r < b_lo + k->nb; ++r) path[r] = 0;
     for (int r = 0; r < nr; ++r)
-        if (!covered[r])
+        if (!covered[r]) {
+            path[r] = 2;
             for (int j = 0; j < R[r].n; j += 128) gen.push_back(make_int4(r, j, 0, 0));
+        }
+    if (int rc0 = upload(path, &k->d_ring_path)) return rc0;
     k->n_items_gen = (int)gen.size();
     int rc = upload(gen, &k->d_items_gen);
     if (rc) return rc;
@@ -231,6 +237,8 @@ JobDesc base_desc(const SkJob &jb) {
     d.pairs = k->d_pairs;
     d.tab = k->d_tab;
     d.kp = k->kp;
+    d.kd = k->kd;
+    d.ab64 = k->d_ab64;
     d.nr = k->g->nr;
     d.x = jb.x;
     d.y = jb.y;
@@ -275,7 +283,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             JobDesc d = base_desc(jobs[i]);
             d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
             d.brng = k->d_brng;
+            cudaEvent_t ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_belt_weights(d, wrows[i], st));
+            sk_prof_end(ctx, "belt_weights", ev, st);
         }
     }
 
@@ -284,7 +294,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         auto flush = [&]() -> int {
             if (b.a.total > 0) {
                 b.a.status = ctx->d_status;
+                cudaEvent_t ev = sk_prof_begin(ctx, st);
                 SK_CU(sk_launch_conv_general(b.a, grid_for(b.a.total, 16, ctx->num_sms), st));
+                sk_prof_end(ctx, "conv_general", ev, st);
             }
             b.reset();
             return SK_OK;
@@ -305,7 +317,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (b.a.total > 0) {
                 b.a.status = ctx->d_status;
                 int per = sk_belt_blocks_per_sm(b.a, P);
+                cudaEvent_t ev = sk_prof_begin(ctx, st);
                 SK_CU(sk_launch_conv_belt(b.a, P, grid_for(b.a.total, per, ctx->num_sms), st));
+                sk_prof_end(ctx, "conv_belt", ev, st);
             }
             b.reset();
             return SK_OK;
@@ -331,7 +345,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (b.a.total > 0) {
                 b.a.status = ctx->d_status;
                 int per = sk_cap_blocks_per_sm(SK_CAP_LS[c]);
+                cudaEvent_t ev = sk_prof_begin(ctx, st);
                 SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], grid_for(b.a.total, per, ctx->num_sms), st));
+                sk_prof_end(ctx, "conv_cap", ev, st);
             }
             b.reset();
             return SK_OK;
@@ -354,7 +370,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         auto flush = [&]() -> int {
             if (b.a.total > 0) {
                 b.a.status = ctx->d_status;
+                cudaEvent_t ev = sk_prof_begin(ctx, st);
                 SK_CU(sk_launch_conv_general(b.a, grid_for(b.a.total, 16, ctx->num_sms), st));
+                sk_prof_end(ctx, "conv_general", ev, st);
             }
             b.reset();
             return SK_OK;
@@ -382,7 +400,9 @@ int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, 
         Batcher b;
         b.add(base_desc(jb), k->d_items_all, k->n_items_all);
         b.a.status = ctx->d_status;
+        cudaEvent_t ev = sk_prof_begin(ctx, st);
         SK_CU(sk_launch_grad_general(b.a, gy, acc, grid_for(b.a.total, 8, ctx->num_sms), st));
+        sk_prof_end(ctx, "grad_general", ev, st);
     }
     SK_CU(sk_launch_grad_finish(acc, k->nt, 4.0 * SK_PI / (double)k->g->npix, out, st));
     return SK_OK;

@@ -16,7 +16,10 @@ struct sk_ctx {
     int *d_status = nullptr;       // device status word
     void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
     size_t ws_bytes = 0;
-    int occ_general = 0;           // cached blocks per SM
+    // optional per-launch timing (sk_profile_enable): events around each kernel
+    bool prof = false;
+    struct ProfRec { const char *name; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_recs;
 };
 
 struct sk_geom {
@@ -39,6 +42,8 @@ struct sk_kern {
     int *d_pair_off = nullptr;
     PairInfo *d_pairs = nullptr;
     double *d_dphimax = nullptr;
+    double2 *d_ab64 = nullptr;             // FP64 chord coefficients per pair (table gradient)
+    KernParams64 kd{};
     int n_pairs = 0;
     std::vector<int> h_pair_off, h_lo, h_hi;
     std::vector<PairInfo> h_pairs;
@@ -61,10 +66,13 @@ struct sk_kern {
     int4 *d_items_cap[SK_CAP_LS_CLASSES] = {nullptr, nullptr, nullptr};
     int n_items_cap[SK_CAP_LS_CLASSES] = {0, 0, 0};
     int n_cap_rings = 0;
+    unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere), 2 general
 };
 
 // api.cu
 int sk_fail(int code, const char *fmt, ...);
+cudaEvent_t sk_prof_begin(sk_ctx *ctx, cudaStream_t st);
+void sk_prof_end(sk_ctx *ctx, const char *name, cudaEvent_t a, cudaStream_t st);
 int sk_ctx_workspace(sk_ctx *ctx, size_t bytes, void **out);
 
 // plan.cu

@@ -22,6 +22,8 @@ struct JobDesc {
     const PairInfo *pairs;
     const float2 *tab;
     KernParams kp;
+    KernParams64 kd;          // table gradient only
+    const double2 *ab64;      // table gradient only: FP64 (A, B) per pair
     int nr;
     // maps
     const float *x;
@@ -66,12 +68,12 @@ cudaError_t sk_launch_pair_ranges(int nr, const double *theta, double tc, int *l
                                   cudaStream_t st);
 cudaError_t sk_launch_pair_info(int nr, const RingDev *rings, const double *z, const double *rho,
                                 const double *theta, const int *off, const int *lo, double tc,
-                                PairInfo *pairs, double *dphimax, cudaStream_t st);
+                                PairInfo *pairs, double *dphimax, double2 *ab64, cudaStream_t st);
 cudaError_t sk_launch_tabulate(const double *kl, int lmin, int lmax, int nt, double tc, int layout,
                                double taper_start, double *V, cudaStream_t st);
 cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 *tab, cudaStream_t st);
 cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const int *off,
-                                  const PairInfo *pairs, const double *dphimax,
+                                  const PairInfo *pairs, const double *dphimax, const unsigned char *cls,
                                   unsigned long long *total, cudaStream_t st);
 
 // convolution kernels; grid = number of blocks (persistent)

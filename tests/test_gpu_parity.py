@@ -201,10 +201,10 @@ def test_adjoint_dot_product(sk):
 
 # ------------------------------------------------------------------ table gradient
 
-@pytest.mark.parametrize("nside,tc,layout", [(16, 0.25, 0), (32, 0.1, 1)])
-def test_grad_table_matches_oracle(sk, nside, tc, layout):
+@pytest.mark.parametrize("nside,tc,layout,nt", [(16, 0.25, 0, 64), (32, 0.1, 1, 64), (32, 0.12, 0, 512),
+                                                 (64, 0.05, 0, 4096)])
+def test_grad_table_matches_oracle(sk, nside, tc, layout, nt):
     import torch
-    nt = 64
     V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, nt, layout)
     g = sk.Geometry(sk._ctx, nside)
     k = sk.Kernel(g, V, tc, layout)
