@@ -258,6 +258,12 @@ static int finish_kernel(sk_kern *k) {
         kp.Mf = (float)M;
     }
     kp.small_angle = tc <= 0.25 ? 1 : 0;
+    {
+        const double coef[5] = {1.0, 1.0 / 24.0, 3.0 / 640.0, 5.0 / 7168.0, 35.0 / 294912.0};
+        const double ih = (double)(nt - 1) / tc;       // uniform layout only
+        for (int i = 0; i < 5; ++i) kp.sa[i] = (float)(ih * coef[i]);
+        kp.umax = (float)(nt - 1) - 1.0f / 256.0f;
+    }
     KernParams64 &kd = k->kd;
     kd.tcut = 4.0 * sh * sh;
     if (k->layout == SK_NODES_UNIFORM) {

@@ -11,18 +11,22 @@
 // path (the real-space convolution of Sec. 2, Eq. 1, tabulated kernel of
 // Sec. 3); only the order of work differs.
 //
-// Work item: (northern output ring, first quarter-ring pixel) for 128 outputs.
+// Work item: (northern output ring, first quarter-ring pixel) for CT outputs.
 // For each input ring of the window the block stages 8 strips (4 rotations x
-// 2 hemispheres, each the union of the 128 outputs' phi windows, unwrapped)
+// 2 hemispheres, each the union of the CT outputs' phi windows, unwrapped)
 // into shared memory with cp.async, double-buffered; a strip row has LS
 // floats, so the 8 images of one input pixel sit at fixed offsets k * LS.
+// The kernel table sits in shared memory too: the lanes of a warp look up
+// nodes spread over a few hundred entries, a gather that costs one L1
+// wavefront per distinct 128-byte line from global memory but only a few
+// bank-conflict wavefronts from shared memory.
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
 
 namespace {
 
-constexpr int CT = 128;
+constexpr int CT = SK_CAP_CT;
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -31,9 +35,16 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Nearest input pixel of quarter-ring output jo.  In the caps jo < n_o / 4 <= 2 Nside and
+// n_i <= 4 Nside <= 32768, so the numerator stays below 2^31 and 32-bit arithmetic is exact.
 __device__ __forceinline__ int centre_of(int jo, int n_o, int s_o, const PairInfo &P) {
-    long long num = (long long)(2 * jo + s_o) * P.n_i + (long long)(1 - P.s_i) * n_o;
-    return (int)(num / (2LL * n_o));
+    const unsigned num = (unsigned)(2 * jo + s_o) * (unsigned)P.n_i + (unsigned)(1 - P.s_i) * (unsigned)n_o;
+    return (int)(num / (2u * (unsigned)n_o));
+}
+
+// q of window pixel jlo (may be negative) for output jo: both products are below 2^31.
+__device__ __forceinline__ int q_of(int jlo, int jo, int n_o, int s_o, const PairInfo &P) {
+    return (2 * jlo + P.s_i) * n_o - (2 * jo + s_o) * P.n_i;
 }
 
 // Window start relative to the centre, and length, of input ring P.
@@ -59,13 +70,23 @@ __device__ __forceinline__ void stage_ring(float *buf, const JobDesc &J, const f
     }
 }
 
-template <int LS>
+template <int LS, int MODE>
 __global__ void __launch_bounds__(CT)
 k_conv_cap(const __grid_constant__ JobsArg A) {
-    extern __shared__ __align__(16) float sx[];       // [2][8][LS]
+    constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
+    extern __shared__ __align__(16) float sx[];       // [2][8][LS] strips, then the table
+    float2 *stab = reinterpret_cast<float2 *>(sx + 2 * 8 * LS);
     const int t = threadIdx.x;
+    int cur_job = -1;
     for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
-        const JobDesc &J = A.j[sk_find_job(A, f)];
+        const int jn = sk_find_job(A, f);
+        const JobDesc &J = A.j[jn];
+        if (jn != cur_job) {                 // uniform across the block
+            __syncthreads();
+            for (int k = t; k < J.kp.nt; k += CT) stab[k] = J.tab[k];
+            __syncthreads();
+            cur_job = jn;
+        }
         const int local = f - J.flat_base;
         const int map = local / J.n_items;
         const int4 it = J.items[local - map * J.n_items];
@@ -111,13 +132,15 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const int cb = centre_of(j0, R.n, R.s, P);
                 const int c = centre_of(jo, R.n, R.s, P);
                 const int jlo = c - before;
-                // |q| < 2^24 on this window (checked when the plan was built): exact in FP32
-                float qf = (float)pair_q(jlo, jo, R.n, R.s, P);
+                // |q| < 2^24 on this window (checked when the plan was built): q = qf + m dq
+                // is exact in FP32
+                const float qf = (float)q_of(jlo, jo, R.n, R.s, P);
                 const float dq = (float)(2 * R.n);
                 const float *xs = sx + buf * 8 * LS + (c - cb);
+#pragma unroll 2
                 for (int m = 0; m < cnt; ++m) {
-                    const float w = pair_weight(qf * P.c0, P.A, P.B, J.kp, J.tab);
-                    qf += dq;
+                    const float w = fast_weight<SERIES, SMALLA, BIASED>(fmaf((float)m, dq, qf) * P.c0,
+                                                                        P.A, P.B, J.kp, stab);
 #pragma unroll
                     for (int s = 0; s < 8; ++s) acc[s] = fmaf(w, xs[s * LS + m], acc[s]);
                 }
@@ -136,41 +159,79 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
     }
 }
 
-template <int LS>
-cudaError_t launch_ls(const JobsArg &a, int grid, cudaStream_t st) {
-    const size_t smem = (size_t)2 * 8 * LS * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+size_t cap_smem(int LS, int nt) { return (size_t)2 * 8 * LS * sizeof(float) + (size_t)nt * sizeof(float2); }
+
+int max_nt(const JobsArg &a) {
+    int m = 2;
+    for (int j = 0; j < a.n_jobs; ++j) m = a.j[j].kp.nt > m ? a.j[j].kp.nt : m;
+    return m;
+}
+
+template <int LS, int MODE>
+cudaError_t launch_lm(const JobsArg &a, int grid, cudaStream_t st) {
+    const size_t smem = cap_smem(LS, max_nt(a));
+    cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_cap<LS><<<grid, CT, smem, st>>>(a);
+    k_conv_cap<LS, MODE><<<grid, CT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int LS>
-int occupancy_ls() {
-    const size_t smem = (size_t)2 * 8 * LS * sizeof(float);
-    cudaFuncSetAttribute(k_conv_cap<LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int LS, int MODE>
+int occupancy_lm(int nt) {
+    const size_t smem = cap_smem(LS, nt);
+    cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS>, CT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE>, CT, smem);
     return nb;
 }
 
-}  // namespace
-
-cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int grid, cudaStream_t st) {
-    if (a.total <= 0) return cudaSuccess;
-    switch (ls) {
-        case 256: return launch_ls<256>(a, grid, st);
-        case 512: return launch_ls<512>(a, grid, st);
-        case 1024: return launch_ls<1024>(a, grid, st);
+template <int LS>
+cudaError_t launch_ls(const JobsArg &a, int mode, int grid, cudaStream_t st) {
+    switch (mode) {
+        case 0: return launch_lm<LS, 0>(a, grid, st);
+        case 1: return launch_lm<LS, 1>(a, grid, st);
+        case 2: return launch_lm<LS, 2>(a, grid, st);
+        case 3: return launch_lm<LS, 3>(a, grid, st);
+        case 4: return launch_lm<LS, 4>(a, grid, st);
+        case 5: return launch_lm<LS, 5>(a, grid, st);
+        case 6: return launch_lm<LS, 6>(a, grid, st);
+        case 7: return launch_lm<LS, 7>(a, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-int sk_cap_blocks_per_sm(int ls) {
+template <int LS>
+int occupancy_ls(int mode, int nt) {
+    switch (mode) {
+        case 0: return occupancy_lm<LS, 0>(nt);
+        case 1: return occupancy_lm<LS, 1>(nt);
+        case 2: return occupancy_lm<LS, 2>(nt);
+        case 3: return occupancy_lm<LS, 3>(nt);
+        case 4: return occupancy_lm<LS, 4>(nt);
+        case 5: return occupancy_lm<LS, 5>(nt);
+        case 6: return occupancy_lm<LS, 6>(nt);
+        case 7: return occupancy_lm<LS, 7>(nt);
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cudaStream_t st) {
+    if (a.total <= 0) return cudaSuccess;
     switch (ls) {
-        case 256: return occupancy_ls<256>();
-        case 512: return occupancy_ls<512>();
-        case 1024: return occupancy_ls<1024>();
+        case SK_CAP_LS[0]: return launch_ls<SK_CAP_LS[0]>(a, mode, grid, st);
+        case SK_CAP_LS[1]: return launch_ls<SK_CAP_LS[1]>(a, mode, grid, st);
+        case SK_CAP_LS[2]: return launch_ls<SK_CAP_LS[2]>(a, mode, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int sk_cap_blocks_per_sm(int ls, int mode, int nt) {
+    switch (ls) {
+        case SK_CAP_LS[0]: return occupancy_ls<SK_CAP_LS[0]>(mode, nt);
+        case SK_CAP_LS[1]: return occupancy_ls<SK_CAP_LS[1]>(mode, nt);
+        case SK_CAP_LS[2]: return occupancy_ls<SK_CAP_LS[2]>(mode, nt);
         default: return 0;
     }
 }

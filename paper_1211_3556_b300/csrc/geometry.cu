@@ -86,7 +86,8 @@ __global__ void k_pair_info(int nr, const RingDev *rings, const double *z, const
             dpm = 2.0 * asin(sqrt(hc));
             double D = dpm * (double)P.n_i / (2.0 * SK_PI);
             if (h < 0.0) dpm = -1.0;      // no pixel of this ring is within the cut
-            long long W = (long long)floor(D + 0.5) + 1;
+            // nearest-pixel centre c: |j - jc| <= D implies |j - c| <= D + 1/2
+            long long W = (long long)floor(D + 0.5 + 1e-9);
             if (2 * W + 1 >= P.n_i) P.W = -1; else P.W = (int)W;
         }
         pairs[off[o] + t] = P;

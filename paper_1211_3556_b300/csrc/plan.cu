@@ -63,7 +63,8 @@ void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_brng); k->d_brng = nullptr;
     cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
     cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
-    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c) { cudaFree(k->d_items_cap[c]); k->d_items_cap[c] = nullptr; }
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v) { cudaFree(k->d_items_cap[c][v]); k->d_items_cap[c][v] = nullptr; }
     k->plan_ok = false;
 }
 
@@ -159,15 +160,20 @@ int sk_plan_build(sk_kern *k) {
     }
 
     // ---- caps: northern rings below the belt (never the equator ring) and mirrors
-    std::vector<int4> cap_items[SK_CAP_LS_CLASSES];
+    std::vector<int4> cap_items[SK_CAP_LS_CLASSES][2];
     const int cap_end = k->nb > 0 ? b_lo : eq;
     k->n_cap_rings = 0;
     for (int r = 0; r < cap_end; ++r) {
         const int Q = R[r].n / 4;
         int need = 0;
         bool ok = (nr - 1 - r) != r;
-        for (int j0 = 0; j0 < Q && ok; j0 += 128) {
-            const int jl = std::min(j0 + 127, Q - 1);
+        bool series = true;        // |dphi / 2| <= 1/8 on every window of the ring
+        for (int p = off[r]; p < off[r + 1]; ++p) {
+            const PairInfo &P = pairs[p];
+            if (P.W < 0 || (P.W + 1.5) * SK_PI / P.n_i > 0.125) series = false;
+        }
+        for (int j0 = 0; j0 < Q && ok; j0 += SK_CAP_CT) {
+            const int jl = std::min(j0 + SK_CAP_CT - 1, Q - 1);
             for (int p = off[r]; p < off[r + 1]; ++p) {
                 int L; long long qm;
                 cap_needs(j0, jl, R[r].n, R[r].s, pairs[p], L, qm);
@@ -181,17 +187,18 @@ int sk_plan_build(sk_kern *k) {
         if (!ok || cls < 0) continue;
         covered[r] = covered[nr - 1 - r] = 1;
         ++k->n_cap_rings;
-        for (int j0 = 0; j0 < Q; j0 += 128) cap_items[cls].push_back(make_int4(r, j0, 0, 0));
+        for (int j0 = 0; j0 < Q; j0 += SK_CAP_CT) cap_items[cls][series ? 1 : 0].push_back(make_int4(r, j0, 0, 0));
     }
-    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c) {
-        // heavier rings first: per-item cost grows with the number of window pixels
-        std::stable_sort(cap_items[c].begin(), cap_items[c].end(), [&](const int4 &a, const int4 &b) {
-            return (off[a.x + 1] - off[a.x]) > (off[b.x + 1] - off[b.x]);
-        });
-        k->n_items_cap[c] = (int)cap_items[c].size();
-        int rc = upload(cap_items[c], &k->d_items_cap[c]);
-        if (rc) return rc;
-    }
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v) {
+            // heavier rings first: per-item cost grows with the number of window pixels
+            std::stable_sort(cap_items[c][v].begin(), cap_items[c][v].end(), [&](const int4 &a, const int4 &b) {
+                return (off[a.x + 1] - off[a.x]) > (off[b.x + 1] - off[b.x]);
+            });
+            k->n_items_cap[c][v] = (int)cap_items[c][v].size();
+            int rc = upload(cap_items[c][v], &k->d_items_cap[c][v]);
+            if (rc) return rc;
+        }
 
     // ---- general: the rest
     std::vector<int4> gen;
@@ -338,31 +345,37 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         if (rc) return rc;
     }
 
-    // caps: one launch family per strip class
-    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c) {
-        Batcher b;
-        auto flush = [&]() -> int {
-            if (b.a.total > 0) {
-                b.a.status = ctx->d_status;
-                int per = sk_cap_blocks_per_sm(SK_CAP_LS[c]);
-                cudaEvent_t ev = sk_prof_begin(ctx, st);
-                SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], grid_for(b.a.total, per, ctx->num_sms), st));
-                sk_prof_end(ctx, "conv_cap", ev, st);
+    // caps: one launch family per (strip class, mode)
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int mode = 0; mode < 8; ++mode) {
+            const int v = mode & 1;
+            Batcher b;
+            auto flush = [&]() -> int {
+                if (b.a.total > 0) {
+                    b.a.status = ctx->d_status;
+                    int mnt = 2;
+                    for (int j = 0; j < b.a.n_jobs; ++j) mnt = std::max(mnt, b.a.j[j].kp.nt);
+                    int per = sk_cap_blocks_per_sm(SK_CAP_LS[c], mode, mnt);
+                    cudaEvent_t ev = sk_prof_begin(ctx, st);
+                    SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(b.a.total, per, ctx->num_sms), st));
+                    sk_prof_end(ctx, v ? "conv_cap" : "conv_cap_polar", ev, st);
+                }
+                b.reset();
+                return SK_OK;
+            };
+            for (int i = 0; i < n; ++i) {
+                const sk_kern *k = jobs[i].k;
+                if (!k->plan_ok || k->n_items_cap[c][v] == 0 || jobs[i].batch == 0) continue;
+                const int kmode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
+                if (kmode != mode) continue;
+                JobDesc d = base_desc(jobs[i]);
+                d.cap_ls = SK_CAP_LS[c];
+                b.add(d, k->d_items_cap[c][v], k->n_items_cap[c][v]);
+                if (b.full()) { int rc = flush(); if (rc) return rc; }
             }
-            b.reset();
-            return SK_OK;
-        };
-        for (int i = 0; i < n; ++i) {
-            const sk_kern *k = jobs[i].k;
-            if (!k->plan_ok || k->n_items_cap[c] == 0 || jobs[i].batch == 0) continue;
-            JobDesc d = base_desc(jobs[i]);
-            d.cap_ls = SK_CAP_LS[c];
-            b.add(d, k->d_items_cap[c], k->n_items_cap[c]);
-            if (b.full()) { int rc = flush(); if (rc) return rc; }
+            int rc = flush();
+            if (rc) return rc;
         }
-        int rc = flush();
-        if (rc) return rc;
-    }
 
     // general fallback rings
     {

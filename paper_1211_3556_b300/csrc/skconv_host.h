@@ -63,8 +63,9 @@ struct sk_kern {
     int4 *d_items_belt = nullptr;
     int n_items_belt = 0;
     // caps (one item list per strip class)
-    int4 *d_items_cap[SK_CAP_LS_CLASSES] = {nullptr, nullptr, nullptr};
-    int n_items_cap[SK_CAP_LS_CLASSES] = {0, 0, 0};
+    // [strip class][sin series valid]
+    int4 *d_items_cap[SK_CAP_LS_CLASSES][2] = {};
+    int n_items_cap[SK_CAP_LS_CLASSES][2] = {};
     int n_cap_rings = 0;
     unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere), 2 general
 };

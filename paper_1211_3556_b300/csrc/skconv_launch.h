@@ -80,11 +80,14 @@ cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const
 cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);
 cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st);
 cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st);
-cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int grid, cudaStream_t st);
+// mode bits: 1 sin series valid on every window of the items, 2 theta_cut <= 0.25
+// (asin series), 4 biased node layout
+cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cudaStream_t st);
 int sk_belt_blocks_per_sm(const JobsArg &a, int P);
-int sk_cap_blocks_per_sm(int ls);
+int sk_cap_blocks_per_sm(int ls, int mode, int nt);
 constexpr int SK_CAP_LS_CLASSES = 3;
-constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {256, 512, 1024};   // strip strides of the cap path
+constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {640, 1024, 1536};  // strip strides of the cap path
+constexpr int SK_CAP_CT = 512;         // output pixels (threads) per cap work item
 
 // table gradient (grad.cu)
 cudaError_t sk_launch_grad_general(const JobsArg &a, const float *gy, double *acc, int grid,
