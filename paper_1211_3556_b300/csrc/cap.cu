@@ -1,25 +1,28 @@
-// cap.cu -- polar-cap path: per-pair weights shared by the 8 symmetric images.
+// cap.cu -- polar-cap path: one weight evaluation shared by up to 16 symmetric pairs.
 //
-// Every HEALPix ring is invariant under a quarter turn in phi (pixel j ->
-// j + n/4) and the pixelisation is mirror-symmetric about the equator (ring r
-// <-> ring 4N - r with the same pixel phis).  So the pair (o, i) and its images
-// under the 4 rotations and the mirror have the same angle and the same
-// weight dOmega K_lin(gamma).  A thread owns one output pixel in the first
-// quarter of a northern ring and the 7 images of it, evaluates each pair's
-// weight once (chord, asin series, table lerp -- the per-pair formula of the
-// general path) and applies it with 8 FFMAs.  Same operator as the per-pair
-// path (the real-space convolution of Sec. 2, Eq. 1, tabulated kernel of
-// Sec. 3); only the order of work differs.
+// The HEALPix pixelisation is invariant under
+//   * a quarter turn in phi (pixel j -> j + n/4 on every ring),
+//   * the reflection phi -> pi/2 - phi (pixel j -> n/4 - j - s on a ring whose
+//     pixels sit at phi = pi (2j + s) / n),
+//   * the mirror about the equator (ring r <-> ring 4N - r, same phis),
+// and the angle between two pixel centres is invariant under all three.  So a
+// pair (o, i) and its images have the same weight dOmega K_lin(gamma).  A
+// thread owns one "base" output of the first half quarter of a northern ring,
+// evaluates the weight of each window pair once (the per-pair formula:
+// chord from A + B sin^2(dphi/2), asin series, table lerp), and applies it to
+// the 16 images: 4 quarter turns x 2 hemispheres x {pair, reflected pair}.
+// Outputs on a symmetry axis (phi = 0 or pi/4) are their own reflections (or
+// a quarter turn of it): they keep the 8 images without reflection, so no
+// output is written twice.  Same operator as the per-pair path (Sec. 2, Eq. 1
+// with the tabulated kernel of Sec. 3); only the order of work differs.
 //
-// Work item: (northern output ring, first quarter-ring pixel) for CT outputs.
-// For each input ring of the window the block stages 8 strips (4 rotations x
-// 2 hemispheres, each the union of the CT outputs' phi windows, unwrapped)
-// into shared memory with cp.async, double-buffered; a strip row has LS
-// floats, so the 8 images of one input pixel sit at fixed offsets k * LS.
-// The kernel table sits in shared memory too: the lanes of a warp look up
-// nodes spread over a few hundred entries, a gather that costs one L1
-// wavefront per distinct 128-byte line from global memory but only a few
-// bank-conflict wavefronts from shared memory.
+// Work item: (northern output ring, first base pixel) for CT base outputs.
+// For every input ring of the window the block stages 8 rows (4 quarter turns
+// x 2 hemispheres) of (pixel, reflected pixel) float2 pairs covering the union
+// of the CT windows, unwrapped, with cp.async, double-buffered; one LDS.64
+// then feeds a pair and its reflection.  The kernel table sits in shared
+// memory: the lanes of a warp look up nodes spread over a few hundred
+// entries, a gather that costs a few bank wavefronts from shared memory.
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
@@ -35,8 +38,8 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Nearest input pixel of quarter-ring output jo.  In the caps jo < n_o / 4 <= 2 Nside and
-// n_i <= 4 Nside <= 32768, so the numerator stays below 2^31 and 32-bit arithmetic is exact.
+// Nearest input pixel of output jo.  In the caps jo < n_o / 4 <= 2 Nside and
+// n_i <= 4 Nside <= 32768, so the numerator stays below 2^31.
 __device__ __forceinline__ int centre_of(int jo, int n_o, int s_o, const PairInfo &P) {
     const unsigned num = (unsigned)(2 * jo + s_o) * (unsigned)P.n_i + (unsigned)(1 - P.s_i) * (unsigned)n_o;
     return (int)(num / (2u * (unsigned)n_o));
@@ -53,19 +56,30 @@ __device__ __forceinline__ void win_shape(const PairInfo &P, int &before, int &c
     else         { before = P.W; cnt = 2 * P.W + 1; }
 }
 
+// Base outputs of a quarter ring of Q pixels with shift s: [0, T).
+__device__ __forceinline__ int base_count(int Q, int s) { return s ? (Q + 1) / 2 : Q / 2 + 1; }
+
+// Stage rows (h, k): element m = (x[u0 + m + kQ], x[Q - s - (u0 + m) + kQ]) (indices mod n).
 template <int LS>
-__device__ __forceinline__ void stage_ring(float *buf, const JobDesc &J, const float *xmap,
+__device__ __forceinline__ void stage_ring(float2 *buf, const JobDesc &J, const float *xmap,
                                            const PairInfo &P, int ri_south, int u0, int L) {
-    const int n = P.n_i, Q = n >> 2;
-    const long long st_n = J.rings[P.ri].start, st_s = J.rings[ri_south].start;
+    const int n = P.n_i, Q = n >> 2, s = P.s_i;
+    const float *xn = xmap + J.rings[P.ri].start, *xs = xmap + J.rings[ri_south].start;
+    float *b = reinterpret_cast<float *>(buf);
     for (int k = 0; k < 4; ++k) {
-        int idx = (u0 + (int)threadIdx.x + k * Q) % n;
-        if (idx < 0) idx += n;
+        int io = (u0 + (int)threadIdx.x + k * Q) % n;
+        if (io < 0) io += n;
+        int ir = (Q - s - u0 - (int)threadIdx.x + k * Q) % n;
+        if (ir < 0) ir += n;
         for (int m = threadIdx.x; m < L; m += CT) {
-            cp_async4(buf + k * LS + m, xmap + st_n + idx);
-            cp_async4(buf + (4 + k) * LS + m, xmap + st_s + idx);
-            idx += CT;
-            while (idx >= n) idx -= n;
+            cp_async4(b + 2 * (k * LS + m), xn + io);
+            cp_async4(b + 2 * (k * LS + m) + 1, xn + ir);
+            cp_async4(b + 2 * ((4 + k) * LS + m), xs + io);
+            cp_async4(b + 2 * ((4 + k) * LS + m) + 1, xs + ir);
+            io += CT;
+            while (io >= n) io -= n;
+            ir -= CT;
+            while (ir < 0) ir += n;
         }
     }
 }
@@ -74,8 +88,8 @@ template <int LS, int MODE>
 __global__ void __launch_bounds__(CT)
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
-    extern __shared__ __align__(16) float sx[];       // [2][8][LS] strips, then the table
-    float2 *stab = reinterpret_cast<float2 *>(sx + 2 * 8 * LS);
+    extern __shared__ __align__(16) float2 sx[];      // [2][8][LS] strips, then the table
+    float2 *stab = sx + 2 * 8 * LS;
     const int t = threadIdx.x;
     int cur_job = -1;
     for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
@@ -93,18 +107,20 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const int ro = it.x, j0 = it.y;
         const RingDev R = J.rings[ro];
         const int Qo = R.n >> 2;
-        const int jlast = min(j0 + CT - 1, Qo - 1);
+        const int T = base_count(Qo, R.s);
+        const int jlast = min(j0 + CT - 1, T - 1);
         const int jo = j0 + t;
-        const bool active = jo < Qo;
+        const bool active = jo < T;
+        const int jr = Qo - jo - R.s;                       // reflection of jo in the quarter
+        const bool refl = active && jr < Qo && jr >= T;
         const int ro_s = J.nr - 1 - ro;
         const float *xmap = J.x + (long long)map * J.stride;
         const int p0 = J.pair_off[ro], p1 = J.pair_off[ro + 1];
 
-        float acc[8];
+        float acc[16];                                      // [h*4+k] pair, [8 + h*4+k] reflected
 #pragma unroll
-        for (int s = 0; s < 8; ++s) acc[s] = 0.0f;
+        for (int s = 0; s < 16; ++s) acc[s] = 0.0f;
 
-        // prologue: stage the first input ring
         {
             const PairInfo P = J.pairs[p0];
             int before, cnt;
@@ -120,7 +136,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 int before, cnt;
                 win_shape(Pn, before, cnt);
                 const int c0 = centre_of(j0, R.n, R.s, Pn), c1 = centre_of(jlast, R.n, R.s, Pn);
-                stage_ring<LS>(sx + (buf ^ 1) * 8 * LS, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before, c1 - c0 + cnt);
+                stage_ring<LS>(sx + (buf ^ 1) * 8 * LS, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before,
+                               c1 - c0 + cnt);
             }
             cp_commit();
             cp_wait1();
@@ -131,18 +148,20 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 win_shape(P, before, cnt);
                 const int cb = centre_of(j0, R.n, R.s, P);
                 const int c = centre_of(jo, R.n, R.s, P);
-                const int jlo = c - before;
-                // |q| < 2^24 on this window (checked when the plan was built): q = qf + m dq
-                // is exact in FP32
-                const float qf = (float)q_of(jlo, jo, R.n, R.s, P);
+                // |q| < 2^24 on this window (checked when the plan was built): qf + m dq is exact
+                const float qf = (float)q_of(c - before, jo, R.n, R.s, P);
                 const float dq = (float)(2 * R.n);
-                const float *xs = sx + buf * 8 * LS + (c - cb);
+                const float2 *xs = sx + buf * 8 * LS + (c - cb);
 #pragma unroll 2
                 for (int m = 0; m < cnt; ++m) {
                     const float w = fast_weight<SERIES, SMALLA, BIASED>(fmaf((float)m, dq, qf) * P.c0,
                                                                         P.A, P.B, J.kp, stab);
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) acc[s] = fmaf(w, xs[s * LS + m], acc[s]);
+                    for (int s = 0; s < 8; ++s) {
+                        const float2 v = xs[s * LS + m];
+                        acc[s] = fmaf(w, v.x, acc[s]);
+                        acc[8 + s] = fmaf(w, v.y, acc[8 + s]);
+                    }
                 }
             }
             __syncthreads();
@@ -155,11 +174,18 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 yn[jo + k * Qo] = acc[k];
                 ys[jo + k * Qo] = acc[4 + k];
             }
+            if (refl) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    yn[jr + k * Qo] = acc[8 + k];
+                    ys[jr + k * Qo] = acc[12 + k];
+                }
+            }
         }
     }
 }
 
-size_t cap_smem(int LS, int nt) { return (size_t)2 * 8 * LS * sizeof(float) + (size_t)nt * sizeof(float2); }
+size_t cap_smem(int LS, int nt) { return (size_t)2 * 8 * LS * sizeof(float2) + (size_t)nt * sizeof(float2); }
 
 int max_nt(const JobsArg &a) {
     int m = 2;

@@ -165,6 +165,7 @@ int sk_plan_build(sk_kern *k) {
     k->n_cap_rings = 0;
     for (int r = 0; r < cap_end; ++r) {
         const int Q = R[r].n / 4;
+        const int T = R[r].s ? (Q + 1) / 2 : Q / 2 + 1;     // base outputs (the rest are reflections)
         int need = 0;
         bool ok = (nr - 1 - r) != r;
         bool series = true;        // |dphi / 2| <= 1/8 on every window of the ring
@@ -172,8 +173,8 @@ int sk_plan_build(sk_kern *k) {
             const PairInfo &P = pairs[p];
             if (P.W < 0 || (P.W + 1.5) * SK_PI / P.n_i > 0.125) series = false;
         }
-        for (int j0 = 0; j0 < Q && ok; j0 += SK_CAP_CT) {
-            const int jl = std::min(j0 + SK_CAP_CT - 1, Q - 1);
+        for (int j0 = 0; j0 < T && ok; j0 += SK_CAP_CT) {
+            const int jl = std::min(j0 + SK_CAP_CT - 1, T - 1);
             for (int p = off[r]; p < off[r + 1]; ++p) {
                 int L; long long qm;
                 cap_needs(j0, jl, R[r].n, R[r].s, pairs[p], L, qm);
@@ -187,7 +188,7 @@ int sk_plan_build(sk_kern *k) {
         if (!ok || cls < 0) continue;
         covered[r] = covered[nr - 1 - r] = 1;
         ++k->n_cap_rings;
-        for (int j0 = 0; j0 < Q; j0 += SK_CAP_CT) cap_items[cls][series ? 1 : 0].push_back(make_int4(r, j0, 0, 0));
+        for (int j0 = 0; j0 < T; j0 += SK_CAP_CT) cap_items[cls][series ? 1 : 0].push_back(make_int4(r, j0, 0, 0));
     }
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int v = 0; v < 2; ++v) {
