@@ -165,6 +165,23 @@ int sk_convolve_adjoint(sk_ctx *ctx, const sk_kern *k, const float *d_gy, float 
 int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, const float *d_gy,
                   int64_t batch, int64_t map_stride, float *d_gtable, void *stream);
 
+/* The same table gradient without any device allocation.  There is no
+ * counterpart in the paper: it exists for callers that cannot let a library
+ * allocate device memory -- hosts whose device memory belongs to their own
+ * allocator or budget, and latency-critical loops in which cudaMalloc or
+ * cudaFree would synchronise the device.  Instead of the context workspace it
+ * accumulates in a fixed FP64 array of 16384 entries compiled into the
+ * library (128 KiB, held on every GPU that loads the library until the
+ * process exits).  Arguments as sk_grad_table; n_nodes above 16384 is
+ * rejected with SK_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call clears the array before
+ * using it, and all calls on a device share it: two calls whose work overlaps
+ * on the GPU (e.g. on unordered streams) race and give wrong results.
+ * Errors: SK_EINVAL, SK_ECUDA, SK_EUNSUPPORTED (device index above 63). */
+int sk_grad_table_noalloc(sk_ctx *ctx, const sk_kern *k, const float *d_x, const float *d_gy,
+                          int64_t batch, int64_t map_stride, float *d_gtable, void *stream);
+
 /* End-to-end convolution from and to host memory: copies `batch` maps from
  * h_in to the context workspace, convolves, copies the result to h_out, and
  * synchronises `stream`.  h_in/h_out: [batch][map_stride] FP32 host buffers.

@@ -67,6 +67,7 @@ def _declare(L):
         "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
         "sk_convolve_adjoint": (I, [P, P, P, P, I64, I64, P]),
         "sk_grad_table": (I, [P, P, P, P, I64, I64, P, P]),
+        "sk_grad_table_noalloc": (I, [P, P, P, P, I64, I64, P, P]),
         "sk_convolve_host": (I, [P, P, P, P, I64, I64, P]),
         "sk_convolve_jobs": (I, [P, ctypes.POINTER(sk_job), I, I, P]),
         "sk_graph_capture": (I, [P, ctypes.POINTER(sk_job), I, I, P, PP]),
