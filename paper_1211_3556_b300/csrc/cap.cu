@@ -17,12 +17,14 @@
 // with the tabulated kernel of Sec. 3); only the order of work differs.
 //
 // Work item: (northern output ring, first base pixel) for CT base outputs.
-// For every input ring of the window the block stages 8 rows (4 quarter turns
-// x 2 hemispheres) of (pixel, reflected pixel) float2 pairs covering the union
-// of the CT windows, unwrapped, with cp.async, double-buffered; one LDS.64
-// then feeds a pair and its reflection.  The kernel table sits in shared
-// memory: the lanes of a warp look up nodes spread over a few hundred
-// entries, a gather that costs a few bank wavefronts from shared memory.
+// For every input ring of the window the block stages 4 rows (quarter turns) of
+// float4 (north pixel, its reflection, south pixel, its reflection) covering
+// the union of the CT windows, unwrapped, with cp.async, double-buffered; one
+// 128-bit load then feeds 4 of the 16 images.  The node values V_k dOmega sit
+// in shared memory (FP32, the slope formed on the fly): the lanes of a warp
+// look up nodes spread over a few hundred entries, a gather that costs a few
+// bank wavefronts from shared memory but one L1 wavefront per distinct line
+// from global memory.
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
@@ -59,23 +61,29 @@ __device__ __forceinline__ void win_shape(const PairInfo &P, int &before, int &c
 // Base outputs of a quarter ring of Q pixels with shift s: [0, T).
 __device__ __forceinline__ int base_count(int Q, int s) { return s ? (Q + 1) / 2 : Q / 2 + 1; }
 
-// Stage rows (h, k): element m = (x[u0 + m + kQ], x[Q - s - (u0 + m) + kQ]) (indices mod n).
+// Stage row k, element m = (xN[a], xN[b], xS[a], xS[b]) with a = u0 + m + kQ and
+// b = Q - s - (u0 + m) + kQ (indices mod n): the pixel and its reflection on the
+// northern ring and on its southern mirror.
 template <int LS>
-__device__ __forceinline__ void stage_ring(float2 *buf, const JobDesc &J, const float *xmap,
+__device__ __forceinline__ void stage_ring(float4 *buf, const JobDesc &J, const float *xmap,
                                            const PairInfo &P, int ri_south, int u0, int L) {
     const int n = P.n_i, Q = n >> 2, s = P.s_i;
     const float *xn = xmap + J.rings[P.ri].start, *xs = xmap + J.rings[ri_south].start;
     float *b = reinterpret_cast<float *>(buf);
+    int io0 = (u0 + (int)threadIdx.x) % n;
+    if (io0 < 0) io0 += n;
+    int ir0 = (Q - s - u0 - (int)threadIdx.x) % n;
+    if (ir0 < 0) ir0 += n;
     for (int k = 0; k < 4; ++k) {
-        int io = (u0 + (int)threadIdx.x + k * Q) % n;
-        if (io < 0) io += n;
-        int ir = (Q - s - u0 - (int)threadIdx.x + k * Q) % n;
-        if (ir < 0) ir += n;
+        int io = io0 + k * Q, ir = ir0 + k * Q;
+        if (io >= n) io -= n;
+        if (ir >= n) ir -= n;
         for (int m = threadIdx.x; m < L; m += CT) {
-            cp_async4(b + 2 * (k * LS + m), xn + io);
-            cp_async4(b + 2 * (k * LS + m) + 1, xn + ir);
-            cp_async4(b + 2 * ((4 + k) * LS + m), xs + io);
-            cp_async4(b + 2 * ((4 + k) * LS + m) + 1, xs + ir);
+            float *d = b + 4 * (k * LS + m);
+            cp_async4(d, xn + io);
+            cp_async4(d + 1, xn + ir);
+            cp_async4(d + 2, xs + io);
+            cp_async4(d + 3, xs + ir);
             io += CT;
             while (io >= n) io -= n;
             ir -= CT;
@@ -88,8 +96,8 @@ template <int LS, int MODE>
 __global__ void __launch_bounds__(CT)
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
-    extern __shared__ __align__(16) float2 sx[];      // [2][8][LS] strips, then the table
-    float2 *stab = sx + 2 * 8 * LS;
+    extern __shared__ __align__(16) float4 sx[];      // [2][4][LS] strips, then the node values
+    float *stab = reinterpret_cast<float *>(sx + 2 * 4 * LS);
     const int t = threadIdx.x;
     int cur_job = -1;
     for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
@@ -97,7 +105,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const JobDesc &J = A.j[jn];
         if (jn != cur_job) {                 // uniform across the block
             __syncthreads();
-            for (int k = t; k < J.kp.nt; k += CT) stab[k] = J.tab[k];
+            for (int k = t; k < J.kp.nt; k += CT) stab[k] = J.tab[k].x;
             __syncthreads();
             cur_job = jn;
         }
@@ -136,7 +144,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 int before, cnt;
                 win_shape(Pn, before, cnt);
                 const int c0 = centre_of(j0, R.n, R.s, Pn), c1 = centre_of(jlast, R.n, R.s, Pn);
-                stage_ring<LS>(sx + (buf ^ 1) * 8 * LS, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before,
+                stage_ring<LS>(sx + (buf ^ 1) * 4 * LS, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before,
                                c1 - c0 + cnt);
             }
             cp_commit();
@@ -151,16 +159,18 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 // |q| < 2^24 on this window (checked when the plan was built): qf + m dq is exact
                 const float qf = (float)q_of(c - before, jo, R.n, R.s, P);
                 const float dq = (float)(2 * R.n);
-                const float2 *xs = sx + buf * 8 * LS + (c - cb);
+                const float4 *xs = sx + buf * 4 * LS + (c - cb);
 #pragma unroll 2
                 for (int m = 0; m < cnt; ++m) {
                     const float w = fast_weight<SERIES, SMALLA, BIASED>(fmaf((float)m, dq, qf) * P.c0,
                                                                         P.A, P.B, J.kp, stab);
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        const float2 v = xs[s * LS + m];
-                        acc[s] = fmaf(w, v.x, acc[s]);
-                        acc[8 + s] = fmaf(w, v.y, acc[8 + s]);
+                    for (int k = 0; k < 4; ++k) {
+                        const float4 v = xs[k * LS + m];
+                        acc[k] = fmaf(w, v.x, acc[k]);             // north, pair
+                        acc[8 + k] = fmaf(w, v.y, acc[8 + k]);     // north, reflected
+                        acc[4 + k] = fmaf(w, v.z, acc[4 + k]);     // south, pair
+                        acc[12 + k] = fmaf(w, v.w, acc[12 + k]);   // south, reflected
                     }
                 }
             }
@@ -185,7 +195,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
     }
 }
 
-size_t cap_smem(int LS, int nt) { return (size_t)2 * 8 * LS * sizeof(float2) + (size_t)nt * sizeof(float2); }
+size_t cap_smem(int LS, int nt) { return (size_t)2 * 4 * LS * sizeof(float4) + (size_t)nt * sizeof(float); }
 
 int max_nt(const JobsArg &a) {
     int m = 2;
