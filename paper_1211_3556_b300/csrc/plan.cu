@@ -123,24 +123,30 @@ int sk_plan_build(sk_kern *k) {
         const int R2 = 2 * HM + 1;
         k->ngroups = (k->nb + SK_BELT_G - 1) / SK_BELT_G;
         const int nb_pad = k->ngroups * SK_BELT_G;
-        std::vector<int2> rng((size_t)nb_pad * R2, make_int2(0, 0));
-        int EMIN = 1 << 30, EMAX = -(1 << 30), WPM = 4;
+        // rows on a common offset grid e = EMIN + c: chunk c4 = (e - EMIN) / 4
+        std::vector<int2> rng((size_t)nb_pad * R2, make_int2(1, 0));
+        int EMIN = 1 << 30, EMAX = -(1 << 30);
+        for (int rb = 0; rb < k->nb; ++rb) {
+            const int r = b_lo + rb;
+            for (int p = off[r]; p < off[r + 1]; ++p) {
+                const PairInfo &P = pairs[p];
+                const int ec = (R[r].s + 1 - P.s_i) >> 1;     // offset of the nearest input pixel
+                EMIN = std::min(EMIN, ec - P.W);
+                EMAX = std::max(EMAX, ec + P.W);
+            }
+        }
         for (int rb = 0; rb < k->nb; ++rb) {
             const int r = b_lo + rb;
             covered[r] = 1;
             for (int p = off[r]; p < off[r + 1]; ++p) {
                 const PairInfo &P = pairs[p];
                 const int d = P.ri - r;
-                const int ec = (R[r].s + 1 - P.s_i) >> 1;     // offset of the nearest input pixel
-                const int elo = ec - P.W;
-                const int nch = (2 * P.W + 1 + 3) / 4;
-                rng[(size_t)rb * R2 + d + HM] = make_int2(elo, nch);
-                EMIN = std::min(EMIN, elo);
-                EMAX = std::max(EMAX, elo + 4 * nch - 1);
-                WPM = std::max(WPM, 4 * nch);
+                const int ec = (R[r].s + 1 - P.s_i) >> 1;
+                rng[(size_t)rb * R2 + d + HM] = make_int2((ec - P.W - EMIN) >> 2, (ec + P.W - EMIN) >> 2);
             }
         }
-        k->EMIN = EMIN; k->EMAX = EMAX; k->WPM = WPM;
+        const int WPM = ((EMAX - EMIN + 1) + 3) & ~3;
+        k->EMIN = EMIN; k->EMAX = EMIN + WPM - 1; k->WPM = WPM;
         std::vector<int2> grp(k->ngroups);
         for (int gi = 0; gi < k->ngroups; ++gi) {
             int lo = 1 << 30, hi = -1;
@@ -290,6 +296,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             wp += sk_plan_workspace_bytes(k);
             JobDesc d = base_desc(jobs[i]);
             d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
+            d.EMIN = k->EMIN; d.EMAX = k->EMAX;
             d.brng = k->d_brng;
             cudaEvent_t ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_belt_weights(d, wrows[i], st));

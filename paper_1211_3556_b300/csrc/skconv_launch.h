@@ -12,8 +12,9 @@
 
 constexpr int SK_MAXJ = 16;            // jobs per launch (more: several launches)
 constexpr int SK_MAX_NODES = 16384;    // largest kernel table
-constexpr int SK_BELT_G = 8;           // output rings per belt block (one warp each)
-constexpr int SK_BELT_STAGES = 4;      // input-ring strips in flight per belt block
+constexpr int SK_BELT_G = 16;          // output rings per belt block (two per consumer warp)
+constexpr int SK_BELT_WARPS = SK_BELT_G / 2;   // consumer warps per belt block
+constexpr int SK_BELT_STAGES = 8;      // input-ring strips in flight per belt block
 
 struct JobDesc {
     // operator
@@ -38,11 +39,11 @@ struct JobDesc {
     int b_lo;             // first belt output ring
     int nb;               // belt output rings
     int HM;               // max |input ring - output ring| over the belt
-    int WPM;              // weights per (output ring, input ring) row, multiple of 4
+    int WPM;              // weights per (output ring, input ring) row: offsets EMIN .. EMIN+WPM-1, multiple of 4
     int EMIN, EMAX;       // pixel offset range of all belt windows
     int n4;               // pixels per belt ring (4 Nside)
-    const int2 *brng;     // [nb_pad][2HM+1] (first offset, number of 4-chunks)
-    const float *bw;      // [nb_pad][2HM+1][WPM] weights (workspace, per call)
+    const int2 *brng;     // [nb_pad][2HM+1] first and last 4-chunk (of offsets EMIN + 4c ..) with weights
+    const float *bw;      // [nb_pad][2HM+1][WPM] weights on the common offset grid (workspace, per call)
     const int2 *bgrp;     // [groups] first and last input ring of each group
     // cap path
     int cap_ls;           // strip stride class
