@@ -53,7 +53,7 @@ FLOP_PER_PAIR_EVAL = 14.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n2048_plain", choices=sorted(WORKLOADS))
@@ -69,6 +69,30 @@ def dist_env():
     return rank, world, local
 
 
+def shard_maps(maps: np.ndarray, rank: int, world: int) -> np.ndarray:
+    """Maps of one rank under weak scaling: every rank convolves its own copy of the
+    workload, made distinct by a cyclic pixel shift of `rank` (no data exchange)."""
+    if world <= 1:
+        return maps
+    return np.ascontiguousarray(np.roll(maps, rank, axis=1))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the slowest rank sets the step time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the max step time."""
+    return units_per_rank * world / seconds
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
@@ -82,10 +106,17 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                       "-i", str(gpu_index), "-lms", "50"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # wait (bounded) for the first sample so that the timed region is covered
+        t0 = time.time()
+        while self.p is not None and time.time() - t0 < 5.0:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is not None:
@@ -144,7 +175,7 @@ def time_steps(torch, fn, steps, warmup, barrier):
     return e0.elapsed_time(e1) / steps
 
 
-def cpu_baseline_leg(wl, group, y_gpu_first_map, target_s=15.0):
+def cpu_baseline_leg(wl, group, y_gpu_first_map, target_s=40.0):
     """The FP64 oracle, as it stands, on a bounded random sample of output pixels of
     the same workload (all host cores); also the rms error of the GPU result on
     that sample against it."""
@@ -153,11 +184,12 @@ def cpu_baseline_leg(wl, group, y_gpu_first_map, target_s=15.0):
     V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
     x = make_maps(group, wl.sources[0] if wl.sources else None)[0].astype(np.float64)
     npx = npix_of(group.nside)
-    probe = sample_indices(npx, 2000, 9001)
+    n_probe = min(npx, 40000)
+    probe = sample_indices(npx, n_probe, 9001)
     t0 = time.perf_counter()
     O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, probe)
     dt = max(time.perf_counter() - t0, 1e-3)
-    n = int(min(npx, max(2000, 2000 * target_s / dt)))
+    n = int(min(npx, max(n_probe, n_probe * target_s / dt)))
     outs = sample_indices(npx, n, 9002)
     t0 = time.perf_counter()
     yo = O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, outs)
@@ -192,9 +224,7 @@ def run_ours(args):
     for gi, group in enumerate(wl.groups):
         g, k = build_operator(sk, ctx, group)
         src = wl.sources[gi] if wl.sources and gi < len(wl.sources) else None
-        maps = make_maps(group, src)
-        if world > 1:                 # every rank convolves its own maps (weak scaling)
-            maps = np.ascontiguousarray(np.roll(maps, rank, axis=1))
+        maps = shard_maps(make_maps(group, src), rank, world)
         x = torch.from_numpy(maps).cuda()
         y = torch.empty_like(x)
         pairs = k.count_pairs()
@@ -218,22 +248,18 @@ def run_ours(args):
     step()
     torch.cuda.synchronize()
     ctx.status()
+    sampler = ClockSampler(local)          # sampled from the warm-up to the end of the timed steps
     for _ in range(args.warmup):
         step()
     ctx.profile(True)
     ctx.profile_read()
-    sampler = ClockSampler(local)
     ms = time_steps(torch, step, args.steps, 0, barrier)
     clocks = sampler.stop()
     ctx.profile(False)
     prof = ctx.profile_read()
     ctx.status()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = pairs_step * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = aggregate_rate(pairs_step, world, ms * 1e-3)
     launches = sum(c for _, c in prof.values())
 
     # roofline of the dominant kernel: F_mac flops per pair of the outputs it evaluates
@@ -265,13 +291,9 @@ def run_ours(args):
         for _ in range(k_e2e):
             sk.convolve_host(o["kern"], hxn, hyn)
         t_e2e = (time.perf_counter() - t0) / k_e2e
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, world, "cuda")
         nbytes = int(o["maps"].nbytes)
-        e2e = {"value": pairs_step * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": aggregate_rate(pairs_step, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
                "api": "sk_convolve_host (pinned host buffers)"}
         del hx, hy

@@ -238,6 +238,24 @@ int sk_profile_read(sk_ctx *ctx, int max_kernels, char *names, double *ms, int *
 int sk_kernel_set_tiles(sk_kern *k, int belt_p, int cap_t);
 int sk_kernel_get_tiles(const sk_kern *k, int *belt_p, int *cap_t);
 
+/* Autotuner of the belt tile width: times every candidate P on the caller's
+ * maps (d_in -> d_out, `batch` maps), keeps the fastest in k and returns it in
+ * *chosen.  If cache_path is not NULL, a text file of "key P" lines keyed by
+ * GPU name, Nside, cut, node count, layout and batch is consulted first and
+ * appended to after tuning.  Synchronises `stream`.  Not safe while k is used
+ * from another thread.  Errors: as sk_convolve. */
+int sk_kernel_autotune(sk_ctx *ctx, sk_kern *k, const float *d_in, float *d_out, int64_t batch,
+                       int64_t map_stride, const char *cache_path, void *stream, int *chosen);
+
+/* ---- self-test of device-side failure reporting --------------------------- */
+
+/* Launch a kernel whose bounded wait on an mbarrier can never complete: after
+ * `seconds` (0 < seconds <= 2) it records SK_ETIMEOUT in the context's status
+ * word and returns, as the library's pipelined kernels do when a copy never
+ * lands.  sk_get_status then reports SK_ETIMEOUT and the context stays usable.
+ * Errors: SK_EINVAL, SK_ECUDA. */
+int sk_selftest_wait_timeout(sk_ctx *ctx, double seconds, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def _declare(L):
         "sk_graph_launch": (I, [P, P]),
         "sk_graph_destroy": (I, [P]),
         "sk_kernel_set_tiles": (I, [P, I, I]),
+        "sk_kernel_autotune": (I, [P, P, P, P, I64, I64, ctypes.c_char_p, P, ctypes.POINTER(I)]),
+        "sk_selftest_wait_timeout": (I, [P, D, P]),
         "sk_kernel_get_tiles": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
@@ -139,6 +141,10 @@ class Context:
 
     def status(self, stream=None):
         _check(lib().sk_get_status(self._h, _stream_ptr(stream)))
+
+    def selftest_wait_timeout(self, seconds: float = 0.05, stream=None):
+        """Launch the bounded-wait self-test kernel (it records SK_ETIMEOUT)."""
+        _check(lib().sk_selftest_wait_timeout(self._h, float(seconds), _stream_ptr(stream)))
 
     def profile(self, on: bool):
         _check(lib().sk_profile_enable(self._h, 1 if on else 0))
@@ -252,6 +258,19 @@ class Kernel:
         c = (ctypes.c_int64 * 3)()
         _check(lib().sk_count_pairs_by_path(self.ctx._h, self._h, c))
         return int(c[0]), int(c[1]), int(c[2])
+
+    def autotune(self, x, out=None, cache_path=None, stream=None) -> int:
+        """Time every belt tile width on maps x and keep the fastest; returns it."""
+        import torch
+        x2, b, stride = _map_args(x, self.geom.npix)
+        if out is None:
+            out = torch.empty_like(x2)
+        p = ctypes.c_int()
+        cp = cache_path.encode() if cache_path else None
+        _check(lib().sk_kernel_autotune(self.ctx._h, self._h, ctypes.c_void_p(x2.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), b, stride, cp, _stream_ptr(stream),
+                                        ctypes.byref(p)))
+        return p.value
 
     def set_tiles(self, belt_p=0, cap_t=0):
         _check(lib().sk_kernel_set_tiles(self._h, belt_p, cap_t))

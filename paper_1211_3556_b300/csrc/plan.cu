@@ -324,6 +324,12 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         return flush();
     }
 
+    // The polar cap rings and any per-pair rings are small launches: run them on the
+    // context's side stream, forked from `st` here and joined back at the end.
+    cudaStream_t side = ctx->aux;
+    SK_CU(cudaEventRecord(ctx->ev_fork, st));
+    SK_CU(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
+
     // belt: one launch family per tile width P
     const int Ps[] = {5, 7, 9, 11, 13, 15, 17};
     for (int P : Ps) {
@@ -364,9 +370,10 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                     int mnt = 2;
                     for (int j = 0; j < b.a.n_jobs; ++j) mnt = std::max(mnt, b.a.j[j].kp.nt);
                     int per = sk_cap_blocks_per_sm(SK_CAP_LS[c], mode, mnt);
-                    cudaEvent_t ev = sk_prof_begin(ctx, st);
-                    SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(b.a.total, per, ctx->num_sms), st));
-                    sk_prof_end(ctx, v ? "conv_cap" : "conv_cap_polar", ev, st);
+                    cudaStream_t cs = v ? st : side;
+                    cudaEvent_t ev = sk_prof_begin(ctx, cs);
+                    SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(b.a.total, per, ctx->num_sms), cs));
+                    sk_prof_end(ctx, v ? "conv_cap" : "conv_cap_polar", ev, cs);
                 }
                 b.reset();
                 return SK_OK;
@@ -391,9 +398,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         auto flush = [&]() -> int {
             if (b.a.total > 0) {
                 b.a.status = ctx->d_status;
-                cudaEvent_t ev = sk_prof_begin(ctx, st);
-                SK_CU(sk_launch_conv_general(b.a, grid_for(b.a.total, 16, ctx->num_sms), st));
-                sk_prof_end(ctx, "conv_general", ev, st);
+                cudaEvent_t ev = sk_prof_begin(ctx, side);
+                SK_CU(sk_launch_conv_general(b.a, grid_for(b.a.total, 16, ctx->num_sms), side));
+                sk_prof_end(ctx, "conv_general", ev, side);
             }
             b.reset();
             return SK_OK;
@@ -410,6 +417,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         int rc = flush();
         if (rc) return rc;
     }
+    SK_CU(cudaEventRecord(ctx->ev_join, side));
+    SK_CU(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     return SK_OK;
 }
 

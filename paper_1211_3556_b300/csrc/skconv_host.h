@@ -16,6 +16,10 @@ struct sk_ctx {
     int *d_status = nullptr;       // device status word
     void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
     size_t ws_bytes = 0;
+    // side stream for the small launches that overlap the large ones (polar caps,
+    // per-pair fallback rings), forked from and joined into the caller's stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // optional per-launch timing (sk_profile_enable): events around each kernel
     bool prof = false;
     struct ProfRec { const char *name; cudaEvent_t a, b; };

@@ -276,3 +276,45 @@ def test_argument_errors(sk):
     with pytest.raises(sk.SkError):
         sk.convolve(k, big[:, 1:1 + 12 * 16 * 16])        # misaligned map pointer
     sk._ctx.status()
+
+
+# ------------------------------------------------------------------ failure reporting, tuning
+
+def test_bounded_wait_reports_timeout_and_context_survives(sk):
+    import torch
+    sk._ctx.status()
+    sk._ctx.selftest_wait_timeout(0.05)
+    with pytest.raises(sk.SkError) as ei:
+        sk._ctx.status()
+    assert ei.value.code == sk.SK_ETIMEOUT
+    sk._ctx.status()                                   # the word was cleared
+    nside, tc = 32, 0.1
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 96, 24, tc, 256)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc)
+    x = white_noise_maps(nside, 1, 3)
+    y = gpu_conv(sk, k, x)[0]                          # the context is still usable
+    assert rms_rel(y, O.conv_window(nside, V, tc, 0, x[0].astype(np.float64))) <= RMS_BOUND
+
+
+def test_belt_tile_widths_give_identical_results_and_autotune(sk, tmp_path):
+    import torch
+    nside, tc = 256, 0.02
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 768, 192, tc, 2048)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc)
+    x = torch.from_numpy(white_noise_maps(nside, 2, 9)).cuda()
+    ref = None
+    for p in (5, 7, 9, 11, 13, 15, 17):
+        k.set_tiles(belt_p=p)
+        assert k.tiles()[0] == p
+        y = sk.convolve(k, x)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = y.clone()
+        else:
+            assert torch.equal(y, ref)                 # same summation order for every tile width
+    cache = str(tmp_path / "tune.txt")
+    p1 = k.autotune(x, cache_path=cache)
+    p2 = k.autotune(x, cache_path=cache)               # second call is served by the cache
+    assert p1 == p2 and p1 in (5, 7, 9, 11, 13, 15, 17)
+    assert torch.equal(sk.convolve(k, x), ref)
+    sk._ctx.status()
