@@ -256,6 +256,15 @@ int sk_kernel_autotune(sk_ctx *ctx, sk_kern *k, const float *d_in, float *d_out,
  * Errors: SK_EINVAL, SK_ECUDA. */
 int sk_selftest_wait_timeout(sk_ctx *ctx, double seconds, void *stream);
 
+/* Self-test of the tensor-core building blocks the batched path uses: one block
+ * computes D = A B^T (A: 128 x k, B: n x k, D: 128 x n, all row-major FP32 device
+ * buffers) with tcgen05 TF32 MMAs from 128-byte-swizzled K-major shared-memory
+ * operands into tensor memory; passes = 1 multiplies the TF32 parts only,
+ * passes = 3 adds the hi*lo and lo*hi products (3xTF32).  n a multiple of 16 in
+ * [16, 256], k a multiple of 32 in [32, 128].  Errors: SK_EINVAL, SK_ECUDA. */
+int sk_selftest_tc_gemm(sk_ctx *ctx, const float *d_a, const float *d_b, float *d_d, int n, int k,
+                        int passes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,54 @@
+"""Tensor-core building blocks (tcgen05 TF32 MMA from swizzled shared memory into
+tensor memory) against a host product, through the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1211_3556_b300 as sk
+    return sk, sk.Context(0), torch
+
+
+def _run(sk, ctx, torch, A, B, passes):
+    a = torch.from_numpy(np.ascontiguousarray(A, np.float32)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(B, np.float32)).cuda()
+    d = torch.full((A.shape[0], B.shape[0]), float("nan"), device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = sk.lib()
+    rc = L.sk_selftest_tc_gemm(ctx._h, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                               ctypes.c_void_p(d.data_ptr()), B.shape[0], A.shape[1], passes, st)
+    assert rc == 0, L.sk_last_error()
+    torch.cuda.synchronize()
+    assert L.sk_get_status(ctx._h, st) == 0
+    return d.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n,k", [(64, 64), (16, 32), (128, 96)])
+def test_tf32_mma_exact_on_small_integers(env, n, k):
+    sk, ctx, torch = env
+    rng = np.random.default_rng(n + k)
+    A = rng.integers(-8, 9, size=(128, k)).astype(np.float32)
+    B = rng.integers(-8, 9, size=(n, k)).astype(np.float32)
+    D = _run(sk, ctx, torch, A, B, 1)
+    assert np.array_equal(D, A.astype(np.float64) @ B.T.astype(np.float64))
+
+
+def test_3xtf32_accuracy(env):
+    sk, ctx, torch = env
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((128, 64)).astype(np.float32)
+    B = rng.standard_normal((64, 64)).astype(np.float32)
+    want = A.astype(np.float64) @ B.T.astype(np.float64)
+    D3 = _run(sk, ctx, torch, A, B, 3)
+    D1 = _run(sk, ctx, torch, A, B, 1)
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).T.astype(np.float64)
+    assert np.max(np.abs(D3 - want) / scale) < 2e-6          # 3xTF32 ~ FP32 accuracy
+    assert np.max(np.abs(D1 - want) / scale) > 1e-5          # plain TF32 is visibly coarser
