@@ -298,7 +298,8 @@ def run_ours(args):
                "api": "sk_convolve_host (pinned host buffers)"}
         del hx, hy
 
-    # the batched form beside the plain one (64 maps at Nside 1024 sharing one kernel)
+    # the batched forms beside the plain one (64 maps at Nside 1024 sharing one kernel):
+    # FP32 (weights shared by the batch) and tensor cores (3xTF32 tcgen05 belt)
     batched = None
     if not args.no_batched and args.workload == "n2048_plain":
         grp = WORKLOADS["n1024x64_batched"].groups[0]
@@ -306,9 +307,13 @@ def run_ours(args):
         xb = torch.from_numpy(make_maps(grp)).cuda()
         yb = torch.empty_like(xb)
         pb = kb.count_pairs()
-        msb = time_steps(torch, lambda: sk.convolve(kb, xb, out=yb), max(3, args.steps // 4), 2, barrier)
-        batched = {"workload": "n1024x64_batched", "value": pb * grp.batch / (msb * 1e-3), "unit": UNIT,
-                   "ms_per_map": msb / grp.batch, "ms_per_step": msb, "form": "fp32 belt+cap, weights shared by the batch"}
+        batched = {"workload": "n1024x64_batched", "unit": UNIT}
+        for name, path in (("fp32", sk.PATH_AUTO), ("tensor_3xtf32", sk.PATH_TENSOR)):
+            msb = time_steps(torch, lambda: sk.convolve(kb, xb, out=yb, path=path), max(3, min(args.steps, 20)), 2,
+                             barrier)
+            batched[name] = {"value": pb * grp.batch / (msb * 1e-3), "ms_per_map": msb / grp.batch,
+                             "ms_per_step": msb}
+        batched["value"] = max(batched["fp32"]["value"], batched["tensor_3xtf32"]["value"])
         del xb, yb
 
     o0 = ops[0]

@@ -60,6 +60,8 @@ extern "C" {
 /* Path selection for sk_convolve_path / sk_convolve_jobs / sk_graph_capture. */
 #define SK_PATH_AUTO       0   /* belt Toeplitz + symmetric caps where they apply   */
 #define SK_PATH_GENERAL    1   /* per-pair evaluation for every output ring        */
+#define SK_PATH_TENSOR     2   /* as AUTO, with the belt as 3xTF32 tcgen05 contractions over */
+                               /* 32-map blocks (the batched form; caps stay FP32)            */
 
 typedef struct sk_ctx  sk_ctx;
 typedef struct sk_geom sk_geom;
@@ -146,7 +148,7 @@ int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3);
 int sk_convolve(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
                 int64_t batch, int64_t map_stride, void *stream);
 
-/* Same, forcing a path (SK_PATH_AUTO or SK_PATH_GENERAL). */
+/* Same, choosing a path (SK_PATH_AUTO, SK_PATH_GENERAL or SK_PATH_TENSOR). */
 int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
                      int64_t batch, int64_t map_stride, int path, void *stream);
 

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libskconv.so")
 
 SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 NODES_UNIFORM, NODES_BIASED = 0, 1
-PATH_AUTO, PATH_GENERAL = 0, 1
+PATH_AUTO, PATH_GENERAL, PATH_TENSOR = 0, 1, 2
 
 _ERRNAMES = {SK_EINVAL: "SK_EINVAL", SK_ENOMEM: "SK_ENOMEM", SK_ECUDA: "SK_ECUDA",
              SK_ETIMEOUT: "SK_ETIMEOUT", SK_EUNSUPPORTED: "SK_EUNSUPPORTED"}

@@ -485,12 +485,13 @@ extern "C" int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve: NULL context");
     int rc = check_maps("sk_convolve", k, d_in, d_out, batch, map_stride);
     if (rc) return rc;
-    if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL) return sk_fail(SK_EINVAL, "unknown path %d", path);
+    if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL && path != SK_PATH_TENSOR)
+        return sk_fail(SK_EINVAL, "unknown path %d", path);
     if (batch == 0) return SK_OK;
     SK_CU(cudaSetDevice(ctx->device));
     SkJob jb{k, d_in, d_out, batch, map_stride};
     void *ws = nullptr;
-    size_t need = path == SK_PATH_AUTO ? sk_jobs_workspace_bytes(&jb, 1) : 0;
+    size_t need = path != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(&jb, 1) : 0;
     if (need && (rc = sk_ctx_workspace(ctx, need, &ws))) return rc;
     return sk_run_jobs(ctx, &jb, 1, path, ws, (cudaStream_t)stream);
 }
@@ -562,13 +563,14 @@ static int convert_jobs(const sk_job *jobs, int n, std::vector<SkJob> &out) {
 
 extern "C" int sk_convolve_jobs(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int flags, void *stream) {
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve_jobs: NULL context");
-    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL) return sk_fail(SK_EINVAL, "unknown flags %d", flags);
+    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR)
+        return sk_fail(SK_EINVAL, "unknown flags %d", flags);
     std::vector<SkJob> js;
     int rc = convert_jobs(jobs, n_jobs, js);
     if (rc) return rc;
     SK_CU(cudaSetDevice(ctx->device));
     void *ws = nullptr;
-    size_t need = flags == SK_PATH_AUTO ? sk_jobs_workspace_bytes(js.data(), n_jobs) : 0;
+    size_t need = flags != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(js.data(), n_jobs) : 0;
     if (need && (rc = sk_ctx_workspace(ctx, need, &ws))) return rc;
     return sk_run_jobs(ctx, js.data(), n_jobs, flags, ws, (cudaStream_t)stream);
 }
@@ -583,7 +585,8 @@ extern "C" int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int
                                 void **graph_exec) {
     if (!ctx || !graph_exec) return sk_fail(SK_EINVAL, "sk_graph_capture: NULL argument");
     *graph_exec = nullptr;
-    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL) return sk_fail(SK_EINVAL, "unknown flags %d", flags);
+    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR)
+        return sk_fail(SK_EINVAL, "unknown flags %d", flags);
     if (!stream) return sk_fail(SK_EINVAL, "sk_graph_capture: capture needs a non-default stream");
     std::vector<SkJob> js;
     int rc = convert_jobs(jobs, n_jobs, js);
@@ -591,7 +594,7 @@ extern "C" int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int
     SK_CU(cudaSetDevice(ctx->device));
     sk_graph *g = new sk_graph();
     g->device = ctx->device;
-    size_t need = flags == SK_PATH_AUTO ? sk_jobs_workspace_bytes(js.data(), n_jobs) : 0;
+    size_t need = flags != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(js.data(), n_jobs) : 0;
     if (need) {
         cudaError_t e = cudaMalloc(&g->ws, need);
         if (e != cudaSuccess) { delete g; return sk_fail(SK_ENOMEM, "graph workspace: %s", cudaGetErrorString(e)); }

@@ -63,6 +63,8 @@ void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_brng); k->d_brng = nullptr;
     cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
     cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
+    cudaFree(k->d_items_tc); k->d_items_tc = nullptr;
+    k->tc_ok = false;
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int v = 0; v < 2; ++v) { cudaFree(k->d_items_cap[c][v]); k->d_items_cap[c][v] = nullptr; }
     k->plan_ok = false;
@@ -163,6 +165,14 @@ int sk_plan_build(sk_kern *k) {
         if ((rc = upload(grp, &k->d_bgrp))) return rc;
         k->belt_P = belt_cost_p(n4);
         if ((rc = sk_plan_rebuild_belt_items(k))) return rc;
+        k->tc_ok = sk_tc_geometry(k->WPM, k->EMIN, n4, &k->tcg);
+        if (k->tc_ok) {
+            std::vector<int4> ti;
+            for (int gi = 0; gi < k->ngroups; ++gi)
+                for (int sb = 0; sb < n4 / SK_TC_SEGW; ++sb) ti.push_back(make_int4(gi, sb, 0, 0));
+            k->n_items_tc = (int)ti.size();
+            if ((rc = upload(ti, &k->d_items_tc))) return rc;
+        }
     }
 
     // ---- caps: northern rings below the belt (never the equator ring) and mirrors
@@ -288,7 +298,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
     // belt weight rows first (one pre-pass per job, shared by all its maps)
     std::vector<float *> wrows(n, nullptr);
     char *wp = (char *)ws;
-    if (path == SK_PATH_AUTO) {
+    if (path == SK_PATH_AUTO || path == SK_PATH_TENSOR) {
         for (int i = 0; i < n; ++i) {
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
@@ -330,6 +340,29 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
     SK_CU(cudaEventRecord(ctx->ev_fork, st));
     SK_CU(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
 
+    // batched tensor-core belt: one launch per job (its tile geometry is per operator)
+    if (path == SK_PATH_TENSOR) {
+        for (int i = 0; i < n; ++i) {
+            const sk_kern *k = jobs[i].k;
+            if (!k->plan_ok || k->nb == 0 || !k->tc_ok || jobs[i].batch == 0) continue;
+            Batcher b;
+            JobDesc d = base_desc(jobs[i]);
+            d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
+            d.EMIN = k->EMIN; d.EMAX = k->EMAX;
+            d.brng = k->d_brng; d.bw = wrows[i]; d.bgrp = k->d_bgrp;
+            d.items = k->d_items_tc;
+            d.n_items = k->n_items_tc;
+            d.flat_base = 0;
+            b.a.j[0] = d;
+            b.a.n_jobs = 1;
+            b.a.total = k->n_items_tc * (int)((jobs[i].batch + SK_TC_MAPS - 1) / SK_TC_MAPS);
+            b.a.status = ctx->d_status;
+            cudaEvent_t ev = sk_prof_begin(ctx, st);
+            SK_CU(sk_launch_belt_tc(b.a, k->tcg, k->WPM, std::min(b.a.total, ctx->num_sms), st));
+            sk_prof_end(ctx, "conv_belt_tc", ev, st);
+        }
+    }
+
     // belt: one launch family per tile width P
     const int Ps[] = {5, 7, 9, 11, 13, 15, 17};
     for (int P : Ps) {
@@ -348,6 +381,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         for (int i = 0; i < n; ++i) {
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || k->belt_P != P || jobs[i].batch == 0) continue;
+            if (path == SK_PATH_TENSOR && k->tc_ok) continue;     // done on the tensor cores
             JobDesc d = base_desc(jobs[i]);
             d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
             d.EMIN = k->EMIN; d.EMAX = k->EMAX;

@@ -72,6 +72,11 @@ struct sk_kern {
     int n_items_cap[SK_CAP_LS_CLASSES][2] = {};
     int n_cap_rings = 0;
     unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere), 2 general
+    // batched tensor-core form of the belt: (group, 128-pixel block) items
+    bool tc_ok = false;
+    TcGeom tcg{};
+    int4 *d_items_tc = nullptr;
+    int n_items_tc = 0;
 };
 
 // api.cu

@@ -62,6 +62,20 @@ __device__ __forceinline__ int sk_find_job(const JobsArg &a, int f) {
     return j;
 }
 
+// batched tensor-core belt (belt_tc.cu): items of SK_BELT_G rings x SK_TC_SEGW pixels x SK_TC_MAPS maps
+constexpr int SK_TC_MAPS = 32;
+constexpr int SK_TC_SEGW = 64;
+struct TcGeom {
+    int kt8;    // K extent of one segment's window, multiple of 8
+    int ka;     // 32-column atoms of the weight tile
+    int xl;     // pixels of the map tile (multiple of 32)
+    int xa;     // 32-column atoms of the map tile
+    int off4;   // EMIN - EMIN rounded down to a multiple of 4
+};
+bool sk_tc_geometry(int wpm, int emin, int n4, TcGeom *g);
+size_t sk_tc_smem(const TcGeom &g, int wpm);
+cudaError_t sk_launch_belt_tc(const JobsArg &a, const TcGeom &g, int wpm_max, int grid, cudaStream_t st);
+
 // set-up kernels (geometry.cu)
 cudaError_t sk_launch_ring_geom(long long nside, RingDev *rings, double *z, double *rho,
                                 double *theta, cudaStream_t st);

@@ -111,11 +111,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
 }
 
-// TF32 split of an fp32 value: hi keeps the 19 bits a TF32 operand reads (the
-// tensor core ignores the low 13 mantissa bits), lo = x - hi exactly.
+// TF32 split of an fp32 value, both parts rounded to nearest TF32 (a TF32
+// operand keeps 10 mantissa bits; truncation would bias every product the same
+// way): hi = rn(x), lo = rn(x - hi), x - hi exact in FP32.  hi*hi + hi*lo + lo*hi
+// then misses x*y by about 3 * 2^-22 relative, unbiased.
+__device__ __forceinline__ float rna_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    lo = x - hi;
+    hi = rna_tf32(x);
+    lo = rna_tf32(x - hi);
 }
 
 }  // namespace tc

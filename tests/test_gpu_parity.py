@@ -318,3 +318,32 @@ def test_belt_tile_widths_give_identical_results_and_autotune(sk, tmp_path):
     assert p1 == p2 and p1 in (5, 7, 9, 11, 13, 15, 17)
     assert torch.equal(sk.convolve(k, x), ref)
     sk._ctx.status()
+
+
+# ------------------------------------------------------------------ batched tensor-core form
+
+@pytest.mark.parametrize("nside,tc,batch,layout", [(32, 0.08, 40, 0), (64, 0.05, 33, 1), (128, 0.03, 32, 0),
+                                                   (256, 0.02, 5, 0)])
+def test_tensor_path_matches_oracle(sk, nside, tc, batch, layout):
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, 1024, layout)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc, layout)
+    x = white_noise_maps(nside, batch, 700 + nside)
+    y = gpu_conv(sk, k, x, path=sk.PATH_TENSOR)
+    yf = gpu_conv(sk, k, x, path=sk.PATH_AUTO)
+    for b in sorted({0, batch // 2, batch - 1}):
+        yo = O.conv_window(nside, V, tc, layout, x[b].astype(np.float64))
+        assert rms_rel(y[b], yo) <= RMS_BOUND, (b, rms_rel(y[b], yo))
+    assert rms_rel(y, yf) <= RMS_BOUND
+
+
+def test_tensor_path_n1024_batch_sampled(sk):
+    grp = WORKLOADS["n1024x64_batched"].groups[0]
+    ks = grp.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    k = sk.Kernel(sk.Geometry(sk._ctx, grp.nside), V, ks.theta_cut, ks.layout)
+    x = white_noise_maps(grp.nside, 64, grp.seed)
+    y = gpu_conv(sk, k, x, path=sk.PATH_TENSOR)
+    outs = sample_indices(x.shape[1], 3000, 303)
+    for b in (0, 31, 32, 63):
+        yo = O.conv_window(grp.nside, V, ks.theta_cut, ks.layout, x[b].astype(np.float64), outs)
+        assert rms_rel(y[b][outs], yo) <= RMS_BOUND
