@@ -5,21 +5,25 @@
 // the pair weight dOmega K_lin(gamma) depends on (o, i, e) only, not on j.  A
 // pre-pass evaluates those weight rows once per call (per-pair formula of the
 // general path, FP32, exact half-angle); the main kernel is then a register-
-// blocked 1-D correlation along each ring, one FFMA per in-cut pair.  Same
-// operator as the per-pair path (the real-space convolution of Sec. 2, Eq. 1
-// with the tabulated kernel of Sec. 3); only the order of work differs.
+// blocked 1-D correlation along each ring, one FMA per pair of its window.
+// Same operator as the per-pair path (the real-space convolution of Sec. 2,
+// Eq. 1 with the tabulated kernel of Sec. 3); only the order of work differs.
 //
 // Main kernel block: SK_BELT_G consecutive output rings, the same 32 P-pixel
-// segment of each, computed by SK_BELT_G / 2 consumer warps (two rings each, so
-// every staged strip value feeds two weight rows) plus one producer warp.  The
-// producer streams the segment's input-ring strips into shared memory with
-// 1-D TMA bulk copies (cp.async.bulk, 16-byte aligned pieces, split where the
-// strip wraps past phi = 2 pi) through SK_BELT_STAGES slots guarded by
-// full/empty mbarriers.  Lane l of a consumer warp owns outputs l P .. l P + P-1
-// of its two rings (P odd: the lanes' strip reads hit 32 distinct banks) and
-// slides 4 weights of each ring at a time over P + 3 strip values held in
-// registers.  Weight rows of all rings share one offset grid, so the two rows
-// of a warp line up on the same strip values.
+// segment of each, computed by SK_BELT_G / 2 consumer warps (two rings each)
+// plus one producer warp.  The producer streams, per input ring of the group,
+// the segment's strip of that ring together with the weight rows the eight
+// warps apply to it, into shared memory with 1-D TMA bulk copies
+// (cp.async.bulk, 16-byte aligned pieces, the strip split where it wraps past
+// phi = 2 pi) through SK_BELT_STAGES slots guarded by full/empty mbarriers.
+// Weight rows are stored as ring pairs, (w of ring 2w, w of ring 2w+1) per
+// offset, on one offset grid for all rings, so a lane applies both with one
+// paired FMA (fma.rn.f32x2, two IEEE FMAs) to the same strip value: lane l
+// owns outputs l P .. l P + P-1 of both rings (P odd: the lanes' strip reads
+// hit 32 distinct banks) and slides 4 offsets at a time over P + 3 strip
+// values held in registers.
+#include <algorithm>
+
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
@@ -107,10 +111,54 @@ __global__ void k_belt_weights(const JobDesc J, float *w) {
     }
 }
 
+// Weight rows as ring pairs, in the order the main kernel streams them: for
+// group grp, strip si (input ring i = bgrp[grp].x + si) and consumer warp w,
+// element c holds the weights at offset e = EMIN + c of output rings
+// o = b_lo + grp G + 2w and o + 1 against ring i, zero outside a row's window
+// (or where ring i is not in that output ring's window list).  One thread per
+// element.
+__global__ void k_belt_pairs(const JobDesc J, int ngroups, float2 *w) {
+    constexpr int NW = SK_BELT_WARPS;
+    const long long n = (long long)ngroups * J.smax * NW * J.WPM;
+    const double half_step = SK_PI / (2.0 * (double)J.n4);
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % J.WPM);
+        long long rest = idx / J.WPM;
+        const int wp = (int)(rest % NW);
+        rest /= NW;
+        const int si = (int)(rest % J.smax);
+        const int grp = (int)(rest / J.smax);
+        const int2 gr = J.bgrp[grp];
+        const int i = gr.x + si;
+        const int e = J.EMIN + c;
+        float v[2] = {0.0f, 0.0f};
+        if (i <= gr.y) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int rb = grp * SK_BELT_G + 2 * wp + q;
+                if (rb >= J.nb) continue;
+                const int ro = J.b_lo + rb;
+                const int p0 = J.pair_off[ro], p1 = J.pair_off[ro + 1];
+                const int p = p0 + (i - J.pairs[p0].ri);
+                if (p < p0 || p >= p1) continue;
+                const PairInfo P = J.pairs[p];
+                const int s_o = J.rings[ro].s;
+                const int ec = (s_o + 1 - P.s_i) >> 1;
+                if (e < ec - P.W || e > ec + P.W) continue;
+                const float x = (float)((double)(2 * e + P.s_i - s_o) * half_step);
+                v[q] = pair_weight(x, P.A, P.B, J.kp, J.tab);
+            }
+        }
+        w[idx] = make_float2(v[0], v[1]);
+    }
+}
+
 // Consumer warp w owns output rings b_lo + grp*G + 2w and + 2w + 1; lane l owns
-// pixels j0 + l P .. j0 + l P + P - 1 of both.  Strip s holds input ring
-// gr.x + i at offsets e = EMIN + m - lane-independent start, so pixel j + e of
-// the strip is xs[l P + (e - EMIN) + k].
+// pixels j0 + l P .. j0 + l P + P-1 of both.  Stage slot s holds the strip of
+// input ring gr.x + si at offsets e = EMIN + m (pixel j + e of the strip is
+// xs[l P + (e - EMIN) + k]), then the eight warps' pair rows of that ring, then
+// their chunk ranges.
 template <int P>
 __global__ void __launch_bounds__(32 * (SK_BELT_WARPS + 1))
 k_conv_belt(const __grid_constant__ JobsArg A) {
@@ -120,7 +168,6 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8 * (2 * S + 1));
     const uint32_t full0 = smem_addr(&bars[0]);
     const uint32_t empty0 = smem_addr(&bars[S]);
-    const uint32_t wfull = smem_addr(&bars[2 * S]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int TS = 32 * P;
 
@@ -129,14 +176,12 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, NW);
         }
-        mbar_init(wfull, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     uint32_t gs = 0;        // strips issued/consumed so far (stage and phase)
-    uint32_t witer = 0;     // weight loads so far (phase of wfull)
 
     for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
         if (*abort_flag) break;
@@ -148,13 +193,11 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
         const int j0 = it.y * TS;
         const int2 gr = J.bgrp[grp];
         const int nstrips = gr.y - gr.x + 1;
-        const int R2 = 2 * J.HM + 1;
-        float *sw = reinterpret_cast<float *>(smem + HDR);
-        float *szero = sw + G * R2 * J.WPM;
-        int2 *srng = reinterpret_cast<int2 *>(szero + J.WPM);
-        float *sstr = reinterpret_cast<float *>(srng + G * R2);
         const int L = TS + J.WPM;
-        const int slot = (L + 8 + 3) & ~3;
+        const int slot = (L + 8 + 3) & ~3;                          // strip floats
+        const uint32_t wbytes = (uint32_t)(NW * J.WPM * 8);         // pair rows of one strip
+        const uint32_t stage = (uint32_t)slot * 4u + wbytes + NW * 8u;
+        unsigned char *stage0 = smem + HDR;
         const long long js = (long long)j0 + J.EMIN;
         const int phase = (int)(((js % 4) + 4) % 4);
         const float *xmap = J.x + (long long)map * J.stride;
@@ -162,13 +205,20 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
         if (warp == NW) {
             // ---------------- producer ----------------
             if (lane == 0) {
-                const uint32_t wb = (uint32_t)(G * R2 * J.WPM * 4), rbytes = (uint32_t)(G * R2 * 8);
-                mbar_expect_tx(wfull, wb + rbytes);
-                bulk_g2s(smem_addr(sw), J.bw + (size_t)grp * G * R2 * J.WPM, wb, wfull);
-                bulk_g2s(smem_addr(srng), J.brng + (size_t)grp * G * R2, rbytes, wfull);
                 const int n = J.n4;
                 int pos0 = (int)(js % n);
                 if (pos0 < 0) pos0 += n;
+                uint32_t xbytes = 0;
+                {
+                    int pos = pos0, rem = L;
+                    while (rem > 0) {
+                        int len = min(rem, n - pos);
+                        int a0 = pos & ~3, a1 = (pos + len + 3) & ~3;
+                        xbytes += (uint32_t)(a1 - a0) * 4u;
+                        rem -= len; pos = 0;
+                    }
+                }
+                const size_t wrow0 = (size_t)grp * J.smax * NW;
                 for (int i = 0; i < nstrips; ++i) {
                     const uint32_t g = gs + i;
                     const int s = (int)(g % S);
@@ -176,18 +226,8 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                         !mbar_wait(empty0 + 8 * s, ((g / S) - 1) & 1, abort_flag, A.status))
                         break;
                     const float *xr = xmap + J.rings[gr.x + i].start;
-                    const uint32_t dst0 = smem_addr(sstr + (size_t)s * slot);
-                    uint32_t total = 0;
-                    {
-                        int pos = pos0, rem = L;
-                        while (rem > 0) {
-                            int len = min(rem, n - pos);
-                            int a0 = pos & ~3, a1 = (pos + len + 3) & ~3;
-                            total += (uint32_t)(a1 - a0) * 4u;
-                            rem -= len; pos = 0;
-                        }
-                    }
-                    mbar_expect_tx(full0 + 8 * s, total);
+                    const uint32_t dst0 = smem_addr(stage0 + (size_t)s * stage);
+                    mbar_expect_tx(full0 + 8 * s, xbytes + wbytes + NW * 8u);
                     int pos = pos0, rem = L, m = 0;
                     while (rem > 0) {
                         int len = min(rem, n - pos);
@@ -196,54 +236,40 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                         bulk_g2s(dst, xr + a0, (uint32_t)(a1 - a0) * 4u, full0 + 8 * s);
                         m += len; rem -= len; pos = 0;
                     }
+                    const size_t row = wrow0 + (size_t)i * NW;
+                    bulk_g2s(dst0 + (uint32_t)slot * 4u, J.bwp + row * J.WPM, wbytes, full0 + 8 * s);
+                    bulk_g2s(dst0 + (uint32_t)slot * 4u + wbytes, J.bpr + row, NW * 8u, full0 + 8 * s);
                 }
             }
         } else {
             // ---------------- consumers ----------------
-            for (int c = threadIdx.x; c < J.WPM; c += 32 * NW) szero[c] = 0.0f;
-            asm volatile("bar.sync 1, %0;" ::"r"(32 * NW));       // consumers only
-            const int rb0 = grp * G + 2 * warp;                   // belt-relative output rings rb0, rb0 + 1
+            const int rb0 = grp * SK_BELT_G + 2 * warp;           // belt-relative output rings rb0, rb0 + 1
             const int ro0 = J.b_lo + rb0;
             const bool v0 = rb0 < J.nb, v1 = rb0 + 1 < J.nb;
-            float acc0[P], acc1[P];
+            float2 acc[P];                                        // (ring rb0, ring rb0 + 1)
 #pragma unroll
-            for (int k = 0; k < P; ++k) { acc0[k] = 0.0f; acc1[k] = 0.0f; }
-            bool ok = mbar_wait(wfull, witer & 1, abort_flag, A.status);
-            for (int i = 0; i < nstrips && ok; ++i) {
+            for (int k = 0; k < P; ++k) acc[k] = make_float2(0.0f, 0.0f);
+            bool ok = true;
+            for (int i = 0; i < nstrips; ++i) {
                 const uint32_t g = gs + i;
                 const int s = (int)(g % S);
                 if (!mbar_wait(full0 + 8 * s, (g / S) & 1, abort_flag, A.status)) { ok = false; break; }
-                const int d0 = gr.x + i - ro0, d1 = d0 - 1;
-                const bool u0 = v0 && d0 >= -J.HM && d0 <= J.HM;
-                const bool u1 = v1 && d1 >= -J.HM && d1 <= J.HM;
-                const int2 r0 = u0 ? srng[(2 * warp) * R2 + d0 + J.HM] : make_int2(1, 0);
-                const int2 r1 = u1 ? srng[(2 * warp + 1) * R2 + d1 + J.HM] : make_int2(1, 0);
-                const int ca = min(r0.x, r1.x), cb = max(r0.y, r1.y);
-                const float *wr0 = (r0.x <= r0.y) ? sw + (size_t)((2 * warp) * R2 + d0 + J.HM) * J.WPM : szero;
-                const float *wr1 = (r1.x <= r1.y) ? sw + (size_t)((2 * warp + 1) * R2 + d1 + J.HM) * J.WPM : szero;
-                const float *xs = sstr + (size_t)s * slot + phase + lane * P;
-                for (int c = ca; c <= cb; ++c) {
-                    const float4 wa = *reinterpret_cast<const float4 *>(wr0 + 4 * c);
-                    const float4 wb = *reinterpret_cast<const float4 *>(wr1 + 4 * c);
+                const unsigned char *sb = stage0 + (size_t)s * stage;
+                const int2 r = reinterpret_cast<const int2 *>(sb + (size_t)slot * 4 + wbytes)[warp];
+                const float4 *wr = reinterpret_cast<const float4 *>(sb + (size_t)slot * 4) + warp * (J.WPM / 2);
+                const float *xs = reinterpret_cast<const float *>(sb) + phase + lane * P;
+                for (int c = r.x; c <= r.y; ++c) {
+                    const float4 wa = wr[2 * c], wb = wr[2 * c + 1];
+                    const float2 w4[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
+                                          make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
                     float xv[P + 3];
 #pragma unroll
                     for (int u = 0; u < P + 3; ++u) xv[u] = xs[4 * c + u];
 #pragma unroll
-                    for (int k = 0; k < P; ++k) acc0[k] = fmaf(wa.x, xv[k], acc0[k]);
+                    for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int k = 0; k < P; ++k) acc1[k] = fmaf(wb.x, xv[k], acc1[k]);
-#pragma unroll
-                    for (int k = 0; k < P; ++k) acc0[k] = fmaf(wa.y, xv[k + 1], acc0[k]);
-#pragma unroll
-                    for (int k = 0; k < P; ++k) acc1[k] = fmaf(wb.y, xv[k + 1], acc1[k]);
-#pragma unroll
-                    for (int k = 0; k < P; ++k) acc0[k] = fmaf(wa.z, xv[k + 2], acc0[k]);
-#pragma unroll
-                    for (int k = 0; k < P; ++k) acc1[k] = fmaf(wb.z, xv[k + 2], acc1[k]);
-#pragma unroll
-                    for (int k = 0; k < P; ++k) acc0[k] = fmaf(wa.w, xv[k + 3], acc0[k]);
-#pragma unroll
-                    for (int k = 0; k < P; ++k) acc1[k] = fmaf(wb.w, xv[k + 3], acc1[k]);
+                        for (int k = 0; k < P; ++k)
+                            acc[k] = __ffma2_rn(w4[u], make_float2(xv[k + u], xv[k + u]), acc[k]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty0 + 8 * s);
@@ -255,7 +281,7 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
                         const int j = j0 + lane * P + k;
-                        if (j < J.n4) yr[j] = acc0[k];
+                        if (j < J.n4) yr[j] = acc[k].x;
                     }
                 }
                 if (v1) {
@@ -263,13 +289,12 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
                         const int j = j0 + lane * P + k;
-                        if (j < J.n4) yr[j] = acc1[k];
+                        if (j < J.n4) yr[j] = acc[k].y;
                     }
                 }
             }
         }
         gs += (uint32_t)nstrips;
-        ++witer;
         __syncthreads();
     }
 }
@@ -290,14 +315,16 @@ int occupancy_p(size_t smem) {
     return nb;
 }
 
+size_t stage_bytes(int P, int wpm) {
+    const int L = 32 * P + wpm;
+    const int slot = (L + 8 + 3) & ~3;
+    return (size_t)slot * 4 + (size_t)SK_BELT_WARPS * wpm * 8 + (size_t)SK_BELT_WARPS * 8;
+}
+
 size_t belt_smem(const JobsArg &a, int P) {
     size_t m = 0;
     for (int j = 0; j < a.n_jobs; ++j) {
-        const JobDesc &J = a.j[j];
-        const int R2 = 2 * J.HM + 1;
-        const int L = 32 * P + J.WPM;
-        const int slot = (L + 8 + 3) & ~3;
-        size_t b = HDR + (size_t)G * R2 * J.WPM * 4 + (size_t)J.WPM * 4 + (size_t)G * R2 * 8 + (size_t)S * slot * 4;
+        const size_t b = HDR + (size_t)S * stage_bytes(P, a.j[j].WPM);
         m = b > m ? b : m;
     }
     return m;
@@ -311,6 +338,16 @@ cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st) 
     k_belt_weights<<<rows, 32, 0, st>>>(j, w);
     return cudaGetLastError();
 }
+
+cudaError_t sk_launch_belt_pairs(const JobDesc &j, int ngroups, float2 *w, cudaStream_t st) {
+    const long long n = (long long)ngroups * j.smax * SK_BELT_WARPS * j.WPM;
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    k_belt_pairs<<<(unsigned)std::min<long long>(blocks, 1 << 20), 256, 0, st>>>(j, ngroups, w);
+    return cudaGetLastError();
+}
+
+size_t sk_belt_smem_bytes(int P, int wpm) { return HDR + (size_t)S * stage_bytes(P, wpm); }
 
 cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st) {
     if (a.total <= 0) return cudaSuccess;

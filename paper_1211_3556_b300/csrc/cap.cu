@@ -40,11 +40,14 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Nearest input pixel of output jo.  In the caps jo < n_o / 4 <= 2 Nside and
-// n_i <= 4 Nside <= 32768, so the numerator stays below 2^31.
-__device__ __forceinline__ int centre_of(int jo, int n_o, int s_o, const PairInfo &P) {
+// Nearest input pixel of output jo: floor(num / (2 n_o)) with num below 2^31
+// (in the caps jo < n_o / 4 <= 2 Nside and n_i <= 4 Nside <= 32768), by the
+// item's multiply-high constants for the divisor 2 n_o: mg = ceil(2^(31+l) / d),
+// l = ceil(log2 d), quotient = umulhi(num, mg) >> (l - 1), exact for every
+// num < 2^31 (Granlund and Montgomery 1994, Thm 4.2).
+__device__ __forceinline__ int centre_of(int jo, int n_o, int s_o, const PairInfo &P, unsigned mg, int sh) {
     const unsigned num = (unsigned)(2 * jo + s_o) * (unsigned)P.n_i + (unsigned)(1 - P.s_i) * (unsigned)n_o;
-    return (int)(num / (2u * (unsigned)n_o));
+    return (int)(__umulhi(num, mg) >> sh);
 }
 
 // q of window pixel jlo (may be negative) for output jo: both products are below 2^31.
@@ -70,10 +73,13 @@ __device__ __forceinline__ void stage_ring(float4 *buf, const JobDesc &J, const 
     const int n = P.n_i, Q = n >> 2, s = P.s_i;
     const float *xn = xmap + J.rings[P.ri].start, *xs = xmap + J.rings[ri_south].start;
     float *b = reinterpret_cast<float *>(buf);
-    int io0 = (u0 + (int)threadIdx.x) % n;
-    if (io0 < 0) io0 += n;
-    int ir0 = (Q - s - u0 - (int)threadIdx.x) % n;
-    if (ir0 < 0) ir0 += n;
+    // first element of this thread, reduced into [0, n) (u0 > -n, the offsets stay below 2n + CT)
+    int io0 = u0 + (int)threadIdx.x;
+    while (io0 < 0) io0 += n;
+    while (io0 >= n) io0 -= n;
+    int ir0 = Q - s - u0 - (int)threadIdx.x;
+    while (ir0 < 0) ir0 += n;
+    while (ir0 >= n) ir0 -= n;
     for (int k = 0; k < 4; ++k) {
         int io = io0 + k * Q, ir = ir0 + k * Q;
         if (io >= n) io -= n;
@@ -113,6 +119,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const int map = local / J.n_items;
         const int4 it = J.items[local - map * J.n_items];
         const int ro = it.x, j0 = it.y;
+        const unsigned mg = (unsigned)it.z;            // division by 2 n_o (centre_of)
+        const int sh = it.w;
         const RingDev R = J.rings[ro];
         const int Qo = R.n >> 2;
         const int T = base_count(Qo, R.s);
@@ -125,15 +133,17 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const float *xmap = J.x + (long long)map * J.stride;
         const int p0 = J.pair_off[ro], p1 = J.pair_off[ro + 1];
 
-        float acc[16];                                      // [h*4+k] pair, [8 + h*4+k] reflected
+        // acc2[k] = (north pair, north reflected), acc2[4 + k] = (south pair, south reflected)
+        // of quarter turn k
+        float2 acc2[8];
 #pragma unroll
-        for (int s = 0; s < 16; ++s) acc[s] = 0.0f;
+        for (int s = 0; s < 8; ++s) acc2[s] = make_float2(0.0f, 0.0f);
 
         {
             const PairInfo P = J.pairs[p0];
             int before, cnt;
             win_shape(P, before, cnt);
-            const int c0 = centre_of(j0, R.n, R.s, P), c1 = centre_of(jlast, R.n, R.s, P);
+            const int c0 = centre_of(j0, R.n, R.s, P, mg, sh), c1 = centre_of(jlast, R.n, R.s, P, mg, sh);
             stage_ring<LS>(sx, J, xmap, P, J.nr - 1 - P.ri, c0 - before, c1 - c0 + cnt);
             cp_commit();
         }
@@ -143,7 +153,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const PairInfo Pn = J.pairs[p + 1];
                 int before, cnt;
                 win_shape(Pn, before, cnt);
-                const int c0 = centre_of(j0, R.n, R.s, Pn), c1 = centre_of(jlast, R.n, R.s, Pn);
+                const int c0 = centre_of(j0, R.n, R.s, Pn, mg, sh), c1 = centre_of(jlast, R.n, R.s, Pn, mg, sh);
                 stage_ring<LS>(sx + (buf ^ 1) * 4 * LS, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before,
                                c1 - c0 + cnt);
             }
@@ -154,23 +164,40 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const PairInfo P = J.pairs[p];
                 int before, cnt;
                 win_shape(P, before, cnt);
-                const int cb = centre_of(j0, R.n, R.s, P);
-                const int c = centre_of(jo, R.n, R.s, P);
+                const int cb = centre_of(j0, R.n, R.s, P, mg, sh);
+                const int c = centre_of(jo, R.n, R.s, P, mg, sh);
                 // |q| < 2^24 on this window (checked when the plan was built): qf + m dq is exact
                 const float qf = (float)q_of(c - before, jo, R.n, R.s, P);
                 const float dq = (float)(2 * R.n);
                 const float4 *xs = sx + buf * 4 * LS + (c - cb);
-#pragma unroll 2
-                for (int m = 0; m < cnt; ++m) {
-                    const float w = fast_weight<SERIES, SMALLA, BIASED>(fmaf((float)m, dq, qf) * P.c0,
-                                                                        P.A, P.B, J.kp, stab);
+                int m = 0;
+                if (SERIES) {
+                    // two window pixels per step in paired FP32 arithmetic
+                    float2 mm = make_float2(0.0f, 1.0f);
+                    for (; m + 1 < cnt; m += 2) {
+                        const float2 w = fast_weight2<SMALLA, BIASED>(
+                            __fmul2_rn(__ffma2_rn(mm, f2(dq), f2(qf)), f2(P.c0)), P.A, P.B, J.kp, stab);
+                        mm = __fadd2_rn(mm, f2(2.0f));
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 wh = f2(h ? w.y : w.x);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const float4 v = xs[k * LS + m + h];
+                                acc2[k] = __ffma2_rn(wh, make_float2(v.x, v.y), acc2[k]);        // north: pair, reflected
+                                acc2[4 + k] = __ffma2_rn(wh, make_float2(v.z, v.w), acc2[4 + k]);  // south: pair, reflected
+                            }
+                        }
+                    }
+                }
+                for (; m < cnt; ++m) {
+                    const float2 w = f2(fast_weight<SERIES, SMALLA, BIASED>(fmaf((float)m, dq, qf) * P.c0, P.A, P.B,
+                                                                            J.kp, stab));
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float4 v = xs[k * LS + m];
-                        acc[k] = fmaf(w, v.x, acc[k]);             // north, pair
-                        acc[8 + k] = fmaf(w, v.y, acc[8 + k]);     // north, reflected
-                        acc[4 + k] = fmaf(w, v.z, acc[4 + k]);     // south, pair
-                        acc[12 + k] = fmaf(w, v.w, acc[12 + k]);   // south, reflected
+                        acc2[k] = __ffma2_rn(w, make_float2(v.x, v.y), acc2[k]);
+                        acc2[4 + k] = __ffma2_rn(w, make_float2(v.z, v.w), acc2[4 + k]);
                     }
                 }
             }
@@ -181,14 +208,14 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
             float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                yn[jo + k * Qo] = acc[k];
-                ys[jo + k * Qo] = acc[4 + k];
+                yn[jo + k * Qo] = acc2[k].x;
+                ys[jo + k * Qo] = acc2[4 + k].x;
             }
             if (refl) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    yn[jr + k * Qo] = acc[8 + k];
-                    ys[jr + k * Qo] = acc[12 + k];
+                    yn[jr + k * Qo] = acc2[k].y;
+                    ys[jr + k * Qo] = acc2[4 + k].y;
                 }
             }
         }

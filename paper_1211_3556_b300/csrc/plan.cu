@@ -40,6 +40,17 @@ void cap_needs(int j0, int jlast, int n_o, int s_o, const PairInfo &P, int &L, l
     qmax = (long long)n_o + P.n_i + (long long)cnt * 2 * n_o;
 }
 
+// Multiply-high division by d (2 <= d < 2^31) for numerators below 2^31:
+// mg = ceil(2^(31+l) / d) with l = ceil(log2 d) (below 2^32), and
+// floor(n / d) = umulhi(n, mg) >> sh, sh = l - 1 (Granlund and Montgomery 1994).
+void div_magic(unsigned d, unsigned &mg, int &sh) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long m = ((1ull << (31 + l)) + d - 1) / d;
+    mg = (unsigned)m;
+    sh = l - 1;
+}
+
 int belt_cost_p(int n4) {
     // choose the outputs-per-thread P: tail waste of the last segment against the
     // per-chunk overhead of reloading P + 3 strip values for 4P FFMAs
@@ -62,6 +73,7 @@ void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_ring_path); k->d_ring_path = nullptr;
     cudaFree(k->d_brng); k->d_brng = nullptr;
     cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
+    cudaFree(k->d_bpr); k->d_bpr = nullptr;
     cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
     cudaFree(k->d_items_tc); k->d_items_tc = nullptr;
     k->tc_ok = false;
@@ -103,6 +115,8 @@ int sk_plan_build(sk_kern *k) {
             if (P.n_i != n4 || P.W < 0) return false;
             int nch = (2 * P.W + 1 + 3) / 4;
             if (4 * nch > n4) return false;
+            // the streamed strips and weight rows of the widest tile must fit in shared memory
+            if (sk_belt_smem_bytes(17, 2 * P.W + 8) > (size_t)200 * 1024) return false;
         }
         return true;
     };
@@ -160,9 +174,31 @@ int sk_plan_build(sk_kern *k) {
             }
             grp[gi] = make_int2(lo, hi);
         }
+        // pair rows as the FP32 kernel streams them: strip si of group gi is input
+        // ring grp[gi].x + si; warp w applies rows (2w, i) and (2w + 1, i) to it
+        int smax = 0;
+        for (int gi = 0; gi < k->ngroups; ++gi) smax = std::max(smax, grp[gi].y - grp[gi].x + 1);
+        k->smax = smax;
+        std::vector<int2> pr((size_t)k->ngroups * smax * SK_BELT_WARPS, make_int2(1, 0));
+        for (int gi = 0; gi < k->ngroups; ++gi)
+            for (int si = 0; si <= grp[gi].y - grp[gi].x; ++si)
+                for (int w = 0; w < SK_BELT_WARPS; ++w) {
+                    int lo = 1 << 30, hi = -1;
+                    for (int q = 0; q < 2; ++q) {
+                        const int rb = gi * SK_BELT_G + 2 * w + q;
+                        const int d = grp[gi].x + si - (b_lo + rb);
+                        if (rb >= k->nb || d < -HM || d > HM) continue;
+                        const int2 r = rng[(size_t)rb * R2 + d + HM];
+                        if (r.x > r.y) continue;
+                        lo = std::min(lo, r.x);
+                        hi = std::max(hi, r.y);
+                    }
+                    if (lo <= hi) pr[((size_t)gi * smax + si) * SK_BELT_WARPS + w] = make_int2(lo, hi);
+                }
         int rc;
         if ((rc = upload(rng, &k->d_brng))) return rc;
         if ((rc = upload(grp, &k->d_bgrp))) return rc;
+        if ((rc = upload(pr, &k->d_bpr))) return rc;
         k->belt_P = belt_cost_p(n4);
         if ((rc = sk_plan_rebuild_belt_items(k))) return rc;
         k->tc_ok = sk_tc_geometry(k->WPM, k->EMIN, n4, &k->tcg);
@@ -204,7 +240,10 @@ int sk_plan_build(sk_kern *k) {
         if (!ok || cls < 0) continue;
         covered[r] = covered[nr - 1 - r] = 1;
         ++k->n_cap_rings;
-        for (int j0 = 0; j0 < T; j0 += SK_CAP_CT) cap_items[cls][series ? 1 : 0].push_back(make_int4(r, j0, 0, 0));
+        unsigned mg; int sh;
+        div_magic(2u * (unsigned)R[r].n, mg, sh);
+        for (int j0 = 0; j0 < T; j0 += SK_CAP_CT)
+            cap_items[cls][series ? 1 : 0].push_back(make_int4(r, j0, (int)mg, sh));
     }
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int v = 0; v < 2; ++v) {
@@ -236,8 +275,10 @@ int sk_plan_build(sk_kern *k) {
 
 size_t sk_plan_workspace_bytes(const sk_kern *k) {
     if (!k->plan_ok || k->nb == 0) return 0;
-    size_t rows = (size_t)k->ngroups * SK_BELT_G * (2 * k->HM + 1);
-    return (rows * k->WPM * sizeof(float) + 255) & ~(size_t)255;
+    // the larger of the two weight layouts: rows (tensor-core form) and ring pairs (FP32 form)
+    const size_t rows = (size_t)k->ngroups * SK_BELT_G * (2 * k->HM + 1) * k->WPM * sizeof(float);
+    const size_t pairs = (size_t)k->ngroups * k->smax * SK_BELT_WARPS * k->WPM * sizeof(float2);
+    return (std::max(rows, pairs) + 255) & ~(size_t)255;
 }
 
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n) {
@@ -269,6 +310,18 @@ JobDesc base_desc(const SkJob &jb) {
     d.stride = jb.stride;
     d.batch = (int)jb.batch;
     d.n4 = (int)(4 * k->g->nside);
+    return d;
+}
+
+// The job's belt fields; w is the per-call weight workspace (rows or ring pairs).
+JobDesc belt_desc(const SkJob &jb, float *w) {
+    const sk_kern *k = jb.k;
+    JobDesc d = base_desc(jb);
+    d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
+    d.EMIN = k->EMIN; d.EMAX = k->EMAX;
+    d.brng = k->d_brng; d.bgrp = k->d_bgrp;
+    d.bw = w;
+    d.smax = k->smax; d.bpr = k->d_bpr; d.bwp = reinterpret_cast<const float2 *>(w);
     return d;
 }
 
@@ -304,12 +357,12 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
             wrows[i] = (float *)wp;
             wp += sk_plan_workspace_bytes(k);
-            JobDesc d = base_desc(jobs[i]);
-            d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
-            d.EMIN = k->EMIN; d.EMAX = k->EMAX;
-            d.brng = k->d_brng;
+            JobDesc d = belt_desc(jobs[i], nullptr);
             cudaEvent_t ev = sk_prof_begin(ctx, st);
-            SK_CU(sk_launch_belt_weights(d, wrows[i], st));
+            if (path == SK_PATH_TENSOR && k->tc_ok)
+                SK_CU(sk_launch_belt_weights(d, wrows[i], st));                 // rows
+            else
+                SK_CU(sk_launch_belt_pairs(d, k->ngroups, (float2 *)wrows[i], st));  // ring pairs
             sk_prof_end(ctx, "belt_weights", ev, st);
         }
     }
@@ -346,10 +399,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || !k->tc_ok || jobs[i].batch == 0) continue;
             Batcher b;
-            JobDesc d = base_desc(jobs[i]);
-            d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
-            d.EMIN = k->EMIN; d.EMAX = k->EMAX;
-            d.brng = k->d_brng; d.bw = wrows[i]; d.bgrp = k->d_bgrp;
+            JobDesc d = belt_desc(jobs[i], wrows[i]);
             d.items = k->d_items_tc;
             d.n_items = k->n_items_tc;
             d.flat_base = 0;
@@ -382,10 +432,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || k->belt_P != P || jobs[i].batch == 0) continue;
             if (path == SK_PATH_TENSOR && k->tc_ok) continue;     // done on the tensor cores
-            JobDesc d = base_desc(jobs[i]);
-            d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
-            d.EMIN = k->EMIN; d.EMAX = k->EMAX;
-            d.brng = k->d_brng; d.bw = wrows[i]; d.bgrp = k->d_bgrp;
+            JobDesc d = belt_desc(jobs[i], wrows[i]);
             b.add(d, k->d_items_belt, k->n_items_belt);
             if (b.full()) { int rc = flush(); if (rc) return rc; }
         }

@@ -64,6 +64,8 @@ struct sk_kern {
     int b_lo = 0, nb = 0, HM = 0, WPM = 0, EMIN = 0, EMAX = 0, ngroups = 0;
     int belt_P = 13;
     int2 *d_brng = nullptr, *d_bgrp = nullptr;
+    int smax = 0;                          // strips per group of the pair layout
+    int2 *d_bpr = nullptr;                 // [groups][smax][warps] pair-row chunk ranges
     int4 *d_items_belt = nullptr;
     int n_items_belt = 0;
     // caps (one item list per strip class)

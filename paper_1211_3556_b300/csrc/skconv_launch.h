@@ -45,6 +45,10 @@ struct JobDesc {
     const int2 *brng;     // [nb_pad][2HM+1] first and last 4-chunk (of offsets EMIN + 4c ..) with weights
     const float *bw;      // [nb_pad][2HM+1][WPM] weights on the common offset grid (workspace, per call)
     const int2 *bgrp;     // [groups] first and last input ring of each group
+    // belt weights as ring pairs, streamed with the strips (FP32 CUDA-core path)
+    int smax;             // strips per group in the pair layout (max over groups)
+    const int2 *bpr;      // [groups][smax][SK_BELT_WARPS] chunk range of the pair row (union of both rows)
+    const float2 *bwp;    // [groups][smax][SK_BELT_WARPS][WPM] (weight of ring 2w, of ring 2w+1) per offset
     // cap path
     int cap_ls;           // strip stride class
 };
@@ -94,6 +98,8 @@ cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const
 // convolution kernels; grid = number of blocks (persistent)
 cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);
 cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st);
+cudaError_t sk_launch_belt_pairs(const JobDesc &j, int ngroups, float2 *w, cudaStream_t st);
+size_t sk_belt_smem_bytes(int P, int wpm);   // dynamic shared memory of a belt block
 cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st);
 // mode bits: 1 sin series valid on every window of the items, 2 theta_cut <= 0.25
 // (asin series), 4 biased node layout
