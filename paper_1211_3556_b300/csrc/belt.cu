@@ -20,8 +20,8 @@
 // offset, on one offset grid for all rings, so a lane applies both with one
 // paired FMA (fma.rn.f32x2, two IEEE FMAs) to the same strip value: lane l
 // owns outputs l P .. l P + P-1 of both rings (P odd: the lanes' strip reads
-// hit 32 distinct banks) and slides 4 offsets at a time over P + 3 strip
-// values held in registers.
+// hit 32 distinct banks) and slides 4 offsets at a time over a ring of strip
+// values held in registers, loading 4 new values per step.
 #include <algorithm>
 
 #include "skconv.h"
@@ -113,10 +113,10 @@ __global__ void k_belt_weights(const JobDesc J, float *w) {
 
 // Weight rows as ring pairs, in the order the main kernel streams them: for
 // group grp, strip si (input ring i = bgrp[grp].x + si) and consumer warp w,
-// element c holds the weights at offset e = EMIN + c of output rings
-// o = b_lo + grp G + 2w and o + 1 against ring i, zero outside a row's window
-// (or where ring i is not in that output ring's window list).  One thread per
-// element.
+// with (o, nch) = bpr of that row, element c < 4 nch holds the weights at offset
+// e = EMIN + o + c of output rings b_lo + grp G + 2w and + 1 against ring i,
+// zero outside a row's window (or where ring i is not in that output ring's
+// window list) and past 4 nch.  One thread per element.
 __global__ void k_belt_pairs(const JobDesc J, int ngroups, float2 *w) {
     constexpr int NW = SK_BELT_WARPS;
     const long long n = (long long)ngroups * J.smax * NW * J.WPM;
@@ -131,9 +131,10 @@ __global__ void k_belt_pairs(const JobDesc J, int ngroups, float2 *w) {
         const int grp = (int)(rest / J.smax);
         const int2 gr = J.bgrp[grp];
         const int i = gr.x + si;
-        const int e = J.EMIN + c;
+        const int2 on = J.bpr[rest * NW + wp];
+        const int e = J.EMIN + on.x + c;
         float v[2] = {0.0f, 0.0f};
-        if (i <= gr.y) {
+        if (i <= gr.y && c < 4 * on.y) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int rb = grp * SK_BELT_G + 2 * wp + q;
@@ -157,8 +158,10 @@ __global__ void k_belt_pairs(const JobDesc J, int ngroups, float2 *w) {
 // Consumer warp w owns output rings b_lo + grp*G + 2w and + 2w + 1; lane l owns
 // pixels j0 + l P .. j0 + l P + P-1 of both.  Stage slot s holds the strip of
 // input ring gr.x + si at offsets e = EMIN + m (pixel j + e of the strip is
-// xs[l P + (e - EMIN) + k]), then the eight warps' pair rows of that ring, then
-// their chunk ranges.
+// xs[l P + (e - EMIN) + k]; 4 values past the last offset, so that a row's
+// last 4-offset chunk reads loaded values), then the eight warps' pair rows of
+// that ring, then their (start, chunks).  Warps meet only at the stage
+// barriers: no block-wide barrier between work items.
 template <int P>
 __global__ void __launch_bounds__(32 * (SK_BELT_WARPS + 1))
 k_conv_belt(const __grid_constant__ JobsArg A) {
@@ -193,7 +196,7 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
         const int j0 = it.y * TS;
         const int2 gr = J.bgrp[grp];
         const int nstrips = gr.y - gr.x + 1;
-        const int L = TS + J.WPM;
+        const int L = TS + J.WPM + 4;
         const int slot = (L + 8 + 3) & ~3;                          // strip floats
         const uint32_t wbytes = (uint32_t)(NW * J.WPM * 8);         // pair rows of one strip
         const uint32_t stage = (uint32_t)slot * 4u + wbytes + NW * 8u;
@@ -257,19 +260,43 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                 const unsigned char *sb = stage0 + (size_t)s * stage;
                 const int2 r = reinterpret_cast<const int2 *>(sb + (size_t)slot * 4 + wbytes)[warp];
                 const float4 *wr = reinterpret_cast<const float4 *>(sb + (size_t)slot * 4) + warp * (J.WPM / 2);
-                const float *xs = reinterpret_cast<const float *>(sb) + phase + lane * P;
-                for (int c = r.x; c <= r.y; ++c) {
-                    const float4 wa = wr[2 * c], wb = wr[2 * c + 1];
-                    const float2 w4[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
-                                          make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
-                    float xv[P + 3];
+                const float *xs = reinterpret_cast<const float *>(sb) + phase + lane * P + r.x;
+                // Strip values x[m] = xs[m] in a register ring of XB slots (slot m mod XB),
+                // duplicated into both halves of a float2 for the paired FMA.  Chunk c
+                // (offsets 4c .. 4c+3) uses x[4c .. 4c + P + 2]; while it runs, the 4
+                // values chunk c + 1 adds are loaded into slots it does not use
+                // (XB >= P + 7).  The chunk loop is unrolled XB / 4 times so that every
+                // slot index is a compile-time constant.
+                constexpr int XB = ((P + 7 + 3) / 4) * 4, U = XB / 4;
+                const int nch = r.y;
+                float2 xb[XB];
 #pragma unroll
-                    for (int u = 0; u < P + 3; ++u) xv[u] = xs[4 * c + u];
+                for (int j = 0; j < P + 3; ++j) {
+                    const float v = xs[j];
+                    xb[j] = make_float2(v, v);
+                }
+                for (int c0 = 0; c0 < nch; c0 += U) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                    for (int uu = 0; uu < U; ++uu) {
+                        const int c = c0 + uu;
+                        if (c < nch) {
+                            if (c + 1 < nch) {
 #pragma unroll
-                        for (int k = 0; k < P; ++k)
-                            acc[k] = __ffma2_rn(w4[u], make_float2(xv[k + u], xv[k + u]), acc[k]);
+                                for (int v = 0; v < 4; ++v) {
+                                    const float t = xs[4 * c + P + 3 + v];
+                                    xb[(4 * uu + P + 3 + v) % XB] = make_float2(t, t);
+                                }
+                            }
+                            const float4 wa = wr[2 * c], wb = wr[2 * c + 1];
+                            const float2 w4[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
+                                                  make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                                for (int k = 0; k < P; ++k)
+                                    acc[k] = __ffma2_rn(w4[u], xb[(4 * uu + k + u) % XB], acc[k]);
+                        }
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty0 + 8 * s);
@@ -295,7 +322,6 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
             }
         }
         gs += (uint32_t)nstrips;
-        __syncthreads();
     }
 }
 
@@ -316,7 +342,7 @@ int occupancy_p(size_t smem) {
 }
 
 size_t stage_bytes(int P, int wpm) {
-    const int L = 32 * P + wpm;
+    const int L = 32 * P + wpm + 4;
     const int slot = (L + 8 + 3) & ~3;
     return (size_t)slot * 4 + (size_t)SK_BELT_WARPS * wpm * 8 + (size_t)SK_BELT_WARPS * 8;
 }

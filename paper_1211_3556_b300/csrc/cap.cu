@@ -16,22 +16,26 @@
 // output is written twice.  Same operator as the per-pair path (Sec. 2, Eq. 1
 // with the tabulated kernel of Sec. 3); only the order of work differs.
 //
-// Work item: (northern output ring, first base pixel) for CT base outputs.
-// For every input ring of the window the block stages 4 rows (quarter turns) of
+// Work item: (northern output ring, first base pixel) for CT base outputs,
+// CT / 2 threads, each owning two adjacent base outputs jA, jB = jA + 1.  For
+// every input ring of the window the block stages 4 rows (quarter turns) of
 // float4 (north pixel, its reflection, south pixel, its reflection) covering
-// the union of the CT windows, unwrapped, with cp.async, double-buffered; one
-// 128-bit load then feeds 4 of the 16 images.  The node values V_k dOmega sit
-// in shared memory (FP32, the slope formed on the fly): the lanes of a warp
-// look up nodes spread over a few hundred entries, a gather that costs a few
-// bank wavefronts from shared memory but one L1 wavefront per distinct line
-// from global memory.
+// the union of the CT windows, unwrapped, even positions before odd ones, with
+// cp.async, double-buffered.  A thread walks the union of its two windows
+// (they start at most a pixel or two apart): one 128-bit load feeds 4 of the
+// 16 images of both outputs, and both weights come from one paired evaluation
+// (fma.rn.f32x2: two IEEE operations).  The node values V_k dOmega sit in shared memory (FP32, the
+// slope formed on the fly): the lanes of a warp look up nodes spread over a
+// few hundred entries, a gather that costs a few bank wavefronts from shared
+// memory but one L1 wavefront per distinct line from global memory.
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
 
 namespace {
 
-constexpr int CT = SK_CAP_CT;
+constexpr int CT = SK_CAP_CT;       // base outputs per work item
+constexpr int NTH = CT / 2;         // threads per block: two adjacent base outputs each
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -64,16 +68,23 @@ __device__ __forceinline__ void win_shape(const PairInfo &P, int &before, int &c
 // Base outputs of a quarter ring of Q pixels with shift s: [0, T).
 __device__ __forceinline__ int base_count(int Q, int s) { return s ? (Q + 1) / 2 : Q / 2 + 1; }
 
+// Strip layout of one row: even positions first, then odd ones.  A lane owns
+// two adjacent outputs, so at one step the lanes of a warp read positions about
+// two apart; with this layout they read consecutive float4 (one parity) instead
+// of every other one.
+template <int LS>
+__device__ __forceinline__ int split_index(int m) { return (m & 1) * (LS / 2) + (m >> 1); }
+
 // Stage row k, element m = (xN[a], xN[b], xS[a], xS[b]) with a = u0 + m + kQ and
 // b = Q - s - (u0 + m) + kQ (indices mod n): the pixel and its reflection on the
-// northern ring and on its southern mirror.
+// northern ring and on its southern mirror, at split_index(m).
 template <int LS>
 __device__ __forceinline__ void stage_ring(float4 *buf, const JobDesc &J, const float *xmap,
                                            const PairInfo &P, int ri_south, int u0, int L) {
     const int n = P.n_i, Q = n >> 2, s = P.s_i;
     const float *xn = xmap + J.rings[P.ri].start, *xs = xmap + J.rings[ri_south].start;
     float *b = reinterpret_cast<float *>(buf);
-    // first element of this thread, reduced into [0, n) (u0 > -n, the offsets stay below 2n + CT)
+    // first element of this thread, reduced into [0, n) (u0 > -n, the offsets stay below 2n + NTH)
     int io0 = u0 + (int)threadIdx.x;
     while (io0 < 0) io0 += n;
     while (io0 >= n) io0 -= n;
@@ -84,22 +95,35 @@ __device__ __forceinline__ void stage_ring(float4 *buf, const JobDesc &J, const 
         int io = io0 + k * Q, ir = ir0 + k * Q;
         if (io >= n) io -= n;
         if (ir >= n) ir -= n;
-        for (int m = threadIdx.x; m < L; m += CT) {
-            float *d = b + 4 * (k * LS + m);
+        for (int m = threadIdx.x; m < L; m += NTH) {
+            float *d = b + 4 * (k * LS + split_index<LS>(m));
             cp_async4(d, xn + io);
             cp_async4(d + 1, xn + ir);
             cp_async4(d + 2, xs + io);
             cp_async4(d + 3, xs + ir);
-            io += CT;
+            io += NTH;
             while (io >= n) io -= n;
-            ir -= CT;
+            ir -= NTH;
             while (ir < 0) ir += n;
         }
     }
 }
 
+// acc[k] += w (v.x, v.y), acc[4 + k] += w (v.z, v.w) for the staged pixel m of
+// each quarter turn k: (north pair, north reflected), (south pair, south reflected).
+template <int LS>
+__device__ __forceinline__ void mac16(float2 *acc, float w, const float4 *xs, int m) {
+    const float2 ww = f2(w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 v = xs[k * LS + m];
+        acc[k] = __ffma2_rn(ww, make_float2(v.x, v.y), acc[k]);
+        acc[4 + k] = __ffma2_rn(ww, make_float2(v.z, v.w), acc[4 + k]);
+    }
+}
+
 template <int LS, int MODE>
-__global__ void __launch_bounds__(CT)
+__global__ void __launch_bounds__(NTH)
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
     extern __shared__ __align__(16) float4 sx[];      // [2][4][LS] strips, then the node values
@@ -111,7 +135,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const JobDesc &J = A.j[jn];
         if (jn != cur_job) {                 // uniform across the block
             __syncthreads();
-            for (int k = t; k < J.kp.nt; k += CT) stab[k] = J.tab[k].x;
+            for (int k = t; k < J.kp.nt; k += NTH) stab[k] = J.tab[k].x;
             __syncthreads();
             cur_job = jn;
         }
@@ -125,19 +149,20 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const int Qo = R.n >> 2;
         const int T = base_count(Qo, R.s);
         const int jlast = min(j0 + CT - 1, T - 1);
-        const int jo = j0 + t;
-        const bool active = jo < T;
-        const int jr = Qo - jo - R.s;                       // reflection of jo in the quarter
-        const bool refl = active && jr < Qo && jr >= T;
+        const int jA = j0 + 2 * t, jB = jA + 1;
+        const bool actA = jA < T, actB = jB < T;
+        const int jrA = Qo - jA - R.s, jrB = Qo - jB - R.s;   // reflections in the quarter
+        const bool reflA = actA && jrA < Qo && jrA >= T;
+        const bool reflB = actB && jrB < Qo && jrB >= T;
         const int ro_s = J.nr - 1 - ro;
         const float *xmap = J.x + (long long)map * J.stride;
         const int p0 = J.pair_off[ro], p1 = J.pair_off[ro + 1];
 
-        // acc2[k] = (north pair, north reflected), acc2[4 + k] = (south pair, south reflected)
-        // of quarter turn k
-        float2 acc2[8];
+        // accX[k] = (north pair, north reflected), accX[4 + k] = (south pair, south
+        // reflected) of quarter turn k, for outputs jA and jB
+        float2 accA[8], accB[8];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) acc2[s] = make_float2(0.0f, 0.0f);
+        for (int s = 0; s < 8; ++s) { accA[s] = make_float2(0.0f, 0.0f); accB[s] = make_float2(0.0f, 0.0f); }
 
         {
             const PairInfo P = J.pairs[p0];
@@ -160,62 +185,84 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
             cp_commit();
             cp_wait1();
             __syncthreads();
-            if (active) {
+            if (actA) {
                 const PairInfo P = J.pairs[p];
                 int before, cnt;
                 win_shape(P, before, cnt);
                 const int cb = centre_of(j0, R.n, R.s, P, mg, sh);
-                const int c = centre_of(jo, R.n, R.s, P, mg, sh);
-                // |q| < 2^24 on this window (checked when the plan was built): qf + m dq is exact
-                const float qf = (float)q_of(c - before, jo, R.n, R.s, P);
-                const float dq = (float)(2 * R.n);
-                const float4 *xs = sx + buf * 4 * LS + (c - cb);
-                int m = 0;
+                const int cA = centre_of(jA, R.n, R.s, P, mg, sh);
+                const int dl = actB ? centre_of(jB, R.n, R.s, P, mg, sh) - cA : 0;   // 0, 1 or 2
+                const int cnt_u = cnt + dl;             // union of the two windows, from A's start
+                // |q| < 2^24 on these windows (checked when the plan was built): exact in FP32
+                const float qA0 = (float)q_of(cA - before, jA, R.n, R.s, P);
+                const float dqo = (float)(2 * R.n);     // q step per input pixel
+                const float dqi = (float)(2 * P.n_i);   // q of output jA minus q of output jB
+                const float4 *xrow = sx + buf * 4 * LS;
+                const int pA = cA - cb;                 // strip position of the union's first pixel
                 if (SERIES) {
-                    // two window pixels per step in paired FP32 arithmetic
-                    float2 mm = make_float2(0.0f, 1.0f);
-                    for (; m + 1 < cnt; m += 2) {
-                        const float2 w = fast_weight2<SMALLA, BIASED>(
-                            __fmul2_rn(__ffma2_rn(mm, f2(dq), f2(qf)), f2(P.c0)), P.A, P.B, J.kp, stab);
-                        mm = __fadd2_rn(mm, f2(2.0f));
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float2 wh = f2(h ? w.y : w.x);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float4 v = xs[k * LS + m + h];
-                                acc2[k] = __ffma2_rn(wh, make_float2(v.x, v.y), acc2[k]);        // north: pair, reflected
-                                acc2[4 + k] = __ffma2_rn(wh, make_float2(v.z, v.w), acc2[4 + k]);  // south: pair, reflected
-                            }
+                    // narrow windows only: a pixel of the union outside one output's window is
+                    // outside its cut, and the cut test gives it weight 0.  Pixels go in pairs
+                    // (pA + m, pA + m + 1): one of each parity, at x0[i] and x1[i], i = m / 2.
+                    const float4 *x0 = xrow + split_index<LS>(pA);
+                    const float4 *x1 = xrow + split_index<LS>(pA + 1);
+                    float2 q = make_float2(qA0, qA0 - dqi);   // q of pixel m for outputs (A, B)
+#pragma unroll 1
+                    for (int m = 0; m < cnt_u; m += 2) {
+                        const int i = m >> 1;
+                        const float2 q1 = __fadd2_rn(q, f2(dqo));
+                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), P.A, P.B, J.kp, stab);
+                        const float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), P.A, P.B, J.kp, stab);
+                        q = __fadd2_rn(q1, f2(dqo));
+                        mac16<LS>(accA, w0.x, x0, i);
+                        mac16<LS>(accB, w0.y, x0, i);
+                        if (m + 1 < cnt_u) {
+                            mac16<LS>(accA, w1.x, x1, i);
+                            mac16<LS>(accB, w1.y, x1, i);
                         }
                     }
-                }
-                for (; m < cnt; ++m) {
-                    const float2 w = f2(fast_weight<SERIES, SMALLA, BIASED>(fmaf((float)m, dq, qf) * P.c0, P.A, P.B,
-                                                                            J.kp, stab));
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float4 v = xs[k * LS + m];
-                        acc2[k] = __ffma2_rn(w, make_float2(v.x, v.y), acc2[k]);
-                        acc2[4 + k] = __ffma2_rn(w, make_float2(v.z, v.w), acc2[4 + k]);
+                } else {
+                    // windows may be whole rings: restrict each output to its own window
+                    for (int m = 0; m < cnt_u; ++m) {
+                        const float qa = fmaf((float)m, dqo, qA0);
+                        float wa = fast_weight<SERIES, SMALLA, BIASED>(qa * P.c0, P.A, P.B, J.kp, stab);
+                        float wb = fast_weight<SERIES, SMALLA, BIASED>((qa - dqi) * P.c0, P.A, P.B, J.kp, stab);
+                        wa = m < cnt ? wa : 0.0f;
+                        wb = m >= dl ? wb : 0.0f;
+                        const float4 *xm = xrow + split_index<LS>(pA + m);
+                        mac16<LS>(accA, wa, xm, 0);
+                        mac16<LS>(accB, wb, xm, 0);
                     }
                 }
             }
             __syncthreads();
         }
-        if (active) {
-            float *yn = J.y + (long long)map * J.stride + R.start;
-            float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
+        float *yn = J.y + (long long)map * J.stride + R.start;
+        float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
+        if (actA) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                yn[jo + k * Qo] = acc2[k].x;
-                ys[jo + k * Qo] = acc2[4 + k].x;
+                yn[jA + k * Qo] = accA[k].x;
+                ys[jA + k * Qo] = accA[4 + k].x;
             }
-            if (refl) {
+            if (reflA) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    yn[jr + k * Qo] = acc2[k].y;
-                    ys[jr + k * Qo] = acc2[4 + k].y;
+                    yn[jrA + k * Qo] = accA[k].y;
+                    ys[jrA + k * Qo] = accA[4 + k].y;
+                }
+            }
+        }
+        if (actB) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                yn[jB + k * Qo] = accB[k].x;
+                ys[jB + k * Qo] = accB[4 + k].x;
+            }
+            if (reflB) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    yn[jrB + k * Qo] = accB[k].y;
+                    ys[jrB + k * Qo] = accB[4 + k].y;
                 }
             }
         }
@@ -235,7 +282,7 @@ cudaError_t launch_lm(const JobsArg &a, int grid, cudaStream_t st) {
     const size_t smem = cap_smem(LS, max_nt(a));
     cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_cap<LS, MODE><<<grid, CT, smem, st>>>(a);
+    k_conv_cap<LS, MODE><<<grid, NTH, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -244,7 +291,7 @@ int occupancy_lm(int nt) {
     const size_t smem = cap_smem(LS, nt);
     cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE>, CT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE>, NTH, smem);
     return nb;
 }
 

@@ -33,11 +33,13 @@ int centre(int jo, int n_o, int s_o, const PairInfo &P) {
 }
 
 // Strip length a cap item needs for input ring P, and the largest |q| of its windows.
+// The cap kernel evaluates narrow windows in pixel pairs, one pixel past the
+// window when its count is odd (that pixel is outside the cut).
 void cap_needs(int j0, int jlast, int n_o, int s_o, const PairInfo &P, int &L, long long &qmax) {
     int cnt = P.W < 0 ? P.n_i : 2 * P.W + 1;
-    L = centre(jlast, n_o, s_o, P) - centre(j0, n_o, s_o, P) + cnt;
+    L = centre(jlast, n_o, s_o, P) - centre(j0, n_o, s_o, P) + cnt + 1;
     // q at the window centre is below n_o + n_i in magnitude; each step adds 2 n_o
-    qmax = (long long)n_o + P.n_i + (long long)cnt * 2 * n_o;
+    qmax = (long long)n_o + P.n_i + (long long)(cnt + 1) * 2 * n_o;
 }
 
 // Multiply-high division by d (2 <= d < 2^31) for numerators below 2^31:
@@ -151,6 +153,7 @@ int sk_plan_build(sk_kern *k) {
                 EMAX = std::max(EMAX, ec + P.W);
             }
         }
+        std::vector<int2> ew((size_t)nb_pad * R2, make_int2(1, 0));     // exact offset range per row
         for (int rb = 0; rb < k->nb; ++rb) {
             const int r = b_lo + rb;
             covered[r] = 1;
@@ -159,6 +162,7 @@ int sk_plan_build(sk_kern *k) {
                 const int d = P.ri - r;
                 const int ec = (R[r].s + 1 - P.s_i) >> 1;
                 rng[(size_t)rb * R2 + d + HM] = make_int2((ec - P.W - EMIN) >> 2, (ec + P.W - EMIN) >> 2);
+                ew[(size_t)rb * R2 + d + HM] = make_int2(ec - P.W, ec + P.W);
             }
         }
         const int WPM = ((EMAX - EMIN + 1) + 3) & ~3;
@@ -179,21 +183,23 @@ int sk_plan_build(sk_kern *k) {
         int smax = 0;
         for (int gi = 0; gi < k->ngroups; ++gi) smax = std::max(smax, grp[gi].y - grp[gi].x + 1);
         k->smax = smax;
-        std::vector<int2> pr((size_t)k->ngroups * smax * SK_BELT_WARPS, make_int2(1, 0));
+        // (first offset - EMIN, 4-offset chunks) of the union of both rows' windows; (0, 0) = empty
+        std::vector<int2> pr((size_t)k->ngroups * smax * SK_BELT_WARPS, make_int2(0, 0));
         for (int gi = 0; gi < k->ngroups; ++gi)
             for (int si = 0; si <= grp[gi].y - grp[gi].x; ++si)
                 for (int w = 0; w < SK_BELT_WARPS; ++w) {
-                    int lo = 1 << 30, hi = -1;
+                    int lo = 1 << 30, hi = -(1 << 30);
                     for (int q = 0; q < 2; ++q) {
                         const int rb = gi * SK_BELT_G + 2 * w + q;
                         const int d = grp[gi].x + si - (b_lo + rb);
                         if (rb >= k->nb || d < -HM || d > HM) continue;
-                        const int2 r = rng[(size_t)rb * R2 + d + HM];
-                        if (r.x > r.y) continue;
-                        lo = std::min(lo, r.x);
-                        hi = std::max(hi, r.y);
+                        const int2 e = ew[(size_t)rb * R2 + d + HM];
+                        if (e.x > e.y) continue;
+                        lo = std::min(lo, e.x);
+                        hi = std::max(hi, e.y);
                     }
-                    if (lo <= hi) pr[((size_t)gi * smax + si) * SK_BELT_WARPS + w] = make_int2(lo, hi);
+                    if (lo <= hi)
+                        pr[((size_t)gi * smax + si) * SK_BELT_WARPS + w] = make_int2(lo - EMIN, (hi - lo + 4) / 4);
                 }
         int rc;
         if ((rc = upload(rng, &k->d_brng))) return rc;
@@ -223,7 +229,7 @@ int sk_plan_build(sk_kern *k) {
         bool series = true;        // |dphi / 2| <= 1/8 on every window of the ring
         for (int p = off[r]; p < off[r + 1]; ++p) {
             const PairInfo &P = pairs[p];
-            if (P.W < 0 || (P.W + 1.5) * SK_PI / P.n_i > 0.125) series = false;
+            if (P.W < 0 || (P.W + 2.5) * SK_PI / P.n_i > 0.125) series = false;
         }
         for (int j0 = 0; j0 < T && ok; j0 += SK_CAP_CT) {
             const int jl = std::min(j0 + SK_CAP_CT - 1, T - 1);

@@ -14,7 +14,7 @@ constexpr int SK_MAXJ = 16;            // jobs per launch (more: several launche
 constexpr int SK_MAX_NODES = 16384;    // largest kernel table
 constexpr int SK_BELT_G = 16;          // output rings per belt block (two per consumer warp)
 constexpr int SK_BELT_WARPS = SK_BELT_G / 2;   // consumer warps per belt block
-constexpr int SK_BELT_STAGES = 8;      // input-ring strips in flight per belt block
+constexpr int SK_BELT_STAGES = 16;     // input-ring strips in flight per belt block
 
 struct JobDesc {
     // operator
@@ -47,8 +47,10 @@ struct JobDesc {
     const int2 *bgrp;     // [groups] first and last input ring of each group
     // belt weights as ring pairs, streamed with the strips (FP32 CUDA-core path)
     int smax;             // strips per group in the pair layout (max over groups)
-    const int2 *bpr;      // [groups][smax][SK_BELT_WARPS] chunk range of the pair row (union of both rows)
-    const float2 *bwp;    // [groups][smax][SK_BELT_WARPS][WPM] (weight of ring 2w, of ring 2w+1) per offset
+    const int2 *bpr;      // [groups][smax][SK_BELT_WARPS] (o, nch): the pair row covers offsets
+                          // EMIN + o .. EMIN + o + 4 nch - 1 (union of both rows' windows)
+    const float2 *bwp;    // [groups][smax][SK_BELT_WARPS][WPM]: element c = (weight of ring 2w, of
+                          // ring 2w+1) at offset EMIN + o + c, zero past 4 nch
     // cap path
     int cap_ls;           // strip stride class
 };
