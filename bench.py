@@ -232,6 +232,8 @@ def run_ours(args):
         ops.append(dict(group=group, geom=g, kern=k, x=x, y=y, maps=maps, pairs=pairs, by_path=by_path))
     pairs_step = sum(o["pairs"] * o["group"].batch for o in ops)
     maps_step = sum(o["group"].batch for o in ops)
+    # plan-time tuning of the belt tile width on the step's own maps (outside the timed region)
+    belt_tiles = [o["kern"].autotune(o["x"], out=o["y"]) for o in ops]
 
     if len(ops) == 1:
         o = ops[0]
@@ -307,6 +309,7 @@ def run_ours(args):
         xb = torch.from_numpy(make_maps(grp)).cuda()
         yb = torch.empty_like(xb)
         pb = kb.count_pairs()
+        kb.autotune(xb, out=yb)
         batched = {"workload": "n1024x64_batched", "unit": UNIT}
         for name, path in (("fp32", sk.PATH_AUTO), ("tensor_3xtf32", sk.PATH_TENSOR)):
             msb = time_steps(torch, lambda: sk.convolve(kb, xb, out=yb, path=path), max(3, min(args.steps, 20)), 2,
@@ -334,7 +337,8 @@ def run_ours(args):
                        "n_nodes": ks.n_nodes, "fwhm_arcmin": ks.fwhm_arcmin, "lmax": ks.lmax, "lcut": ks.lcut,
                        "pairs_per_step_per_gpu": pairs_step,
                        "l2": "inputs larger than L2 (map bytes %d > 126 MB)" % int(sum(o["maps"].nbytes for o in ops)),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "belt_tile": belt_tiles},
             "rms_rel_vs_fp64": rms,
             "f_eval": value / world * FLOP_PER_PAIR_EVAL / (FP32_PEAK_TFLOPS * 1e12),
             "f_mac": value / world * FLOP_PER_PAIR / (FP32_PEAK_TFLOPS * 1e12),

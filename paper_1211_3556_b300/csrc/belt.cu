@@ -163,7 +163,7 @@ __global__ void k_belt_pairs(const JobDesc J, int ngroups, float2 *w) {
 // that ring, then their (start, chunks).  Warps meet only at the stage
 // barriers: no block-wide barrier between work items.
 template <int P>
-__global__ void __launch_bounds__(32 * (SK_BELT_WARPS + 1))
+__global__ void __launch_bounds__(32 * (SK_BELT_WARPS + 1), 3)
 k_conv_belt(const __grid_constant__ JobsArg A) {
     constexpr int NW = SK_BELT_WARPS;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -275,21 +275,26 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                     const float v = xs[j];
                     xb[j] = make_float2(v, v);
                 }
+                float4 wa = wr[0], wb = wr[1];              // weights of chunk c, loaded a chunk ahead
                 for (int c0 = 0; c0 < nch; c0 += U) {
 #pragma unroll
                     for (int uu = 0; uu < U; ++uu) {
                         const int c = c0 + uu;
                         if (c < nch) {
+                            float4 wa_n = wa, wb_n = wb;
                             if (c + 1 < nch) {
 #pragma unroll
                                 for (int v = 0; v < 4; ++v) {
                                     const float t = xs[4 * c + P + 3 + v];
                                     xb[(4 * uu + P + 3 + v) % XB] = make_float2(t, t);
                                 }
+                                wa_n = wr[2 * c + 2];
+                                wb_n = wr[2 * c + 3];
                             }
-                            const float4 wa = wr[2 * c], wb = wr[2 * c + 1];
                             const float2 w4[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
                                                   make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
+                            wa = wa_n;
+                            wb = wb_n;
 #pragma unroll
                             for (int u = 0; u < 4; ++u)
 #pragma unroll

@@ -21,7 +21,8 @@
 // every input ring of the window the block stages 4 rows (quarter turns) of
 // float4 (north pixel, its reflection, south pixel, its reflection) covering
 // the union of the CT windows, unwrapped, even positions before odd ones, with
-// cp.async, double-buffered.  A thread walks the union of its two windows
+// cp.async (one buffer: the small footprint lets four blocks share an SM, and
+// they cover each other's staging waits).  A thread walks the union of its two windows
 // (they start at most a pixel or two apart): one 128-bit load feeds 4 of the
 // 16 images of both outputs, and both weights come from one paired evaluation
 // (fma.rn.f32x2: two IEEE operations).  The node values V_k dOmega sit in shared memory (FP32, the
@@ -42,7 +43,7 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Nearest input pixel of output jo: floor(num / (2 n_o)) with num below 2^31
 // (in the caps jo < n_o / 4 <= 2 Nside and n_i <= 4 Nside <= 32768), by the
@@ -126,8 +127,8 @@ template <int LS, int MODE>
 __global__ void __launch_bounds__(NTH)
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
-    extern __shared__ __align__(16) float4 sx[];      // [2][4][LS] strips, then the node values
-    float *stab = reinterpret_cast<float *>(sx + 2 * 4 * LS);
+    extern __shared__ __align__(16) float4 sx[];      // [4][LS] strip rows, then the node values
+    float *stab = reinterpret_cast<float *>(sx + 4 * LS);
     const int t = threadIdx.x;
     int cur_job = -1;
     for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
@@ -164,26 +165,18 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
 #pragma unroll
         for (int s = 0; s < 8; ++s) { accA[s] = make_float2(0.0f, 0.0f); accB[s] = make_float2(0.0f, 0.0f); }
 
-        {
-            const PairInfo P = J.pairs[p0];
-            int before, cnt;
-            win_shape(P, before, cnt);
-            const int c0 = centre_of(j0, R.n, R.s, P, mg, sh), c1 = centre_of(jlast, R.n, R.s, P, mg, sh);
-            stage_ring<LS>(sx, J, xmap, P, J.nr - 1 - P.ri, c0 - before, c1 - c0 + cnt);
-            cp_commit();
-        }
         for (int p = p0; p < p1; ++p) {
-            const int buf = (p - p0) & 1;
-            if (p + 1 < p1) {
-                const PairInfo Pn = J.pairs[p + 1];
+            // one strip buffer: stage ring p once every thread is done with ring p - 1 (the
+            // barrier at the end of the previous step); other blocks on the SM cover the wait
+            {
+                const PairInfo Pn = J.pairs[p];
                 int before, cnt;
                 win_shape(Pn, before, cnt);
                 const int c0 = centre_of(j0, R.n, R.s, Pn, mg, sh), c1 = centre_of(jlast, R.n, R.s, Pn, mg, sh);
-                stage_ring<LS>(sx + (buf ^ 1) * 4 * LS, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before,
-                               c1 - c0 + cnt);
+                stage_ring<LS>(sx, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before, c1 - c0 + cnt);
             }
             cp_commit();
-            cp_wait1();
+            cp_wait0();
             __syncthreads();
             if (actA) {
                 const PairInfo P = J.pairs[p];
@@ -197,7 +190,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const float qA0 = (float)q_of(cA - before, jA, R.n, R.s, P);
                 const float dqo = (float)(2 * R.n);     // q step per input pixel
                 const float dqi = (float)(2 * P.n_i);   // q of output jA minus q of output jB
-                const float4 *xrow = sx + buf * 4 * LS;
+                const float4 *xrow = sx;
                 const int pA = cA - cb;                 // strip position of the union's first pixel
                 if (SERIES) {
                     // narrow windows only: a pixel of the union outside one output's window is
@@ -269,7 +262,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
     }
 }
 
-size_t cap_smem(int LS, int nt) { return (size_t)2 * 4 * LS * sizeof(float4) + (size_t)nt * sizeof(float); }
+size_t cap_smem(int LS, int nt) { return (size_t)4 * LS * sizeof(float4) + (size_t)nt * sizeof(float); }
 
 int max_nt(const JobsArg &a) {
     int m = 2;
