@@ -17,15 +17,17 @@
 // with the tabulated kernel of Sec. 3); only the order of work differs.
 //
 // Work item: (northern output ring, first base pixel) for CT base outputs,
-// CT / 2 threads, each owning two adjacent base outputs jA, jB = jA + 1.  For
-// every input ring of the window the block stages 4 rows (quarter turns) of
-// float4 (north pixel, its reflection, south pixel, its reflection) covering
-// the union of the CT windows, unwrapped, even positions before odd ones, with
-// cp.async (one buffer: the small footprint lets four blocks share an SM, and
-// they cover each other's staging waits).  A thread walks the union of its two windows
-// (they start at most a pixel or two apart): one 128-bit load feeds 4 of the
-// 16 images of both outputs, and both weights come from one paired evaluation
-// (fma.rn.f32x2: two IEEE operations).  The node values V_k dOmega sit in shared memory (FP32, the
+// CT / 2 threads, each owning two adjacent base outputs jA, jB = jA + 1; a
+// block runs two work items side by side (each half with its own named
+// barrier), so that they share one copy of the node table.  For every input
+// ring of the window a half stages 4 rows (quarter turns) of float4 (north
+// pixel, its reflection, south pixel, its reflection) covering the union of
+// its CT windows, unwrapped, even positions before odd ones, with cp.async
+// into two buffers (ring p + 1 is copied while ring p is summed).  A thread
+// walks the union of its two windows (they start at most a pixel or two
+// apart): one 128-bit load feeds 4 of the 16 images of both outputs, and both
+// weights come from one paired evaluation (fma.rn.f32x2: two IEEE
+// operations).  The node values V_k dOmega sit in shared memory (FP32, the
 // slope formed on the fly): the lanes of a warp look up nodes spread over a
 // few hundred entries, a gather that costs a few bank wavefronts from shared
 // memory but one L1 wavefront per distinct line from global memory.
@@ -36,7 +38,15 @@
 namespace {
 
 constexpr int CT = SK_CAP_CT;       // base outputs per work item
-constexpr int NTH = CT / 2;         // threads per block: two adjacent base outputs each
+constexpr int NTH = CT / 2;         // threads per work item: two adjacent base outputs each
+constexpr int HALVES = SK_CAP_ITEMS_PER_BLOCK;   // work items in flight per block (one node table)
+// strip buffers per work item: two (stage ring p + 1 while ring p is summed) where they fit
+template <int LS>
+__host__ __device__ constexpr int cap_bufs() { return LS <= 320 ? 2 : 1; }
+
+__device__ __forceinline__ void half_sync(int half) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(NTH) : "memory");
+}
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -44,6 +54,7 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Nearest input pixel of output jo: floor(num / (2 n_o)) with num below 2^31
 // (in the caps jo < n_o / 4 <= 2 Nside and n_i <= 4 Nside <= 32768), by the
@@ -81,22 +92,22 @@ __device__ __forceinline__ int split_index(int m) { return (m & 1) * (LS / 2) + 
 // northern ring and on its southern mirror, at split_index(m).
 template <int LS>
 __device__ __forceinline__ void stage_ring(float4 *buf, const JobDesc &J, const float *xmap,
-                                           const PairInfo &P, int ri_south, int u0, int L) {
+                                           const PairInfo &P, int ri_south, int u0, int L, int t) {
     const int n = P.n_i, Q = n >> 2, s = P.s_i;
     const float *xn = xmap + J.rings[P.ri].start, *xs = xmap + J.rings[ri_south].start;
     float *b = reinterpret_cast<float *>(buf);
     // first element of this thread, reduced into [0, n) (u0 > -n, the offsets stay below 2n + NTH)
-    int io0 = u0 + (int)threadIdx.x;
+    int io0 = u0 + t;
     while (io0 < 0) io0 += n;
     while (io0 >= n) io0 -= n;
-    int ir0 = Q - s - u0 - (int)threadIdx.x;
+    int ir0 = Q - s - u0 - t;
     while (ir0 < 0) ir0 += n;
     while (ir0 >= n) ir0 -= n;
     for (int k = 0; k < 4; ++k) {
         int io = io0 + k * Q, ir = ir0 + k * Q;
         if (io >= n) io -= n;
         if (ir >= n) ir -= n;
-        for (int m = threadIdx.x; m < L; m += NTH) {
+        for (int m = t; m < L; m += NTH) {
             float *d = b + 4 * (k * LS + split_index<LS>(m));
             cp_async4(d, xn + io);
             cp_async4(d + 1, xn + ir);
@@ -124,22 +135,20 @@ __device__ __forceinline__ void mac16(float2 *acc, float w, const float4 *xs, in
 }
 
 template <int LS, int MODE>
-__global__ void __launch_bounds__(NTH)
+__global__ void __launch_bounds__(NTH * HALVES)
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
-    extern __shared__ __align__(16) float4 sx[];      // [4][LS] strip rows, then the node values
-    float *stab = reinterpret_cast<float *>(sx + 4 * LS);
-    const int t = threadIdx.x;
-    int cur_job = -1;
-    for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
-        const int jn = sk_find_job(A, f);
-        const JobDesc &J = A.j[jn];
-        if (jn != cur_job) {                 // uniform across the block
-            __syncthreads();
-            for (int k = t; k < J.kp.nt; k += NTH) stab[k] = J.tab[k].x;
-            __syncthreads();
-            cur_job = jn;
-        }
+    constexpr int NB = cap_bufs<LS>();
+    // [HALVES][NB][4][LS] strip rows, then the node values (one table: every job of a launch
+    // uses the same kernel table)
+    extern __shared__ __align__(16) float4 sx[];
+    float *stab = reinterpret_cast<float *>(sx + HALVES * NB * 4 * LS);
+    for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * HALVES) stab[k] = A.j[0].tab[k].x;
+    __syncthreads();
+    const int half = threadIdx.x / NTH, t = threadIdx.x % NTH;
+    float4 *const sbuf = sx + half * NB * 4 * LS;
+    for (int f = blockIdx.x * HALVES + half; f < A.total; f += gridDim.x * HALVES) {
+        const JobDesc &J = A.j[sk_find_job(A, f)];
         const int local = f - J.flat_base;
         const int map = local / J.n_items;
         const int4 it = J.items[local - map * J.n_items];
@@ -165,19 +174,29 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
 #pragma unroll
         for (int s = 0; s < 8; ++s) { accA[s] = make_float2(0.0f, 0.0f); accB[s] = make_float2(0.0f, 0.0f); }
 
-        for (int p = p0; p < p1; ++p) {
-            // one strip buffer: stage ring p once every thread is done with ring p - 1 (the
-            // barrier at the end of the previous step); other blocks on the SM cover the wait
-            {
-                const PairInfo Pn = J.pairs[p];
-                int before, cnt;
-                win_shape(Pn, before, cnt);
-                const int c0 = centre_of(j0, R.n, R.s, Pn, mg, sh), c1 = centre_of(jlast, R.n, R.s, Pn, mg, sh);
-                stage_ring<LS>(sx, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before, c1 - c0 + cnt);
-            }
+        auto stage = [&](int p, float4 *dst) {
+            const PairInfo Pn = J.pairs[p];
+            int before, cnt;
+            win_shape(Pn, before, cnt);
+            const int c0 = centre_of(j0, R.n, R.s, Pn, mg, sh), c1 = centre_of(jlast, R.n, R.s, Pn, mg, sh);
+            stage_ring<LS>(dst, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before, c1 - c0 + cnt, t);
             cp_commit();
-            cp_wait0();
-            __syncthreads();
+        };
+        if (NB == 2) stage(p0, sbuf);
+        for (int p = p0; p < p1; ++p) {
+            float4 *const xbuf = sbuf + (NB == 2 ? ((p - p0) & 1) : 0) * 4 * LS;
+            if (NB == 2) {
+                // stage ring p + 1 into the other buffer (free since the barrier that ended
+                // ring p - 1), then wait for ring p's copies
+                if (p + 1 < p1) stage(p + 1, sbuf + ((p + 1 - p0) & 1) * 4 * LS);
+                else cp_commit();
+                cp_wait1();
+            } else {
+                // one buffer: stage ring p once every thread is done with ring p - 1
+                stage(p, xbuf);
+                cp_wait0();
+            }
+            half_sync(half);
             if (actA) {
                 const PairInfo P = J.pairs[p];
                 int before, cnt;
@@ -190,7 +209,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const float qA0 = (float)q_of(cA - before, jA, R.n, R.s, P);
                 const float dqo = (float)(2 * R.n);     // q step per input pixel
                 const float dqi = (float)(2 * P.n_i);   // q of output jA minus q of output jB
-                const float4 *xrow = sx;
+                const float4 *xrow = xbuf;
                 const int pA = cA - cb;                 // strip position of the union's first pixel
                 if (SERIES) {
                     // narrow windows only: a pixel of the union outside one output's window is
@@ -227,7 +246,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     }
                 }
             }
-            __syncthreads();
+            half_sync(half);
         }
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
@@ -262,7 +281,10 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
     }
 }
 
-size_t cap_smem(int LS, int nt) { return (size_t)4 * LS * sizeof(float4) + (size_t)nt * sizeof(float); }
+size_t cap_smem(int LS, int nt) {
+    const int nb = LS <= 320 ? 2 : 1;         // cap_bufs<LS>()
+    return (size_t)HALVES * nb * 4 * LS * sizeof(float4) + (size_t)nt * sizeof(float);
+}
 
 int max_nt(const JobsArg &a) {
     int m = 2;
@@ -275,7 +297,7 @@ cudaError_t launch_lm(const JobsArg &a, int grid, cudaStream_t st) {
     const size_t smem = cap_smem(LS, max_nt(a));
     cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_cap<LS, MODE><<<grid, NTH, smem, st>>>(a);
+    k_conv_cap<LS, MODE><<<grid, NTH * HALVES, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -284,7 +306,7 @@ int occupancy_lm(int nt) {
     const size_t smem = cap_smem(LS, nt);
     cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE>, NTH, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE>, NTH * HALVES, smem);
     return nb;
 }
 

@@ -459,7 +459,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                     int per = sk_cap_blocks_per_sm(SK_CAP_LS[c], mode, mnt);
                     cudaStream_t cs = v ? st : side;
                     cudaEvent_t ev = sk_prof_begin(ctx, cs);
-                    SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(b.a.total, per, ctx->num_sms), cs));
+                    // a block works on SK_CAP_ITEMS_PER_BLOCK items at a time
+                    const int blocks = (b.a.total + SK_CAP_ITEMS_PER_BLOCK - 1) / SK_CAP_ITEMS_PER_BLOCK;
+                    SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(blocks, per, ctx->num_sms), cs));
                     sk_prof_end(ctx, v ? "conv_cap" : "conv_cap_polar", ev, cs);
                 }
                 b.reset();
@@ -470,6 +472,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                 if (!k->plan_ok || k->n_items_cap[c][v] == 0 || jobs[i].batch == 0) continue;
                 const int kmode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
                 if (kmode != mode) continue;
+                // one node table per launch (the blocks load it once)
+                if (b.a.n_jobs > 0 && b.a.j[0].tab != k->d_tab) { int rc = flush(); if (rc) return rc; }
                 JobDesc d = base_desc(jobs[i]);
                 d.cap_ls = SK_CAP_LS[c];
                 b.add(d, k->d_items_cap[c][v], k->n_items_cap[c][v]);
