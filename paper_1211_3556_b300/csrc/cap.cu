@@ -23,7 +23,8 @@
 // ring of the window a half stages 4 rows (quarter turns) of float4 (north
 // pixel, its reflection, south pixel, its reflection) covering the union of
 // its CT windows, unwrapped, even positions before odd ones, with cp.async
-// into two buffers (ring p + 1 is copied while ring p is summed).  A thread
+// into two buffers (ring p + 1 is copied while ring p is summed; one barrier
+// per ring).  A thread
 // walks the union of its two windows (they start at most a pixel or two
 // apart): one 128-bit load feeds 4 of the 16 images of both outputs, and both
 // weights come from one paired evaluation (fma.rn.f32x2: two IEEE
@@ -186,17 +187,19 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         for (int p = p0; p < p1; ++p) {
             float4 *const xbuf = sbuf + (NB == 2 ? ((p - p0) & 1) : 0) * 4 * LS;
             if (NB == 2) {
-                // stage ring p + 1 into the other buffer (free since the barrier that ended
-                // ring p - 1), then wait for ring p's copies
+                // ring p's copies (issued during ring p - 1) are complete for this thread; after
+                // the barrier they are for every thread, and every thread is done with ring
+                // p - 1, whose buffer then receives ring p + 1 while ring p is summed
+                cp_wait0();
+                half_sync(half);
                 if (p + 1 < p1) stage(p + 1, sbuf + ((p + 1 - p0) & 1) * 4 * LS);
-                else cp_commit();
-                cp_wait1();
             } else {
                 // one buffer: stage ring p once every thread is done with ring p - 1
+                half_sync(half);
                 stage(p, xbuf);
                 cp_wait0();
+                half_sync(half);
             }
-            half_sync(half);
             if (actA) {
                 const PairInfo P = J.pairs[p];
                 int before, cnt;
@@ -246,8 +249,9 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     }
                 }
             }
-            half_sync(half);
         }
+        // the next item stages into this half's buffers: everyone must be done reading them
+        half_sync(half);
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
         if (actA) {
