@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--workload", default="n2048_plain", choices=sorted(WORKLOADS))
     ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-split", action="store_true", help="skip the harmonic-half (split) side measurement")
     return ap.parse_args()
 
 
@@ -155,6 +156,32 @@ def build_operator(sk, ctx, group):
     g = sk.Geometry(ctx, group.nside)
     k, _ = sk.Kernel.from_legendre(g, ks.beam(), ks.lcut + 1, ks.lmax, ks.n_nodes, ks.theta_cut, ks.layout)
     return g, k
+
+
+# DRAM traffic per launch from a committed ncu summary (profiles/<kernel>_<workload>.md),
+# valid only while the kernel's sources hash to the value recorded at capture time.
+PROFILED_SOURCES = {
+    "conv_cap": ["cap.cu", "skconv_internal.cuh", "skconv_launch.h"],
+    "conv_belt": ["belt.cu", "skconv_internal.cuh", "skconv_launch.h"],
+}
+
+
+def profiled_traffic(kernel, workload):
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "profiles", f"{kernel}_{workload}.md")
+    if kernel not in PROFILED_SOURCES or not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mb = re.search(r"dram_bytes_per_launch:\s*(\d+)", text)
+    mh = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not mb or not mh:
+        return None
+    h = hashlib.sha256()
+    for f in PROFILED_SOURCES[kernel]:
+        h.update(open(os.path.join(here, "paper_1211_3556_b300", "csrc", f), "rb").read())
+    return int(mb.group(1)) if h.hexdigest() == mh.group(1) else None
 
 
 def time_steps(torch, fn, steps, warmup, barrier):
@@ -275,7 +302,7 @@ def run_ours(args):
         achieved = FLOP_PER_PAIR * per_launch_pairs / (launch_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                    "traffic": None,
+                    "traffic": profiled_traffic(dom, args.workload),
                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
                     "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
 
@@ -319,6 +346,27 @@ def run_ours(args):
         batched["value"] = max(batched["fp32"]["value"], batched["tensor_3xtf32"]["value"])
         del xb, yb
 
+    # the whole split of Eq. 1 beside the real-space step: harmonic part K^_l = K_l - R_l
+    # (l <= l_cut) by the library's ring transform, timed alone and added to the real-space sum
+    split = None
+    if not args.no_split and args.workload == "n2048_plain" and len(ops) == 1:
+        o = ops[0]
+        ks = o["group"].kernel
+        R = sk.kernel_response(o["kern"], ks.lcut)
+        kh = ks.beam()[: ks.lcut + 1] - R
+        t0 = time.perf_counter()
+        h = sk.Harmonic(ctx, o["geom"], kh, ks.lcut)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        yh = torch.empty_like(o["x"])
+        ns = max(3, min(args.steps, 10))
+        ms_h = time_steps(torch, lambda: h.apply(o["x"], out=yh), ns, 2, barrier)
+        ms_s = time_steps(torch, lambda: sk.split_convolve(o["kern"], h, o["x"], out=yh), ns, 2, barrier)
+        split = {"l_cut": ks.lcut, "harmonic_ms_per_map": ms_h, "split_ms_per_map": ms_s,
+                 "real_space_ms_per_map": ms / maps_step, "lambda_table_gb": h.table_bytes() / 1e9,
+                 "harmonic_setup_s": t_create}
+        del h, yh
+
     o0 = ops[0]
     y0 = o0["y"][0].cpu().numpy()
     cpu_baseline, rms = None, None
@@ -349,6 +397,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "batched": batched,
+            "split": split,
             "cpu_baseline": cpu_baseline,
             "context": "paper: GTX 480 + 1 Core2 core, split convolution >10x faster than a full "
                        "single-core SHT convolution (eq. 3 model: 2.89 s at theta_cut 20')",

@@ -267,6 +267,49 @@ int sk_selftest_wait_timeout(sk_ctx *ctx, double seconds, void *stream);
 int sk_selftest_tc_gemm(sk_ctx *ctx, const float *d_a, const float *d_b, float *d_d, int n, int k,
                         int passes, void *stream);
 
+/* ---- harmonic half of the split (Sec. 2, Eq. 1: the l <= l_cut part) ----
+ *
+ * The split convolution adds to the real-space sum above the harmonic part
+ *
+ *   y_p += sum_{l=0}^{L} sum_{m=-l}^{l} K^_l a_lm Y_lm(p),  a_lm = dOmega sum_q x_q Y*_lm(q),
+ *
+ * with L = l_cut and K^_l = K_l - R_l the l-space kernel the paper hands to a
+ * spherical harmonic transform (R_l: the Legendre coefficients of the
+ * real-space part).  The transform is a ring-based one on the same RING maps:
+ * ring DFTs (cuFFT for the 2N+1 rings of 4N pixels, direct sums for the polar
+ * cap rings), and Legendre sums against a table of the orthonormal associated
+ * Legendre functions lambda_lm(theta_r), built once per handle (FP64
+ * recurrence, stored FP32: (L+1)(L+2)/2 * 2N floats on the device).  Arithmetic
+ * of the transforms is FP32. */
+typedef struct sk_harm sk_harm;
+#define SK_HARM_MAX_NSIDE 4096
+
+/* Legendre coefficients of the real-space part, the R_l of K^_l = K_l - R_l
+ * (Sec. 3: the l-space kernel is adjusted so that the two halves add up to K_l
+ * for l <= l_cut): R_l = 2 pi int_0^theta_cut K_lin(theta) P_l(cos theta)
+ * sin theta dtheta for l = 0..lmax, by 8-point Gauss-Legendre quadrature on
+ * every node interval (exact for K_lin P_l sin up to the quadrature's degree),
+ * FP64, into the host array h_R[lmax + 1] (synchronous).  lmax <= 65535.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_kernel_response(sk_ctx *ctx, const sk_kern *k, int lmax, double *h_R);
+
+/* Builds the harmonic operator for geometry g: copies h_kl[0..lmax] (FP64
+ * host array, K^_l) and tabulates lambda_lm on the device.
+ * Errors: SK_EINVAL (NULL, lmax outside [0, 2 nside - 1]), SK_EUNSUPPORTED
+ * (nside outside [2, SK_HARM_MAX_NSIDE]), SK_ENOMEM (the table does not fit),
+ * SK_ECUDA.  *out is NULL on error. */
+int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *h_kl, int lmax, sk_harm **out);
+int sk_harmonic_destroy(sk_harm *h);
+/* Device bytes of the lambda table (for capacity planning). */
+int sk_harmonic_table_bytes(const sk_harm *h, int64_t *bytes);
+/* d_out = H d_in (accumulate = 0) or d_out += H d_in (accumulate != 0) for
+ * `batch` maps [batch][map_stride]; H is the harmonic operator above.  Uses the
+ * handle's own buffers (grown on demand): calls with one handle must not
+ * overlap on the GPU.  Errors: SK_EINVAL (NULL, stride < Npix, misaligned,
+ * aliasing), SK_ENOMEM, SK_ECUDA. */
+int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *h, const float *d_in, float *d_out, int64_t batch,
+                      int64_t map_stride, int accumulate, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,11 @@ def _declare(L):
         "sk_selftest_wait_timeout": (I, [P, D, P]),
         "sk_selftest_tc_gemm": (I, [P, P, P, P, I, I, I, P]),
         "sk_kernel_get_tiles": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "sk_kernel_response": (I, [P, P, I, P]),
+        "sk_harmonic_create": (I, [P, P, P, I, PP]),
+        "sk_harmonic_destroy": (I, [P]),
+        "sk_harmonic_table_bytes": (I, [P, ctypes.POINTER(I64)]),
+        "sk_harmonic_apply": (I, [P, P, P, P, I64, I64, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -361,6 +366,64 @@ def convolve_jobs(ctx: Context, jobs, path: int = PATH_AUTO, stream=None):
     """Several (kernel, x, y) jobs with mixed Nside/kernels/batch in one launch per path family."""
     arr, _keep = _jobs_array(jobs)
     _check(lib().sk_convolve_jobs(ctx._h, arr, len(jobs), path, _stream_ptr(stream)))
+
+
+def kernel_response(kern: Kernel, lmax: int):
+    """R_l = 2 pi int K_lin P_l(cos t) sin t dt, l = 0..lmax (FP64 numpy): the harmonic
+    content of the real-space part, so that K^_l = K_l - R_l completes the split."""
+    R = np.empty(int(lmax) + 1, np.float64)
+    _check(lib().sk_kernel_response(kern.ctx._h, kern._h, int(lmax), R.ctypes.data))
+    return R
+
+
+class Harmonic:
+    """The harmonic half of the split (Sec. 2, Eq. 1): y = sum_{l <= lmax} K^_l a_lm Y_lm
+    with a_lm = dOmega sum_q x_q Y*_lm(q), for a geometry and FP64 coefficients K^_l."""
+
+    def __init__(self, ctx: Context, geom: Geometry, k_hat, lmax: int = None):
+        import numpy as np
+        kl = np.ascontiguousarray(np.asarray(k_hat, dtype=np.float64))
+        self.lmax = len(kl) - 1 if lmax is None else int(lmax)
+        if len(kl) < self.lmax + 1:
+            raise ValueError("k_hat needs lmax + 1 coefficients")
+        self.ctx, self.geom = ctx, geom
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_harmonic_create(ctx._h, geom._h, kl.ctypes.data, self.lmax, ctypes.byref(self._h)))
+
+    def table_bytes(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().sk_harmonic_table_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def apply(self, x, out=None, accumulate: bool = False, stream=None):
+        """out (+)= H x for maps x [batch, npix] (float32 CUDA)."""
+        import torch
+        x2, b, stride = _map_args(x, self.geom.npix)
+        if out is None:
+            out = torch.empty_like(x2)
+        o2, _, ostride = _map_args(out, self.geom.npix)
+        if ostride != stride:
+            raise ValueError("input and output maps need the same stride")
+        _check(lib().sk_harmonic_apply(self.ctx._h, self._h, ctypes.c_void_p(x2.data_ptr()),
+                                       ctypes.c_void_p(o2.data_ptr()), b, stride, 1 if accumulate else 0,
+                                       _stream_ptr(stream)))
+        return out if out.dim() == x.dim() else out.view_as(x)
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().sk_harmonic_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+def split_convolve(kern: Kernel, harm: Harmonic, x, out=None, stream=None):
+    """The whole split convolution (Sec. 2, Eq. 1): the real-space part of kern plus the
+    harmonic part of harm, y = A_real x + H x."""
+    y = convolve(kern, x, out=out, stream=stream)
+    harm.apply(x, out=y, accumulate=True, stream=stream)
+    return y
 
 
 class Graph:

@@ -1,0 +1,573 @@
+// harmonic.cu -- the harmonic half of the split convolution (Sec. 2, Eq. 1):
+//
+//     y_p (+)= sum_{l <= L} sum_m K^_l a_lm Y_lm(p),   a_lm = dOmega sum_q x_q Y*_lm(q)
+//
+// for l <= L = l_cut, the part of the kernel the paper hands to a spherical
+// harmonic transform (libpsht on the CPU in the paper).  With Y_lm(theta, phi) =
+// lambda_lm(theta) e^{i m phi} and real maps this is, ring by ring,
+//
+//   F_r(m)  = sum_j x_{r,j} e^{-i m phi_{r,j}}                          (ring DFT)
+//   a_lm    = dOmega sum_r lambda_lm(theta_r) F_r(m)                     (Legendre analysis)
+//   G_r(m)  = sum_{l >= m} K^_l a_lm lambda_lm(theta_r)                  (Legendre synthesis)
+//   y_{r,j} = Re G_r(0) + 2 Re sum_{m=1}^{L} G_r(m) e^{i m phi_{r,j}}     (ring inverse DFT)
+//
+// lambda_lm are the orthonormal associated Legendre functions (the standard
+// three-term recurrence in l at fixed m), tabulated once per handle in FP64 and
+// stored in FP32 for the northern rings and the equator: the southern ring
+// 4N - r has lambda_lm(pi - theta) = (-1)^(l+m) lambda_lm(theta), so the sums use
+// E_r = F_r + F_r' (l + m even) and O_r = F_r - F_r' (l + m odd).  Table layout
+// [m][l - m][r] (r fastest): the analysis reads it with lanes along r, the
+// synthesis with threads along r, the tabulation writes it with threads along r.
+//
+// Ring DFTs: the 2N + 1 rings of 4N pixels (equatorial zone) go through one
+// batched cuFFT R2C / C2R plan straight on the map; the polar-cap rings (4r
+// pixels, r < N) are summed directly against a twiddle table in shared memory
+// (their bins alias when 4r < 2L + 1, which the direct sum does by itself).
+// Phases: phi_{r,j} = pi (2j + s_r) / n_r, so F_r(m) = e^{-i pi m s_r / n_r} X_r(m)
+// with X_r the plain DFT.
+#include <cufft.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "skconv_host.h"
+
+struct sk_harm {
+    sk_ctx *ctx = nullptr;
+    const sk_geom *g = nullptr;
+    int L = 0;
+    int nrh = 0;                 // northern rings and the equator: 0-based rings 0 .. 2N - 1
+    double *d_kl = nullptr;      // K^_l, l = 0..L
+    float *d_lam = nullptr;      // lambda table [m][l - m][r]
+    long long *d_moff = nullptr; // start of block m in d_lam
+    long long *d_aoff = nullptr; // start of block m in a (l = m..L)
+    long long lam_n = 0, a_n = 0;
+    // per-call buffers (sized for `cap_batch` maps, grown on demand)
+    long long cap_batch = 0;
+    float2 *d_F = nullptr;       // [batch][nr][L + 1] ring coefficients F, then G
+    float2 *d_a = nullptr;       // [batch][a_n]
+    // equatorial-zone FFTs (rings N-1 .. 3N-1, 0-based, all 4N pixels)
+    cufftHandle p_r2c = 0, p_c2r = 0;
+    bool plans = false;
+    float2 *d_X = nullptr;       // [(2N+1)][2N+1] bins of one map
+    float *d_tmp = nullptr;      // [(2N+1) * 4N] synthesised zone of one map
+};
+
+namespace {
+
+constexpr int HT = 256;
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// lambda_lm(theta_r) for l = m..L, FP64 three-term recurrence with an exponent
+// offset: lambda_mm = (-1)^m sqrt((2m+1)/(4 pi) prod_{k<=m} (2k-1)/(2k)) sin^m theta
+// underflows FP64 for large m near the poles; the recurrence runs on
+// v = lambda 2^E and drops E as v grows (values below FP32 range are stored as 0).
+// lg2c[m] = log2 of the constant factor.  One thread per (m, r).
+__global__ void k_lambda(const double *theta, const double *lg2c, const long long *moff, int L, int nrh,
+                         float *lam) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)(L + 1) * nrh) return;
+    const int m = (int)(idx / nrh), r = (int)(idx % nrh);
+    const double th = theta[r];
+    const double x = cos(th), sx = sin(th);
+    float *out = lam + moff[m] + r;
+    // log2 |lambda_mm|
+    const double lg = lg2c[m] + (m > 0 ? m * log2(sx) : 0.0);
+    int E = 0;
+    if (lg < -900.0) E = (int)(-lg) - 600;          // v_mm about 2^-600
+    double v0 = exp2(lg + E);
+    if (m & 1) v0 = -v0;
+    double vm1 = 0.0, v = v0;                        // v_{l-1}, v_l
+    for (int l = m; l <= L; ++l) {
+        if (l == m + 1) {
+            vm1 = v;
+            v = sqrt(2.0 * m + 3.0) * x * vm1;
+        } else if (l > m + 1) {
+            const double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+            const double b = sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+            const double vn = a * (x * v - b * vm1);
+            vm1 = v;
+            v = vn;
+        }
+        if (E > 0 && fabs(v) > 0x1p400) {            // take part of the offset out
+            const int d = E < 400 ? E : 400;
+            v = ldexp(v, -d);
+            vm1 = ldexp(vm1, -d);
+            E -= d;
+        }
+        out[(long long)(l - m) * nrh] = (float)ldexp(v, -E);
+    }
+}
+
+// Polar-cap rings: F_r(m) = e^{-i pi m s / n} sum_j x_j e^{-2 pi i m j / n}, m = 0..L.
+// One block per (cap ring, map); cap ring c < N - 1 is 0-based ring c, else its
+// southern mirror.  Twiddles w_k = e^{-2 pi i k / n} in shared memory.
+__global__ void k_dft_cap(const RingDev *rings, int nside, const float *x, long long stride, int L,
+                          int nr, float2 *F) {
+    extern __shared__ float2 sh[];
+    const int ncap = nside - 1;
+    const int c = blockIdx.x, b = blockIdx.y;
+    const int r = c < ncap ? c : nr - 1 - (c - ncap);
+    const RingDev R = rings[r];
+    const int n = R.n;
+    float2 *tw = sh;
+    float *xs = reinterpret_cast<float *>(sh + n);
+    const float *xr = x + (long long)b * stride + R.start;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * k / n, &sn, &cs);
+        tw[k] = make_float2((float)cs, (float)-sn);
+        xs[k] = xr[k];
+    }
+    __syncthreads();
+    float2 *Fr = F + ((long long)b * nr + r) * (L + 1);
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        const int step = m % n;
+        int idx = 0;
+        float re = 0.0f, im = 0.0f;
+        for (int j = 0; j < n; ++j) {
+            const float2 w = tw[idx];
+            re = fmaf(xs[j], w.x, re);
+            im = fmaf(xs[j], w.y, im);
+            idx += step;
+            if (idx >= n) idx -= n;
+        }
+        double sn, cs;
+        sincospi(-(double)m * R.s / n, &sn, &cs);
+        Fr[m] = cmulf(make_float2(re, im), make_float2((float)cs, (float)sn));
+    }
+}
+
+// Equatorial zone after the R2C: F_r(m) = e^{-i pi m s / n} X_r(m), m = 0..L.
+__global__ void k_zone_in(const RingDev *rings, int nside, const float2 *X, int L, int nr, long long b,
+                          float2 *F) {
+    const int zr = blockIdx.x;                       // 0 .. 2N
+    const int r = nside - 1 + zr;
+    const int n = 4 * nside, nb = 2 * nside + 1;
+    const int s = rings[r].s;
+    float2 *Fr = F + (b * nr + r) * (L + 1);
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        double sn, cs;
+        sincospi(-(double)m * s / n, &sn, &cs);
+        Fr[m] = cmulf(X[(long long)zr * nb + m], make_float2((float)cs, (float)sn));
+    }
+}
+
+// Legendre analysis: a_lm = dOmega sum_r lambda_lm(theta_r) (E_r or O_r), one
+// block per (m, map), a warp per l, lanes along r, warp sum.
+__global__ void k_leg_analysis(const float *lam, const long long *moff, const long long *aoff, const float2 *F,
+                               int L, int nr, int nrh, long long a_n, float domega, float2 *a) {
+    extern __shared__ float2 sEO[];                  // [nrh] E, then [nrh] O
+    const int m = blockIdx.x, b = blockIdx.y;
+    const float2 *Fb = F + (long long)b * nr * (L + 1);
+    for (int r = threadIdx.x; r < nrh; r += blockDim.x) {
+        const float2 fn = Fb[(long long)r * (L + 1) + m];
+        const int rs = nr - 1 - r;
+        if (rs == r) {                               // equator: lambda_lm(pi/2) = 0 for l + m odd
+            sEO[r] = fn;
+            sEO[nrh + r] = make_float2(0.0f, 0.0f);
+        } else {
+            const float2 fs = Fb[(long long)rs * (L + 1) + m];
+            sEO[r] = make_float2(fn.x + fs.x, fn.y + fs.y);
+            sEO[nrh + r] = make_float2(fn.x - fs.x, fn.y - fs.y);
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float *lm = lam + moff[m];
+    for (int l = m + warp; l <= L; l += nw) {
+        const float *row = lm + (long long)(l - m) * nrh;
+        const float2 *S = sEO + (((l + m) & 1) ? nrh : 0);
+        float re = 0.0f, im = 0.0f;
+        for (int r = lane; r < nrh; r += 32) {
+            const float w = row[r];
+            re = fmaf(w, S[r].x, re);
+            im = fmaf(w, S[r].y, im);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) a[(long long)b * a_n + aoff[m] + (l - m)] = make_float2(domega * re, domega * im);
+    }
+}
+
+// Legendre synthesis: G_r(m) = sum_l K^_l a_lm lambda_lm(theta_r), split by the
+// parity of l + m into the northern ring and its mirror.  One block per (m, map),
+// threads along r.
+__global__ void k_leg_synthesis(const float *lam, const long long *moff, const long long *aoff, const double *kl,
+                                const float2 *a, int L, int nr, int nrh, long long a_n, float2 *G) {
+    extern __shared__ float2 sb[];                   // b_l = K^_l a_lm, l = m..L
+    const int m = blockIdx.x, b = blockIdx.y;
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+        const float2 v = a[(long long)b * a_n + aoff[m] + (l - m)];
+        const float k = (float)kl[l];
+        sb[l - m] = make_float2(k * v.x, k * v.y);
+    }
+    __syncthreads();
+    const float *lm = lam + moff[m];
+    float2 *Gb = G + (long long)b * nr * (L + 1);
+    for (int r = threadIdx.x; r < nrh; r += blockDim.x) {
+        float er = 0.0f, ei = 0.0f, orr = 0.0f, oi = 0.0f;
+        int l = m;
+        for (; l + 1 <= L; l += 2) {                 // l + m even, then odd
+            const float w0 = lm[(long long)(l - m) * nrh + r];
+            const float w1 = lm[(long long)(l + 1 - m) * nrh + r];
+            const float2 b0 = sb[l - m], b1 = sb[l + 1 - m];
+            const bool even0 = ((l + m) & 1) == 0;
+            if (even0) {
+                er = fmaf(w0, b0.x, er); ei = fmaf(w0, b0.y, ei);
+                orr = fmaf(w1, b1.x, orr); oi = fmaf(w1, b1.y, oi);
+            } else {
+                orr = fmaf(w0, b0.x, orr); oi = fmaf(w0, b0.y, oi);
+                er = fmaf(w1, b1.x, er); ei = fmaf(w1, b1.y, ei);
+            }
+        }
+        if (l <= L) {
+            const float w0 = lm[(long long)(l - m) * nrh + r];
+            const float2 b0 = sb[l - m];
+            if (((l + m) & 1) == 0) { er = fmaf(w0, b0.x, er); ei = fmaf(w0, b0.y, ei); }
+            else { orr = fmaf(w0, b0.x, orr); oi = fmaf(w0, b0.y, oi); }
+        }
+        const int rs = nr - 1 - r;
+        Gb[(long long)r * (L + 1) + m] = make_float2(er + orr, ei + oi);
+        if (rs != r) Gb[(long long)rs * (L + 1) + m] = make_float2(er - orr, ei - oi);
+    }
+}
+
+// Polar-cap rings: y_j (+)= Re G(0) + 2 Re sum_{m=1}^{L} G(m) e^{i pi m (2j + s) / n}.
+__global__ void k_idft_cap(const RingDev *rings, int nside, const float2 *G, int L, int nr, float *y,
+                           long long stride, int accumulate) {
+    extern __shared__ float2 sh[];
+    const int ncap = nside - 1;
+    const int c = blockIdx.x, b = blockIdx.y;
+    const int r = c < ncap ? c : nr - 1 - (c - ncap);
+    const RingDev R = rings[r];
+    const int n = R.n;
+    float2 *tw = sh;                                 // e^{+2 pi i k / n}
+    float2 *gs = sh + n;                             // G(m) e^{i pi m s / n}, doubled for m >= 1
+    const float2 *Gr = G + ((long long)b * nr + r) * (L + 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * k / n, &sn, &cs);
+        tw[k] = make_float2((float)cs, (float)sn);
+    }
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        double sn, cs;
+        sincospi((double)m * R.s / n, &sn, &cs);
+        float2 v = cmulf(Gr[m], make_float2((float)cs, (float)sn));
+        if (m > 0) { v.x *= 2.0f; v.y *= 2.0f; }
+        gs[m] = v;
+    }
+    __syncthreads();
+    float *yr = y + (long long)b * stride + R.start;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int step = j % n;
+        int idx = 0;
+        float acc = 0.0f;
+        for (int m = 0; m <= L; ++m) {
+            const float2 w = tw[idx], g = gs[m];
+            acc = fmaf(g.x, w.x, acc);
+            acc = fmaf(-g.y, w.y, acc);
+            idx += step;
+            if (idx >= n) idx -= n;
+        }
+        yr[j] = accumulate ? yr[j] + acc : acc;
+    }
+}
+
+// Equatorial zone before the C2R: bins X_r(m) = G_r(m) e^{i pi m s / n} for m <= L, 0 above.
+__global__ void k_zone_out(const RingDev *rings, int nside, const float2 *G, int L, int nr, long long b,
+                           float2 *X) {
+    const int zr = blockIdx.x;
+    const int r = nside - 1 + zr;
+    const int n = 4 * nside, nb = 2 * nside + 1;
+    const int s = rings[r].s;
+    const float2 *Gr = G + (b * nr + r) * (L + 1);
+    for (int m = threadIdx.x; m < nb; m += blockDim.x) {
+        float2 v = make_float2(0.0f, 0.0f);
+        if (m <= L) {
+            double sn, cs;
+            sincospi((double)m * s / n, &sn, &cs);
+            v = cmulf(Gr[m], make_float2((float)cs, (float)sn));
+            if (m == 0) v.y = 0.0f;
+        }
+        X[(long long)zr * nb + m] = v;
+    }
+}
+
+__global__ void k_zone_store(const float *tmp, long long n, float *y, int accumulate) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = accumulate ? y[i] + tmp[i] : tmp[i];
+}
+
+// R_l = 2 pi int_0^theta_cut K_lin(theta) P_l(cos theta) sin theta dtheta, l = 0..L:
+// Gauss-Legendre with npts points on every node interval (K_lin is linear there),
+// one thread per quadrature point, P_l by the Bonnet recurrence, warp sums into
+// shared FP64 bins, one global atomic per bin and block.
+__device__ __forceinline__ double node_theta(int k, int nt, double tc, int layout) {
+    if (layout == 0) return (double)k * tc / (double)(nt - 1);
+    const int M = nt / 2;
+    const double t1 = tc / 16.0;
+    return k <= M ? (double)k * t1 / (double)M : t1 + (double)(k - M) * (tc - t1) / (double)(nt - 1 - M);
+}
+
+__global__ void k_response(const double *V, int nt, double tc, int layout, int L, const double *gx,
+                           const double *gw, int npts, double *R) {
+    extern __shared__ double sR[];
+    for (int l = threadIdx.x; l <= L; l += blockDim.x) sR[l] = 0.0;
+    __syncthreads();
+    const long long nq = (long long)(nt - 1) * npts;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double c = 0.0, x = 1.0;
+    if (q < nq) {
+        const int k = (int)(q / npts), i = (int)(q % npts);
+        const double a = node_theta(k, nt, tc, layout), b = node_theta(k + 1, nt, tc, layout);
+        const double t = 0.5 * (b - a) * gx[i] + 0.5 * (a + b);
+        const double f = (t - a) / (b - a);
+        const double K = V[k] + f * (V[k + 1] - V[k]);
+        c = 0.5 * (b - a) * gw[i] * K * sin(t);
+        x = cos(t);
+    }
+    const int lane = threadIdx.x & 31;
+    double p0 = 1.0, p1 = x;
+    for (int l = 0; l <= L; ++l) {
+        double pl;
+        if (l == 0) pl = p0;
+        else if (l == 1) pl = p1;
+        else {
+            pl = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / (double)l;
+            p0 = p1;
+            p1 = pl;
+        }
+        double v = c * pl;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(&sR[l], v);
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l <= L; l += blockDim.x) atomicAdd(&R[l], 2.0 * SK_PI * sR[l]);
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from the cosine guesses).
+void gauss_legendre(int n, double *x, double *w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(SK_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int l = 2; l <= n; ++l) {
+                const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void free_harm(sk_harm *h) {
+    if (!h) return;
+    if (h->plans) { cufftDestroy(h->p_r2c); cufftDestroy(h->p_c2r); }
+    cudaFree(h->d_kl); cudaFree(h->d_lam); cudaFree(h->d_moff); cudaFree(h->d_aoff);
+    cudaFree(h->d_F); cudaFree(h->d_a); cudaFree(h->d_X); cudaFree(h->d_tmp);
+    delete h;
+}
+
+int cufft_fail(cufftResult r, const char *what) {
+    return sk_fail(r == CUFFT_ALLOC_FAILED ? SK_ENOMEM : SK_ECUDA, "%s: cuFFT error %d", what, (int)r);
+}
+
+}  // namespace
+
+extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *kl, int lmax, sk_harm **out) {
+    if (!ctx || !g || !kl || !out) return sk_fail(SK_EINVAL, "sk_harmonic_create: NULL argument");
+    *out = nullptr;
+    const long long N = g->nside;
+    if (N < 2 || N > SK_HARM_MAX_NSIDE)
+        return sk_fail(SK_EUNSUPPORTED, "sk_harmonic_create: nside %lld outside [2, %d]", N, SK_HARM_MAX_NSIDE);
+    if (lmax < 0 || lmax > 2 * N - 1)
+        return sk_fail(SK_EINVAL, "sk_harmonic_create: lmax %d outside [0, 2 nside - 1]", lmax);
+    SK_CU(cudaSetDevice(ctx->device));
+    sk_harm *h = new sk_harm();
+    h->ctx = ctx;
+    h->g = g;
+    h->L = lmax;
+    h->nrh = (int)(2 * N);
+    const int L = lmax, nrh = h->nrh;
+    std::vector<long long> moff(L + 1), aoff(L + 1);
+    long long tot = 0, atot = 0;
+    for (int m = 0; m <= L; ++m) {
+        moff[m] = tot; tot += (long long)(L - m + 1) * nrh;
+        aoff[m] = atot; atot += L - m + 1;
+    }
+    h->lam_n = tot;
+    h->a_n = atot;
+    std::vector<double> lg2c(L + 1);
+    {
+        double acc = 0.0;                            // log2 prod_{k<=m} (2k-1)/(2k)
+        for (int m = 0; m <= L; ++m) {
+            if (m > 0) acc += log2((2.0 * m - 1.0) / (2.0 * m));
+            lg2c[m] = 0.5 * (log2((2.0 * m + 1.0) / (4.0 * SK_PI)) + acc);
+        }
+    }
+    double *d_lg2c = nullptr;
+    const int nb = (int)(2 * N + 1), n4 = (int)(4 * N);
+    cudaError_t e = cudaMalloc(&h->d_kl, sizeof(double) * (L + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_lam, sizeof(float) * tot);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_moff, sizeof(long long) * (L + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_aoff, sizeof(long long) * (L + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_lg2c, sizeof(double) * (L + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_X, sizeof(float2) * (size_t)nb * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_tmp, sizeof(float) * (size_t)nb * n4);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_kl, kl, sizeof(double) * (L + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_moff, moff.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_aoff, aoff.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_lg2c, lg2c.data(), sizeof(double) * (L + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const long long nthr = (long long)(L + 1) * nrh;
+        k_lambda<<<(unsigned)((nthr + HT - 1) / HT), HT>>>(g->d_theta, d_lg2c, h->d_moff, L, nrh, h->d_lam);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_lg2c);
+    if (e != cudaSuccess) {
+        free_harm(h);
+        return sk_fail(e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA, "sk_harmonic_create: %s",
+                       cudaGetErrorString(e));
+    }
+    int len[1] = {n4};
+    cufftResult cr = cufftPlanMany(&h->p_r2c, 1, len, nullptr, 1, n4, nullptr, 1, nb, CUFFT_R2C, nb);
+    if (cr == CUFFT_SUCCESS) cr = cufftPlanMany(&h->p_c2r, 1, len, nullptr, 1, nb, nullptr, 1, n4, CUFFT_C2R, nb);
+    if (cr != CUFFT_SUCCESS) { free_harm(h); return cufft_fail(cr, "sk_harmonic_create"); }
+    h->plans = true;
+    *out = h;
+    return SK_OK;
+}
+
+extern "C" int sk_harmonic_destroy(sk_harm *h) {
+    if (!h) return SK_OK;
+    cudaSetDevice(h->ctx->device);
+    free_harm(h);
+    return SK_OK;
+}
+
+extern "C" int sk_harmonic_table_bytes(const sk_harm *h, int64_t *bytes) {
+    if (!h || !bytes) return sk_fail(SK_EINVAL, "sk_harmonic_table_bytes: NULL argument");
+    *bytes = h->lam_n * (int64_t)sizeof(float);
+    return SK_OK;
+}
+
+extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_in, float *d_out, int64_t batch,
+                                 int64_t map_stride, int accumulate, void *stream) {
+    if (!ctx || !hc || (!d_in && batch > 0) || (!d_out && batch > 0))
+        return sk_fail(SK_EINVAL, "sk_harmonic_apply: NULL argument");
+    sk_harm *h = const_cast<sk_harm *>(hc);
+    const sk_geom *g = h->g;
+    if (batch < 0 || map_stride < g->npix) return sk_fail(SK_EINVAL, "sk_harmonic_apply: bad batch or stride");
+    if (batch == 0) return SK_OK;
+    if (d_in == d_out) return sk_fail(SK_EINVAL, "sk_harmonic_apply: input and output alias");
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15) || (map_stride & 3))
+        return sk_fail(SK_EINVAL, "sk_harmonic_apply: maps must be 16-byte aligned with a stride multiple of 4");
+    SK_CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = (int)g->nside, nr = g->nr, L = h->L, nrh = h->nrh;
+    if (batch > h->cap_batch) {
+        cudaFree(h->d_F); h->d_F = nullptr;
+        cudaFree(h->d_a); h->d_a = nullptr;
+        h->cap_batch = 0;
+        SK_CU(cudaMalloc(&h->d_F, sizeof(float2) * (size_t)batch * nr * (L + 1)));
+        SK_CU(cudaMalloc(&h->d_a, sizeof(float2) * (size_t)batch * h->a_n));
+        h->cap_batch = batch;
+    }
+    const int nb = 2 * N + 1, n4 = 4 * N;
+    const float domega = (float)(4.0 * SK_PI / (double)g->npix);
+    const long long zone0 = g->h_rings[N - 1].start;     // first pixel of the equatorial zone
+    if (cufftSetStream(h->p_r2c, st) != CUFFT_SUCCESS || cufftSetStream(h->p_c2r, st) != CUFFT_SUCCESS)
+        return sk_fail(SK_ECUDA, "sk_harmonic_apply: cufftSetStream failed");
+    // ring DFTs
+    const int ncap = 2 * (N - 1);
+    if (ncap > 0) {
+        const size_t sm = sizeof(float2) * 4 * (N - 1) + sizeof(float) * 4 * (N - 1);
+        SK_CU(cudaFuncSetAttribute(k_dft_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_dft_cap<<<dim3(ncap, (unsigned)batch), HT, sm, st>>>(g->d_rings, N, d_in, map_stride, L, nr, h->d_F);
+        SK_CU(cudaGetLastError());
+    }
+    for (long long b = 0; b < batch; ++b) {
+        cufftResult cr = cufftExecR2C(h->p_r2c, const_cast<float *>(d_in) + b * map_stride + zone0,
+                                      reinterpret_cast<cufftComplex *>(h->d_X));
+        if (cr != CUFFT_SUCCESS) return cufft_fail(cr, "sk_harmonic_apply");
+        k_zone_in<<<nb, HT, 0, st>>>(g->d_rings, N, h->d_X, L, nr, b, h->d_F);
+        SK_CU(cudaGetLastError());
+    }
+    // Legendre analysis and synthesis
+    const size_t sm_a = sizeof(float2) * 2 * nrh;
+    SK_CU(cudaFuncSetAttribute(k_leg_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_a));
+    k_leg_analysis<<<dim3(L + 1, (unsigned)batch), HT, sm_a, st>>>(h->d_lam, h->d_moff, h->d_aoff, h->d_F, L, nr,
+                                                                    nrh, h->a_n, domega, h->d_a);
+    SK_CU(cudaGetLastError());
+    k_leg_synthesis<<<dim3(L + 1, (unsigned)batch), HT, sizeof(float2) * (L + 1), st>>>(
+        h->d_lam, h->d_moff, h->d_aoff, h->d_kl, h->d_a, L, nr, nrh, h->a_n, h->d_F);
+    SK_CU(cudaGetLastError());
+    // inverse ring DFTs
+    if (ncap > 0) {
+        const size_t sm = sizeof(float2) * 4 * (N - 1) + sizeof(float2) * (L + 1);
+        SK_CU(cudaFuncSetAttribute(k_idft_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_idft_cap<<<dim3(ncap, (unsigned)batch), HT, sm, st>>>(g->d_rings, N, h->d_F, L, nr, d_out, map_stride,
+                                                                 accumulate);
+        SK_CU(cudaGetLastError());
+    }
+    for (long long b = 0; b < batch; ++b) {
+        k_zone_out<<<nb, HT, 0, st>>>(g->d_rings, N, h->d_F, L, nr, b, h->d_X);
+        SK_CU(cudaGetLastError());
+        cufftResult cr = cufftExecC2R(h->p_c2r, reinterpret_cast<cufftComplex *>(h->d_X), h->d_tmp);
+        if (cr != CUFFT_SUCCESS) return cufft_fail(cr, "sk_harmonic_apply");
+        const long long zn = (long long)nb * n4;
+        k_zone_store<<<std::min<long long>((zn + HT - 1) / HT, 4096), HT, 0, st>>>(h->d_tmp, zn,
+                                                                                 d_out + b * map_stride + zone0,
+                                                                                 accumulate);
+        SK_CU(cudaGetLastError());
+    }
+    return SK_OK;
+}
+
+extern "C" int sk_kernel_response(sk_ctx *ctx, const sk_kern *k, int lmax, double *h_R) {
+    if (!ctx || !k || !h_R) return sk_fail(SK_EINVAL, "sk_kernel_response: NULL argument");
+    if (lmax < 0 || lmax > 65535) return sk_fail(SK_EINVAL, "sk_kernel_response: lmax %d outside [0, 65535]", lmax);
+    SK_CU(cudaSetDevice(ctx->device));
+    constexpr int NP = 8;
+    double gx[NP], gw[NP];
+    gauss_legendre(NP, gx, gw);
+    double *d_g = nullptr, *d_R = nullptr;
+    cudaError_t e = cudaMalloc(&d_g, sizeof(double) * 2 * NP);
+    if (e == cudaSuccess) e = cudaMalloc(&d_R, sizeof(double) * (lmax + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(d_g, gx, sizeof(double) * NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_g + NP, gw, sizeof(double) * NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_R, 0, sizeof(double) * (lmax + 1));
+    if (e == cudaSuccess) {
+        const long long nq = (long long)(k->nt - 1) * NP;
+        const size_t sm = sizeof(double) * (lmax + 1);
+        e = cudaFuncSetAttribute(k_response, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess) {
+            k_response<<<(unsigned)((nq + HT - 1) / HT), HT, sm>>>(k->d_V, k->nt, k->tc, k->layout, lmax, d_g,
+                                                                   d_g + NP, NP, d_R);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h_R, d_R, sizeof(double) * (lmax + 1), cudaMemcpyDeviceToHost);
+    cudaFree(d_g);
+    cudaFree(d_R);
+    if (e != cudaSuccess)
+        return sk_fail(e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA, "sk_kernel_response: %s",
+                       cudaGetErrorString(e));
+    return SK_OK;
+}
