@@ -57,6 +57,7 @@ struct sk_harm {
 namespace {
 
 constexpr int HT = 256;
+constexpr int RESYNC = 32;     // ring DFTs: exact twiddle every RESYNC rotations
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -126,15 +127,24 @@ __global__ void k_dft_cap(const RingDev *rings, int nside, const float *x, long 
     __syncthreads();
     float2 *Fr = F + ((long long)b * nr + r) * (L + 1);
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        // w = e^{-2 pi i m j / n}: rotated by w_m per pixel, reset from the exact table
+        // every RESYNC pixels (rounding of the rotation stays below ~RESYNC ulp)
         const int step = m % n;
-        int idx = 0;
+        const float2 rot = tw[step];
         float re = 0.0f, im = 0.0f;
-        for (int j = 0; j < n; ++j) {
-            const float2 w = tw[idx];
-            re = fmaf(xs[j], w.x, re);
-            im = fmaf(xs[j], w.y, im);
-            idx += step;
-            if (idx >= n) idx -= n;
+        int idx = 0;
+        for (int j0 = 0; j0 < n; j0 += RESYNC) {
+            float2 w = tw[idx];
+            const int j1 = min(j0 + RESYNC, n);
+            for (int j = j0; j < j1; ++j) {
+                const float xv = xs[j];
+                re = fmaf(xv, w.x, re);
+                im = fmaf(xv, w.y, im);
+                const float wx = w.x * rot.x - w.y * rot.y;
+                w.y = w.x * rot.y + w.y * rot.x;
+                w.x = wx;
+            }
+            idx = (int)(((long long)step * j1) % n);
         }
         double sn, cs;
         sincospi(-(double)m * R.s / n, &sn, &cs);
@@ -182,12 +192,21 @@ __global__ void k_leg_analysis(const float *lam, const long long *moff, const lo
     for (int l = m + warp; l <= L; l += nw) {
         const float *row = lm + (long long)(l - m) * nrh;
         const float2 *S = sEO + (((l + m) & 1) ? nrh : 0);
-        float re = 0.0f, im = 0.0f;
-        for (int r = lane; r < nrh; r += 32) {
-            const float w = row[r];
-            re = fmaf(w, S[r].x, re);
-            im = fmaf(w, S[r].y, im);
+        float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;
+        int r = lane;
+        for (; r + 96 < nrh; r += 128) {             // four independent loads in flight per lane
+            const float w0 = row[r], w1 = row[r + 32], w2 = row[r + 64], w3 = row[r + 96];
+            re0 = fmaf(w0, S[r].x, re0); im0 = fmaf(w0, S[r].y, im0);
+            re1 = fmaf(w1, S[r + 32].x, re1); im1 = fmaf(w1, S[r + 32].y, im1);
+            re0 = fmaf(w2, S[r + 64].x, re0); im0 = fmaf(w2, S[r + 64].y, im0);
+            re1 = fmaf(w3, S[r + 96].x, re1); im1 = fmaf(w3, S[r + 96].y, im1);
         }
+        for (; r < nrh; r += 32) {
+            const float w = row[r];
+            re0 = fmaf(w, S[r].x, re0);
+            im0 = fmaf(w, S[r].y, im0);
+        }
+        float re = re0 + re1, im = im0 + im1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -267,15 +286,23 @@ __global__ void k_idft_cap(const RingDev *rings, int nside, const float2 *G, int
     __syncthreads();
     float *yr = y + (long long)b * stride + R.start;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        // w = e^{2 pi i m j / n}: rotated by w_j per multipole, reset every RESYNC
         const int step = j % n;
-        int idx = 0;
+        const float2 rot = tw[step];
         float acc = 0.0f;
-        for (int m = 0; m <= L; ++m) {
-            const float2 w = tw[idx], g = gs[m];
-            acc = fmaf(g.x, w.x, acc);
-            acc = fmaf(-g.y, w.y, acc);
-            idx += step;
-            if (idx >= n) idx -= n;
+        int idx = 0;
+        for (int m0 = 0; m0 <= L; m0 += RESYNC) {
+            float2 w = tw[idx];
+            const int m1 = min(m0 + RESYNC, L + 1);
+            for (int m = m0; m < m1; ++m) {
+                const float2 g = gs[m];
+                acc = fmaf(g.x, w.x, acc);
+                acc = fmaf(-g.y, w.y, acc);
+                const float wx = w.x * rot.x - w.y * rot.y;
+                w.y = w.x * rot.y + w.y * rot.x;
+                w.x = wx;
+            }
+            idx = (int)(((long long)step * m1) % n);
         }
         yr[j] = accumulate ? yr[j] + acc : acc;
     }
