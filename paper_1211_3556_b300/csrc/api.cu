@@ -81,6 +81,13 @@ extern "C" int sk_destroy(sk_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->h2d) cudaStreamDestroy(ctx->h2d);
+    if (ctx->d2h) cudaStreamDestroy(ctx->d2h);
+    for (int b = 0; b < SK_HOST_BANDS; ++b) {
+        if (ctx->ev_in[b]) cudaEventDestroy(ctx->ev_in[b]);
+        if (ctx->ev_out[b]) cudaEventDestroy(ctx->ev_out[b]);
+    }
+    if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
@@ -519,6 +526,24 @@ extern "C" int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, co
     return sk_run_grad(ctx, k, d_x, d_gy, batch, map_stride, d_gtable, (double *)ws, (cudaStream_t)stream);
 }
 
+// Host buffers: the map goes up in ring bands ordered by distance from the poles
+// (northern and southern rings of a band together), the sums of a band start once
+// every band its windows reach has arrived, and its outputs go back while later
+// bands are still copied or summed: host-to-device copies, sums and device-to-host
+// copies overlap on three streams.  Page-locked host memory is needed for the
+// copies to be asynchronous (pageable memory still gives the right result).
+static int host_streams(sk_ctx *ctx) {
+    if (ctx->h2d) return SK_OK;
+    SK_CU(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
+    SK_CU(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
+    for (int b = 0; b < SK_HOST_BANDS; ++b) {
+        SK_CU(cudaEventCreateWithFlags(&ctx->ev_in[b], cudaEventDisableTiming));
+        SK_CU(cudaEventCreateWithFlags(&ctx->ev_out[b], cudaEventDisableTiming));
+    }
+    SK_CU(cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming));
+    return SK_OK;
+}
+
 extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in, float *h_out, int64_t batch,
                                 int64_t map_stride, void *stream) {
     if (!ctx || !k) return sk_fail(SK_EINVAL, "sk_convolve_host: NULL argument");
@@ -535,12 +560,63 @@ extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in
     int rc = sk_ctx_workspace(ctx, 2 * half + sk_jobs_workspace_bytes(&jb, 1), &ws);
     if (rc) return rc;
     float *d_in = (float *)ws, *d_out = (float *)((char *)ws + half);
-    jb.x = d_in;
-    jb.y = d_out;
-    SK_CU(cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, st));
-    rc = sk_run_jobs(ctx, &jb, 1, SK_PATH_AUTO, (char *)ws + 2 * half, st);
-    if (rc) return rc;
-    SK_CU(cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st));
+    void *wsj = (char *)ws + 2 * half;
+    sk_kern *km = const_cast<sk_kern *>(k);
+    if ((rc = sk_plan_bands(km))) return rc;
+    if (k->bands.empty()) {                      // no plan (general path only): one block of work
+        jb.x = d_in;
+        jb.y = d_out;
+        SK_CU(cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, st));
+        if ((rc = sk_run_jobs(ctx, &jb, 1, SK_PATH_AUTO, wsj, st))) return rc;
+        SK_CU(cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st));
+        SK_CU(cudaStreamSynchronize(st));
+        return SK_OK;
+    }
+    if ((rc = host_streams(ctx))) return rc;
+    const auto &R = k->g->h_rings;
+    const long long npix = k->g->npix;
+    auto pix = [&](int r) { return r >= k->g->nr ? npix : R[r].start; };
+    // the copies wait for whatever the caller queued on its stream before this call
+    SK_CU(cudaEventRecord(ctx->ev_done, st));
+    SK_CU(cudaStreamWaitEvent(ctx->h2d, ctx->ev_done, 0));
+    for (long long m = 0; m < batch; ++m) {
+        const long long mo = m * map_stride;
+        for (size_t b = 0; b < k->bands.size(); ++b) {
+            const sk_kern::Band &B = k->bands[b];
+            const long long n0 = pix(B.n_lo), n1 = pix(B.n_hi), s0 = pix(B.s_lo), s1 = pix(B.s_hi);
+            if (n1 > n0)
+                SK_CU(cudaMemcpyAsync(d_in + mo + n0, h_in + mo + n0, sizeof(float) * (n1 - n0),
+                                      cudaMemcpyHostToDevice, ctx->h2d));
+            if (s1 > s0)
+                SK_CU(cudaMemcpyAsync(d_in + mo + s0, h_in + mo + s0, sizeof(float) * (s1 - s0),
+                                      cudaMemcpyHostToDevice, ctx->h2d));
+            SK_CU(cudaEventRecord(ctx->ev_in[b], ctx->h2d));
+        }
+        for (size_t b = 0; b < k->bands.size(); ++b) {
+            const sk_kern::Band &B = k->bands[b];
+            SK_CU(cudaStreamWaitEvent(st, ctx->ev_in[B.need], 0));
+            SkJob j{k, d_in + mo, d_out + mo, 1, map_stride};
+            j.sub = &B.items;
+            j.weights = (m == 0 && b == 0);      // the belt weight rows stay in the workspace
+            if ((rc = sk_run_jobs(ctx, &j, 1, SK_PATH_AUTO, wsj, st))) return rc;
+            SK_CU(cudaEventRecord(ctx->ev_out[b], st));
+            SK_CU(cudaStreamWaitEvent(ctx->d2h, ctx->ev_out[b], 0));
+            // every band whose outputs are complete once this band's sums are done
+            for (size_t o = 0; o < k->bands.size(); ++o) {
+                const sk_kern::Band &O = k->bands[o];
+                if (O.ready != (int)b) continue;
+                const long long n0 = pix(O.n_lo), n1 = pix(O.n_hi), s0 = pix(O.s_lo), s1 = pix(O.s_hi);
+                if (n1 > n0)
+                    SK_CU(cudaMemcpyAsync(h_out + mo + n0, d_out + mo + n0, sizeof(float) * (n1 - n0),
+                                          cudaMemcpyDeviceToHost, ctx->d2h));
+                if (s1 > s0)
+                    SK_CU(cudaMemcpyAsync(h_out + mo + s0, d_out + mo + s0, sizeof(float) * (s1 - s0),
+                                          cudaMemcpyDeviceToHost, ctx->d2h));
+            }
+        }
+    }
+    SK_CU(cudaEventRecord(ctx->ev_done, ctx->d2h));
+    SK_CU(cudaStreamWaitEvent(st, ctx->ev_done, 0));
     SK_CU(cudaStreamSynchronize(st));
     return SK_OK;
 }

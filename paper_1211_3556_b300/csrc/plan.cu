@@ -80,7 +80,15 @@ void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_items_tc); k->d_items_tc = nullptr;
     k->tc_ok = false;
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
-        for (int v = 0; v < 2; ++v) { cudaFree(k->d_items_cap[c][v]); k->d_items_cap[c][v] = nullptr; }
+        for (int v = 0; v < 2; ++v) {
+            cudaFree(k->d_items_cap[c][v]); k->d_items_cap[c][v] = nullptr;
+            k->h_items_cap[c][v].clear();
+        }
+    k->h_items_belt.clear();
+    k->h_items_gen.clear();
+    cudaFree(k->d_band_items); k->d_band_items = nullptr;
+    k->bands.clear();
+    k->bands_P = 0;
     k->plan_ok = false;
 }
 
@@ -96,6 +104,7 @@ int sk_plan_rebuild_belt_items(sk_kern *k) {
     for (int g = 0; g < k->ngroups; ++g)
         for (int s = 0; s < nseg; ++s) it.push_back(make_int4(g, s, 0, 0));
     k->n_items_belt = (int)it.size();
+    k->h_items_belt = it;
     return upload(it, &k->d_items_belt);
 }
 
@@ -258,6 +267,7 @@ int sk_plan_build(sk_kern *k) {
                 return (off[a.x + 1] - off[a.x]) > (off[b.x + 1] - off[b.x]);
             });
             k->n_items_cap[c][v] = (int)cap_items[c][v].size();
+            k->h_items_cap[c][v] = cap_items[c][v];
             int rc = upload(cap_items[c][v], &k->d_items_cap[c][v]);
             if (rc) return rc;
         }
@@ -273,9 +283,120 @@ int sk_plan_build(sk_kern *k) {
         }
     if (int rc0 = upload(path, &k->d_ring_path)) return rc0;
     k->n_items_gen = (int)gen.size();
+    k->h_items_gen = gen;
     int rc = upload(gen, &k->d_items_gen);
     if (rc) return rc;
     k->plan_ok = true;
+    return SK_OK;
+}
+
+int sk_plan_bands(sk_kern *k) {
+    if (!k->plan_ok) return SK_OK;
+    if (!k->bands.empty() && k->bands_P == k->belt_P) return SK_OK;
+    cudaFree(k->d_band_items);
+    k->d_band_items = nullptr;
+    k->bands.clear();
+    const sk_geom *g = k->g;
+    const int nr = g->nr, eq = nr / 2;                   // equator ring (0-based): distance eq from both poles
+    auto dist = [&](int r) { return std::min(r, nr - 1 - r); };
+    // band edges in pole distance: equal pixel counts (both hemispheres)
+    const int K = SK_HOST_BANDS;
+    std::vector<int> edge(K + 1, eq + 1);
+    edge[0] = 0;
+    {
+        long long tot = g->npix, acc = 0;
+        int b = 1;
+        for (int d = 0; d <= eq && b < K; ++d) {
+            acc += (d == eq) ? g->h_rings[d].n : 2LL * g->h_rings[d].n;
+            while (b < K && acc * K >= tot * b) edge[b++] = d + 1;
+        }
+        for (int i = 1; i <= K; ++i) edge[i] = std::max(edge[i], edge[i - 1]);
+    }
+    auto band_of = [&](int d) {
+        int b = 0;
+        while (b + 1 < K && d >= edge[b + 1]) ++b;
+        return b;
+    };
+    // largest pole distance of any input ring of output ring r
+    auto reach = [&](int r) {
+        const int lo = k->h_lo[r], hi = k->h_hi[r];
+        return (lo <= eq && eq <= hi) ? eq : std::max(dist(lo), dist(hi));
+    };
+    std::vector<std::vector<int4>> belt(K), gen(K), cap[SK_CAP_LS_CLASSES][2];
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v) cap[c][v].resize(K);
+    std::vector<int> reach_b(K, 0), ready(K);
+    for (int b = 0; b < K; ++b) ready[b] = b;
+    for (const int4 &it : k->h_items_belt) {
+        // a group of belt rings runs in the band of its ring nearest the equator; the
+        // outputs of its other rings are ready only then
+        int dmax = 0, rmax = 0;
+        for (int w = 0; w < SK_BELT_G; ++w) {
+            const int r = k->b_lo + it.x * SK_BELT_G + w;
+            if (r >= k->b_lo + k->nb) break;
+            dmax = std::max(dmax, dist(r));
+            rmax = std::max(rmax, reach(r));
+        }
+        const int b = band_of(dmax);
+        belt[b].push_back(it);
+        reach_b[b] = std::max(reach_b[b], rmax);
+        for (int w = 0; w < SK_BELT_G; ++w) {
+            const int r = k->b_lo + it.x * SK_BELT_G + w;
+            if (r >= k->b_lo + k->nb) break;
+            ready[band_of(dist(r))] = std::max(ready[band_of(dist(r))], b);
+        }
+    }
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v)
+            for (const int4 &it : k->h_items_cap[c][v]) {
+                const int b = band_of(dist(it.x));
+                cap[c][v][b].push_back(it);
+                reach_b[b] = std::max(reach_b[b], reach(it.x));
+            }
+    for (const int4 &it : k->h_items_gen) {
+        const int b = band_of(dist(it.x));
+        gen[b].push_back(it);
+        reach_b[b] = std::max(reach_b[b], reach(it.x));
+    }
+    // one device array, band by band and path by path
+    std::vector<int4> all;
+    struct Off { size_t belt, cap[SK_CAP_LS_CLASSES][2], gen; };
+    std::vector<Off> off(K);
+    for (int b = 0; b < K; ++b) {
+        off[b].belt = all.size();
+        all.insert(all.end(), belt[b].begin(), belt[b].end());
+        for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+            for (int v = 0; v < 2; ++v) {
+                off[b].cap[c][v] = all.size();
+                all.insert(all.end(), cap[c][v][b].begin(), cap[c][v][b].end());
+            }
+        off[b].gen = all.size();
+        all.insert(all.end(), gen[b].begin(), gen[b].end());
+    }
+    int4 *d = nullptr;
+    if (int rc = upload(all, &d)) return rc;
+    k->d_band_items = d;
+    k->bands.resize(K);
+    for (int b = 0; b < K; ++b) {
+        sk_kern::Band &B = k->bands[b];
+        B.n_lo = edge[b];
+        B.n_hi = std::min(edge[b + 1], eq + 1);
+        B.s_lo = std::max(nr - edge[b + 1], eq + 1);
+        B.s_hi = nr - edge[b];
+        B.need = band_of(reach_b[b]);
+        B.need = std::max(B.need, b);
+        B.ready = ready[b];
+        B.items.belt = belt[b].empty() ? nullptr : d + off[b].belt;
+        B.items.n_belt = (int)belt[b].size();
+        for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+            for (int v = 0; v < 2; ++v) {
+                B.items.cap[c][v] = cap[c][v][b].empty() ? nullptr : d + off[b].cap[c][v];
+                B.items.n_cap[c][v] = (int)cap[c][v][b].size();
+            }
+        B.items.gen = gen[b].empty() ? nullptr : d + off[b].gen;
+        B.items.n_gen = (int)gen[b].size();
+    }
+    k->bands_P = k->belt_P;
     return SK_OK;
 }
 
@@ -363,6 +484,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
             wrows[i] = (float *)wp;
             wp += sk_plan_workspace_bytes(k);
+            if (!jobs[i].weights) continue;             // rows already in the workspace
             JobDesc d = belt_desc(jobs[i], nullptr);
             cudaEvent_t ev = sk_prof_begin(ctx, st);
             if (path == SK_PATH_TENSOR && k->tc_ok)
@@ -438,8 +560,12 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || k->belt_P != P || jobs[i].batch == 0) continue;
             if (path == SK_PATH_TENSOR && k->tc_ok) continue;     // done on the tensor cores
+            const SkItems *sub = jobs[i].sub;
+            const int4 *items = sub ? sub->belt : k->d_items_belt;
+            const int n_items = sub ? sub->n_belt : k->n_items_belt;
+            if (n_items == 0) continue;
             JobDesc d = belt_desc(jobs[i], wrows[i]);
-            b.add(d, k->d_items_belt, k->n_items_belt);
+            b.add(d, items, n_items);
             if (b.full()) { int rc = flush(); if (rc) return rc; }
         }
         int rc = flush();
@@ -469,14 +595,17 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             };
             for (int i = 0; i < n; ++i) {
                 const sk_kern *k = jobs[i].k;
-                if (!k->plan_ok || k->n_items_cap[c][v] == 0 || jobs[i].batch == 0) continue;
+                const SkItems *sub = jobs[i].sub;
+                const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
+                const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
+                if (!k->plan_ok || cn == 0 || jobs[i].batch == 0) continue;
                 const int kmode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
                 if (kmode != mode) continue;
                 // one node table per launch (the blocks load it once)
                 if (b.a.n_jobs > 0 && b.a.j[0].tab != k->d_tab) { int rc = flush(); if (rc) return rc; }
                 JobDesc d = base_desc(jobs[i]);
                 d.cap_ls = SK_CAP_LS[c];
-                b.add(d, k->d_items_cap[c][v], k->n_items_cap[c][v]);
+                b.add(d, citems, cn);
                 if (b.full()) { int rc = flush(); if (rc) return rc; }
             }
             int rc = flush();
@@ -499,8 +628,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         for (int i = 0; i < n; ++i) {
             const sk_kern *k = jobs[i].k;
             if (jobs[i].batch == 0) continue;
-            const int4 *items = k->plan_ok ? k->d_items_gen : k->d_items_all;
-            const int ni = k->plan_ok ? k->n_items_gen : k->n_items_all;
+            const SkItems *sub = jobs[i].sub;
+            const int4 *items = sub ? sub->gen : (k->plan_ok ? k->d_items_gen : k->d_items_all);
+            const int ni = sub ? sub->n_gen : (k->plan_ok ? k->n_items_gen : k->n_items_all);
             if (ni == 0) continue;
             b.add(base_desc(jobs[i]), items, ni);
             if (b.full()) { int rc = flush(); if (rc) return rc; }

@@ -10,6 +10,8 @@
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
 
+constexpr int SK_HOST_BANDS = 8;   // ring bands of the host-buffer pipeline (sk_convolve_host)
+
 struct sk_ctx {
     int device = 0;
     int num_sms = 0;
@@ -24,6 +26,20 @@ struct sk_ctx {
     bool prof = false;
     struct ProfRec { const char *name; cudaEvent_t a, b; };
     std::vector<ProfRec> prof_recs;
+    // host-buffer pipeline: copy streams and per-band events (created on first use)
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[SK_HOST_BANDS] = {}, ev_out[SK_HOST_BANDS] = {}, ev_done = nullptr;
+};
+
+// A subset of a kernel's work items (the output rings of one band); null lists mean
+// "none of this path".
+struct SkItems {
+    const int4 *belt = nullptr;
+    int n_belt = 0;
+    const int4 *cap[SK_CAP_LS_CLASSES][2] = {};
+    int n_cap[SK_CAP_LS_CLASSES][2] = {};
+    const int4 *gen = nullptr;
+    int n_gen = 0;
 };
 
 struct sk_geom {
@@ -79,6 +95,19 @@ struct sk_kern {
     TcGeom tcg{};
     int4 *d_items_tc = nullptr;
     int n_items_tc = 0;
+    // host copies of the item lists, and their partition into ring bands by distance
+    // from the nearest pole (sk_convolve_host overlaps the copies of one band with the
+    // sums of another); rebuilt when the belt tile width changes
+    std::vector<int4> h_items_belt, h_items_cap[SK_CAP_LS_CLASSES][2], h_items_gen;
+    struct Band {
+        int n_lo, n_hi, s_lo, s_hi;   // output rings [n_lo, n_hi) and [s_lo, s_hi)
+        int need;                     // last band whose input rings the sums read
+        int ready;                    // last band whose sums write output rings of this band
+        SkItems items;
+    };
+    std::vector<Band> bands;
+    int bands_P = 0;
+    int4 *d_band_items = nullptr;
 };
 
 // api.cu
@@ -99,7 +128,11 @@ struct SkJob {
     const float *x;
     float *y;
     long long batch, stride;
+    const SkItems *sub = nullptr;   // only these items (null: all of the kernel's)
+    bool weights = true;            // run the belt weight pre-pass (else the workspace holds it)
 };
+// Partition of k's items into ring bands (kept in k; rebuilt when stale).
+int sk_plan_bands(sk_kern *k);
 // Launch sequence of the forward operator for a set of jobs.  `ws` must hold
 // sk_jobs_workspace_bytes(jobs) bytes (belt weight rows).
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n);
