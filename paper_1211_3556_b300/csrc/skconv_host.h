@@ -10,7 +10,7 @@
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
 
-constexpr int SK_HOST_BANDS = 8;   // ring bands of the host-buffer pipeline (sk_convolve_host)
+constexpr int SK_HOST_BANDS = 16;  // ring bands of the host-buffer pipeline (sk_convolve_host)
 
 struct sk_ctx {
     int device = 0;
