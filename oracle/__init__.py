@@ -23,6 +23,10 @@ splitting"):
 * ``real_ylm`` / ``sht_convolve``: a plain spherical-harmonic transform for the
   harmonic part (the role the paper gives to the CPU SHT, Sec. 2);
 * ``relative_error_estimate``: the fractional rms estimate of Eq. 2;
+* ``hat_response_matrix`` / ``fit_real_kernel``: the real-space part as a
+  least-squares fit (Sec. 3: K^_theta is fit so that its harmonic transform
+  matches K_l above l_cut), a piecewise-linear kernel on [0, theta_cut] that
+  vanishes at theta_cut, by ``numpy.linalg.lstsq`` on the plain objective;
 * gradients: the table gradient in C and a finite-difference helper.
 """
 from __future__ import annotations
@@ -235,6 +239,61 @@ def harmonic_part(k_ell: np.ndarray, R: np.ndarray, lcut: int) -> np.ndarray:
     kh = np.zeros_like(k_ell)
     kh[: lcut + 1] = k_ell[: lcut + 1] - R[: lcut + 1]
     return kh
+
+
+def hat_response_matrix(n_basis: int, theta_cut: float, lmin: int, lmax: int, npts: int = 8) -> np.ndarray:
+    """M[l - lmin, k] = 2 pi int hat_k(theta) P_l(cos theta) sin theta dtheta for
+    l = lmin..lmax and the hat functions of the uniform nodes theta_k =
+    k theta_cut / (n_basis - 1), k = 0..n_basis - 2 (the node at theta_cut is
+    held at 0).  Gauss-Legendre with npts points on every node interval."""
+    th = np.linspace(0.0, theta_cut, n_basis)
+    g, w = np.polynomial.legendre.leggauss(npts)
+    a, b = th[:-1, None], th[1:, None]
+    tq = (0.5 * (b - a) * g[None, :] + 0.5 * (a + b)).ravel()          # [(n-1) npts]
+    wq = np.broadcast_to(0.5 * (b - a) * w[None, :], (n_basis - 1, npts)).ravel()
+    f = ((tq.reshape(n_basis - 1, npts) - a) / (b - a)).ravel()
+    ivl = np.repeat(np.arange(n_basis - 1), npts)
+    # hat_k on interval i: 1 - f for k = i, f for k = i + 1
+    H = np.zeros((len(tq), n_basis))
+    H[np.arange(len(tq)), ivl] = 1.0 - f
+    H[np.arange(len(tq)), ivl + 1] = f
+    P = legendre_P(lmax, np.cos(tq))[lmin:]                              # [l, q]
+    M = 2.0 * math.pi * (P * (wq * np.sin(tq))[None, :]) @ H
+    return M[:, : n_basis - 1]
+
+
+def fit_real_kernel(k_ell: np.ndarray, lcut: int, lfit: int, theta_cut: float, n_basis: int,
+                    nt_out: int, low_weight: float = 1e-3, reg: float = 1e-9):
+    """Node values (nt_out uniform nodes) of the least-squares real-space part:
+    minimise sum_{l=0}^{lfit} w_l (2l+1) (R_l(c) - K_l)^2 + lam |c|^2 over the
+    hat-basis coefficients c, with w_l = 1 above l_cut (where the real-space part
+    alone carries K_l) and w_l = low_weight at and below l_cut (there K^_l = K_l -
+    R_l absorbs any mismatch; the small weight keeps the two halves from
+    carrying large parts that cancel), lam = reg * trace(A^T A) / n.  The
+    piecewise-linear kernel is sampled at the output nodes ((nt_out - 1) a
+    multiple of (n_basis - 1), so the output table represents it exactly).
+    Returns (V, sigma_rms): sigma_rms^2 = sum_{l>lcut}^{lfit} (2l+1)(R_l - K_l)^2 /
+    sum_{l<=lfit} (2l+1) K_l^2 (Eq. 2 without alpha)."""
+    k_ell = _f64(k_ell)
+    M = hat_response_matrix(n_basis, theta_cut, 0, lfit)
+    ell = np.arange(0, lfit + 1, dtype=np.float64)
+    wl = np.where(ell > lcut, 1.0, low_weight)
+    sw = np.sqrt(wl * (2.0 * ell + 1.0))
+    A = M * sw[:, None]
+    y = k_ell[: lfit + 1] * sw
+    n = M.shape[1]
+    lam = reg * float(np.sum(A * A)) / n
+    Aa = np.vstack([A, math.sqrt(lam) * np.eye(n)])
+    ya = np.concatenate([y, np.zeros(n)])
+    c = np.linalg.lstsq(Aa, ya, rcond=None)[0]
+    coarse = np.concatenate([c, [0.0]])
+    th_out = np.linspace(0.0, theta_cut, nt_out)
+    V = np.interp(th_out, np.linspace(0.0, theta_cut, n_basis), coarse)
+    res = (M @ c - k_ell[: lfit + 1])[lcut + 1:]
+    hi = ell[lcut + 1:]
+    sig = math.sqrt(float(np.sum((2 * hi + 1) * res ** 2)) /
+                    float(np.sum((2 * ell + 1) * k_ell[: lfit + 1] ** 2)))
+    return V, sig
 
 
 def relative_error_estimate(k_ell: np.ndarray, k_approx: np.ndarray, alpha: float = 5.0) -> float:

@@ -354,3 +354,53 @@ def test_table_gradient_equals_central_differences():
             e = np.zeros(nt); e[n] = h
             fd = (loss(V + e) - loss(V - e)) / (2 * h)   # quadratic: exact up to rounding
             assert fd == pytest.approx(g[n], rel=1e-8, abs=1e-9 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------- least-squares split
+
+def _trunc_on_basis(k_ell, lcut, lfit, tc, n_basis):
+    # the high-pass-and-truncate kernel (reading of Sec. 3) sampled on the basis nodes
+    th = np.linspace(0.0, tc, n_basis)
+    v = O.legendre_series(k_ell, lcut + 1, lfit, th) * O.taper(th, tc, 0.9)
+    v[-1] = 0.0
+    return v
+
+
+def test_fit_recovers_a_planted_response():
+    # K_l made from a kernel of the basis: the fit reproduces it above l_cut
+    nb, tc, lcut, lfit = 33, 0.3, 10, 120
+    M = O.hat_response_matrix(nb, tc, 0, lfit)
+    c_true = 10.0 * np.sin(np.linspace(0.0, 3.0, nb - 1))
+    kl = M @ c_true
+    V, sig = O.fit_real_kernel(kl, lcut, lfit, tc, nb, nb)
+    assert sig < 1e-6
+    R = O.kernel_response(V, tc, 0, lfit)
+    assert np.max(np.abs(R[lcut + 1:] - kl[lcut + 1:])) < 1e-5 * np.max(np.abs(kl))
+
+
+def test_fit_reported_sigma_matches_independent_response():
+    # sigma from the fit's own response matrix equals the one recomputed from the
+    # output table by kernel_response (a separate quadrature over the fine nodes)
+    tc, lcut, lfit, nb = 180.0 * ARCMIN, 96, 384, 129
+    kl = gaussian_beam(60.0, lfit)
+    V, sig = O.fit_real_kernel(kl, lcut, lfit, tc, nb, 8 * (nb - 1) + 1)
+    R = O.kernel_response(V, tc, 0, lfit)
+    ell = np.arange(lfit + 1)
+    num = np.sum((2 * ell[lcut + 1:] + 1) * (R[lcut + 1:] - kl[lcut + 1:]) ** 2)
+    den = np.sum((2 * ell + 1) * kl ** 2)
+    assert abs(math.sqrt(num / den) - sig) <= 1e-6 * sig + 1e-12
+
+
+@pytest.mark.parametrize("fwhm,tcf,lcut,lfit", [(60.0, 3.0, 96, 384), (7.1, 2.8, 1024, 4096)])
+def test_fit_beats_truncation(fwhm, tcf, lcut, lfit):
+    # the least-squares kernel minimises Eq. 2's residual over the basis, so it is
+    # no worse than the truncated high-pass kernel on the same nodes
+    tc, nb = tcf * fwhm * ARCMIN, 129
+    kl = gaussian_beam(fwhm, lfit)
+    V, sig = O.fit_real_kernel(kl, lcut, lfit, tc, nb, nb)
+    vt = _trunc_on_basis(kl, lcut, lfit, tc, nb)
+    Rt = O.hat_response_matrix(nb, tc, 0, lfit) @ vt[:-1]
+    ell = np.arange(lfit + 1)
+    num = np.sum((2 * ell[lcut + 1:] + 1) * (Rt[lcut + 1:] - kl[lcut + 1:]) ** 2)
+    sig_t = math.sqrt(num / np.sum((2 * ell + 1) * kl ** 2))
+    assert sig <= sig_t
