@@ -293,6 +293,27 @@ typedef struct sk_harm sk_harm;
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int sk_kernel_response(sk_ctx *ctx, const sk_kern *k, int lmax, double *h_R);
 
+/* The real-space part as a least-squares fit (Sec. 3: the real-space kernel
+ * K^_theta is fit so that its harmonic transform matches K_l above l_cut; the
+ * paper does not say how).  Unknowns: the values c_k of a piecewise-linear
+ * kernel on the uniform nodes k theta_cut/(n_basis-1), k < n_basis-1, zero at
+ * theta_cut.  Objective:
+ *   sum_{l=0}^{lfit} w_l (2l+1) (R_l(c) - K_l)^2 + lam |c|^2,
+ *   w_l = 1 for l > lcut, low_weight for l <= lcut (K^_l = K_l - R_l carries
+ *   those; a small weight keeps the halves from carrying large cancelling parts),
+ *   lam = reg * trace(normal matrix) / (n_basis - 1),
+ * with R_l(c) by 8-point Gauss-Legendre per node interval (FP64 on the device),
+ * solved by Cholesky of the normal equations (FP64, host).  h_kl[0..lfit]: K_l.
+ * Output: h_V[nt_out] node values on nt_out uniform nodes of [0, theta_cut]
+ * ((nt_out-1) a multiple of (n_basis-1): the table represents the fitted kernel
+ * exactly), and *h_sigma_rms (may be NULL) =
+ *   sqrt(sum_{l>lcut}^{lfit} (2l+1)(R_l - K_l)^2 / sum_{l<=lfit} (2l+1) K_l^2),
+ * Eq. 2's sigma_rms relative to the kernel (without its factor alpha).
+ * Errors: SK_EINVAL (ranges; a normal matrix that is not positive definite:
+ * raise reg), SK_ENOMEM, SK_ECUDA. */
+int sk_fit_real_kernel(sk_ctx *ctx, const double *h_kl, int lfit, int lcut, double theta_cut, int n_basis,
+                       int nt_out, double low_weight, double reg, double *h_V, double *h_sigma_rms);
+
 /* Builds the harmonic operator for geometry g: copies h_kl[0..lmax] (FP64
  * host array, K^_l) and tabulates lambda_lm on the device.
  * Errors: SK_EINVAL (NULL, lmax outside [0, 2 nside - 1]), SK_EUNSUPPORTED

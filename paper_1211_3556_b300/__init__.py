@@ -79,6 +79,7 @@ def _declare(L):
         "sk_selftest_tc_gemm": (I, [P, P, P, P, I, I, I, P]),
         "sk_kernel_get_tiles": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sk_kernel_response": (I, [P, P, I, P]),
+        "sk_fit_real_kernel": (I, [P, P, I, I, D, I, I, D, D, P, P]),
         "sk_harmonic_create": (I, [P, P, P, I, PP]),
         "sk_harmonic_destroy": (I, [P]),
         "sk_harmonic_table_bytes": (I, [P, ctypes.POINTER(I64)]),
@@ -374,6 +375,21 @@ def kernel_response(kern: Kernel, lmax: int):
     R = np.empty(int(lmax) + 1, np.float64)
     _check(lib().sk_kernel_response(kern.ctx._h, kern._h, int(lmax), R.ctypes.data))
     return R
+
+
+def fit_real_kernel(ctx: Context, k_ell, lcut: int, theta_cut: float, n_basis: int = 257, nt_out: int = None,
+                    lfit: int = None, low_weight: float = 1e-3, reg: float = 1e-9):
+    """Least-squares real-space part of K_l (see sk_fit_real_kernel): returns
+    (node values on nt_out uniform nodes of [0, theta_cut], sigma_rms)."""
+    kl = np.ascontiguousarray(np.asarray(k_ell, dtype=np.float64))
+    lfit = len(kl) - 1 if lfit is None else int(lfit)
+    if nt_out is None:
+        nt_out = 32 * (n_basis - 1) + 1
+    V = np.empty(int(nt_out), np.float64)
+    sig = ctypes.c_double()
+    _check(lib().sk_fit_real_kernel(ctx._h, kl.ctypes.data, lfit, int(lcut), float(theta_cut), int(n_basis),
+                                    int(nt_out), float(low_weight), float(reg), V.ctypes.data, ctypes.byref(sig)))
+    return V, sig.value
 
 
 class Harmonic:

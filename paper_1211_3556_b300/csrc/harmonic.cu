@@ -402,6 +402,50 @@ void gauss_legendre(int n, double *x, double *w) {
     }
 }
 
+// Response matrix of the hat basis: M[l][k] = 2 pi int hat_k P_l(cos t) sin t dt,
+// l = 0..lfit, k = 0..n_u-1 (uniform nodes t_k = k h, h = theta_cut / n_u; the
+// node at theta_cut is held at 0).  Half a warp per hat: lanes 0-7 take the 8
+// Gauss points of [t_{k-1}, t_k], lanes 8-15 those of [t_k, t_{k+1}].
+__global__ void k_hat_response(int n_u, double h, int lfit, const double *gx, const double *gw, double *M) {
+    const int hw = (blockIdx.x * blockDim.x + threadIdx.x) >> 4, ln = threadIdx.x & 15;
+    const bool live = hw < n_u;
+    const int k = live ? hw : 0;
+    const int side = ln >> 3, i = ln & 7;             // 0: interval left of node k, 1: right
+    double c = 0.0, x = 1.0;
+    if (live && !(side == 0 && k == 0)) {
+        const double a = (k - 1 + side) * h;          // interval [a, a + h]
+        const double t = a + 0.5 * h * (gx[i] + 1.0);
+        const double f = (t - a) / h;
+        const double hat = side == 0 ? f : 1.0 - f;
+        c = 2.0 * SK_PI * 0.5 * h * gw[i] * hat * sin(t);
+        x = cos(t);
+    }
+    double p0 = 1.0, p1 = x;
+    for (int l = 0; l <= lfit; ++l) {
+        double pl;
+        if (l == 0) pl = p0;
+        else if (l == 1) pl = p1;
+        else {
+            pl = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / (double)l;
+            p0 = p1;
+            p1 = pl;
+        }
+        double v = c * pl;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (live && ln == 0) M[(long long)l * n_u + k] = v;
+    }
+}
+
+// A[i][j] = sum_l W_l M[l][i] M[l][j]: one thread per entry.
+__global__ void k_normal_matrix(const double *M, const double *W, int n_u, int lfit, double *A) {
+    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_u) return;
+    double acc = 0.0;
+    for (int l = 0; l <= lfit; ++l) acc += W[l] * M[(long long)l * n_u + i] * M[(long long)l * n_u + j];
+    A[(long long)i * n_u + j] = acc;
+}
+
 void free_harm(sk_harm *h) {
     if (!h) return;
     if (h->plans) { cufftDestroy(h->p_r2c); cufftDestroy(h->p_c2r); }
@@ -596,5 +640,102 @@ extern "C" int sk_kernel_response(sk_ctx *ctx, const sk_kern *k, int lmax, doubl
     if (e != cudaSuccess)
         return sk_fail(e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA, "sk_kernel_response: %s",
                        cudaGetErrorString(e));
+    return SK_OK;
+}
+
+// Least-squares real-space part (Sec. 3: K^_theta is fit so that its harmonic
+// transform matches K_l above l_cut).  See skconv.h.
+extern "C" int sk_fit_real_kernel(sk_ctx *ctx, const double *h_kl, int lfit, int lcut, double theta_cut,
+                                  int n_basis, int nt_out, double low_weight, double reg, double *h_V,
+                                  double *h_sigma_rms) {
+    if (!ctx || !h_kl || !h_V) return sk_fail(SK_EINVAL, "sk_fit_real_kernel: NULL argument");
+    if (lfit < 1 || lfit > 65535 || lcut < 0 || lcut >= lfit)
+        return sk_fail(SK_EINVAL, "sk_fit_real_kernel: need 0 <= lcut < lfit <= 65535");
+    if (!(theta_cut > 0.0 && theta_cut <= SK_PI)) return sk_fail(SK_EINVAL, "sk_fit_real_kernel: theta_cut");
+    if (n_basis < 3 || n_basis > 4097 || nt_out < n_basis || (nt_out - 1) % (n_basis - 1))
+        return sk_fail(SK_EINVAL, "sk_fit_real_kernel: need 3 <= n_basis <= 4097 and (nt_out-1) a multiple of (n_basis-1)");
+    if (!(low_weight >= 0.0) || !(reg >= 0.0)) return sk_fail(SK_EINVAL, "sk_fit_real_kernel: negative weight");
+    SK_CU(cudaSetDevice(ctx->device));
+    const int n_u = n_basis - 1;
+    const double h = theta_cut / n_u;
+    constexpr int NP = 8;
+    double gx[NP], gw[NP];
+    gauss_legendre(NP, gx, gw);
+    std::vector<double> W(lfit + 1);
+    for (int l = 0; l <= lfit; ++l) W[l] = (l > lcut ? 1.0 : low_weight) * (2.0 * l + 1.0);
+    double *d_g = nullptr, *d_M = nullptr, *d_W = nullptr, *d_A = nullptr;
+    const size_t mbytes = sizeof(double) * (size_t)(lfit + 1) * n_u;
+    cudaError_t e = cudaMalloc(&d_g, sizeof(double) * 2 * NP);
+    if (e == cudaSuccess) e = cudaMalloc(&d_M, mbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_W, sizeof(double) * (lfit + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_A, sizeof(double) * (size_t)n_u * n_u);
+    if (e == cudaSuccess) e = cudaMemcpy(d_g, gx, sizeof(double) * NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_g + NP, gw, sizeof(double) * NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_W, W.data(), sizeof(double) * (lfit + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const long long thr = (long long)n_u * 16;
+        k_hat_response<<<(unsigned)((thr + HT - 1) / HT), HT>>>(n_u, h, lfit, d_g, d_g + NP, d_M);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_normal_matrix<<<dim3((n_u + 127) / 128, n_u), 128>>>(d_M, d_W, n_u, lfit, d_A);
+        e = cudaGetLastError();
+    }
+    std::vector<double> M((size_t)(lfit + 1) * n_u), A((size_t)n_u * n_u);
+    if (e == cudaSuccess) e = cudaMemcpy(M.data(), d_M, mbytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(A.data(), d_A, sizeof(double) * A.size(), cudaMemcpyDeviceToHost);
+    cudaFree(d_g); cudaFree(d_M); cudaFree(d_W); cudaFree(d_A);
+    if (e != cudaSuccess)
+        return sk_fail(e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA, "sk_fit_real_kernel: %s",
+                       cudaGetErrorString(e));
+    // right-hand side, Tikhonov term, Cholesky (A is symmetric positive definite with lam > 0)
+    std::vector<double> b(n_u, 0.0);
+    for (int l = 0; l <= lfit; ++l)
+        for (int k = 0; k < n_u; ++k) b[k] += W[l] * h_kl[l] * M[(size_t)l * n_u + k];
+    double tr = 0.0;
+    for (int k = 0; k < n_u; ++k) tr += A[(size_t)k * n_u + k];
+    const double lam = reg * tr / n_u;
+    for (int k = 0; k < n_u; ++k) A[(size_t)k * n_u + k] += lam;
+    for (int j = 0; j < n_u; ++j) {
+        double d = A[(size_t)j * n_u + j];
+        for (int q = 0; q < j; ++q) d -= A[(size_t)j * n_u + q] * A[(size_t)j * n_u + q];
+        if (!(d > 0.0)) return sk_fail(SK_EINVAL, "sk_fit_real_kernel: normal matrix not positive definite (raise reg)");
+        const double ljj = sqrt(d);
+        A[(size_t)j * n_u + j] = ljj;
+        for (int i = j + 1; i < n_u; ++i) {
+            double v = A[(size_t)i * n_u + j];
+            for (int q = 0; q < j; ++q) v -= A[(size_t)i * n_u + q] * A[(size_t)j * n_u + q];
+            A[(size_t)i * n_u + j] = v / ljj;
+        }
+    }
+    std::vector<double> c(n_u);
+    for (int i = 0; i < n_u; ++i) {                  // L z = b
+        double v = b[i];
+        for (int q = 0; q < i; ++q) v -= A[(size_t)i * n_u + q] * c[q];
+        c[i] = v / A[(size_t)i * n_u + i];
+    }
+    for (int i = n_u - 1; i >= 0; --i) {             // L^T c = z
+        double v = c[i];
+        for (int q = i + 1; q < n_u; ++q) v -= A[(size_t)q * n_u + i] * c[q];
+        c[i] = v / A[(size_t)i * n_u + i];
+    }
+    // sample the piecewise-linear kernel at the output nodes (the coarse nodes are among them)
+    const int q = (nt_out - 1) / n_u;
+    for (int i = 0; i < nt_out; ++i) {
+        const int k = i / q, r = i % q;
+        const double ck = k < n_u ? c[k] : 0.0, ck1 = (k + 1) < n_u ? c[k + 1] : 0.0;
+        h_V[i] = r == 0 ? ck : ck + (ck1 - ck) * (double)r / (double)q;
+    }
+    if (h_sigma_rms) {
+        double num = 0.0, den = 0.0;
+        for (int l = 0; l <= lfit; ++l) {
+            den += (2.0 * l + 1.0) * h_kl[l] * h_kl[l];
+            if (l <= lcut) continue;
+            double R = 0.0;
+            for (int k = 0; k < n_u; ++k) R += M[(size_t)l * n_u + k] * c[k];
+            num += (2.0 * l + 1.0) * (R - h_kl[l]) * (R - h_kl[l]);
+        }
+        *h_sigma_rms = den > 0.0 ? sqrt(num / den) : 0.0;
+    }
     return SK_OK;
 }
