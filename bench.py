@@ -151,6 +151,11 @@ class ClockSampler:
 # our arm
 # --------------------------------------------------------------------------
 
+def gaussian_beam_of(ks, lmax):
+    from inputs import gaussian_beam
+    return gaussian_beam(ks.fwhm_arcmin, lmax)
+
+
 def build_operator(sk, ctx, group):
     ks = group.kernel
     g = sk.Geometry(ctx, group.nside)
@@ -362,9 +367,19 @@ def run_ours(args):
         ns = max(3, min(args.steps, 10))
         ms_h = time_steps(torch, lambda: h.apply(o["x"], out=yh), ns, 2, barrier)
         ms_s = time_steps(torch, lambda: sk.split_convolve(o["kern"], h, o["x"], out=yh), ns, 2, barrier)
+        # Eq. 2's error of this split (the high-pass-and-truncate table of the workload) and of
+        # the least-squares real-space part on the same cut, both relative to K_l up to 2 l_max
+        lfit = 2 * ks.lmax
+        kl2 = gaussian_beam_of(ks, lfit)
+        R2 = sk.kernel_response(o["kern"], lfit)
+        ell = np.arange(lfit + 1)
+        sig_trunc = math.sqrt(float(np.sum((2 * ell[ks.lcut + 1:] + 1) * (R2[ks.lcut + 1:] - kl2[ks.lcut + 1:]) ** 2))
+                              / float(np.sum((2 * ell + 1) * kl2 ** 2)))
+        _, sig_fit = sk.fit_real_kernel(ctx, kl2, ks.lcut, ks.theta_cut, n_basis=257, lfit=lfit)
         split = {"l_cut": ks.lcut, "harmonic_ms_per_map": ms_h, "split_ms_per_map": ms_s,
                  "real_space_ms_per_map": ms / maps_step, "lambda_table_gb": h.table_bytes() / 1e9,
-                 "harmonic_setup_s": t_create}
+                 "harmonic_setup_s": t_create, "sigma_rms_eq2_table": sig_trunc,
+                 "sigma_rms_eq2_least_squares": sig_fit}
         del h, yh
 
     o0 = ops[0]

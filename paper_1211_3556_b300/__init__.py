@@ -442,6 +442,51 @@ def split_convolve(kern: Kernel, harm: Harmonic, x, out=None, stream=None):
     return y
 
 
+def plan_split(ctx: Context, geom: Geometry, k_ell, target_sigma: float, lcut_options, theta_cut_options,
+               alpha: float = 5.0, n_basis: int = 257, lfit: int = None, reps: int = 3):
+    """Choose (l_cut, theta_cut) for the split of K_l like the paper's optimiser
+    (Sec. 2 and 4: the cheapest split whose Eq. 2 error meets the target), with
+    measured costs instead of cost models: for every candidate the real-space part
+    is fitted (fit_real_kernel), its error taken as alpha * sigma_rms (Eq. 2), and
+    the whole split timed on this GPU (real-space sum with the fitted table plus
+    the harmonic part with K^_l = K_l - R_l) on a white-noise map.  Returns
+    (best, rows): best is the fastest row meeting the target (None if none does);
+    a row is a dict with lcut, theta_cut, sigma, ms_real, ms_harmonic, ms_total."""
+    import torch
+    kl = np.asarray(k_ell, dtype=np.float64)
+    lfit = len(kl) - 1 if lfit is None else int(lfit)
+    npix = geom.npix
+    x = torch.randn(1, npix, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    y = torch.empty_like(x)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    for lcut in lcut_options:
+        for tc in theta_cut_options:
+            V, sig = fit_real_kernel(ctx, kl, lcut, tc, n_basis=n_basis, lfit=lfit)
+            kern = Kernel(geom, V, tc)
+            R = kernel_response(kern, lcut)
+            harm = Harmonic(ctx, geom, kl[: lcut + 1] - R, lcut)
+            ms_r = timed(lambda: convolve(kern, x, out=y))
+            ms_h = timed(lambda: harm.apply(x, out=y, accumulate=True))
+            rows.append(dict(lcut=int(lcut), theta_cut=float(tc), sigma=alpha * sig, ms_real=ms_r,
+                             ms_harmonic=ms_h, ms_total=ms_r + ms_h))
+            del harm, kern
+    ok = [r for r in rows if r["sigma"] <= target_sigma]
+    best = min(ok, key=lambda r: r["ms_total"]) if ok else None
+    return best, rows
+
+
 class Graph:
     """A CUDA graph of convolve_jobs(jobs) on fixed buffers."""
 

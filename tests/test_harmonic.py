@@ -151,3 +151,45 @@ def test_harmonic_argument_errors(sk):
     with pytest.raises(sk.SkError):
         h.apply(x, out=x)                                  # aliasing
     assert h.table_bytes() == 4 * (8 * 9 // 2) * 8
+
+
+# ------------------------------------------------ least-squares real-space part
+
+@pytest.mark.parametrize("fwhm,tcf,lcut,lfit,nb", [(60.0, 3.0, 96, 384, 129), (7.1, 2.8, 1024, 4096, 257)])
+def test_fit_matches_oracle(sk, fwhm, tcf, lcut, lfit, nb):
+    # Cholesky of the normal equations (library) vs lstsq (oracle) on the same
+    # objective: the same Eq. 2 residual, and tables with the same response above l_cut
+    tc = tcf * fwhm * ARCMIN
+    kl = gaussian_beam(fwhm, lfit)
+    nt = 4 * (nb - 1) + 1
+    V, sig = sk.fit_real_kernel(sk._hctx, kl, lcut, tc, n_basis=nb, nt_out=nt, lfit=lfit)
+    Vo, sigo = O.fit_real_kernel(kl, lcut, lfit, tc, nb, nt)
+    assert abs(sig - sigo) <= 1e-3 * sigo + 1e-12
+    R = O.kernel_response(V, tc, 0, lfit)
+    Ro = O.kernel_response(Vo, tc, 0, lfit)
+    ell = np.arange(lcut + 1, lfit + 1)
+    w = 2 * ell + 1
+    den = math.sqrt(np.sum((2 * np.arange(lfit + 1) + 1) * kl ** 2))
+    assert math.sqrt(np.sum(w * (R[lcut + 1:] - Ro[lcut + 1:]) ** 2)) <= 1e-6 * den
+
+
+def test_fit_planted_response(sk):
+    nb, tc, lcut, lfit = 33, 0.3, 10, 120
+    M = O.hat_response_matrix(nb, tc, 0, lfit)
+    kl = M @ (10.0 * np.sin(np.linspace(0.0, 3.0, nb - 1)))
+    V, sig = sk.fit_real_kernel(sk._hctx, kl, lcut, tc, n_basis=nb, nt_out=nb, lfit=lfit)
+    assert sig < 1e-6
+
+
+def test_plan_split_picks_the_fastest_feasible_candidate(sk):
+    nside = 32
+    g = sk.Geometry(sk._hctx, nside)
+    kl = gaussian_beam(300.0, 4 * nside)
+    best, rows = sk.plan_split(sk._hctx, g, kl, 1e-2, [16, 24], [600.0 * ARCMIN, 900.0 * ARCMIN],
+                               n_basis=65, reps=2)
+    assert len(rows) == 4
+    ok = [r for r in rows if r["sigma"] <= 1e-2]
+    assert ok and best is not None
+    assert best["ms_total"] == min(r["ms_total"] for r in ok)
+    for r in rows:
+        assert r["ms_real"] > 0 and r["ms_harmonic"] > 0
