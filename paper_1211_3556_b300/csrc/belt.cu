@@ -185,6 +185,14 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
     __syncthreads();
 
     uint32_t gs = 0;        // strips issued/consumed so far (stage and phase)
+    // One stage layout for every job of the launch (jobs may differ in WPM): a stage
+    // is sized for the widest job, so that stage s has the same bytes whichever job's
+    // strip it holds (the full/empty barriers guard stage indices, not byte ranges).
+    int wpm_max = 0;
+    for (int j = 0; j < A.n_jobs; ++j) wpm_max = max(wpm_max, A.j[j].WPM);
+    const int slot = (TS + wpm_max + 4 + 8 + 3) & ~3;               // strip floats
+    const uint32_t wmax = (uint32_t)(NW * wpm_max * 8);             // pair-row bytes of a stage
+    const uint32_t stage = (uint32_t)slot * 4u + wmax + NW * 8u;
 
     for (int f = blockIdx.x; f < A.total; f += gridDim.x) {
         if (*abort_flag) break;
@@ -196,10 +204,8 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
         const int j0 = it.y * TS;
         const int2 gr = J.bgrp[grp];
         const int nstrips = gr.y - gr.x + 1;
-        const int L = TS + J.WPM + 4;
-        const int slot = (L + 8 + 3) & ~3;                          // strip floats
+        const int L = TS + J.WPM + 4;                               // strip values this job copies
         const uint32_t wbytes = (uint32_t)(NW * J.WPM * 8);         // pair rows of one strip
-        const uint32_t stage = (uint32_t)slot * 4u + wbytes + NW * 8u;
         unsigned char *stage0 = smem + HDR;
         const long long js = (long long)j0 + J.EMIN;
         const int phase = (int)(((js % 4) + 4) % 4);
@@ -241,7 +247,7 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                     }
                     const size_t row = wrow0 + (size_t)i * NW;
                     bulk_g2s(dst0 + (uint32_t)slot * 4u, J.bwp + row * J.WPM, wbytes, full0 + 8 * s);
-                    bulk_g2s(dst0 + (uint32_t)slot * 4u + wbytes, J.bpr + row, NW * 8u, full0 + 8 * s);
+                    bulk_g2s(dst0 + (uint32_t)slot * 4u + wmax, J.bpr + row, NW * 8u, full0 + 8 * s);
                 }
             }
         } else {
@@ -258,7 +264,7 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                 const int s = (int)(g % S);
                 if (!mbar_wait(full0 + 8 * s, (g / S) & 1, abort_flag, A.status)) { ok = false; break; }
                 const unsigned char *sb = stage0 + (size_t)s * stage;
-                const int2 r = reinterpret_cast<const int2 *>(sb + (size_t)slot * 4 + wbytes)[warp];
+                const int2 r = reinterpret_cast<const int2 *>(sb + (size_t)slot * 4 + wmax)[warp];
                 const float4 *wr = reinterpret_cast<const float4 *>(sb + (size_t)slot * 4) + warp * (J.WPM / 2);
                 const float *xs = reinterpret_cast<const float *>(sb) + phase + lane * P + r.x;
                 // Strip values x[m] = xs[m] in a register ring of XB slots (slot m mod XB),

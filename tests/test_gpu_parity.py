@@ -171,6 +171,68 @@ def test_config_n2048_sampled_outputs(sk):
     assert rms_rel(y[outs], yo) <= RMS_BOUND
 
 
+def test_config_n8192_sampled_outputs(sk):
+    # the largest workload (Nside 8192, 16384 nodes, 3.2 GB per map) in bench.py's
+    # launch configuration, on sampled outputs
+    grp = WORKLOADS["n8192_plain"].groups[0]
+    ks = grp.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    g = sk.Geometry(sk._ctx, grp.nside)
+    k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+    x = white_noise_maps(grp.nside, 1, grp.seed)
+    y = gpu_conv(sk, k, x)[0]
+    outs = np.concatenate([sample_indices(x.shape[1], 5000, 503), _special_pixels(grp.nside)])
+    yo = O.conv_window(grp.nside, V, ks.theta_cut, ks.layout, x[0].astype(np.float64), outs)
+    assert rms_rel(y[outs], yo) <= RMS_BOUND
+
+
+def test_config_mixed_batch_sampled_outputs(sk):
+    # the uneven batch (8 x Nside 256, 8 x 512, 4 x 1024, 2 x 2048, four kernels) in one
+    # convolve_jobs call, every map checked on sampled outputs
+    import torch
+    wl = WORKLOADS["mixed_batch"]
+    jobs, keep = [], []
+    for grp in wl.groups:
+        ks = grp.kernel
+        V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+        g = sk.Geometry(sk._ctx, grp.nside)
+        k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+        x = white_noise_maps(grp.nside, grp.batch, grp.seed)
+        xt = torch.from_numpy(x).cuda()
+        yt = torch.empty_like(xt)
+        jobs.append((k, xt, yt))
+        keep.append((grp, V, x, g))
+    sk.convolve_jobs(sk._ctx, jobs)
+    torch.cuda.synchronize()
+    sk._ctx.status()
+    for (grp, V, x, g), (k, xt, yt) in zip(keep, jobs):
+        ks = grp.kernel
+        y = yt.cpu().numpy()
+        for b in range(grp.batch):
+            outs = sample_indices(x.shape[1], 1500, 610 + b)
+            yo = O.conv_window(grp.nside, V, ks.theta_cut, ks.layout, x[b].astype(np.float64), outs)
+            assert rms_rel(y[b, outs], yo) <= RMS_BOUND
+
+
+def test_config_grad_full_size_euler_identity(sk):
+    # y is linear in the node values, so for L = <gy, y> with gy held fixed,
+    # sum_n V_n dL/dV_n = <gy, y>; with gy = y the right side is |y|^2 (no
+    # cancellation), and a node shift or a lost term moves the left side by ~1e-3
+    import torch
+    grp = WORKLOADS["n1024x16_grad"].groups[0]
+    ks = grp.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    g = sk.Geometry(sk._ctx, grp.nside)
+    k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+    x = torch.from_numpy(white_noise_maps(grp.nside, grp.batch, grp.seed)).cuda()
+    y = sk.convolve(k, x)
+    gt = sk.grad_table(k, x, y)
+    torch.cuda.synchronize()
+    lhs = float(np.dot(V, gt.cpu().numpy().astype(np.float64)))
+    rhs = float((y.double() * y.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * rhs
+
+
 # ------------------------------------------------------------------ batch, adjoint
 
 def test_batch_equals_single_maps(sk):
