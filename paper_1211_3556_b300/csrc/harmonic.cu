@@ -52,12 +52,17 @@ struct sk_harm {
     bool plans = false;
     float2 *d_X = nullptr;       // [(2N+1)][2N+1] bins of one map
     float *d_tmp = nullptr;      // [(2N+1) * 4N] synthesised zone of one map
+    // twiddles and ring phases, FP64-accurate, stored FP32 (built once per handle)
+    float2 *d_tw = nullptr;      // cap ring of 4r pixels: e^{-2 pi i k / 4r} at [2r(r-1) + k]
+    float2 *d_ph = nullptr;      // cap ring r: e^{-i pi m / 4r} at [(r-1)(L+1) + m]
+    float2 *d_zph = nullptr;     // rings of 4N pixels with s = 1: e^{-i pi m / 4N}, m = 0..L
 };
 
 namespace {
 
 constexpr int HT = 256;
-constexpr int RESYNC = 32;     // ring DFTs: exact twiddle every RESYNC rotations
+constexpr int RESYNC = 32;     // ring DFTs: Horner blocks of RESYNC terms, exact twiddle per block
+constexpr int CH = 4;          // ring DFTs: independent chains per thread
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -104,11 +109,40 @@ __global__ void k_lambda(const double *theta, const double *lg2c, const long lon
     }
 }
 
+// Twiddle and phase tables of the ring DFTs (FP64 sincospi, stored FP32).
+__global__ void k_ring_tables(int nside, int L, float2 *tw, float2 *ph, float2 *zph) {
+    const long long ntw = 2LL * nside * (nside - 1);               // sum of 4r, r < N
+    const long long nph = (long long)(nside - 1) * (L + 1);
+    const long long tot = ntw + nph + (L + 1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        double sn, cs;
+        if (i < ntw) {
+            // ring r (1-based) owns [2r(r-1), 2r(r+1)): solve 2r(r-1) <= i
+            long long r = (long long)((1.0 + sqrt(1.0 + 2.0 * (double)i)) * 0.5);
+            while (2 * r * (r - 1) > i) --r;
+            while (2 * (r + 1) * r <= i) ++r;
+            const long long k = i - 2 * r * (r - 1);
+            sincospi(2.0 * (double)k / (double)(4 * r), &sn, &cs);
+            tw[i] = make_float2((float)cs, (float)-sn);
+        } else if (i < ntw + nph) {
+            const long long j = i - ntw;
+            const long long r = j / (L + 1) + 1, m = j % (L + 1);
+            sincospi(-(double)m / (double)(4 * r), &sn, &cs);
+            ph[j] = make_float2((float)cs, (float)sn);
+        } else {
+            const long long m = i - ntw - nph;
+            sincospi(-(double)m / (double)(4 * nside), &sn, &cs);
+            zph[m] = make_float2((float)cs, (float)sn);
+        }
+    }
+}
+
 // Polar-cap rings: F_r(m) = e^{-i pi m s / n} sum_j x_j e^{-2 pi i m j / n}, m = 0..L.
 // One block per (cap ring, map); cap ring c < N - 1 is 0-based ring c, else its
 // southern mirror.  Twiddles w_k = e^{-2 pi i k / n} in shared memory.
 __global__ void k_dft_cap(const RingDev *rings, int nside, const float *x, long long stride, int L,
-                          int nr, float2 *F) {
+                          int nr, const float2 *twg, const float2 *phg, float2 *F) {
     extern __shared__ float2 sh[];
     const int ncap = nside - 1;
     const int c = blockIdx.x, b = blockIdx.y;
@@ -118,52 +152,71 @@ __global__ void k_dft_cap(const RingDev *rings, int nside, const float *x, long 
     float2 *tw = sh;
     float *xs = reinterpret_cast<float *>(sh + n);
     const float *xr = x + (long long)b * stride + R.start;
+    const int r1 = n / 4;                            // cap ring of 4 r1 pixels (shift 1)
+    const float2 *twr = twg + 2LL * r1 * (r1 - 1);
+    const float2 *phr = phg + (long long)(r1 - 1) * (L + 1);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        double sn, cs;
-        sincospi(2.0 * k / n, &sn, &cs);
-        tw[k] = make_float2((float)cs, (float)-sn);
+        tw[k] = twr[k];
         xs[k] = xr[k];
     }
     __syncthreads();
     float2 *Fr = F + ((long long)b * nr + r) * (L + 1);
-    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        // w = e^{-2 pi i m j / n}: rotated by w_m per pixel, reset from the exact table
-        // every RESYNC pixels (rounding of the rotation stays below ~RESYNC ulp)
-        const int step = m % n;
-        const float2 rot = tw[step];
-        float re = 0.0f, im = 0.0f;
-        int idx = 0;
-        for (int j0 = 0; j0 < n; j0 += RESYNC) {
-            float2 w = tw[idx];
-            const int j1 = min(j0 + RESYNC, n);
-            for (int j = j0; j < j1; ++j) {
-                const float xv = xs[j];
-                re = fmaf(xv, w.x, re);
-                im = fmaf(xv, w.y, im);
-                const float wx = w.x * rot.x - w.y * rot.y;
-                w.y = w.x * rot.y + w.y * rot.x;
-                w.x = wx;
-            }
-            idx = (int)(((long long)step * j1) % n);
+    // CH multipoles per thread, their Horner chains interleaved (independent, one load of x_j each)
+    for (int mb = threadIdx.x; mb <= L; mb += CH * blockDim.x) {
+        // blocks of RESYNC pixels: S_b = sum_t x_{j0+t} w^t by Horner's rule (w = e^{-2 pi i m / n},
+        // rounding grows with the block length only), F += w^{j0} S_b with w^{j0} exact
+        int step[CH];
+        float2 rot[CH];
+        float re[CH], im[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int m = min(mb + c * (int)blockDim.x, L);
+            step[c] = m % n;
+            rot[c] = tw[step[c]];
+            re[c] = 0.0f;
+            im[c] = 0.0f;
         }
-        double sn, cs;
-        sincospi(-(double)m * R.s / n, &sn, &cs);
-        Fr[m] = cmulf(make_float2(re, im), make_float2((float)cs, (float)sn));
+        for (int j0 = 0; j0 < n; j0 += RESYNC) {
+            const int j1 = min(j0 + RESYNC, n);
+            float hr[CH], hi[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) { hr[c] = xs[j1 - 1]; hi[c] = 0.0f; }
+            for (int j = j1 - 2; j >= j0; --j) {
+                const float xv = xs[j];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const float nr = fmaf(hr[c], rot[c].x, fmaf(-hi[c], rot[c].y, xv));
+                    hi[c] = fmaf(hr[c], rot[c].y, hi[c] * rot[c].x);
+                    hr[c] = nr;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float2 w0 = tw[(int)(((long long)step[c] * j0) % n)];
+                re[c] = fmaf(hr[c], w0.x, fmaf(-hi[c], w0.y, re[c]));
+                im[c] = fmaf(hr[c], w0.y, fmaf(hi[c], w0.x, im[c]));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int m = mb + c * (int)blockDim.x;
+            if (m > L) continue;
+            Fr[m] = cmulf(make_float2(re[c], im[c]), phr[m]);
+        }
     }
 }
 
 // Equatorial zone after the R2C: F_r(m) = e^{-i pi m s / n} X_r(m), m = 0..L.
 __global__ void k_zone_in(const RingDev *rings, int nside, const float2 *X, int L, int nr, long long b,
-                          float2 *F) {
+                          const float2 *zph, float2 *F) {
     const int zr = blockIdx.x;                       // 0 .. 2N
     const int r = nside - 1 + zr;
-    const int n = 4 * nside, nb = 2 * nside + 1;
+    const int nb = 2 * nside + 1;
     const int s = rings[r].s;
     float2 *Fr = F + (b * nr + r) * (L + 1);
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        double sn, cs;
-        sincospi(-(double)m * s / n, &sn, &cs);
-        Fr[m] = cmulf(X[(long long)zr * nb + m], make_float2((float)cs, (float)sn));
+        const float2 v = X[(long long)zr * nb + m];
+        Fr[m] = s ? cmulf(v, zph[m]) : v;
     }
 }
 
@@ -261,7 +314,7 @@ __global__ void k_leg_synthesis(const float *lam, const long long *moff, const l
 
 // Polar-cap rings: y_j (+)= Re G(0) + 2 Re sum_{m=1}^{L} G(m) e^{i pi m (2j + s) / n}.
 __global__ void k_idft_cap(const RingDev *rings, int nside, const float2 *G, int L, int nr, float *y,
-                           long long stride, int accumulate) {
+                           long long stride, int accumulate, const float2 *twg, const float2 *phg) {
     extern __shared__ float2 sh[];
     const int ncap = nside - 1;
     const int c = blockIdx.x, b = blockIdx.y;
@@ -271,57 +324,76 @@ __global__ void k_idft_cap(const RingDev *rings, int nside, const float2 *G, int
     float2 *tw = sh;                                 // e^{+2 pi i k / n}
     float2 *gs = sh + n;                             // G(m) e^{i pi m s / n}, doubled for m >= 1
     const float2 *Gr = G + ((long long)b * nr + r) * (L + 1);
+    const int r1 = n / 4;                            // cap ring of 4 r1 pixels (shift 1)
+    const float2 *twr = twg + 2LL * r1 * (r1 - 1);
+    const float2 *phr = phg + (long long)(r1 - 1) * (L + 1);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        double sn, cs;
-        sincospi(2.0 * k / n, &sn, &cs);
-        tw[k] = make_float2((float)cs, (float)sn);
+        const float2 w = twr[k];
+        tw[k] = make_float2(w.x, -w.y);              // e^{+2 pi i k / n}
     }
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        double sn, cs;
-        sincospi((double)m * R.s / n, &sn, &cs);
-        float2 v = cmulf(Gr[m], make_float2((float)cs, (float)sn));
+        const float2 p = phr[m];
+        float2 v = cmulf(Gr[m], make_float2(p.x, -p.y));   // G(m) e^{+i pi m / n}
         if (m > 0) { v.x *= 2.0f; v.y *= 2.0f; }
         gs[m] = v;
     }
     __syncthreads();
     float *yr = y + (long long)b * stride + R.start;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        // w = e^{2 pi i m j / n}: rotated by w_j per multipole, reset every RESYNC
-        const int step = j % n;
-        const float2 rot = tw[step];
-        float acc = 0.0f;
-        int idx = 0;
-        for (int m0 = 0; m0 <= L; m0 += RESYNC) {
-            float2 w = tw[idx];
-            const int m1 = min(m0 + RESYNC, L + 1);
-            for (int m = m0; m < m1; ++m) {
-                const float2 g = gs[m];
-                acc = fmaf(g.x, w.x, acc);
-                acc = fmaf(-g.y, w.y, acc);
-                const float wx = w.x * rot.x - w.y * rot.y;
-                w.y = w.x * rot.y + w.y * rot.x;
-                w.x = wx;
-            }
-            idx = (int)(((long long)step * m1) % n);
+    // CH pixels per thread, their Horner chains interleaved (one load of g_m each)
+    for (int jb = threadIdx.x; jb < n; jb += CH * blockDim.x) {
+        // blocks of RESYNC multipoles: S_b = sum_t g_{m0+t} w^t by Horner's rule
+        // (w = e^{2 pi i j / n}), y += Re(w^{m0} S_b) with w^{m0} exact
+        int step[CH];
+        float2 rot[CH];
+        float acc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int j = min(jb + c * (int)blockDim.x, n - 1);
+            step[c] = j;
+            rot[c] = tw[j];
+            acc[c] = 0.0f;
         }
-        yr[j] = accumulate ? yr[j] + acc : acc;
+        for (int m0 = 0; m0 <= L; m0 += RESYNC) {
+            const int m1 = min(m0 + RESYNC, L + 1);
+            float2 h[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) h[c] = gs[m1 - 1];
+            for (int m = m1 - 2; m >= m0; --m) {
+                const float2 g = gs[m];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const float nr = fmaf(h[c].x, rot[c].x, fmaf(-h[c].y, rot[c].y, g.x));
+                    h[c].y = fmaf(h[c].x, rot[c].y, fmaf(h[c].y, rot[c].x, g.y));
+                    h[c].x = nr;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float2 w0 = tw[(int)(((long long)step[c] * m0) % n)];
+                acc[c] = fmaf(h[c].x, w0.x, fmaf(-h[c].y, w0.y, acc[c]));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int j = jb + c * (int)blockDim.x;
+            if (j >= n) continue;
+            yr[j] = accumulate ? yr[j] + acc[c] : acc[c];
+        }
     }
 }
 
 // Equatorial zone before the C2R: bins X_r(m) = G_r(m) e^{i pi m s / n} for m <= L, 0 above.
 __global__ void k_zone_out(const RingDev *rings, int nside, const float2 *G, int L, int nr, long long b,
-                           float2 *X) {
+                           const float2 *zph, float2 *X) {
     const int zr = blockIdx.x;
     const int r = nside - 1 + zr;
-    const int n = 4 * nside, nb = 2 * nside + 1;
+    const int nb = 2 * nside + 1;
     const int s = rings[r].s;
     const float2 *Gr = G + (b * nr + r) * (L + 1);
     for (int m = threadIdx.x; m < nb; m += blockDim.x) {
         float2 v = make_float2(0.0f, 0.0f);
         if (m <= L) {
-            double sn, cs;
-            sincospi((double)m * s / n, &sn, &cs);
-            v = cmulf(Gr[m], make_float2((float)cs, (float)sn));
+            v = s ? cmulf(Gr[m], make_float2(zph[m].x, -zph[m].y)) : Gr[m];
             if (m == 0) v.y = 0.0f;
         }
         X[(long long)zr * nb + m] = v;
@@ -451,6 +523,7 @@ void free_harm(sk_harm *h) {
     if (h->plans) { cufftDestroy(h->p_r2c); cufftDestroy(h->p_c2r); }
     cudaFree(h->d_kl); cudaFree(h->d_lam); cudaFree(h->d_moff); cudaFree(h->d_aoff);
     cudaFree(h->d_F); cudaFree(h->d_a); cudaFree(h->d_X); cudaFree(h->d_tmp);
+    cudaFree(h->d_tw); cudaFree(h->d_ph); cudaFree(h->d_zph);
     delete h;
 }
 
@@ -500,6 +573,16 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
     if (e == cudaSuccess) e = cudaMalloc(&d_lg2c, sizeof(double) * (L + 1));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_X, sizeof(float2) * (size_t)nb * nb);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_tmp, sizeof(float) * (size_t)nb * n4);
+    const long long ntw = 2LL * N * (N - 1), nph = (N - 1) * (long long)(L + 1);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_tw, sizeof(float2) * (size_t)std::max(1LL, ntw));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_ph, sizeof(float2) * (size_t)std::max(1LL, nph));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_zph, sizeof(float2) * (size_t)(L + 1));
+    if (e == cudaSuccess) {
+        const long long tot = ntw + nph + L + 1;
+        k_ring_tables<<<(unsigned)std::min<long long>((tot + HT - 1) / HT, 65535), HT>>>((int)N, L, h->d_tw, h->d_ph,
+                                                                                           h->d_zph);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpy(h->d_kl, kl, sizeof(double) * (L + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_moff, moff.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_aoff, aoff.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice);
@@ -570,14 +653,17 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
     if (ncap > 0) {
         const size_t sm = sizeof(float2) * 4 * (N - 1) + sizeof(float) * 4 * (N - 1);
         SK_CU(cudaFuncSetAttribute(k_dft_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_dft_cap<<<dim3(ncap, (unsigned)batch), HT, sm, st>>>(g->d_rings, N, d_in, map_stride, L, nr, h->d_F);
+        // enough threads that one pass of CH chains covers every multipole
+        const int thr = std::min(1024, ((L + CH) / CH + 31) / 32 * 32);
+        k_dft_cap<<<dim3(ncap, (unsigned)batch), thr, sm, st>>>(g->d_rings, N, d_in, map_stride, L, nr, h->d_tw,
+                                                                  h->d_ph, h->d_F);
         SK_CU(cudaGetLastError());
     }
     for (long long b = 0; b < batch; ++b) {
         cufftResult cr = cufftExecR2C(h->p_r2c, const_cast<float *>(d_in) + b * map_stride + zone0,
                                       reinterpret_cast<cufftComplex *>(h->d_X));
         if (cr != CUFFT_SUCCESS) return cufft_fail(cr, "sk_harmonic_apply");
-        k_zone_in<<<nb, HT, 0, st>>>(g->d_rings, N, h->d_X, L, nr, b, h->d_F);
+        k_zone_in<<<nb, HT, 0, st>>>(g->d_rings, N, h->d_X, L, nr, b, h->d_zph, h->d_F);
         SK_CU(cudaGetLastError());
     }
     // Legendre analysis and synthesis
@@ -594,11 +680,11 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
         const size_t sm = sizeof(float2) * 4 * (N - 1) + sizeof(float2) * (L + 1);
         SK_CU(cudaFuncSetAttribute(k_idft_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_idft_cap<<<dim3(ncap, (unsigned)batch), HT, sm, st>>>(g->d_rings, N, h->d_F, L, nr, d_out, map_stride,
-                                                                 accumulate);
+                                                                 accumulate, h->d_tw, h->d_ph);
         SK_CU(cudaGetLastError());
     }
     for (long long b = 0; b < batch; ++b) {
-        k_zone_out<<<nb, HT, 0, st>>>(g->d_rings, N, h->d_F, L, nr, b, h->d_X);
+        k_zone_out<<<nb, HT, 0, st>>>(g->d_rings, N, h->d_F, L, nr, b, h->d_zph, h->d_X);
         SK_CU(cudaGetLastError());
         cufftResult cr = cufftExecC2R(h->p_c2r, reinterpret_cast<cufftComplex *>(h->d_X), h->d_tmp);
         if (cr != CUFFT_SUCCESS) return cufft_fail(cr, "sk_harmonic_apply");
