@@ -242,22 +242,31 @@ __global__ void k_leg_analysis(const float *lam, const long long *moff, const lo
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const float *lm = lam + moff[m];
+    const int n4 = nrh >> 2;                          // rings in fours (nrh = 2 Nside, a multiple of 4)
     for (int l = m + warp; l <= L; l += nw) {
-        const float *row = lm + (long long)(l - m) * nrh;
-        const float2 *S = sEO + (((l + m) & 1) ? nrh : 0);
+        const float4 *row = reinterpret_cast<const float4 *>(lm + (long long)(l - m) * nrh);
+        const float4 *S = reinterpret_cast<const float4 *>(sEO + (((l + m) & 1) ? nrh : 0));
         float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;
-        int r = lane;
-        for (; r + 96 < nrh; r += 128) {             // four independent loads in flight per lane
-            const float w0 = row[r], w1 = row[r + 32], w2 = row[r + 64], w3 = row[r + 96];
-            re0 = fmaf(w0, S[r].x, re0); im0 = fmaf(w0, S[r].y, im0);
-            re1 = fmaf(w1, S[r + 32].x, re1); im1 = fmaf(w1, S[r + 32].y, im1);
-            re0 = fmaf(w2, S[r + 64].x, re0); im0 = fmaf(w2, S[r + 64].y, im0);
-            re1 = fmaf(w3, S[r + 96].x, re1); im1 = fmaf(w3, S[r + 96].y, im1);
+        int q = lane;
+        for (; q + 32 < n4; q += 64) {               // two 16-byte loads in flight per lane
+            const float4 w = row[q], v = row[q + 32];
+            const float4 s0 = S[2 * q], s1 = S[2 * q + 1], t0 = S[2 * (q + 32)], t1 = S[2 * (q + 32) + 1];
+            re0 = fmaf(w.x, s0.x, re0); im0 = fmaf(w.x, s0.y, im0);
+            re1 = fmaf(w.y, s0.z, re1); im1 = fmaf(w.y, s0.w, im1);
+            re0 = fmaf(w.z, s1.x, re0); im0 = fmaf(w.z, s1.y, im0);
+            re1 = fmaf(w.w, s1.z, re1); im1 = fmaf(w.w, s1.w, im1);
+            re0 = fmaf(v.x, t0.x, re0); im0 = fmaf(v.x, t0.y, im0);
+            re1 = fmaf(v.y, t0.z, re1); im1 = fmaf(v.y, t0.w, im1);
+            re0 = fmaf(v.z, t1.x, re0); im0 = fmaf(v.z, t1.y, im0);
+            re1 = fmaf(v.w, t1.z, re1); im1 = fmaf(v.w, t1.w, im1);
         }
-        for (; r < nrh; r += 32) {
-            const float w = row[r];
-            re0 = fmaf(w, S[r].x, re0);
-            im0 = fmaf(w, S[r].y, im0);
+        for (; q < n4; q += 32) {
+            const float4 w = row[q];
+            const float4 s0 = S[2 * q], s1 = S[2 * q + 1];
+            re0 = fmaf(w.x, s0.x, re0); im0 = fmaf(w.x, s0.y, im0);
+            re1 = fmaf(w.y, s0.z, re1); im1 = fmaf(w.y, s0.w, im1);
+            re0 = fmaf(w.z, s1.x, re0); im0 = fmaf(w.z, s1.y, im0);
+            re1 = fmaf(w.w, s1.z, re1); im1 = fmaf(w.w, s1.w, im1);
         }
         float re = re0 + re1, im = im0 + im1;
 #pragma unroll
@@ -268,10 +277,6 @@ __global__ void k_leg_analysis(const float *lam, const long long *moff, const lo
         if (lane == 0) a[(long long)b * a_n + aoff[m] + (l - m)] = make_float2(domega * re, domega * im);
     }
 }
-
-// Legendre synthesis: G_r(m) = sum_l K^_l a_lm lambda_lm(theta_r), split by the
-// parity of l + m into the northern ring and its mirror.  One block per (m, map),
-// threads along r.
 __global__ void k_leg_synthesis(const float *lam, const long long *moff, const long long *aoff, const double *kl,
                                 const float2 *a, int L, int nr, int nrh, long long a_n, float2 *G) {
     extern __shared__ float2 sb[];                   // b_l = K^_l a_lm, l = m..L
@@ -284,31 +289,35 @@ __global__ void k_leg_synthesis(const float *lam, const long long *moff, const l
     __syncthreads();
     const float *lm = lam + moff[m];
     float2 *Gb = G + (long long)b * nr * (L + 1);
-    for (int r = threadIdx.x; r < nrh; r += blockDim.x) {
-        float er = 0.0f, ei = 0.0f, orr = 0.0f, oi = 0.0f;
+    const int n4 = nrh >> 2;                          // rings in fours: one 16-byte load per l
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+        float er[4] = {}, ei[4] = {}, orr[4] = {}, oi[4] = {};
         int l = m;
-        for (; l + 1 <= L; l += 2) {                 // l + m even, then odd
-            const float w0 = lm[(long long)(l - m) * nrh + r];
-            const float w1 = lm[(long long)(l + 1 - m) * nrh + r];
+        for (; l + 1 <= L; l += 2) {                 // l - m even (l + m even), then odd
+            const float4 w0 = reinterpret_cast<const float4 *>(lm + (long long)(l - m) * nrh)[q];
+            const float4 w1 = reinterpret_cast<const float4 *>(lm + (long long)(l + 1 - m) * nrh)[q];
             const float2 b0 = sb[l - m], b1 = sb[l + 1 - m];
-            const bool even0 = ((l + m) & 1) == 0;
-            if (even0) {
-                er = fmaf(w0, b0.x, er); ei = fmaf(w0, b0.y, ei);
-                orr = fmaf(w1, b1.x, orr); oi = fmaf(w1, b1.y, oi);
-            } else {
-                orr = fmaf(w0, b0.x, orr); oi = fmaf(w0, b0.y, oi);
-                er = fmaf(w1, b1.x, er); ei = fmaf(w1, b1.y, ei);
+            const float a0[4] = {w0.x, w0.y, w0.z, w0.w}, a1[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                er[u] = fmaf(a0[u], b0.x, er[u]); ei[u] = fmaf(a0[u], b0.y, ei[u]);
+                orr[u] = fmaf(a1[u], b1.x, orr[u]); oi[u] = fmaf(a1[u], b1.y, oi[u]);
             }
         }
         if (l <= L) {
-            const float w0 = lm[(long long)(l - m) * nrh + r];
+            const float4 w0 = reinterpret_cast<const float4 *>(lm + (long long)(l - m) * nrh)[q];
             const float2 b0 = sb[l - m];
-            if (((l + m) & 1) == 0) { er = fmaf(w0, b0.x, er); ei = fmaf(w0, b0.y, ei); }
-            else { orr = fmaf(w0, b0.x, orr); oi = fmaf(w0, b0.y, oi); }
+            const float a0[4] = {w0.x, w0.y, w0.z, w0.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { er[u] = fmaf(a0[u], b0.x, er[u]); ei[u] = fmaf(a0[u], b0.y, ei[u]); }
         }
-        const int rs = nr - 1 - r;
-        Gb[(long long)r * (L + 1) + m] = make_float2(er + orr, ei + oi);
-        if (rs != r) Gb[(long long)rs * (L + 1) + m] = make_float2(er - orr, ei - oi);
+        // (l + m) has the parity of (l - m): the first of each pair is even
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = 4 * q + u, rs = nr - 1 - r;
+            Gb[(long long)r * (L + 1) + m] = make_float2(er[u] + orr[u], ei[u] + oi[u]);
+            if (rs != r) Gb[(long long)rs * (L + 1) + m] = make_float2(er[u] - orr[u], ei[u] - oi[u]);
+        }
     }
 }
 
