@@ -186,8 +186,13 @@ int sk_grad_table_noalloc(sk_ctx *ctx, const sk_kern *k, const float *d_x, const
 
 /* End-to-end convolution from and to host memory: copies `batch` maps from
  * h_in to the context workspace, convolves, copies the result to h_out, and
- * synchronises `stream`.  h_in/h_out: [batch][map_stride] FP32 host buffers.
- * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+ * synchronises `stream`.  h_in/h_out: [batch][map_stride] FP32 host buffers
+ * (page-locked memory lets the copies overlap the sums).  The maps move in 16
+ * ring bands ordered by distance from the poles: the sums of a band start once
+ * the bands its windows reach have arrived, and a band's outputs go back once
+ * the sums writing them are done, on two copy streams of the context beside
+ * `stream`.  Same results, bit for bit, as sk_convolve on device buffers.
+ * Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in, float *h_out,
                      int64_t batch, int64_t map_stride, void *stream);
 
