@@ -442,7 +442,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     O.conv_window(group.nside, V, ks.theta_cut, ks.layout, x, probe)
     dt = max(time.perf_counter() - t0, 1e-3)
-    per_step_s = max(1.0, 150.0 / (args.steps + args.warmup))
+    per_step_s = max(0.2, 150.0 / (args.steps + args.warmup))   # whole run about 150 s of oracle work
     n = int(min(npx, max(1000, 1000 * per_step_s / dt)))
     samples = [sample_indices(npx, n, 8100 + s) for s in range(args.warmup + args.steps)]
     for s in range(args.warmup):
