@@ -148,7 +148,14 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
     __syncthreads();
     const int half = threadIdx.x / NTH, t = threadIdx.x % NTH;
     float4 *const sbuf = sx + half * NB * 4 * LS;
-    for (int f = blockIdx.x * HALVES + half; f < A.total; f += gridDim.x * HALVES) {
+    // work queue: each half takes the next item (items are ordered heaviest first), so the
+    // halves that drew light items take more of them and all finish together
+    __shared__ int s_item[HALVES];
+    for (;;) {
+        if (t == 0) s_item[half] = atomicAdd(A.queue, 1);
+        half_sync(half);
+        const int f = s_item[half];
+        if (f >= A.total) break;
         const JobDesc &J = A.j[sk_find_job(A, f)];
         const int local = f - J.flat_base;
         const int map = local / J.n_items;

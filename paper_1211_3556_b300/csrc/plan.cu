@@ -587,6 +587,10 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                     cudaEvent_t ev = sk_prof_begin(ctx, cs);
                     // a block works on SK_CAP_ITEMS_PER_BLOCK items at a time
                     const int blocks = (b.a.total + SK_CAP_ITEMS_PER_BLOCK - 1) / SK_CAP_ITEMS_PER_BLOCK;
+                    int *q = ctx->d_queue + ctx->next_queue;
+                    ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
+                    SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));
+                    b.a.queue = q;
                     SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(blocks, per, ctx->num_sms), cs));
                     sk_prof_end(ctx, v ? "conv_cap" : "conv_cap_polar", ev, cs);
                 }

@@ -16,6 +16,11 @@ struct sk_ctx {
     int device = 0;
     int num_sms = 0;
     int *d_status = nullptr;       // device status word
+    // work-queue counters of the cap launches (one per launch in flight, reused in turn;
+    // each is zeroed on the launch's stream right before it)
+    static constexpr int NQUEUE = 64;
+    int *d_queue = nullptr;
+    int next_queue = 0;
     void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
     size_t ws_bytes = 0;
     // side stream for the small launches that overlap the large ones (polar caps,

@@ -59,6 +59,7 @@ struct JobsArg {
     int n_jobs;
     int total;            // flat items over all jobs
     int *status;          // device status word
+    int *queue;           // work-queue counter (zero at launch) of kernels that take items dynamically
     JobDesc j[SK_MAXJ];
 };
 
