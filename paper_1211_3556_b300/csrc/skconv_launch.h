@@ -110,7 +110,7 @@ cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cud
 int sk_belt_blocks_per_sm(const JobsArg &a, int P);
 int sk_cap_blocks_per_sm(int ls, int mode, int nt);
 constexpr int SK_CAP_LS_CLASSES = 3;
-constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {320, 640, 1280};  // strip rows of the cap path (float2)
+constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {320, 640, 1280};  // strip positions per row of the cap path (float4)
 constexpr int SK_CAP_CT = 256;         // base output pixels per cap work item (two per thread)
 constexpr int SK_CAP_ITEMS_PER_BLOCK = 2;   // cap work items a block holds at a time (one node table)
 
