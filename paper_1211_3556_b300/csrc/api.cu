@@ -564,8 +564,6 @@ extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in
     if (rc) return rc;
     float *d_in = (float *)ws, *d_out = (float *)((char *)ws + half);
     void *wsj = (char *)ws + 2 * half;
-    sk_kern *km = const_cast<sk_kern *>(k);
-    if ((rc = sk_plan_bands(km))) return rc;
     if (k->bands.empty()) {                      // no plan (general path only): one block of work
         jb.x = d_in;
         jb.y = d_out;

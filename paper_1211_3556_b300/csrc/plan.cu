@@ -105,7 +105,10 @@ int sk_plan_rebuild_belt_items(sk_kern *k) {
         for (int s = 0; s < nseg; ++s) it.push_back(make_int4(g, s, 0, 0));
     k->n_items_belt = (int)it.size();
     k->h_items_belt = it;
-    return upload(it, &k->d_items_belt);
+    if (int rc = upload(it, &k->d_items_belt)) return rc;
+    // the band partition of the host-buffer path holds belt items: rebuild it (a no-op
+    // before the first plan is complete)
+    return k->plan_ok ? sk_plan_bands(k) : SK_OK;
 }
 
 int sk_plan_build(sk_kern *k) {
@@ -287,7 +290,7 @@ int sk_plan_build(sk_kern *k) {
     int rc = upload(gen, &k->d_items_gen);
     if (rc) return rc;
     k->plan_ok = true;
-    return SK_OK;
+    return sk_plan_bands(k);
 }
 
 int sk_plan_bands(sk_kern *k) {
