@@ -14,7 +14,7 @@ constexpr int SK_MAXJ = 16;            // jobs per launch (more: several launche
 constexpr int SK_MAX_NODES = 16384;    // largest kernel table
 constexpr int SK_BELT_G = 16;          // output rings per belt block (two per consumer warp)
 constexpr int SK_BELT_WARPS = SK_BELT_G / 2;   // consumer warps per belt block
-constexpr int SK_BELT_STAGES = 16;     // input-ring strips in flight per belt block
+constexpr int SK_BELT_STAGES = 20;     // input-ring strips in flight per belt block
 
 struct JobDesc {
     // operator
