@@ -63,12 +63,14 @@ extern "C" int sk_create(sk_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sym, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaFree(c->d_status);
         cudaFree(c->d_queue);
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         if (c->ev_join) cudaEventDestroy(c->ev_join);
+        if (c->ev_sym) cudaEventDestroy(c->ev_sym);
         delete c;
         return sk_fail(SK_ECUDA, "sk_create: %s", cudaGetErrorString(e));
     }
@@ -93,6 +95,7 @@ extern "C" int sk_destroy(sk_ctx *ctx) {
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_sym) cudaEventDestroy(ctx->ev_sym);
     delete ctx;
     return SK_OK;
 }
@@ -559,8 +562,11 @@ extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in
     const size_t bytes = (size_t)batch * map_stride * sizeof(float);
     const size_t half = (bytes + 255) & ~(size_t)255;
     SkJob jb{k, nullptr, nullptr, batch, map_stride};
+    // the band runs below convolve one map at a time: their workspace is that of one map
+    SkJob one = jb;
+    one.batch = 1;
     void *ws = nullptr;
-    int rc = sk_ctx_workspace(ctx, 2 * half + sk_jobs_workspace_bytes(&jb, 1), &ws);
+    int rc = sk_ctx_workspace(ctx, 2 * half + sk_jobs_workspace_bytes(&one, 1), &ws);
     if (rc) return rc;
     float *d_in = (float *)ws, *d_out = (float *)((char *)ws + half);
     void *wsj = (char *)ws + 2 * half;

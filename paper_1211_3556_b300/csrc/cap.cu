@@ -16,46 +16,68 @@
 // output is written twice.  Same operator as the per-pair path (Sec. 2, Eq. 1
 // with the tabulated kernel of Sec. 3); only the order of work differs.
 //
+// Symmetric copy of the input (k_cap_sym, once per call): for every ring r the
+// caps read, H_r[a] = (x_r[a], x_r[a + n/2], x_m[a], x_m[a + n/2]) with m the
+// mirror ring, stored even pixels first, then odd ones.  One float4 of H holds a
+// pixel, its half turn and both mirrors, so the 16 images of a window pixel a
+// (base frame) are four float4: H[a], H[a + n/4] (the other two quarter turns),
+// H[b], H[b + n/4] with b = n/4 - s - a its reflection.
+//
 // Work item: (northern output ring, first base pixel) for CT base outputs,
 // CT / 2 threads, each owning two adjacent base outputs jA, jB = jA + 1; a
 // block runs two work items side by side (each half with its own named
 // barrier), so that they share one copy of the node table.  For every input
-// ring of the window a half stages 4 rows (quarter turns) of float4 (north
-// pixel, its reflection, south pixel, its reflection) covering the union of
-// its CT windows, unwrapped, even positions before odd ones, with cp.async
-// into two buffers (ring p + 1 is copied while ring p is summed; one barrier
-// per ring).  A thread
-// walks the union of its two windows (they start at most a pixel or two
-// apart): one 128-bit load feeds 4 of the 16 images of both outputs, and both
+// ring of the window a half stages four segments of H covering the union of its
+// CT windows -- the window pixels from a0 and from a0 + n/4, their reflections
+// from b0 and b0 + n/4 (read backwards) -- with 1-D bulk copies (TMA) issued by
+// eight lanes of its first warp: each segment splits into an even and an odd
+// part, contiguous in H up to one wrap past phi = 2 pi.  Two buffers per item:
+// ring p + 1 is copied while ring p is summed (an mbarrier per buffer counts its
+// bytes; one named barrier per ring frees the buffer of ring p - 1).  Rings whose
+// strip wraps the whole ring (a few near the poles) are copied by all threads.
+// A thread walks the union of its two windows (they start at most a pixel or two
+// apart): four 128-bit loads feed the 16 images of both outputs, and both
 // weights come from one paired evaluation (fma.rn.f32x2: two IEEE
-// operations).  The node values V_k dOmega sit in shared memory (FP32, the
-// slope formed on the fly): the lanes of a warp look up nodes spread over a
-// few hundred entries, a gather that costs a few bank wavefronts from shared
-// memory but one L1 wavefront per distinct line from global memory.
+// operations).  Because lanes two pixels apart read consecutive float4 of one
+// parity, a warp's loads hit distinct banks.  The node values V_k dOmega sit in
+// shared memory (FP32, the slope formed on the fly): the lanes of a warp look up
+// nodes spread over a few hundred entries, a gather that costs a few bank
+// wavefronts from shared memory but one L1 wavefront per distinct line from
+// global memory.
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
+#include "tc.cuh"
 
 namespace {
 
 constexpr int CT = SK_CAP_CT;       // base outputs per work item
 constexpr int NTH = CT / 2;         // threads per work item: two adjacent base outputs each
 constexpr int HALVES = SK_CAP_ITEMS_PER_BLOCK;   // work items in flight per block (one node table)
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every wait on a copy
 // strip buffers per work item: two (stage ring p + 1 while ring p is summed) where they fit
 template <int LS>
 __host__ __device__ constexpr int cap_bufs() { return LS <= 320 ? 2 : 1; }
+// dynamic shared memory: strips [HALVES][NB][4][LS] float4, then one mbarrier per
+// strip buffer and the abort flag (16 bytes), then the node table
+__host__ __device__ constexpr size_t cap_strip_bytes(int ls, int nb) { return (size_t)HALVES * nb * 4 * ls * 16; }
+__host__ __device__ constexpr size_t cap_bar_bytes(int nb) { return ((size_t)HALVES * nb * 8 + 4 + 15) / 16 * 16; }
 
 __device__ __forceinline__ void half_sync(int half) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(NTH) : "memory");
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-    uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+// Bounded wait for a strip: false after WAIT_NS, or at once when another thread of the
+// block has given up (the abort flag).
+__device__ __forceinline__ bool strip_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (tc::mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = tc::gtimer();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (tc::mbar_try(bar, parity)) return true;
+        if (*abort_flag || tc::gtimer() - t0 > WAIT_NS) return false;
+    }
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Nearest input pixel of output jo: floor(num / (2 n_o)) with num below 2^31
 // (in the caps jo < n_o / 4 <= 2 Nside and n_i <= 4 Nside <= 32768), by the
@@ -81,57 +103,127 @@ __device__ __forceinline__ void win_shape(const PairInfo &P, int &before, int &c
 // Base outputs of a quarter ring of Q pixels with shift s: [0, T).
 __device__ __forceinline__ int base_count(int Q, int s) { return s ? (Q + 1) / 2 : Q / 2 + 1; }
 
-// Strip layout of one row: even positions first, then odd ones.  A lane owns
+// Strip layout of one segment: even positions first, then odd ones.  A lane owns
 // two adjacent outputs, so at one step the lanes of a warp read positions about
 // two apart; with this layout they read consecutive float4 (one parity) instead
 // of every other one.
 template <int LS>
 __device__ __forceinline__ int split_index(int m) { return (m & 1) * (LS / 2) + (m >> 1); }
 
-// Stage row k, element m = (xN[a], xN[b], xS[a], xS[b]) with a = u0 + m + kQ and
-// b = Q - s - (u0 + m) + kQ (indices mod n): the pixel and its reflection on the
-// northern ring and on its southern mirror, at split_index(m).
+// Position of pixel a (any integer) of a ring of n pixels in its H row.
+__device__ __forceinline__ int h_index(int a, int n) {
+    a %= n;
+    if (a < 0) a += n;
+    return (a & 1) * (n >> 1) + (a >> 1);
+}
+
+// The strip of input ring P for the item's outputs j0 .. jlast: L window
+// positions from pixel u0 (base frame); the segments start at the natural pixels
+// seg_start(0..3).
+struct Strip {
+    int L, u0;
+};
+__device__ __forceinline__ Strip strip_of(const PairInfo &P, int j0, int jlast, int n_o, int s_o, unsigned mg, int sh) {
+    int before, cnt;
+    win_shape(P, before, cnt);
+    const int c0 = centre_of(j0, n_o, s_o, P, mg, sh), c1 = centre_of(jlast, n_o, s_o, P, mg, sh);
+    return Strip{c1 - c0 + cnt, c0 - before};
+}
+// Segment g: window pixels from u0 (g = 0) and from u0 + n/4 (g = 1); their
+// reflections n/4 - s - (u0 + m) (g = 2) and that + n/4 (g = 3) in natural order,
+// i.e. starting at the reflection of the last position.
+__device__ __forceinline__ int seg_start(int g, const Strip &S, const PairInfo &P) {
+    const int Q = P.n_i >> 2;
+    const int rf = Q - P.s_i - S.u0 - (S.L - 1);
+    return g == 0 ? S.u0 : g == 1 ? S.u0 + Q : g == 2 ? rf : rf + Q;
+}
+
+// Bulk copies of ring P's strip (L < n_i: each parity part of a segment is at most
+// half a ring, so it is one or two contiguous pieces of H) into buf, completing
+// on mbarrier bar.  Called by the 32 lanes of one warp.
 template <int LS>
-__device__ __forceinline__ void stage_ring(float4 *buf, const JobDesc &J, const float *xmap,
-                                           const PairInfo &P, int ri_south, int u0, int L, int t) {
-    const int n = P.n_i, Q = n >> 2, s = P.s_i;
-    const float *xn = xmap + J.rings[P.ri].start, *xs = xmap + J.rings[ri_south].start;
-    float *b = reinterpret_cast<float *>(buf);
-    // first element of this thread, reduced into [0, n) (u0 > -n, the offsets stay below 2n + NTH)
-    int io0 = u0 + t;
-    while (io0 < 0) io0 += n;
-    while (io0 >= n) io0 -= n;
-    int ir0 = Q - s - u0 - t;
-    while (ir0 < 0) ir0 += n;
-    while (ir0 >= n) ir0 -= n;
-    for (int k = 0; k < 4; ++k) {
-        int io = io0 + k * Q, ir = ir0 + k * Q;
-        if (io >= n) io -= n;
-        if (ir >= n) ir -= n;
-        for (int m = t; m < L; m += NTH) {
-            float *d = b + 4 * (k * LS + split_index<LS>(m));
-            cp_async4(d, xn + io);
-            cp_async4(d + 1, xn + ir);
-            cp_async4(d + 2, xs + io);
-            cp_async4(d + 3, xs + ir);
-            io += NTH;
-            while (io >= n) io -= n;
-            ir -= NTH;
-            while (ir < 0) ir += n;
+__device__ __forceinline__ void issue_strip(float4 *buf, uint32_t bar, const float4 *hrow, const Strip &S,
+                                            const PairInfo &P, int lane) {
+    if (lane == 0) tc::mbar_expect_tx(bar, (uint32_t)(4 * S.L) * 16u);
+    __syncwarp();
+    if (lane < 8) {
+        const int g = lane >> 1, e = lane & 1;
+        const int n = P.n_i, h = n >> 1;
+        const int cnt = e ? S.L / 2 : (S.L + 1) / 2;
+        if (cnt > 0) {
+            const int i0 = h_index(seg_start(g, S, P) + e, n);
+            const float4 *src = hrow + (i0 >= h ? h : 0);
+            const int g0 = i0 >= h ? i0 - h : i0;
+            const uint32_t dst = tc::smem_u32(buf + g * LS + e * (LS / 2));
+            const int len = min(cnt, h - g0);
+            tc::bulk_g2s(dst, src + g0, (uint32_t)len * 16u, bar);
+            if (cnt > len) tc::bulk_g2s(dst + (uint32_t)len * 16u, src, (uint32_t)(cnt - len) * 16u, bar);
         }
     }
 }
 
-// acc[k] += w (v.x, v.y), acc[4 + k] += w (v.z, v.w) for the staged pixel m of
-// each quarter turn k: (north pair, north reflected), (south pair, south reflected).
+// The same strip copied by the NTH threads of an item with plain loads (strips that
+// wrap the whole ring); the caller synchronises the item's threads afterwards.
 template <int LS>
-__device__ __forceinline__ void mac16(float2 *acc, float w, const float4 *xs, int m) {
+__device__ __forceinline__ void copy_strip(float4 *buf, const float4 *hrow, const Strip &S, const PairInfo &P, int t) {
+    for (int g = 0; g < 4; ++g) {
+        const int a0 = seg_start(g, S, P);
+        for (int m = t; m < S.L; m += NTH) buf[g * LS + split_index<LS>(m)] = hrow[h_index(a0 + m, P.n_i)];
+    }
+}
+
+// The 16 images of staged position m (forward segments at xf[i], xf[LS + i],
+// reflected ones at xr[-i], xr[LS - i]): acc[0..3] = (north, its half turn),
+// (south, its half turn) for quarter turns 0 and 1; acc[4..7] the same for the
+// reflected pair.
+template <int LS>
+__device__ __forceinline__ void mac16(float2 *acc, float w, const float4 *xf, const float4 *xr, int i) {
     const float2 ww = f2(w);
+    const float4 a = xf[i], b = xf[LS + i], c = xr[-i], d = xr[LS - i];
+    acc[0] = __ffma2_rn(ww, make_float2(a.x, a.y), acc[0]);
+    acc[1] = __ffma2_rn(ww, make_float2(a.z, a.w), acc[1]);
+    acc[2] = __ffma2_rn(ww, make_float2(b.x, b.y), acc[2]);
+    acc[3] = __ffma2_rn(ww, make_float2(b.z, b.w), acc[3]);
+    acc[4] = __ffma2_rn(ww, make_float2(c.x, c.y), acc[4]);
+    acc[5] = __ffma2_rn(ww, make_float2(c.z, c.w), acc[5]);
+    acc[6] = __ffma2_rn(ww, make_float2(d.x, d.y), acc[6]);
+    acc[7] = __ffma2_rn(ww, make_float2(d.z, d.w), acc[7]);
+}
+
+// Outputs of base pixel j (and of its reflection jr when it has one) from acc.
+__device__ __forceinline__ void store16(float *yn, float *ys, int j, int jr, bool refl, int Q, const float2 *acc) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float4 v = xs[k * LS + m];
-        acc[k] = __ffma2_rn(ww, make_float2(v.x, v.y), acc[k]);
-        acc[4 + k] = __ffma2_rn(ww, make_float2(v.z, v.w), acc[4 + k]);
+    for (int r = 0; r < 2; ++r) {
+        if (r == 1 && !refl) break;
+        const int jj = r ? jr : j;
+        const float2 *a = acc + 4 * r;
+        yn[jj] = a[0].x;
+        yn[jj + 2 * Q] = a[0].y;
+        ys[jj] = a[1].x;
+        ys[jj + 2 * Q] = a[1].y;
+        yn[jj + Q] = a[2].x;
+        yn[jj + 3 * Q] = a[2].y;
+        ys[jj + Q] = a[3].x;
+        ys[jj + 3 * Q] = a[3].y;
+    }
+}
+
+// H rows of rings [r0, r0 + gridDim.x) of every map of job J (grid: rings x map slices).
+__global__ void k_cap_sym(const JobDesc J, int r0) {
+    const int r = r0 + blockIdx.x;
+    const RingDev R = J.rings[r];
+    const int n = R.n, h = n >> 1;
+    const long long mstart = J.rings[J.nr - 1 - r].start;
+    for (int map = blockIdx.y; map < J.batch; map += gridDim.y) {
+        const float *xr = J.x + (long long)map * J.stride + R.start;
+        const float *xm = J.x + (long long)map * J.stride + mstart;
+        float4 *out = J.hx + (long long)map * J.hstride + R.start;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int par = i >= h ? 1 : 0;
+            const int a = 2 * (i - par * h) + par;
+            const int a2 = a + h < n ? a + h : a + h - n;
+            out[i] = make_float4(xr[a], xr[a2], xm[a], xm[a2]);
+        }
     }
 }
 
@@ -140,19 +232,28 @@ __global__ void __launch_bounds__(NTH * HALVES)
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
     constexpr int NB = cap_bufs<LS>();
-    // [HALVES][NB][4][LS] strip rows, then the node values (one table: every job of a launch
-    // uses the same kernel table)
     extern __shared__ __align__(16) float4 sx[];
-    float *stab = reinterpret_cast<float *>(sx + HALVES * NB * 4 * LS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(sx) + cap_strip_bytes(LS, NB));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + HALVES * NB);
+    // one node table per launch: every job of a launch uses the same kernel table
+    float *stab = reinterpret_cast<float *>(reinterpret_cast<char *>(bars) + cap_bar_bytes(NB));
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < HALVES * NB; ++b) tc::mbar_init(tc::smem_u32(bars + b), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * HALVES) stab[k] = A.j[0].tab[k].x;
     __syncthreads();
     const int half = threadIdx.x / NTH, t = threadIdx.x % NTH;
     float4 *const sbuf = sx + half * NB * 4 * LS;
+    const uint32_t bar0 = tc::smem_u32(bars + half * NB);
+    uint32_t phase = 0;     // bit b: parity of the next phase of buffer b (the same in every thread)
+    uint32_t pend = 0;      // lanes of warp 0: bit b set while a copy into buffer b is not waited for
     // work queue: each half takes the next item (items are ordered heaviest first), so the
     // halves that drew light items take more of them and all finish together
     __shared__ int s_item[HALVES];
     for (;;) {
-        if (t == 0) s_item[half] = atomicAdd(A.queue, 1);
+        if (t == 0) s_item[half] = *abort_flag ? A.total : atomicAdd(A.queue, 1);
         half_sync(half);
         const int f = s_item[half];
         if (f >= A.total) break;
@@ -173,42 +274,57 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         const bool reflA = actA && jrA < Qo && jrA >= T;
         const bool reflB = actB && jrB < Qo && jrB >= T;
         const int ro_s = J.nr - 1 - ro;
-        const float *xmap = J.x + (long long)map * J.stride;
+        const float4 *hmap = J.hx + (long long)map * J.hstride;
         const int p0 = J.pair_off[ro], p1 = J.pair_off[ro + 1];
 
-        // accX[k] = (north pair, north reflected), accX[4 + k] = (south pair, south
-        // reflected) of quarter turn k, for outputs jA and jB
         float2 accA[8], accB[8];
 #pragma unroll
         for (int s = 0; s < 8; ++s) { accA[s] = make_float2(0.0f, 0.0f); accB[s] = make_float2(0.0f, 0.0f); }
 
-        auto stage = [&](int p, float4 *dst) {
+        // ring p's strip into buffer b by bulk copies (warp 0 of the half), unless it wraps;
+        // the whole warp takes lane 0's view of the abort flag
+        auto issue = [&](int p, int b) {
+            if (t >= 32) return;
             const PairInfo Pn = J.pairs[p];
-            int before, cnt;
-            win_shape(Pn, before, cnt);
-            const int c0 = centre_of(j0, R.n, R.s, Pn, mg, sh), c1 = centre_of(jlast, R.n, R.s, Pn, mg, sh);
-            stage_ring<LS>(dst, J, xmap, Pn, J.nr - 1 - Pn.ri, c0 - before, c1 - c0 + cnt, t);
-            cp_commit();
+            const Strip S = strip_of(Pn, j0, jlast, R.n, R.s, mg, sh);
+            const int stop = __shfl_sync(0xffffffffu, *abort_flag, 0);
+            if (S.L < Pn.n_i && !stop) {
+                issue_strip<LS>(sbuf + b * 4 * LS, bar0 + 8 * b, hmap + J.rings[Pn.ri].start, S, Pn, t);
+                pend |= 1u << b;
+            }
         };
-        if (NB == 2) stage(p0, sbuf);
+        if (NB == 2 && p0 < p1) issue(p0, 0);
         for (int p = p0; p < p1; ++p) {
-            float4 *const xbuf = sbuf + (NB == 2 ? ((p - p0) & 1) : 0) * 4 * LS;
+            const int b = NB == 2 ? ((p - p0) & 1) : 0;
+            float4 *const xbuf = sbuf + b * 4 * LS;
+            const PairInfo P = J.pairs[p];
+            const Strip S = strip_of(P, j0, jlast, R.n, R.s, mg, sh);
+            const bool bulk = S.L < P.n_i;
+            // every thread is done with ring p - 1: its buffer takes ring p + 1 (two
+            // buffers) or ring p (one)
+            half_sync(half);
             if (NB == 2) {
-                // ring p's copies (issued during ring p - 1) are complete for this thread; after
-                // the barrier they are for every thread, and every thread is done with ring
-                // p - 1, whose buffer then receives ring p + 1 while ring p is summed
-                cp_wait0();
-                half_sync(half);
-                if (p + 1 < p1) stage(p + 1, sbuf + ((p + 1 - p0) & 1) * 4 * LS);
+                if (p + 1 < p1) issue(p + 1, b ^ 1);
+            } else if (bulk) {
+                issue(p, 0);
+            }
+            bool ok = true;
+            if (bulk) {
+                if (strip_wait(bar0 + 8 * b, (phase >> b) & 1, abort_flag)) {
+                    pend &= ~(1u << b);
+                } else {
+                    ok = false;
+                    if (!*abort_flag) {
+                        *abort_flag = 1;
+                        sk_record_error(A.status, SK_ETIMEOUT);
+                    }
+                }
+                phase ^= 1u << b;
             } else {
-                // one buffer: stage ring p once every thread is done with ring p - 1
-                half_sync(half);
-                stage(p, xbuf);
-                cp_wait0();
+                copy_strip<LS>(xbuf, hmap + J.rings[P.ri].start, S, P, t);
                 half_sync(half);
             }
-            if (actA) {
-                const PairInfo P = J.pairs[p];
+            if (ok && actA) {
                 int before, cnt;
                 win_shape(P, before, cnt);
                 const int cb = centre_of(j0, R.n, R.s, P, mg, sh);
@@ -219,14 +335,15 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const float qA0 = (float)q_of(cA - before, jA, R.n, R.s, P);
                 const float dqo = (float)(2 * R.n);     // q step per input pixel
                 const float dqi = (float)(2 * P.n_i);   // q of output jA minus q of output jB
-                const float4 *xrow = xbuf;
                 const int pA = cA - cb;                 // strip position of the union's first pixel
+                const int o0 = S.L - 1 - pA;            // its natural position in the reflected segments
+                const float4 *xr0 = xbuf + 2 * LS;
                 if (SERIES) {
                     // narrow windows only: a pixel of the union outside one output's window is
                     // outside its cut, and the cut test gives it weight 0.  Pixels go in pairs
-                    // (pA + m, pA + m + 1): one of each parity, at x0[i] and x1[i], i = m / 2.
-                    const float4 *x0 = xrow + split_index<LS>(pA);
-                    const float4 *x1 = xrow + split_index<LS>(pA + 1);
+                    // (pA + m, pA + m + 1): one of each parity, i = m / 2.
+                    const float4 *x0 = xbuf + split_index<LS>(pA), *x1 = xbuf + split_index<LS>(pA + 1);
+                    const float4 *r0 = xr0 + split_index<LS>(o0), *r1 = xr0 + split_index<LS>(o0 - 1);
                     float2 q = make_float2(qA0, qA0 - dqi);   // q of pixel m for outputs (A, B)
 #pragma unroll 1
                     for (int m = 0; m < cnt_u; m += 2) {
@@ -235,11 +352,11 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                         const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), P.A, P.B, J.kp, stab);
                         const float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), P.A, P.B, J.kp, stab);
                         q = __fadd2_rn(q1, f2(dqo));
-                        mac16<LS>(accA, w0.x, x0, i);
-                        mac16<LS>(accB, w0.y, x0, i);
+                        mac16<LS>(accA, w0.x, x0, r0, i);
+                        mac16<LS>(accB, w0.y, x0, r0, i);
                         if (m + 1 < cnt_u) {
-                            mac16<LS>(accA, w1.x, x1, i);
-                            mac16<LS>(accB, w1.y, x1, i);
+                            mac16<LS>(accA, w1.x, x1, r1, i);
+                            mac16<LS>(accB, w1.y, x1, r1, i);
                         }
                     }
                 } else {
@@ -250,51 +367,32 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                         float wb = fast_weight<SERIES, SMALLA, BIASED>((qa - dqi) * P.c0, P.A, P.B, J.kp, stab);
                         wa = m < cnt ? wa : 0.0f;
                         wb = m >= dl ? wb : 0.0f;
-                        const float4 *xm = xrow + split_index<LS>(pA + m);
-                        mac16<LS>(accA, wa, xm, 0);
-                        mac16<LS>(accB, wb, xm, 0);
+                        const float4 *xm = xbuf + split_index<LS>(pA + m);
+                        const float4 *rm = xr0 + split_index<LS>(o0 - m);
+                        mac16<LS>(accA, wa, xm, rm, 0);
+                        mac16<LS>(accB, wb, xm, rm, 0);
                     }
                 }
             }
         }
         // the next item stages into this half's buffers: everyone must be done reading them
         half_sync(half);
+        if (*abort_flag) continue;
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
-        if (actA) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                yn[jA + k * Qo] = accA[k].x;
-                ys[jA + k * Qo] = accA[4 + k].x;
-            }
-            if (reflA) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    yn[jrA + k * Qo] = accA[k].y;
-                    ys[jrA + k * Qo] = accA[4 + k].y;
-                }
-            }
-        }
-        if (actB) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                yn[jB + k * Qo] = accB[k].x;
-                ys[jB + k * Qo] = accB[4 + k].x;
-            }
-            if (reflB) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    yn[jrB + k * Qo] = accB[k].y;
-                    ys[jrB + k * Qo] = accB[4 + k].y;
-                }
-            }
-        }
+        if (actA) store16(yn, ys, jA, jrA, reflA, Qo, accA);
+        if (actB) store16(yn, ys, jB, jrB, reflB, Qo, accB);
+    }
+    // after an abort: wait (bounded) for this half's copies still in flight
+    if (t < 32 && pend) {
+        for (int b = 0; b < NB; ++b)
+            if ((pend >> b) & 1) tc::mbar_wait(bar0 + 8 * b, (phase >> b) & 1, WAIT_NS);
     }
 }
 
 size_t cap_smem(int LS, int nt) {
     const int nb = LS <= 320 ? 2 : 1;         // cap_bufs<LS>()
-    return (size_t)HALVES * nb * 4 * LS * sizeof(float4) + (size_t)nt * sizeof(float);
+    return cap_strip_bytes(LS, nb) + cap_bar_bytes(nb) + (size_t)nt * sizeof(float);
 }
 
 int max_nt(const JobsArg &a) {
@@ -352,6 +450,12 @@ int occupancy_ls(int mode, int nt) {
 }
 
 }  // namespace
+
+cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, cudaStream_t st) {
+    if (r1 <= r0 || j.batch <= 0) return cudaSuccess;
+    k_cap_sym<<<dim3(r1 - r0, j.batch < 65535 ? j.batch : 65535), 256, 0, st>>>(j, r0);
+    return cudaGetLastError();
+}
 
 cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cudaStream_t st) {
     if (a.total <= 0) return cudaSuccess;

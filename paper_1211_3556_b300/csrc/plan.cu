@@ -263,6 +263,13 @@ int sk_plan_build(sk_kern *k) {
         for (int j0 = 0; j0 < T; j0 += SK_CAP_CT)
             cap_items[cls][series ? 1 : 0].push_back(make_int4(r, j0, (int)mg, sh));
     }
+    // input rings of the cap items: their symmetric copy is built per call
+    k->sym_hi = 0;
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v)
+            for (const int4 &it : cap_items[c][v])
+                for (int p = off[it.x]; p < off[it.x + 1]; ++p) k->sym_hi = std::max(k->sym_hi, pairs[p].ri + 1);
+    k->sym_stride = k->sym_hi >= nr ? g->npix : R[k->sym_hi].start;
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int v = 0; v < 2; ++v) {
             // heavier rings first: per-item cost grows with the number of window pixels
@@ -399,6 +406,20 @@ int sk_plan_bands(sk_kern *k) {
         B.items.gen = gen[b].empty() ? nullptr : d + off[b].gen;
         B.items.n_gen = (int)gen[b].size();
     }
+    // symmetric copies for the caps: the run of band b builds those of the bands up to
+    // its `need` that no earlier band built (their maps have arrived by then)
+    for (int b = 0, built = -1; b < K; ++b) {
+        sk_kern::Band &B = k->bands[b];
+        const int upto = std::max(built, B.need);
+        if (upto > built) {
+            const sk_kern::Band &F = k->bands[built + 1], &U = k->bands[upto];
+            B.items.sym[0][0] = std::min(F.n_lo, k->sym_hi);
+            B.items.sym[0][1] = std::min(U.n_hi, k->sym_hi);
+            B.items.sym[1][0] = std::min(U.s_lo, k->sym_hi);
+            B.items.sym[1][1] = std::min(F.s_hi, k->sym_hi);
+            built = upto;
+        }
+    }
     k->bands_P = k->belt_P;
     return SK_OK;
 }
@@ -411,9 +432,14 @@ size_t sk_plan_workspace_bytes(const sk_kern *k) {
     return (std::max(rows, pairs) + 255) & ~(size_t)255;
 }
 
+size_t sk_sym_bytes(const sk_kern *k, long long batch) {
+    if (!k->plan_ok || k->sym_hi == 0 || batch <= 0) return 0;
+    return ((size_t)batch * (size_t)k->sym_stride * sizeof(float4) + 255) & ~(size_t)255;
+}
+
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n) {
     size_t b = 0;
-    for (int i = 0; i < n; ++i) b += sk_plan_workspace_bytes(jobs[i].k);
+    for (int i = 0; i < n; ++i) b += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
     return b;
 }
 
@@ -498,6 +524,41 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         }
     }
 
+    // The polar cap rings and any per-pair rings are small launches: run them on the
+    // context's side stream, forked from `st` here (after the belt weight rows, so that
+    // the belt is launched before the polar caps take SMs) and joined back at the end.
+    // The symmetric copies of the maps' cap input rings (in the workspace after the belt
+    // rows of all jobs) go first on the side stream, beside the belt (a band run of the
+    // host-buffer path builds its band's rings).
+    cudaStream_t side = ctx->aux;
+    std::vector<float4 *> hx(n, nullptr);
+    auto sym = [&](int i, int r0, int r1, cudaStream_t s) -> int {
+        if (r1 <= r0) return SK_OK;
+        JobDesc d = base_desc(jobs[i]);
+        d.hx = hx[i];
+        d.hstride = jobs[i].k->sym_stride;
+        cudaEvent_t ev = sk_prof_begin(ctx, s);
+        SK_CU(sk_launch_cap_sym(d, r0, r1, s));
+        sk_prof_end(ctx, "cap_sym", ev, s);
+        return SK_OK;
+    };
+    if (path != SK_PATH_GENERAL) {
+        SK_CU(cudaEventRecord(ctx->ev_fork, st));
+        SK_CU(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
+        char *hp = (char *)ws;
+        for (int i = 0; i < n; ++i) hp += sk_plan_workspace_bytes(jobs[i].k);
+        for (int i = 0; i < n; ++i) {
+            const size_t bytes = sk_sym_bytes(jobs[i].k, jobs[i].batch);
+            if (!bytes) continue;
+            hx[i] = (float4 *)hp;
+            hp += bytes;
+            const SkItems *sub = jobs[i].sub;
+            int rc = sub ? sym(i, sub->sym[0][0], sub->sym[0][1], side) : sym(i, 0, jobs[i].k->sym_hi, side);
+            if (!rc && sub) rc = sym(i, sub->sym[1][0], sub->sym[1][1], side);
+            if (rc) return rc;
+        }
+    }
+
     if (path == SK_PATH_GENERAL) {
         Batcher b;
         auto flush = [&]() -> int {
@@ -517,12 +578,6 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         }
         return flush();
     }
-
-    // The polar cap rings and any per-pair rings are small launches: run them on the
-    // context's side stream, forked from `st` here and joined back at the end.
-    cudaStream_t side = ctx->aux;
-    SK_CU(cudaEventRecord(ctx->ev_fork, st));
-    SK_CU(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
 
     // batched tensor-core belt: one launch per job (its tile geometry is per operator)
     if (path == SK_PATH_TENSOR) {
@@ -575,7 +630,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         if (rc) return rc;
     }
 
-    // caps: one launch family per (strip class, mode)
+    // caps: one launch family per (strip class, mode); those on `st` wait for the copies
+    SK_CU(cudaEventRecord(ctx->ev_sym, side));
+    SK_CU(cudaStreamWaitEvent(st, ctx->ev_sym, 0));
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int mode = 0; mode < 8; ++mode) {
             const int v = mode & 1;
@@ -612,6 +669,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                 if (b.a.n_jobs > 0 && b.a.j[0].tab != k->d_tab) { int rc = flush(); if (rc) return rc; }
                 JobDesc d = base_desc(jobs[i]);
                 d.cap_ls = SK_CAP_LS[c];
+                d.hx = hx[i];
+                d.hstride = k->sym_stride;
                 b.add(d, citems, cn);
                 if (b.full()) { int rc = flush(); if (rc) return rc; }
             }

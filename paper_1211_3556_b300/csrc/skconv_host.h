@@ -27,6 +27,7 @@ struct sk_ctx {
     // per-pair fallback rings), forked from and joined into the caller's stream
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_sym = nullptr;  // the side stream's symmetric copies for the caps are built
     // optional per-launch timing (sk_profile_enable): events around each kernel
     bool prof = false;
     struct ProfRec { const char *name; cudaEvent_t a, b; };
@@ -45,6 +46,9 @@ struct SkItems {
     int n_cap[SK_CAP_LS_CLASSES][2] = {};
     const int4 *gen = nullptr;
     int n_gen = 0;
+    // rings whose symmetric copy (the cap kernel's input) this subset's run builds:
+    // [sym[0][0], sym[0][1]) and [sym[1][0], sym[1][1])
+    int sym[2][2] = {};
 };
 
 struct sk_geom {
@@ -94,6 +98,9 @@ struct sk_kern {
     int4 *d_items_cap[SK_CAP_LS_CLASSES][2] = {};
     int n_items_cap[SK_CAP_LS_CLASSES][2] = {};
     int n_cap_rings = 0;
+    // the cap kernel reads the symmetric copy of input rings [0, sym_hi): sym_stride float4 per map
+    int sym_hi = 0;
+    long long sym_stride = 0;
     unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere), 2 general
     // batched tensor-core form of the belt: (group, 128-pixel block) items
     bool tc_ok = false;
@@ -126,6 +133,7 @@ int sk_plan_build(sk_kern *k);
 void sk_plan_free(sk_kern *k);
 int sk_plan_rebuild_belt_items(sk_kern *k);
 size_t sk_plan_workspace_bytes(const sk_kern *k);
+size_t sk_sym_bytes(const sk_kern *k, long long batch);   // symmetric copy of `batch` maps
 
 // One job of a launch sequence.
 struct SkJob {
@@ -139,7 +147,8 @@ struct SkJob {
 // Partition of k's items into ring bands (kept in k; rebuilt when stale).
 int sk_plan_bands(sk_kern *k);
 // Launch sequence of the forward operator for a set of jobs.  `ws` must hold
-// sk_jobs_workspace_bytes(jobs) bytes (belt weight rows).
+// sk_jobs_workspace_bytes(jobs) bytes: the belt weight rows of every job, then the
+// symmetric copies of every job's maps for the caps.
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n);
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st);
 int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,

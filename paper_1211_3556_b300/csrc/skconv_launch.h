@@ -53,6 +53,9 @@ struct JobDesc {
                           // ring 2w+1) at offset EMIN + o + c, zero past 4 nch
     // cap path
     int cap_ls;           // strip stride class
+    float4 *hx;           // symmetric copy of the input rings the caps read (workspace, per call):
+                          // ring r of map b at hx + b hstride + rings[r].start, n_r float4
+    long long hstride;    // float4 per map of hx
 };
 
 struct JobsArg {
@@ -107,6 +110,8 @@ cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t 
 // mode bits: 1 sin series valid on every window of the items, 2 theta_cut <= 0.25
 // (asin series), 4 biased node layout
 cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cudaStream_t st);
+// symmetric copy (hx) of rings [r0, r1) of every map of job j, for the cap kernel
+cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, cudaStream_t st);
 int sk_belt_blocks_per_sm(const JobsArg &a, int P);
 int sk_cap_blocks_per_sm(int ls, int mode, int nt);
 constexpr int SK_CAP_LS_CLASSES = 3;

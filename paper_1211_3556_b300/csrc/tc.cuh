@@ -1,7 +1,8 @@
 // tc.cuh -- tcgen05 building blocks (sm_100-family tensor cores) used by the
 // batched tensor-core path: tensor-memory allocation, shared-memory operand
 // descriptors for the 128-byte-swizzled K-major layout, the TF32 MMA, its
-// completion barrier and the tensor-memory loads.  Inline PTX only.
+// completion barrier and the tensor-memory loads; and the mbarrier and 1-D bulk
+// copy (TMA) primitives that the cap path uses too.  Inline PTX only.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -99,6 +100,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+// Arrive on the barrier and add `bytes` to the transaction count of its current phase.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completing `bytes` of the barrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 // Bounded wait (limit in ns); false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
