@@ -53,15 +53,20 @@ namespace {
 
 constexpr int CT = SK_CAP_CT;       // base outputs per work item
 constexpr int NTH = CT / 2;         // threads per work item: two adjacent base outputs each
-constexpr int HALVES = SK_CAP_ITEMS_PER_BLOCK;   // work items in flight per block (one node table)
+static_assert(NTH == 128, "an item's strips are issued by its four warps in turn");
+// work items in flight per block (they share one node table): four where their strips fit
+template <int LS>
+__host__ __device__ constexpr int cap_halves() { return LS <= 640 ? 4 : 2; }
+// node tables of up to this many nodes are held as (value, slope) pairs, larger ones as values
+constexpr int PAIR_TABLE_NODES = 8192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every wait on a copy
 // strip buffers per work item: two (stage ring p + 1 while ring p is summed) where they fit
 template <int LS>
 __host__ __device__ constexpr int cap_bufs() { return LS <= 320 ? 2 : 1; }
-// dynamic shared memory: strips [HALVES][NB][4][LS] float4, then one mbarrier per
-// strip buffer and the abort flag (16 bytes), then the node table
-__host__ __device__ constexpr size_t cap_strip_bytes(int ls, int nb) { return (size_t)HALVES * nb * 4 * ls * 16; }
-__host__ __device__ constexpr size_t cap_bar_bytes(int nb) { return ((size_t)HALVES * nb * 8 + 4 + 15) / 16 * 16; }
+// dynamic shared memory: strips [halves][NB][4][LS] float4, then one mbarrier per
+// strip buffer and the abort flag (16-byte multiple), then the node table
+__host__ __device__ constexpr size_t cap_strip_bytes(int ls, int nb, int halves) { return (size_t)halves * nb * 4 * ls * 16; }
+__host__ __device__ constexpr size_t cap_bar_bytes(int nb, int halves) { return ((size_t)halves * nb * 8 + 4 + 15) / 16 * 16; }
 
 __device__ __forceinline__ void half_sync(int half) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(NTH) : "memory");
@@ -116,6 +121,14 @@ __device__ __forceinline__ int h_index(int a, int n) {
     if (a < 0) a += n;
     return (a & 1) * (n >> 1) + (a >> 1);
 }
+// The same for -2n < a < 2n (the segment starts of a strip shorter than the ring).
+__device__ __forceinline__ int h_index_near(int a, int n) {
+    a = a < 0 ? a + n : a;
+    a = a < 0 ? a + n : a;
+    a = a >= n ? a - n : a;
+    a = a >= n ? a - n : a;
+    return (a & 1) * (n >> 1) + (a >> 1);
+}
 
 // The strip of input ring P for the item's outputs j0 .. jlast: L window
 // positions from pixel u0 (base frame); the segments start at the natural pixels
@@ -140,7 +153,7 @@ __device__ __forceinline__ int seg_start(int g, const Strip &S, const PairInfo &
 
 // Bulk copies of ring P's strip (L < n_i: each parity part of a segment is at most
 // half a ring, so it is one or two contiguous pieces of H) into buf, completing
-// on mbarrier bar.  Called by the 32 lanes of one warp.
+// on mbarrier bar.  Called by the 32 lanes of one warp (the item's warps take turns).
 template <int LS>
 __device__ __forceinline__ void issue_strip(float4 *buf, uint32_t bar, const float4 *hrow, const Strip &S,
                                             const PairInfo &P, int lane) {
@@ -151,7 +164,7 @@ __device__ __forceinline__ void issue_strip(float4 *buf, uint32_t bar, const flo
         const int n = P.n_i, h = n >> 1;
         const int cnt = e ? S.L / 2 : (S.L + 1) / 2;
         if (cnt > 0) {
-            const int i0 = h_index(seg_start(g, S, P) + e, n);
+            const int i0 = h_index_near(seg_start(g, S, P) + e, n);
             const float4 *src = hrow + (i0 >= h ? h : 0);
             const int g0 = i0 >= h ? i0 - h : i0;
             const uint32_t dst = tc::smem_u32(buf + g * LS + e * (LS / 2));
@@ -227,28 +240,32 @@ __global__ void k_cap_sym(const JobDesc J, int r0) {
     }
 }
 
-template <int LS, int MODE>
-__global__ void __launch_bounds__(NTH * HALVES)
+template <int LS, int MODE, typename TabT>
+__global__ void __launch_bounds__(NTH * cap_halves<LS>())
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
-    constexpr int NB = cap_bufs<LS>();
+    constexpr int NB = cap_bufs<LS>(), HALVES = cap_halves<LS>();
     extern __shared__ __align__(16) float4 sx[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(sx) + cap_strip_bytes(LS, NB));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(sx) + cap_strip_bytes(LS, NB, HALVES));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + HALVES * NB);
-    // one node table per launch: every job of a launch uses the same kernel table
-    float *stab = reinterpret_cast<float *>(reinterpret_cast<char *>(bars) + cap_bar_bytes(NB));
+    // one node table per launch (every job of a launch uses the same kernel table):
+    // (value, slope) pairs, or the values alone
+    TabT *stab = reinterpret_cast<TabT *>(reinterpret_cast<char *>(bars) + cap_bar_bytes(NB, HALVES));
     if (threadIdx.x == 0) {
         for (int b = 0; b < HALVES * NB; ++b) tc::mbar_init(tc::smem_u32(bars + b), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * HALVES) stab[k] = A.j[0].tab[k].x;
+    for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * HALVES) {
+        if constexpr (sizeof(TabT) == sizeof(float2)) stab[k] = A.j[0].tab[k];
+        else stab[k] = A.j[0].tab[k].x;
+    }
     __syncthreads();
     const int half = threadIdx.x / NTH, t = threadIdx.x % NTH;
     float4 *const sbuf = sx + half * NB * 4 * LS;
     const uint32_t bar0 = tc::smem_u32(bars + half * NB);
     uint32_t phase = 0;     // bit b: parity of the next phase of buffer b (the same in every thread)
-    uint32_t pend = 0;      // lanes of warp 0: bit b set while a copy into buffer b is not waited for
+    uint32_t pend = 0;      // bit b set while a copy this thread's warp issued into buffer b is not waited for
     // work queue: each half takes the next item (items are ordered heaviest first), so the
     // halves that drew light items take more of them and all finish together
     __shared__ int s_item[HALVES];
@@ -281,15 +298,16 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
 #pragma unroll
         for (int s = 0; s < 8; ++s) { accA[s] = make_float2(0.0f, 0.0f); accB[s] = make_float2(0.0f, 0.0f); }
 
-        // ring p's strip into buffer b by bulk copies (warp 0 of the half), unless it wraps;
-        // the whole warp takes lane 0's view of the abort flag
+        // ring p's strip into buffer b by bulk copies, unless it wraps; the item's warps
+        // take turns (ring p by warp (p - p0) mod 4), and the issuing warp takes lane 0's
+        // view of the abort flag
         auto issue = [&](int p, int b) {
-            if (t >= 32) return;
+            if (((p - p0) & 3) != (t >> 5)) return;
             const PairInfo Pn = J.pairs[p];
             const Strip S = strip_of(Pn, j0, jlast, R.n, R.s, mg, sh);
             const int stop = __shfl_sync(0xffffffffu, *abort_flag, 0);
             if (S.L < Pn.n_i && !stop) {
-                issue_strip<LS>(sbuf + b * 4 * LS, bar0 + 8 * b, hmap + J.rings[Pn.ri].start, S, Pn, t);
+                issue_strip<LS>(sbuf + b * 4 * LS, bar0 + 8 * b, hmap + J.rings[Pn.ri].start, S, Pn, t & 31);
                 pend |= 1u << b;
             }
         };
@@ -337,6 +355,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 const float dqi = (float)(2 * P.n_i);   // q of output jA minus q of output jB
                 const int pA = cA - cb;                 // strip position of the union's first pixel
                 const int o0 = S.L - 1 - pA;            // its natural position in the reflected segments
+                const float Ae = fmaxf(P.A, 1e-30f);    // t >= 1e-30: a normal number for rsqrt
                 const float4 *xr0 = xbuf + 2 * LS;
                 if (SERIES) {
                     // narrow windows only: a pixel of the union outside one output's window is
@@ -349,8 +368,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     for (int m = 0; m < cnt_u; m += 2) {
                         const int i = m >> 1;
                         const float2 q1 = __fadd2_rn(q, f2(dqo));
-                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), P.A, P.B, J.kp, stab);
-                        const float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), P.A, P.B, J.kp, stab);
+                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
+                        const float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), Ae, P.B, J.kp, stab);
                         q = __fadd2_rn(q1, f2(dqo));
                         mac16<LS>(accA, w0.x, x0, r0, i);
                         mac16<LS>(accB, w0.y, x0, r0, i);
@@ -363,8 +382,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     // windows may be whole rings: restrict each output to its own window
                     for (int m = 0; m < cnt_u; ++m) {
                         const float qa = fmaf((float)m, dqo, qA0);
-                        float wa = fast_weight<SERIES, SMALLA, BIASED>(qa * P.c0, P.A, P.B, J.kp, stab);
-                        float wb = fast_weight<SERIES, SMALLA, BIASED>((qa - dqi) * P.c0, P.A, P.B, J.kp, stab);
+                        float wa = fast_weight<SERIES, SMALLA, BIASED>(qa * P.c0, Ae, P.B, J.kp, stab);
+                        float wb = fast_weight<SERIES, SMALLA, BIASED>((qa - dqi) * P.c0, Ae, P.B, J.kp, stab);
                         wa = m < cnt ? wa : 0.0f;
                         wb = m >= dl ? wb : 0.0f;
                         const float4 *xm = xbuf + split_index<LS>(pA + m);
@@ -383,16 +402,16 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         if (actA) store16(yn, ys, jA, jrA, reflA, Qo, accA);
         if (actB) store16(yn, ys, jB, jrB, reflB, Qo, accB);
     }
-    // after an abort: wait (bounded) for this half's copies still in flight
-    if (t < 32 && pend) {
+    // after an abort: wait (bounded) for the copies this warp issued that are still in flight
+    if (pend) {
         for (int b = 0; b < NB; ++b)
             if ((pend >> b) & 1) tc::mbar_wait(bar0 + 8 * b, (phase >> b) & 1, WAIT_NS);
     }
 }
 
-size_t cap_smem(int LS, int nt) {
-    const int nb = LS <= 320 ? 2 : 1;         // cap_bufs<LS>()
-    return cap_strip_bytes(LS, nb) + cap_bar_bytes(nb) + (size_t)nt * sizeof(float);
+size_t cap_smem(int LS, int nt, bool pairs) {
+    const int nb = LS <= 320 ? 2 : 1, halves = LS <= 640 ? 4 : 2;     // cap_bufs, cap_halves
+    return cap_strip_bytes(LS, nb, halves) + cap_bar_bytes(nb, halves) + (size_t)nt * (pairs ? 8 : 4);
 }
 
 int max_nt(const JobsArg &a) {
@@ -401,22 +420,34 @@ int max_nt(const JobsArg &a) {
     return m;
 }
 
-template <int LS, int MODE>
-cudaError_t launch_lm(const JobsArg &a, int grid, cudaStream_t st) {
-    const size_t smem = cap_smem(LS, max_nt(a));
-    cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int LS, int MODE, typename TabT>
+cudaError_t launch_t(const JobsArg &a, int nt, int grid, cudaStream_t st) {
+    const size_t smem = cap_smem(LS, nt, sizeof(TabT) == sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS, MODE, TabT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_cap<LS, MODE><<<grid, NTH * HALVES, smem, st>>>(a);
+    k_conv_cap<LS, MODE, TabT><<<grid, NTH * cap_halves<LS>(), smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int LS, int MODE>
-int occupancy_lm(int nt) {
-    const size_t smem = cap_smem(LS, nt);
-    cudaFuncSetAttribute(k_conv_cap<LS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_lm(const JobsArg &a, int grid, cudaStream_t st) {
+    const int nt = max_nt(a);
+    return nt <= PAIR_TABLE_NODES ? launch_t<LS, MODE, float2>(a, nt, grid, st)
+                                  : launch_t<LS, MODE, float>(a, nt, grid, st);
+}
+
+template <int LS, int MODE, typename TabT>
+int occupancy_t(int nt) {
+    const size_t smem = cap_smem(LS, nt, sizeof(TabT) == sizeof(float2));
+    cudaFuncSetAttribute(k_conv_cap<LS, MODE, TabT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE>, NTH * HALVES, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE, TabT>, NTH * cap_halves<LS>(), smem);
     return nb;
+}
+
+template <int LS, int MODE>
+int occupancy_lm(int nt) {
+    return nt <= PAIR_TABLE_NODES ? occupancy_t<LS, MODE, float2>(nt) : occupancy_t<LS, MODE, float>(nt);
 }
 
 template <int LS>
@@ -466,6 +497,8 @@ cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cud
         default: return cudaErrorInvalidValue;
     }
 }
+
+int sk_cap_items_per_block(int ls) { return ls <= 640 ? 4 : 2; }
 
 int sk_cap_blocks_per_sm(int ls, int mode, int nt) {
     switch (ls) {

@@ -645,8 +645,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                     int per = sk_cap_blocks_per_sm(SK_CAP_LS[c], mode, mnt);
                     cudaStream_t cs = v ? st : side;
                     cudaEvent_t ev = sk_prof_begin(ctx, cs);
-                    // a block works on SK_CAP_ITEMS_PER_BLOCK items at a time
-                    const int blocks = (b.a.total + SK_CAP_ITEMS_PER_BLOCK - 1) / SK_CAP_ITEMS_PER_BLOCK;
+                    // a block works on several items at a time
+                    const int ipb = sk_cap_items_per_block(SK_CAP_LS[c]);
+                    const int blocks = (b.a.total + ipb - 1) / ipb;
                     int *q = ctx->d_queue + ctx->next_queue;
                     ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
                     SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));

@@ -117,7 +117,7 @@ int sk_cap_blocks_per_sm(int ls, int mode, int nt);
 constexpr int SK_CAP_LS_CLASSES = 3;
 constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {320, 640, 1280};  // strip positions per row of the cap path (float4)
 constexpr int SK_CAP_CT = 256;         // base output pixels per cap work item (two per thread)
-constexpr int SK_CAP_ITEMS_PER_BLOCK = 2;   // cap work items a block holds at a time (one node table)
+int sk_cap_items_per_block(int ls);   // cap work items a block holds at a time (one node table)
 
 // table gradient (grad.cu)
 cudaError_t sk_launch_grad_general(const JobsArg &a, const float *gy, double *acc, int grid,
