@@ -166,7 +166,7 @@ def build_operator(sk, ctx, group):
 # DRAM traffic per launch from a committed ncu summary (profiles/<kernel>_<workload>.md),
 # valid only while the kernel's sources hash to the value recorded at capture time.
 PROFILED_SOURCES = {
-    "conv_cap": ["cap.cu", "skconv_internal.cuh", "skconv_launch.h"],
+    "conv_cap": ["cap.cu", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
     "conv_belt": ["belt.cu", "skconv_internal.cuh", "skconv_launch.h"],
 }
 
