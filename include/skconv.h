@@ -336,6 +336,32 @@ int sk_harmonic_table_bytes(const sk_harm *h, int64_t *bytes);
 int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *h, const float *d_in, float *d_out, int64_t batch,
                       int64_t map_stride, int accumulate, void *stream);
 
+/* ---- ring-pair Fourier form of the belt, for wide theta_cut --------------- */
+
+/* In the equatorial zone (rings of 4 Nside pixels) the real-space sum between
+ * two rings is a circular correlation along the ring, diagonal in the ring's
+ * Fourier modes m: Y_o(m) = sum_i W_oi(m) X_i(m) (the paper's Eq. 3 cost model
+ * is linear in theta_cut; direct sums grow with its square).  The handle holds
+ * W_oi(m) (as real G_oi(m) and a phase) for every output ring whose whole
+ * window lies in the zone and every input ring of its window, built once from
+ * FP64 weights through FP32 FFTs; the other rings (polar caps, rings whose
+ * window leaves the zone) run through the kernel's direct paths.  Same
+ * operator as sk_convolve (FP32 FFTs and mode sums: rms differences ~1e-7).
+ * Device memory: f_nb (2H+1) (2 Nside + 1) floats for G, see sk_fourier_info.
+ * Errors: SK_EINVAL (NULL), SK_ENOMEM, SK_ECUDA.  *out is NULL on error. */
+typedef struct sk_fourier sk_fourier;
+int sk_fourier_create(sk_ctx *ctx, const sk_kern *k, sk_fourier **out);
+int sk_fourier_destroy(sk_fourier *f);
+/* out4[0] = first output ring of the Fourier form (0-based), out4[1] = its number
+ * of rings (0: none qualifies, all rings run direct), out4[2] = H (ring offsets
+ * -H..H), out4[3] = device bytes of G. */
+int sk_fourier_info(const sk_fourier *f, int64_t *out4);
+/* d_out = A d_in for `batch` maps [batch][map_stride] (as sk_convolve), the zone
+ * rings by the Fourier form.  Uses the handle's buffers: calls with one handle
+ * must not overlap on the GPU.  Errors: as sk_convolve. */
+int sk_fourier_apply(sk_ctx *ctx, const sk_fourier *f, const float *d_in, float *d_out, int64_t batch,
+                     int64_t map_stride, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

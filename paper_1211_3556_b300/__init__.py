@@ -84,6 +84,10 @@ def _declare(L):
         "sk_harmonic_destroy": (I, [P]),
         "sk_harmonic_table_bytes": (I, [P, ctypes.POINTER(I64)]),
         "sk_harmonic_apply": (I, [P, P, P, P, I64, I64, I, P]),
+        "sk_fourier_create": (I, [P, P, PP]),
+        "sk_fourier_destroy": (I, [P]),
+        "sk_fourier_info": (I, [P, ctypes.POINTER(I64)]),
+        "sk_fourier_apply": (I, [P, P, P, P, I64, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -429,6 +433,44 @@ class Harmonic:
         try:
             if self._h:
                 lib().sk_harmonic_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+class FourierBelt:
+    """The real-space convolution of a kernel with its equatorial-zone rings done in the
+    rings' Fourier modes (Y_o(m) = sum_i W_oi(m) X_i(m), linear in theta_cut), the other
+    rings by the direct paths: for wide theta_cut, where direct sums grow with its square."""
+
+    def __init__(self, kern: Kernel):
+        self.kern, self.ctx, self.geom = kern, kern.geom.ctx, kern.geom
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_fourier_create(self.ctx._h, kern._h, ctypes.byref(self._h)))
+
+    def info(self) -> dict:
+        """first_ring, rings (0: none in the Fourier form), H (ring offsets -H..H), bytes of G."""
+        v = (ctypes.c_int64 * 4)()
+        _check(lib().sk_fourier_info(self._h, v))
+        return {"first_ring": v[0], "rings": v[1], "H": v[2], "bytes": v[3]}
+
+    def apply(self, x, out=None, stream=None):
+        """out = A x for maps x [batch, npix] (float32 CUDA)."""
+        import torch
+        x2, b, stride = _map_args(x, self.geom.npix)
+        if out is None:
+            out = torch.empty_like(x2)
+        o2, _, ostride = _map_args(out, self.geom.npix)
+        if ostride != stride:
+            raise ValueError("input and output maps need the same stride")
+        _check(lib().sk_fourier_apply(self.ctx._h, self._h, ctypes.c_void_p(x2.data_ptr()),
+                                      ctypes.c_void_p(o2.data_ptr()), b, stride, _stream_ptr(stream)))
+        return out if out.dim() == x.dim() else out.view_as(x)
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().sk_fourier_destroy(self._h)
                 self._h = ctypes.c_void_p()
         except Exception:
             pass

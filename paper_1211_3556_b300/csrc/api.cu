@@ -475,8 +475,8 @@ extern "C" int sk_kernel_get_tiles(const sk_kern *k, int *belt_p, int *cap_t) {
 // convolution
 // ---------------------------------------------------------------------------
 
-static int check_maps(const char *who, const sk_kern *k, const void *in, const void *out, int64_t batch,
-                      int64_t stride, bool disjoint = true) {
+int sk_check_maps(const char *who, const sk_kern *k, const void *in, const void *out, int64_t batch,
+                  int64_t stride, bool disjoint) {
     if (!k) return sk_fail(SK_EINVAL, "%s: NULL operator", who);
     if (batch < 0) return sk_fail(SK_EINVAL, "%s: batch %lld < 0", who, (long long)batch);
     if (batch == 0) return SK_OK;
@@ -496,7 +496,7 @@ static int check_maps(const char *who, const sk_kern *k, const void *in, const v
 extern "C" int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
                                 int64_t map_stride, int path, void *stream) {
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve: NULL context");
-    int rc = check_maps("sk_convolve", k, d_in, d_out, batch, map_stride);
+    int rc = sk_check_maps("sk_convolve", k, d_in, d_out, batch, map_stride);
     if (rc) return rc;
     if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL && path != SK_PATH_TENSOR)
         return sk_fail(SK_EINVAL, "unknown path %d", path);
@@ -524,7 +524,7 @@ extern "C" int sk_convolve_adjoint(sk_ctx *ctx, const sk_kern *k, const float *d
 extern "C" int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, const float *d_gy, int64_t batch,
                              int64_t map_stride, float *d_gtable, void *stream) {
     if (!ctx || !k || !d_gtable) return sk_fail(SK_EINVAL, "sk_grad_table: NULL argument");
-    int rc = check_maps("sk_grad_table", k, d_x, d_gy, batch, map_stride, false);
+    int rc = sk_check_maps("sk_grad_table", k, d_x, d_gy, batch, map_stride, false);
     if (rc) return rc;
     SK_CU(cudaSetDevice(ctx->device));
     void *ws = nullptr;
@@ -636,7 +636,7 @@ static int convert_jobs(const sk_job *jobs, int n, std::vector<SkJob> &out) {
     if (n < 0 || (n > 0 && !jobs)) return sk_fail(SK_EINVAL, "bad job list");
     out.resize(n);
     for (int i = 0; i < n; ++i) {
-        int rc = check_maps("sk_convolve_jobs", jobs[i].k, jobs[i].d_in, jobs[i].d_out, jobs[i].batch,
+        int rc = sk_check_maps("sk_convolve_jobs", jobs[i].k, jobs[i].d_in, jobs[i].d_out, jobs[i].batch,
                             jobs[i].map_stride);
         if (rc) return rc;
         out[i] = SkJob{jobs[i].k, jobs[i].d_in, jobs[i].d_out, jobs[i].batch, jobs[i].map_stride};

@@ -127,6 +127,9 @@ int sk_fail(int code, const char *fmt, ...);
 cudaEvent_t sk_prof_begin(sk_ctx *ctx, cudaStream_t st);
 void sk_prof_end(sk_ctx *ctx, const char *name, cudaEvent_t a, cudaStream_t st);
 int sk_ctx_workspace(sk_ctx *ctx, size_t bytes, void **out);
+// Argument checks of the map-taking entry points (null, batch, stride, alignment, overlap).
+int sk_check_maps(const char *who, const sk_kern *k, const void *in, const void *out, int64_t batch,
+                  int64_t stride, bool disjoint = true);
 
 // plan.cu
 int sk_plan_build(sk_kern *k);
