@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-split", action="store_true", help="skip the harmonic-half (split) side measurement")
+    ap.add_argument("--no-fourier", action="store_true", help="skip the wide-cut (ring-pair Fourier) side measurement")
     return ap.parse_args()
 
 
@@ -385,6 +386,41 @@ def run_ours(args):
                  "sigma_rms_eq2_least_squares": sig_fit}
         del h, yh
 
+    # wide cut (300' at Nside 1024): the equatorial-zone rings by the ring-pair Fourier form
+    # against the direct sums (per-pair there: the belt kernel's stages do not fit such windows)
+    fourier = None
+    if not args.no_fourier and args.workload == "n2048_plain":
+        grp = WORKLOADS["n1024_wide"].groups[0]
+        gw, kw = build_operator(sk, ctx, grp)
+        t0 = time.perf_counter()
+        fw = sk.FourierBelt(kw)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        xw = torch.from_numpy(make_maps(grp)).cuda()
+        yf, yd = torch.empty_like(xw), torch.empty_like(xw)
+        nw = max(3, min(args.steps, 5))
+        ctx.profile(True)
+        ctx.profile_read()
+        ms_f = time_steps(torch, lambda: fw.apply(xw, out=yf), nw, 1, barrier)
+        pf = ctx.profile_read()
+        ms_d = time_steps(torch, lambda: sk.convolve(kw, xw, out=yd), nw, 1, barrier)
+        pd = ctx.profile_read()
+        ctx.profile(False)
+        info = fw.info()
+        n_, st_, _, _, _ = gw.rings()
+        r0, r1 = info["first_ring"], info["first_ring"] + info["rings"]
+        zs = slice(int(st_[r0]), int(st_[r1 - 1] + n_[r1 - 1]))
+        a = yf[0, zs].double()
+        b = yd[0, zs].double()
+        per = lambda p, names: sum(p[n][0] for n in names if n in p) / nw
+        fourier = {"workload": "n1024_wide", "theta_cut_arcmin": grp.kernel.theta_cut_arcmin,
+                   "zone_rings": info["rings"], "ring_offsets_H": info["H"], "G_gb": info["bytes"] / 1e9,
+                   "create_s": t_create, "ms_per_map_fourier_operator": ms_f, "ms_per_map_direct_operator": ms_d,
+                   "zone_ms_fourier": per(pf, ("fourier_fft", "fourier_mix")),
+                   "zone_ms_direct_per_pair": per(pd, ("conv_general",)),
+                   "zone_rms_rel_fourier_vs_direct": float(torch.linalg.norm(a - b) / torch.linalg.norm(b))}
+        del fw, xw, yf, yd
+
     o0 = ops[0]
     y0 = o0["y"][0].cpu().numpy()
     cpu_baseline, rms = None, None
@@ -416,6 +452,7 @@ def run_ours(args):
             "e2e": e2e,
             "batched": batched,
             "split": split,
+            "fourier": fourier,
             "cpu_baseline": cpu_baseline,
             "context": "paper: GTX 480 + 1 Core2 core, split convolution >10x faster than a full "
                        "single-core SHT convolution (eq. 3 model: 2.89 s at theta_cut 20')",

@@ -97,7 +97,7 @@ def _k(fwhm, nside, tc, nt, lmax=None, lcut=None):
     return KernelSpec(fwhm, lmax, lcut, tc, nt)
 
 
-# The five workloads.  Sizes: Nside 64 .. 8192; theta_cut 5' .. 180'.
+# The workloads.  Sizes: Nside 64 .. 8192; theta_cut 5' .. 300'.
 WORKLOADS = {
     "n64_plain": Workload("n64_plain", (Group(64, 1, _k(60.0, 64, 180.0, 4096, 192, 96), 101),)),
     "n2048_plain": Workload("n2048_plain",
@@ -115,6 +115,8 @@ WORKLOADS = {
                               (Group(1024, 16, _k(10.0, 1024, 30.0, 4096), 401),)),
     "n8192_plain": Workload("n8192_plain",
                             (Group(8192, 1, _k(2.0, 8192, 5.0, 16384, 16384, 4096), 501),)),
+    # wide cut (the ring-pair Fourier form of the belt): 300' windows, ~2.3e4 neighbours per pixel
+    "n1024_wide": Workload("n1024_wide", (Group(1024, 1, _k(60.0, 1024, 300.0, 4096), 601),)),
 }
 
 # Gradient workload: the target map comes from the same maps convolved with a

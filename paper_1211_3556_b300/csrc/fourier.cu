@@ -108,30 +108,42 @@ __global__ void k_fw_finish(const RingDev *rings, const float2 *R, int f_lo, int
 }
 
 // Y[o][m] = sum_{d even} G X + e^{-2 pi i m delta_o / n} sum_{d odd} G X, one thread
-// per (output ring, mode); partial sums over blocks of 32 offsets.
+// per (output ring, mode), reading G once (coalesced along m); offsets whose input
+// ring lies outside the buffer (their G rows are zero) are skipped by the loop
+// bounds.  Partial sums over blocks of 32 offsets, two offsets per step.
 __global__ void k_fmix(const RingDev *rings, const float *__restrict__ G, const float2 *__restrict__ X, int f_lo,
                        int f_nb, int in_lo, int in_n, int H, int n, int M, float2 *Y) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int oi = blockIdx.y;
     if (m >= M || oi >= f_nb) return;
     const int o = f_lo + oi;
+    const int dlo = max(0, in_lo - (o - H)), dhi = min(2 * H, in_lo + in_n - 1 - (o - H));
     const float *g = G + (size_t)oi * (2 * H + 1) * M + m;
-    const float2 *x = X + (size_t)(o - H - in_lo) * M + m;
-    float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
-    for (int d0 = 0; d0 < 2 * H + 1; d0 += 32) {
-        float2 be = make_float2(0.f, 0.f), bo = make_float2(0.f, 0.f);
-        const int d1 = min(d0 + 32, 2 * H + 1);
-        for (int dd = d0; dd < d1; ++dd) {
-            const int ring = o - H + dd;                 // input ring
-            if (ring < in_lo || ring >= in_lo + in_n) continue;
-            const float gv = g[(size_t)dd * M];
-            const float2 xv = x[(size_t)dd * M];
-            if (((dd - H) & 1) == 0) { be.x = fmaf(gv, xv.x, be.x); be.y = fmaf(gv, xv.y, be.y); }
-            else                     { bo.x = fmaf(gv, xv.x, bo.x); bo.y = fmaf(gv, xv.y, bo.y); }
+    const float2 *x = X + (ptrdiff_t)(o - H - in_lo) * M + m;
+    // accumulators a0 (offsets dlo, dlo + 2, ...) and a1 (dlo + 1, ...); even ring offsets
+    // d = dd - H are a0 when dlo - H is even
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+    for (int d0 = dlo; d0 <= dhi; d0 += 32) {
+        const int d1 = min(d0 + 31, dhi);
+        float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
+        int dd = d0;
+#pragma unroll 4
+        for (; dd + 1 <= d1; dd += 2) {
+            const float g0 = g[(size_t)dd * M], g1 = g[(size_t)(dd + 1) * M];
+            const float2 x0 = x[(size_t)dd * M], x1 = x[(size_t)(dd + 1) * M];
+            b0.x = fmaf(g0, x0.x, b0.x); b0.y = fmaf(g0, x0.y, b0.y);
+            b1.x = fmaf(g1, x1.x, b1.x); b1.y = fmaf(g1, x1.y, b1.y);
         }
-        ev.x += be.x; ev.y += be.y;
-        od.x += bo.x; od.y += bo.y;
+        if (dd == d1) {
+            const float g0 = g[(size_t)dd * M];
+            const float2 x0 = x[(size_t)dd * M];
+            b0.x = fmaf(g0, x0.x, b0.x); b0.y = fmaf(g0, x0.y, b0.y);
+        }
+        a0.x += b0.x; a0.y += b0.y;
+        a1.x += b1.x; a1.y += b1.y;
     }
+    const bool swap = ((dlo - H) & 1) != 0;
+    const float2 ev = swap ? a1 : a0, od = swap ? a0 : a1;
     // odd offsets: s_i = 1 - s_o in the zone, 2 delta_o = 1 - 2 s_o; phase e^{-i pi m (1 - 2 s_o) / n}
     const int ds = 1 - 2 * rings[o].s;
     float sn, cs;

@@ -116,3 +116,31 @@ def test_fourier_argument_errors(sk):
         f.apply(x, out=x)                               # aliasing
     with pytest.raises(ValueError):
         f.apply(torch.zeros(1, g.npix - 4, device="cuda"))
+
+
+def test_wide_workload_sampled_outputs(sk):
+    # the 300' workload at Nside 1024: zone rings (Fourier form) on sampled outputs against
+    # the oracle; the other rings run the direct sums, whose FP32 accumulation over the
+    # ~2.3e4 neighbours of a pixel at this cut gives a few 1e-6 (bound 5e-6 there)
+    import torch
+    from inputs import WORKLOADS, make_maps, sample_indices
+    grp = WORKLOADS["n1024_wide"].groups[0]
+    ks = grp.kernel
+    V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
+    g = sk.Geometry(sk._ctx, grp.nside)
+    k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+    f = sk.FourierBelt(k)
+    info = f.info()
+    assert info["rings"] > 1000
+    x = make_maps(grp)
+    y = f.apply(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)[0]
+    sk._ctx.status()
+    n, st, s, z, sn = g.rings()
+    r0, r1 = info["first_ring"], info["first_ring"] + info["rings"]
+    p0, p1 = int(st[r0]), int(st[r1 - 1] + n[r1 - 1])
+    zone = p0 + sample_indices(p1 - p0, 600, 602)
+    other = sample_indices(g.npix, 1200, 603)
+    other = other[(other < p0) | (other >= p1)][:400]
+    xs = x[0].astype(np.float64)
+    assert rms_rel(y[zone], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=zone)) <= RMS_BOUND
+    assert rms_rel(y[other], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=other)) <= 5e-6
