@@ -20,11 +20,17 @@
 // synthesis with threads along r, the tabulation writes it with threads along r.
 //
 // Ring DFTs: the 2N + 1 rings of 4N pixels (equatorial zone) go through one
-// batched cuFFT R2C / C2R plan straight on the map; the polar-cap rings (4r
-// pixels, r < N) are summed directly against a twiddle table in shared memory
-// (their bins alias when 4r < 2L + 1, which the direct sum does by itself).
-// Phases: phi_{r,j} = pi (2j + s_r) / n_r, so F_r(m) = e^{-i pi m s_r / n_r} X_r(m)
-// with X_r the plain DFT.
+// batched cuFFT R2C / C2R plan straight on the map.  The polar-cap rings (n = 4r
+// pixels, r < N, all lengths) go through chirp-z transforms (Bluestein): with
+// jk = (j^2 + k^2 - (k-j)^2)/2, X(k) = sum_j x_j W^{jk} (W = e^{-2 pi i/n}) is
+// W^{k^2/2} times the convolution of x_j W^{j^2/2} with W^{-t^2/2}, done by FFTs
+// of a common length P >= n + K - 1 (K = min(n, L+1) bins: X is n-periodic, so
+// F(m) needs X(m mod n) only); the synthesis is the same with W conjugated,
+// after folding the m > n aliases onto m mod n.  The rings are grouped by P (a
+// power of two or three times one), each group one batched cuFFT plan; the FFTs
+// of the chirp filters are made once per handle.  Phases: phi_{r,j} =
+// pi (2j + s_r) / n_r, so F_r(m) = e^{-i pi m s_r / n_r} X_r(m) with X_r the plain
+// DFT; chirp phases use j^2 mod 2n in integers.
 #include <cufft.h>
 #include <math.h>
 
@@ -52,17 +58,30 @@ struct sk_harm {
     bool plans = false;
     float2 *d_X = nullptr;       // [(2N+1)][2N+1] bins of one map
     float *d_tmp = nullptr;      // [(2N+1) * 4N] synthesised zone of one map
-    // twiddles and ring phases, FP64-accurate, stored FP32 (built once per handle)
-    float2 *d_tw = nullptr;      // cap ring of 4r pixels: e^{-2 pi i k / 4r} at [2r(r-1) + k]
-    float2 *d_ph = nullptr;      // cap ring r: e^{-i pi m / 4r} at [(r-1)(L+1) + m]
     float2 *d_zph = nullptr;     // rings of 4N pixels with s = 1: e^{-i pi m / 4N}, m = 0..L
+    // chirp-z transforms of the polar-cap rings (see above): classes of rings sharing an FFT
+    // length, a row per (ring, hemisphere), the filters' FFTs, a work buffer per map
+    struct CzClass { int P, r0, cnt; long long woff; cufftHandle plan; };
+    std::vector<CzClass> cz;
+    struct CzRow *d_czrow = nullptr;   // [2 (N - 1)] rows of one map
+    float2 *d_czf = nullptr;           // per cap ring r: [analysis filter P][synthesis filter P], FFT'd
+    long long cz_n = 0;                // complex values of one map's work rows
+    long long cz_batch = 0;
+    float2 *d_czw = nullptr;           // [batch][cz_n]
+};
+
+// A chirp-z row: cap ring r (1-based, 4r pixels), hemisphere h (0 north: ring r - 1,
+// 1 south: ring nr - r, 0-based), FFT length P, offset of its work row (one map) and of its
+// ring's filters.
+struct CzRow {
+    int r, h, P;
+    int woff;
+    long long foff;
 };
 
 namespace {
 
 constexpr int HT = 256;
-constexpr int RESYNC = 32;     // ring DFTs: Horner blocks of RESYNC terms, exact twiddle per block
-constexpr int CH = 4;          // ring DFTs: independent chains per thread
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -110,99 +129,134 @@ __global__ void k_lambda(const double *theta, const double *lg2c, const long lon
 }
 
 // Twiddle and phase tables of the ring DFTs (FP64 sincospi, stored FP32).
-__global__ void k_ring_tables(int nside, int L, float2 *tw, float2 *ph, float2 *zph) {
-    const long long ntw = 2LL * nside * (nside - 1);               // sum of 4r, r < N
-    const long long nph = (long long)(nside - 1) * (L + 1);
-    const long long tot = ntw + nph + (L + 1);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
-         i += (long long)gridDim.x * blockDim.x) {
+// Phases of the zone rings with s = 1: e^{-i pi m / 4N}, m = 0..L (FP64, stored FP32).
+__global__ void k_zone_phase(int nside, int L, float2 *zph) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > L) return;
+    double sn, cs;
+    sincospi(-(double)m / (double)(4 * nside), &sn, &cs);
+    zph[m] = make_float2((float)cs, (float)sn);
+}
+
+// e^{i pi sign q / n} for q = t^2 mod 2n (exact integer reduction).
+__device__ __forceinline__ float2 chirp(long long t, int n, float sign) {
+    const long long q = (t * t) % (2LL * n);
+    float sn, cs;
+    sincospif(sign * (float)q / (float)n, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+// The chirp filters of cap ring rows (north rows only: the filters depend on n), in the
+// time domain at index t mod P: analysis e^{+i pi t^2/n} for t in [-(n-1), K-1],
+// synthesis e^{-i pi t^2/n} for t in [-(K-1), n-1]; FP64 phases.
+__global__ void k_cz_filters(const CzRow *rows, int L, float2 *f) {
+    const CzRow R = rows[blockIdx.x];
+    if (R.h != 0) return;
+    const int n = 4 * R.r, K = min(n, L + 1), P = R.P;
+    const long long none = -(1LL << 40);
+    float2 *fa = f + R.foff, *fs = fa + P;
+    // index i stands for t = i (the non-negative part) or t = i - P (the negative part);
+    // P >= n + K - 1 keeps the two parts apart
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const long long ta = i <= K - 1 ? i : (i >= P - (n - 1) ? (long long)i - P : none);
+        const long long ts = i <= n - 1 ? i : (i >= P - (K - 1) ? (long long)i - P : none);
         double sn, cs;
-        if (i < ntw) {
-            // ring r (1-based) owns [2r(r-1), 2r(r+1)): solve 2r(r-1) <= i
-            long long r = (long long)((1.0 + sqrt(1.0 + 2.0 * (double)i)) * 0.5);
-            while (2 * r * (r - 1) > i) --r;
-            while (2 * (r + 1) * r <= i) ++r;
-            const long long k = i - 2 * r * (r - 1);
-            sincospi(2.0 * (double)k / (double)(4 * r), &sn, &cs);
-            tw[i] = make_float2((float)cs, (float)-sn);
-        } else if (i < ntw + nph) {
-            const long long j = i - ntw;
-            const long long r = j / (L + 1) + 1, m = j % (L + 1);
-            sincospi(-(double)m / (double)(4 * r), &sn, &cs);
-            ph[j] = make_float2((float)cs, (float)sn);
-        } else {
-            const long long m = i - ntw - nph;
-            sincospi(-(double)m / (double)(4 * nside), &sn, &cs);
-            zph[m] = make_float2((float)cs, (float)sn);
+        float2 va = make_float2(0.f, 0.f), vs = make_float2(0.f, 0.f);
+        if (ta != none) {
+            sincospi((double)((ta * ta) % (2LL * n)) / (double)n, &sn, &cs);
+            va = make_float2((float)cs, (float)sn);
         }
+        if (ts != none) {
+            sincospi(-(double)((ts * ts) % (2LL * n)) / (double)n, &sn, &cs);
+            vs = make_float2((float)cs, (float)sn);
+        }
+        fa[i] = va;
+        fs[i] = vs;
     }
 }
 
-// Polar-cap rings: F_r(m) = e^{-i pi m s / n} sum_j x_j e^{-2 pi i m j / n}, m = 0..L.
-// One block per (cap ring, map); cap ring c < N - 1 is 0-based ring c, else its
-// southern mirror.  Twiddles w_k = e^{-2 pi i k / n} in shared memory.
-__global__ void k_dft_cap(const RingDev *rings, int nside, const float *x, long long stride, int L,
-                          int nr, const float2 *twg, const float2 *phg, float2 *F) {
-    extern __shared__ float2 sh[];
-    const int ncap = nside - 1;
-    const int c = blockIdx.x, b = blockIdx.y;
-    const int r = c < ncap ? c : nr - 1 - (c - ncap);
-    const RingDev R = rings[r];
-    const int n = R.n;
-    float2 *tw = sh;
-    float *xs = reinterpret_cast<float *>(sh + n);
-    const float *xr = x + (long long)b * stride + R.start;
-    const int r1 = n / 4;                            // cap ring of 4 r1 pixels (shift 1)
-    const float2 *twr = twg + 2LL * r1 * (r1 - 1);
-    const float2 *phr = phg + (long long)(r1 - 1) * (L + 1);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        tw[k] = twr[k];
-        xs[k] = xr[k];
+__device__ __forceinline__ int cz_ring(const CzRow &R, int nr) { return R.h == 0 ? R.r - 1 : nr - R.r; }
+
+// Analysis, before the FFT: a_j = x_j e^{-i pi j^2/n} (j < n), 0 up to P.
+__global__ void k_cz_a_pre(const CzRow *rows, const RingDev *rings, int nr, const float *x, long long stride,
+                           long long cz_n, float2 *w) {
+    const CzRow R = rows[blockIdx.x];
+    const int b = blockIdx.y, n = 4 * R.r;
+    const float *xr = x + (long long)b * stride + rings[cz_ring(R, nr)].start;
+    float2 *wr = w + (long long)b * cz_n + R.woff;
+    for (int j = threadIdx.x; j < R.P; j += blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        if (j < n) {
+            const float xv = xr[j];
+            const float2 c = chirp(j, n, -1.0f);
+            v = make_float2(xv * c.x, xv * c.y);
+        }
+        wr[j] = v;
     }
-    __syncthreads();
-    float2 *Fr = F + ((long long)b * nr + r) * (L + 1);
-    // CH multipoles per thread, their Horner chains interleaved (independent, one load of x_j each)
-    for (int mb = threadIdx.x; mb <= L; mb += CH * blockDim.x) {
-        // blocks of RESYNC pixels: S_b = sum_t x_{j0+t} w^t by Horner's rule (w = e^{-2 pi i m / n},
-        // rounding grows with the block length only), F += w^{j0} S_b with w^{j0} exact
-        int step[CH];
-        float2 rot[CH];
-        float re[CH], im[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int m = min(mb + c * (int)blockDim.x, L);
-            step[c] = m % n;
-            rot[c] = tw[step[c]];
-            re[c] = 0.0f;
-            im[c] = 0.0f;
-        }
-        for (int j0 = 0; j0 < n; j0 += RESYNC) {
-            const int j1 = min(j0 + RESYNC, n);
-            float hr[CH], hi[CH];
-#pragma unroll
-            for (int c = 0; c < CH; ++c) { hr[c] = xs[j1 - 1]; hi[c] = 0.0f; }
-            for (int j = j1 - 2; j >= j0; --j) {
-                const float xv = xs[j];
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const float nr = fmaf(hr[c], rot[c].x, fmaf(-hi[c], rot[c].y, xv));
-                    hi[c] = fmaf(hr[c], rot[c].y, hi[c] * rot[c].x);
-                    hr[c] = nr;
-                }
+}
+
+// Between the FFTs: w *= the row's filter (analysis: which = 0, synthesis: 1).
+__global__ void k_cz_mul(const CzRow *rows, const float2 *f, int which, long long cz_n, float2 *w) {
+    const CzRow R = rows[blockIdx.x];
+    const int b = blockIdx.y;
+    const float2 *fr = f + R.foff + (long long)which * R.P;
+    float2 *wr = w + (long long)b * cz_n + R.woff;
+    for (int k = threadIdx.x; k < R.P; k += blockDim.x) wr[k] = cmulf(wr[k], fr[k]);
+}
+
+// Analysis, after the inverse FFT: F(m) = e^{-i pi m/n} X(m mod n), X(k) = e^{-i pi k^2/n} conv(k) / P.
+__global__ void k_cz_a_post(const CzRow *rows, int nr, int L, long long cz_n, const float2 *w, float2 *F) {
+    const CzRow R = rows[blockIdx.x];
+    const int b = blockIdx.y, n = 4 * R.r;
+    const float2 *wr = w + (long long)b * cz_n + R.woff;
+    float2 *Fr = F + ((long long)b * nr + cz_ring(R, nr)) * (L + 1);
+    const float inv = 1.0f / (float)R.P;
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        const int k = m % n;
+        float2 v = cmulf(wr[k], chirp(k, n, -1.0f));
+        float sn, cs;
+        sincospif(-(float)(m % (2 * n)) / (float)n, &sn, &cs);
+        v = cmulf(v, make_float2(cs, sn));
+        Fr[m] = make_float2(v.x * inv, v.y * inv);
+    }
+}
+
+// Synthesis, before the FFT: c_k = sum_{m = k mod n, m <= L} g_m e^{i pi m/n} (doubled for m >= 1),
+// a'_k = c_k e^{i pi k^2/n} for k < K, 0 up to P.
+__global__ void k_cz_s_pre(const CzRow *rows, int nr, int L, long long cz_n, const float2 *G, float2 *w) {
+    const CzRow R = rows[blockIdx.x];
+    const int b = blockIdx.y, n = 4 * R.r, K = min(n, L + 1);
+    const float2 *Gr = G + ((long long)b * nr + cz_ring(R, nr)) * (L + 1);
+    float2 *wr = w + (long long)b * cz_n + R.woff;
+    for (int k = threadIdx.x; k < R.P; k += blockDim.x) {
+        float2 c = make_float2(0.f, 0.f);
+        if (k < K) {
+            for (int m = k; m <= L; m += n) {
+                float sn, cs;
+                sincospif((float)(m % (2 * n)) / (float)n, &sn, &cs);
+                float2 v = cmulf(Gr[m], make_float2(cs, sn));
+                if (m > 0) { v.x *= 2.0f; v.y *= 2.0f; }
+                c.x += v.x;
+                c.y += v.y;
             }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const float2 w0 = tw[(int)(((long long)step[c] * j0) % n)];
-                re[c] = fmaf(hr[c], w0.x, fmaf(-hi[c], w0.y, re[c]));
-                im[c] = fmaf(hr[c], w0.y, fmaf(hi[c], w0.x, im[c]));
-            }
+            c = cmulf(c, chirp(k, n, 1.0f));
         }
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int m = mb + c * (int)blockDim.x;
-            if (m > L) continue;
-            Fr[m] = cmulf(make_float2(re[c], im[c]), phr[m]);
-        }
+        wr[k] = c;
+    }
+}
+
+// Synthesis, after the inverse FFT: y_j (+)= Re(e^{i pi j^2/n} conv(j)) / P, j < n.
+__global__ void k_cz_s_post(const CzRow *rows, const RingDev *rings, int nr, long long cz_n, const float2 *w,
+                            float *y, long long stride, int accumulate) {
+    const CzRow R = rows[blockIdx.x];
+    const int b = blockIdx.y, n = 4 * R.r;
+    const float2 *wr = w + (long long)b * cz_n + R.woff;
+    float *yr = y + (long long)b * stride + rings[cz_ring(R, nr)].start;
+    const float inv = 1.0f / (float)R.P;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const float2 c = chirp(j, n, 1.0f), v = wr[j];
+        const float val = (v.x * c.x - v.y * c.y) * inv;
+        yr[j] = accumulate ? yr[j] + val : val;
     }
 }
 
@@ -322,75 +376,6 @@ __global__ void k_leg_synthesis(const float *lam, const long long *moff, const l
 }
 
 // Polar-cap rings: y_j (+)= Re G(0) + 2 Re sum_{m=1}^{L} G(m) e^{i pi m (2j + s) / n}.
-__global__ void k_idft_cap(const RingDev *rings, int nside, const float2 *G, int L, int nr, float *y,
-                           long long stride, int accumulate, const float2 *twg, const float2 *phg) {
-    extern __shared__ float2 sh[];
-    const int ncap = nside - 1;
-    const int c = blockIdx.x, b = blockIdx.y;
-    const int r = c < ncap ? c : nr - 1 - (c - ncap);
-    const RingDev R = rings[r];
-    const int n = R.n;
-    float2 *tw = sh;                                 // e^{+2 pi i k / n}
-    float2 *gs = sh + n;                             // G(m) e^{i pi m s / n}, doubled for m >= 1
-    const float2 *Gr = G + ((long long)b * nr + r) * (L + 1);
-    const int r1 = n / 4;                            // cap ring of 4 r1 pixels (shift 1)
-    const float2 *twr = twg + 2LL * r1 * (r1 - 1);
-    const float2 *phr = phg + (long long)(r1 - 1) * (L + 1);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const float2 w = twr[k];
-        tw[k] = make_float2(w.x, -w.y);              // e^{+2 pi i k / n}
-    }
-    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        const float2 p = phr[m];
-        float2 v = cmulf(Gr[m], make_float2(p.x, -p.y));   // G(m) e^{+i pi m / n}
-        if (m > 0) { v.x *= 2.0f; v.y *= 2.0f; }
-        gs[m] = v;
-    }
-    __syncthreads();
-    float *yr = y + (long long)b * stride + R.start;
-    // CH pixels per thread, their Horner chains interleaved (one load of g_m each)
-    for (int jb = threadIdx.x; jb < n; jb += CH * blockDim.x) {
-        // blocks of RESYNC multipoles: S_b = sum_t g_{m0+t} w^t by Horner's rule
-        // (w = e^{2 pi i j / n}), y += Re(w^{m0} S_b) with w^{m0} exact
-        int step[CH];
-        float2 rot[CH];
-        float acc[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int j = min(jb + c * (int)blockDim.x, n - 1);
-            step[c] = j;
-            rot[c] = tw[j];
-            acc[c] = 0.0f;
-        }
-        for (int m0 = 0; m0 <= L; m0 += RESYNC) {
-            const int m1 = min(m0 + RESYNC, L + 1);
-            float2 h[CH];
-#pragma unroll
-            for (int c = 0; c < CH; ++c) h[c] = gs[m1 - 1];
-            for (int m = m1 - 2; m >= m0; --m) {
-                const float2 g = gs[m];
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const float nr = fmaf(h[c].x, rot[c].x, fmaf(-h[c].y, rot[c].y, g.x));
-                    h[c].y = fmaf(h[c].x, rot[c].y, fmaf(h[c].y, rot[c].x, g.y));
-                    h[c].x = nr;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const float2 w0 = tw[(int)(((long long)step[c] * m0) % n)];
-                acc[c] = fmaf(h[c].x, w0.x, fmaf(-h[c].y, w0.y, acc[c]));
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int j = jb + c * (int)blockDim.x;
-            if (j >= n) continue;
-            yr[j] = accumulate ? yr[j] + acc[c] : acc[c];
-        }
-    }
-}
-
 // Equatorial zone before the C2R: bins X_r(m) = G_r(m) e^{i pi m s / n} for m <= L, 0 above.
 __global__ void k_zone_out(const RingDev *rings, int nside, const float2 *G, int L, int nr, long long b,
                            const float2 *zph, float2 *X) {
@@ -532,7 +517,10 @@ void free_harm(sk_harm *h) {
     if (h->plans) { cufftDestroy(h->p_r2c); cufftDestroy(h->p_c2r); }
     cudaFree(h->d_kl); cudaFree(h->d_lam); cudaFree(h->d_moff); cudaFree(h->d_aoff);
     cudaFree(h->d_F); cudaFree(h->d_a); cudaFree(h->d_X); cudaFree(h->d_tmp);
-    cudaFree(h->d_tw); cudaFree(h->d_ph); cudaFree(h->d_zph);
+    cudaFree(h->d_zph);
+    for (auto &c : h->cz)
+        if (c.plan) cufftDestroy(c.plan);
+    cudaFree(h->d_czrow); cudaFree(h->d_czf); cudaFree(h->d_czw);
     delete h;
 }
 
@@ -582,15 +570,45 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
     if (e == cudaSuccess) e = cudaMalloc(&d_lg2c, sizeof(double) * (L + 1));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_X, sizeof(float2) * (size_t)nb * nb);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_tmp, sizeof(float) * (size_t)nb * n4);
-    const long long ntw = 2LL * N * (N - 1), nph = (N - 1) * (long long)(L + 1);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_tw, sizeof(float2) * (size_t)std::max(1LL, ntw));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_ph, sizeof(float2) * (size_t)std::max(1LL, nph));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_zph, sizeof(float2) * (size_t)(L + 1));
     if (e == cudaSuccess) {
-        const long long tot = ntw + nph + L + 1;
-        k_ring_tables<<<(unsigned)std::min<long long>((tot + HT - 1) / HT, 65535), HT>>>((int)N, L, h->d_tw, h->d_ph,
-                                                                                           h->d_zph);
+        k_zone_phase<<<(L + HT) / HT, HT>>>((int)N, L, h->d_zph);
         e = cudaGetLastError();
+    }
+    // chirp-z classes of the cap rings r = 1 .. N-1: FFT length P = the smallest 2^a or 3 2^a
+    // that holds n + K - 1 (n = 4r, K = min(n, L+1)); rows north then south per class
+    std::vector<CzRow> rows;
+    if (e == cudaSuccess && N > 1) {
+        auto fft_len = [](long long need) {
+            long long p = 1;
+            while (p < need) p <<= 1;
+            const long long p3 = 3 * (p >> 2);           // 3 2^(a-2) between p/2 and p
+            return (int)(p3 >= need ? p3 : p);
+        };
+        long long woff = 0, foff = 0;
+        for (int r = 1; r < N;) {
+            const int n = 4 * r, P = fft_len(n + std::min(n, L + 1) - 1);
+            int r1 = r;
+            while (r1 + 1 < N && fft_len(4 * (r1 + 1) + std::min(4 * (r1 + 1), L + 1) - 1) == P) ++r1;
+            sk_harm::CzClass c{P, r, r1 - r + 1, woff, 0};
+            for (int hh = 0; hh < 2; ++hh)
+                for (int i = 0; i < c.cnt; ++i)
+                    rows.push_back(CzRow{r + i, hh, P, (int)(woff + ((long long)hh * c.cnt + i) * P),
+                                         foff + 2LL * i * P});
+            woff += 2LL * c.cnt * P;
+            foff += 2LL * c.cnt * P;
+            h->cz.push_back(c);
+            r = r1 + 1;
+        }
+        h->cz_n = woff;
+        if (woff >= (1LL << 31)) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_czrow, sizeof(CzRow) * rows.size());
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_czrow, rows.data(), sizeof(CzRow) * rows.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_czf, sizeof(float2) * (size_t)foff);
+        if (e == cudaSuccess) {
+            k_cz_filters<<<(unsigned)rows.size(), HT>>>(h->d_czrow, L, h->d_czf);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpy(h->d_kl, kl, sizeof(double) * (L + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_moff, moff.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice);
@@ -613,6 +631,18 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
     if (cr == CUFFT_SUCCESS) cr = cufftPlanMany(&h->p_c2r, 1, len, nullptr, 1, nb, nullptr, 1, n4, CUFFT_C2R, nb);
     if (cr != CUFFT_SUCCESS) { free_harm(h); return cufft_fail(cr, "sk_harmonic_create"); }
     h->plans = true;
+    // one C2C plan per chirp-z class (2 cnt rows of length P: one map's rows, or the class's
+    // filter pairs, which have the same layout); the filters go to the frequency domain now
+    for (auto &c : h->cz) {
+        int plen[1] = {c.P};
+        cr = cufftPlanMany(&c.plan, 1, plen, nullptr, 1, c.P, nullptr, 1, c.P, CUFFT_C2C, 2 * c.cnt);
+        if (cr != CUFFT_SUCCESS) { free_harm(h); return cufft_fail(cr, "sk_harmonic_create"); }
+        cufftComplex *fz = reinterpret_cast<cufftComplex *>(h->d_czf + c.woff);
+        cr = cufftExecC2C(c.plan, fz, fz, CUFFT_FORWARD);
+        if (cr != CUFFT_SUCCESS) { free_harm(h); return cufft_fail(cr, "sk_harmonic_create"); }
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { free_harm(h); return sk_fail(SK_ECUDA, "sk_harmonic_create: %s", cudaGetErrorString(e)); }
     *out = h;
     return SK_OK;
 }
@@ -627,6 +657,17 @@ extern "C" int sk_harmonic_destroy(sk_harm *h) {
 extern "C" int sk_harmonic_table_bytes(const sk_harm *h, int64_t *bytes) {
     if (!h || !bytes) return sk_fail(SK_EINVAL, "sk_harmonic_table_bytes: NULL argument");
     *bytes = h->lam_n * (int64_t)sizeof(float);
+    return SK_OK;
+}
+
+// The chirp-z FFTs (in place) of every class for `batch` maps.
+static int cz_fft(sk_harm *h, long long batch, int dir) {
+    for (long long b = 0; b < batch; ++b)
+        for (auto &c : h->cz) {
+            cufftComplex *w = reinterpret_cast<cufftComplex *>(h->d_czw + b * h->cz_n + c.woff);
+            cufftResult cr = cufftExecC2C(c.plan, w, w, dir);
+            if (cr != CUFFT_SUCCESS) return cufft_fail(cr, "sk_harmonic_apply");
+        }
     return SK_OK;
 }
 
@@ -657,15 +698,26 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
     const long long zone0 = g->h_rings[N - 1].start;     // first pixel of the equatorial zone
     if (cufftSetStream(h->p_r2c, st) != CUFFT_SUCCESS || cufftSetStream(h->p_c2r, st) != CUFFT_SUCCESS)
         return sk_fail(SK_ECUDA, "sk_harmonic_apply: cufftSetStream failed");
-    // ring DFTs
+    // ring DFTs: the cap rings by chirp-z transforms, the zone by one R2C per map
     const int ncap = 2 * (N - 1);
     if (ncap > 0) {
-        const size_t sm = sizeof(float2) * 4 * (N - 1) + sizeof(float) * 4 * (N - 1);
-        SK_CU(cudaFuncSetAttribute(k_dft_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        // enough threads that one pass of CH chains covers every multipole
-        const int thr = std::min(1024, ((L + CH) / CH + 31) / 32 * 32);
-        k_dft_cap<<<dim3(ncap, (unsigned)batch), thr, sm, st>>>(g->d_rings, N, d_in, map_stride, L, nr, h->d_tw,
-                                                                  h->d_ph, h->d_F);
+        if (batch > h->cz_batch) {
+            cudaFree(h->d_czw); h->d_czw = nullptr;
+            h->cz_batch = 0;
+            SK_CU(cudaMalloc(&h->d_czw, sizeof(float2) * (size_t)batch * h->cz_n));
+            h->cz_batch = batch;
+        }
+        for (auto &c : h->cz)
+            if (cufftSetStream(c.plan, st) != CUFFT_SUCCESS)
+                return sk_fail(SK_ECUDA, "sk_harmonic_apply: cufftSetStream failed");
+        const dim3 grid(ncap, (unsigned)batch);
+        k_cz_a_pre<<<grid, HT, 0, st>>>(h->d_czrow, g->d_rings, nr, d_in, map_stride, h->cz_n, h->d_czw);
+        SK_CU(cudaGetLastError());
+        if (int rc = cz_fft(h, batch, CUFFT_FORWARD)) return rc;
+        k_cz_mul<<<grid, HT, 0, st>>>(h->d_czrow, h->d_czf, 0, h->cz_n, h->d_czw);
+        SK_CU(cudaGetLastError());
+        if (int rc = cz_fft(h, batch, CUFFT_INVERSE)) return rc;
+        k_cz_a_post<<<grid, HT, 0, st>>>(h->d_czrow, nr, L, h->cz_n, h->d_czw, h->d_F);
         SK_CU(cudaGetLastError());
     }
     for (long long b = 0; b < batch; ++b) {
@@ -686,10 +738,15 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
     SK_CU(cudaGetLastError());
     // inverse ring DFTs
     if (ncap > 0) {
-        const size_t sm = sizeof(float2) * 4 * (N - 1) + sizeof(float2) * (L + 1);
-        SK_CU(cudaFuncSetAttribute(k_idft_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_idft_cap<<<dim3(ncap, (unsigned)batch), HT, sm, st>>>(g->d_rings, N, h->d_F, L, nr, d_out, map_stride,
-                                                                 accumulate, h->d_tw, h->d_ph);
+        const dim3 grid(ncap, (unsigned)batch);
+        k_cz_s_pre<<<grid, HT, 0, st>>>(h->d_czrow, nr, L, h->cz_n, h->d_F, h->d_czw);
+        SK_CU(cudaGetLastError());
+        if (int rc = cz_fft(h, batch, CUFFT_FORWARD)) return rc;
+        k_cz_mul<<<grid, HT, 0, st>>>(h->d_czrow, h->d_czf, 1, h->cz_n, h->d_czw);
+        SK_CU(cudaGetLastError());
+        if (int rc = cz_fft(h, batch, CUFFT_INVERSE)) return rc;
+        k_cz_s_post<<<grid, HT, 0, st>>>(h->d_czrow, g->d_rings, nr, h->cz_n, h->d_czw, d_out, map_stride,
+                                         accumulate);
         SK_CU(cudaGetLastError());
     }
     for (long long b = 0; b < batch; ++b) {
