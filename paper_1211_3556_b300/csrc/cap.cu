@@ -25,9 +25,10 @@
 //
 // Work item: (northern output ring, first base pixel) for CT base outputs,
 // CT / 2 threads, each owning two adjacent base outputs jA, jB = jA + 1; a
-// block runs two work items side by side (each half with its own named
-// barrier), so that they share one copy of the node table.  For every input
-// ring of the window a half stages four segments of H covering the union of its
+// block runs four work items side by side (two for the largest strip class),
+// each in its own slot with its own named barrier, so that they share one copy
+// of the node table.  For every input
+// ring of the window a work item stages four segments of H covering the union of its
 // CT windows -- the window pixels from a0 and from a0 + n/4, their reflections
 // from b0 and b0 + n/4 (read backwards) -- with 1-D bulk copies (TMA) issued by
 // eight lanes of its first warp: each segment splits into an even and an odd
@@ -56,20 +57,20 @@ constexpr int NTH = CT / 2;         // threads per work item: two adjacent base 
 static_assert(NTH == 128, "an item's strips are issued by its four warps in turn");
 // work items in flight per block (they share one node table): four where their strips fit
 template <int LS>
-__host__ __device__ constexpr int cap_halves() { return LS <= 640 ? 4 : 2; }
+__host__ __device__ constexpr int cap_slots() { return LS <= 640 ? 4 : 2; }
 // node tables of up to this many nodes are held as (value, slope) pairs, larger ones as values
 constexpr int PAIR_TABLE_NODES = 8192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every wait on a copy
 // strip buffers per work item: two (stage ring p + 1 while ring p is summed) where they fit
 template <int LS>
 __host__ __device__ constexpr int cap_bufs() { return LS <= 320 ? 2 : 1; }
-// dynamic shared memory: strips [halves][NB][4][LS] float4, then one mbarrier per
+// dynamic shared memory: strips [slots][NB][4][LS] float4, then one mbarrier per
 // strip buffer and the abort flag (16-byte multiple), then the node table
-__host__ __device__ constexpr size_t cap_strip_bytes(int ls, int nb, int halves) { return (size_t)halves * nb * 4 * ls * 16; }
-__host__ __device__ constexpr size_t cap_bar_bytes(int nb, int halves) { return ((size_t)halves * nb * 8 + 4 + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t cap_strip_bytes(int ls, int nb, int slots) { return (size_t)slots * nb * 4 * ls * 16; }
+__host__ __device__ constexpr size_t cap_bar_bytes(int nb, int slots) { return ((size_t)slots * nb * 8 + 4 + 15) / 16 * 16; }
 
-__device__ __forceinline__ void half_sync(int half) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(NTH) : "memory");
+__device__ __forceinline__ void slot_sync(int slot) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(NTH) : "memory");
 }
 
 // Bounded wait for a strip: false after WAIT_NS, or at once when another thread of the
@@ -241,38 +242,38 @@ __global__ void k_cap_sym(const JobDesc J, int r0) {
 }
 
 template <int LS, int MODE, typename TabT>
-__global__ void __launch_bounds__(NTH * cap_halves<LS>())
+__global__ void __launch_bounds__(NTH * cap_slots<LS>())
 k_conv_cap(const __grid_constant__ JobsArg A) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
-    constexpr int NB = cap_bufs<LS>(), HALVES = cap_halves<LS>();
+    constexpr int NB = cap_bufs<LS>(), SLOTS = cap_slots<LS>();
     extern __shared__ __align__(16) float4 sx[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(sx) + cap_strip_bytes(LS, NB, HALVES));
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + HALVES * NB);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(sx) + cap_strip_bytes(LS, NB, SLOTS));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + SLOTS * NB);
     // one node table per launch (every job of a launch uses the same kernel table):
     // (value, slope) pairs, or the values alone
-    TabT *stab = reinterpret_cast<TabT *>(reinterpret_cast<char *>(bars) + cap_bar_bytes(NB, HALVES));
+    TabT *stab = reinterpret_cast<TabT *>(reinterpret_cast<char *>(bars) + cap_bar_bytes(NB, SLOTS));
     if (threadIdx.x == 0) {
-        for (int b = 0; b < HALVES * NB; ++b) tc::mbar_init(tc::smem_u32(bars + b), 1);
+        for (int b = 0; b < SLOTS * NB; ++b) tc::mbar_init(tc::smem_u32(bars + b), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * HALVES) {
+    for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * SLOTS) {
         if constexpr (sizeof(TabT) == sizeof(float2)) stab[k] = A.j[0].tab[k];
         else stab[k] = A.j[0].tab[k].x;
     }
     __syncthreads();
-    const int half = threadIdx.x / NTH, t = threadIdx.x % NTH;
-    float4 *const sbuf = sx + half * NB * 4 * LS;
-    const uint32_t bar0 = tc::smem_u32(bars + half * NB);
+    const int slot = threadIdx.x / NTH, t = threadIdx.x % NTH;
+    float4 *const sbuf = sx + slot * NB * 4 * LS;
+    const uint32_t bar0 = tc::smem_u32(bars + slot * NB);
     uint32_t phase = 0;     // bit b: parity of the next phase of buffer b (the same in every thread)
     uint32_t pend = 0;      // bit b set while a copy this thread's warp issued into buffer b is not waited for
-    // work queue: each half takes the next item (items are ordered heaviest first), so the
-    // halves that drew light items take more of them and all finish together
-    __shared__ int s_item[HALVES];
+    // work queue: each slot takes the next item (items are ordered heaviest first), so the
+    // slots that drew light items take more of them and all finish together
+    __shared__ int s_item[SLOTS];
     for (;;) {
-        if (t == 0) s_item[half] = *abort_flag ? A.total : atomicAdd(A.queue, 1);
-        half_sync(half);
-        const int f = s_item[half];
+        if (t == 0) s_item[slot] = *abort_flag ? A.total : atomicAdd(A.queue, 1);
+        slot_sync(slot);
+        const int f = s_item[slot];
         if (f >= A.total) break;
         const JobDesc &J = A.j[sk_find_job(A, f)];
         const int local = f - J.flat_base;
@@ -320,7 +321,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
             const bool bulk = S.L < P.n_i;
             // every thread is done with ring p - 1: its buffer takes ring p + 1 (two
             // buffers) or ring p (one)
-            half_sync(half);
+            slot_sync(slot);
             if (NB == 2) {
                 if (p + 1 < p1) issue(p + 1, b ^ 1);
             } else if (bulk) {
@@ -340,7 +341,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 phase ^= 1u << b;
             } else {
                 copy_strip<LS>(xbuf, hmap + J.rings[P.ri].start, S, P, t);
-                half_sync(half);
+                slot_sync(slot);
             }
             if (ok && actA) {
                 int before, cnt;
@@ -394,8 +395,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 }
             }
         }
-        // the next item stages into this half's buffers: everyone must be done reading them
-        half_sync(half);
+        // the next item stages into this slot's buffers: everyone must be done reading them
+        slot_sync(slot);
         if (*abort_flag) continue;
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
@@ -410,8 +411,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
 }
 
 size_t cap_smem(int LS, int nt, bool pairs) {
-    const int nb = LS <= 320 ? 2 : 1, halves = LS <= 640 ? 4 : 2;     // cap_bufs, cap_halves
-    return cap_strip_bytes(LS, nb, halves) + cap_bar_bytes(nb, halves) + (size_t)nt * (pairs ? 8 : 4);
+    const int nb = LS <= 320 ? 2 : 1, slots = LS <= 640 ? 4 : 2;     // cap_bufs, cap_slots
+    return cap_strip_bytes(LS, nb, slots) + cap_bar_bytes(nb, slots) + (size_t)nt * (pairs ? 8 : 4);
 }
 
 int max_nt(const JobsArg &a) {
@@ -425,7 +426,7 @@ cudaError_t launch_t(const JobsArg &a, int nt, int grid, cudaStream_t st) {
     const size_t smem = cap_smem(LS, nt, sizeof(TabT) == sizeof(float2));
     cudaError_t e = cudaFuncSetAttribute(k_conv_cap<LS, MODE, TabT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_cap<LS, MODE, TabT><<<grid, NTH * cap_halves<LS>(), smem, st>>>(a);
+    k_conv_cap<LS, MODE, TabT><<<grid, NTH * cap_slots<LS>(), smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -441,7 +442,7 @@ int occupancy_t(int nt) {
     const size_t smem = cap_smem(LS, nt, sizeof(TabT) == sizeof(float2));
     cudaFuncSetAttribute(k_conv_cap<LS, MODE, TabT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE, TabT>, NTH * cap_halves<LS>(), smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_cap<LS, MODE, TabT>, NTH * cap_slots<LS>(), smem);
     return nb;
 }
 
