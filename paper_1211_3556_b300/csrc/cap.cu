@@ -31,7 +31,8 @@
 // ring of the window a work item stages four segments of H covering the union of its
 // CT windows -- the window pixels from a0 and from a0 + n/4, their reflections
 // from b0 and b0 + n/4 (read backwards) -- with 1-D bulk copies (TMA) issued by
-// eight lanes of its first warp: each segment splits into an even and an odd
+// eight lanes of one of its warps (the four take turns): each segment splits
+// into an even and an odd
 // part, contiguous in H up to one wrap past phi = 2 pi.  Two buffers per item:
 // ring p + 1 is copied while ring p is summed (an mbarrier per buffer counts its
 // bytes; one named barrier per ring frees the buffer of ring p - 1).  Rings whose

@@ -127,7 +127,7 @@ __global__ void k_fmix(const RingDev *rings, const float *__restrict__ G, const 
         const int d1 = min(d0 + 31, dhi);
         float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
         int dd = d0;
-#pragma unroll 4
+#pragma unroll 8
         for (; dd + 1 <= d1; dd += 2) {
             const float g0 = g[(size_t)dd * M], g1 = g[(size_t)(dd + 1) * M];
             const float2 x0 = x[(size_t)dd * M], x1 = x[(size_t)(dd + 1) * M];
