@@ -366,8 +366,9 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     const float4 *x0 = xbuf + split_index<LS>(pA), *x1 = xbuf + split_index<LS>(pA + 1);
                     const float4 *r0 = xr0 + split_index<LS>(o0), *r1 = xr0 + split_index<LS>(o0 - 1);
                     float2 q = make_float2(qA0, qA0 - dqi);   // q of pixel m for outputs (A, B)
+                    int m = 0;
 #pragma unroll 1
-                    for (int m = 0; m < cnt_u; m += 2) {
+                    for (; m + 1 < cnt_u; m += 2) {
                         const int i = m >> 1;
                         const float2 q1 = __fadd2_rn(q, f2(dqo));
                         const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
@@ -375,10 +376,14 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                         q = __fadd2_rn(q1, f2(dqo));
                         mac16<LS>(accA, w0.x, x0, r0, i);
                         mac16<LS>(accB, w0.y, x0, r0, i);
-                        if (m + 1 < cnt_u) {
-                            mac16<LS>(accA, w1.x, x1, r1, i);
-                            mac16<LS>(accB, w1.y, x1, r1, i);
-                        }
+                        mac16<LS>(accA, w1.x, x1, r1, i);
+                        mac16<LS>(accB, w1.y, x1, r1, i);
+                    }
+                    if (m < cnt_u) {                           // an odd count: the last pixel alone
+                        const int i = m >> 1;
+                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
+                        mac16<LS>(accA, w0.x, x0, r0, i);
+                        mac16<LS>(accB, w0.y, x0, r0, i);
                     }
                 } else {
                     // windows may be whole rings: restrict each output to its own window
