@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from inputs import ARCMIN, WORKLOADS, make_maps, npix_of, sample_indices  # noqa: E402
+from inputs import ARCMIN, WORKLOADS, Group, make_maps, npix_of, sample_indices  # noqa: E402
 
 METRIC = "pixel-pairs/s and ms/map at Nside 2048, plain vs batched, rms err vs FP64"
 UNIT = "pixel-pairs/s"
@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-split", action="store_true", help="skip the harmonic-half (split) side measurement")
     ap.add_argument("--no-fourier", action="store_true", help="skip the wide-cut (ring-pair Fourier) side measurement")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint + table gradient) side measurement")
     return ap.parse_args()
 
 
@@ -421,6 +422,28 @@ def run_ours(args):
                    "zone_rms_rel_fourier_vs_direct": float(torch.linalg.norm(a - b) / torch.linalg.norm(b))}
         del fw, xw, yf, yd
 
+    # gradients (16 maps at Nside 1024, 30'): the forward sums, the adjoint (the same gather: the
+    # operator is symmetric) and the table gradient (per pair, FP64 node coordinates)
+    grad = None
+    if not args.no_grad and args.workload == "n2048_plain":
+        grp = WORKLOADS["n1024x16_grad"].groups[0]
+        gg, kg = build_operator(sk, ctx, grp)
+        xg = torch.from_numpy(make_maps(grp)).cuda()
+        gy = torch.from_numpy(make_maps(Group(grp.nside, grp.batch, grp.kernel, grp.seed + 1))).cuda()
+        yg, gx = torch.empty_like(xg), torch.empty_like(xg)
+        gt = torch.empty(kg.n_nodes, device="cuda")
+        pg = kg.count_pairs() * grp.batch
+        ng = max(3, min(args.steps, 5))
+        ms_fwd = time_steps(torch, lambda: sk.convolve(kg, xg, out=yg), ng, 1, barrier)
+        ms_adj = time_steps(torch, lambda: sk.convolve_adjoint(kg, gy, out=gx), ng, 1, barrier)
+        ms_tab = time_steps(torch, lambda: sk.grad_table(kg, xg, gy, out=gt), ng, 1, barrier)
+        grad = {"workload": "n1024x16_grad", "unit": UNIT, "maps": grp.batch,
+                "forward": {"ms_per_step": ms_fwd, "value": pg / (ms_fwd * 1e-3)},
+                "adjoint": {"ms_per_step": ms_adj, "value": pg / (ms_adj * 1e-3)},
+                "table_gradient": {"ms_per_step": ms_tab, "value": pg / (ms_tab * 1e-3)},
+                "step_ms": ms_fwd + ms_adj + ms_tab}
+        del xg, gy, yg, gx
+
     o0 = ops[0]
     y0 = o0["y"][0].cpu().numpy()
     cpu_baseline, rms = None, None
@@ -453,6 +476,7 @@ def run_ours(args):
             "batched": batched,
             "split": split,
             "fourier": fourier,
+            "grad": grad,
             "cpu_baseline": cpu_baseline,
             "context": "paper: GTX 480 + 1 Core2 core, split convolution >10x faster than a full "
                        "single-core SHT convolution (eq. 3 model: 2.89 s at theta_cut 20')",

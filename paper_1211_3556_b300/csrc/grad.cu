@@ -3,13 +3,22 @@
 // With y_o = dOmega sum_i K_lin(gamma_oi) x_i and K_lin = V_k (1 - f) + V_{k+1} f
 // (linear interpolation of the tabulated kernel, Sec. 3),
 //   dL/dV_n = dOmega sum_b sum_o gy_bo sum_{i in cut} x_bi [(1 - f) delta_{n,k} + f delta_{n,k+1}],
-// a binned scatter-add over all in-cut pairs.  One thread per output pixel
-// walks its window like the per-pair forward path.  Per pair it sums
-// v = sum_b gy_bo x_bi over the maps (FP32), takes (k, f) from FP64 chord
+// a binned scatter-add over all in-cut pairs.  (k, f) come from FP64 chord
 // arithmetic (an FP32 node coordinate u would carry an absolute error near
-// u * 6e-8, which the bins see undamped), and adds (1-f) v and f v into FP32
-// bins in shared memory.  Each persistent block adds its bins into an FP64
-// accumulator in global memory; a last kernel scales by dOmega and rounds.
+// u * 6e-8, which the bins see undamped); the pair sums v are FP32.  The work
+// follows the forward paths' structure:
+//  * belt rings: every pair (o, j) - (i, j + e) of a ring pair has the same (k, f),
+//    so the pairs of one (o, i, e) add up to one cross-correlation
+//    C_oi(e) = sum_b sum_j gy_bo[j] x_bi[j + e] before touching the bins
+//    (k_grad_belt: a block per output ring, lanes over offsets, warps over pixels);
+//  * cap rings: a base pair and its 16 symmetric images share (k, f), so one FP64
+//    evaluation serves 16 products per map (k_grad_cap, inputs from the caps'
+//    symmetric copy, four maps per pass);
+//  * the remaining rings: one thread per output pixel walks its window
+//    (k_grad_general).
+// Each block adds its bins (FP32 in shared memory, or FP64 directly for the belt's
+// few values) into an FP64 accumulator in global memory; a last kernel scales by
+// dOmega and rounds.
 #include "skconv.h"
 #include "skconv_internal.cuh"
 #include "skconv_launch.h"
@@ -75,6 +84,198 @@ k_grad_general(const __grid_constant__ JobsArg A, const float *__restrict__ gy, 
         if (bins[k] != 0.0f) atomicAdd(&acc[k], (double)bins[k]);
 }
 
+// Belt rings, step 1: a block per (belt output ring o, map b).  For every input ring i of
+// o's window and every offset e = EMIN + c of the belt's offset grid (c < WPM),
+// C[o][i][c] += sum_j gy_bo[j] x_bi[j + e]: lanes over c (and, when WPM <= 16, two pixel
+// halves per warp), warps over pixels, partial sums flushed every 128 pixels, the block's
+// parts summed in shared memory and added to C (FP32 atomics, one per map).  Pixels in
+// segments of SEG.
+constexpr int GW = 8;           // warps per belt-gradient block
+constexpr int SEG = 8192;       // pixels of a ring staged at once
+__global__ void __launch_bounds__(32 * GW)
+k_grad_belt(const JobDesc J, const float *__restrict__ gy, float *C) {
+    extern __shared__ float sm[];
+    const int rb = blockIdx.x, b = blockIdx.y;
+    if (rb >= J.nb) return;
+    const int n = J.n4, o = J.b_lo + rb;
+    const int p0 = J.pair_off[o], np = J.pair_off[o + 1] - p0;
+    const int R2 = 2 * J.HM + 1;
+    const int WC = J.WPM <= 16 ? 16 : 32;             // offsets per lane group
+    const int NG = 32 / WC;                           // lane groups per warp
+    const int NPART = GW * NG;                        // pixel parts of a segment
+    const int segn = min(n, SEG);
+    float *gys = sm;                                  // [SEG]
+    float *xs = gys + SEG;                            // [SEG + WPM + 32]
+    float *red = xs + SEG + J.WPM + 32;               // [NPART][WC]
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int cl = lane % WC, part = warp * NG + lane / WC;
+    const float *gyo = gy + (long long)b * J.stride + J.rings[o].start;
+    for (int cb = 0; cb < J.WPM; cb += WC) {
+        const int c = cb + cl;
+        for (int pp = 0; pp < np; ++pp) {
+            const float *xi = J.x + (long long)b * J.stride + J.rings[J.pairs[p0 + pp].ri].start;
+            float tot = 0.0f;
+            for (int s0 = 0; s0 < n; s0 += segn) {
+                const int sn = min(segn, n - s0);
+                __syncthreads();                      // the previous segment is consumed
+                if (pp == 0 || n > segn)
+                    for (int q = t; q < sn; q += blockDim.x) gys[q] = gyo[s0 + q];
+                for (int q = t; q < sn + WC + cb; q += blockDim.x) {
+                    int pos = s0 + q + J.EMIN;               // in (-n, 2n)
+                    pos = pos < 0 ? pos + n : (pos >= n ? pos - n : pos);
+                    xs[q] = xi[pos];
+                }
+                __syncthreads();
+                const int j0 = (part * sn / NPART) & ~3, j1 = part + 1 == NPART ? sn : ((part + 1) * sn / NPART) & ~3;
+                for (int jb = j0; jb < j1; jb += 128) {
+                    const int je = min(jb + 128, j1);
+                    // four independent chains (the FMA latency, not the issue rate, bounds one)
+                    // (parts start at multiples of 4 pixels: gy comes as one broadcast float4)
+                    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+                    int j = jb;
+                    for (; j + 3 < je; j += 4) {
+                        const float4 g4 = *reinterpret_cast<const float4 *>(gys + j);
+                        a0 = fmaf(g4.x, xs[j + c], a0);
+                        a1 = fmaf(g4.y, xs[j + 1 + c], a1);
+                        a2 = fmaf(g4.z, xs[j + 2 + c], a2);
+                        a3 = fmaf(g4.w, xs[j + 3 + c], a3);
+                    }
+                    for (; j < je; ++j) a0 = fmaf(gys[j], xs[j + c], a0);
+                    tot += (a0 + a1) + (a2 + a3);
+                }
+            }
+            red[part * WC + cl] = tot;
+            __syncthreads();
+            if (t < WC && cb + t < J.WPM) {
+                float v = 0.0f;
+                for (int q = 0; q < NPART; ++q) v += red[q * WC + t];
+                atomicAdd(&C[((size_t)rb * R2 + pp) * J.WPM + cb + t], v);
+            }
+        }
+    }
+}
+
+// Belt rings, step 2: the pairs' node intervals (FP64, once per call) and the bins: a
+// thread per (belt ring, input ring, offset) of C.
+__global__ void k_grad_belt_bins(const JobDesc J, const float *C, double *acc) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int R2 = 2 * J.HM + 1;
+    if (idx >= (long long)J.nb * R2 * J.WPM) return;
+    const int c = (int)(idx % J.WPM), pp = (int)((idx / J.WPM) % R2), rb = (int)(idx / ((long long)J.WPM * R2));
+    const int o = J.b_lo + rb;
+    const int p0 = J.pair_off[o];
+    if (pp >= J.pair_off[o + 1] - p0) return;
+    const PairInfo P = J.pairs[p0 + pp];
+    const int s_o = J.rings[o].s;
+    const int e = J.EMIN + c;
+    const int ec = (s_o + 1 - P.s_i) >> 1;            // offset of the nearest input pixel
+    if (P.W < 0 || e < ec - P.W || e > ec + P.W) return;
+    const double2 ab = J.ab64[p0 + pp];
+    int k;
+    float fr;
+    if (pair_kf64((double)(2 * e + P.s_i - s_o) * (SK_PI / (2.0 * (double)J.n4)), ab.x, ab.y, J.kp, J.kd, k, fr)) {
+        const double v = (double)C[idx];
+        atomicAdd(&acc[k], v * (1.0 - (double)fr));
+        atomicAdd(&acc[k + 1], v * (double)fr);
+    }
+}
+
+__device__ __forceinline__ float dot4(const float *g, float4 h) {
+    return fmaf(g[0], h.x, fmaf(g[1], h.y, fmaf(g[2], h.z, g[3] * h.w)));
+}
+
+// Cap rings: a thread per base output of a cap item (the forward's items: 256 base
+// outputs), maps four at a time.  The 16 images of the base output (quarter turns,
+// hemispheres, reflection; 8 on a symmetry axis) take gy_b from the map, the images of
+// the input pixel a come from the symmetric copy H (H[a], H[a + n/4], and the reflection
+// b = n/4 - s - a: H[b], H[b + n/4]), in the pairing the forward kernel uses; one FP64
+// (k, f) per base pair.
+constexpr int GC = 4;           // maps per pass of the cap gradient
+__global__ void __launch_bounds__(256)
+k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, double *acc) {
+    extern __shared__ float bins[];
+    const JobDesc &J = A.j[0];
+    const int nt = J.kp.nt;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) bins[k] = 0.0f;
+    __syncthreads();
+    for (int f = blockIdx.x; f < J.n_items; f += gridDim.x) {
+        const int4 it = J.items[f];
+        const int ro = it.x, jo = it.y + (int)threadIdx.x;
+        const RingDev R = J.rings[ro];
+        const int Qo = R.n >> 2;
+        const int T = R.s ? (Qo + 1) / 2 : Qo / 2 + 1;
+        if (jo >= T) continue;
+        const int jr = Qo - jo - R.s;
+        const bool refl = jr < Qo && jr >= T;
+        const long long so = R.start, ss = J.rings[J.nr - 1 - ro].start;
+        for (int b0 = 0; b0 < J.batch; b0 += GC) {
+            const int nb = min(GC, J.batch - b0);
+            float g[GC][16];
+#pragma unroll
+            for (int u = 0; u < GC; ++u) {
+                // maps past the batch, and the reflected images of an output on a symmetry
+                // axis, get gy = 0 (their loads read the base output, which exists)
+                const float *yb = gy + (long long)(b0 + (u < nb ? u : 0)) * J.stride;
+                const float ok = u < nb ? 1.0f : 0.0f;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float o2 = (r == 0 || refl) ? ok : 0.0f;
+                    const int j = (r == 1 && refl) ? jr : jo;
+                    g[u][8 * r + 0] = o2 * yb[so + j];
+                    g[u][8 * r + 1] = o2 * yb[so + j + 2 * Qo];
+                    g[u][8 * r + 2] = o2 * yb[ss + j];
+                    g[u][8 * r + 3] = o2 * yb[ss + j + 2 * Qo];
+                    g[u][8 * r + 4] = o2 * yb[so + j + Qo];
+                    g[u][8 * r + 5] = o2 * yb[so + j + 3 * Qo];
+                    g[u][8 * r + 6] = o2 * yb[ss + j + Qo];
+                    g[u][8 * r + 7] = o2 * yb[ss + j + 3 * Qo];
+                }
+            }
+            for (int p = J.pair_off[ro]; p < J.pair_off[ro + 1]; ++p) {
+                const PairInfo P = J.pairs[p];
+                const double2 ab = J.ab64[p];
+                const double c0 = SK_PI / (2.0 * (double)P.n_i * (double)R.n);
+                const int Qi = P.n_i >> 2;
+                const float4 *h0 = J.hx + (long long)b0 * J.hstride + J.rings[P.ri].start;
+                int jlo, cnt;
+                pair_window(jo, R.n, R.s, P, jlo, cnt);
+                long long q = pair_q(jlo, jo, R.n, R.s, P);
+                // pixels a = jlo + m, a + n/4 (rising) and their reflections n/4 - s - a,
+                // + n/4 (falling), kept reduced mod n
+                const int n_i = P.n_i, hn = n_i >> 1;
+                int pa = jlo % n_i; if (pa < 0) pa += n_i;
+                int pb = pa + Qi; if (pb >= n_i) pb -= n_i;
+                int pc = (Qi - P.s_i - jlo) % n_i; if (pc < 0) pc += n_i;
+                int pd = pc + Qi; if (pd >= n_i) pd -= n_i;
+                for (int m = 0; m < cnt; ++m, q += 2 * R.n) {
+                    const int ia = (pa & 1) * hn + (pa >> 1), ib = (pb & 1) * hn + (pb >> 1);
+                    const int ic = (pc & 1) * hn + (pc >> 1), id = (pd & 1) * hn + (pd >> 1);
+                    pa = pa + 1 == n_i ? 0 : pa + 1;
+                    pb = pb + 1 == n_i ? 0 : pb + 1;
+                    pc = pc == 0 ? n_i - 1 : pc - 1;
+                    pd = pd == 0 ? n_i - 1 : pd - 1;
+                    int k;
+                    float fr;
+                    if (!pair_kf64((double)q * c0, ab.x, ab.y, J.kp, J.kd, k, fr)) continue;
+                    float v = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < GC; ++u) {
+                        if (u >= nb) break;
+                        const float4 *h = h0 + (long long)u * J.hstride;
+                        v += dot4(&g[u][0], __ldg(h + ia)) + dot4(&g[u][4], __ldg(h + ib)) +
+                             dot4(&g[u][8], __ldg(h + ic)) + dot4(&g[u][12], __ldg(h + id));
+                    }
+                    atomicAdd(&bins[k], v - fr * v);
+                    atomicAdd(&bins[k + 1], fr * v);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nt; k += blockDim.x)
+        if (bins[k] != 0.0f) atomicAdd(&acc[k], (double)bins[k]);
+}
+
 __global__ void k_grad_finish(const double *acc, int nt, double scale, float *out) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nt) out[k] = (float)(acc[k] * scale);
@@ -89,6 +290,31 @@ cudaError_t sk_launch_grad_general(const JobsArg &a, const float *gy, double *ac
     cudaError_t e = cudaFuncSetAttribute(k_grad_general, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_grad_general<<<grid, 128, smem, st>>>(a, gy, acc);
+    return cudaGetLastError();
+}
+
+size_t sk_grad_belt_floats(const JobDesc &j) { return (size_t)j.nb * (2 * j.HM + 1) * j.WPM; }
+
+cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, cudaStream_t st) {
+    if (j.nb <= 0 || j.batch <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * sk_grad_belt_floats(j), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(float) * ((size_t)2 * SEG + j.WPM + 32 + GW * 32);
+    e = cudaFuncSetAttribute(k_grad_belt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_grad_belt<<<dim3(j.nb, j.batch), 32 * GW, smem, st>>>(j, gy, C);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long nbins = (long long)sk_grad_belt_floats(j);
+    k_grad_belt_bins<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(j, C, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, cudaStream_t st) {
+    if (a.n_jobs <= 0 || a.j[0].batch <= 0 || a.j[0].n_items <= 0) return cudaSuccess;
+    const size_t smem = (size_t)a.j[0].kp.nt * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_grad_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_grad_cap<<<grid, 256, smem, st>>>(a, gy, acc);
     return cudaGetLastError();
 }
 

@@ -710,17 +710,71 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
     return SK_OK;
 }
 
+// Table-gradient workspace: FP64 bins, the caps' symmetric copy of x, the belt's
+// ring-pair sums.
+static size_t grad_bins_bytes(const sk_kern *k) { return (sizeof(double) * k->nt + 255) & ~(size_t)255; }
+static size_t grad_belt_bytes(const sk_kern *k) {
+    if (!k->plan_ok || k->nb == 0) return 0;
+    return (sizeof(float) * (size_t)k->nb * (2 * k->HM + 1) * k->WPM + 255) & ~(size_t)255;
+}
+size_t sk_grad_workspace_bytes(const sk_kern *k, long long batch) {
+    return grad_bins_bytes(k) + sk_sym_bytes(k, batch) + grad_belt_bytes(k);
+}
+
 int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,
                 long long stride, float *out, double *acc, cudaStream_t st) {
     SK_CU(cudaMemsetAsync(acc, 0, sizeof(double) * k->nt, st));
     if (batch > 0) {
         SkJob jb{k, x, nullptr, batch, stride};
-        Batcher b;
-        b.add(base_desc(jb), k->d_items_all, k->n_items_all);
-        b.a.status = ctx->d_status;
-        cudaEvent_t ev = sk_prof_begin(ctx, st);
-        SK_CU(sk_launch_grad_general(b.a, gy, acc, grid_for(b.a.total, 8, ctx->num_sms), st));
-        sk_prof_end(ctx, "grad_general", ev, st);
+        auto general = [&](const int4 *items, int n_items) -> int {
+            if (n_items <= 0) return SK_OK;
+            Batcher b;
+            b.add(base_desc(jb), items, n_items);
+            b.a.status = ctx->d_status;
+            cudaEvent_t ev = sk_prof_begin(ctx, st);
+            SK_CU(sk_launch_grad_general(b.a, gy, acc, grid_for(b.a.total, 8, ctx->num_sms), st));
+            sk_prof_end(ctx, "grad_general", ev, st);
+            return SK_OK;
+        };
+        if (!k->plan_ok) {
+            if (int rc = general(k->d_items_all, k->n_items_all)) return rc;
+        } else {
+            // belt rings: ring-pair cross-correlations
+            if (k->nb > 0) {
+                JobDesc d = belt_desc(jb, nullptr);
+                float *C = reinterpret_cast<float *>(reinterpret_cast<char *>(acc) + grad_bins_bytes(k) +
+                                                     sk_sym_bytes(k, batch));
+                cudaEvent_t ev = sk_prof_begin(ctx, st);
+                SK_CU(sk_launch_grad_belt(d, gy, C, acc, st));
+                sk_prof_end(ctx, "grad_belt", ev, st);
+            }
+            // cap rings: symmetric base pairs over x's symmetric copy (after the FP64 bins)
+            if (k->sym_hi > 0) {
+                JobDesc d = base_desc(jb);
+                d.hx = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + grad_bins_bytes(k));
+                d.hstride = k->sym_stride;
+                cudaEvent_t ev = sk_prof_begin(ctx, st);
+                SK_CU(sk_launch_cap_sym(d, 0, k->sym_hi, st));
+                sk_prof_end(ctx, "cap_sym", ev, st);
+                for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+                    for (int v = 0; v < 2; ++v) {
+                        if (k->n_items_cap[c][v] == 0) continue;
+                        JobsArg a;
+                        memset(&a, 0, sizeof a);
+                        a.j[0] = d;
+                        a.j[0].items = k->d_items_cap[c][v];
+                        a.j[0].n_items = k->n_items_cap[c][v];
+                        a.n_jobs = 1;
+                        a.total = k->n_items_cap[c][v];
+                        a.status = ctx->d_status;
+                        ev = sk_prof_begin(ctx, st);
+                        SK_CU(sk_launch_grad_cap(a, gy, acc, grid_for(a.total, 4, ctx->num_sms), st));
+                        sk_prof_end(ctx, "grad_cap", ev, st);
+                    }
+            }
+            // the other rings: per pixel
+            if (int rc = general(k->d_items_gen, k->n_items_gen)) return rc;
+        }
     }
     SK_CU(sk_launch_grad_finish(acc, k->nt, 4.0 * SK_PI / (double)k->g->npix, out, st));
     return SK_OK;

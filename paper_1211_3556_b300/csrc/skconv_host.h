@@ -154,6 +154,9 @@ int sk_plan_bands(sk_kern *k);
 // symmetric copies of every job's maps for the caps.
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n);
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st);
+// Table gradient: `acc` is the start of sk_grad_workspace_bytes(k, batch) bytes of
+// workspace (the FP64 bins, then the caps' symmetric copy of x).
+size_t sk_grad_workspace_bytes(const sk_kern *k, long long batch);
 int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,
                 long long stride, float *out, double *acc, cudaStream_t st);
 

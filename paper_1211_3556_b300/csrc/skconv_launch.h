@@ -123,3 +123,9 @@ int sk_cap_items_per_block(int ls);   // cap work items a block holds at a time 
 cudaError_t sk_launch_grad_general(const JobsArg &a, const float *gy, double *acc, int grid,
                                    cudaStream_t st);
 cudaError_t sk_launch_grad_finish(const double *acc, int nt, double scale, float *out, cudaStream_t st);
+// belt rings by ring-pair cross-correlations (j: the belt fields, x, batch, stride) into the
+// FP32 sums C (sk_grad_belt_floats(j) floats), then the bins
+size_t sk_grad_belt_floats(const JobDesc &j);
+cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, cudaStream_t st);
+// cap rings by symmetric base pairs (a.j[0]: the cap items, x's symmetric copy in hx)
+cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, cudaStream_t st);
