@@ -152,6 +152,18 @@ int sk_convolve(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
 int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
                      int64_t batch, int64_t map_stride, int path, void *stream);
 
+/* The outputs of rings [ring_lo, ring_hi) (0-based RING rings) of y = A x, for a
+ * ring-band decomposition of one map over several devices (each device owns a band
+ * of output rings and needs the input rings within theta_cut of it, a halo; the
+ * rest of d_in may hold anything).  Runs the work items that write those rings;
+ * items that also write rings outside the range (a belt ring group across its
+ * edge, the other hemisphere of a cap ring) write values there that depend on
+ * inputs outside the halo: the caller keeps only its band.  In the range the
+ * results are bit-identical to sk_convolve.  Arguments as sk_convolve.
+ * Errors: SK_EINVAL (also a ring range outside [0, rings)), SK_ENOMEM, SK_ECUDA. */
+int sk_convolve_rings(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
+                      int64_t map_stride, int ring_lo, int ring_hi, void *stream);
+
 /* x_bar = A^T y_bar.  The kernel is radial, so A_oi = dOmega K_lin(gamma(o,i))
  * is symmetric and the transpose, written as a gather over the inputs of each
  * output, is the forward gather.  Same arguments and errors as sk_convolve. */

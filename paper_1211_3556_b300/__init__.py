@@ -65,6 +65,7 @@ def _declare(L):
         "sk_profile_read": (I, [P, I, P, P, P, ctypes.POINTER(I)]),
         "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
         "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
+        "sk_convolve_rings": (I, [P, P, P, P, I64, I64, I, I, P]),
         "sk_convolve_adjoint": (I, [P, P, P, P, I64, I64, P]),
         "sk_grad_table": (I, [P, P, P, P, I64, I64, P, P]),
         "sk_grad_table_noalloc": (I, [P, P, P, P, I64, I64, P, P]),
@@ -314,6 +315,23 @@ def convolve(kern: Kernel, x, out=None, path: int = PATH_AUTO, stream=None):
         raise ValueError("out must match x in shape and strides")
     _check(lib().sk_convolve_path(kern.ctx._h, kern._h, ctypes.c_void_p(x2.data_ptr()),
                                   ctypes.c_void_p(o2.data_ptr()), b, stride, path, _stream_ptr(stream)))
+    return out
+
+
+def convolve_rings(kern: Kernel, x, ring_lo: int, ring_hi: int, out=None, stream=None):
+    """The outputs of rings [ring_lo, ring_hi) (0-based) of y = A x, for a ring-band
+    decomposition (see bands.py): x needs valid values on the band's halo rings only, and
+    out is valid on the band only (other rings may hold partial sums)."""
+    import torch
+    x2, b, stride = _map_args(x, kern.geom.npix)
+    if out is None:
+        out = torch.empty_like(x2)
+    o2, b2, stride2 = _map_args(out, kern.geom.npix)
+    if b2 != b or stride2 != stride:
+        raise ValueError("out must match x in shape and strides")
+    _check(lib().sk_convolve_rings(kern.ctx._h, kern._h, ctypes.c_void_p(x2.data_ptr()),
+                                   ctypes.c_void_p(o2.data_ptr()), b, stride, int(ring_lo), int(ring_hi),
+                                   _stream_ptr(stream)))
     return out
 
 

@@ -1,0 +1,96 @@
+"""Ring-band decomposition of one map over several devices (ranks).
+
+The real-space sum of an output pixel reads the input pixels within theta_cut, which
+lie on the rings whose colatitude is within theta_cut of its own (Sec. 2: the kernel is
+truncated at theta_cut).  So a rank that owns a band of output rings [o_lo, o_hi) needs
+the input rings of colatitude within theta_cut of the band, its halo [i_lo, i_hi); in
+RING order both are contiguous pixel ranges.  Bands hold about equal pixel counts (the
+number of in-cut pairs per pixel is nearly the same everywhere).  The input reaches
+every rank by one all-gather of the ranks' own bands (each keeps its halo); each rank
+then computes its band with convolve_rings and the outputs stay sharded (or are
+gathered the same way).  Host-side logic only: the ring tables follow the HEALPix
+RING scheme (Gorski et al. 2005, the pixelisation of Sec. 2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def ring_table(nside: int):
+    """Per ring (0-based, 4 nside - 1 rings): pixel count, first pixel, colatitude."""
+    N = int(nside)
+    nr = 4 * N - 1
+    n = np.empty(nr, np.int64)
+    z = np.empty(nr, np.float64)
+    for r in range(1, nr + 1):
+        if r < N:
+            n[r - 1], z[r - 1] = 4 * r, 1.0 - r * r / (3.0 * N * N)
+        elif r <= 3 * N:
+            n[r - 1], z[r - 1] = 4 * N, 4.0 / 3.0 - 2.0 * r / (3.0 * N)
+        else:
+            rr = 4 * N - r
+            n[r - 1], z[r - 1] = 4 * rr, -(1.0 - rr * rr / (3.0 * N * N))
+    start = np.concatenate(([0], np.cumsum(n)[:-1]))
+    return n, start, np.arccos(np.clip(z, -1.0, 1.0))
+
+
+@dataclass(frozen=True)
+class Band:
+    rank: int
+    out_rings: tuple     # [lo, hi)
+    in_rings: tuple      # [lo, hi): the rings within theta_cut of the band
+    out_pix: tuple       # [p0, p1) in RING order
+    in_pix: tuple
+
+
+def ring_bands(nside: int, theta_cut: float, world: int) -> list:
+    """Split the output rings into `world` contiguous bands of about equal pixel counts."""
+    n, start, theta = ring_table(nside)
+    nr = len(n)
+    npix = int(n.sum())
+    world = max(1, min(int(world), nr))
+    cum = np.cumsum(n)
+    edges = [0]
+    for r in range(1, world):
+        edges.append(max(edges[-1] + 1, int(np.searchsorted(cum, r * npix / world)) + 1))
+    edges.append(nr)
+    edges = [min(e, nr) for e in edges]
+    out = []
+    # rings at a tie, and rings that the device's FP32 cut test (chord^2 <= its FP32 value)
+    # may take in, join the halo: a margin well above FP32 rounding of the angle
+    eps = 1e-6 * max(1.0, theta_cut)
+    for rank in range(world):
+        lo, hi = edges[rank], edges[rank + 1]
+        if hi <= lo:
+            out.append(Band(rank, (lo, lo), (lo, lo), (0, 0), (0, 0)))
+            continue
+        ilo = int(np.searchsorted(theta, theta[lo] - theta_cut - eps, side="left"))
+        ihi = int(np.searchsorted(theta, theta[hi - 1] + theta_cut + eps, side="right"))
+        out.append(Band(rank, (lo, hi), (ilo, ihi),
+                        (int(start[lo]), int(start[hi - 1] + n[hi - 1])),
+                        (int(start[ilo]), int(start[ihi - 1] + n[ihi - 1]))))
+    return out
+
+
+def gather_halo(x_own, band: Band, bands: list, npix: int, group=None):
+    """The input map of `band`'s rank from every rank's own pixels: x_own [batch, p1 - p0]
+    holds this rank's band of the input (its out_pix range).  One all-gather (padded to the
+    largest band); returns [batch, npix] with the halo filled and zeros elsewhere."""
+    import torch
+    import torch.distributed as dist
+    batch = x_own.shape[0]
+    width = max(b.out_pix[1] - b.out_pix[0] for b in bands)
+    mine = torch.zeros(batch, width, dtype=x_own.dtype, device=x_own.device)
+    mine[:, : x_own.shape[1]] = x_own
+    parts = [torch.empty_like(mine) for _ in bands]
+    dist.all_gather(parts, mine, group=group)
+    full = torch.zeros(batch, npix, dtype=x_own.dtype, device=x_own.device)
+    p0, p1 = band.in_pix
+    for b, part in zip(bands, parts):
+        q0, q1 = max(b.out_pix[0], p0), min(b.out_pix[1], p1)
+        if q1 > q0:
+            full[:, q0:q1] = part[:, q0 - b.out_pix[0]: q1 - b.out_pix[0]]
+    return full

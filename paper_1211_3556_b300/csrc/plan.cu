@@ -89,7 +89,72 @@ void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_band_items); k->d_band_items = nullptr;
     k->bands.clear();
     k->bands_P = 0;
+    {
+        std::lock_guard<std::mutex> lock(k->subsets_mu);
+        for (auto &r : k->subsets) cudaFree(r.d_items);
+        k->subsets.clear();
+    }
     k->plan_ok = false;
+}
+
+int sk_plan_ring_subset(sk_kern *k, int lo, int hi, const SkItems **out) {
+    std::lock_guard<std::mutex> lock(k->subsets_mu);
+    for (auto &r : k->subsets)
+        if (r.lo == lo && r.hi == hi && r.P == k->belt_P) { *out = &r.items; return SK_OK; }
+    const sk_geom *g = k->g;
+    const int nr = g->nr;
+    auto in = [&](int r) { return r >= lo && r < hi; };
+    std::vector<int4> all;
+    size_t off_belt = 0, n_belt = 0, off_cap[SK_CAP_LS_CLASSES][2] = {}, n_cap[SK_CAP_LS_CLASSES][2] = {};
+    size_t off_gen = 0, n_gen = 0;
+    bool caps = false;
+    if (k->plan_ok) {
+        // a belt item (ring group, tile) writes rings b_lo + 16 group .. + 15; a cap item its
+        // northern ring and the mirror; a per-pair item its ring
+        for (const int4 &it : k->h_items_belt) {
+            const int r0 = k->b_lo + it.x * SK_BELT_G, r1 = std::min(r0 + SK_BELT_G, k->b_lo + k->nb);
+            if (r0 < hi && r1 > lo) all.push_back(it);
+        }
+        n_belt = all.size();
+        for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+            for (int v = 0; v < 2; ++v) {
+                off_cap[c][v] = all.size();
+                for (const int4 &it : k->h_items_cap[c][v])
+                    if (in(it.x) || in(nr - 1 - it.x)) all.push_back(it);
+                n_cap[c][v] = all.size() - off_cap[c][v];
+                caps = caps || n_cap[c][v] > 0;
+            }
+        off_gen = all.size();
+        for (const int4 &it : k->h_items_gen)
+            if (in(it.x)) all.push_back(it);
+    } else {
+        off_gen = 0;
+        for (int r = std::max(lo, 0); r < std::min(hi, nr); ++r)
+            for (int j = 0; j < g->h_rings[r].n; j += 128) all.push_back(make_int4(r, j, 0, 0));
+    }
+    n_gen = all.size() - off_gen;
+    sk_kern::RingSubset rs{lo, hi, k->belt_P, nullptr, SkItems{}};
+    if (!all.empty()) {
+        cudaError_t e = cudaMalloc(&rs.d_items, sizeof(int4) * all.size());
+        if (e == cudaSuccess) e = cudaMemcpy(rs.d_items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(rs.d_items);
+            return sk_fail(SK_ENOMEM, "ring subset: %s", cudaGetErrorString(e));
+        }
+    }
+    rs.items.belt = n_belt ? rs.d_items + off_belt : nullptr;
+    rs.items.n_belt = (int)n_belt;
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v) {
+            rs.items.cap[c][v] = n_cap[c][v] ? rs.d_items + off_cap[c][v] : nullptr;
+            rs.items.n_cap[c][v] = (int)n_cap[c][v];
+        }
+    rs.items.gen = n_gen ? rs.d_items + off_gen : nullptr;
+    rs.items.n_gen = (int)n_gen;
+    rs.items.sym[0][1] = caps ? k->sym_hi : 0;
+    k->subsets.push_back(rs);                       // entries of other tile widths stay (in use elsewhere)
+    *out = &k->subsets.back().items;
+    return SK_OK;
 }
 
 int sk_plan_rebuild_belt_items(sk_kern *k) {

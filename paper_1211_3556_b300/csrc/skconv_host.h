@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdarg.h>
 
+#include <deque>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -120,6 +122,16 @@ struct sk_kern {
     std::vector<Band> bands;
     int bands_P = 0;
     int4 *d_band_items = nullptr;
+    // sk_convolve_rings: the work items writing output rings [lo, hi), per range asked for
+    // (an entry per tile width; a deque keeps the entries in place as it grows, the mutex
+    // guards it against concurrent first calls)
+    struct RingSubset {
+        int lo, hi, P;
+        int4 *d_items;
+        SkItems items;
+    };
+    std::deque<RingSubset> subsets;
+    std::mutex subsets_mu;
 };
 
 // api.cu
@@ -149,6 +161,8 @@ struct SkJob {
 };
 // Partition of k's items into ring bands (kept in k; rebuilt when stale).
 int sk_plan_bands(sk_kern *k);
+// The items that write output rings [lo, hi) (kept in k; *out points into it).
+int sk_plan_ring_subset(sk_kern *k, int lo, int hi, const SkItems **out);
 // Launch sequence of the forward operator for a set of jobs.  `ws` must hold
 // sk_jobs_workspace_bytes(jobs) bytes: the belt weight rows of every job, then the
 // symmetric copies of every job's maps for the caps.

@@ -47,3 +47,80 @@ def test_weak_scaling_logic_world_size_2():
     assert r0 == pytest.approx(1000.0 * 2 / 0.020) and r0 == r1
     assert s0 == pytest.approx(s1, rel=1e-6)        # same data, shifted: the sums agree
     assert first0 != first1                          # but each rank has its own maps
+
+
+# ---------------------------------------------------------------- ring bands of one map
+
+def _band_rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import math
+    import torch
+    import torch.distributed as dist
+    import oracle as O
+    from inputs import gaussian_beam, white_noise_maps
+    from paper_1211_3556_b300.bands import gather_halo, ring_bands
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    nside, tc = 8, math.radians(30.0)
+    V = O.tabulate_real_kernel(gaussian_beam(600.0, 16), 4, 16, tc, 512, 0)
+    x = white_noise_maps(nside, 1, 77)[0].astype(np.float64)
+    npix = x.size
+    bands = ring_bands(nside, tc, world)
+    me = bands[rank]
+    p0, p1 = me.out_pix
+    # each rank starts from its own band of the input only
+    x_own = torch.from_numpy(x[None, p0:p1].copy())
+    x_halo = gather_halo(x_own, me, bands, npix)[0].numpy()
+    # the oracle stands in for the device sums: this rank's outputs from its halo
+    y_mine = O.conv_window(nside, V, tc, 0, x_halo, outs=np.arange(p0, p1, dtype=np.int64))
+    outs = [None] * world
+    dist.all_gather_object(outs, (p0, p1, y_mine.tolist()))
+    if rank == 0:
+        y = np.zeros(npix)
+        for q0, q1, vals in outs:
+            y[q0:q1] = vals
+        out["stitched"] = y.tolist()
+        out["full"] = O.conv_window(nside, V, tc, 0, x).tolist()
+        out["halo_zero_outside"] = bool(np.all(x_halo[: me.in_pix[0]] == 0) and np.all(x_halo[me.in_pix[1]:] == 0))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_ring_bands_halo_exchange_and_stitching_world_size_2():
+    # one map split into two ring bands; the halo comes by an all-gather over gloo, each
+    # rank sums its band (the FP64 oracle in place of the device), and the stitched map
+    # equals the full sum exactly (the same terms in the same order)
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_band_rank_main, args=(world, port, out), nprocs=world, join=True)
+    assert out["halo_zero_outside"]
+    assert np.array_equal(np.array(out["stitched"]), np.array(out["full"]))
+
+
+@pytest.mark.parametrize("nside,deg,world", [(8, 30.0, 2), (16, 80.0, 4), (64, 3.0, 3), (32, 1.0, 7)])
+def test_ring_bands_tile_the_rings_and_cover_the_windows(nside, deg, world):
+    import math
+    import oracle as O
+    from paper_1211_3556_b300.bands import ring_bands, ring_table
+    n, start, theta = ring_table(nside)
+    for r in range(len(n)):                                   # ring tables pinned to the oracle's
+        on, ost, _, oz, _ = O.ring_info(nside, r + 1)
+        assert (n[r], start[r]) == (on, ost) and math.cos(theta[r]) == pytest.approx(oz, abs=1e-15)
+    tc = math.radians(deg)
+    bands = ring_bands(nside, tc, world)
+    assert bands[0].out_rings[0] == 0 and bands[-1].out_rings[1] == len(n)
+    for a, b in zip(bands, bands[1:]):
+        assert a.out_rings[1] == b.out_rings[0] and a.out_pix[1] == b.out_pix[0]
+    for b in bands:
+        lo, hi = b.out_rings
+        if hi == lo:
+            continue
+        ilo, ihi = b.in_rings
+        assert ilo <= lo and ihi >= hi
+        for i in range(len(n)):                               # the rings within theta_cut, and
+            gap = min(abs(theta[i] - theta[o]) for o in range(lo, hi))   # those within 1e-6 rad
+            if gap <= tc:                                     # of it (FP32 margin)
+                assert ilo <= i < ihi
+            elif ilo <= i < ihi:
+                assert gap - tc <= 1e-6
