@@ -367,17 +367,31 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     const float4 *r0 = xr0 + split_index<LS>(o0), *r1 = xr0 + split_index<LS>(o0 - 1);
                     float2 q = make_float2(qA0, qA0 - dqi);   // q of pixel m for outputs (A, B)
                     int m = 0;
+                    if (cnt_u >= 2) {
+                        // weights one pixel pair ahead of the sums that use them
+                        float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
+                        float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(__fadd2_rn(q, f2(dqo)), f2(P.c0)), Ae, P.B, J.kp, stab);
+                        q = __fadd2_rn(q, f2(2.0f * dqo));
 #pragma unroll 1
-                    for (; m + 1 < cnt_u; m += 2) {
+                        for (; m + 3 < cnt_u; m += 2) {
+                            const int i = m >> 1;
+                            const float2 q1 = __fadd2_rn(q, f2(dqo));
+                            const float2 v0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
+                            const float2 v1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), Ae, P.B, J.kp, stab);
+                            q = __fadd2_rn(q1, f2(dqo));
+                            mac16<LS>(accA, w0.x, x0, r0, i);
+                            mac16<LS>(accB, w0.y, x0, r0, i);
+                            mac16<LS>(accA, w1.x, x1, r1, i);
+                            mac16<LS>(accB, w1.y, x1, r1, i);
+                            w0 = v0;
+                            w1 = v1;
+                        }
                         const int i = m >> 1;
-                        const float2 q1 = __fadd2_rn(q, f2(dqo));
-                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
-                        const float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), Ae, P.B, J.kp, stab);
-                        q = __fadd2_rn(q1, f2(dqo));
                         mac16<LS>(accA, w0.x, x0, r0, i);
                         mac16<LS>(accB, w0.y, x0, r0, i);
                         mac16<LS>(accA, w1.x, x1, r1, i);
                         mac16<LS>(accB, w1.y, x1, r1, i);
+                        m += 2;
                     }
                     if (m < cnt_u) {                           // an odd count: the last pixel alone
                         const int i = m >> 1;
