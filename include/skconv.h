@@ -164,6 +164,39 @@ int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_
 int sk_convolve_rings(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
                       int64_t map_stride, int ring_lo, int ring_hi, void *stream);
 
+/* Re-orientation of maps by a rotation (nearest-centre resampling), for partial-sky
+ * maps moved onto the polar cap, where they occupy few rings and the real-space sums
+ * touch only those (Sec. 4; with sk_convolve_rings).  For every output pixel p of
+ * rings [ring_lo, ring_hi) (0-based): i = the pixel whose centre is nearest to the
+ * direction M v_p (v_p the centre of p; ties to the lower index), and
+ * d_out[b][p] = d_in[b][i] if ring(i) < src_ring_hi, else 0.  Other output pixels
+ * are not written.  h_rot: host array of 9 doubles, M row-major, a rotation
+ * (orthonormal to 1e-9).  Rotating the pole frame onto a field at (theta0, phi0)
+ * and back: M and its transpose.  All geometry in FP64; the index decisions are
+ * exact.  Maps as in sk_convolve (FP32, stride >= npix); d_in and d_out must not
+ * overlap.  Errors: SK_EINVAL (also a ring range outside [0, rings], a matrix that
+ * is not orthogonal, overlapping maps), SK_ECUDA. */
+int sk_resample(sk_ctx *ctx, const sk_geom *g, const float *d_in, float *d_out, int64_t batch,
+                int64_t map_stride, const double *h_rot, int ring_lo, int ring_hi, int src_ring_hi,
+                void *stream);
+
+/* The same resampling planned once: the nearest-centre search depends on the
+ * geometry, the rotation and the ring ranges only, so the plan keeps the kept
+ * (output, source) pixel pairs (8 bytes each, on the device) and every apply is a
+ * gather.  sk_resample_plan_apply(p, x, y) writes exactly what
+ * sk_resample(.., x, y, .., same rotation and ranges) writes (masked outputs of the
+ * ring range are cleared, then the pairs gathered).  The plan refers to the
+ * geometry, which must outlive it.  info: out3[0] = kept pairs, out3[1] = output
+ * pixels of the ring range, out3[2] = device bytes held.
+ * Errors: as sk_resample; SK_ENOMEM when the pairs do not fit. */
+typedef struct sk_resample_plan sk_resample_plan;
+int sk_resample_plan_create(sk_ctx *ctx, const sk_geom *g, const double *h_rot, int ring_lo, int ring_hi,
+                            int src_ring_hi, sk_resample_plan **out);
+int sk_resample_plan_destroy(sk_resample_plan *p);
+int sk_resample_plan_info(const sk_resample_plan *p, int64_t *out3);
+int sk_resample_plan_apply(const sk_resample_plan *p, const float *d_in, float *d_out, int64_t batch,
+                           int64_t map_stride, void *stream);
+
 /* x_bar = A^T y_bar.  The kernel is radial, so A_oi = dOmega K_lin(gamma(o,i))
  * is symmetric and the transpose, written as a gather over the inputs of each
  * output, is the forward gather.  Same arguments and errors as sk_convolve. */

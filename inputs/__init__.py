@@ -117,7 +117,15 @@ WORKLOADS = {
                             (Group(8192, 1, _k(2.0, 8192, 5.0, 16384, 16384, 4096), 501),)),
     # wide cut (the ring-pair Fourier form of the belt): 300' windows, ~2.3e4 neighbours per pixel
     "n1024_wide": Workload("n1024_wide", (Group(1024, 1, _k(60.0, 1024, 300.0, 4096), 601),)),
+    # a partial-sky field (a disc of FIELD_RADIUS_DEG, ~310 square degrees, the size of the
+    # ground-based surveys the paper names) at Nside 8192 with the 5' kernel
+    "n8192_field": Workload("n8192_field",
+                            (Group(8192, 1, _k(2.0, 8192, 5.0, 16384, 16384, 4096), 701),)),
 }
+
+# Centre (colatitude, longitude, radians) and radius of the partial-sky field.
+FIELD_CENTRE = (1.0, 0.5)
+FIELD_RADIUS_DEG = 10.0
 
 # Gradient workload: the target map comes from the same maps convolved with a
 # 10.5' kernel; the finite-difference entries are drawn with this seed.

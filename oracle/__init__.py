@@ -27,7 +27,9 @@ splitting"):
   least-squares fit (Sec. 3: K^_theta is fit so that its harmonic transform
   matches K_l above l_cut), a piecewise-linear kernel on [0, theta_cut] that
   vanishes at theta_cut, by ``numpy.linalg.lstsq`` on the plain objective;
-* gradients: the table gradient in C and a finite-difference helper.
+* gradients: the table gradient in C and a finite-difference helper;
+* ``resample_nearest``: a map re-oriented by a rotation (Sec. 4: a partial-sky
+  field moved onto the polar cap), nearest pixel centre by brute force.
 """
 from __future__ import annotations
 
@@ -412,3 +414,41 @@ def conv_function_brute(nside: int, kernel_fn, theta_cut: float, x: np.ndarray) 
     g = 2.0 * np.arcsin(np.minimum(1.0, 0.5 * d))
     K = np.where(g <= theta_cut, kernel_fn(g), 0.0)
     return (4.0 * math.pi / npix(nside)) * (K @ _f64(x))
+
+
+# --------------------------------------------------------------------------
+# Re-orientation onto the polar cap (Sec. 4)
+# --------------------------------------------------------------------------
+
+def ring_starts(nside: int) -> np.ndarray:
+    """First pixel of each ring (0-based rings), and npix at the end."""
+    nr = 4 * nside - 1
+    st = [ring_info(nside, r)[1] for r in range(1, nr + 1)]
+    return np.array(st + [npix(nside)], dtype=np.int64)
+
+
+def resample_nearest(nside: int, x, M, ring_lo: int, ring_hi: int, src_ring_hi: int = None,
+                     return_index: bool = False):
+    """Nearest-centre resampling under a rotation, by brute force: for every pixel p of
+    rings [ring_lo, ring_hi) (0-based), i = the pixel whose centre has the largest dot
+    product with M v_p (the nearest centre; the first index on ties), and
+    out[p] = x[i] if ring(i) < src_ring_hi else 0; other pixels 0.  x: [npix] or
+    [batch, npix]."""
+    x = np.asarray(x, dtype=np.float64)
+    one = x.ndim == 1
+    X = x[None, :] if one else x
+    v = all_vecs(nside)
+    st = ring_starts(nside)
+    nr = 4 * nside - 1
+    src = nr if src_ring_hi is None else int(src_ring_hi)
+    p0, p1 = int(st[ring_lo]), int(st[ring_hi])
+    W = v[p0:p1] @ np.asarray(M, dtype=np.float64).T          # rows: M v_p
+    idx = np.empty(p1 - p0, dtype=np.int64)
+    rows = max(1, (1 << 23) // len(v))                            # ~64 MB of dot products at a time
+    for a in range(0, p1 - p0, rows):
+        idx[a:a + rows] = np.argmax(W[a:a + rows] @ v.T, axis=1)
+    ring = np.searchsorted(st, idx, side="right") - 1
+    out = np.zeros_like(X)
+    out[:, p0:p1] = np.where(ring < src, X[:, idx], 0.0)
+    out = out[0] if one else out
+    return (out, idx) if return_index else out

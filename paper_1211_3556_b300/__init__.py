@@ -13,6 +13,7 @@ kernel table of Sec. 3.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -66,6 +67,11 @@ def _declare(L):
         "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
         "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
         "sk_convolve_rings": (I, [P, P, P, P, I64, I64, I, I, P]),
+        "sk_resample": (I, [P, P, P, P, I64, I64, P, I, I, I, P]),
+        "sk_resample_plan_create": (I, [P, P, P, I, I, I, PP]),
+        "sk_resample_plan_destroy": (I, [P]),
+        "sk_resample_plan_info": (I, [P, ctypes.POINTER(I64)]),
+        "sk_resample_plan_apply": (I, [P, P, P, I64, I64, P]),
         "sk_convolve_adjoint": (I, [P, P, P, P, I64, I64, P]),
         "sk_grad_table": (I, [P, P, P, P, I64, I64, P, P]),
         "sk_grad_table_noalloc": (I, [P, P, P, P, I64, I64, P, P]),
@@ -333,6 +339,131 @@ def convolve_rings(kern: Kernel, x, ring_lo: int, ring_hi: int, out=None, stream
                                    ctypes.c_void_p(o2.data_ptr()), b, stride, int(ring_lo), int(ring_hi),
                                    _stream_ptr(stream)))
     return out
+
+
+def rotation_to_pole(theta0: float, phi0: float) -> np.ndarray:
+    """The rotation M (3x3, FP64) that takes the north pole to the direction (theta0, phi0):
+    M = R_z(phi0) R_y(theta0).  resample(.., M, ..) moves a field centred there onto the
+    pole; resample(.., M.T, ..) moves it back."""
+    ct, st_ = math.cos(theta0), math.sin(theta0)
+    cp, sp = math.cos(phi0), math.sin(phi0)
+    rz = np.array([[cp, -sp, 0.0], [sp, cp, 0.0], [0.0, 0.0, 1.0]])
+    ry = np.array([[ct, 0.0, st_], [0.0, 1.0, 0.0], [-st_, 0.0, ct]])
+    return rz @ ry
+
+
+def resample(geom: Geometry, x, rot, ring_lo: int, ring_hi: int, src_ring_hi: int = None, out=None, stream=None):
+    """Nearest-centre resampling of maps under a rotation (sk_resample): output pixel p of
+    rings [ring_lo, ring_hi) takes x at the pixel nearest to rot @ v_p (0 if that pixel is
+    on a ring >= src_ring_hi).  Other output pixels are left as they are (zeros if out is
+    None)."""
+    import torch
+    x2, b, stride = _map_args(x, geom.npix)
+    if out is None:
+        out = torch.zeros_like(x2)
+    o2, b2, stride2 = _map_args(out, geom.npix)
+    if b2 != b or stride2 != stride:
+        raise ValueError("out must match x in shape and strides")
+    m = np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(9))
+    nr = 4 * geom.nside - 1
+    src = nr if src_ring_hi is None else int(src_ring_hi)
+    _check(lib().sk_resample(geom.ctx._h, geom._h, ctypes.c_void_p(x2.data_ptr()), ctypes.c_void_p(o2.data_ptr()),
+                             b, stride, m.ctypes.data, int(ring_lo), int(ring_hi), src, _stream_ptr(stream)))
+    return out
+
+
+class ResamplePlan:
+    """resample() planned once for a rotation and ring ranges (sk_resample_plan_*): the
+    nearest-centre search runs at creation; apply() is a gather with the same result."""
+
+    def __init__(self, geom: Geometry, rot, ring_lo: int, ring_hi: int, src_ring_hi: int = None):
+        self.geom = geom
+        m = np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(9))
+        nr = 4 * geom.nside - 1
+        src = nr if src_ring_hi is None else int(src_ring_hi)
+        self._h = ctypes.c_void_p()
+        _check(lib().sk_resample_plan_create(geom.ctx._h, geom._h, m.ctypes.data, int(ring_lo), int(ring_hi), src,
+                                             ctypes.byref(self._h)))
+
+    def info(self):
+        out = (ctypes.c_int64 * 3)()
+        _check(lib().sk_resample_plan_info(self._h, out))
+        return {"pairs": out[0], "pixels": out[1], "bytes": out[2]}
+
+    def apply(self, x, out=None, stream=None):
+        import torch
+        x2, b, stride = _map_args(x, self.geom.npix)
+        if out is None:
+            out = torch.zeros_like(x2)
+        o2, b2, stride2 = _map_args(out, self.geom.npix)
+        if b2 != b or stride2 != stride:
+            raise ValueError("out must match x in shape and strides")
+        _check(lib().sk_resample_plan_apply(self._h, ctypes.c_void_p(x2.data_ptr()), ctypes.c_void_p(o2.data_ptr()),
+                                            b, stride, _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if self._h:
+            lib().sk_resample_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PolarPatch:
+    """A partial-sky field (a disc of `radius` around (theta0, phi0)) convolved on the
+    polar cap (Sec. 4: re-oriented onto the pole, a field spans few rings).  The map is
+    rotated so that the field centre is the pole (nearest-centre resampling of the cap
+    rings the sums read), the output rings of the field are summed (convolve_rings, whose
+    windows stay on those rings), and the result is rotated back onto the sky rings that
+    hold the field; sky pixels whose nearest rotated pixel is outside the summed rings get
+    0.  Up to the two resamplings this is the full-sky operator on the field: the kernel
+    is radial."""
+
+    def __init__(self, kern: Kernel, theta0: float, phi0: float, radius: float):
+        from .bands import ring_table
+        self.kern = kern
+        g = kern.geom
+        self.rot = rotation_to_pole(theta0, phi0)
+        n, start, theta = ring_table(g.nside)
+        nr = len(n)
+        pix = math.sqrt(4.0 * math.pi / g.npix)
+        # output rings: colatitude up to radius plus two pixels (every sky pixel of the
+        # field has its nearest rotated centre among them)
+        self.out_hi = int(np.searchsorted(theta, radius + 2.0 * pix, side="right"))
+        self.out_hi = max(1, min(self.out_hi, nr))
+        # input rings: within theta_cut of the output rings (margin as for ring bands)
+        reach = theta[self.out_hi - 1] + kern.theta_cut + 1e-6 * max(1.0, kern.theta_cut)
+        self.in_hi = max(self.out_hi, min(nr, int(np.searchsorted(theta, reach, side="right"))))
+        # sky rings that hold the field
+        lo_t, hi_t = theta0 - theta[self.out_hi - 1], theta0 + theta[self.out_hi - 1]
+        self.sky_lo = int(np.searchsorted(theta, lo_t - pix, side="left"))
+        self.sky_hi = int(np.searchsorted(theta, hi_t + pix, side="right"))
+        self.sky_lo, self.sky_hi = max(0, self.sky_lo), min(nr, self.sky_hi)
+        if lo_t <= 0.0:
+            self.sky_lo = 0
+        if hi_t >= math.pi:
+            self.sky_hi = nr
+
+        # the two resamplings, planned once (their searches depend on the geometry only)
+        self.to_cap = ResamplePlan(g, self.rot, 0, self.in_hi)
+        self.to_sky = ResamplePlan(g, self.rot.T, self.sky_lo, self.sky_hi, src_ring_hi=self.out_hi)
+
+    def convolve(self, x, out=None, stream=None, work=None):
+        """y on the field's sky rings (other pixels of out untouched; zeros if out is None).
+        work: optional pair of scratch maps shaped like x (the rotated input and output)."""
+        import torch
+        if work is None:
+            x2, _, _ = _map_args(x, self.kern.geom.npix)
+            work = (torch.zeros_like(x2), torch.empty_like(x2))
+        xr, yr = work
+        self.to_cap.apply(x, out=xr, stream=stream)
+        convolve_rings(self.kern, xr, 0, self.out_hi, out=yr, stream=stream)
+        return self.to_sky.apply(yr, out=out, stream=stream)
 
 
 def convolve_adjoint(kern: Kernel, gy, out=None, stream=None):
