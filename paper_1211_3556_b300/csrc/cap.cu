@@ -263,6 +263,11 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         else stab[k] = A.j[0].tab[k].x;
     }
     __syncthreads();
+    // the weight lookups read the table by its shared address (SmemTab2) where it holds pairs
+    const auto tabv = [&]() {
+        if constexpr (sizeof(TabT) == sizeof(float2)) return SmemTab2{tc::smem_u32(stab)};
+        else return static_cast<const float *>(stab);
+    }();
     const int slot = threadIdx.x / NTH, t = threadIdx.x % NTH;
     float4 *const sbuf = sx + slot * NB * 4 * LS;
     const uint32_t bar0 = tc::smem_u32(bars + slot * NB);
@@ -369,15 +374,15 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     int m = 0;
                     if (cnt_u >= 2) {
                         // weights one pixel pair ahead of the sums that use them
-                        float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
-                        float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(__fadd2_rn(q, f2(dqo)), f2(P.c0)), Ae, P.B, J.kp, stab);
+                        float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, tabv);
+                        float2 w1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(__fadd2_rn(q, f2(dqo)), f2(P.c0)), Ae, P.B, J.kp, tabv);
                         q = __fadd2_rn(q, f2(2.0f * dqo));
 #pragma unroll 1
                         for (; m + 3 < cnt_u; m += 2) {
                             const int i = m >> 1;
                             const float2 q1 = __fadd2_rn(q, f2(dqo));
-                            const float2 v0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
-                            const float2 v1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), Ae, P.B, J.kp, stab);
+                            const float2 v0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, tabv);
+                            const float2 v1 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q1, f2(P.c0)), Ae, P.B, J.kp, tabv);
                             q = __fadd2_rn(q1, f2(dqo));
                             mac16<LS>(accA, w0.x, x0, r0, i);
                             mac16<LS>(accB, w0.y, x0, r0, i);
@@ -395,7 +400,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     }
                     if (m < cnt_u) {                           // an odd count: the last pixel alone
                         const int i = m >> 1;
-                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, stab);
+                        const float2 w0 = fast_weight2<SMALLA, BIASED>(__fmul2_rn(q, f2(P.c0)), Ae, P.B, J.kp, tabv);
                         mac16<LS>(accA, w0.x, x0, r0, i);
                         mac16<LS>(accB, w0.y, x0, r0, i);
                     }
@@ -403,8 +408,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                     // windows may be whole rings: restrict each output to its own window
                     for (int m = 0; m < cnt_u; ++m) {
                         const float qa = fmaf((float)m, dqo, qA0);
-                        float wa = fast_weight<SERIES, SMALLA, BIASED>(qa * P.c0, Ae, P.B, J.kp, stab);
-                        float wb = fast_weight<SERIES, SMALLA, BIASED>((qa - dqi) * P.c0, Ae, P.B, J.kp, stab);
+                        float wa = fast_weight<SERIES, SMALLA, BIASED>(qa * P.c0, Ae, P.B, J.kp, tabv);
+                        float wb = fast_weight<SERIES, SMALLA, BIASED>((qa - dqi) * P.c0, Ae, P.B, J.kp, tabv);
                         wa = m < cnt ? wa : 0.0f;
                         wb = m >= dl ? wb : 0.0f;
                         const float4 *xm = xbuf + split_index<LS>(pA + m);
