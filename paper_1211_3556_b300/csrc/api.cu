@@ -286,6 +286,7 @@ static int finish_kernel(sk_kern *k) {
         const double ih = (double)(nt - 1) / tc;       // uniform layout only
         for (int i = 0; i < 5; ++i) kp.sa[i] = (float)(ih * coef[i]);
         kp.umax = (float)(nt - 1) - 1.0f / 256.0f;
+        kp.umax_pad = (float)nt + 0.25f;
     }
     KernParams64 &kd = k->kd;
     kd.tcut = 4.0 * sh * sh;

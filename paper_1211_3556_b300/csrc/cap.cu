@@ -258,9 +258,12 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = threadIdx.x; k < A.j[0].kp.nt; k += NTH * SLOTS) {
-        if constexpr (sizeof(TabT) == sizeof(float2)) stab[k] = A.j[0].tab[k];
-        else stab[k] = A.j[0].tab[k].x;
+    // a (value, slope) table is padded: entries nt - 1 .. nt + 1 hold (0, 0), so that
+    // pairs beyond the cut read weight 0 (fast_weight with SmemTab2)
+    const int ntab = A.j[0].kp.nt;
+    for (int k = threadIdx.x; k < ntab + 2; k += NTH * SLOTS) {
+        if constexpr (sizeof(TabT) == sizeof(float2)) stab[k] = k < ntab - 1 ? A.j[0].tab[k] : make_float2(0.0f, 0.0f);
+        else if (k < ntab) stab[k] = A.j[0].tab[k].x;
     }
     __syncthreads();
     // the weight lookups read the table by its shared address (SmemTab2) where it holds pairs
@@ -437,7 +440,7 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
 
 size_t cap_smem(int LS, int nt, bool pairs) {
     const int nb = LS <= 320 ? 2 : 1, slots = LS <= 640 ? 4 : 2;     // cap_bufs, cap_slots
-    return cap_strip_bytes(LS, nb, slots) + cap_bar_bytes(nb, slots) + (size_t)nt * (pairs ? 8 : 4);
+    return cap_strip_bytes(LS, nb, slots) + cap_bar_bytes(nb, slots) + (pairs ? (size_t)(nt + 2) * 8 : (size_t)nt * 4);
 }
 
 int max_nt(const JobsArg &a) {
