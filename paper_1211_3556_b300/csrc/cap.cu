@@ -258,12 +258,21 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // a (value, slope) table is padded: entries nt - 1 .. nt + 1 hold (0, 0), so that
-    // pairs beyond the cut read weight 0 (fast_weight with SmemTab2)
+    // a (value, slope) table becomes (midpoint, slope), M_k = V_k + S_k / 2, and is
+    // padded: entries nt - 1 .. nt + 1 hold (0, 0), so that pairs beyond the cut read
+    // weight 0 (fast_weight with SmemTab2)
     const int ntab = A.j[0].kp.nt;
     for (int k = threadIdx.x; k < ntab + 2; k += NTH * SLOTS) {
-        if constexpr (sizeof(TabT) == sizeof(float2)) stab[k] = k < ntab - 1 ? A.j[0].tab[k] : make_float2(0.0f, 0.0f);
-        else if (k < ntab) stab[k] = A.j[0].tab[k].x;
+        if constexpr (sizeof(TabT) == sizeof(float2)) {
+            float2 e = make_float2(0.0f, 0.0f);
+            if (k < ntab - 1) {
+                e = A.j[0].tab[k];
+                e.x = fmaf(0.5f, e.y, e.x);
+            }
+            stab[k] = e;
+        } else if (k < ntab) {
+            stab[k] = A.j[0].tab[k].x;
+        }
     }
     __syncthreads();
     // the weight lookups read the table by its shared address (SmemTab2) where it holds pairs
