@@ -59,6 +59,7 @@ static_assert(NTH == 128, "an item's strips are issued by its four warps in turn
 // work items in flight per block (they share one node table): four where their strips fit
 template <int LS>
 __host__ __device__ constexpr int cap_slots() { return LS <= 640 ? 4 : 2; }
+__host__ __device__ constexpr int cap_max_slots() { return 4; }
 // node tables of up to this many nodes are held as (value, slope) pairs, larger ones as values
 constexpr int PAIR_TABLE_NODES = 8192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every wait on a copy
@@ -72,6 +73,17 @@ __host__ __device__ constexpr size_t cap_bar_bytes(int nb, int slots) { return (
 
 __device__ __forceinline__ void slot_sync(int slot) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(NTH) : "memory");
+}
+// Buffer hand-over of a two-buffer item: at the top of ring p every warp is done with
+// ring p - 1; the warp that stages ring p + 1 (into ring p - 1's buffer) waits for the
+// other three (bar.sync), which only signal (bar.arrive) and go on.  Two barriers per
+// slot, by the parity of p: a warp can run at most one ring ahead of the slowest (it
+// needs ring p + 1's strip, staged only after everyone finished ring p - 1), so it
+// never arrives twice in one phase.
+__device__ __forceinline__ void ring_handover(int slot, int parity, bool stager) {
+    const int id = 1 + cap_max_slots() + 2 * slot + parity;
+    if (stager) asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(NTH) : "memory");
+    else asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(NTH) : "memory");
 }
 
 // Bounded wait for a strip: false after WAIT_NS, or at once when another thread of the
@@ -339,11 +351,12 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
             const bool bulk = S.L < P.n_i;
             // every thread is done with ring p - 1: its buffer takes ring p + 1 (two
             // buffers) or ring p (one)
-            slot_sync(slot);
             if (NB == 2) {
+                ring_handover(slot, (p - p0) & 1, ((p + 1 - p0) & 3) == (t >> 5));
                 if (p + 1 < p1) issue(p + 1, b ^ 1);
-            } else if (bulk) {
-                issue(p, 0);
+            } else {
+                slot_sync(slot);
+                if (bulk) issue(p, 0);
             }
             bool ok = true;
             if (bulk) {
@@ -358,6 +371,8 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 }
                 phase ^= 1u << b;
             } else {
+                // buffer b held ring p - 2, which a slow warp may still read (two buffers)
+                if (NB == 2) slot_sync(slot);
                 copy_strip<LS>(xbuf, hmap + J.rings[P.ri].start, S, P, t);
                 slot_sync(slot);
             }
