@@ -13,7 +13,8 @@
 //    (k_grad_belt: a block per output ring, lanes over offsets, warps over pixels);
 //  * cap rings: a base pair and its 16 symmetric images share (k, f), so one FP64
 //    evaluation serves 16 products per map (k_grad_cap, inputs from the caps'
-//    symmetric copy, four maps per pass);
+//    symmetric copy, four maps per pass; the node coordinate in double-float FP32 where
+//    the cut is small, FP64 otherwise);
 //  * the remaining rings: one thread per output pixel walks its window
 //    (k_grad_general).
 // Each block adds its bins (FP32 in shared memory, or FP64 directly for the belt's
@@ -24,6 +25,107 @@
 #include "skconv_launch.h"
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: an unevaluated sum hi + lo of two FP32 values (about 44
+// significant bits), products by FMA (two-product), sums by Knuth's two-sum (Knuth,
+// TAOCP vol. 2, 4.2.2; Dekker 1971).  The table gradient uses it where FP64 would do
+// and FP64 issue would be the limit (B300 runs FP64 at about 1/64 of the FP32 rate).
+// The _rn intrinsics keep the compiler from contracting or reassociating the steps.
+// ---------------------------------------------------------------------------
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ dfloat df_from(double v) {
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {     // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    const dfloat s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return df_fast_two_sum(p, e);
+}
+
+// Per-ring-pair and per-kernel constants of pair_kf_df, split from their FP64 values.
+struct PairDF {
+    dfloat c0, A, B;
+};
+struct KernDF {
+    dfloat tcut, inv_h;
+};
+
+// pair_kf64's node interval and fraction in double-float, for the uniform node layout
+// with theta_cut <= 0.15 and |x| <= 1/8 (returns -1 otherwise: the caller takes
+// pair_kf64); 1 inside the cut, 0 outside.  q is the exact integer of the half-angle
+// x = q c0 (|q| < 2^24).  Same mathematics as pair_kf64:
+//   sin^2 x = x^2 (1 + R), R = -x^2/3 + 2x^4/45 - x^6/315 + 2x^8/14175 in FP32 (|R| <= 5.2e-3,
+//     so its rounding is below 3.1e-10 of sin^2 x; the next term is 4e-15 of it);
+//   t = A + B sin^2 x, the cut t <= tcut in double-float;
+//   c = sqrt(t): the FP32 root refined by one Newton step on the double-float t;
+//   gamma = c (1 + Qm1), Qm1 = t/24 + 3t^2/640 + 5t^3/7168 + 35t^4/294912 in FP32
+//     (|Qm1| <= 1e-3: rounding below 1.2e-10 of gamma; truncation 1.3e-13);
+//   u = gamma inv_h, k = floor(u) (at most nt - 2), f = u - k.
+// About 2.5e-10 relative in gamma at worst, i.e. below 1e-6 in f for 4096 nodes.
+__device__ __forceinline__ int pair_kf_df(float q, const PairDF &P, const KernDF &K, const KernParams &kp,
+                                          int &k, float &f) {
+    const dfloat x = df_mul_f(P.c0, q);
+    if (!(fabsf(x.hi) <= 0.125f)) return -1;
+    const dfloat x2 = df_mul(x, x);
+    const float y = x2.hi;
+    float R = __fmaf_rn(y, 2.0f / 14175.0f, -1.0f / 315.0f);
+    R = __fmaf_rn(y, R, 2.0f / 45.0f);
+    R = __fmaf_rn(y, R, -1.0f / 3.0f);
+    R = __fmul_rn(R, y);
+    const dfloat s2 = df_add(x2, df_mul_f(x2, R));
+    const dfloat t = df_add(P.A, df_mul(P.B, s2));
+    if (!(t.hi < K.tcut.hi || (t.hi == K.tcut.hi && t.lo <= K.tcut.lo))) return 0;
+    float uh = 0.0f, ul = 0.0f;
+    if (t.hi > 0.0f) {
+        const float c32 = __fsqrt_rn(t.hi);
+        const float p = __fmul_rn(c32, c32);
+        const float e = __fmaf_rn(c32, c32, -p);
+        const float r = __fadd_rn(__fsub_rn(__fsub_rn(t.hi, p), e), t.lo);     // t - c32^2
+        const dfloat c = df_fast_two_sum(c32, __fmul_rn(r, __fdiv_rn(0.5f, c32)));
+        const float th = t.hi;
+        float Q = __fmaf_rn(th, 35.0f / 294912.0f, 5.0f / 7168.0f);
+        Q = __fmaf_rn(th, Q, 3.0f / 640.0f);
+        Q = __fmaf_rn(th, Q, 1.0f / 24.0f);
+        Q = __fmul_rn(Q, th);
+        const dfloat u = df_mul(df_add(c, df_mul_f(c, Q)), K.inv_h);
+        uh = u.hi;
+        ul = u.lo;
+    }
+    float kf = floorf(uh);
+    float fr = __fadd_rn(__fsub_rn(uh, kf), ul);         // uh - kf is exact (uh < 2^23)
+    if (fr < 0.0f) { kf -= 1.0f; fr += 1.0f; }
+    int kk = (int)kf;
+    if (kk > kp.nt - 2) { fr += (float)(kk - (kp.nt - 2)); kk = kp.nt - 2; }
+    k = kk;
+    f = fr;
+    return 1;
+}
+
 
 constexpr int GB = 8;           // maps folded into one pair visit
 
@@ -198,6 +300,9 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
     const int nt = J.kp.nt;
     for (int k = threadIdx.x; k < nt; k += blockDim.x) bins[k] = 0.0f;
     __syncthreads();
+    // node coordinates in double-float where pair_kf_df applies (uniform nodes, small cut)
+    const bool dfpath = J.kp.small_angle && J.kp.layout == 0;
+    const KernDF KD{df_from(J.kd.tcut), df_from(J.kd.inv_h)};
     for (int f = blockIdx.x; f < J.n_items; f += gridDim.x) {
         const int4 it = J.items[f];
         const int ro = it.x, jo = it.y + (int)threadIdx.x;
@@ -235,6 +340,7 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
                 const PairInfo P = J.pairs[p];
                 const double2 ab = J.ab64[p];
                 const double c0 = SK_PI / (2.0 * (double)P.n_i * (double)R.n);
+                const PairDF PD{df_from(c0), df_from(ab.x), df_from(ab.y)};
                 const int Qi = P.n_i >> 2;
                 const float4 *h0 = J.hx + (long long)b0 * J.hstride + J.rings[P.ri].start;
                 int jlo, cnt;
@@ -256,7 +362,10 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
                     pd = pd == 0 ? n_i - 1 : pd - 1;
                     int k;
                     float fr;
-                    if (!pair_kf64((double)q * c0, ab.x, ab.y, J.kp, J.kd, k, fr)) continue;
+                    // |q| < 2^24 on the cap windows (checked when the plan was built): exact in FP32
+                    const int in = dfpath ? pair_kf_df((float)q, PD, KD, J.kp, k, fr) : -1;
+                    if (in == 0) continue;
+                    if (in < 0 && !pair_kf64((double)q * c0, ab.x, ab.y, J.kp, J.kd, k, fr)) continue;
                     float v = 0.0f;
 #pragma unroll
                     for (int u = 0; u < GC; ++u) {

@@ -283,7 +283,7 @@ def test_adjoint_dot_product(sk):
 # ------------------------------------------------------------------ table gradient
 
 @pytest.mark.parametrize("nside,tc,layout,nt", [(16, 0.25, 0, 64), (32, 0.1, 1, 64), (32, 0.12, 0, 512),
-                                                 (64, 0.05, 0, 4096)])
+                                                 (64, 0.05, 0, 4096), (256, 0.02, 0, 4096)])
 def test_grad_table_matches_oracle(sk, nside, tc, layout, nt):
     import torch
     V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, nt, layout)
