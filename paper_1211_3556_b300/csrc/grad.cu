@@ -186,73 +186,110 @@ k_grad_general(const __grid_constant__ JobsArg A, const float *__restrict__ gy, 
         if (bins[k] != 0.0f) atomicAdd(&acc[k], (double)bins[k]);
 }
 
-// Belt rings, step 1: a block per (belt output ring o, map b).  For every input ring i of
-// o's window and every offset e = EMIN + c of the belt's offset grid (c < WPM),
-// C[o][i][c] += sum_j gy_bo[j] x_bi[j + e]: lanes over c (and, when WPM <= 16, two pixel
-// halves per warp), warps over pixels, partial sums flushed every 128 pixels, the block's
-// parts summed in shared memory and added to C (FP32 atomics, one per map).  Pixels in
-// segments of SEG.
-constexpr int GW = 8;           // warps per belt-gradient block
-constexpr int SEG = 8192;       // pixels of a ring staged at once
-__global__ void __launch_bounds__(32 * GW)
-k_grad_belt(const JobDesc J, const float *__restrict__ gy, float *C) {
-    extern __shared__ float sm[];
-    const int rb = blockIdx.x, b = blockIdx.y;
-    if (rb >= J.nb) return;
-    const int n = J.n4, o = J.b_lo + rb;
-    const int p0 = J.pair_off[o], np = J.pair_off[o + 1] - p0;
-    const int R2 = 2 * J.HM + 1;
-    const int WC = J.WPM <= 16 ? 16 : 32;             // offsets per lane group
-    const int NG = 32 / WC;                           // lane groups per warp
-    const int NPART = GW * NG;                        // pixel parts of a segment
-    const int segn = min(n, SEG);
-    float *gys = sm;                                  // [SEG]
-    float *xs = gys + SEG;                            // [SEG + WPM + 32]
-    float *red = xs + SEG + J.WPM + 32;               // [NPART][WC]
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int cl = lane % WC, part = warp * NG + lane / WC;
-    const float *gyo = gy + (long long)b * J.stride + J.rings[o].start;
-    for (int cb = 0; cb < J.WPM; cb += WC) {
-        const int c = cb + cl;
-        for (int pp = 0; pp < np; ++pp) {
-            const float *xi = J.x + (long long)b * J.stride + J.rings[J.pairs[p0 + pp].ri].start;
-            float tot = 0.0f;
-            for (int s0 = 0; s0 < n; s0 += segn) {
-                const int sn = min(segn, n - s0);
-                __syncthreads();                      // the previous segment is consumed
-                if (pp == 0 || n > segn)
-                    for (int q = t; q < sn; q += blockDim.x) gys[q] = gyo[s0 + q];
-                for (int q = t; q < sn + WC + cb; q += blockDim.x) {
-                    int pos = s0 + q + J.EMIN;               // in (-n, 2n)
-                    pos = pos < 0 ? pos + n : (pos >= n ? pos - n : pos);
-                    xs[q] = xi[pos];
-                }
-                __syncthreads();
-                const int j0 = (part * sn / NPART) & ~3, j1 = part + 1 == NPART ? sn : ((part + 1) * sn / NPART) & ~3;
-                for (int jb = j0; jb < j1; jb += 128) {
-                    const int je = min(jb + 128, j1);
-                    // four independent chains (the FMA latency, not the issue rate, bounds one)
-                    // (parts start at multiples of 4 pixels: gy comes as one broadcast float4)
-                    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-                    int j = jb;
-                    for (; j + 3 < je; j += 4) {
-                        const float4 g4 = *reinterpret_cast<const float4 *>(gys + j);
-                        a0 = fmaf(g4.x, xs[j + c], a0);
-                        a1 = fmaf(g4.y, xs[j + 1 + c], a1);
-                        a2 = fmaf(g4.z, xs[j + 2 + c], a2);
-                        a3 = fmaf(g4.w, xs[j + 3 + c], a3);
-                    }
-                    for (; j < je; ++j) a0 = fmaf(gys[j], xs[j + c], a0);
-                    tot += (a0 + a1) + (a2 + a3);
+// Belt rings, step 1: C[o][i][c] = sum_b sum_j gy_bo[j] x_bi[j + e], e = EMIN + c, for every
+// belt output ring o, input ring i of its window and offset c < WPM.  A block per (OB
+// consecutive belt output rings, pair of maps, chunk of RC positions of their windows);
+// the input rings the OB windows share are staged once.  A thread per (output ring,
+// quarter of the pixels (G groups), window ring, 8 consecutive offsets).  The two maps
+// travel together as float2 (gy pairs and x pairs interleaved in shared memory), so one
+// paired FMA does both; a thread keeps the 8 x pairs its offsets need at pixel j in
+// registers and, from pixel to pixel, loads one new pair (the window slides by one) and
+// one gy pair (shared by the threads of its output ring): 8 paired FMAs per two 64-bit
+// shared loads.  Pixels in segments of GT_SEG; each segment's sums go into a second
+// accumulator (blocked summation over the 4N pixels x maps).
+constexpr int GT_SEG = 256;     // pixels of a segment
+constexpr int GT_LAG = 8;       // offsets per thread
+__host__ __device__ __forceinline__ int gt_row(int segn, int ncb) { return segn + GT_LAG * ncb + 1; }   // odd: rows spread over banks
+
+__global__ void __launch_bounds__(512)
+k_grad_belt(const JobDesc J, const float *__restrict__ gy, float *C, int RC, int G, int OB, int NR) {
+    extern __shared__ float2 sm2[];
+    const int n = J.n4, R2 = 2 * J.HM + 1;
+    const int rb0 = blockIdx.x * OB, nout = min(OB, J.nb - rb0);
+    const int pc = blockIdx.z * RC;                    // the chunk's first position in each window
+    const int ncb = (J.WPM + GT_LAG - 1) / GT_LAG;
+    const int segn = min(n, GT_SEG);
+    const int LR = gt_row(segn, ncb);
+    // the rings the chunk covers in the block's windows (contiguous: windows are ring ranges
+    // that move with the output ring)
+    int rlo = 1 << 30, rhi = -1;
+    for (int k = 0; k < nout; ++k) {
+        const int o = J.b_lo + rb0 + k;
+        const int a = J.pair_off[o] + pc, e = min(J.pair_off[o] + pc + RC, J.pair_off[o + 1]) - 1;
+        if (a <= e) {
+            rlo = min(rlo, J.pairs[a].ri);
+            rhi = max(rhi, J.pairs[e].ri);
+        }
+    }
+    if (rhi < rlo) return;
+    const int nrows = min(rhi - rlo + 1, NR);
+    float2 *gys = sm2;                                 // [OB][segn]
+    float2 *xs = gys + (size_t)OB * segn;              // [NR][LR]
+    long long *xrow = reinterpret_cast<long long *>(xs + (size_t)NR * LR);   // [NR] input ring starts
+    const int t = threadIdx.x;
+    const int tpg = blockDim.x / (OB * G);
+    const int ob = t / (G * tpg), rem = t - ob * G * tpg, grp = rem / tpg, tt = rem - grp * tpg;
+    const int pp = tt % RC, cb = tt / RC;
+    const int o = J.b_lo + rb0 + ob;
+    const int np = ob < nout ? min(RC, J.pair_off[o + 1] - J.pair_off[o] - pc) : 0;
+    const int row = pp < np ? J.pairs[J.pair_off[o] + pc + pp].ri - rlo : 0;
+    const bool active = pp < np && cb < ncb && row < nrows;
+    const int qn = segn / G, qa = grp * qn;            // this group's pixels of a segment
+    const int b0 = 2 * blockIdx.y;
+    const bool two = b0 + 1 < J.batch;
+    float2 acc[GT_LAG];
+#pragma unroll
+    for (int m = 0; m < GT_LAG; ++m) acc[m] = make_float2(0.0f, 0.0f);
+    const int stage_w = segn + GT_LAG * ncb;           // x positions a segment needs per ring
+    for (int r = t; r < nrows; r += blockDim.x) xrow[r] = (long long)b0 * J.stride + J.rings[rlo + r].start;
+    const int lane = t & 31, nw = blockDim.x >> 5;
+    for (int s0 = 0; s0 < n; s0 += segn) {
+        __syncthreads();                               // the previous segment is consumed (and xrow is set)
+        for (int e = t; e < nout * segn; e += blockDim.x) {
+            const int k = e / segn, q = e - k * segn;
+            const float *g0 = gy + (long long)b0 * J.stride + J.rings[J.b_lo + rb0 + k].start + s0 + q;
+            gys[e] = make_float2(*g0, two ? g0[J.stride] : 0.0f);
+        }
+        // a warp per staged row, lanes along it (coalesced)
+        for (int r = t >> 5; r < nrows; r += nw) {
+            const float *xr = J.x + xrow[r];
+            float2 *dst = xs + r * LR;
+            for (int q = lane; q < stage_w; q += 32) {
+                int pos = s0 + q + J.EMIN;             // in (-n, 2n)
+                pos = pos < 0 ? pos + n : (pos >= n ? pos - n : pos);
+                dst[q] = make_float2(xr[pos], two ? xr[pos + J.stride] : 0.0f);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const float2 *xr = xs + row * LR + GT_LAG * cb + qa;
+            const float2 *gq = gys + ob * segn + qa;
+            float2 w[GT_LAG], a[GT_LAG];
+#pragma unroll
+            for (int m = 0; m < GT_LAG; ++m) {
+                w[m] = xr[m];
+                a[m] = make_float2(0.0f, 0.0f);
+            }
+            // at pixel q + u, offset m reads position q + u + m: slot (u + m) mod 8, slot u
+            // taking position q + u + 8 once pixel q + u is done
+            for (int q = 0; q < qn; q += GT_LAG) {
+#pragma unroll
+                for (int u = 0; u < GT_LAG; ++u) {
+                    const float2 g = gq[q + u];
+#pragma unroll
+                    for (int m = 0; m < GT_LAG; ++m) a[m] = __ffma2_rn(g, w[(u + m) % GT_LAG], a[m]);
+                    w[u] = xr[q + u + GT_LAG];
                 }
             }
-            red[part * WC + cl] = tot;
-            __syncthreads();
-            if (t < WC && cb + t < J.WPM) {
-                float v = 0.0f;
-                for (int q = 0; q < NPART; ++q) v += red[q * WC + t];
-                atomicAdd(&C[((size_t)rb * R2 + pp) * J.WPM + cb + t], v);
-            }
+#pragma unroll
+            for (int m = 0; m < GT_LAG; ++m) acc[m] = __fadd2_rn(acc[m], a[m]);
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < GT_LAG; ++m) {
+            const int c = GT_LAG * cb + m;
+            if (c < J.WPM) atomicAdd(&C[((size_t)(rb0 + ob) * R2 + pc + pp) * J.WPM + c], acc[m].x + acc[m].y);
         }
     }
 }
@@ -404,14 +441,55 @@ cudaError_t sk_launch_grad_general(const JobsArg &a, const float *gy, double *ac
 
 size_t sk_grad_belt_floats(const JobDesc &j) { return (size_t)j.nb * (2 * j.HM + 1) * j.WPM; }
 
-cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, cudaStream_t st) {
+cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, const int *h_lo,
+                                const int *h_np, cudaStream_t st) {
     if (j.nb <= 0 || j.batch <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * sk_grad_belt_floats(j), st);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * ((size_t)2 * SEG + j.WPM + 32 + GW * 32);
+    // window positions per block (RC), output rings per block (OB) and pixel groups (G): a
+    // thread per (output, group, position, 8 offsets), at most 512; the staged rows of a
+    // block (its outputs' windows at the chunk, NR at most) in about 200 KB of shared memory
+    const int R2 = 2 * j.HM + 1, ncb = (j.WPM + GT_LAG - 1) / GT_LAG;
+    const int segn = j.n4 < GT_SEG ? j.n4 : GT_SEG;
+    const size_t row = sizeof(float2) * (size_t)gt_row(segn, ncb) + sizeof(long long);
+    const size_t smem_max = 200 * 1024;
+    if (ncb > 512) return cudaErrorInvalidConfiguration;
+    int RC = R2 * ncb > 512 ? 512 / ncb : R2;
+    int OB = 4;
+    auto rows_needed = [&](int ob, int rc) {           // max over blocks of the staged rows
+        int nr = 1;
+        for (int rb0 = 0; rb0 < j.nb; rb0 += ob)
+            for (int pc = 0; pc < R2; pc += rc) {
+                int lo = 1 << 30, hi = -1;
+                for (int k = 0; k < ob && rb0 + k < j.nb; ++k) {
+                    const int a = pc, z = (pc + rc < h_np[rb0 + k] ? pc + rc : h_np[rb0 + k]) - 1;
+                    if (a <= z) {
+                        lo = lo < h_lo[rb0 + k] + a ? lo : h_lo[rb0 + k] + a;
+                        hi = hi > h_lo[rb0 + k] + z ? hi : h_lo[rb0 + k] + z;
+                    }
+                }
+                if (hi >= lo && hi - lo + 1 > nr) nr = hi - lo + 1;
+            }
+        return nr;
+    };
+    int tpg = (RC * ncb + 31) / 32 * 32;
+    while (OB > 1 && OB * tpg > 512) --OB;
+    int NR = rows_needed(OB, RC);
+    while (sizeof(float2) * OB * segn + row * NR > smem_max && (OB > 1 || RC > 1)) {
+        if (OB > 1) --OB;
+        else RC = RC > 1 ? RC / 2 : 1;
+        tpg = (RC * ncb + 31) / 32 * 32;
+        NR = rows_needed(OB, RC);
+    }
+    if (sizeof(float2) * OB * segn + row * NR > smem_max) return cudaErrorInvalidConfiguration;
+    int G = 512 / (OB * tpg);
+    G = G > 4 ? 4 : (G < 1 ? 1 : G);
+    while (G > 1 && (segn % (8 * G)) != 0) --G;
+    const size_t smem = sizeof(float2) * OB * segn + row * NR;
     e = cudaFuncSetAttribute(k_grad_belt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_grad_belt<<<dim3(j.nb, j.batch), 32 * GW, smem, st>>>(j, gy, C);
+    const dim3 grid((j.nb + OB - 1) / OB, (j.batch + 1) / 2, (R2 + RC - 1) / RC);
+    k_grad_belt<<<grid, OB * G * tpg, smem, st>>>(j, gy, C, RC, G, OB, NR);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const long long nbins = (long long)sk_grad_belt_floats(j);
     k_grad_belt_bins<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(j, C, acc);

@@ -809,8 +809,14 @@ int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, 
                 JobDesc d = belt_desc(jb, nullptr);
                 float *C = reinterpret_cast<float *>(reinterpret_cast<char *>(acc) + grad_bins_bytes(k) +
                                                      sk_sym_bytes(k, batch));
+                std::vector<int> lo(k->nb), np(k->nb);
+                for (int rb = 0; rb < k->nb; ++rb) {
+                    const int o = k->b_lo + rb;
+                    lo[rb] = k->h_pairs[k->h_pair_off[o]].ri;
+                    np[rb] = k->h_pair_off[o + 1] - k->h_pair_off[o];
+                }
                 cudaEvent_t ev = sk_prof_begin(ctx, st);
-                SK_CU(sk_launch_grad_belt(d, gy, C, acc, st));
+                SK_CU(sk_launch_grad_belt(d, gy, C, acc, lo.data(), np.data(), st));
                 sk_prof_end(ctx, "grad_belt", ev, st);
             }
             // cap rings: symmetric base pairs over x's symmetric copy (after the FP64 bins)

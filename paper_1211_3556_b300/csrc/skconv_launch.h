@@ -126,6 +126,9 @@ cudaError_t sk_launch_grad_finish(const double *acc, int nt, double scale, float
 // belt rings by ring-pair cross-correlations (j: the belt fields, x, batch, stride) into the
 // FP32 sums C (sk_grad_belt_floats(j) floats), then the bins
 size_t sk_grad_belt_floats(const JobDesc &j);
-cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, cudaStream_t st);
+// h_lo, h_np: per belt output ring (rb = 0 .. nb - 1), the first ring of its window and
+// the window's ring count (host arrays; the launch shapes depend on them)
+cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, const int *h_lo,
+                                const int *h_np, cudaStream_t st);
 // cap rings by symmetric base pairs (a.j[0]: the cap items, x's symmetric copy in hx)
 cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, cudaStream_t st);
