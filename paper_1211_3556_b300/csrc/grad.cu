@@ -324,11 +324,11 @@ __device__ __forceinline__ float dot4(const float *g, float4 h) {
 }
 
 // Cap rings: a thread per base output of a cap item (the forward's items: 256 base
-// outputs), maps four at a time.  The 16 images of the base output (quarter turns,
+// outputs, taken 32 at a time by a warp), maps four at a time.  The 16 images of the base output (quarter turns,
 // hemispheres, reflection; 8 on a symmetry axis) take gy_b from the map, the images of
 // the input pixel a come from the symmetric copy H (H[a], H[a + n/4], and the reflection
-// b = n/4 - s - a: H[b], H[b + n/4]), in the pairing the forward kernel uses; one FP64
-// (k, f) per base pair.
+// b = n/4 - s - a: H[b], H[b + n/4]), in the pairing the forward kernel uses; one (k, f)
+// per base pair and four maps (double-float, or FP64).
 constexpr int GC = 4;           // maps per pass of the cap gradient
 __global__ void __launch_bounds__(256)
 k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, double *acc) {
@@ -340,9 +340,17 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
     // node coordinates in double-float where pair_kf_df applies (uniform nodes, small cut)
     const bool dfpath = J.kp.small_angle && J.kp.layout == 0;
     const KernDF KD{df_from(J.kd.tcut), df_from(J.kd.inv_h)};
-    for (int f = blockIdx.x; f < J.n_items; f += gridDim.x) {
-        const int4 it = J.items[f];
-        const int ro = it.x, jo = it.y + (int)threadIdx.x;
+    // warps take tasks of 32 base outputs (an eighth of an item) from a queue, in the
+    // items' order (heaviest first): no lane waits on a short ring's item, no warp on a
+    // block's last item
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(A.queue, 1);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if (task >= 8 * J.n_items) break;
+        const int4 it = J.items[task >> 3];
+        const int ro = it.x, j1 = it.y + 32 * (task & 7), jo = j1 + lane;
         const RingDev R = J.rings[ro];
         const int Qo = R.n >> 2;
         const int T = R.s ? (Qo + 1) / 2 : Qo / 2 + 1;
@@ -501,6 +509,7 @@ cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, i
     const size_t smem = (size_t)a.j[0].kp.nt * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_grad_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (!a.queue) return cudaErrorInvalidValue;       // the task queue (zeroed by the caller)
     k_grad_cap<<<grid, 256, smem, st>>>(a, gy, acc);
     return cudaGetLastError();
 }

@@ -838,8 +838,12 @@ int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, 
                         a.n_jobs = 1;
                         a.total = k->n_items_cap[c][v];
                         a.status = ctx->d_status;
+                        a.queue = ctx->d_queue + ctx->next_queue;
+                        ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
+                        SK_CU(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
                         ev = sk_prof_begin(ctx, st);
-                        SK_CU(sk_launch_grad_cap(a, gy, acc, grid_for(a.total, 4, ctx->num_sms), st));
+                        // persistent blocks (two per SM: 256 threads of 128 registers)
+                        SK_CU(sk_launch_grad_cap(a, gy, acc, std::min(8 * a.total, 2 * ctx->num_sms), st));
                         sk_prof_end(ctx, "grad_cap", ev, st);
                     }
             }
