@@ -299,11 +299,22 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
     uint32_t pend = 0;      // bit b set while a copy this thread's warp issued into buffer b is not waited for
     // work queue: each slot takes the next item (items are ordered heaviest first), so the
     // slots that drew light items take more of them and all finish together
+    // With two buffers the warp that stages after an item's last ring also takes the
+    // slot's next item from the queue (one ring before it is needed, so the queue's
+    // balance is kept) and stages that item's first strip into the free buffer: the item
+    // boundary then waits neither for the queue atomic nor for a first copy.  The buffer
+    // of an item's first ring (bbase) follows on from the previous item's last ring.
     __shared__ int s_item[SLOTS];
+    __shared__ int s_pref[SLOTS];       // 1: the item's first strip is staged already
+    if (t == 0) {
+        s_item[slot] = atomicAdd(A.queue, 1);
+        s_pref[slot] = 0;
+    }
+    int bbase = 0;
     for (;;) {
-        if (t == 0) s_item[slot] = *abort_flag ? A.total : atomicAdd(A.queue, 1);
         slot_sync(slot);
         const int f = s_item[slot];
+        const bool pref = NB == 2 && s_pref[slot] != 0;
         if (f >= A.total) break;
         const JobDesc &J = A.j[sk_find_job(A, f)];
         const int local = f - J.flat_base;
@@ -342,9 +353,29 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 pend |= 1u << b;
             }
         };
-        if (NB == 2 && p0 < p1) issue(p0, 0);
+        // the first strip of item fn into buffer b, by the calling warp (bulk copies; a strip
+        // that wraps its ring is copied by the item itself); returns whether it was staged
+        auto stage_first = [&](int fn, int b) -> int {
+            const JobDesc &Jn = A.j[sk_find_job(A, fn)];
+            const int ln = fn - Jn.flat_base;
+            const int mn = ln / Jn.n_items;
+            const int4 itn = Jn.items[ln - mn * Jn.n_items];
+            const RingDev Rn = Jn.rings[itn.x];
+            const int jln = min(itn.y + CT - 1, base_count(Rn.n >> 2, Rn.s) - 1);
+            const PairInfo Pn = Jn.pairs[Jn.pair_off[itn.x]];
+            const Strip Sn = strip_of(Pn, itn.y, jln, Rn.n, Rn.s, (unsigned)itn.z, itn.w);
+            const int stop = __shfl_sync(0xffffffffu, *abort_flag, 0);
+            if (Sn.L < Pn.n_i && !stop) {
+                const float4 *hn = Jn.hx + (long long)mn * Jn.hstride;
+                issue_strip<LS>(sbuf + b * 4 * LS, bar0 + 8 * b, hn + Jn.rings[Pn.ri].start, Sn, Pn, t & 31);
+                pend |= 1u << b;
+                return 1;
+            }
+            return 0;
+        };
+        if (NB == 2 && !pref && p0 < p1) issue(p0, bbase);
         for (int p = p0; p < p1; ++p) {
-            const int b = NB == 2 ? ((p - p0) & 1) : 0;
+            const int b = NB == 2 ? (((p - p0) + bbase) & 1) : 0;
             float4 *const xbuf = sbuf + b * 4 * LS;
             const PairInfo P = J.pairs[p];
             const Strip S = strip_of(P, j0, jlast, R.n, R.s, mg, sh);
@@ -352,8 +383,20 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
             // every thread is done with ring p - 1: its buffer takes ring p + 1 (two
             // buffers) or ring p (one)
             if (NB == 2) {
-                ring_handover(slot, (p - p0) & 1, ((p + 1 - p0) & 3) == (t >> 5));
-                if (p + 1 < p1) issue(p + 1, b ^ 1);
+                const bool stager = ((p + 1 - p0) & 3) == (t >> 5);
+                ring_handover(slot, (p - p0) & 1, stager);
+                if (p + 1 < p1) {
+                    issue(p + 1, b ^ 1);
+                } else if (stager) {
+                    int fn = 0;
+                    if ((t & 31) == 0) fn = *abort_flag ? A.total : atomicAdd(A.queue, 1);
+                    fn = __shfl_sync(0xffffffffu, fn, 0);
+                    const int staged = fn < A.total ? stage_first(fn, b ^ 1) : 0;
+                    if ((t & 31) == 0) {
+                        s_item[slot] = fn;          // read after the slot barrier that opens the next item
+                        s_pref[slot] = staged;
+                    }
+                }
             } else {
                 slot_sync(slot);
                 if (bulk) issue(p, 0);
@@ -447,8 +490,13 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                 }
             }
         }
-        // the next item stages into this slot's buffers: everyone must be done reading them
-        slot_sync(slot);
+        if (NB == 2) {
+            bbase = ((p1 - p0) + bbase) & 1;        // the buffer the next item's first strip went to
+        } else {
+            // the next item stages into this slot's one buffer: everyone must be done reading it
+            slot_sync(slot);
+            if (t == 0) s_item[slot] = *abort_flag ? A.total : atomicAdd(A.queue, 1);
+        }
         if (*abort_flag) continue;
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
