@@ -155,7 +155,9 @@ int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_
 /* The outputs of rings [ring_lo, ring_hi) (0-based RING rings) of y = A x, for a
  * ring-band decomposition of one map over several devices (each device owns a band
  * of output rings and needs the input rings within theta_cut of it, a halo; the
- * rest of d_in may hold anything).  Runs the work items that write those rings;
+ * rest of d_in may hold any finite values -- zeros, say -- but no NaN or Inf: some
+ * sums multiply pixels outside an output's window by a zero weight, and 0 times NaN
+ * is NaN).  Runs the work items that write those rings;
  * items that also write rings outside the range (a belt ring group across its
  * edge, the other hemisphere of a cap ring) write values there that depend on
  * inputs outside the halo: the caller keeps only its band.  In the range the

@@ -326,8 +326,9 @@ def convolve(kern: Kernel, x, out=None, path: int = PATH_AUTO, stream=None):
 
 def convolve_rings(kern: Kernel, x, ring_lo: int, ring_hi: int, out=None, stream=None):
     """The outputs of rings [ring_lo, ring_hi) (0-based) of y = A x, for a ring-band
-    decomposition (see bands.py): x needs valid values on the band's halo rings only, and
-    out is valid on the band only (other rings may hold partial sums)."""
+    decomposition (see bands.py): x needs valid values on the band's halo rings only (the
+    rest finite, e.g. zeros: zero weights meet some pixels outside a window), and out is
+    valid on the band only (other rings may hold partial sums)."""
     import torch
     x2, b, stride = _map_args(x, kern.geom.npix)
     if out is None:
