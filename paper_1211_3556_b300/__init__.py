@@ -456,7 +456,9 @@ class PolarPatch:
 
     def convolve(self, x, out=None, stream=None, work=None):
         """y on the field's sky rings (other pixels of out untouched; zeros if out is None).
-        work: optional pair of scratch maps shaped like x (the rotated input and output)."""
+        work: optional pair of scratch maps shaped like x (the rotated input and output; the
+        first must hold finite values, e.g. zeros, beyond the cap rings, which it is not
+        written on)."""
         import torch
         if work is None:
             x2, _, _ = _map_args(x, self.kern.geom.npix)
