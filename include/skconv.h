@@ -135,8 +135,8 @@ int sk_kernel_update_values(sk_kern *k, const double *h_values);
 int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out);
 
 /* Pair counts split by the path that evaluates each output ring:
- * out3[0] belt (ring-wise Toeplitz sums), out3[1] polar caps (8-fold
- * symmetric per-pair evaluation), out3[2] per-pair general path.  Their sum is
+ * out3[0] belt (ring-wise Toeplitz sums), out3[1] polar caps (one weight
+ * evaluation for up to 16 symmetric pairs), out3[2] per-pair general path.  Their sum is
  * sk_count_pairs.  Blocks until done.  Errors: SK_EINVAL, SK_ECUDA. */
 int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3);
 
@@ -144,7 +144,9 @@ int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3);
 
 /* y = A x for `batch` maps (the real-space convolution above).
  * d_in, d_out: [batch][map_stride] FP32 device buffers.  batch >= 0 (0 is a
- * no-op).  Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+ * no-op).  Inputs should be finite: some sums multiply pixels just outside an
+ * output's window by a zero weight, so a NaN or Inf can reach outputs beyond its
+ * cut.  Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int sk_convolve(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
                 int64_t batch, int64_t map_stride, void *stream);
 
