@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-fourier", action="store_true", help="skip the wide-cut (ring-pair Fourier) side measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint + table gradient) side measurement")
     ap.add_argument("--no-field", action="store_true", help="skip the partial-sky field (polar-cap) side measurement")
+    ap.add_argument("--no-bands", action="store_true", help="skip the ring-band (one map over several GPUs) side measurement")
     return ap.parse_args()
 
 
@@ -458,6 +459,32 @@ def run_ours(args):
                 "step_ms": ms_fwd + ms_adj + ms_tab}
         del xg, gy, yg, gx
 
+    # ring bands of the step's map (the decomposition of one map over several GPUs), run one
+    # band after another on this GPU: each band's time is what its rank would take, so
+    # full / (ranks x slowest band) bounds the strong-scaling efficiency of the sums; bands of
+    # a northern range and its mirror, balanced by estimated cost (symmetric_bands)
+    bands = None
+    if not args.no_bands and args.workload == "n2048_plain" and world == 1:
+        from paper_1211_3556_b300.bands import symmetric_bands
+        o = ops[0]
+        grp = o["group"]
+        xb = o["x"][:1]
+        yb = torch.empty_like(xb)
+        nb_steps = max(3, min(args.steps, 10))
+        full = time_steps(torch, lambda: sk.convolve(o["kern"], xb, out=yb), nb_steps, 1, barrier)
+        bands = {"workload": args.workload, "decomposition": "symmetric_bands (cap_cost 2.5)",
+                 "ms_full_map": full, "ranks": {}}
+        for nrk in (2, 4, 8):
+            per = []
+            for b in symmetric_bands(grp.nside, grp.kernel.theta_cut, nrk):
+                lo, hi = b.north
+                if hi > lo:
+                    per.append(time_steps(torch, lambda: sk.convolve_rings_sym(o["kern"], xb, lo, hi, out=yb),
+                                          nb_steps, 1, barrier))
+            bands["ranks"][str(nrk)] = {"ms_per_band": per, "ms_slowest": max(per),
+                                        "efficiency_bound": full / (nrk * max(per))}
+        del xb, yb
+
     # a partial-sky field at Nside 8192 (5'): re-oriented onto the polar cap, its cap rings
     # summed, rotated back; against the full-sky operator of the same kernel
     field = None
@@ -529,6 +556,7 @@ def run_ours(args):
             "fourier": fourier,
             "grad": grad,
             "field": field,
+            "bands": bands,
             "cpu_baseline": cpu_baseline,
             "context": "paper: GTX 480 + 1 Core2 core, split convolution >10x faster than a full "
                        "single-core SHT convolution (eq. 3 model: 2.89 s at theta_cut 20')",

@@ -168,6 +168,15 @@ int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_
 int sk_convolve_rings(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
                       int64_t map_stride, int ring_lo, int ring_hi, void *stream);
 
+/* The same for rings [ring_lo, ring_hi) together with their mirror rings about the
+ * equator, [rings - ring_hi, rings - ring_lo): a band made of a northern range and its
+ * southern image.  A polar-cap work item sums a ring and its mirror at once, so a
+ * symmetric band runs each such item once, where two one-sided bands would both run it.
+ * The halo is the input rings within theta_cut of either range.  Otherwise as
+ * sk_convolve_rings (the two ranges may overlap at the equator). */
+int sk_convolve_rings_sym(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
+                          int64_t map_stride, int ring_lo, int ring_hi, void *stream);
+
 /* Re-orientation of maps by a rotation (nearest-centre resampling), for partial-sky
  * maps moved onto the polar cap, where they occupy few rings and the real-space sums
  * touch only those (Sec. 4; with sk_convolve_rings).  For every output pixel p of

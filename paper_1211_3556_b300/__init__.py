@@ -67,6 +67,7 @@ def _declare(L):
         "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
         "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
         "sk_convolve_rings": (I, [P, P, P, P, I64, I64, I, I, P]),
+        "sk_convolve_rings_sym": (I, [P, P, P, P, I64, I64, I, I, P]),
         "sk_resample": (I, [P, P, P, P, I64, I64, P, I, I, I, P]),
         "sk_resample_plan_create": (I, [P, P, P, I, I, I, PP]),
         "sk_resample_plan_destroy": (I, [P]),
@@ -467,6 +468,22 @@ class PolarPatch:
         self.to_cap.apply(x, out=xr, stream=stream)
         convolve_rings(self.kern, xr, 0, self.out_hi, out=yr, stream=stream)
         return self.to_sky.apply(yr, out=out, stream=stream)
+
+
+def convolve_rings_sym(kern: Kernel, x, ring_lo: int, ring_hi: int, out=None, stream=None):
+    """convolve_rings for rings [ring_lo, ring_hi) and their mirrors about the equator (a band
+    of bands.symmetric_bands): the polar-cap sums of a ring and its mirror run once."""
+    import torch
+    x2, b, stride = _map_args(x, kern.geom.npix)
+    if out is None:
+        out = torch.empty_like(x2)
+    o2, b2, stride2 = _map_args(out, kern.geom.npix)
+    if b2 != b or stride2 != stride:
+        raise ValueError("out must match x in shape and strides")
+    _check(lib().sk_convolve_rings_sym(kern.ctx._h, kern._h, ctypes.c_void_p(x2.data_ptr()),
+                                       ctypes.c_void_p(o2.data_ptr()), b, stride, int(ring_lo), int(ring_hi),
+                                       _stream_ptr(stream)))
+    return out
 
 
 def convolve_adjoint(kern: Kernel, gy, out=None, stream=None):

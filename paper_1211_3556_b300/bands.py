@@ -10,6 +10,12 @@ every rank by one all-gather of the ranks' own bands (each keeps its halo); each
 then computes its band with convolve_rings and the outputs stay sharded (or are
 gathered the same way).  Host-side logic only: the ring tables follow the HEALPix
 RING scheme (Gorski et al. 2005, the pixelisation of Sec. 2).
+
+symmetric_bands gives each rank a northern range of rings and its mirror about the
+equator instead (convolve_rings_sym): the polar-cap sums treat a ring and its mirror
+together, so a one-sided band holding cap rings would also pay for their mirrors, and
+the bands are balanced by an estimate of their cost (pixels, with the cap rings weighted
+by the cost of a cap pair relative to a belt pair) rather than by pixel count.
 """
 from __future__ import annotations
 
@@ -75,22 +81,92 @@ def ring_bands(nside: int, theta_cut: float, world: int) -> list:
     return out
 
 
-def gather_halo(x_own, band: Band, bands: list, npix: int, group=None):
-    """The input map of `band`'s rank from every rank's own pixels: x_own [batch, p1 - p0]
-    holds this rank's band of the input (its out_pix range).  One all-gather (padded to the
-    largest band); returns [batch, npix] with the halo filled and zeros elsewhere."""
+def _ranges(r) -> list:
+    """A band's ring or pixel ranges as a list of (lo, hi)."""
+    return [tuple(q) for q in r] if len(r) and isinstance(r[0], (tuple, list)) else [tuple(r)]
+
+
+def _merge(ranges) -> tuple:
+    out = []
+    for lo, hi in sorted(r for r in ranges if r[1] > r[0]):
+        if out and lo <= out[-1][1]:
+            out[-1] = (out[-1][0], max(out[-1][1], hi))
+        else:
+            out.append((lo, hi))
+    return tuple(out)
+
+
+@dataclass(frozen=True)
+class SymBand:
+    rank: int
+    north: tuple         # [lo, hi): northern rings (hi at most the equator ring + 1)
+    out_rings: tuple     # ring ranges written: the north range and its mirror, merged where they meet
+    in_rings: tuple      # ring ranges within theta_cut of them
+    out_pix: tuple       # the same as pixel ranges (RING order)
+    in_pix: tuple
+
+
+def symmetric_bands(nside: int, theta_cut: float, world: int, cap_cost: float = 2.5) -> list:
+    """Split the northern rings (the equator included) into `world` contiguous ranges of
+    about equal estimated cost, each with its mirror about the equator.  The cost of a
+    northern ring: its pixels, twice (the ring and its mirror; the equator once), times
+    cap_cost on the polar-cap rings (ring index below Nside, 1-based)."""
+    n, start, theta = ring_table(nside)
+    nr = len(n)
+    N = int(nside)
+    eq = 2 * N - 1                                    # the equator ring (0-based), its own mirror
+    w = np.array([n[r] * (cap_cost if r < N - 1 else 1.0) * (1.0 if r == eq else 2.0) for r in range(eq + 1)])
+    cum = np.cumsum(w)
+    world = max(1, min(int(world), eq + 1))
+    edges = [0]
+    for k in range(1, world):
+        edges.append(max(edges[-1] + 1, int(np.searchsorted(cum, k * cum[-1] / world)) + 1))
+    edges.append(eq + 1)
+    edges = [min(e, eq + 1) for e in edges]
+    eps = 1e-6 * max(1.0, theta_cut)                  # the margin of ring_bands
+
+    def halo(lo, hi):
+        ilo = int(np.searchsorted(theta, theta[lo] - theta_cut - eps, side="left"))
+        ihi = int(np.searchsorted(theta, theta[hi - 1] + theta_cut + eps, side="right"))
+        return ilo, ihi
+
+    def pix(rr):
+        return tuple((int(start[lo]), int(start[hi - 1] + n[hi - 1])) for lo, hi in rr)
+
+    out = []
+    for rank in range(world):
+        lo, hi = edges[rank], edges[rank + 1]
+        if hi <= lo:
+            out.append(SymBand(rank, (lo, lo), (), (), (), ()))
+            continue
+        rings = _merge([(lo, hi), (nr - hi, nr - lo)])
+        halos = _merge([halo(a, b) for a, b in rings])
+        out.append(SymBand(rank, (lo, hi), rings, halos, pix(rings), pix(halos)))
+    return out
+
+
+def gather_halo(x_own, band, bands: list, npix: int, group=None):
+    """The input map of `band`'s rank from every rank's own pixels: x_own [batch, own]
+    holds this rank's band of the input (its out_pix ranges, concatenated in order).  One
+    all-gather (padded to the largest band); returns [batch, npix] with the halo filled
+    and zeros elsewhere.  Bands of ring_bands or of symmetric_bands."""
     import torch
     import torch.distributed as dist
     batch = x_own.shape[0]
-    width = max(b.out_pix[1] - b.out_pix[0] for b in bands)
+    own = [_ranges(b.out_pix) if len(b.out_pix) else [] for b in bands]
+    width = max(sum(q1 - q0 for q0, q1 in r) for r in own)
     mine = torch.zeros(batch, width, dtype=x_own.dtype, device=x_own.device)
     mine[:, : x_own.shape[1]] = x_own
     parts = [torch.empty_like(mine) for _ in bands]
     dist.all_gather(parts, mine, group=group)
     full = torch.zeros(batch, npix, dtype=x_own.dtype, device=x_own.device)
-    p0, p1 = band.in_pix
-    for b, part in zip(bands, parts):
-        q0, q1 = max(b.out_pix[0], p0), min(b.out_pix[1], p1)
-        if q1 > q0:
-            full[:, q0:q1] = part[:, q0 - b.out_pix[0]: q1 - b.out_pix[0]]
+    halo = _ranges(band.in_pix) if len(band.in_pix) else []
+    for ranges, part in zip(own, parts):
+        pos = 0
+        for q0, q1 in ranges:
+            for p0, p1 in halo:
+                a, z = max(q0, p0), min(q1, p1)
+                if z > a:
+                    full[:, a:z] = part[:, pos + a - q0: pos + z - q0]
+            pos += q1 - q0
     return full

@@ -511,22 +511,34 @@ extern "C" int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in
     return sk_run_jobs(ctx, &jb, 1, path, ws, (cudaStream_t)stream);
 }
 
-extern "C" int sk_convolve_rings(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
-                                 int64_t map_stride, int ring_lo, int ring_hi, void *stream) {
-    if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve_rings: NULL context");
-    int rc = sk_check_maps("sk_convolve_rings", k, d_in, d_out, batch, map_stride);
+static int convolve_ring_subset(const char *who, sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
+                                int64_t batch, int64_t map_stride, int ring_lo, int ring_hi, bool sym, void *stream) {
+    if (!ctx) return sk_fail(SK_EINVAL, "%s: NULL context", who);
+    int rc = sk_check_maps(who, k, d_in, d_out, batch, map_stride);
     if (rc) return rc;
     if (ring_lo < 0 || ring_hi > k->g->nr || ring_lo > ring_hi)
-        return sk_fail(SK_EINVAL, "sk_convolve_rings: ring range [%d, %d) outside [0, %d)", ring_lo, ring_hi, k->g->nr);
+        return sk_fail(SK_EINVAL, "%s: ring range [%d, %d) outside [0, %d)", who, ring_lo, ring_hi, k->g->nr);
     if (batch == 0 || ring_lo == ring_hi) return SK_OK;
     SK_CU(cudaSetDevice(ctx->device));
     const SkItems *sub = nullptr;
-    if ((rc = sk_plan_ring_subset(const_cast<sk_kern *>(k), ring_lo, ring_hi, &sub))) return rc;
+    if ((rc = sk_plan_ring_subset(const_cast<sk_kern *>(k), ring_lo, ring_hi, sym, &sub))) return rc;
     SkJob jb{k, d_in, d_out, batch, map_stride};
     jb.sub = sub;
     void *ws = nullptr;
     if ((rc = sk_ctx_workspace(ctx, sk_jobs_workspace_bytes(&jb, 1), &ws))) return rc;
     return sk_run_jobs(ctx, &jb, 1, SK_PATH_AUTO, ws, (cudaStream_t)stream);
+}
+
+extern "C" int sk_convolve_rings(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
+                                 int64_t map_stride, int ring_lo, int ring_hi, void *stream) {
+    return convolve_ring_subset("sk_convolve_rings", ctx, k, d_in, d_out, batch, map_stride, ring_lo, ring_hi,
+                                false, stream);
+}
+
+extern "C" int sk_convolve_rings_sym(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
+                                     int64_t map_stride, int ring_lo, int ring_hi, void *stream) {
+    return convolve_ring_subset("sk_convolve_rings_sym", ctx, k, d_in, d_out, batch, map_stride, ring_lo, ring_hi,
+                                true, stream);
 }
 
 extern "C" int sk_convolve(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,

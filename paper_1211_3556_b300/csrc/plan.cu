@@ -97,13 +97,13 @@ void sk_plan_free(sk_kern *k) {
     k->plan_ok = false;
 }
 
-int sk_plan_ring_subset(sk_kern *k, int lo, int hi, const SkItems **out) {
+int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **out) {
     std::lock_guard<std::mutex> lock(k->subsets_mu);
     for (auto &r : k->subsets)
-        if (r.lo == lo && r.hi == hi && r.P == k->belt_P) { *out = &r.items; return SK_OK; }
+        if (r.lo == lo && r.hi == hi && r.sym == sym && r.P == k->belt_P) { *out = &r.items; return SK_OK; }
     const sk_geom *g = k->g;
     const int nr = g->nr;
-    auto in = [&](int r) { return r >= lo && r < hi; };
+    auto in = [&](int r) { return (r >= lo && r < hi) || (sym && nr - 1 - r >= lo && nr - 1 - r < hi); };
     std::vector<int4> all;
     size_t off_belt = 0, n_belt = 0, off_cap[SK_CAP_LS_CLASSES][2] = {}, n_cap[SK_CAP_LS_CLASSES][2] = {};
     size_t off_gen = 0, n_gen = 0;
@@ -113,7 +113,7 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, const SkItems **out) {
         // northern ring and the mirror; a per-pair item its ring
         for (const int4 &it : k->h_items_belt) {
             const int r0 = k->b_lo + it.x * SK_BELT_G, r1 = std::min(r0 + SK_BELT_G, k->b_lo + k->nb);
-            if (r0 < hi && r1 > lo) all.push_back(it);
+            if ((r0 < hi && r1 > lo) || (sym && r0 < nr - lo && r1 > nr - hi)) all.push_back(it);
         }
         n_belt = all.size();
         for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
@@ -129,11 +129,12 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, const SkItems **out) {
             if (in(it.x)) all.push_back(it);
     } else {
         off_gen = 0;
-        for (int r = std::max(lo, 0); r < std::min(hi, nr); ++r)
-            for (int j = 0; j < g->h_rings[r].n; j += 128) all.push_back(make_int4(r, j, 0, 0));
+        for (int r = 0; r < nr; ++r)
+            if (in(r))
+                for (int j = 0; j < g->h_rings[r].n; j += 128) all.push_back(make_int4(r, j, 0, 0));
     }
     n_gen = all.size() - off_gen;
-    sk_kern::RingSubset rs{lo, hi, k->belt_P, nullptr, SkItems{}};
+    sk_kern::RingSubset rs{lo, hi, k->belt_P, sym, nullptr, SkItems{}};
     if (!all.empty()) {
         cudaError_t e = cudaMalloc(&rs.d_items, sizeof(int4) * all.size());
         if (e == cudaSuccess) e = cudaMemcpy(rs.d_items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice);

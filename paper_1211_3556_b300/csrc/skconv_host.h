@@ -127,6 +127,7 @@ struct sk_kern {
     // guards it against concurrent first calls)
     struct RingSubset {
         int lo, hi, P;
+        bool sym;                          // the range and its mirror about the equator
         int4 *d_items;
         SkItems items;
     };
@@ -162,7 +163,9 @@ struct SkJob {
 // Partition of k's items into ring bands (kept in k; rebuilt when stale).
 int sk_plan_bands(sk_kern *k);
 // The items that write output rings [lo, hi) (kept in k; *out points into it).
-int sk_plan_ring_subset(sk_kern *k, int lo, int hi, const SkItems **out);
+// Work items that write rings [lo, hi), and with sym also the mirror rings
+// [nr - hi, nr - lo) (a cap item, which writes a ring and its mirror, taken once).
+int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **out);
 // Launch sequence of the forward operator for a set of jobs.  `ws` must hold
 // sk_jobs_workspace_bytes(jobs) bytes: the belt weight rows of every job, then the
 // symmetric copies of every job's maps for the caps.

@@ -76,6 +76,36 @@ def test_bands_stitch_to_the_full_operator(sk, case, outside):
         assert rms_rel(stitched[m, outs], ref) <= 1e-6
 
 
+@pytest.mark.parametrize("case", CASES)
+def test_symmetric_bands_stitch_to_the_full_operator(sk, case):
+    # bands of a northern range and its mirror (convolve_rings_sym), from inputs that hold the
+    # halo and noise elsewhere: stitched, bit-identical to the full operator
+    import torch
+    from paper_1211_3556_b300.bands import symmetric_bands
+    nside, fwhm, tcm, lmax, lcut, nt, world, batch = case
+    tc = tcm * ARCMIN
+    V = O.tabulate_real_kernel(gaussian_beam(fwhm, lmax), lcut, lmax, tc, nt, 0)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc, 0)
+    x = white_noise_maps(nside, batch, 1350 + nside)
+    y_full = sk.convolve(k, torch.from_numpy(x).cuda()).cpu().numpy()
+    stitched = np.full_like(y_full, np.nan)
+    rng = np.random.default_rng(nside + 1)
+    for b in symmetric_bands(nside, tc, world):
+        lo, hi = b.north
+        if hi == lo:
+            continue
+        xm = (1e3 * rng.standard_normal(x.shape)).astype(np.float32)
+        for p0, p1 in b.in_pix:
+            xm[:, p0:p1] = x[:, p0:p1]
+        y = sk.convolve_rings_sym(k, torch.from_numpy(xm).cuda(), lo, hi).cpu().numpy()
+        for q0, q1 in b.out_pix:
+            assert np.all(np.isnan(stitched[:, q0:q1]))
+            stitched[:, q0:q1] = y[:, q0:q1]
+    sk._ctx.status()
+    assert np.array_equal(stitched, y_full)
+
+
 def test_convolve_rings_ranges(sk):
     import torch
     tc = 360.0 * ARCMIN

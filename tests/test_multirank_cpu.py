@@ -124,3 +124,97 @@ def test_ring_bands_tile_the_rings_and_cover_the_windows(nside, deg, world):
                 assert ilo <= i < ihi
             elif ilo <= i < ihi:
                 assert gap - tc <= 1e-6
+
+
+# ---------------------------------------------------------------- symmetric ring bands
+
+def _sym_band_rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import math
+    import torch
+    import torch.distributed as dist
+    import oracle as O
+    from inputs import gaussian_beam, white_noise_maps
+    from paper_1211_3556_b300.bands import gather_halo, symmetric_bands
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    nside, tc = 16, math.radians(12.0)
+    V = O.tabulate_real_kernel(gaussian_beam(240.0, 32), 8, 32, tc, 512, 0)
+    x = white_noise_maps(nside, 1, 78)[0].astype(np.float64)
+    npix = x.size
+    bands = symmetric_bands(nside, tc, world)
+    me = bands[rank]
+    # each rank starts from its own rings only (north range and mirror, concatenated)
+    outs_mine = np.concatenate([np.arange(q0, q1, dtype=np.int64) for q0, q1 in me.out_pix])
+    x_own = torch.from_numpy(x[None, outs_mine].copy())
+    x_halo = gather_halo(x_own, me, bands, npix)[0].numpy()
+    inside = np.zeros(npix, bool)
+    for p0, p1 in me.in_pix:
+        inside[p0:p1] = True
+    y_mine = O.conv_window(nside, V, tc, 0, x_halo, outs=outs_mine)
+    res = [None] * world
+    dist.all_gather_object(res, (outs_mine.tolist(), y_mine.tolist()))
+    if rank == 0:
+        y = np.full(npix, np.nan)
+        for o, vals in res:
+            assert np.all(np.isnan(y[o]))                 # every pixel written by one rank only
+            y[o] = vals
+        out["stitched"] = y.tolist()
+        out["full"] = O.conv_window(nside, V, tc, 0, x).tolist()
+    out[f"halo_ok_{rank}"] = bool(np.all(x_halo[~inside] == 0) and np.array_equal(x_halo[inside], x[inside]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_symmetric_bands_halo_exchange_and_stitching_world_size_3():
+    # bands of a northern range and its mirror: halos (two ranges, or one where they meet)
+    # by one all-gather, each rank's sums from its halo (the oracle in place of the device),
+    # the stitched map equal to the full sum exactly
+    world = 3
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_sym_band_rank_main, args=(world, port, out), nprocs=world, join=True)
+    assert all(out[f"halo_ok_{r}"] for r in range(world))
+    assert np.array_equal(np.array(out["stitched"]), np.array(out["full"]))
+
+
+@pytest.mark.parametrize("nside,deg,world", [(8, 30.0, 2), (16, 12.0, 3), (64, 3.0, 5), (128, 1.0, 8)])
+def test_symmetric_bands_tile_the_rings_cover_the_windows_and_balance(nside, deg, world):
+    import math
+    from paper_1211_3556_b300.bands import ring_table, symmetric_bands
+    n, start, theta = ring_table(nside)
+    nr = len(n)
+    tc = math.radians(deg)
+    bands = symmetric_bands(nside, tc, world, cap_cost=2.5)
+    owner = np.full(nr, -1)
+    for b in bands:
+        lo, hi = b.north
+        assert 0 <= lo <= hi <= 2 * nside
+        for a, z in b.out_rings:
+            assert np.all(owner[a:z] == -1)
+            owner[a:z] = b.rank
+        for r in range(lo, hi):                               # a northern ring with its mirror
+            assert owner[r] == b.rank and owner[nr - 1 - r] == b.rank
+        inr = np.zeros(nr, bool)
+        for a, z in b.in_rings:
+            inr[a:z] = True
+        outs = [o for a, z in b.out_rings for o in range(a, z)]
+        for i in range(nr):
+            if not outs:
+                break
+            gap = min(abs(theta[i] - theta[o]) for o in outs)
+            if gap <= tc:
+                assert inr[i]
+            elif inr[i]:
+                assert gap - tc <= 1e-6
+        for (a, z), (p, q) in zip(b.out_rings, b.out_pix):
+            assert (p, q) == (start[a], start[z - 1] + n[z - 1])
+    assert np.all(owner >= 0)
+    # balance of the cost estimate the split uses
+    cost = []
+    for b in bands:
+        lo, hi = b.north
+        cost.append(sum(n[r] * (2.5 if r < nside - 1 else 1.0) * (1 if r == 2 * nside - 1 else 2)
+                        for r in range(lo, hi)))
+    ring_max = max(n[r] * 2.5 * 2 for r in range(2 * nside))
+    assert max(cost) - min(cost) <= 2 * ring_max + 1e-9
