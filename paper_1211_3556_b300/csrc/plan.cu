@@ -108,19 +108,34 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **ou
     size_t off_belt = 0, n_belt = 0, off_cap[SK_CAP_LS_CLASSES][2] = {}, n_cap[SK_CAP_LS_CLASSES][2] = {};
     size_t off_gen = 0, n_gen = 0;
     bool caps = false;
+    int bg0 = 0, bg1 = -1;                 // belt groups (all without a plan)
+    int smin = 1 << 30, smax = 0;          // rings of the symmetric copy the cap items read
     if (k->plan_ok) {
         // a belt item (ring group, tile) writes rings b_lo + 16 group .. + 15; a cap item its
         // northern ring and the mirror; a per-pair item its ring
+        int gmin = 1 << 30, gmax = -1;
         for (const int4 &it : k->h_items_belt) {
             const int r0 = k->b_lo + it.x * SK_BELT_G, r1 = std::min(r0 + SK_BELT_G, k->b_lo + k->nb);
-            if ((r0 < hi && r1 > lo) || (sym && r0 < nr - lo && r1 > nr - hi)) all.push_back(it);
+            if ((r0 < hi && r1 > lo) || (sym && r0 < nr - lo && r1 > nr - hi)) {
+                all.push_back(it);
+                gmin = std::min(gmin, it.x);
+                gmax = std::max(gmax, it.x);
+            }
         }
+        bg0 = gmax >= 0 ? gmin : 0;
+        bg1 = gmax >= 0 ? gmax + 1 : 0;
         n_belt = all.size();
         for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
             for (int v = 0; v < 2; ++v) {
                 off_cap[c][v] = all.size();
                 for (const int4 &it : k->h_items_cap[c][v])
-                    if (in(it.x) || in(nr - 1 - it.x)) all.push_back(it);
+                    if (in(it.x) || in(nr - 1 - it.x)) {
+                        all.push_back(it);
+                        // the symmetric copy rows its windows read
+                        const int a = k->h_pair_off[it.x], z = k->h_pair_off[it.x + 1] - 1;
+                        smin = std::min(smin, k->h_pairs[a].ri);
+                        smax = std::max(smax, k->h_pairs[z].ri + 1);
+                    }
                 n_cap[c][v] = all.size() - off_cap[c][v];
                 caps = caps || n_cap[c][v] > 0;
             }
@@ -152,7 +167,12 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **ou
         }
     rs.items.gen = n_gen ? rs.d_items + off_gen : nullptr;
     rs.items.n_gen = (int)n_gen;
-    rs.items.sym[0][1] = caps ? k->sym_hi : 0;
+    if (caps) {
+        rs.items.sym[0][0] = std::max(0, smin);
+        rs.items.sym[0][1] = std::min(k->sym_hi, smax);
+    }
+    rs.items.bg0 = bg0;
+    rs.items.bg1 = bg1;
     k->subsets.push_back(rs);                       // entries of other tile widths stay (in use elsewhere)
     *out = &k->subsets.back().items;
     return SK_OK;
@@ -585,7 +605,13 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (path == SK_PATH_TENSOR && k->tc_ok)
                 SK_CU(sk_launch_belt_weights(d, wrows[i], st));                 // rows
             else
-                SK_CU(sk_launch_belt_pairs(d, k->ngroups, (float2 *)wrows[i], st));  // ring pairs
+            {
+                // ring pairs: the groups a ring subset runs, or all
+                const SkItems *sub = jobs[i].sub;
+                const int g0 = sub && sub->bg1 >= 0 ? sub->bg0 : 0;
+                const int g1 = sub && sub->bg1 >= 0 ? sub->bg1 : k->ngroups;
+                SK_CU(sk_launch_belt_pairs(d, g0, g1, (float2 *)wrows[i], st));
+            }
             sk_prof_end(ctx, "belt_weights", ev, st);
         }
     }

@@ -51,6 +51,8 @@ struct SkItems {
     // rings whose symmetric copy (the cap kernel's input) this subset's run builds:
     // [sym[0][0], sym[0][1]) and [sym[1][0], sym[1][1])
     int sym[2][2] = {};
+    // belt ring groups whose weight rows the run needs: [bg0, bg1), or all when bg1 < 0
+    int bg0 = 0, bg1 = -1;
 };
 
 struct sk_geom {
