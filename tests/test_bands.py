@@ -131,3 +131,31 @@ def test_convolve_rings_ranges(sk):
     for lo, hi in ((-1, 4), (0, nr + 1), (9, 8)):
         with pytest.raises(sk.SkError):
             sk.convolve_rings(k, x, lo, hi)
+
+
+def test_convolve_rings_sym_ranges(sk):
+    import torch
+    tc = 360.0 * ARCMIN
+    V = O.tabulate_real_kernel(gaussian_beam(240.0, 128), 32, 128, tc, 2048, 0)
+    g = sk.Geometry(sk._ctx, 64)
+    k = sk.Kernel(g, V, tc, 0)
+    x = torch.from_numpy(white_noise_maps(64, 1, 1401)).cuda()
+    nr = 4 * 64 - 1
+    y_full = sk.convolve(k, x).cpu().numpy()
+    n, st, s, z, sn = g.rings()
+    # the northern half with the equator and its mirror is the whole map
+    assert np.array_equal(sk.convolve_rings_sym(k, x, 0, 2 * 64).cpu().numpy(), y_full)
+    # a range that crosses the equator overlaps its mirror; single rings with their mirrors
+    for lo, hi in ((100, 160), (0, 1), (40, 41), (127, 128)):
+        out = torch.full_like(x, 3.0)
+        sk.convolve_rings_sym(k, x, lo, hi, out=out)
+        o = out.cpu().numpy()[0]
+        for a, b in ((lo, hi), (nr - hi, nr - lo)):
+            p, q = int(st[a]), int(st[b - 1] + n[b - 1])
+            assert np.array_equal(o[p:q], y_full[0, p:q])
+    out = torch.full_like(x, 3.0)
+    sk.convolve_rings_sym(k, x, 7, 7, out=out)
+    assert bool((out == 3.0).all())
+    for lo, hi in ((-1, 4), (0, nr + 1), (9, 8)):
+        with pytest.raises(sk.SkError):
+            sk.convolve_rings_sym(k, x, lo, hi)
