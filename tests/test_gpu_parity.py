@@ -119,6 +119,34 @@ def test_forward_matches_oracle(sk, nside, tc, nt, layout, path):
     assert np.abs(y - yo).max() <= 1e-5 * np.abs(yo).max()
 
 
+# The smallest pixelisations and the widest cut the ABI accepts (theta_cut = pi: every
+# window is a whole ring and every pixel reaches the whole map, its antipode included).
+# The table is any smooth function, tapered to 0 at theta_cut (reading: the cut is
+# closed and the table vanishes there, so FP32/FP64 inclusion at the edge agrees).
+TINY_CASES = [
+    # nside, theta_cut, path
+    (1, math.pi, 0), (1, math.pi, 1), (1, 1.3, 0),
+    (2, math.pi, 0), (2, math.pi, 1), (2, 0.8, 0),
+    (4, math.pi, 0), (4, math.pi, 1), (4, 0.45, 0),
+    (8, math.pi, 0), (8, math.pi, 1),
+]
+
+
+@pytest.mark.parametrize("nside,tc,path", TINY_CASES)
+def test_forward_tiny_and_whole_sphere(sk, nside, tc, path):
+    nt = 512
+    th = O.node_thetas(nt, tc, 0)
+    V = (1.0 + 0.5 * np.cos(3.0 * th) - 0.2 * th) * O.taper(th, tc)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc)
+    x = white_noise_maps(nside, 2, 1100 + nside)
+    y = gpu_conv(sk, k, x, path)
+    for b in range(2):
+        yo = O.conv_brute(nside, V, tc, 0, x[b].astype(np.float64))
+        assert rms_rel(y[b], yo) <= RMS_BOUND, (b, rms_rel(y[b], yo))
+        assert np.abs(y[b] - yo).max() <= 1e-5 * np.abs(yo).max()
+
+
 def test_config_n64_full_map(sk):
     wl = WORKLOADS["n64_plain"].groups[0]
     ks = wl.kernel

@@ -193,6 +193,51 @@ def test_split_reproduces_kernel_below_lcut():
     assert V[-1] == 0.0
 
 
+def test_tabulation_l_range_and_taper_against_scipy():
+    """The tabulated real-space part at nodes that fall on the taper's closed-form
+    points: with 21 uniform nodes, theta_18 = 0.9 theta_cut (taper 1), theta_19 =
+    0.95 theta_cut (taper (1 + cos(pi/2)) / 2 = 1/2) and theta_20 = theta_cut (0).
+    The series sum_{l = l_cut + 1}^{l_max} (2l+1)/(4 pi) b_l P_l(cos theta) is
+    evaluated independently with scipy's Legendre polynomials; starting the sum at
+    l_cut (one term too many) or a different taper moves these values."""
+    from scipy.special import eval_legendre
+    lmax, lcut, tc = 64, 16, 0.5
+    b = gaussian_beam(120.0, lmax)
+    V = O.tabulate_real_kernel(b, lcut, lmax, tc, 21)
+    th = tc * np.arange(21) / 20.0
+    ell = np.arange(lcut + 1, lmax + 1)
+    series = np.array([np.sum((2 * ell + 1) / (4 * math.pi) * b[ell] * eval_legendre(ell, math.cos(t)))
+                       for t in th])
+    w = np.ones(21)
+    w[19], w[20] = 0.5, 0.0
+    assert np.allclose(V, series * w, rtol=1e-12, atol=1e-12 * np.abs(series).max())
+    # the l_cut term alone is far above that tolerance (the pin sees an off-by-one)
+    extra = (2 * lcut + 1) / (4 * math.pi) * b[lcut] * eval_legendre(lcut, np.cos(th[:19]))
+    assert np.abs(extra).max() > 1e-3 * np.abs(series).max()
+    # the taper's shape between its closed-form points: (1 + cos(pi u)) / 2, u = (theta - 0.9 tc) / (0.1 tc)
+    u = np.array([0.0, 0.25, 0.5, 0.75, 1.0])
+    tq = (0.9 + 0.1 * u) * tc
+    assert np.allclose(O.taper(tq, tc), [1.0, (1 + math.sqrt(0.5)) / 2, 0.5, (1 - math.sqrt(0.5)) / 2, 0.0],
+                       rtol=0, atol=1e-15)
+
+
+def test_whole_sphere_high_pass_response_is_the_beam_above_lcut():
+    """With theta_cut = pi and no taper, the real-space part is the whole l > l_cut
+    series, so by orthogonality of the P_l its response is b_l for l_cut < l <= l_max
+    and 0 for l <= l_cut (and above l_max), up to the quadrature error of the
+    piecewise-linear table (16384 nodes: below 1e-4 of the largest b_l here).  An
+    l range that starts at l_cut or stops before l_max fails the first check."""
+    lmax, lcut = 40, 12
+    b = gaussian_beam(300.0, lmax)
+    V = O.tabulate_real_kernel(b, lcut, lmax, math.pi, 16384, taper_start=1.0)
+    R = O.kernel_response(V, math.pi, 0, lmax + 8)
+    tol = 1e-4 * b.max()
+    assert np.abs(R[lcut + 1: lmax + 1] - b[lcut + 1:]).max() <= tol
+    assert np.abs(R[: lcut + 1]).max() <= tol
+    assert np.abs(R[lmax + 1:]).max() <= tol
+    assert b[lcut] > 100 * tol and b[lmax] > 100 * tol       # both ends of the range are visible
+
+
 def test_relative_error_estimate_definition():
     k = np.ones(11)
     assert O.relative_error_estimate(k, k) == 0.0
