@@ -37,10 +37,9 @@ from inputs import ARCMIN, WORKLOADS, Group, make_maps, npix_of, sample_indices 
 METRIC = "pixel-pairs/s and ms/map at Nside 2048, plain vs batched, rms err vs FP64"
 UNIT = "pixel-pairs/s"
 
-# FP32 issue peak of the B300 derived from its unit counts and clock: 148 SMs x
-# 128 FP32 lanes x 2 flop per FFMA x 2.032 GHz (maximum SM clock).
-SMS, LANES, MAX_GHZ = 148, 128, 2.032
-FP32_PEAK_TFLOPS = SMS * LANES * 2 * MAX_GHZ / 1e3
+# FP32 lanes per SM (the unit count behind the derived FP32 peak, SM count x lanes x
+# 2 flop x maximum SM clock, which the bench reports beside the measured one).
+LANES = 128
 # Algorithmic flops per in-cut pixel pair and map: the multiply-accumulate every
 # direct sum must do (the table lerp and chord are amortised by the belt and cap
 # paths, so they are not counted).
@@ -193,6 +192,26 @@ def profiled_traffic(kernel, workload):
     return int(mb.group(1)) if h.hexdigest() == mh.group(1) else None
 
 
+def measure_peaks(ctx, gpu_index, seconds=2.0):
+    """Measured FP32 (fma.rn.f32 and fma.rn.f32x2 chains) and TF32 (tcgen05.mma 128x256x8)
+    rates of this GPU, each with the SM clock sampled while it ran, and the derived FP32
+    figure (SM count from the device x 128 lanes x 2 flop x maximum SM clock)."""
+    import paper_1211_3556_b300 as sk
+    info = ctx.device_info()
+    out = {"sms": info["sms"], "sm_clock_max_mhz": info["sm_clock_khz"] / 1e3,
+           "fp32_derived_tflops": info["sms"] * LANES * 2 * info["sm_clock_khz"] * 1e3 / 1e12}
+    for name, kind in (("ffma", sk.PEAK_FFMA), ("ffma2", sk.PEAK_FFMA2), ("tf32_tcgen05", sk.PEAK_TF32)):
+        ctx.measure_peak(kind, 0.2)                       # warm-up
+        smp = ClockSampler(gpu_index)
+        r = ctx.measure_peak(kind, seconds)
+        clk = smp.stop()
+        out[name] = {"tflops": r, "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+                     "tflops_per_ghz": r / (clk["sm_mhz"] / 1e3) if clk.get("sm_mhz") else None}
+    ctx.status()
+    out["fp32_tflops"] = max(out["ffma"]["tflops"], out["ffma2"]["tflops"])
+    return out
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -315,6 +334,9 @@ def run_ours(args):
     ms = max_over_ranks(ms, world, "cuda")
     value = aggregate_rate(pairs_step, world, ms * 1e-3)
     launches = sum(c for _, c in prof.values())
+    # the roofline's denominators, measured on this GPU after the timed region
+    peaks = measure_peaks(ctx, local)
+    fp32_peak = peaks["fp32_tflops"]
 
     # roofline of the dominant kernel: F_mac flops per pair of the outputs it evaluates
     dom = max(prof, key=lambda n: prof[n][0]) if prof else None
@@ -325,10 +347,12 @@ def run_ours(args):
         launch_ms = prof[dom][0] / prof[dom][1]
         per_launch_pairs = dom_pairs * args.steps / prof[dom][1]
         achieved = FLOP_PER_PAIR * per_launch_pairs / (launch_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                     "traffic": profiled_traffic(dom, args.workload),
-                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                    "peak_source": "measured on this GPU in this run: FP32 FMA chains (sk_measure_peak), "
+                                   "SM clock %s MHz while it ran" % peaks["ffma2"]["sm_mhz"],
+                    "frac_of_derived": achieved / peaks["fp32_derived_tflops"],
                     "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -368,6 +392,14 @@ def run_ours(args):
                              barrier)
             batched[name] = {"value": pb * grp.batch / (msb * 1e-3), "ms_per_map": msb / grp.batch,
                              "ms_per_step": msb}
+        for name in ("fp32", "tensor_3xtf32"):
+            useful = FLOP_PER_PAIR * batched[name]["value"] / 1e12
+            batched[name]["useful_tflops"] = useful
+            batched[name]["frac_fp32_peak"] = useful / fp32_peak
+        # the tensor form's useful flops against the TF32 tensor peak (3xTF32 issues three
+        # MMAs per useful product, so 1/3 is its ceiling)
+        batched["tensor_3xtf32"]["frac_tf32_peak"] = (batched["tensor_3xtf32"]["useful_tflops"]
+                                                      / peaks["tf32_tcgen05"]["tflops"])
         batched["value"] = max(batched["fp32"]["value"], batched["tensor_3xtf32"]["value"])
         del xb, yb
 
@@ -543,8 +575,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "belt_tile": belt_tiles},
             "rms_rel_vs_fp64": rms,
-            "f_eval": value / world * FLOP_PER_PAIR_EVAL / (FP32_PEAK_TFLOPS * 1e12),
-            "f_mac": value / world * FLOP_PER_PAIR / (FP32_PEAK_TFLOPS * 1e12),
+            "f_eval": value / world * FLOP_PER_PAIR_EVAL / (fp32_peak * 1e12),
+            "f_mac": value / world * FLOP_PER_PAIR / (fp32_peak * 1e12),
+            "peaks": peaks,
             "roofline": roofline,
             "kernels": {n: {"ms_total": t, "launches": c, "ms_per_launch": t / c} for n, (t, c) in prof.items()},
             "gpu_launches": launches,

@@ -293,6 +293,28 @@ int sk_profile_enable(sk_ctx *ctx, int on);
 int sk_profile_read(sk_ctx *ctx, int max_kernels, char *names, double *ms, int *launches,
                     int *n_kernels);
 
+/* ---- measured peaks (denominators of the roofline fractions) -------------- */
+
+/* Arithmetic forms whose peak rate sk_measure_peak measures. */
+#define SK_PEAK_FFMA   0   /* FP32 fma.rn.f32: independent FMA chains in registers, 2 flop each      */
+#define SK_PEAK_FFMA2  1   /* FP32 fma.rn.f32x2 (two FMAs per instruction), 2 flop per FMA          */
+#define SK_PEAK_TF32   2   /* tcgen05.mma.kind::tf32, 128 x 256 x 8 per MMA from shared memory into  */
+                           /* tensor memory, one block per SM, 2 flop per multiply-add              */
+
+/* Measure the device's peak rate of one arithmetic form (no counterpart in the
+ * paper; the rate the convolution's useful flops are compared against): runs
+ * launches of a fixed amount of that arithmetic on `stream` for about
+ * `seconds` (0 < seconds <= 60) and writes TFLOP/s to *tflops (CUDA-event time;
+ * synchronises `stream`).  The clock the GPU ran at is the caller's to record.
+ * Errors: SK_EINVAL (NULL, bad kind or seconds), SK_ENOMEM, SK_ECUDA; a
+ * bounded wait of the TF32 form that gives up is reported by sk_get_status. */
+int sk_measure_peak(sk_ctx *ctx, int kind, double seconds, double *tflops, void *stream);
+
+/* Device properties the benchmark's peaks and grids use: out4[0] = SM count,
+ * out4[1] = maximum SM clock in kHz, out4[2] = opt-in shared memory per block in
+ * bytes, out4[3] = L2 bytes.  Errors: SK_EINVAL, SK_ECUDA. */
+int sk_device_info(sk_ctx *ctx, int64_t *out4);
+
 /* ---- tuning -------------------------------------------------------------- */
 
 /* Set the tile parameters of operator k: belt_p = outputs per thread along a

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libskconv.so")
 SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 NODES_UNIFORM, NODES_BIASED = 0, 1
 PATH_AUTO, PATH_GENERAL, PATH_TENSOR = 0, 1, 2
+PEAK_FFMA, PEAK_FFMA2, PEAK_TF32 = 0, 1, 2
 
 _ERRNAMES = {SK_EINVAL: "SK_EINVAL", SK_ENOMEM: "SK_ENOMEM", SK_ECUDA: "SK_ECUDA",
              SK_ETIMEOUT: "SK_ETIMEOUT", SK_EUNSUPPORTED: "SK_EUNSUPPORTED"}
@@ -96,6 +97,8 @@ def _declare(L):
         "sk_fourier_destroy": (I, [P]),
         "sk_fourier_info": (I, [P, ctypes.POINTER(I64)]),
         "sk_fourier_apply": (I, [P, P, P, P, I64, I64, P]),
+        "sk_measure_peak": (I, [P, I, D, ctypes.POINTER(D), P]),
+        "sk_device_info": (I, [P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -164,6 +167,18 @@ class Context:
     def selftest_wait_timeout(self, seconds: float = 0.05, stream=None):
         """Launch the bounded-wait self-test kernel (it records SK_ETIMEOUT)."""
         _check(lib().sk_selftest_wait_timeout(self._h, float(seconds), _stream_ptr(stream)))
+
+    def measure_peak(self, kind: int, seconds: float = 2.0, stream=None) -> float:
+        """TFLOP/s of one arithmetic form (PEAK_FFMA, PEAK_FFMA2, PEAK_TF32) over about `seconds`."""
+        r = ctypes.c_double()
+        _check(lib().sk_measure_peak(self._h, kind, float(seconds), ctypes.byref(r), _stream_ptr(stream)))
+        return r.value
+
+    def device_info(self) -> dict:
+        """SM count, maximum SM clock (kHz), opt-in shared memory per block and L2 bytes."""
+        a = (ctypes.c_int64 * 4)()
+        _check(lib().sk_device_info(self._h, a))
+        return {"sms": int(a[0]), "sm_clock_khz": int(a[1]), "smem_per_block": int(a[2]), "l2_bytes": int(a[3])}
 
     def profile(self, on: bool):
         _check(lib().sk_profile_enable(self._h, 1 if on else 0))
