@@ -169,7 +169,8 @@ def build_operator(sk, ctx, group):
 # DRAM traffic per launch from a committed ncu summary (profiles/<kernel>_<workload>.md),
 # valid only while the kernel's sources hash to the value recorded at capture time.
 PROFILED_SOURCES = {
-    "conv_cap": ["cap.cu", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
+    "conv_cap": ["cap.cu", "cap_common.cuh", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
+    "conv_capw": ["capw.cu", "cap_common.cuh", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
     "conv_belt": ["belt.cu", "skconv_internal.cuh", "skconv_launch.h"],
 }
 
@@ -297,7 +298,9 @@ def run_ours(args):
         y = torch.empty_like(x)
         pairs = k.count_pairs()
         by_path = k.count_pairs_by_path()
-        ops.append(dict(group=group, geom=g, kern=k, x=x, y=y, maps=maps, pairs=pairs, by_path=by_path))
+        by_launch = k.count_pairs_by_launch()
+        ops.append(dict(group=group, geom=g, kern=k, x=x, y=y, maps=maps, pairs=pairs, by_path=by_path,
+                        by_launch=by_launch, cap_weight_bytes=k.cap_weight_bytes()))
     pairs_step = sum(o["pairs"] * o["group"].batch for o in ops)
     maps_step = sum(o["group"].batch for o in ops)
     # plan-time tuning of the belt tile width on the step's own maps (outside the timed region);
@@ -340,10 +343,13 @@ def run_ours(args):
 
     # roofline of the dominant kernel: F_mac flops per pair of the outputs it evaluates
     dom = max(prof, key=lambda n: prof[n][0]) if prof else None
-    path_idx = {"conv_belt": 0, "conv_cap": 1, "conv_general": 2}
+    # the pairs each launch sums (sk_count_pairs_by_launch): belt, caps with narrow windows,
+    # caps with wide windows (polar rings, side stream), per-pair rings
+    launch_idx = {"conv_belt": 0, "conv_cap": 1, "conv_capw": 1, "conv_cap_polar": 2, "conv_capw_polar": 2,
+                  "conv_general": 3}
     roofline = None
-    if dom in path_idx:
-        dom_pairs = sum(o["by_path"][path_idx[dom]] * o["group"].batch for o in ops)
+    if dom in launch_idx:
+        dom_pairs = sum(o["by_launch"][launch_idx[dom]] * o["group"].batch for o in ops)
         launch_ms = prof[dom][0] / prof[dom][1]
         per_launch_pairs = dom_pairs * args.steps / prof[dom][1]
         achieved = FLOP_PER_PAIR * per_launch_pairs / (launch_ms * 1e-3) / 1e12
@@ -582,6 +588,8 @@ def run_ours(args):
             "kernels": {n: {"ms_total": t, "launches": c, "ms_per_launch": t / c} for n, (t, c) in prof.items()},
             "gpu_launches": launches,
             "pairs_by_path": {"belt": o0["by_path"][0], "cap": o0["by_path"][1], "general": o0["by_path"][2]},
+            "pairs_by_launch": dict(zip(("belt", "cap_narrow", "cap_wide", "general"), o0["by_launch"])),
+            "cap_weight_bytes": [o["cap_weight_bytes"] for o in ops],
             "clocks": clocks,
             "e2e": e2e,
             "batched": batched,

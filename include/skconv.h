@@ -130,6 +130,22 @@ int sk_kernel_destroy(sk_kern *k);
  * (host; copied).  Synchronises the device.  Errors: SK_EINVAL, SK_ECUDA. */
 int sk_kernel_update_values(sk_kern *k, const double *h_values);
 
+/* Stored weights of the polar caps.  The operator does not change between calls, so
+ * sk_kernel_create (and sk_kernel_update_values) evaluate the weights
+ * dOmega K_lin(gamma) of the caps' symmetric base pairs once -- the same FP32 values,
+ * bit for bit, that the sums would otherwise compute per call -- and keep them on the
+ * device as a stream that the cap sums read (16 bytes per four base pairs, plus the
+ * union windows' zeros: about 2.3 GB at Nside 2048 and theta_cut 20', 1/16 of the
+ * cap pairs).  Results are bit-identical either way; stored weights make the caps'
+ * sums bound by memory and shared-memory bandwidth instead of the weight evaluation.
+ * At creation the stream is built only if it takes at most half of the free device
+ * memory.  stored = 0 frees it (the caps then evaluate per call); stored = 1 builds it
+ * (SK_ENOMEM if it does not fit).  Synchronises the device; not safe while k is in
+ * use.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_kernel_set_cap_weights(sk_kern *k, int stored);
+/* Device bytes of k's stored cap weights (0: the caps evaluate per call). */
+int sk_kernel_cap_weight_bytes(const sk_kern *k, int64_t *bytes);
+
 /* Number of ordered pixel pairs (o, i) with gamma(o,i) <= theta_cut, counted on
  * the device in FP64 from the per-ring-pair phi windows.  Blocks until done. */
 int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out);
@@ -139,6 +155,13 @@ int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out);
  * evaluation for up to 16 symmetric pairs), out3[2] per-pair general path.  Their sum is
  * sk_count_pairs.  Blocks until done.  Errors: SK_EINVAL, SK_ECUDA. */
 int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3);
+
+/* The same counts split by the launch that sums them: out4[0] belt, out4[1] polar
+ * caps with narrow windows (the main cap launch), out4[2] polar caps with wide or
+ * whole-ring windows (the rings nearest the poles, summed on a side stream),
+ * out4[3] per-pair general path.  Blocks until done.  Errors: SK_EINVAL,
+ * SK_EUNSUPPORTED (no plan), SK_ECUDA. */
+int sk_count_pairs_by_launch(sk_ctx *ctx, const sk_kern *k, int64_t *out4);
 
 /* ---- convolution --------------------------------------------------------- */
 

@@ -63,6 +63,7 @@ def _declare(L):
         "sk_kernel_destroy": (I, [P]),
         "sk_count_pairs": (I, [P, P, ctypes.POINTER(I64)]),
         "sk_count_pairs_by_path": (I, [P, P, ctypes.POINTER(I64)]),
+        "sk_count_pairs_by_launch": (I, [P, P, ctypes.POINTER(I64)]),
         "sk_profile_enable": (I, [P, I]),
         "sk_profile_read": (I, [P, I, P, P, P, ctypes.POINTER(I)]),
         "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
@@ -98,6 +99,8 @@ def _declare(L):
         "sk_fourier_info": (I, [P, ctypes.POINTER(I64)]),
         "sk_fourier_apply": (I, [P, P, P, P, I64, I64, P]),
         "sk_measure_peak": (I, [P, I, D, ctypes.POINTER(D), P]),
+        "sk_kernel_set_cap_weights": (I, [P, I]),
+        "sk_kernel_cap_weight_bytes": (I, [P, ctypes.POINTER(I64)]),
         "sk_device_info": (I, [P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
@@ -293,6 +296,12 @@ class Kernel:
         _check(lib().sk_count_pairs_by_path(self.ctx._h, self._h, c))
         return int(c[0]), int(c[1]), int(c[2])
 
+    def count_pairs_by_launch(self):
+        """In-cut pairs (belt, caps with narrow windows, caps with wide windows, per-pair general)."""
+        a = (ctypes.c_int64 * 4)()
+        _check(lib().sk_count_pairs_by_launch(self.ctx._h, self._h, a))
+        return [int(v) for v in a]
+
     def autotune(self, x, out=None, cache_path=None, stream=None) -> int:
         """Time every belt tile width on maps x and keep the fastest; returns it."""
         import torch
@@ -305,6 +314,16 @@ class Kernel:
                                         ctypes.c_void_p(out.data_ptr()), b, stride, cp, _stream_ptr(stream),
                                         ctypes.byref(p)))
         return p.value
+
+    def set_cap_weights(self, stored: bool):
+        """Keep the caps' weights stored on the device (True) or evaluate them per call (False)."""
+        _check(lib().sk_kernel_set_cap_weights(self._h, 1 if stored else 0))
+
+    def cap_weight_bytes(self) -> int:
+        """Device bytes of the stored cap weights (0 when the caps evaluate per call)."""
+        b = ctypes.c_int64()
+        _check(lib().sk_kernel_cap_weight_bytes(self._h, ctypes.byref(b)))
+        return b.value
 
     def set_tiles(self, belt_p=0, cap_t=0):
         _check(lib().sk_kernel_set_tiles(self._h, belt_p, cap_t))

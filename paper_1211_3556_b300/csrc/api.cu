@@ -340,6 +340,8 @@ static int finish_kernel(sk_kern *k) {
 
     int rc = sk_plan_build(k);
     if (rc) return rc;
+    rc = sk_capw_build(k);
+    if (rc) return rc;
     SK_CU(cudaDeviceSynchronize());
     return SK_OK;
 }
@@ -412,7 +414,36 @@ extern "C" int sk_kernel_update_values(sk_kern *k, const double *h_values) {
     SK_CU(cudaDeviceSynchronize());                 // no launch may still read the old table
     SK_CU(cudaMemcpy(k->d_V, h_values, sizeof(double) * k->nt, cudaMemcpyHostToDevice));
     SK_CU(sk_launch_make_table(k->d_V, k->nt, 4.0 * SK_PI / (double)k->g->npix, k->d_tab, 0));
+    if (k->d_capw) {
+        int rc = sk_capw_build(k);                  // the stored cap weights follow the table
+        if (rc) return rc;
+    }
     SK_CU(cudaDeviceSynchronize());
+    return SK_OK;
+}
+
+extern "C" int sk_kernel_set_cap_weights(sk_kern *k, int stored) {
+    if (!k || (stored != 0 && stored != 1)) return sk_fail(SK_EINVAL, "sk_kernel_set_cap_weights: bad argument");
+    SK_CU(cudaSetDevice(k->ctx->device));
+    SK_CU(cudaDeviceSynchronize());                 // no launch may still read the weights
+    k->capw_wanted = stored != 0;
+    if (!stored) {
+        sk_capw_free(k);
+        return SK_OK;
+    }
+    if (k->d_capw) return SK_OK;
+    int rc = sk_capw_build(k, true);
+    if (rc) return rc;
+    SK_CU(cudaDeviceSynchronize());
+    if (!k->d_capw && k->capw_len > 0)
+        return sk_fail(SK_ENOMEM, "sk_kernel_set_cap_weights: %lld bytes of weights do not fit",
+                       (long long)k->capw_len * 16);
+    return SK_OK;
+}
+
+extern "C" int sk_kernel_cap_weight_bytes(const sk_kern *k, int64_t *bytes) {
+    if (!k || !bytes) return sk_fail(SK_EINVAL, "sk_kernel_cap_weight_bytes: NULL argument");
+    *bytes = k->d_capw ? (int64_t)k->capw_len * 16 : 0;
     return SK_OK;
 }
 
@@ -433,21 +464,35 @@ extern "C" int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out) {
     return SK_OK;
 }
 
-extern "C" int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3) {
-    if (!ctx || !k || !out3) return sk_fail(SK_EINVAL, "sk_count_pairs_by_path: NULL argument");
+extern "C" int sk_count_pairs_by_launch(sk_ctx *ctx, const sk_kern *k, int64_t *out4) {
+    if (!ctx || !k || !out4) return sk_fail(SK_EINVAL, "sk_count_pairs_by_launch: NULL argument");
     if (!k->plan_ok) return sk_fail(SK_EUNSUPPORTED, "operator has no plan");
     SK_CU(cudaSetDevice(ctx->device));
     unsigned long long *d_total = nullptr;
-    SK_CU(cudaMalloc(&d_total, 3 * sizeof(unsigned long long)));
-    cudaError_t e = cudaMemset(d_total, 0, 3 * sizeof(unsigned long long));
+    SK_CU(cudaMalloc(&d_total, 4 * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemset(d_total, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess)
         e = sk_launch_count_pairs(k->g->nr, (int)(4 * k->g->nside), k->g->d_rings, k->d_pair_off, k->d_pairs,
                                   k->d_dphimax, k->d_ring_path, d_total, 0);
-    unsigned long long h[3] = {0, 0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};        // by ring class: belt, narrow caps, general, wide caps
     if (e == cudaSuccess) e = cudaMemcpy(h, d_total, sizeof h, cudaMemcpyDeviceToHost);
     cudaFree(d_total);
-    if (e != cudaSuccess) return sk_fail(SK_ECUDA, "sk_count_pairs_by_path: %s", cudaGetErrorString(e));
-    for (int i = 0; i < 3; ++i) out3[i] = (int64_t)h[i];
+    if (e != cudaSuccess) return sk_fail(SK_ECUDA, "sk_count_pairs_by_launch: %s", cudaGetErrorString(e));
+    out4[0] = (int64_t)h[0];
+    out4[1] = (int64_t)h[1];
+    out4[2] = (int64_t)h[3];
+    out4[3] = (int64_t)h[2];
+    return SK_OK;
+}
+
+extern "C" int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3) {
+    if (!out3) return sk_fail(SK_EINVAL, "sk_count_pairs_by_path: NULL argument");
+    int64_t c[4];
+    int rc = sk_count_pairs_by_launch(ctx, k, c);
+    if (rc) return rc;
+    out3[0] = c[0];
+    out3[1] = c[1] + c[2];
+    out3[2] = c[3];
     return SK_OK;
 }
 

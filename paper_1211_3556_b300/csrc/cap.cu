@@ -47,13 +47,20 @@
 // wavefronts from shared memory but one L1 wavefront per distinct line from
 // global memory.
 #include "skconv.h"
-#include "skconv_internal.cuh"
-#include "skconv_launch.h"
-#include "tc.cuh"
+#include "cap_common.cuh"
 
 namespace {
 
-constexpr int CT = SK_CAP_CT;       // base outputs per work item
+using capc::CT;
+using capc::WAIT_NS;
+using capc::base_count;
+using capc::centre_of;
+using capc::q_of;
+using capc::seg_start;
+using capc::store16;
+using capc::strip_wait;
+using capc::win_shape;
+using capc::Strip;
 constexpr int NTH = CT / 2;         // threads per work item: two adjacent base outputs each
 static_assert(NTH == 128, "an item's strips are issued by its four warps in turn");
 // work items in flight per block (they share one node table): four where their strips fit
@@ -62,7 +69,6 @@ __host__ __device__ constexpr int cap_slots() { return LS <= 640 ? 4 : 2; }
 __host__ __device__ constexpr int cap_max_slots() { return 4; }
 // node tables of up to this many nodes are held as (value, slope) pairs, larger ones as values
 constexpr int PAIR_TABLE_NODES = 8192;
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every wait on a copy
 // strip buffers per work item: two (stage ring p + 1 while ring p is summed) where they fit
 template <int LS>
 __host__ __device__ constexpr int cap_bufs() { return LS <= 320 ? 2 : 1; }
@@ -86,117 +92,32 @@ __device__ __forceinline__ void ring_handover(int slot, int parity, bool stager)
     else asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(NTH) : "memory");
 }
 
-// Bounded wait for a strip: false after WAIT_NS, or at once when another thread of the
-// block has given up (the abort flag).
-__device__ __forceinline__ bool strip_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    if (tc::mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = tc::gtimer();
-    for (;;) {
-        for (int i = 0; i < 64; ++i)
-            if (tc::mbar_try(bar, parity)) return true;
-        if (*abort_flag || tc::gtimer() - t0 > WAIT_NS) return false;
-    }
-}
-
-// Nearest input pixel of output jo: floor(num / (2 n_o)) with num below 2^31
-// (in the caps jo < n_o / 4 <= 2 Nside and n_i <= 4 Nside <= 32768), by the
-// item's multiply-high constants for the divisor 2 n_o: mg = ceil(2^(31+l) / d),
-// l = ceil(log2 d), quotient = umulhi(num, mg) >> (l - 1), exact for every
-// num < 2^31 (Granlund and Montgomery 1994, Thm 4.2).
-__device__ __forceinline__ int centre_of(int jo, int n_o, int s_o, const PairInfo &P, unsigned mg, int sh) {
-    const unsigned num = (unsigned)(2 * jo + s_o) * (unsigned)P.n_i + (unsigned)(1 - P.s_i) * (unsigned)n_o;
-    return (int)(__umulhi(num, mg) >> sh);
-}
-
-// q of window pixel jlo (may be negative) for output jo: both products are below 2^31.
-__device__ __forceinline__ int q_of(int jlo, int jo, int n_o, int s_o, const PairInfo &P) {
-    return (2 * jlo + P.s_i) * n_o - (2 * jo + s_o) * P.n_i;
-}
-
-// Window start relative to the centre, and length, of input ring P.
-__device__ __forceinline__ void win_shape(const PairInfo &P, int &before, int &cnt) {
-    if (P.W < 0) { before = (P.n_i - 1) / 2; cnt = P.n_i; }
-    else         { before = P.W; cnt = 2 * P.W + 1; }
-}
-
-// Base outputs of a quarter ring of Q pixels with shift s: [0, T).
-__device__ __forceinline__ int base_count(int Q, int s) { return s ? (Q + 1) / 2 : Q / 2 + 1; }
-
 // Strip layout of one segment: even positions first, then odd ones.  A lane owns
 // two adjacent outputs, so at one step the lanes of a warp read positions about
 // two apart; with this layout they read consecutive float4 (one parity) instead
 // of every other one.
 template <int LS>
-__device__ __forceinline__ int split_index(int m) { return (m & 1) * (LS / 2) + (m >> 1); }
-
-// Position of pixel a (any integer) of a ring of n pixels in its H row.
-__device__ __forceinline__ int h_index(int a, int n) {
-    a %= n;
-    if (a < 0) a += n;
-    return (a & 1) * (n >> 1) + (a >> 1);
-}
-// The same for -2n < a < 2n (the segment starts of a strip shorter than the ring).
-__device__ __forceinline__ int h_index_near(int a, int n) {
-    a = a < 0 ? a + n : a;
-    a = a < 0 ? a + n : a;
-    a = a >= n ? a - n : a;
-    a = a >= n ? a - n : a;
-    return (a & 1) * (n >> 1) + (a >> 1);
-}
+__device__ __forceinline__ int split_index(int m) { return capc::split_index<2, LS>(m); }
 
 // The strip of input ring P for the item's outputs j0 .. jlast: L window
 // positions from pixel u0 (base frame); the segments start at the natural pixels
 // seg_start(0..3).
-struct Strip {
-    int L, u0;
-};
 __device__ __forceinline__ Strip strip_of(const PairInfo &P, int j0, int jlast, int n_o, int s_o, unsigned mg, int sh) {
     int before, cnt;
     win_shape(P, before, cnt);
     const int c0 = centre_of(j0, n_o, s_o, P, mg, sh), c1 = centre_of(jlast, n_o, s_o, P, mg, sh);
     return Strip{c1 - c0 + cnt, c0 - before};
 }
-// Segment g: window pixels from u0 (g = 0) and from u0 + n/4 (g = 1); their
-// reflections n/4 - s - (u0 + m) (g = 2) and that + n/4 (g = 3) in natural order,
-// i.e. starting at the reflection of the last position.
-__device__ __forceinline__ int seg_start(int g, const Strip &S, const PairInfo &P) {
-    const int Q = P.n_i >> 2;
-    const int rf = Q - P.s_i - S.u0 - (S.L - 1);
-    return g == 0 ? S.u0 : g == 1 ? S.u0 + Q : g == 2 ? rf : rf + Q;
-}
-
-// Bulk copies of ring P's strip (L < n_i: each parity part of a segment is at most
-// half a ring, so it is one or two contiguous pieces of H) into buf, completing
-// on mbarrier bar.  Called by the 32 lanes of one warp (the item's warps take turns).
+// Bulk copies (strips shorter than the ring) and plain copies (strips that wrap it)
+// of ring P's strip in the parity layout.
 template <int LS>
 __device__ __forceinline__ void issue_strip(float4 *buf, uint32_t bar, const float4 *hrow, const Strip &S,
                                             const PairInfo &P, int lane) {
-    if (lane == 0) tc::mbar_expect_tx(bar, (uint32_t)(4 * S.L) * 16u);
-    __syncwarp();
-    if (lane < 8) {
-        const int g = lane >> 1, e = lane & 1;
-        const int n = P.n_i, h = n >> 1;
-        const int cnt = e ? S.L / 2 : (S.L + 1) / 2;
-        if (cnt > 0) {
-            const int i0 = h_index_near(seg_start(g, S, P) + e, n);
-            const float4 *src = hrow + (i0 >= h ? h : 0);
-            const int g0 = i0 >= h ? i0 - h : i0;
-            const uint32_t dst = tc::smem_u32(buf + g * LS + e * (LS / 2));
-            const int len = min(cnt, h - g0);
-            tc::bulk_g2s(dst, src + g0, (uint32_t)len * 16u, bar);
-            if (cnt > len) tc::bulk_g2s(dst + (uint32_t)len * 16u, src, (uint32_t)(cnt - len) * 16u, bar);
-        }
-    }
+    capc::issue_strip<2, LS>(buf, bar, hrow, S, P, lane);
 }
-
-// The same strip copied by the NTH threads of an item with plain loads (strips that
-// wrap the whole ring); the caller synchronises the item's threads afterwards.
 template <int LS>
 __device__ __forceinline__ void copy_strip(float4 *buf, const float4 *hrow, const Strip &S, const PairInfo &P, int t) {
-    for (int g = 0; g < 4; ++g) {
-        const int a0 = seg_start(g, S, P);
-        for (int m = t; m < S.L; m += NTH) buf[g * LS + split_index<LS>(m)] = hrow[h_index(a0 + m, P.n_i)];
-    }
+    capc::copy_strip<2, LS>(buf, hrow, S, P, t, NTH);
 }
 
 // The 16 images of staged position m (forward segments at xf[i], xf[LS + i],
@@ -217,37 +138,22 @@ __device__ __forceinline__ void mac16(float2 *acc, float w, const float4 *xf, co
     acc[7] = __ffma2_rn(ww, make_float2(d.z, d.w), acc[7]);
 }
 
-// Outputs of base pixel j (and of its reflection jr when it has one) from acc.
-__device__ __forceinline__ void store16(float *yn, float *ys, int j, int jr, bool refl, int Q, const float2 *acc) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        if (r == 1 && !refl) break;
-        const int jj = r ? jr : j;
-        const float2 *a = acc + 4 * r;
-        yn[jj] = a[0].x;
-        yn[jj + 2 * Q] = a[0].y;
-        ys[jj] = a[1].x;
-        ys[jj + 2 * Q] = a[1].y;
-        yn[jj + Q] = a[2].x;
-        yn[jj + 3 * Q] = a[2].y;
-        ys[jj + Q] = a[3].x;
-        ys[jj + 3 * Q] = a[3].y;
-    }
-}
-
-// H rows of rings [r0, r0 + gridDim.x) of every map of job J (grid: rings x map slices).
+// H rows of rings [r0, r0 + gridDim.x) of every map of job J (grid: rings x map slices),
+// pixels split by residue modulo SPLIT: row position i holds pixel
+// a = SPLIT (i mod n/SPLIT) + floor(i / (n/SPLIT)).
+template <int SPLIT>
 __global__ void k_cap_sym(const JobDesc J, int r0) {
     const int r = r0 + blockIdx.x;
     const RingDev R = J.rings[r];
-    const int n = R.n, h = n >> 1;
+    const int n = R.n, h = n >> 1, w = n / SPLIT;
     const long long mstart = J.rings[J.nr - 1 - r].start;
     for (int map = blockIdx.y; map < J.batch; map += gridDim.y) {
         const float *xr = J.x + (long long)map * J.stride + R.start;
         const float *xm = J.x + (long long)map * J.stride + mstart;
         float4 *out = J.hx + (long long)map * J.hstride + R.start;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int par = i >= h ? 1 : 0;
-            const int a = 2 * (i - par * h) + par;
+            const int e = i / w;
+            const int a = SPLIT * (i - e * w) + e;
             const int a2 = a + h < n ? a + h : a + h - n;
             out[i] = make_float4(xr[a], xr[a2], xm[a], xm[a2]);
         }
@@ -583,9 +489,12 @@ int occupancy_ls(int mode, int nt) {
 
 }  // namespace
 
-cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, cudaStream_t st) {
+cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, int split, cudaStream_t st) {
     if (r1 <= r0 || j.batch <= 0) return cudaSuccess;
-    k_cap_sym<<<dim3(r1 - r0, j.batch < 65535 ? j.batch : 65535), 256, 0, st>>>(j, r0);
+    const dim3 grid(r1 - r0, j.batch < 65535 ? j.batch : 65535);
+    if (split == 4) k_cap_sym<4><<<grid, 256, 0, st>>>(j, r0);
+    else if (split == 2) k_cap_sym<2><<<grid, 256, 0, st>>>(j, r0);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

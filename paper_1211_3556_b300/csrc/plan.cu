@@ -35,9 +35,13 @@ int centre(int jo, int n_o, int s_o, const PairInfo &P) {
 // Strip length a cap item needs for input ring P, and the largest |q| of its windows.
 // The cap kernel evaluates narrow windows in pixel pairs, one pixel past the
 // window when its count is odd (that pixel is outside the cut).
+// The stored-weight kernel's strip holds the union windows of its last active thread
+// (outputs j0 + 4 k .. + 3): the larger of the two lengths sizes the item's strip class.
 void cap_needs(int j0, int jlast, int n_o, int s_o, const PairInfo &P, int &L, long long &qmax) {
     int cnt = P.W < 0 ? P.n_i : 2 * P.W + 1;
     L = centre(jlast, n_o, s_o, P) - centre(j0, n_o, s_o, P) + cnt + 1;
+    const int jl = j0 + 4 * ((jlast - j0) / 4);
+    L = std::max(L, centre(jl, n_o, s_o, P) - centre(j0, n_o, s_o, P) + sk_capw_steps(cnt, P.n_i, n_o));
     // q at the window centre is below n_o + n_i in magnitude; each step adds 2 n_o
     qmax = (long long)n_o + P.n_i + (long long)(cnt + 1) * 2 * n_o;
 }
@@ -70,7 +74,16 @@ int belt_cost_p(int n4) {
 
 }  // namespace
 
+void sk_capw_free(sk_kern *k) {
+    cudaFree(k->d_capw);
+    k->d_capw = nullptr;
+}
+
 void sk_plan_free(sk_kern *k) {
+    sk_capw_free(k);
+    cudaFree(k->d_capw_ring); k->d_capw_ring = nullptr;
+    k->h_capw_ring.clear();
+    k->capw_len = 0;
     cudaFree(k->d_items_gen); k->d_items_gen = nullptr;
     cudaFree(k->d_ring_path); k->d_ring_path = nullptr;
     cudaFree(k->d_brng); k->d_brng = nullptr;
@@ -319,6 +332,7 @@ int sk_plan_build(sk_kern *k) {
     std::vector<int4> cap_items[SK_CAP_LS_CLASSES][2];
     const int cap_end = k->nb > 0 ? b_lo : eq;
     k->n_cap_rings = 0;
+    std::vector<char> cap_wide(nr, 0);      // cap rings whose windows are too wide for the sine series
     for (int r = 0; r < cap_end; ++r) {
         const int Q = R[r].n / 4;
         const int T = R[r].s ? (Q + 1) / 2 : Q / 2 + 1;     // base outputs (the rest are reflections)
@@ -343,6 +357,7 @@ int sk_plan_build(sk_kern *k) {
             if (need <= SK_CAP_LS[c]) { cls = c; break; }
         if (!ok || cls < 0) continue;
         covered[r] = covered[nr - 1 - r] = 1;
+        if (!series) cap_wide[r] = cap_wide[nr - 1 - r] = 1;
         ++k->n_cap_rings;
         unsigned mg; int sh;
         div_magic(2u * (unsigned)R[r].n, mg, sh);
@@ -367,10 +382,38 @@ int sk_plan_build(sk_kern *k) {
             int rc = upload(cap_items[c][v], &k->d_items_cap[c][v]);
             if (rc) return rc;
         }
+    // layout of the stored cap weights: the items of a ring share its step count (the sum
+    // over its window rings of the union steps), rings one after another
+    {
+        std::vector<char> is_cap(nr, 0);
+        for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+            for (int v = 0; v < 2; ++v)
+                for (const int4 &it : cap_items[c][v]) is_cap[it.x] = 1;
+        k->h_capw_ring.assign(nr, make_longlong2(-1, 0));
+        long long len = 0;
+        for (int r = 0; r < nr; ++r) {
+            if (!is_cap[r]) continue;
+            long long steps = 0;
+            for (int p = off[r]; p < off[r + 1]; ++p) {
+                const PairInfo &P = pairs[p];
+                steps += sk_capw_steps(P.W < 0 ? P.n_i : 2 * P.W + 1, P.n_i, R[r].n);
+            }
+            const int Q = R[r].n / 4;
+            const int T = R[r].s ? (Q + 1) / 2 : Q / 2 + 1;
+            const long long items = (T + SK_CAP_CT - 1) / SK_CAP_CT;
+            k->h_capw_ring[r] = make_longlong2(len, steps);
+            len += items * steps * (SK_CAP_CT / 4);
+        }
+        // the kernel loads one group of four steps ahead of the one it sums
+        k->capw_len = len > 0 ? len + 8 * (SK_CAP_CT / 4) : 0;
+        if (int rc = upload(k->h_capw_ring, &k->d_capw_ring)) return rc;
+    }
 
     // ---- general: the rest
     std::vector<int4> gen;
     std::vector<unsigned char> path(nr, 1);
+    for (int r = 0; r < nr; ++r)
+        if (cap_wide[r]) path[r] = 3;
     for (int r = b_lo; r < b_lo + k->nb; ++r) path[r] = 0;
     for (int r = 0; r < nr; ++r)
         if (!covered[r]) {
@@ -589,6 +632,43 @@ int grid_for(int total, int per_sm, int sms) {
 
 }  // namespace
 
+int sk_capw_build(sk_kern *k, bool force) {
+    if (!k->plan_ok || k->capw_len == 0 || !k->capw_wanted) {
+        sk_capw_free(k);
+        return SK_OK;
+    }
+    const size_t bytes = (size_t)k->capw_len * sizeof(float4);
+    if (!k->d_capw) {
+        // the weights are a cache of the operator: unless asked for, build them only where
+        // they leave half of the free device memory to the maps and workspaces
+        size_t free_b = 0, total_b = 0;
+        SK_CU(cudaMemGetInfo(&free_b, &total_b));
+        if (!force && bytes > free_b / 2) return SK_OK;
+        if (cudaMalloc(&k->d_capw, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            k->d_capw = nullptr;
+            return SK_OK;
+        }
+    }
+    SkJob jb{k, nullptr, nullptr, 1, 0};
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 0; v < 2; ++v) {
+            const int n = k->n_items_cap[c][v];
+            if (n == 0) continue;
+            JobsArg a;
+            memset(&a, 0, sizeof a);
+            a.j[0] = base_desc(jb);
+            a.j[0].items = k->d_items_cap[c][v];
+            a.j[0].n_items = n;
+            a.j[0].capw_ring = k->d_capw_ring;
+            a.n_jobs = 1;
+            a.total = n;
+            const int mode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
+            SK_CU(sk_launch_capw_build(a, mode, k->d_capw, std::min((n + 3) / 4, 8 * k->ctx->num_sms), 0));
+        }
+    return SK_OK;
+}
+
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
     // belt weight rows first (one pre-pass per job, shared by all its maps)
     std::vector<float *> wrows(n, nullptr);
@@ -630,7 +710,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         d.hx = hx[i];
         d.hstride = jobs[i].k->sym_stride;
         cudaEvent_t ev = sk_prof_begin(ctx, s);
-        SK_CU(sk_launch_cap_sym(d, r0, r1, s));
+        SK_CU(sk_launch_cap_sym(d, r0, r1, jobs[i].k->d_capw ? 4 : 2, s));
         sk_prof_end(ctx, "cap_sym", ev, s);
         return SK_OK;
     };
@@ -722,9 +802,49 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         if (rc) return rc;
     }
 
-    // caps: one launch family per (strip class, mode); those on `st` wait for the copies
+    // caps; the launches on `st` wait for the copies.  Jobs with stored weights: one launch
+    // per (strip class, narrow windows or not), any tables together
     SK_CU(cudaEventRecord(ctx->ev_sym, side));
     SK_CU(cudaStreamWaitEvent(st, ctx->ev_sym, 0));
+    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+        for (int v = 1; v >= 0; --v) {
+            Batcher b;
+            auto flush = [&]() -> int {
+                if (b.a.total > 0) {
+                    b.a.status = ctx->d_status;
+                    cudaStream_t cs = v ? st : side;
+                    cudaEvent_t ev = sk_prof_begin(ctx, cs);
+                    const int ipb = sk_capw_items_per_block(SK_CAP_LS[c]);
+                    const int blocks = (b.a.total + ipb - 1) / ipb;
+                    int *q = ctx->d_queue + ctx->next_queue;
+                    ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
+                    SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));
+                    b.a.queue = q;
+                    SK_CU(sk_launch_conv_capw(b.a, SK_CAP_LS[c], std::min(blocks, ctx->num_sms), cs));
+                    sk_prof_end(ctx, v ? "conv_capw" : "conv_capw_polar", ev, cs);
+                }
+                b.reset();
+                return SK_OK;
+            };
+            for (int i = 0; i < n; ++i) {
+                const sk_kern *k = jobs[i].k;
+                const SkItems *sub = jobs[i].sub;
+                const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
+                const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
+                if (!k->plan_ok || !k->d_capw || cn == 0 || jobs[i].batch == 0) continue;
+                JobDesc d = base_desc(jobs[i]);
+                d.cap_ls = SK_CAP_LS[c];
+                d.hx = hx[i];
+                d.hstride = k->sym_stride;
+                d.capw = k->d_capw;
+                d.capw_ring = k->d_capw_ring;
+                b.add(d, citems, cn);
+                if (b.full()) { int rc = flush(); if (rc) return rc; }
+            }
+            int rc = flush();
+            if (rc) return rc;
+        }
+    // jobs whose caps evaluate their weights: one launch family per (strip class, mode)
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int mode = 0; mode < 8; ++mode) {
             const int v = mode & 1;
@@ -755,7 +875,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                 const SkItems *sub = jobs[i].sub;
                 const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
                 const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
-                if (!k->plan_ok || cn == 0 || jobs[i].batch == 0) continue;
+                if (!k->plan_ok || k->d_capw || cn == 0 || jobs[i].batch == 0) continue;
                 const int kmode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
                 if (kmode != mode) continue;
                 // one node table per launch (the blocks load it once)
@@ -852,7 +972,7 @@ int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, 
                 d.hx = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + grad_bins_bytes(k));
                 d.hstride = k->sym_stride;
                 cudaEvent_t ev = sk_prof_begin(ctx, st);
-                SK_CU(sk_launch_cap_sym(d, 0, k->sym_hi, st));
+                SK_CU(sk_launch_cap_sym(d, 0, k->sym_hi, 2, st));
                 sk_prof_end(ctx, "cap_sym", ev, st);
                 for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
                     for (int v = 0; v < 2; ++v) {

@@ -105,7 +105,18 @@ struct sk_kern {
     // the cap kernel reads the symmetric copy of input rings [0, sym_hi): sym_stride float4 per map
     int sym_hi = 0;
     long long sym_stride = 0;
-    unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere), 2 general
+    unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere) with
+                                           // narrow windows, 3 cap with wide or whole-ring windows,
+                                           // 2 general
+    // stored cap weights (capw.cu): per output ring (float4 offset of its first item's
+    // weights, pixel steps per item), the stream length in float4 (with the tail the
+    // kernel's one-group-ahead loads read), and the stream itself -- null when the caps
+    // evaluate their weights per call (sk_kernel_set_cap_weights)
+    std::vector<longlong2> h_capw_ring;
+    longlong2 *d_capw_ring = nullptr;
+    long long capw_len = 0;
+    float4 *d_capw = nullptr;
+    bool capw_wanted = true;
     // batched tensor-core form of the belt: (group, 128-pixel block) items
     bool tc_ok = false;
     TcGeom tcg{};
@@ -148,6 +159,12 @@ int sk_check_maps(const char *who, const sk_kern *k, const void *in, const void 
 
 // plan.cu
 int sk_plan_build(sk_kern *k);
+// Stored cap weights: allocate (if absent) and evaluate the weight stream from the current
+// node table on the legacy stream.  Without `force` the stream is only allocated if it
+// takes at most half of the free device memory; a failed allocation leaves the caps
+// evaluating their weights per call.
+int sk_capw_build(sk_kern *k, bool force = false);
+void sk_capw_free(sk_kern *k);
 void sk_plan_free(sk_kern *k);
 int sk_plan_rebuild_belt_items(sk_kern *k);
 size_t sk_plan_workspace_bytes(const sk_kern *k);

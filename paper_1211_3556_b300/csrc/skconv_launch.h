@@ -56,6 +56,10 @@ struct JobDesc {
     float4 *hx;           // symmetric copy of the input rings the caps read (workspace, per call):
                           // ring r of map b at hx + b hstride + rings[r].start, n_r float4
     long long hstride;    // float4 per map of hx
+    // stored cap weights (capw.cu): the weight stream, and per output ring (x) the float4
+    // offset of the ring's first work item, (y) the pixel steps of one item
+    const float4 *capw;
+    const longlong2 *capw_ring;
 };
 
 struct JobsArg {
@@ -111,13 +115,27 @@ cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t 
 // mode bits: 1 sin series valid on every window of the items, 2 theta_cut <= 0.25
 // (asin series), 4 biased node layout
 cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cudaStream_t st);
-// symmetric copy (hx) of rings [r0, r1) of every map of job j, for the cap kernel
-cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, cudaStream_t st);
+// symmetric copy (hx) of rings [r0, r1) of every map of job j, for the cap kernels, pixels
+// split by residue modulo `split` (2: the evaluating kernel, 4: the stored-weight kernel)
+cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, int split, cudaStream_t st);
 int sk_belt_blocks_per_sm(const JobsArg &a, int P);
 int sk_cap_blocks_per_sm(int ls, int mode, int nt);
 constexpr int SK_CAP_LS_CLASSES = 3;
-constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {320, 640, 1280};  // strip positions per row of the cap path (float4)
-constexpr int SK_CAP_CT = 256;         // base output pixels per cap work item (two per thread)
+constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {288, 640, 1280};  // strip positions per row of the cap path (float4)
+constexpr int SK_CAP_CT = 256;         // base output pixels per cap work item
+// Pixel steps of a stored-weight cap thread on an input ring whose windows hold cnt
+// pixels: the union of its four outputs' windows (they start at most ceil(3 n_i / n_o)
+// pixels apart), rounded up to whole groups of four.
+__host__ __device__ inline int sk_capw_steps(int cnt, int n_i, int n_o) {
+    return (cnt + (3 * n_i + n_o - 1) / n_o + 3) & ~3;
+}
+// stored-weight cap kernel (capw.cu): items of one strip class; the jobs' hx hold the
+// symmetric copies split by residue modulo 4
+cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, int grid, cudaStream_t st);
+int sk_capw_items_per_block(int ls);
+// weight streams of the items of a.j[0] (a kernel's cap items of one list) into w; mode as
+// sk_launch_conv_cap
+cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st);
 int sk_cap_items_per_block(int ls);   // cap work items a block holds at a time (one node table)
 
 // table gradient (grad.cu)

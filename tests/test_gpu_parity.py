@@ -456,3 +456,51 @@ def test_tensor_path_n1024_batch_sampled(sk):
     for b in (0, 31, 32, 63):
         yo = O.conv_window(grp.nside, V, ks.theta_cut, ks.layout, x[b].astype(np.float64), outs)
         assert rms_rel(y[b][outs], yo) <= RMS_BOUND
+
+
+# ------------------------------------------------------------------ stored cap weights
+
+@pytest.mark.parametrize("nside,tc,nt,layout,batch", [
+    (8, math.pi, 512, 0, 1), (16, 1.2, 512, 0, 1), (16, 0.2, 512, 1, 2), (32, 0.08, 1024, 0, 1),
+    (64, 180 * ARCMIN, 4096, 0, 2), (128, 0.03, 2048, 1, 1), (256, 0.02, 16384, 0, 1), (512, 0.0262, 4096, 0, 3)])
+def test_stored_cap_weights_equal_evaluated(sk, nside, tc, nt, layout, batch):
+    # the stored weights are the evaluating kernel's FP32 weights, summed in the same
+    # order per output (extra terms of the wider union windows have weight 0): the two
+    # forms agree bit for bit, and both match the oracle
+    import torch
+    th = O.node_thetas(nt, tc, layout)
+    V = (1.0 + 0.5 * np.cos(3.0 * th) - 0.2 * th) * O.taper(th, tc)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc, layout)
+    assert k.cap_weight_bytes() > 0
+    x = white_noise_maps(nside, batch, 1300 + nside)
+    y_stored = gpu_conv(sk, k, x)
+    k.set_cap_weights(False)
+    assert k.cap_weight_bytes() == 0
+    y_eval = gpu_conv(sk, k, x)
+    assert np.array_equal(y_stored, y_eval)
+    k.set_cap_weights(True)
+    assert k.cap_weight_bytes() > 0
+    assert np.array_equal(gpu_conv(sk, k, x), y_stored)
+    yo = O.conv_window(nside, V, tc, layout, x[0].astype(np.float64))
+    assert rms_rel(y_stored[0], yo) <= RMS_BOUND
+
+
+def test_stored_cap_weights_follow_table_updates(sk):
+    nside, tc, nt = 64, 0.06, 1024
+    V1 = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 192, 48, tc, nt)
+    V2 = oracle_table(nside, 3.0 * tc / 3 / ARCMIN, 192, 48, tc, nt)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V1, tc)
+    x = white_noise_maps(nside, 1, 77)
+    k.update_values(V2)
+    y = gpu_conv(sk, k, x)[0]
+    assert rms_rel(y, O.conv_window(nside, V2, tc, 0, x[0].astype(np.float64))) <= RMS_BOUND
+
+
+def test_pair_counts_by_launch_add_up(sk):
+    for nside, tc in [(16, 1.2), (64, 0.05), (256, 0.02)]:
+        k = sk.Kernel(sk.Geometry(sk._ctx, nside), np.ones(64), tc)
+        by_launch = k.count_pairs_by_launch()
+        by_path = k.count_pairs_by_path()
+        assert sum(by_launch) == k.count_pairs() == sum(by_path)
+        assert by_launch[0] == by_path[0] and by_launch[1] + by_launch[2] == by_path[1]
+        assert by_launch[3] == by_path[2]
