@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint + table gradient) side measurement")
     ap.add_argument("--no-field", action="store_true", help="skip the partial-sky field (polar-cap) side measurement")
     ap.add_argument("--no-bands", action="store_true", help="skip the ring-band (one map over several GPUs) side measurement")
+    ap.add_argument("--bands", action="store_true",
+                    help="strong scaling of one map: under torchrun each rank owns a symmetric ring band of "
+                         "the workload's first map, and a step is the halo exchange plus the band's sums")
     return ap.parse_args()
 
 
@@ -490,10 +493,21 @@ def run_ours(args):
         ms_fwd = time_steps(torch, lambda: sk.convolve(kg, xg, out=yg), ng, 1, barrier)
         ms_adj = time_steps(torch, lambda: sk.convolve_adjoint(kg, gy, out=gx), ng, 1, barrier)
         ms_tab = time_steps(torch, lambda: sk.grad_table(kg, xg, gy, out=gt), ng, 1, barrier)
+        # the allocation-free entry point (per-pixel gradient kernel on every ring)
+        import ctypes
+        L = sk.lib()
+        strm = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+        def noalloc():
+            rc = L.sk_grad_table_noalloc(ctx._h, kg._h, ctypes.c_void_p(xg.data_ptr()), ctypes.c_void_p(gy.data_ptr()),
+                                         grp.batch, xg.stride(0), ctypes.c_void_p(gt.data_ptr()), strm)
+            assert rc == 0, L.sk_last_error()
+        ms_noalloc = time_steps(torch, noalloc, 1, 1, barrier)
         grad = {"workload": "n1024x16_grad", "unit": UNIT, "maps": grp.batch,
                 "forward": {"ms_per_step": ms_fwd, "value": pg / (ms_fwd * 1e-3)},
                 "adjoint": {"ms_per_step": ms_adj, "value": pg / (ms_adj * 1e-3)},
                 "table_gradient": {"ms_per_step": ms_tab, "value": pg / (ms_tab * 1e-3)},
+                "table_gradient_noalloc": {"ms_per_step": ms_noalloc, "value": pg / (ms_noalloc * 1e-3)},
                 "step_ms": ms_fwd + ms_adj + ms_tab}
         del xg, gy, yg, gx
 
@@ -655,10 +669,72 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bands(args):
+    """One map over the ranks in symmetric ring bands: every step each rank receives the
+    halo pixels its band reads from the ranks that own them (point-to-point) and sums its
+    band (strong scaling: the map is the same at every rank count)."""
+    import torch
+    import paper_1211_3556_b300 as sk
+    from paper_1211_3556_b300.bands import exchange_halo, symmetric_bands
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+    wl = WORKLOADS[args.workload]
+    group = wl.groups[0]
+    ks = group.kernel
+    ctx = sk.Context(local)
+    g, k = build_operator(sk, ctx, group)
+    maps = make_maps(group, wl.sources[0] if wl.sources else None)[:1]
+    npix = maps.shape[1]
+    bands = symmetric_bands(group.nside, ks.theta_cut, world)
+    me = bands[rank]
+    own = np.concatenate([maps[:, q0:q1] for q0, q1 in me.out_pix], axis=1) if me.out_pix else maps[:, :0]
+    x_own = torch.from_numpy(np.ascontiguousarray(own)).cuda()
+    x_full = torch.zeros(1, npix, device="cuda")
+    y = torch.empty_like(x_full)
+    lo, hi = me.north
+    stats = {}
+
+    def step():
+        exchange_halo(x_own, me, bands, npix, out=x_full, stats=stats)
+        if hi > lo:
+            sk.convolve_rings_sym(k, x_full, lo, hi, out=y)
+
+    sampler = ClockSampler(local)
+    ms = time_steps(torch, step, args.steps, args.warmup, barrier)
+    clocks = sampler.stop()
+    ctx.status()
+    ms = max_over_ranks(ms, world, "cuda")
+    pairs = k.count_pairs()
+    if rank == 0:
+        line = {"metric": METRIC, "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "ms_per_map": ms, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "nside": [group.nside], "maps_per_step": 1,
+                           "theta_cut_arcmin": ks.theta_cut_arcmin, "decomposition": "symmetric ring bands",
+                           "parallelism": f"ring bands x{world}", "pairs_per_step": pairs},
+                "halo_bytes_recv_rank0": stats.get("recv_bytes", 0), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.bands:
+        run_bands(args)
     else:
         run_ours(args)
 

@@ -146,6 +146,19 @@ int sk_kernel_set_cap_weights(sk_kern *k, int stored);
 /* Device bytes of k's stored cap weights (0: the caps evaluate per call). */
 int sk_kernel_cap_weight_bytes(const sk_kern *k, int64_t *bytes);
 
+/* Replace the node values from device memory, asynchronously on `stream`: d_values
+ * holds n_nodes FP64 values (device; read on `stream`).  One kernel compares them with
+ * the current values and takes them only if any differs; the (value, slope) table and
+ * the stored cap weights are rebuilt on `stream` only then (their kernels return at
+ * once otherwise).  No host synchronisation, so a training step that updates the table
+ * can be captured in a CUDA graph.  Calls on `stream` after this one see the new
+ * values; calls on other streams must be ordered after it by the caller, and calls
+ * still running with k on other streams must finish before it.  The first call
+ * allocates a 4-byte flag (make it before any stream capture).  When the values change
+ * at every call, sk_kernel_set_cap_weights(k, 0) saves the weights' rebuild (one
+ * evaluation of the cap weights per update).  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int sk_kernel_update_values_async(sk_kern *k, const double *d_values, void *stream);
+
 /* Number of ordered pixel pairs (o, i) with gamma(o,i) <= theta_cut, counted on
  * the device in FP64 from the per-ring-pair phi windows.  Blocks until done. */
 int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out);
@@ -190,6 +203,14 @@ int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_
  * Errors: SK_EINVAL (also a ring range outside [0, rings)), SK_ENOMEM, SK_ECUDA. */
 int sk_convolve_rings(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out, int64_t batch,
                       int64_t map_stride, int ring_lo, int ring_hi, void *stream);
+
+/* Planning: the first call for a ring range (and belt tile width) builds the range's
+ * work-item lists on the device, which allocates and synchronises the device -- make
+ * it before any stream capture.  The lists are kept on the operator for up to 256
+ * ranges; the next new range then synchronises the device and drops them all (so
+ * callers that vary the band edges do not grow device memory without bound).  Calls
+ * for ranges of one operator from several host threads must not overlap with that
+ * drop: plan every range once from one thread first. */
 
 /* The same for rings [ring_lo, ring_hi) together with their mirror rings about the
  * equator, [rings - ring_hi, rings - ring_lo): a band made of a northern range and its
@@ -255,7 +276,9 @@ int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, const float *
  * cudaFree would synchronise the device.  Instead of the context workspace it
  * accumulates in a fixed FP64 array of 16384 entries compiled into the
  * library (128 KiB, held on every GPU that loads the library until the
- * process exits).  Arguments as sk_grad_table; n_nodes above 16384 is
+ * process exits).  It always runs the per-pixel gradient kernel on every ring
+ * (the belt and cap gradient kernels need workspace), so at large sizes it is
+ * several times slower than sk_grad_table; results agree within rounding.  Arguments as sk_grad_table; n_nodes above 16384 is
  * rejected with SK_EINVAL.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  Every call clears the array before

@@ -60,6 +60,7 @@ def _declare(L):
         "sk_kernel_create": (I, [P, P, P, I64, D, I, PP]),
         "sk_kernel_from_legendre": (I, [P, P, P, I64, I64, I64, D, I, D, P, PP]),
         "sk_kernel_update_values": (I, [P, P]),
+        "sk_kernel_update_values_async": (I, [P, P, P]),
         "sk_kernel_destroy": (I, [P]),
         "sk_count_pairs": (I, [P, P, ctypes.POINTER(I64)]),
         "sk_count_pairs_by_path": (I, [P, P, ctypes.POINTER(I64)]),
@@ -277,6 +278,19 @@ class Kernel:
                                              float(theta_cut), layout, float(taper_start),
                                              vals.ctypes.data, None))
         return vals
+
+    def update_values_async(self, values, stream=None):
+        """Take node values from a float64 CUDA tensor on `stream` (no host synchronisation;
+        the table and stored cap weights are rebuilt on the device only if the values changed)."""
+        import torch
+        if not (isinstance(values, torch.Tensor) and values.is_cuda and values.dtype == torch.float64):
+            raise TypeError("values must be a float64 CUDA tensor")
+        v = values.contiguous()
+        if v.numel() != self.n_nodes:
+            raise ValueError("node count differs")
+        _check(lib().sk_kernel_update_values_async(self._h, ctypes.c_void_p(v.data_ptr()), _stream_ptr(stream)))
+        self.values = None                  # the host copy no longer describes the device table
+        self._async_values = v              # kept alive until the stream has read it
 
     def update_values(self, values):
         v = np.ascontiguousarray(values, dtype=np.float64)
@@ -772,9 +786,14 @@ def _make_autograd():
     class SphConv(torch.autograd.Function):
         @staticmethod
         def forward(ctx, x, table, kern):
-            v = table.detach().to(torch.float64).cpu().numpy()
-            if kern.values is None or not np.array_equal(v, kern.values):
-                kern.update_values(v)
+            if table.is_cuda:
+                # on the device, on the current stream: no host round trip (the kernels
+                # rebuild the table only if the values changed)
+                kern.update_values_async(table.detach().to(torch.float64))
+            else:
+                v = table.detach().to(torch.float64).numpy()
+                if kern.values is None or not np.array_equal(v, kern.values):
+                    kern.update_values(v)
             ctx.kern = kern
             ctx.table_dtype = table.dtype
             ctx.table_device = table.device

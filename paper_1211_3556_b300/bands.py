@@ -6,9 +6,9 @@ truncated at theta_cut).  So a rank that owns a band of output rings [o_lo, o_hi
 the input rings of colatitude within theta_cut of the band, its halo [i_lo, i_hi); in
 RING order both are contiguous pixel ranges.  Bands hold about equal pixel counts (the
 number of in-cut pairs per pixel is nearly the same everywhere).  The input reaches
-every rank by one all-gather of the ranks' own bands (each keeps its halo); each rank
-then computes its band with convolve_rings and the outputs stay sharded (or are
-gathered the same way).  Host-side logic only: the ring tables follow the HEALPix
+every rank by one halo exchange: each rank sends every other rank only the part of its
+own band inside that rank's halo (point-to-point; exchange_halo); each rank then computes
+its band with convolve_rings and the outputs stay sharded.  Host-side logic only: the ring tables follow the HEALPix
 RING scheme (Gorski et al. 2005, the pixelisation of Sec. 2).
 
 symmetric_bands gives each rank a northern range of rings and its mirror about the
@@ -145,28 +145,90 @@ def symmetric_bands(nside: int, theta_cut: float, world: int, cap_cost: float = 
     return out
 
 
-def gather_halo(x_own, band, bands: list, npix: int, group=None):
-    """The input map of `band`'s rank from every rank's own pixels: x_own [batch, own]
-    holds this rank's band of the input (its out_pix ranges, concatenated in order).  One
-    all-gather (padded to the largest band); returns [batch, npix] with the halo filled
-    and zeros elsewhere.  Bands of ring_bands or of symmetric_bands."""
+def _intersect(a: list, b: list) -> list:
+    """Pieces (lo, hi) of the ranges a that lie in the ranges b, in the order of a."""
+    out = []
+    for a0, a1 in a:
+        for b0, b1 in b:
+            lo, hi = max(a0, b0), min(a1, b1)
+            if hi > lo:
+                out.append((lo, hi))
+    return out
+
+
+def halo_plan(band, bands: list):
+    """What `band`'s rank exchanges: for every other rank q, the pixel pieces of its own
+    bands it sends to q (its out_pix inside q's halo) and the pieces it receives from q
+    (q's out_pix inside its own halo).  Pieces are RING-order pixel ranges; both sides
+    derive them from the same band table, so no sizes are exchanged."""
+    me = band.rank
+    mine = _ranges(band.out_pix) if len(band.out_pix) else []
+    my_halo = _ranges(band.in_pix) if len(band.in_pix) else []
+    send, recv = {}, {}
+    for b in bands:
+        if b.rank == me:
+            continue
+        theirs = _ranges(b.out_pix) if len(b.out_pix) else []
+        their_halo = _ranges(b.in_pix) if len(b.in_pix) else []
+        s = _intersect(mine, their_halo)
+        r = _intersect(theirs, my_halo)
+        if s:
+            send[b.rank] = s
+        if r:
+            recv[b.rank] = r
+    return send, recv
+
+
+def exchange_halo(x_own, band, bands: list, npix: int, group=None, stats: dict = None, out=None):
+    """The input map of `band`'s rank from every rank's own pixels, moving only halos:
+    x_own [batch, own] holds this rank's band of the input (its out_pix ranges,
+    concatenated in order).  Each rank sends every other rank the part of its band that
+    lies in that rank's halo and receives the parts of the others' bands in its own halo
+    (point-to-point, batched: NCCL or gloo).  Returns [batch, npix] with the halo (and
+    the own band) filled and zeros elsewhere -- or fills `out` ([batch, npix], whose
+    other pixels are left as they are: they must be finite) and returns it.  With
+    `stats`, stats["recv_bytes"] and stats["send_bytes"] count the bytes moved.  Bands
+    of ring_bands or symmetric_bands."""
     import torch
     import torch.distributed as dist
     batch = x_own.shape[0]
-    own = [_ranges(b.out_pix) if len(b.out_pix) else [] for b in bands]
-    width = max(sum(q1 - q0 for q0, q1 in r) for r in own)
-    mine = torch.zeros(batch, width, dtype=x_own.dtype, device=x_own.device)
-    mine[:, : x_own.shape[1]] = x_own
-    parts = [torch.empty_like(mine) for _ in bands]
-    dist.all_gather(parts, mine, group=group)
-    full = torch.zeros(batch, npix, dtype=x_own.dtype, device=x_own.device)
-    halo = _ranges(band.in_pix) if len(band.in_pix) else []
-    for ranges, part in zip(own, parts):
+    full = out if out is not None else torch.zeros(batch, npix, dtype=x_own.dtype, device=x_own.device)
+    mine = _ranges(band.out_pix) if len(band.out_pix) else []
+    pos = 0
+    for q0, q1 in mine:
+        full[:, q0:q1] = x_own[:, pos: pos + q1 - q0]
+        pos += q1 - q0
+    send, recv = halo_plan(band, bands)
+
+    def own_offset(p):                        # position of own pixel p in x_own
+        off = 0
+        for q0, q1 in mine:
+            if q0 <= p < q1:
+                return off + p - q0
+            off += q1 - q0
+        raise ValueError(p)
+
+    ops, bufs = [], {}
+    nb = 0
+    for q, pieces in sorted(send.items()):
+        t = torch.cat([x_own[:, own_offset(a): own_offset(a) + (z - a)] for a, z in pieces], dim=1).contiguous()
+        ops.append(dist.P2POp(dist.isend, t, q, group=group))
+        nb += t.numel() * t.element_size()
+    nr = 0
+    for q, pieces in sorted(recv.items()):
+        t = torch.empty(batch, sum(z - a for a, z in pieces), dtype=x_own.dtype, device=x_own.device)
+        bufs[q] = t
+        ops.append(dist.P2POp(dist.irecv, t, q, group=group))
+        nr += t.numel() * t.element_size()
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    for q, pieces in recv.items():
         pos = 0
-        for q0, q1 in ranges:
-            for p0, p1 in halo:
-                a, z = max(q0, p0), min(q1, p1)
-                if z > a:
-                    full[:, a:z] = part[:, pos + a - q0: pos + z - q0]
-            pos += q1 - q0
+        for a, z in pieces:
+            full[:, a:z] = bufs[q][:, pos: pos + z - a]
+            pos += z - a
+    if stats is not None:
+        stats["recv_bytes"] = nr
+        stats["send_bytes"] = nb
     return full

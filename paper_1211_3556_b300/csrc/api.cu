@@ -229,6 +229,7 @@ extern "C" int sk_geometry_rings(const sk_geom *g, int32_t *h_n, int64_t *h_star
 
 static void free_kern(sk_kern *k) {
     if (!k) return;
+    cudaFree(k->d_changed);
     cudaFree(k->d_V); cudaFree(k->d_tab); cudaFree(k->d_pair_off); cudaFree(k->d_pairs);
     cudaFree(k->d_dphimax); cudaFree(k->d_items_all); cudaFree(k->d_ab64);
     sk_plan_free(k);
@@ -419,6 +420,17 @@ extern "C" int sk_kernel_update_values(sk_kern *k, const double *h_values) {
         if (rc) return rc;
     }
     SK_CU(cudaDeviceSynchronize());
+    return SK_OK;
+}
+
+extern "C" int sk_kernel_update_values_async(sk_kern *k, const double *d_values, void *stream) {
+    if (!k || !d_values) return sk_fail(SK_EINVAL, "sk_kernel_update_values_async: NULL argument");
+    SK_CU(cudaSetDevice(k->ctx->device));
+    if (!k->d_changed) SK_CU(cudaMalloc(&k->d_changed, sizeof(int)));
+    cudaStream_t st = (cudaStream_t)stream;
+    SK_CU(sk_launch_update_values(d_values, k->d_V, k->nt, k->d_changed, st));
+    SK_CU(sk_launch_make_table(k->d_V, k->nt, 4.0 * SK_PI / (double)k->g->npix, k->d_tab, st, k->d_changed));
+    if (k->d_capw) return sk_capw_build(k, false, st, k->d_changed);
     return SK_OK;
 }
 

@@ -75,8 +75,10 @@ __device__ __forceinline__ float4 lds4(uint32_t a) {
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
-// Steps of the weight stream the L2 prefetch keeps ahead of the sums (about two rings).
-constexpr int PF_STEPS = 48;
+// Steps of the weight stream the L2 prefetch keeps ahead of the sums (about a ring;
+// measured at Nside 2048: 24 steps 0.754 ms, 48 0.773, 96 0.884, 160 0.927 -- a longer
+// run-ahead displaces the symmetric copy from L2)
+constexpr int PF_STEPS = 24;
 
 // Streamed weights: read once per call, kept out of L1, first out of L2 (policy).
 __device__ __forceinline__ float4 ld_stream(const float4 *p, uint64_t policy) {
@@ -368,8 +370,9 @@ k_conv_capw(const __grid_constant__ JobsArg A) {
 // ---------------------------------------------------------------------------
 template <int MODE, typename TabT>
 __global__ void __launch_bounds__(256)
-k_capw_build(const __grid_constant__ JobsArg A, float4 *__restrict__ W) {
+k_capw_build(const __grid_constant__ JobsArg A, float4 *__restrict__ W, const int *gate) {
     constexpr bool SERIES = (MODE & 1) != 0, SMALLA = (MODE & 2) != 0, BIASED = (MODE & 4) != 0;
+    if (gate && !*gate) return;                  // table unchanged: the weights stand
     extern __shared__ __align__(16) unsigned char smraw[];
     TabT *stab = reinterpret_cast<TabT *>(smraw);
     const JobDesc &J = A.j[0];
@@ -450,20 +453,20 @@ cudaError_t launch_conv(const JobsArg &a, int grid, cudaStream_t st) {
 }
 
 template <int MODE>
-cudaError_t launch_build_m(const JobsArg &a, float4 *w, int grid, cudaStream_t st) {
+cudaError_t launch_build_m(const JobsArg &a, float4 *w, int grid, cudaStream_t st, const int *gate) {
     const int nt = a.j[0].kp.nt;
     if (nt <= PAIR_TABLE_NODES) {
         const size_t smem = (size_t)(nt + 2) * sizeof(float2);
         cudaError_t e = cudaFuncSetAttribute(k_capw_build<MODE, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        k_capw_build<MODE, float2><<<grid, 256, smem, st>>>(a, w);
+        k_capw_build<MODE, float2><<<grid, 256, smem, st>>>(a, w, gate);
     } else {
         const size_t smem = (size_t)(nt + 2) * sizeof(float);
         cudaError_t e = cudaFuncSetAttribute(k_capw_build<MODE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        k_capw_build<MODE, float><<<grid, 256, smem, st>>>(a, w);
+        k_capw_build<MODE, float><<<grid, 256, smem, st>>>(a, w, gate);
     }
     return cudaGetLastError();
 }
@@ -482,17 +485,18 @@ cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, int grid, cudaStream_t
 
 int sk_capw_items_per_block(int ls) { return ls <= 288 ? 6 : 2; }
 
-cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st) {
+cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st,
+                                 const int *gate) {
     if (a.j[0].n_items <= 0) return cudaSuccess;
     switch (mode) {
-        case 0: return launch_build_m<0>(a, w, grid, st);
-        case 1: return launch_build_m<1>(a, w, grid, st);
-        case 2: return launch_build_m<2>(a, w, grid, st);
-        case 3: return launch_build_m<3>(a, w, grid, st);
-        case 4: return launch_build_m<4>(a, w, grid, st);
-        case 5: return launch_build_m<5>(a, w, grid, st);
-        case 6: return launch_build_m<6>(a, w, grid, st);
-        case 7: return launch_build_m<7>(a, w, grid, st);
+        case 0: return launch_build_m<0>(a, w, grid, st, gate);
+        case 1: return launch_build_m<1>(a, w, grid, st, gate);
+        case 2: return launch_build_m<2>(a, w, grid, st, gate);
+        case 3: return launch_build_m<3>(a, w, grid, st, gate);
+        case 4: return launch_build_m<4>(a, w, grid, st, gate);
+        case 5: return launch_build_m<5>(a, w, grid, st, gate);
+        case 6: return launch_build_m<6>(a, w, grid, st, gate);
+        case 7: return launch_build_m<7>(a, w, grid, st, gate);
         default: return cudaErrorInvalidValue;
     }
 }

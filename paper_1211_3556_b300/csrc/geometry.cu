@@ -126,7 +126,8 @@ __global__ void k_tabulate(const double *kl, int lmin, int lmax, int nt, double 
     V[k] = acc * w;
 }
 
-__global__ void k_make_table(const double *V, int nt, double dOmega, float2 *tab) {
+__global__ void k_make_table(const double *V, int nt, double dOmega, float2 *tab, const int *gate) {
+    if (gate && !*gate) return;                  // values unchanged: the table stands
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
     double v = V[k];
@@ -195,8 +196,25 @@ cudaError_t sk_launch_tabulate(const double *kl, int lmin, int lmax, int nt, dou
     return cudaGetLastError();
 }
 
-cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 *tab, cudaStream_t st) {
-    k_make_table<<<(nt + 255) / 256, 256, 0, st>>>(V, nt, dOmega, tab);
+cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 *tab, cudaStream_t st,
+                                 const int *gate) {
+    k_make_table<<<(nt + 255) / 256, 256, 0, st>>>(V, nt, dOmega, tab, gate);
+    return cudaGetLastError();
+}
+
+// New node values from device memory (nt <= 16384, one block): *changed = whether any
+// differs from V, and V takes them if so.
+__global__ void __launch_bounds__(1024) k_update_values(const double *nv, double *V, int nt, int *changed) {
+    int diff = 0;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) diff |= nv[k] != V[k];
+    diff = __syncthreads_or(diff);
+    if (diff)
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) V[k] = nv[k];
+    if (threadIdx.x == 0) *changed = diff ? 1 : 0;
+}
+
+cudaError_t sk_launch_update_values(const double *nv, double *V, int nt, int *changed, cudaStream_t st) {
+    k_update_values<<<1, 1024, 0, st>>>(nv, V, nt, changed);
     return cudaGetLastError();
 }
 

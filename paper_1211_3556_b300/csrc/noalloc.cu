@@ -4,8 +4,12 @@
 // the library grows with cudaMalloc on demand.  Some callers cannot let a
 // library allocate: hosts whose device memory is owned by their own allocator
 // or budget, and latency-critical loops where a cudaMalloc or cudaFree would
-// synchronise the device.  sk_grad_table_noalloc runs the same kernels with
-// the FP64 accumulator in a fixed array compiled into this library instead.
+// synchronise the device.  sk_grad_table_noalloc computes the same gradient
+// with the FP64 accumulator in a fixed array compiled into this library instead.
+// It uses only the per-pixel gradient kernel (one FP64 node coordinate per pair,
+// on every output ring): the belt's ring-pair correlations and the caps'
+// symmetric base pairs need workspace (their FP32 sums and the symmetric copy of
+// the maps), so it is several times slower than sk_grad_table at large sizes.
 //
 // The array lives for as long as the library is loaded, on every GPU that
 // loads it (SK_NOALLOC_MAX_NODES doubles = 128 KiB each).  All calls on a

@@ -114,6 +114,13 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **ou
     std::lock_guard<std::mutex> lock(k->subsets_mu);
     for (auto &r : k->subsets)
         if (r.lo == lo && r.hi == hi && r.sym == sym && r.P == k->belt_P) { *out = &r.items; return SK_OK; }
+    // a bounded cache: past SK_MAX_RING_SUBSETS ranges the lists are dropped (after every
+    // launch that may read them has finished) and rebuilt as ranges are asked for again
+    if (k->subsets.size() >= (size_t)SK_MAX_RING_SUBSETS) {
+        SK_CU(cudaDeviceSynchronize());
+        for (auto &r : k->subsets) cudaFree(r.d_items);
+        k->subsets.clear();
+    }
     const sk_geom *g = k->g;
     const int nr = g->nr;
     auto in = [&](int r) { return (r >= lo && r < hi) || (sym && nr - 1 - r >= lo && nr - 1 - r < hi); };
@@ -121,22 +128,34 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **ou
     size_t off_belt = 0, n_belt = 0, off_cap[SK_CAP_LS_CLASSES][2] = {}, n_cap[SK_CAP_LS_CLASSES][2] = {};
     size_t off_gen = 0, n_gen = 0;
     bool caps = false;
-    int bg0 = 0, bg1 = -1;                 // belt groups (all without a plan)
+    int bg[2][2] = {{0, -1}, {0, 0}};     // belt groups (all without a plan)
     int smin = 1 << 30, smax = 0;          // rings of the symmetric copy the cap items read
     if (k->plan_ok) {
         // a belt item (ring group, tile) writes rings b_lo + 16 group .. + 15; a cap item its
-        // northern ring and the mirror; a per-pair item its ring
-        int gmin = 1 << 30, gmax = -1;
+        // northern ring and the mirror; a per-pair item its ring.  The groups of the range
+        // and those of its mirror are kept as two group ranges (the belt weight rows of the
+        // groups between them are not needed)
+        int gmin[2] = {1 << 30, 1 << 30}, gmax[2] = {-1, -1};
         for (const int4 &it : k->h_items_belt) {
             const int r0 = k->b_lo + it.x * SK_BELT_G, r1 = std::min(r0 + SK_BELT_G, k->b_lo + k->nb);
-            if ((r0 < hi && r1 > lo) || (sym && r0 < nr - lo && r1 > nr - hi)) {
-                all.push_back(it);
-                gmin = std::min(gmin, it.x);
-                gmax = std::max(gmax, it.x);
-            }
+            const bool north = r0 < hi && r1 > lo, mirror = sym && r0 < nr - lo && r1 > nr - hi;
+            if (north || mirror) all.push_back(it);
+            for (int q = 0; q < 2; ++q)
+                if (q == 0 ? north : mirror) {
+                    gmin[q] = std::min(gmin[q], it.x);
+                    gmax[q] = std::max(gmax[q], it.x);
+                }
         }
-        bg0 = gmax >= 0 ? gmin : 0;
-        bg1 = gmax >= 0 ? gmax + 1 : 0;
+        for (int q = 0; q < 2; ++q) {
+            bg[q][0] = gmax[q] >= 0 ? gmin[q] : 0;
+            bg[q][1] = gmax[q] >= 0 ? gmax[q] + 1 : 0;
+        }
+        // overlapping (or adjacent) ranges: one range
+        if (bg[1][1] > bg[1][0] && bg[0][1] > bg[0][0] && bg[1][0] <= bg[0][1] && bg[0][0] <= bg[1][1]) {
+            bg[0][0] = std::min(bg[0][0], bg[1][0]);
+            bg[0][1] = std::max(bg[0][1], bg[1][1]);
+            bg[1][0] = bg[1][1] = 0;
+        }
         n_belt = all.size();
         for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
             for (int v = 0; v < 2; ++v) {
@@ -184,8 +203,10 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **ou
         rs.items.sym[0][0] = std::max(0, smin);
         rs.items.sym[0][1] = std::min(k->sym_hi, smax);
     }
-    rs.items.bg0 = bg0;
-    rs.items.bg1 = bg1;
+    for (int q = 0; q < 2; ++q) {
+        rs.items.bg[q][0] = bg[q][0];
+        rs.items.bg[q][1] = bg[q][1];
+    }
     k->subsets.push_back(rs);                       // entries of other tile widths stay (in use elsewhere)
     *out = &k->subsets.back().items;
     return SK_OK;
@@ -632,7 +653,7 @@ int grid_for(int total, int per_sm, int sms) {
 
 }  // namespace
 
-int sk_capw_build(sk_kern *k, bool force) {
+int sk_capw_build(sk_kern *k, bool force, cudaStream_t st, const int *gate) {
     if (!k->plan_ok || k->capw_len == 0 || !k->capw_wanted) {
         sk_capw_free(k);
         return SK_OK;
@@ -664,7 +685,7 @@ int sk_capw_build(sk_kern *k, bool force) {
             a.n_jobs = 1;
             a.total = n;
             const int mode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
-            SK_CU(sk_launch_capw_build(a, mode, k->d_capw, std::min((n + 3) / 4, 8 * k->ctx->num_sms), 0));
+            SK_CU(sk_launch_capw_build(a, mode, k->d_capw, std::min((n + 3) / 4, 8 * k->ctx->num_sms), st, gate));
         }
     return SK_OK;
 }
@@ -686,11 +707,15 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                 SK_CU(sk_launch_belt_weights(d, wrows[i], st));                 // rows
             else
             {
-                // ring pairs: the groups a ring subset runs, or all
+                // ring pairs: the groups a ring subset runs (one or two ranges), or all
                 const SkItems *sub = jobs[i].sub;
-                const int g0 = sub && sub->bg1 >= 0 ? sub->bg0 : 0;
-                const int g1 = sub && sub->bg1 >= 0 ? sub->bg1 : k->ngroups;
-                SK_CU(sk_launch_belt_pairs(d, g0, g1, (float2 *)wrows[i], st));
+                if (!sub || sub->bg[0][1] < 0) {
+                    SK_CU(sk_launch_belt_pairs(d, 0, k->ngroups, (float2 *)wrows[i], st));
+                } else {
+                    for (int q = 0; q < 2; ++q)
+                        if (sub->bg[q][1] > sub->bg[q][0])
+                            SK_CU(sk_launch_belt_pairs(d, sub->bg[q][0], sub->bg[q][1], (float2 *)wrows[i], st));
+                }
             }
             sk_prof_end(ctx, "belt_weights", ev, st);
         }

@@ -13,6 +13,7 @@
 #include "skconv_launch.h"
 
 constexpr int SK_HOST_BANDS = 16;  // ring bands of the host-buffer pipeline (sk_convolve_host)
+constexpr int SK_MAX_RING_SUBSETS = 256;   // ring ranges whose work items an operator keeps
 
 struct sk_ctx {
     int device = 0;
@@ -51,8 +52,9 @@ struct SkItems {
     // rings whose symmetric copy (the cap kernel's input) this subset's run builds:
     // [sym[0][0], sym[0][1]) and [sym[1][0], sym[1][1])
     int sym[2][2] = {};
-    // belt ring groups whose weight rows the run needs: [bg0, bg1), or all when bg1 < 0
-    int bg0 = 0, bg1 = -1;
+    // belt ring groups whose weight rows the run needs: [bg[0][0], bg[0][1]) and
+    // [bg[1][0], bg[1][1]) (a range and its mirror), or all when bg[0][1] < 0
+    int bg[2][2] = {{0, -1}, {0, 0}};
 };
 
 struct sk_geom {
@@ -117,6 +119,7 @@ struct sk_kern {
     long long capw_len = 0;
     float4 *d_capw = nullptr;
     bool capw_wanted = true;
+    int *d_changed = nullptr;              // sk_kernel_update_values_async: whether the values changed
     // batched tensor-core form of the belt: (group, 128-pixel block) items
     bool tc_ok = false;
     TcGeom tcg{};
@@ -163,7 +166,8 @@ int sk_plan_build(sk_kern *k);
 // node table on the legacy stream.  Without `force` the stream is only allocated if it
 // takes at most half of the free device memory; a failed allocation leaves the caps
 // evaluating their weights per call.
-int sk_capw_build(sk_kern *k, bool force = false);
+// With `gate`, the rebuild kernels run on `st` and return at once unless *gate is set.
+int sk_capw_build(sk_kern *k, bool force = false, cudaStream_t st = 0, const int *gate = nullptr);
 void sk_capw_free(sk_kern *k);
 void sk_plan_free(sk_kern *k);
 int sk_plan_rebuild_belt_items(sk_kern *k);

@@ -100,7 +100,11 @@ cudaError_t sk_launch_pair_info(int nr, const RingDev *rings, const double *z, c
                                 PairInfo *pairs, double *dphimax, double2 *ab64, cudaStream_t st);
 cudaError_t sk_launch_tabulate(const double *kl, int lmin, int lmax, int nt, double tc, int layout,
                                double taper_start, double *V, cudaStream_t st);
-cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 *tab, cudaStream_t st);
+// (value, slope) dOmega table from FP64 nodes; with `gate`, only if *gate is non-zero
+cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 *tab, cudaStream_t st,
+                                 const int *gate = nullptr);
+// V = nv where they differ (one block, nt <= 16384); *changed = 1 if they did, else 0
+cudaError_t sk_launch_update_values(const double *nv, double *V, int nt, int *changed, cudaStream_t st);
 cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const int *off,
                                   const PairInfo *pairs, const double *dphimax, const unsigned char *cls,
                                   unsigned long long *total, cudaStream_t st);
@@ -135,7 +139,8 @@ cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, int grid, cudaStream_t
 int sk_capw_items_per_block(int ls);
 // weight streams of the items of a.j[0] (a kernel's cap items of one list) into w; mode as
 // sk_launch_conv_cap
-cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st);
+cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st,
+                                 const int *gate = nullptr);
 int sk_cap_items_per_block(int ls);   // cap work items a block holds at a time (one node table)
 
 // table gradient (grad.cu)

@@ -58,7 +58,7 @@ def _band_rank_main(rank, world, port, out):
     import torch.distributed as dist
     import oracle as O
     from inputs import gaussian_beam, white_noise_maps
-    from paper_1211_3556_b300.bands import gather_halo, ring_bands
+    from paper_1211_3556_b300.bands import exchange_halo, ring_bands
     dist.init_process_group("gloo", rank=rank, world_size=world)
     nside, tc = 8, math.radians(30.0)
     V = O.tabulate_real_kernel(gaussian_beam(600.0, 16), 4, 16, tc, 512, 0)
@@ -69,7 +69,10 @@ def _band_rank_main(rank, world, port, out):
     p0, p1 = me.out_pix
     # each rank starts from its own band of the input only
     x_own = torch.from_numpy(x[None, p0:p1].copy())
-    x_halo = gather_halo(x_own, me, bands, npix)[0].numpy()
+    stats = {}
+    x_halo = exchange_halo(x_own, me, bands, npix, stats=stats)[0].numpy()
+    # only the halo moves: the pixels of the halo that other ranks own, once each
+    out[f"bytes_ok_{rank}"] = stats["recv_bytes"] == ((me.in_pix[1] - me.in_pix[0]) - (p1 - p0)) * 8
     # the oracle stands in for the device sums: this rank's outputs from its halo
     y_mine = O.conv_window(nside, V, tc, 0, x_halo, outs=np.arange(p0, p1, dtype=np.int64))
     outs = [None] * world
@@ -86,7 +89,7 @@ def _band_rank_main(rank, world, port, out):
 
 
 def test_ring_bands_halo_exchange_and_stitching_world_size_2():
-    # one map split into two ring bands; the halo comes by an all-gather over gloo, each
+    # one map split into two ring bands; the halo comes by a halo-only exchange over gloo, each
     # rank sums its band (the FP64 oracle in place of the device), and the stitched map
     # equals the full sum exactly (the same terms in the same order)
     world = 2
@@ -95,6 +98,7 @@ def test_ring_bands_halo_exchange_and_stitching_world_size_2():
     out = mgr.dict()
     mp.spawn(_band_rank_main, args=(world, port, out), nprocs=world, join=True)
     assert out["halo_zero_outside"]
+    assert all(out[f"bytes_ok_{r}"] for r in range(world))
     assert np.array_equal(np.array(out["stitched"]), np.array(out["full"]))
 
 
@@ -135,7 +139,7 @@ def _sym_band_rank_main(rank, world, port, out):
     import torch.distributed as dist
     import oracle as O
     from inputs import gaussian_beam, white_noise_maps
-    from paper_1211_3556_b300.bands import gather_halo, symmetric_bands
+    from paper_1211_3556_b300.bands import exchange_halo, symmetric_bands
     dist.init_process_group("gloo", rank=rank, world_size=world)
     nside, tc = 16, math.radians(12.0)
     V = O.tabulate_real_kernel(gaussian_beam(240.0, 32), 8, 32, tc, 512, 0)
@@ -146,7 +150,10 @@ def _sym_band_rank_main(rank, world, port, out):
     # each rank starts from its own rings only (north range and mirror, concatenated)
     outs_mine = np.concatenate([np.arange(q0, q1, dtype=np.int64) for q0, q1 in me.out_pix])
     x_own = torch.from_numpy(x[None, outs_mine].copy())
-    x_halo = gather_halo(x_own, me, bands, npix)[0].numpy()
+    stats = {}
+    x_halo = exchange_halo(x_own, me, bands, npix, stats=stats)[0].numpy()
+    halo_px = sum(p1 - p0 for p0, p1 in me.in_pix)
+    out[f"bytes_ok_{rank}"] = stats["recv_bytes"] == (halo_px - len(outs_mine)) * 8
     inside = np.zeros(npix, bool)
     for p0, p1 in me.in_pix:
         inside[p0:p1] = True
@@ -167,7 +174,7 @@ def _sym_band_rank_main(rank, world, port, out):
 
 def test_symmetric_bands_halo_exchange_and_stitching_world_size_3():
     # bands of a northern range and its mirror: halos (two ranges, or one where they meet)
-    # by one all-gather, each rank's sums from its halo (the oracle in place of the device),
+    # by a halo-only exchange, each rank's sums from its halo (the oracle in place of the device),
     # the stitched map equal to the full sum exactly
     world = 3
     port = _free_port()
@@ -175,6 +182,7 @@ def test_symmetric_bands_halo_exchange_and_stitching_world_size_3():
     out = mgr.dict()
     mp.spawn(_sym_band_rank_main, args=(world, port, out), nprocs=world, join=True)
     assert all(out[f"halo_ok_{r}"] for r in range(world))
+    assert all(out[f"bytes_ok_{r}"] for r in range(world))
     assert np.array_equal(np.array(out["stitched"]), np.array(out["full"]))
 
 
