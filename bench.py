@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint + table gradient) side measurement")
     ap.add_argument("--no-field", action="store_true", help="skip the partial-sky field (polar-cap) side measurement")
     ap.add_argument("--no-bands", action="store_true", help="skip the ring-band (one map over several GPUs) side measurement")
+    ap.add_argument("--errors", action="store_true",
+                    help="the split's error study (Sec. 3): estimated and actual errors of the split "
+                         "convolution of a white-noise map for several l_cut at a fixed theta_cut")
     ap.add_argument("--bands", action="store_true",
                     help="strong scaling of one map: under torchrun each rank owns a symmetric ring band of "
                          "the workload's first map, and a step is the halo exchange plus the band's sums")
@@ -729,10 +732,101 @@ def run_bands(args):
         dist.destroy_process_group()
 
 
+def run_errors(args):
+    """Two settings of the study: the paper's (l_max = 2 Nside) and one with the band
+    limit four times below the pixel scale (l_max = Nside / 2, the beam scaled with it)."""
+    out = [split_error_study(1024, 2047, 14.0, 240.0, (256, 512, 768, 1024, 1280)),
+           split_error_study(1024, 511, 56.0, 240.0, (64, 128, 192, 256, 320))]
+    print(json.dumps({"study": "split errors (Sec. 3)", "settings": out}), flush=True)
+
+
+def split_error_study(nside, lmax, fwhm, tc_arcmin, lcuts, alpha=5.0):
+    """The split's errors as the paper studies them (Sec. 3, Eq. 2 and the relative-error
+    curve sigma_l = log10|1 - K~_l / K_l|), e.g. at Nside 1024 with l_max = 2047 (the paper's
+    7' beam at l_max 4096 scaled to half the resolution: FWHM 14'), C_l = 1, theta_cut 240'.
+    For each l_cut: the real-space part fitted by least squares, K^_l = K_l - R_l below l_cut;
+    a white-noise map band-limited to l_max convolved with the full l-space kernel (the
+    library's ring transform up to l_max) and with the split (harmonic part + real-space
+    sums); the map rms error,
+    the power spectra of both maps and their relative error per l, the spectrum rms error,
+    and Eq. 2's estimate with alpha = 5."""
+    import torch
+    import paper_1211_3556_b300 as sk
+    from inputs import gaussian_beam, white_noise_maps
+    torch.cuda.set_device(0)
+    ctx = sk.Context(0)
+    g = sk.Geometry(ctx, nside)
+    kl = gaussian_beam(fwhm, lmax)
+    ell = np.arange(lmax + 1)
+    tc = tc_arcmin * ARCMIN
+    # the input: white noise band-limited to l_max (C_l flat up to l_max, nothing above: the
+    # paper gives the input spectrum and the kernel the same band limit), made by the
+    # library's transform with K_l = 1
+    h_one = sk.Harmonic(ctx, g, np.ones(lmax + 1), lmax)
+    x = h_one.apply(torch.from_numpy(white_noise_maps(nside, 1, 901)).cuda())
+    del h_one
+    t0 = time.perf_counter()
+    h_full = sk.Harmonic(ctx, g, kl, lmax)
+    y_full = h_full.apply(x)
+    c_full = h_full.spectrum(y_full)[0].cpu().numpy()
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    edges = np.unique(np.round(np.geomspace(2, lmax + 1, 25)).astype(int))
+
+    def binned(v):
+        out = []
+        for a, b in zip(edges[:-1], edges[1:]):
+            seg = v[a:b]
+            seg = seg[np.isfinite(seg)]
+            out.append(float(np.median(seg)) if len(seg) else None)
+        return out
+
+    rows = []
+    for lcut in lcuts:
+        V, sig_fit = sk.fit_real_kernel(ctx, kl, lcut, tc, n_basis=513, nt_out=8193, lfit=lmax)
+        k = sk.Kernel(g, V, tc)
+        R = sk.kernel_response(k, lmax)
+        khat = kl[: lcut + 1] - R[: lcut + 1]
+        k_tilde = R.copy()
+        k_tilde[: lcut + 1] += khat                       # K~_l = K^_l + R_l
+        with np.errstate(divide="ignore"):
+            sigma_l = np.log10(np.abs(1.0 - k_tilde / kl))
+        srms2 = np.sum((2 * ell + 1) * (k_tilde - kl) ** 2) / (4 * math.pi)
+        est = alpha * math.sqrt(srms2 / (np.sum((2 * ell + 1) * kl ** 2) / (4 * math.pi)))
+        h = sk.Harmonic(ctx, g, khat, lcut)
+        y = sk.convolve(k, x)
+        # the real-space part's pixel sum against the harmonic convolution with its response
+        # R_l on the same band-limited map: the quadrature error of the pixel sum
+        h_r = sk.Harmonic(ctx, g, R, lmax)
+        y_rc = h_r.apply(x)
+        quad = float(torch.linalg.norm((y - y_rc).double()) / torch.linalg.norm(y_full.double()))
+        del h_r, y_rc
+        h.apply(x, out=y, accumulate=True)                # the split: real-space + harmonic parts
+        c_split = h_full.spectrum(y)[0].cpu().numpy()
+        map_rms = float(torch.linalg.norm((y - y_full).double()) / torch.linalg.norm(y_full.double()))
+        spec_err = c_split / c_full - 1.0
+        spec_rms = math.sqrt(float(np.sum((2 * ell + 1) * (c_split - c_full) ** 2) /
+                                   np.sum((2 * ell + 1) * c_full ** 2)))
+        rows.append({"l_cut": lcut, "sigma_rms_fit": sig_fit, "estimate_eq2_alpha5": est,
+                     "map_rms_error": map_rms, "spectrum_rms_error": spec_rms,
+                     "real_space_quadrature_rms": quad,
+                     "sigma_l_estimated_binned": binned(sigma_l),
+                     "spectrum_rel_error_binned": binned(np.abs(spec_err)),
+                     "cap_weight_bytes": k.cap_weight_bytes()})
+        del k, h, y
+        torch.cuda.synchronize()
+    ctx.status()
+    return {"nside": nside, "lmax": lmax, "fwhm_arcmin": fwhm, "theta_cut_arcmin": tc_arcmin, "alpha": alpha,
+            "l_bins": edges.tolist(), "full_kernel_setup_and_apply_s": t_full, "rows": rows,
+            "data": "white noise band-limited to l_max (C_l flat, the paper's uniform-noise input)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.errors:
+        run_errors(args)
     elif args.bands:
         run_bands(args)
     else:

@@ -462,6 +462,15 @@ int sk_harmonic_table_bytes(const sk_harm *h, int64_t *bytes);
 int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *h, const float *d_in, float *d_out, int64_t batch,
                       int64_t map_stride, int accumulate, void *stream);
 
+/* Power spectra of maps by the handle's analysis (the spectra the paper extracts from
+ * convolved uniform-noise maps to judge a split, Sec. 3):
+ *   d_cl[b][l] = (|a_l0|^2 + 2 sum_{m=1}^{l} |a_lm|^2) / (2l + 1),  l = 0..lmax,
+ * with a_lm = dOmega sum_q x_q Y*_lm(q) of map b, accumulated in FP64 from the FP32
+ * transform.  d_cl: FP64 device [batch][lmax + 1].  Uses the handle's buffers: calls
+ * with one handle must not overlap on the GPU.  Errors: as sk_harmonic_apply. */
+int sk_harmonic_spectrum(sk_ctx *ctx, const sk_harm *h, const float *d_in, int64_t batch, int64_t map_stride,
+                         double *d_cl, void *stream);
+
 /* ---- ring-pair Fourier form of the belt, for wide theta_cut --------------- */
 
 /* In the equatorial zone (rings of 4 Nside pixels) the real-space sum between

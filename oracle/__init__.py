@@ -21,7 +21,10 @@ splitting"):
   sin theta dtheta, i.e. P_{l theta} K^_theta of Eq. 1, and ``harmonic_part``:
   K^_l = K_l - R_l for l <= l_cut (so K~_l = K^_l + R_l reproduces K_l there);
 * ``real_ylm`` / ``sht_convolve``: a plain spherical-harmonic transform for the
-  harmonic part (the role the paper gives to the CPU SHT, Sec. 2);
+  harmonic part (the role the paper gives to the CPU SHT, Sec. 2), brute force;
+  ``sht_analysis_rings`` / ``sht_synthesis_rings`` / ``power_spectrum``: the same
+  pixel-sum transform written ring by ring (for larger maps), and the power spectrum
+  the paper extracts from convolved maps (Sec. 3, the spectra of its error figures);
 * ``relative_error_estimate``: the fractional rms estimate of Eq. 2;
 * ``hat_response_matrix`` / ``fit_real_kernel``: the real-space part as a
   least-squares fit (Sec. 3: K^_theta is fit so that its harmonic transform
@@ -404,6 +407,86 @@ def sht_convolve(nside: int, x: np.ndarray, k_ell: np.ndarray, lmax: int) -> np.
     a = dOmega * (Y @ _f64(x))
     kl = np.concatenate([np.full(2 * l + 1, k_ell[l]) for l in range(lmax + 1)])
     return Y.T @ (kl * a)
+
+
+def _ring_geometry(nside: int):
+    """Per ring (0-based): pixel count, first pixel, shift, colatitude (from ring_info)."""
+    nr = 4 * nside - 1
+    rows = [ring_info(nside, r) for r in range(1, nr + 1)]
+    n = np.array([q[0] for q in rows], np.int64)
+    st = np.array([q[1] for q in rows], np.int64)
+    sh = np.array([q[2] for q in rows], np.int64)
+    th = np.arctan2(np.array([q[4] for q in rows]), np.array([q[3] for q in rows]))
+    return n, st, sh, th
+
+
+def _lambda_lm(lmax: int, theta: np.ndarray):
+    """Orthonormal associated Legendre functions lambda_lm(theta) (Y_lm = lambda_lm e^{i m phi}),
+    l = 0..lmax, m = 0..l, by the same three-term recurrence in l at fixed m as real_ylm;
+    returns a dict m -> array [l - m, len(theta)]."""
+    x = np.cos(theta); sx = np.sin(theta)
+    out = {}
+    pmm = np.full(len(x), math.sqrt(1.0 / (4.0 * math.pi)))
+    for m in range(lmax + 1):
+        if m > 0:
+            pmm = -math.sqrt((2 * m + 1) / (2.0 * m)) * sx * pmm
+        rows = np.empty((lmax - m + 1, len(x)))
+        rows[0] = pmm
+        if m + 1 <= lmax:
+            rows[1] = math.sqrt(2 * m + 3) * x * pmm
+        for l in range(m + 2, lmax + 1):
+            a = math.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
+            b = math.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0))
+            rows[l - m] = a * (x * rows[l - 1 - m] - b * rows[l - 2 - m])
+        out[m] = rows
+    return out
+
+
+def sht_analysis_rings(nside: int, x: np.ndarray, lmax: int) -> dict:
+    """a_lm = dOmega sum_p x_p Y*_lm(p) for m = 0..l (complex; a_{l,-m} = (-1)^m conj a_lm
+    for a real map), the pixel sum of the plain transform written ring by ring: with
+    Y_lm = lambda_lm(theta) e^{i m phi} and phi_j = pi (2j + s)/n on a ring,
+    a_lm = dOmega sum_r lambda_lm(theta_r) F_r(m), F_r(m) = sum_j x_j e^{-i m phi_j} =
+    e^{-i pi m s / n} X_r(m mod n) with X_r the ring's DFT (numpy FFT).  FP64.
+    Returns a dict m -> complex array [l - m]."""
+    n, st, sh, th = _ring_geometry(nside)
+    x = np.asarray(x, np.float64)
+    dOmega = 4.0 * math.pi / npix(nside)
+    ms = np.arange(lmax + 1)
+    F = np.empty((len(n), lmax + 1), np.complex128)
+    for r in range(len(n)):
+        X = np.fft.fft(x[st[r]: st[r] + n[r]])
+        F[r] = np.exp(-1j * math.pi * ms * sh[r] / n[r]) * X[ms % n[r]]
+    lam = _lambda_lm(lmax, th)
+    return {m: dOmega * (lam[m] @ F[:, m]) for m in range(lmax + 1)}
+
+
+def sht_synthesis_rings(nside: int, alm: dict, lmax: int, k_ell: np.ndarray = None) -> np.ndarray:
+    """y_p = sum_{l <= lmax} sum_m k_l a_lm Y_lm(p) for a real map (k_l = 1 if None):
+    y = Re G_r(0) + 2 Re sum_{m >= 1} G_r(m) e^{i m phi_j}, G_r(m) = sum_l k_l a_lm
+    lambda_lm(theta_r).  On a ring of n pixels e^{i m phi_j} = e^{i pi m s/n} e^{2 pi i j m/n},
+    so the sum over m is an inverse DFT of the terms folded onto m mod n (numpy FFT).  FP64."""
+    n, st, sh, th = _ring_geometry(nside)
+    lam = _lambda_lm(lmax, th)
+    kl = np.ones(lmax + 1) if k_ell is None else np.asarray(k_ell, np.float64)
+    G = np.stack([(kl[m:lmax + 1, None] * lam[m] * alm[m][:, None]).sum(axis=0) for m in range(lmax + 1)],
+                 axis=1)                                       # [rings, m]
+    y = np.empty(npix(nside))
+    ms = np.arange(lmax + 1)
+    wm = np.where(ms == 0, 1.0, 2.0)
+    for r in range(len(n)):
+        H = np.zeros(n[r], np.complex128)
+        np.add.at(H, ms % n[r], wm * G[r] * np.exp(1j * math.pi * ms * sh[r] / n[r]))
+        y[st[r]: st[r] + n[r]] = (n[r] * np.fft.ifft(H)).real
+    return y
+
+
+def power_spectrum(alm: dict, lmax: int) -> np.ndarray:
+    """C_l = (|a_l0|^2 + 2 sum_{m >= 1} |a_lm|^2) / (2l + 1) of a real map's a_lm (m >= 0)."""
+    C = np.zeros(lmax + 1)
+    for m in range(lmax + 1):
+        C[m:] += (1.0 if m == 0 else 2.0) * np.abs(alm[m]) ** 2
+    return C / (2.0 * np.arange(lmax + 1) + 1.0)
 
 
 def conv_function_brute(nside: int, kernel_fn, theta_cut: float, x: np.ndarray) -> np.ndarray:

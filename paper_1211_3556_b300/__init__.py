@@ -95,6 +95,7 @@ def _declare(L):
         "sk_harmonic_destroy": (I, [P]),
         "sk_harmonic_table_bytes": (I, [P, ctypes.POINTER(I64)]),
         "sk_harmonic_apply": (I, [P, P, P, P, I64, I64, I, P]),
+        "sk_harmonic_spectrum": (I, [P, P, P, I64, I64, P, P]),
         "sk_fourier_create": (I, [P, P, PP]),
         "sk_fourier_destroy": (I, [P]),
         "sk_fourier_info": (I, [P, ctypes.POINTER(I64)]),
@@ -645,6 +646,16 @@ class Harmonic:
                                        ctypes.c_void_p(o2.data_ptr()), b, stride, 1 if accumulate else 0,
                                        _stream_ptr(stream)))
         return out if out.dim() == x.dim() else out.view_as(x)
+
+    def spectrum(self, x, stream=None):
+        """Power spectra C_l = sum_m |a_lm|^2 / (2l + 1), l = 0..lmax, of maps x [batch, npix]
+        (float32 CUDA) from the handle's analysis: a float64 CUDA tensor [batch, lmax + 1]."""
+        import torch
+        x2, b, stride = _map_args(x, self.geom.npix)
+        cl = torch.empty(b, self.lmax + 1, dtype=torch.float64, device=x2.device)
+        _check(lib().sk_harmonic_spectrum(self.ctx._h, self._h, ctypes.c_void_p(x2.data_ptr()), b, stride,
+                                          ctypes.c_void_p(cl.data_ptr()), _stream_ptr(stream)))
+        return cl
 
     def __del__(self):
         try:

@@ -671,19 +671,11 @@ static int cz_fft(sk_harm *h, long long batch, int dir) {
     return SK_OK;
 }
 
-extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_in, float *d_out, int64_t batch,
-                                 int64_t map_stride, int accumulate, void *stream) {
-    if (!ctx || !hc || (!d_in && batch > 0) || (!d_out && batch > 0))
-        return sk_fail(SK_EINVAL, "sk_harmonic_apply: NULL argument");
-    sk_harm *h = const_cast<sk_harm *>(hc);
+// The analysis half of the transform: ring DFTs of `batch` maps into h->d_F and the
+// Legendre analysis into h->d_a (a_lm, m = 0..L, l = m..L; per map a_n float2).
+static int harm_analysis(sk_ctx *ctx, sk_harm *h, const float *d_in, int64_t batch, int64_t map_stride,
+                         cudaStream_t st) {
     const sk_geom *g = h->g;
-    if (batch < 0 || map_stride < g->npix) return sk_fail(SK_EINVAL, "sk_harmonic_apply: bad batch or stride");
-    if (batch == 0) return SK_OK;
-    if (d_in == d_out) return sk_fail(SK_EINVAL, "sk_harmonic_apply: input and output alias");
-    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15) || (map_stride & 3))
-        return sk_fail(SK_EINVAL, "sk_harmonic_apply: maps must be 16-byte aligned with a stride multiple of 4");
-    SK_CU(cudaSetDevice(ctx->device));
-    cudaStream_t st = (cudaStream_t)stream;
     const int N = (int)g->nside, nr = g->nr, L = h->L, nrh = h->nrh;
     if (batch > h->cap_batch) {
         cudaFree(h->d_F); h->d_F = nullptr;
@@ -693,9 +685,10 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
         SK_CU(cudaMalloc(&h->d_a, sizeof(float2) * (size_t)batch * h->a_n));
         h->cap_batch = batch;
     }
-    const int nb = 2 * N + 1, n4 = 4 * N;
+    const int nb = 2 * N + 1;
     const float domega = (float)(4.0 * SK_PI / (double)g->npix);
     const long long zone0 = g->h_rings[N - 1].start;     // first pixel of the equatorial zone
+    (void)ctx;
     if (cufftSetStream(h->p_r2c, st) != CUFFT_SUCCESS || cufftSetStream(h->p_c2r, st) != CUFFT_SUCCESS)
         return sk_fail(SK_ECUDA, "sk_harmonic_apply: cufftSetStream failed");
     // ring DFTs: the cap rings by chirp-z transforms, the zone by one R2C per map
@@ -733,6 +726,18 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
     k_leg_analysis<<<dim3(L + 1, (unsigned)batch), HT, sm_a, st>>>(h->d_lam, h->d_moff, h->d_aoff, h->d_F, L, nr,
                                                                     nrh, h->a_n, domega, h->d_a);
     SK_CU(cudaGetLastError());
+    return SK_OK;
+}
+
+// The synthesis half: y (+)= sum_lm K^_l a_lm Y_lm from h->d_a.
+static int harm_synthesis(sk_ctx *ctx, sk_harm *h, float *d_out, int64_t batch, int64_t map_stride, int accumulate,
+                          cudaStream_t st) {
+    const sk_geom *g = h->g;
+    const int N = (int)g->nside, nr = g->nr, L = h->L, nrh = h->nrh;
+    const int nb = 2 * N + 1, n4 = 4 * N;
+    const long long zone0 = g->h_rings[N - 1].start;
+    const int ncap = 2 * (N - 1);
+    (void)ctx;
     k_leg_synthesis<<<dim3(L + 1, (unsigned)batch), HT, sizeof(float2) * (L + 1), st>>>(
         h->d_lam, h->d_moff, h->d_aoff, h->d_kl, h->d_a, L, nr, nrh, h->a_n, h->d_F);
     SK_CU(cudaGetLastError());
@@ -760,6 +765,56 @@ extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_
                                                                                  accumulate);
         SK_CU(cudaGetLastError());
     }
+    return SK_OK;
+}
+
+static int check_harm_maps(const char *who, const sk_harm *h, const float *in, const float *out, int64_t batch,
+                           int64_t map_stride) {
+    if (batch < 0 || map_stride < h->g->npix) return sk_fail(SK_EINVAL, "%s: bad batch or stride", who);
+    if (batch > 0 && (!in || (out && in == out))) return sk_fail(SK_EINVAL, "%s: NULL or aliasing maps", who);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15) || (map_stride & 3))
+        return sk_fail(SK_EINVAL, "%s: maps must be 16-byte aligned with a stride multiple of 4", who);
+    return SK_OK;
+}
+
+extern "C" int sk_harmonic_apply(sk_ctx *ctx, const sk_harm *hc, const float *d_in, float *d_out, int64_t batch,
+                                 int64_t map_stride, int accumulate, void *stream) {
+    if (!ctx || !hc || (!d_in && batch > 0) || (!d_out && batch > 0))
+        return sk_fail(SK_EINVAL, "sk_harmonic_apply: NULL argument");
+    sk_harm *h = const_cast<sk_harm *>(hc);
+    if (int rc = check_harm_maps("sk_harmonic_apply", h, d_in, d_out, batch, map_stride)) return rc;
+    if (batch == 0) return SK_OK;
+    SK_CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = harm_analysis(ctx, h, d_in, batch, map_stride, st)) return rc;
+    return harm_synthesis(ctx, h, d_out, batch, map_stride, accumulate, st);
+}
+
+// C_l = (|a_l0|^2 + 2 sum_{m>=1} |a_lm|^2) / (2l + 1), in FP64, one thread per (l, map).
+__global__ void k_spectrum(const float2 *a, const long long *aoff, int L, long long a_n, int batch, double *cl) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (l > L || b >= batch) return;
+    const float2 *ab = a + (long long)b * a_n;
+    double s = 0.0;
+    for (int m = 0; m <= l; ++m) {
+        const float2 v = ab[aoff[m] + (l - m)];
+        s += (m == 0 ? 1.0 : 2.0) * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+    cl[(long long)b * (L + 1) + l] = s / (2.0 * l + 1.0);
+}
+
+extern "C" int sk_harmonic_spectrum(sk_ctx *ctx, const sk_harm *hc, const float *d_in, int64_t batch,
+                                    int64_t map_stride, double *d_cl, void *stream) {
+    if (!ctx || !hc || (batch > 0 && (!d_in || !d_cl))) return sk_fail(SK_EINVAL, "sk_harmonic_spectrum: NULL argument");
+    sk_harm *h = const_cast<sk_harm *>(hc);
+    if (int rc = check_harm_maps("sk_harmonic_spectrum", h, d_in, nullptr, batch, map_stride)) return rc;
+    if (batch == 0) return SK_OK;
+    SK_CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = harm_analysis(ctx, h, d_in, batch, map_stride, st)) return rc;
+    k_spectrum<<<dim3((h->L + HT) / HT, (unsigned)batch), HT, 0, st>>>(h->d_a, h->d_aoff, h->L, h->a_n, (int)batch,
+                                                                       d_cl);
+    SK_CU(cudaGetLastError());
     return SK_OK;
 }
 

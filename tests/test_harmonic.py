@@ -193,3 +193,32 @@ def test_plan_split_picks_the_fastest_feasible_candidate(sk):
     assert best["ms_total"] == min(r["ms_total"] for r in ok)
     for r in rows:
         assert r["ms_real"] > 0 and r["ms_harmonic"] > 0
+
+
+# ------------------------------------------------------------------ larger maps, spectra
+
+@pytest.mark.parametrize("nside,lmax", [(128, 200), (256, 383)])
+def test_harmonic_matches_ring_oracle_above_nside_32(sk, nside, lmax):
+    # the oracle's ring-by-ring FP64 transform (the pixel-sum transform rewritten with ring
+    # FFTs, pinned to the brute-force one on the CPU): y = synthesis(K^_l analysis(x))
+    kl = np.exp(-np.arange(lmax + 1) / (0.4 * lmax)) * (1.0 + 0.3 * np.cos(np.arange(lmax + 1) / 7.0))
+    x = white_noise_maps(nside, 1, 730 + nside)[0]
+    y = run_harm(sk, nside, kl, lmax, x)[0]
+    a = O.sht_analysis_rings(nside, x.astype(np.float64), lmax)
+    ref = O.sht_synthesis_rings(nside, a, lmax, kl)
+    assert rms_rel(y, ref) <= HARM_BOUND
+
+
+@pytest.mark.parametrize("nside,lmax", [(32, 63), (128, 255)])
+def test_power_spectrum_matches_oracle(sk, nside, lmax):
+    import torch
+    g = sk.Geometry(sk._hctx, nside)
+    h = sk.Harmonic(sk._hctx, g, np.ones(lmax + 1), lmax)
+    x = white_noise_maps(nside, 2, 740 + nside)
+    cl = h.spectrum(torch.from_numpy(x).cuda()).cpu().numpy()
+    torch.cuda.synchronize()
+    sk._hctx.status()
+    for b in range(2):
+        ref = O.power_spectrum(O.sht_analysis_rings(nside, x[b].astype(np.float64), lmax), lmax)
+        assert np.abs(cl[b] - ref).max() <= 1e-5 * ref.max()
+        assert np.abs(cl[b] / ref - 1.0).max() <= 1e-4       # every l: white noise keeps C_l ~ 1

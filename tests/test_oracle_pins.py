@@ -381,6 +381,32 @@ def test_sht_convolution_equals_real_space_sum_of_its_kernel():
 
 # ----------------------------------------------------------------- gradient
 
+@pytest.mark.parametrize("nside", [4, 8, 16])
+def test_ring_transform_equals_the_pixel_sum_transform(nside):
+    """The ring-by-ring transform (ring FFTs times lambda_lm, for larger maps) is the
+    brute-force pixel-sum transform of real_ylm (itself pinned by the addition theorem)
+    rewritten: same a_lm (as spectra), same synthesis, and the power spectrum of a map
+    made of one real harmonic is that harmonic's l alone (up to the pixel quadrature)."""
+    lmax = 2 * nside
+    x = white_noise_maps(nside, 1, 300 + nside)[0].astype(np.float64)
+    a = O.sht_analysis_rings(nside, x, lmax)
+    th, ph = O.pixel_angles(nside)
+    Y = O.real_ylm(lmax, th, ph)
+    ar = (4 * math.pi / O.npix(nside)) * (Y @ x)
+    C_brute = np.array([np.sum(ar[l * l:(l + 1) ** 2] ** 2) / (2 * l + 1) for l in range(lmax + 1)])
+    assert np.allclose(O.power_spectrum(a, lmax), C_brute, rtol=1e-12, atol=1e-14 * C_brute.max())
+    kl = np.linspace(1.0, 0.1, lmax + 1)
+    kr = np.concatenate([np.full(2 * l + 1, kl[l]) for l in range(lmax + 1)])
+    y_brute = Y.T @ (kr * ar)
+    y_ring = O.sht_synthesis_rings(nside, a, lmax, kl)
+    assert np.abs(y_ring - y_brute).max() <= 1e-12 * np.abs(y_brute).max()
+    # a single harmonic l = nside / 2: the spectrum peaks there
+    l0 = nside // 2
+    a1 = O.sht_analysis_rings(nside, Y[l0 * l0 + l0], lmax)
+    C1 = O.power_spectrum(a1, lmax)
+    assert np.argmax(C1) == l0 and C1[l0] > 0.9 / (2 * l0 + 1)
+
+
 def test_table_gradient_equals_central_differences():
     nside, tc, nt = 8, 0.35, 24
     rng = np.random.default_rng(11)
