@@ -343,6 +343,8 @@ static int finish_kernel(sk_kern *k) {
     if (rc) return rc;
     rc = sk_capw_build(k);
     if (rc) return rc;
+    rc = sk_beltw_build(k);
+    if (rc) return rc;
     SK_CU(cudaDeviceSynchronize());
     return SK_OK;
 }
@@ -419,6 +421,10 @@ extern "C" int sk_kernel_update_values(sk_kern *k, const double *h_values) {
         int rc = sk_capw_build(k);                  // the stored cap weights follow the table
         if (rc) return rc;
     }
+    if (k->d_beltw) {
+        int rc = sk_beltw_build(k);                 // and the stored belt rows
+        if (rc) return rc;
+    }
     SK_CU(cudaDeviceSynchronize());
     return SK_OK;
 }
@@ -430,6 +436,10 @@ extern "C" int sk_kernel_update_values_async(sk_kern *k, const double *d_values,
     cudaStream_t st = (cudaStream_t)stream;
     SK_CU(sk_launch_update_values(d_values, k->d_V, k->nt, k->d_changed, st));
     SK_CU(sk_launch_make_table(k->d_V, k->nt, 4.0 * SK_PI / (double)k->g->npix, k->d_tab, st, k->d_changed));
+    if (k->d_beltw) {
+        int rc = sk_beltw_build(k, st, k->d_changed);
+        if (rc) return rc;
+    }
     if (k->d_capw) return sk_capw_build(k, false, st, k->d_changed);
     return SK_OK;
 }

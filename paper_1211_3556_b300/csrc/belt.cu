@@ -116,9 +116,11 @@ __global__ void k_belt_weights(const JobDesc J, float *w) {
 // with (o, nch) = bpr of that row, element c < 4 nch holds the weights at offset
 // e = EMIN + o + c of output rings b_lo + grp G + 2w and + 1 against ring i,
 // zero outside a row's window (or where ring i is not in that output ring's
-// window list) and past 4 nch.  One thread per element.
-__global__ void k_belt_pairs(const JobDesc J, int g0, int g1, float2 *w) {
+// window list) and past 4 nch.  One thread per element.  With `gate`, nothing is
+// written unless *gate is set (the table did not change: the stored rows stand).
+__global__ void k_belt_pairs(const JobDesc J, int g0, int g1, float2 *w, const int *gate) {
     constexpr int NW = SK_BELT_WARPS;
+    if (gate && !*gate) return;
     const long long base = (long long)g0 * J.smax * NW * J.WPM;
     const long long n = (long long)g1 * J.smax * NW * J.WPM;
     const double half_step = SK_PI / (2.0 * (double)J.n4);
@@ -377,11 +379,11 @@ cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st) {
+cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st, const int *gate) {
     const long long n = (long long)(g1 - g0) * j.smax * SK_BELT_WARPS * j.WPM;
     if (n <= 0) return cudaSuccess;
     const long long blocks = (n + 255) / 256;
-    k_belt_pairs<<<(unsigned)std::min<long long>(blocks, 1 << 20), 256, 0, st>>>(j, g0, g1, w);
+    k_belt_pairs<<<(unsigned)std::min<long long>(blocks, 1 << 20), 256, 0, st>>>(j, g0, g1, w, gate);
     return cudaGetLastError();
 }
 

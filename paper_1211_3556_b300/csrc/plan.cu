@@ -81,6 +81,7 @@ void sk_capw_free(sk_kern *k) {
 
 void sk_plan_free(sk_kern *k) {
     sk_capw_free(k);
+    cudaFree(k->d_beltw); k->d_beltw = nullptr;
     cudaFree(k->d_capw_ring); k->d_capw_ring = nullptr;
     k->h_capw_ring.clear();
     k->capw_len = 0;
@@ -690,8 +691,24 @@ int sk_capw_build(sk_kern *k, bool force, cudaStream_t st, const int *gate) {
     return SK_OK;
 }
 
+int sk_beltw_build(sk_kern *k, cudaStream_t st, const int *gate) {
+    if (!k->plan_ok || k->nb == 0) return SK_OK;
+    if (!k->d_beltw) {
+        const size_t bytes = (size_t)k->ngroups * k->smax * SK_BELT_WARPS * k->WPM * sizeof(float2);
+        if (cudaMalloc(&k->d_beltw, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            k->d_beltw = nullptr;                   // the pre-pass stays per call
+            return SK_OK;
+        }
+    }
+    SkJob jb{k, nullptr, nullptr, 1, 0};
+    SK_CU(sk_launch_belt_pairs(belt_desc(jb, nullptr), 0, k->ngroups, k->d_beltw, st, gate));
+    return SK_OK;
+}
+
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
-    // belt weight rows first (one pre-pass per job, shared by all its maps)
+    // belt weight rows first: stored with the operator for the FP32 belt, else one pre-pass
+    // per job into the workspace, shared by all its maps
     std::vector<float *> wrows(n, nullptr);
     char *wp = (char *)ws;
     if (path == SK_PATH_AUTO || path == SK_PATH_TENSOR) {
@@ -700,10 +717,15 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
             wrows[i] = (float *)wp;
             wp += sk_plan_workspace_bytes(k);
+            const bool tensor = path == SK_PATH_TENSOR && k->tc_ok;
+            if (!tensor && k->d_beltw) {
+                wrows[i] = (float *)k->d_beltw;
+                continue;
+            }
             if (!jobs[i].weights) continue;             // rows already in the workspace
             JobDesc d = belt_desc(jobs[i], nullptr);
             cudaEvent_t ev = sk_prof_begin(ctx, st);
-            if (path == SK_PATH_TENSOR && k->tc_ok)
+            if (tensor)
                 SK_CU(sk_launch_belt_weights(d, wrows[i], st));                 // rows
             else
             {

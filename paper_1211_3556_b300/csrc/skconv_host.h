@@ -120,6 +120,10 @@ struct sk_kern {
     float4 *d_capw = nullptr;
     bool capw_wanted = true;
     int *d_changed = nullptr;              // sk_kernel_update_values_async: whether the values changed
+    // stored belt weights of the FP32 belt kernel (ring-pair rows of all groups, as the
+    // pair-row pre-pass writes them), rebuilt with the table; null: the pre-pass runs
+    // per call into the workspace
+    float2 *d_beltw = nullptr;
     // batched tensor-core form of the belt: (group, 128-pixel block) items
     bool tc_ok = false;
     TcGeom tcg{};
@@ -169,6 +173,10 @@ int sk_plan_build(sk_kern *k);
 // With `gate`, the rebuild kernels run on `st` and return at once unless *gate is set.
 int sk_capw_build(sk_kern *k, bool force = false, cudaStream_t st = 0, const int *gate = nullptr);
 void sk_capw_free(sk_kern *k);
+// Stored belt ring-pair rows: allocate (if absent) and evaluate from the current table
+// (same gate and stream rules as sk_capw_build; an allocation that fails leaves the
+// pre-pass per call).
+int sk_beltw_build(sk_kern *k, cudaStream_t st = 0, const int *gate = nullptr);
 void sk_plan_free(sk_kern *k);
 int sk_plan_rebuild_belt_items(sk_kern *k);
 size_t sk_plan_workspace_bytes(const sk_kern *k);

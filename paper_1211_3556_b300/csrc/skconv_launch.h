@@ -112,8 +112,10 @@ cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const
 // convolution kernels; grid = number of blocks (persistent)
 cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);
 cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st);
-// weight rows of belt ring groups [g0, g1) (the rows of other groups are not written)
-cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st);
+// weight rows of belt ring groups [g0, g1) (the rows of other groups are not written);
+// with `gate`, only if *gate is non-zero
+cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st,
+                                 const int *gate = nullptr);
 size_t sk_belt_smem_bytes(int P, int wpm);   // dynamic shared memory of a belt block
 cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st);
 // mode bits: 1 sin series valid on every window of the items, 2 theta_cut <= 0.25
