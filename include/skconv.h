@@ -398,6 +398,15 @@ int sk_selftest_wait_timeout(sk_ctx *ctx, double seconds, void *stream);
 int sk_selftest_tc_gemm(sk_ctx *ctx, const float *d_a, const float *d_b, float *d_d, int n, int k,
                         int passes, void *stream);
 
+/* Self-test of the operand form of the tensor-core belt: one block computes
+ * D[r][s] = sum_{k < K} A[r][k] x[8 s + k + off] (A: 128 x k row-major, x: at least
+ * 8 (n + k/8 + 2) floats, D: 128 x n row-major; FP32 device buffers) with 3xTF32
+ * tcgen05 MMAs from no-swizzle K-major shared-memory operands, x read as sliding
+ * rows of three 16-byte-row planes.  n a multiple of 16 in [16, 256], k a multiple
+ * of 8 in [8, 64], off 0 or 4.  Errors: SK_EINVAL, SK_ECUDA. */
+int sk_selftest_tc_sliding(sk_ctx *ctx, const float *d_a, const float *d_x, float *d_d, int n, int k, int off,
+                           void *stream);
+
 /* ---- harmonic half of the split (Sec. 2, Eq. 1: the l <= l_cut part) ----
  *
  * The split convolution adds to the real-space sum above the harmonic part

@@ -88,6 +88,7 @@ def _declare(L):
         "sk_kernel_autotune": (I, [P, P, P, P, I64, I64, ctypes.c_char_p, P, ctypes.POINTER(I)]),
         "sk_selftest_wait_timeout": (I, [P, D, P]),
         "sk_selftest_tc_gemm": (I, [P, P, P, P, I, I, I, P]),
+        "sk_selftest_tc_sliding": (I, [P, P, P, P, I, I, I, P]),
         "sk_kernel_get_tiles": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sk_kernel_response": (I, [P, P, I, P]),
         "sk_fit_real_kernel": (I, [P, P, I, I, D, I, I, D, D, P, P]),

@@ -83,6 +83,7 @@ extern "C" int sk_destroy(sk_ctx *ctx) {
     if (!ctx) return SK_OK;
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->tcz) cudaFree(ctx->tcz);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_queue) cudaFree(ctx->d_queue);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
@@ -425,6 +426,10 @@ extern "C" int sk_kernel_update_values(sk_kern *k, const double *h_values) {
         int rc = sk_beltw_build(k);                 // and the stored belt rows
         if (rc) return rc;
     }
+    if (k->d_tca) {
+        int rc = sk_tca_build(k);                   // and the tensor-core belt's tiles
+        if (rc) return rc;
+    }
     SK_CU(cudaDeviceSynchronize());
     return SK_OK;
 }
@@ -438,6 +443,10 @@ extern "C" int sk_kernel_update_values_async(sk_kern *k, const double *d_values,
     SK_CU(sk_launch_make_table(k->d_V, k->nt, 4.0 * SK_PI / (double)k->g->npix, k->d_tab, st, k->d_changed));
     if (k->d_beltw) {
         int rc = sk_beltw_build(k, st, k->d_changed);
+        if (rc) return rc;
+    }
+    if (k->d_tca) {
+        int rc = sk_tca_build(k, st, k->d_changed);
         if (rc) return rc;
     }
     if (k->d_capw) return sk_capw_build(k, false, st, k->d_changed);

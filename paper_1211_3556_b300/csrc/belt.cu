@@ -82,35 +82,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Weight rows: w[rb][d + HM][c] = dOmega K_lin for output ring b_lo + rb, input
-// ring +d, pixel offset e = EMIN + c; zero outside the row's window |e - e_c| <= W.
-__global__ void k_belt_weights(const JobDesc J, float *w) {
-    const int R2 = 2 * J.HM + 1;
-    const int row = blockIdx.x;
-    const int rb = row / R2, d = row % R2 - J.HM;
-    float *out = w + (size_t)row * J.WPM;
-    const int2 r = (rb < J.nb) ? J.brng[row] : make_int2(1, 0);
-    const int ro = J.b_lo + rb;
-    PairInfo P;
-    int s_o = 0, ec = 0;
-    if (r.x <= r.y) {
-        const int p0 = J.pair_off[ro];
-        P = J.pairs[p0 + (ro + d - J.pairs[p0].ri)];
-        s_o = J.rings[ro].s;
-        ec = (s_o + 1 - P.s_i) >> 1;
-    }
-    const double half_step = SK_PI / (2.0 * (double)J.n4);
-    for (int c = threadIdx.x; c < J.WPM; c += blockDim.x) {
-        float v = 0.0f;
-        const int e = J.EMIN + c;
-        if (r.x <= r.y && e >= ec - P.W && e <= ec + P.W) {
-            const float x = (float)((double)(2 * e + P.s_i - s_o) * half_step);
-            v = pair_weight(x, P.A, P.B, J.kp, J.tab);
-        }
-        out[c] = v;
-    }
-}
-
 // Weight rows as ring pairs, in the order the main kernel streams them: for
 // group grp, strip si (input ring i = bgrp[grp].x + si) and consumer warp w,
 // with (o, nch) = bpr of that row, element c < 4 nch holds the weights at offset
@@ -371,13 +342,6 @@ size_t belt_smem(const JobsArg &a, int P) {
 }
 
 }  // namespace
-
-cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st) {
-    const int groups = (j.nb + G - 1) / G;
-    const int rows = groups * G * (2 * j.HM + 1);
-    k_belt_weights<<<rows, 32, 0, st>>>(j, w);
-    return cudaGetLastError();
-}
 
 cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st, const int *gate) {
     const long long n = (long long)(g1 - g0) * j.smax * SK_BELT_WARPS * j.WPM;

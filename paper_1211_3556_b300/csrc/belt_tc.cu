@@ -1,35 +1,41 @@
-// belt_tc.cu -- batched tensor-core form of the belt path (tcgen05, 3xTF32).
+// belt_tc.cu -- tensor-core form of the belt path (tcgen05, 3xTF32).
 //
-// For many maps sharing one kernel the belt sums are a dense contraction per
-// ring block: for input ring i and output ring o (both with 4 Nside pixels)
-//   Y[o][j][b] += sum_k W_{o,i}[j, k] X[i][k][b],   W_{o,i}[j, k] = w(o, i, e = k - j)
-// with the Toeplitz weight rows w of the belt path (the same operator: the
-// real-space convolution of Sec. 2, Eq. 1 with the tabulated kernel of Sec. 3).
-//
-// Work item: 16 consecutive belt rings x 64 consecutive pixels x 32 maps.
-//  * MMA shape M = 128 (16 rings x 8 output pixels), N = 32 maps, K = 8.
-//  * A (weights, 128 x KT): row (r, n) = ring r of the block, output pixel n of
-//    an 8-pixel segment; column k = input pixel j0s + EMIN4 + k.  Toeplitz, so
-//    the same tile serves all 8 segments of the item; rebuilt per input ring.
-//  * B (maps, 32 x XL): the 32 maps' pixels j0 + EMIN4 .. j0 + EMIN4 + XL of
-//    input ring i (wrapped around the ring); segment s uses columns 8s ..
-//    8s + KT, i.e. the same tile with the descriptor start moved by 32 bytes
-//    per segment.
-//  * 3xTF32: A and B are split into TF32 hi/lo parts (both rounded to nearest)
-//    and hi*hi + hi*lo + lo*hi approximates the FP32 product.
-//  * D: per segment two 128 x 32 accumulators in tensor memory (all 512
-//    columns): one for hi*hi, one for the small hi*lo + lo*hi terms.  The
-//    tensor core adds each MMA's products into its FP32 accumulator with a
-//    truncation relative to the accumulator; keeping the small terms apart
-//    keeps that error ~2^-10 smaller for them, and the two are added in FP32
-//    when read back.
-// Warp-specialised: 15 builder warps write the operands into 128-byte-swizzled
-// K-major shared memory (two stages), loading the next input ring's maps and
-// weight rows into registers while the current one is built, and arrive on
-// the stage's "full" mbarrier; one MMA warp waits on it, issues the MMAs (the
-// descriptors differ only in their start-address field) and commits them to
-// the stage's "empty" mbarrier, which releases the stage to the builders.
-// Bounded waits record SK_ETIMEOUT.
+// Same operator as the FP32 belt (the real-space convolution of Sec. 2, Eq. 1
+// with the tabulated kernel of Sec. 3); only the order of work differs.  In the
+// belt every ring has n = 4 Nside pixels and the weight of output pixel j of ring
+// o against input pixel j + e of ring i depends on (o, i, e) only.  For a group of
+// SK_BELT_G = 16 output rings and one input ring i:
+//   y_o[j0 + 8 s + n] += sum_k A_i[(o, n)][k] x_i[j0 + E0 + 8 s + k]
+//   A_i[(o, n)][k] = w(o, i, e = k - n + E0)
+// a dense product with rows (o, n) = 16 rings x 8 pixels (M = 128), columns
+// s = the item's 8-pixel segments (N = nn <= 256) and k < K_i, where E0 is the
+// first offset of the union of the group's windows against ring i rounded down
+// to a multiple of 4 and K_i covers the union plus the 7 extra columns of the
+// 8 output pixels (a multiple of 8).  For k-step q the B operand is
+// B_q[s][t] = x_i[j0 + E0 + 8 (s + q) + t]: the input ring read in sliding rows.
+// Staged as planes of 16-byte rows (pixels 8m .. 8m+3, "even", and 8m+4 ..
+// 8m+7, "odd", of the ring), every k-step of both operands is a start address
+// in shared memory (no-swizzle K-major, rows 16 bytes apart), so nothing is
+// rebuilt inside the loop:
+//  * A (TF32 hi and lo parts) is stored per (group, input ring) with the
+//    operator (k_tc_tiles) and rebuilt with its table;
+//  * the maps' planes (hi and lo parts, wrapped around each ring) are written
+//    by one pass per call (k_tc_planes);
+// one producer thread streams both into shared memory with 1-D bulk copies.
+// 3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation): the tiles of a group are
+// taken in chunks of consecutive input rings with at least SK_TC_CHUNK_KSTEPS
+// k-steps; each chunk is accumulated by the tensor cores in a fresh
+// tensor-memory accumulator, two of them in turn (256 columns each), and the
+// epilogue warps add the chunks' partial sums into registers with FP32
+// round-to-nearest additions while the next chunk is multiplied.  The tensor
+// cores' own accumulation then spans a few tens of MMAs: summing a whole item
+// (about 40 tiles, 500 MMAs) in tensor memory measured an rms relative error
+// near 1.1e-6 against the FP32 path at Nside 2048, per-tile partial sums 3.6e-7.
+// A chunk also keeps each hand-over of an accumulator longer than its round trip
+// (single tiles at the window's edge are one k-step).
+// Warp roles: 0 producer (bulk copies), 1 MMA issuer, 2..9 epilogue (tensor
+// memory -> registers -> outputs).  Every wait is bounded and records
+// SK_ETIMEOUT.
 #include <string.h>
 
 #include <algorithm>
@@ -39,257 +45,213 @@
 
 namespace {
 
-constexpr int NB = SK_TC_MAPS;         // maps per item (MMA N)
-constexpr int RG = SK_BELT_G;          // rings per item
-constexpr int SO = 128 / RG;           // output pixels per ring per segment (8)
-constexpr int NSEG = 256 / NB;         // segments per item (two accumulators each in 512 columns)
-constexpr int SEGW = SO * NSEG;        // output pixels per ring per item (128)
+constexpr int RG = SK_BELT_G;          // output rings per item
+constexpr int SO = 128 / RG;           // output pixels per ring per segment
 static_assert(RG * SO == 128, "M must be 128");
-static_assert(SEGW == SK_TC_SEGW, "item width");
+constexpr int NEPI = 8;                // epilogue warps
+constexpr int NT = 32 * (2 + NEPI);
+constexpr unsigned long long LIMIT = 2000000000ull;
 
-struct Lay {
-    uint32_t a_bytes, x_bytes, w_off, stage;
+// One pipeline stage: A (hi then lo, K x 512 bytes each, room for kmax), then three
+// hi and three lo plane slots of `slot` bytes (nn + kmax/8 rows of 16 bytes).
+struct Stage {
+    uint32_t a_bytes, slot, bytes;
 };
-
-__host__ __device__ inline Lay layout(const TcGeom &g, int wpm) {
-    Lay l;
-    l.a_bytes = (uint32_t)g.ka * 128 * 128;
-    l.x_bytes = (uint32_t)g.xa * NB * 128;
-    l.w_off = 2 * l.a_bytes + 2 * l.x_bytes;
-    l.stage = (l.w_off + (uint32_t)RG * wpm * 4 + 1023) & ~1023u;
-    return l;
+__host__ __device__ inline Stage stage_of(int kmax, int nn) {
+    Stage s;
+    s.a_bytes = 2u * (uint32_t)kmax * 512u;
+    s.slot = (uint32_t)(nn + kmax / 8) * 16u;
+    s.bytes = (s.a_bytes + 6u * s.slot + 1023u) & ~1023u;
+    return s;
 }
 
-constexpr int NT = 512;                 // threads per block: 15 builder warps + 1 MMA warp
-constexpr int NBLD = NT - 32;           // builder threads
-constexpr int XQ = 2;                   // 16-byte map chunks per builder thread per strip
-constexpr int WQ = 2;                   // weight-row values per builder thread per strip
-
-// Loads (into registers) of one strip: the maps' pixels and the 16 weight rows.
-struct Prefetch {
-    float4 x[XQ];
-    float w[WQ];
-};
-
-__device__ __forceinline__ void load_strip(Prefetch &pf, const JobDesc &J, const TcGeom &tg, int grp, int ri,
-                                           int j0, int b0, int nmaps) {
-    const int t = threadIdx.x;
-    const int nq = tg.xl >> 2;
-    const int emin4 = J.EMIN - tg.off4;
-    const long long st_i = J.rings[ri].start;
-#pragma unroll
-    for (int u = 0; u < XQ; ++u) {
-        const int q = t + u * NBLD;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q < NB * nq) {
-            const int m = q / nq, c4 = q - m * nq;
-            int pos = (j0 + emin4 + 4 * c4) % J.n4;
-            if (pos < 0) pos += J.n4;
-            if (m < nmaps) v = __ldg(reinterpret_cast<const float4 *>(J.x + (long long)(b0 + m) * J.stride + st_i + pos));
-        }
-        pf.x[u] = v;
-    }
-    const int R2 = 2 * J.HM + 1;
-#pragma unroll
-    for (int u = 0; u < WQ; ++u) {
-        const int q = t + u * NBLD;
-        float v = 0.0f;
-        if (q < RG * J.WPM) {
-            const int r = q / J.WPM, c = q - r * J.WPM;
-            const int rb = grp * RG + r, d = ri - (J.b_lo + rb);
-            if (rb < J.nb && d >= -J.HM && d <= J.HM) v = __ldg(J.bw + ((size_t)rb * R2 + d + J.HM) * J.WPM + c);
-        }
-        pf.w[u] = v;
-    }
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status) {
+    if (*abort_flag) return false;
+    if (tc::mbar_wait(bar, parity, LIMIT)) return true;
+    *abort_flag = 1;
+    atomicCAS(status, 0, SK_ETIMEOUT);
+    return false;
 }
 
-__device__ __forceinline__ void bld_sync() { asm volatile("bar.sync 1, %0;" ::"r"(NBLD) : "memory"); }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__global__ void __launch_bounds__(NT, 1)
-k_belt_tc(const __grid_constant__ JobsArg A, const TcGeom tg) {
+__global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArgs T) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[2];      // builders -> MMA warp: operands of a stage ready
-    __shared__ __align__(8) uint64_t empty_bar[2];     // MMA completion -> builders: stage free
+    __shared__ __align__(8) uint64_t full_bar[SK_TC_MAX_STAGES];    // copies of a stage landed
+    __shared__ __align__(8) uint64_t empty_bar[SK_TC_MAX_STAGES];   // MMAs reading a stage done
+    __shared__ __align__(8) uint64_t tfull_bar[2];                  // a tile's partial sums complete
+    __shared__ __align__(8) uint64_t tempty_bar[2];                 // the epilogue has read them
+    __shared__ __align__(8) uint64_t drain_bar;                     // teardown
     __shared__ uint32_t tslot;
-    __shared__ int abort_flag;
+    __shared__ int abort_s;
+    volatile int *abort_flag = &abort_s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const bool mma_warp = warp == NT / 32 - 1;
+    const int S = T.nstages;
+    const Stage L = stage_of(T.kmax, T.nn);
+    const int per_g = T.batch * T.nblk;
 
     if (warp == 0) tc::tmem_alloc(&tslot, 512);
     if (t == 0) {
-        for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(tc::smem_u32(&full_bar[s]), NBLD / 32);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(tc::smem_u32(&full_bar[s]), 1);
             tc::mbar_init(tc::smem_u32(&empty_bar[s]), 1);
         }
-        abort_flag = 0;
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(tc::smem_u32(&tfull_bar[a]), 1);
+            tc::mbar_init(tc::smem_u32(&tempty_bar[a]), NEPI);
+        }
+        tc::mbar_init(tc::smem_u32(&drain_bar), 1);
+        abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tslot;
-    const uint32_t idesc = tc::idesc_tf32(128, NB);
-    const unsigned long long LIMIT = 2000000000ull;
 
-    uint32_t gi = 0;                                   // strips so far (stage, phase)
-    for (int f = blockIdx.x; f < A.total && !abort_flag; f += gridDim.x) {
-        const JobDesc &J = A.j[sk_find_job(A, f)];
-        const Lay L = layout(tg, J.WPM);
-        const int local = f - J.flat_base;
-        const int mb = local / J.n_items;
-        const int4 it = J.items[local - mb * J.n_items];
-        const int grp = it.x, j0 = it.y * SEGW;
-        const int b0 = mb * NB, nmaps = min(NB, J.batch - b0);
-        const int2 gr = J.bgrp[grp];
-        const int nstrips = gr.y - gr.x + 1;
-        const int n4 = J.n4;
-        const uint32_t gi0 = gi;
-
-        if (!mma_warp) {
-            // ---------------- builders ----------------
-            Prefetch pf;
-            load_strip(pf, J, tg, grp, gr.x, j0, b0, nmaps);
-            const int nq = tg.xl >> 2;
-            const int ach = tg.kt8 >> 2;                   // 16-byte chunks per weight-tile row
-            for (int i = 0; i < nstrips; ++i) {
-                const uint32_t g = gi0 + i;
-                const int st = (int)(g & 1);
-                unsigned char *a_hi = base + st * L.stage;
-                unsigned char *a_lo = a_hi + L.a_bytes;
-                unsigned char *x_hi = a_lo + L.a_bytes;
-                unsigned char *x_lo = x_hi + L.x_bytes;
-                float *wrow = reinterpret_cast<float *>(a_hi + L.w_off);
-                if (g >= 2 && !tc::mbar_wait(tc::smem_u32(&empty_bar[st]), ((g >> 1) - 1) & 1, LIMIT)) {
-                    abort_flag = 1;
-                    atomicCAS(A.status, 0, SK_ETIMEOUT);
-                }
-                bld_sync();                                // every builder decides on the same flag
-                if (abort_flag) break;
-#pragma unroll
-                for (int u = 0; u < WQ; ++u) {
-                    const int q = t + u * NBLD;
-                    if (q < RG * J.WPM) wrow[q] = pf.w[u];
-                }
-#pragma unroll
-                for (int u = 0; u < XQ; ++u) {
-                    const int q = t + u * NBLD;
-                    if (q < NB * nq) {
-                        const int m = q / nq, k = 4 * (q - m * nq);
-                        float4 hi, lo;
-                        tc::split_tf32(pf.x[u].x, hi.x, lo.x);
-                        tc::split_tf32(pf.x[u].y, hi.y, lo.y);
-                        tc::split_tf32(pf.x[u].z, hi.z, lo.z);
-                        tc::split_tf32(pf.x[u].w, hi.w, lo.w);
-                        const uint32_t off = (uint32_t)(k >> 5) * NB * 128 + tc::sw128_offset(m, k);
-                        *reinterpret_cast<float4 *>(x_hi + off) = hi;
-                        *reinterpret_cast<float4 *>(x_lo + off) = lo;
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
+                const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
+                const int j0 = pb * 8 * T.nn;
+                const int2 tr = T.trng[g];
+                const float4 *zb = T.Z + (size_t)b * T.nz * 4 * T.zrows;
+                for (int u = 0; u < tr.y; ++u, ++cnt) {
+                    const int4 tl = T.tiles[tr.x + u];            // (input ring, E0, K | flags, A offset in KB)
+                    const int s = (int)(cnt % (uint32_t)S);
+                    if (cnt >= (uint32_t)S &&
+                        !wait_or_abort(tc::smem_u32(&empty_bar[s]), ((cnt / S) - 1) & 1, abort_flag, T.status))
+                        break;
+                    const int K = tl.z & SK_TC_K_MASK;
+                    const uint32_t rbytes = (uint32_t)(T.nn + K / 8 - 1) * 16u;
+                    const int u0 = (j0 + tl.y - T.pbase) >> 2;    // 4-pixel row of the first column
+                    const int m0 = u0 >> 1;
+                    const float4 *zr = zb + (size_t)(tl.x - T.zi0) * 4 * T.zrows;
+                    unsigned char *sb = base + (size_t)s * L.bytes;
+                    const uint32_t bar = tc::smem_u32(&full_bar[s]);
+                    tc::mbar_expect_tx(bar, (uint32_t)K * 1024u + 4u * rbytes);
+                    tc::bulk_g2s(tc::smem_u32(sb), T.A + (size_t)tl.w * 1024, (uint32_t)K * 1024u, bar);
+                    for (int h = 0; h < 2; ++h) {                 // hi, lo parts
+                        const float4 *pe = zr + (size_t)(2 * h) * T.zrows, *po = pe + T.zrows;
+                        const uint32_t sl = tc::smem_u32(sb + L.a_bytes + 3u * (uint32_t)h * L.slot);
+                        if (!(u0 & 1)) {                          // k-steps start on an even row
+                            tc::bulk_g2s(sl, pe + m0, rbytes, bar);
+                            tc::bulk_g2s(sl + L.slot, po + m0, rbytes, bar);
+                        } else {                                  // on an odd row: odd, then even one on
+                            tc::bulk_g2s(sl + L.slot, po + m0, rbytes, bar);
+                            tc::bulk_g2s(sl + 2u * L.slot, pe + m0 + 1, rbytes, bar);
+                        }
                     }
                 }
-                if (i + 1 < nstrips) load_strip(pf, J, tg, grp, gr.x + i + 1, j0, b0, nmaps);
-                bld_sync();                                // weight rows visible to all builders
-                // A: 16-byte chunk (row, k..k+3), row = (r, n): w_r[k + u - n - off4]
-                for (int q = t; q < 128 * ach; q += NBLD) {
-                    const int row = q / ach, k = 4 * (q - row * ach);
-                    const int r = row >> 3, n = row & 7;
-                    const float *wr = wrow + r * J.WPM;
-                    float v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = k + u - n - tg.off4;
-                        v[u] = (c >= 0 && c < J.WPM) ? wr[c] : 0.0f;
-                    }
-                    float4 hi, lo;
-                    tc::split_tf32(v[0], hi.x, lo.x);
-                    tc::split_tf32(v[1], hi.y, lo.y);
-                    tc::split_tf32(v[2], hi.z, lo.z);
-                    tc::split_tf32(v[3], hi.w, lo.w);
-                    const uint32_t off = (uint32_t)(k >> 5) * 128 * 128 + tc::sw128_offset(row, k);
-                    *reinterpret_cast<float4 *>(a_hi + off) = hi;
-                    *reinterpret_cast<float4 *>(a_lo + off) = lo;
-                }
-                tc::fence_smem_to_async();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tc::smem_u32(&full_bar[st]));
             }
-        } else if (lane == 0) {
-            // ---------------- MMA issuer ----------------
-            for (int i = 0; i < nstrips; ++i) {
-                const uint32_t g = gi0 + i;
-                const int st = (int)(g & 1);
-                if (!tc::mbar_wait(tc::smem_u32(&full_bar[st]), (g >> 1) & 1, LIMIT)) {
-                    abort_flag = 1;
-                    atomicCAS(A.status, 0, SK_ETIMEOUT);
+            // copies still in flight land before the block exits (bounded)
+            for (uint32_t c = cnt > (uint32_t)S ? cnt - S : 0; c < cnt; ++c)
+                tc::mbar_wait(tc::smem_u32(&full_bar[c % S]), (c / S) & 1, LIMIT);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t cnt = 0, ccnt = 0;                           // tiles, chunks
+            const uint32_t idesc = tc::idesc_tf32(128, T.nn);
+            for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
+                const int g = f / per_g, rem = f - g * per_g, pb = rem % T.nblk;
+                const int j0 = pb * 8 * T.nn;
+                const int2 tr = T.trng[g];
+                for (int u = 0; u < tr.y; ++u, ++cnt) {
+                    const int4 tl = T.tiles[tr.x + u];
+                    const int s = (int)(cnt % (uint32_t)S);
+                    const int ab = (int)(ccnt & 1);               // accumulator of this chunk
+                    const bool first = (tl.z & SK_TC_FIRST) != 0, last = (tl.z & SK_TC_LAST) != 0;
+                    if (first && ccnt >= 2 &&
+                        !wait_or_abort(tc::smem_u32(&tempty_bar[ab]), ((ccnt >> 1) - 1) & 1, abort_flag, T.status))
+                        break;
+                    if (!wait_or_abort(tc::smem_u32(&full_bar[s]), (cnt / S) & 1, abort_flag, T.status)) break;
+                    tc::fence_after_sync();
+                    const int K = tl.z & SK_TC_K_MASK;
+                    const int u0 = (j0 + tl.y - T.pbase) >> 2;
+                    const uint32_t sb = tc::smem_u32(base + (size_t)s * L.bytes);
+                    const uint32_t a_hi = sb, a_lo = sb + (uint32_t)K * 512u;
+                    const uint32_t b_hi = sb + L.a_bytes + ((u0 & 1) ? L.slot : 0u), b_lo = b_hi + 3u * L.slot;
+                    const uint32_t d = taddr + 256u * (uint32_t)ab;
+                    for (int q = 0; q < K / 8; ++q) {
+                        const uint64_t ah = tc::kmajor_desc(a_hi + 4096u * q, 2048, 128);
+                        const uint64_t al = tc::kmajor_desc(a_lo + 4096u * q, 2048, 128);
+                        const uint64_t bh = tc::kmajor_desc(b_hi + 16u * q, L.slot, 128);
+                        const uint64_t bl = tc::kmajor_desc(b_lo + 16u * q, L.slot, 128);
+                        tc::mma_tf32(d, ah, bh, idesc, (first && q == 0) ? 0 : 1);
+                        tc::mma_tf32(d, ah, bl, idesc, 1);
+                        tc::mma_tf32(d, al, bh, idesc, 1);
+                    }
+                    tc::mma_commit(tc::smem_u32(&empty_bar[s]));
+                    if (last) {
+                        tc::mma_commit(tc::smem_u32(&tfull_bar[ab]));
+                        ++ccnt;
+                    }
                 }
-                if (abort_flag) break;
+            }
+            // every MMA this thread issued has completed before tensor memory is released
+            tc::mma_commit(tc::smem_u32(&drain_bar));
+            tc::mbar_wait(tc::smem_u32(&drain_bar), 0, LIMIT);
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        // warp w reads lane quadrant w % 4 (rows 32 (w % 4) ..) and the 16-column chunks
+        // 16 half, 16 half + 32, ...: up to eight chunks of partial sums held in registers
+        constexpr int CH = 8;
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int row = quad * 32 + lane, r = row / SO, n = row - r * SO;
+        const int nch = (T.nn - 16 * half + 31) / 32;
+        uint32_t ccnt = 0;
+        for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
+            const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
+            const int j0 = pb * 8 * T.nn;
+            const int2 tr = T.trng[g];
+            float acc[CH][16];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+                for (int m = 0; m < 16; ++m) acc[c][m] = 0.0f;
+            bool ok = true;
+            for (int u = 0; u < tr.y; ++u) {
+                if (!(T.tiles[tr.x + u].z & SK_TC_LAST)) continue;
+                const int ab = (int)(ccnt & 1);
+                if (!wait_or_abort(tc::smem_u32(&tfull_bar[ab]), (ccnt >> 1) & 1, abort_flag, T.status)) {
+                    ok = false;
+                    break;
+                }
                 tc::fence_after_sync();
-                unsigned char *a_hi = base + st * L.stage;
-                const uint64_t dah0 = tc::sw128_desc(tc::smem_u32(a_hi));
-                const uint64_t dal0 = tc::sw128_desc(tc::smem_u32(a_hi + L.a_bytes));
-                const uint64_t dxh0 = tc::sw128_desc(tc::smem_u32(a_hi + 2 * L.a_bytes));
-                const uint64_t dxl0 = tc::sw128_desc(tc::smem_u32(a_hi + 2 * L.a_bytes + L.x_bytes));
-                for (int s = 0; s < NSEG; ++s) {
-                    const uint32_t d_big = taddr + (uint32_t)(s * NB);
-                    const uint32_t d_small = taddr + 256u + (uint32_t)(s * NB);
-                    for (int tk = 0; tk < tg.kt8 / 8; ++tk) {
-                        const int ka = 8 * tk, kx = 8 * s + 8 * tk;
-                        // the start address is the descriptor's low field (in 16-byte units)
-                        const uint64_t ao = ((uint32_t)(ka >> 5) * 128 * 128 + (uint32_t)(ka & 31) * 4) >> 4;
-                        const uint64_t xo = ((uint32_t)(kx >> 5) * NB * 128 + (uint32_t)(kx & 31) * 4) >> 4;
-                        const int acc = (i > 0 || tk > 0) ? 1 : 0;
-                        tc::mma_tf32(d_big, dah0 + ao, dxh0 + xo, idesc, acc);
-                        tc::mma_tf32(d_small, dah0 + ao, dxl0 + xo, idesc, acc);
-                        tc::mma_tf32(d_small, dal0 + ao, dxh0 + xo, idesc, 1);
-                    }
-                }
-                tc::mma_commit(tc::smem_u32(&empty_bar[st]));
-            }
-        }
-        gi = gi0 + (uint32_t)nstrips;
-        __syncthreads();
-        if (abort_flag) break;
-        // all MMAs of the item are done once the last commit has landed
-        const uint32_t last = gi - 1;
-        if (!tc::mbar_wait(tc::smem_u32(&empty_bar[last & 1]), (last >> 1) & 1, LIMIT)) {
-            if (t == 0) { abort_flag = 1; atomicCAS(A.status, 0, SK_ETIMEOUT); }
-        }
-        __syncthreads();
-        if (abort_flag) break;
-        tc::fence_after_sync();
-        {
-            // warp w reads lane quadrant w % 4 (rows 32 (w % 4) ..) of segments s = w / 4, w / 4 + 4, ...
-            const int quad = warp & 3;
-            const int row = quad * 32 + lane;
-            const int r = row / SO, n = row - r * SO;
-            const int rb = grp * RG + r;
-            const bool valid = rb < J.nb;
-            float *yr = J.y + (long long)b0 * J.stride + (valid ? J.rings[J.b_lo + rb].start : 0);
-            for (int s = warp >> 2; s < NSEG; s += NT / 128) {
-                float v[16], w[16];
-                for (int h = 0; h < NB / 16; ++h) {
-                    const uint32_t lane_base = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * NB + 16 * h);
-                    tc::tmem_ld16(lane_base, v);
-                    tc::tmem_ld16(lane_base + 256u, w);
-                    const int j = j0 + s * SO + n;
-                    if (valid && j < n4) {
+                const uint32_t lane_base = taddr + ((uint32_t)(quad * 32) << 16) + 256u * (uint32_t)ab;
 #pragma unroll
-                        for (int m = 0; m < 16; ++m)
-                            if (16 * h + m < nmaps) yr[(long long)(16 * h + m) * J.stride + j] = v[m] + w[m];
+                for (int c = 0; c < CH; ++c) {
+                    if (c < nch) {
+                        float v[16];
+                        tc::tmem_ld16(lane_base + (uint32_t)(16 * half + 32 * c), v);
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) acc[c][m] += v[m];
+                    }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive1(tc::smem_u32(&tempty_bar[ab]));
+                ++ccnt;
+            }
+            if (!ok) break;
+            const int rb = g * RG + r;
+            if (rb < T.nb) {
+                float *yr = T.y + (long long)b * T.stride + T.rings[T.b_lo + rb].start;
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    if (c < nch) {
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) {
+                            const int j = j0 + SO * (16 * half + 32 * c + m) + n;
+                            if (j < T.n4) yr[j] = acc[c][m];
+                        }
                     }
                 }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-    }
-    // leave no MMA in flight before releasing tensor memory (bounded)
-    if (gi > 0) {
-        const uint32_t last = gi - 1;
-        tc::mbar_wait(tc::smem_u32(&empty_bar[last & 1]), (last >> 1) & 1, LIMIT);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -299,29 +261,116 @@ k_belt_tc(const __grid_constant__ JobsArg A, const TcGeom tg) {
     }
 }
 
-}  // namespace
-
-bool sk_tc_geometry(int wpm, int emin, int n4, TcGeom *g) {
-    const int emin4 = emin >= 0 ? (emin & ~3) : -(((-emin) + 3) & ~3);
-    g->off4 = emin - emin4;
-    const int kt = wpm + (SO - 1) + g->off4;
-    g->kt8 = (kt + 7) & ~7;
-    g->ka = (g->kt8 + 31) / 32;
-    g->xl = ((8 * (NSEG - 1) + g->kt8) + 31) & ~31;
-    g->xa = g->xl / 32;
-    if (g->ka > 2 || n4 % SEGW) return false;
-    if (NB * (g->xl / 4) > XQ * NBLD || RG * wpm > WQ * NBLD) return false;   // per-thread prefetch slots
-    return sk_tc_smem(*g, wpm) <= 220 * 1024;
+// One block per tile: A_i[(o, n)][k] = w(o, i, k - n + E0) for the group's rings,
+// zero outside each ring's window, split into TF32 hi and lo parts and written in
+// the no-swizzle K-major image the MMA reads (kmajor128_offset; lo K x 512 bytes
+// after hi).  The weight is the FP32 belt's (pair_weight of the same half-angle).
+__global__ void k_tc_tiles(const __grid_constant__ TcTileArgs T, const int *gate) {
+    if (gate && !*gate) return;                      // table unchanged: the tiles stand
+    const int tile = blockIdx.x;
+    const int4 tl = T.tiles[tile];
+    const int g = T.tile_group[tile];
+    const int K = tl.z & SK_TC_K_MASK;
+    unsigned char *hi = T.A + (size_t)tl.w * 1024, *lo = hi + (size_t)K * 512;
+    const double half_step = SK_PI / (2.0 * (double)T.n4);
+    for (int idx = threadIdx.x; idx < 128 * K; idx += blockDim.x) {
+        const int row = idx / K, k = idx - row * K;
+        const int r = row / SO, n = row - r * SO;
+        const int rb = g * RG + r, e = k - n + tl.y;
+        float v = 0.0f;
+        if (rb < T.nb) {
+            const int ro = T.b_lo + rb;
+            const int p0 = T.pair_off[ro], p1 = T.pair_off[ro + 1];
+            const int p = p0 + (tl.x - T.pairs[p0].ri);
+            if (p >= p0 && p < p1) {
+                const PairInfo P = T.pairs[p];
+                const int s_o = T.rings[ro].s;
+                const int ec = (s_o + 1 - P.s_i) >> 1;
+                if (e >= ec - P.W && e <= ec + P.W) {
+                    const float x = (float)((double)(2 * e + P.s_i - s_o) * half_step);
+                    v = pair_weight(x, P.A, P.B, T.kp, T.tab);
+                }
+            }
+        }
+        float h, l;
+        tc::split_tf32(v, h, l);
+        *reinterpret_cast<float *>(hi + tc::kmajor128_offset(row, k)) = h;
+        *reinterpret_cast<float *>(lo + tc::kmajor128_offset(row, k)) = l;
+    }
 }
 
-size_t sk_tc_smem(const TcGeom &g, int wpm) { return 1024 + 2 * (size_t)layout(g, wpm).stage; }
+// Planes of the maps' belt input rings: for map b, ring zi0 + ri and row m, the
+// pixels pbase + 8m .. + 7 (wrapped around the ring) split into TF32 hi and lo
+// parts, stored as four planes of float4 rows: hi even (first four pixels), hi odd,
+// lo even, lo odd.
+__global__ void k_tc_planes(const float *__restrict__ x, long long stride, const RingDev *__restrict__ rings, int zi0,
+                            int nz, int zrows, int pbase, int n4, long long total, float4 *__restrict__ Z) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(idx % zrows);
+        const long long rest = idx / zrows;
+        const int ri = (int)(rest % nz);
+        const long long b = rest / nz;
+        const float *xr = x + b * stride + rings[zi0 + ri].start;
+        int p = (pbase + 8 * m) % n4;
+        if (p < 0) p += n4;
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            int q = p + u;
+            if (q >= n4) q -= n4;
+            v[u] = xr[q];
+        }
+        float4 he, ho, le, lo;
+        tc::split_tf32(v[0], he.x, le.x);
+        tc::split_tf32(v[1], he.y, le.y);
+        tc::split_tf32(v[2], he.z, le.z);
+        tc::split_tf32(v[3], he.w, le.w);
+        tc::split_tf32(v[4], ho.x, lo.x);
+        tc::split_tf32(v[5], ho.y, lo.y);
+        tc::split_tf32(v[6], ho.z, lo.z);
+        tc::split_tf32(v[7], ho.w, lo.w);
+        float4 *zr = Z + (size_t)(b * nz + ri) * 4 * zrows;
+        zr[m] = he;
+        zr[zrows + m] = ho;
+        zr[2 * (size_t)zrows + m] = le;
+        zr[3 * (size_t)zrows + m] = lo;
+    }
+}
 
-cudaError_t sk_launch_belt_tc(const JobsArg &a, const TcGeom &g, int wpm_max, int grid, cudaStream_t st) {
-    if (a.total <= 0) return cudaSuccess;
+}  // namespace
+
+int sk_tc_stages(int kmax, int nn, size_t *smem) {
+    const Stage L = stage_of(kmax, nn);
+    const size_t avail = (size_t)220 * 1024 - 1024;
+    int S = (int)std::min<size_t>(SK_TC_MAX_STAGES, avail / L.bytes);
+    if (S < 2) return 0;
     // at least 120 KB so that one block holds an SM (it allocates all 512 tensor-memory columns)
-    const size_t smem = std::max(sk_tc_smem(g, wpm_max), (size_t)120 * 1024);
+    if (smem) *smem = std::max((size_t)1024 + (size_t)S * L.bytes, (size_t)120 * 1024);
+    return S;
+}
+
+cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st) {
+    if (a.total <= 0) return cudaSuccess;
+    size_t smem = 0;
+    if (sk_tc_stages(a.kmax, a.nn, &smem) != a.nstages) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_belt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_belt_tc<<<grid, NT, smem, st>>>(a, g);
+    k_belt_tc<<<grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st, const int *gate) {
+    if (n_tiles <= 0) return cudaSuccess;
+    k_tc_tiles<<<n_tiles, 256, 0, st>>>(a, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
+                                int zrows, int pbase, int n4, float4 *Z, int sms, cudaStream_t st) {
+    const long long total = (long long)batch * nz * zrows;
+    if (total <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((total + 255) / 256, (long long)sms * 16);
+    k_tc_planes<<<(unsigned)blocks, 256, 0, st>>>(x, stride, rings, zi0, nz, zrows, pbase, n4, total, Z);
     return cudaGetLastError();
 }

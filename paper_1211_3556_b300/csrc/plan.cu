@@ -87,11 +87,14 @@ void sk_plan_free(sk_kern *k) {
     k->capw_len = 0;
     cudaFree(k->d_items_gen); k->d_items_gen = nullptr;
     cudaFree(k->d_ring_path); k->d_ring_path = nullptr;
-    cudaFree(k->d_brng); k->d_brng = nullptr;
     cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
     cudaFree(k->d_bpr); k->d_bpr = nullptr;
     cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
-    cudaFree(k->d_items_tc); k->d_items_tc = nullptr;
+    cudaFree(k->d_tct); k->d_tct = nullptr;
+    cudaFree(k->d_tcg); k->d_tcg = nullptr;
+    cudaFree(k->d_tcr); k->d_tcr = nullptr;
+    cudaFree(k->d_tca); k->d_tca = nullptr;
+    k->h_tct.clear();
     k->tc_ok = false;
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int v = 0; v < 2; ++v) {
@@ -274,8 +277,6 @@ int sk_plan_build(sk_kern *k) {
         const int R2 = 2 * HM + 1;
         k->ngroups = (k->nb + SK_BELT_G - 1) / SK_BELT_G;
         const int nb_pad = k->ngroups * SK_BELT_G;
-        // rows on a common offset grid e = EMIN + c: chunk c4 = (e - EMIN) / 4
-        std::vector<int2> rng((size_t)nb_pad * R2, make_int2(1, 0));
         int EMIN = 1 << 30, EMAX = -(1 << 30);
         for (int rb = 0; rb < k->nb; ++rb) {
             const int r = b_lo + rb;
@@ -294,7 +295,6 @@ int sk_plan_build(sk_kern *k) {
                 const PairInfo &P = pairs[p];
                 const int d = P.ri - r;
                 const int ec = (R[r].s + 1 - P.s_i) >> 1;
-                rng[(size_t)rb * R2 + d + HM] = make_int2((ec - P.W - EMIN) >> 2, (ec + P.W - EMIN) >> 2);
                 ew[(size_t)rb * R2 + d + HM] = make_int2(ec - P.W, ec + P.W);
             }
         }
@@ -335,18 +335,82 @@ int sk_plan_build(sk_kern *k) {
                         pr[((size_t)gi * smax + si) * SK_BELT_WARPS + w] = make_int2(lo - EMIN, (hi - lo + 4) / 4);
                 }
         int rc;
-        if ((rc = upload(rng, &k->d_brng))) return rc;
         if ((rc = upload(grp, &k->d_bgrp))) return rc;
         if ((rc = upload(pr, &k->d_bpr))) return rc;
         k->belt_P = belt_cost_p(n4);
         if ((rc = sk_plan_rebuild_belt_items(k))) return rc;
-        k->tc_ok = sk_tc_geometry(k->WPM, k->EMIN, n4, &k->tcg);
-        if (k->tc_ok) {
-            std::vector<int4> ti;
-            for (int gi = 0; gi < k->ngroups; ++gi)
-                for (int sb = 0; sb < n4 / SK_TC_SEGW; ++sb) ti.push_back(make_int4(gi, sb, 0, 0));
-            k->n_items_tc = (int)ti.size();
-            if ((rc = upload(ti, &k->d_items_tc))) return rc;
+        // tensor-core belt: one tile per (group, input ring) with any window; E0 = the
+        // union's first offset rounded down to a multiple of 4, K covers the union plus
+        // the 7 extra columns of a segment's 8 output pixels, rounded up to 8
+        {
+            std::vector<int4> tl;
+            std::vector<int> tg;
+            std::vector<int2> tr(k->ngroups);
+            long long kb = 0;
+            int kmax = 0, e0min = 1 << 30, e0max = -(1 << 30), zi1 = 0;
+            for (int gi = 0; gi < k->ngroups; ++gi) {
+                const int first = (int)tl.size();
+                for (int i = grp[gi].x; i <= grp[gi].y; ++i) {
+                    int lo = 1 << 30, hi = -(1 << 30);
+                    for (int w = 0; w < SK_BELT_G; ++w) {
+                        const int rb = gi * SK_BELT_G + w, d = i - (b_lo + rb);
+                        if (rb >= k->nb || d < -HM || d > HM) continue;
+                        const int2 e = ew[(size_t)rb * R2 + d + HM];
+                        if (e.x > e.y) continue;
+                        lo = std::min(lo, e.x);
+                        hi = std::max(hi, e.y);
+                    }
+                    if (lo > hi) continue;
+                    const int E0 = lo >= 0 ? (lo & ~3) : -(((-lo) + 3) & ~3);
+                    const int K = (hi - E0 + 8 + 7) & ~7;
+                    tl.push_back(make_int4(i, E0, K, (int)std::min<long long>(kb, 1 << 30)));
+                    tg.push_back(gi);
+                    kb += K;
+                    kmax = std::max(kmax, K);
+                    e0min = std::min(e0min, E0);
+                    e0max = std::max(e0max, E0);
+                    zi1 = std::max(zi1, i);
+                }
+                tr[gi] = make_int2(first, (int)tl.size() - first);
+                // chunks of consecutive tiles accumulated together in tensor memory
+                int ks = 0;
+                for (int u = first; u < (int)tl.size(); ++u) {
+                    if (ks == 0) tl[u].z |= SK_TC_FIRST;
+                    ks += (tl[u].z & SK_TC_K_MASK) / 8;
+                    if (ks >= SK_TC_CHUNK_KSTEPS || u + 1 == (int)tl.size()) {
+                        tl[u].z |= SK_TC_LAST;
+                        ks = 0;
+                    }
+                }
+            }
+            const int nn = std::min(256, (n4 / 8) & ~15);
+            k->tc_ok = false;
+            if (nn >= 16 && kmax <= 64 && kb < (1 << 30) && !tl.empty()) {
+                k->tc_nn = nn;
+                k->tc_nblk = (n4 + 8 * nn - 1) / (8 * nn);
+                k->tc_kmax = kmax;
+                k->tc_pbase = e0min >= 0 ? (e0min & ~7) : -(((-e0min) + 7) & ~7);
+                k->tc_zi0 = grp[0].x;
+                k->tc_nz = zi1 - grp[0].x + 1;
+                k->tc_zrows = (8 * nn * (k->tc_nblk - 1) + e0max - k->tc_pbase) / 8 + nn + kmax / 8 + 2;
+                k->tc_stages = sk_tc_stages(kmax, nn, nullptr);
+                k->tca_kb = kb;
+                // every plane row an item copies lies inside its ring's planes
+                bool rows_ok = true;
+                for (const int4 &t4 : tl)
+                    for (int pb = 0; pb < k->tc_nblk; pb += std::max(1, k->tc_nblk - 1)) {
+                        const int u0 = (8 * nn * pb + t4.y - k->tc_pbase) >> 2;
+                        const int last = (u0 >> 1) + (u0 & 1) + nn + (t4.z & SK_TC_K_MASK) / 8 - 2;
+                        if (u0 < 0 || ((8 * nn * pb + t4.y - k->tc_pbase) & 3) || last >= k->tc_zrows) rows_ok = false;
+                    }
+                if (k->tc_stages >= 2 && rows_ok) {
+                    k->h_tct = tl;
+                    if ((rc = upload(tl, &k->d_tct))) return rc;
+                    if ((rc = upload(tg, &k->d_tcg))) return rc;
+                    if ((rc = upload(tr, &k->d_tcr))) return rc;
+                    k->tc_ok = true;
+                }
+            }
         }
     }
 
@@ -577,10 +641,9 @@ int sk_plan_bands(sk_kern *k) {
 
 size_t sk_plan_workspace_bytes(const sk_kern *k) {
     if (!k->plan_ok || k->nb == 0) return 0;
-    // the larger of the two weight layouts: rows (tensor-core form) and ring pairs (FP32 form)
-    const size_t rows = (size_t)k->ngroups * SK_BELT_G * (2 * k->HM + 1) * k->WPM * sizeof(float);
+    // the FP32 belt's ring-pair rows (when the operator does not store them)
     const size_t pairs = (size_t)k->ngroups * k->smax * SK_BELT_WARPS * k->WPM * sizeof(float2);
-    return (std::max(rows, pairs) + 255) & ~(size_t)255;
+    return (pairs + 255) & ~(size_t)255;
 }
 
 size_t sk_sym_bytes(const sk_kern *k, long long batch) {
@@ -626,8 +689,7 @@ JobDesc belt_desc(const SkJob &jb, float *w) {
     JobDesc d = base_desc(jb);
     d.b_lo = k->b_lo; d.nb = k->nb; d.HM = k->HM; d.WPM = k->WPM;
     d.EMIN = k->EMIN; d.EMAX = k->EMAX;
-    d.brng = k->d_brng; d.bgrp = k->d_bgrp;
-    d.bw = w;
+    d.bgrp = k->d_bgrp;
     d.smax = k->smax; d.bpr = k->d_bpr; d.bwp = reinterpret_cast<const float2 *>(w);
     return d;
 }
@@ -706,8 +768,60 @@ int sk_beltw_build(sk_kern *k, cudaStream_t st, const int *gate) {
     return SK_OK;
 }
 
+int sk_tca_build(sk_kern *k, cudaStream_t st, const int *gate) {
+    if (!k->tc_ok) return SK_OK;
+    if (!k->d_tca) {
+        if (gate) return SK_OK;                     // built on first use, from the table then
+        if (cudaMalloc(&k->d_tca, (size_t)k->tca_kb * 1024) != cudaSuccess) {
+            cudaGetLastError();
+            k->d_tca = nullptr;                     // the tensor path runs the FP32 belt
+            return SK_OK;
+        }
+    }
+    TcTileArgs a;
+    memset(&a, 0, sizeof a);
+    a.tiles = k->d_tct;
+    a.tile_group = k->d_tcg;
+    a.A = k->d_tca;
+    a.rings = k->g->d_rings;
+    a.pair_off = k->d_pair_off;
+    a.pairs = k->d_pairs;
+    a.kp = k->kp;
+    a.tab = k->d_tab;
+    a.b_lo = k->b_lo;
+    a.nb = k->nb;
+    a.n4 = (int)(4 * k->g->nside);
+    SK_CU(sk_launch_tc_tiles(a, (int)k->h_tct.size(), st, gate));
+    return SK_OK;
+}
+
+static int tc_workspace(sk_ctx *ctx, size_t bytes, void **out) {
+    if (bytes > ctx->tcz_bytes) {
+        if (ctx->tcz) cudaFree(ctx->tcz);           // cudaFree waits for work using it
+        ctx->tcz = nullptr;
+        ctx->tcz_bytes = 0;
+        SK_CU(cudaMalloc(&ctx->tcz, bytes));
+        ctx->tcz_bytes = bytes;
+    }
+    *out = ctx->tcz;
+    return SK_OK;
+}
+
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
-    // belt weight rows first: stored with the operator for the FP32 belt, else one pre-pass
+    // jobs whose belt runs on the tensor cores (their A tiles are built on first use)
+    std::vector<char> use_tc(n, 0);
+    if (path == SK_PATH_TENSOR)
+        for (int i = 0; i < n; ++i) {
+            sk_kern *k = const_cast<sk_kern *>(jobs[i].k);
+            if (!k->plan_ok || k->nb == 0 || !k->tc_ok || jobs[i].batch == 0) continue;
+            if (!k->d_tca) {
+                int rc = sk_tca_build(k, st);
+                if (rc) return rc;
+            }
+            use_tc[i] = k->d_tca != nullptr;
+        }
+
+    // belt weight rows of the FP32 belt: stored with the operator, else one pre-pass
     // per job into the workspace, shared by all its maps
     std::vector<float *> wrows(n, nullptr);
     char *wp = (char *)ws;
@@ -717,27 +831,22 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
             wrows[i] = (float *)wp;
             wp += sk_plan_workspace_bytes(k);
-            const bool tensor = path == SK_PATH_TENSOR && k->tc_ok;
-            if (!tensor && k->d_beltw) {
+            if (use_tc[i]) continue;
+            if (k->d_beltw) {
                 wrows[i] = (float *)k->d_beltw;
                 continue;
             }
             if (!jobs[i].weights) continue;             // rows already in the workspace
             JobDesc d = belt_desc(jobs[i], nullptr);
             cudaEvent_t ev = sk_prof_begin(ctx, st);
-            if (tensor)
-                SK_CU(sk_launch_belt_weights(d, wrows[i], st));                 // rows
-            else
-            {
-                // ring pairs: the groups a ring subset runs (one or two ranges), or all
-                const SkItems *sub = jobs[i].sub;
-                if (!sub || sub->bg[0][1] < 0) {
-                    SK_CU(sk_launch_belt_pairs(d, 0, k->ngroups, (float2 *)wrows[i], st));
-                } else {
-                    for (int q = 0; q < 2; ++q)
-                        if (sub->bg[q][1] > sub->bg[q][0])
-                            SK_CU(sk_launch_belt_pairs(d, sub->bg[q][0], sub->bg[q][1], (float2 *)wrows[i], st));
-                }
+            // ring pairs: the groups a ring subset runs (one or two ranges), or all
+            const SkItems *sub = jobs[i].sub;
+            if (!sub || sub->bg[0][1] < 0) {
+                SK_CU(sk_launch_belt_pairs(d, 0, k->ngroups, (float2 *)wrows[i], st));
+            } else {
+                for (int q = 0; q < 2; ++q)
+                    if (sub->bg[q][1] > sub->bg[q][0])
+                        SK_CU(sk_launch_belt_pairs(d, sub->bg[q][0], sub->bg[q][1], (float2 *)wrows[i], st));
             }
             sk_prof_end(ctx, "belt_weights", ev, st);
         }
@@ -798,22 +907,45 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         return flush();
     }
 
-    // batched tensor-core belt: one launch per job (its tile geometry is per operator)
+    // tensor-core belt: per job, the maps' planes, then one launch over all its maps
     if (path == SK_PATH_TENSOR) {
         for (int i = 0; i < n; ++i) {
+            if (!use_tc[i]) continue;
             const sk_kern *k = jobs[i].k;
-            if (!k->plan_ok || k->nb == 0 || !k->tc_ok || jobs[i].batch == 0) continue;
-            Batcher b;
-            JobDesc d = belt_desc(jobs[i], wrows[i]);
-            d.items = k->d_items_tc;
-            d.n_items = k->n_items_tc;
-            d.flat_base = 0;
-            b.a.j[0] = d;
-            b.a.n_jobs = 1;
-            b.a.total = k->n_items_tc * (int)((jobs[i].batch + SK_TC_MAPS - 1) / SK_TC_MAPS);
-            b.a.status = ctx->d_status;
+            const size_t zbytes = (size_t)jobs[i].batch * k->tc_nz * 4 * k->tc_zrows * sizeof(float4);
+            void *z = nullptr;
+            int rc = tc_workspace(ctx, zbytes, &z);
+            if (rc) return rc;
             cudaEvent_t ev = sk_prof_begin(ctx, st);
-            SK_CU(sk_launch_belt_tc(b.a, k->tcg, k->WPM, std::min(b.a.total, ctx->num_sms), st));
+            SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, k->tc_zi0,
+                                      k->tc_nz, k->tc_zrows, k->tc_pbase, (int)(4 * k->g->nside), (float4 *)z,
+                                      ctx->num_sms, st));
+            sk_prof_end(ctx, "tc_planes", ev, st);
+            TcArgs a;
+            memset(&a, 0, sizeof a);
+            a.rings = k->g->d_rings;
+            a.y = jobs[i].y;
+            a.stride = jobs[i].stride;
+            a.batch = (int)jobs[i].batch;
+            a.b_lo = k->b_lo;
+            a.nb = k->nb;
+            a.n4 = (int)(4 * k->g->nside);
+            a.tiles = k->d_tct;
+            a.trng = k->d_tcr;
+            a.A = k->d_tca;
+            a.Z = (const float4 *)z;
+            a.zi0 = k->tc_zi0;
+            a.nz = k->tc_nz;
+            a.zrows = k->tc_zrows;
+            a.pbase = k->tc_pbase;
+            a.nn = k->tc_nn;
+            a.nblk = k->tc_nblk;
+            a.kmax = k->tc_kmax;
+            a.nstages = k->tc_stages;
+            a.total = k->ngroups * (int)jobs[i].batch * k->tc_nblk;
+            a.status = ctx->d_status;
+            ev = sk_prof_begin(ctx, st);
+            SK_CU(sk_launch_belt_tc(a, std::min(a.total, ctx->num_sms), st));
             sk_prof_end(ctx, "conv_belt_tc", ev, st);
         }
     }
@@ -836,7 +968,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         for (int i = 0; i < n; ++i) {
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || k->belt_P != P || jobs[i].batch == 0) continue;
-            if (path == SK_PATH_TENSOR && k->tc_ok) continue;     // done on the tensor cores
+            if (use_tc[i]) continue;                              // done on the tensor cores
             const SkItems *sub = jobs[i].sub;
             const int4 *items = sub ? sub->belt : k->d_items_belt;
             const int n_items = sub ? sub->n_belt : k->n_items_belt;

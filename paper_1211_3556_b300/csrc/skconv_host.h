@@ -26,6 +26,8 @@ struct sk_ctx {
     int next_queue = 0;
     void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
     size_t ws_bytes = 0;
+    void *tcz = nullptr;           // workspace of the tensor-core belt's map planes
+    size_t tcz_bytes = 0;
     // side stream for the small launches that overlap the large ones (polar caps,
     // per-pair fallback rings), forked from and joined into the caller's stream
     cudaStream_t aux = nullptr;
@@ -94,7 +96,7 @@ struct sk_kern {
     // belt
     int b_lo = 0, nb = 0, HM = 0, WPM = 0, EMIN = 0, EMAX = 0, ngroups = 0;
     int belt_P = 13;
-    int2 *d_brng = nullptr, *d_bgrp = nullptr;
+    int2 *d_bgrp = nullptr;
     int smax = 0;                          // strips per group of the pair layout
     int2 *d_bpr = nullptr;                 // [groups][smax][warps] pair-row chunk ranges
     int4 *d_items_belt = nullptr;
@@ -124,11 +126,18 @@ struct sk_kern {
     // pair-row pre-pass writes them), rebuilt with the table; null: the pre-pass runs
     // per call into the workspace
     float2 *d_beltw = nullptr;
-    // batched tensor-core form of the belt: (group, 128-pixel block) items
+    // tensor-core belt (belt_tc.cu): one tile per (ring group, input ring) with
+    // (input ring, E0, K, A offset in KB), its group, and per group (first tile, tiles);
+    // the A store (TF32 hi/lo tiles, built on first use and rebuilt with the table);
+    // the geometry of the per-call map planes
     bool tc_ok = false;
-    TcGeom tcg{};
-    int4 *d_items_tc = nullptr;
-    int n_items_tc = 0;
+    std::vector<int4> h_tct;
+    int4 *d_tct = nullptr;
+    int *d_tcg = nullptr;
+    int2 *d_tcr = nullptr;
+    long long tca_kb = 0;
+    unsigned char *d_tca = nullptr;
+    int tc_kmax = 0, tc_nn = 0, tc_nblk = 0, tc_pbase = 0, tc_zrows = 0, tc_zi0 = 0, tc_nz = 0, tc_stages = 0;
     // host copies of the item lists, and their partition into ring bands by distance
     // from the nearest pole (sk_convolve_host overlaps the copies of one band with the
     // sums of another); rebuilt when the belt tile width changes
@@ -177,6 +186,9 @@ void sk_capw_free(sk_kern *k);
 // (same gate and stream rules as sk_capw_build; an allocation that fails leaves the
 // pre-pass per call).
 int sk_beltw_build(sk_kern *k, cudaStream_t st = 0, const int *gate = nullptr);
+// A tiles of the tensor-core belt: allocate (if absent; a failed allocation leaves the
+// tensor path to the FP32 belt) and evaluate them from the current table, gated as above.
+int sk_tca_build(sk_kern *k, cudaStream_t st = 0, const int *gate = nullptr);
 void sk_plan_free(sk_kern *k);
 int sk_plan_rebuild_belt_items(sk_kern *k);
 size_t sk_plan_workspace_bytes(const sk_kern *k);

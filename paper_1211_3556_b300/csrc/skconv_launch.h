@@ -42,8 +42,6 @@ struct JobDesc {
     int WPM;              // weights per (output ring, input ring) row: offsets EMIN .. EMIN+WPM-1, multiple of 4
     int EMIN, EMAX;       // pixel offset range of all belt windows
     int n4;               // pixels per belt ring (4 Nside)
-    const int2 *brng;     // [nb_pad][2HM+1] first and last 4-chunk (of offsets EMIN + 4c ..) with weights
-    const float *bw;      // [nb_pad][2HM+1][WPM] weights on the common offset grid (workspace, per call)
     const int2 *bgrp;     // [groups] first and last input ring of each group
     // belt weights as ring pairs, streamed with the strips (FP32 CUDA-core path)
     int smax;             // strips per group in the pair layout (max over groups)
@@ -76,19 +74,47 @@ __device__ __forceinline__ int sk_find_job(const JobsArg &a, int f) {
     return j;
 }
 
-// batched tensor-core belt (belt_tc.cu): items of SK_BELT_G rings x SK_TC_SEGW pixels x SK_TC_MAPS maps
-constexpr int SK_TC_MAPS = 32;
-constexpr int SK_TC_SEGW = 64;
-struct TcGeom {
-    int kt8;    // K extent of one segment's window, multiple of 8
-    int ka;     // 32-column atoms of the weight tile
-    int xl;     // pixels of the map tile (multiple of 32)
-    int xa;     // 32-column atoms of the map tile
-    int off4;   // EMIN - EMIN rounded down to a multiple of 4
+// tensor-core belt (belt_tc.cu): items of SK_BELT_G rings x 8 nn pixels of one map
+constexpr int SK_TC_MAX_STAGES = 6;
+// tile field z: K in the low bits, and whether the tile starts / ends a chunk of tiles
+// accumulated together (at least SK_TC_CHUNK_KSTEPS k-steps, or the group's last)
+constexpr int SK_TC_K_MASK = 0xFFFF;
+constexpr int SK_TC_FIRST = 1 << 16;
+constexpr int SK_TC_LAST = 1 << 17;
+constexpr int SK_TC_CHUNK_KSTEPS = 6;
+struct TcArgs {
+    const RingDev *rings;
+    float *y;
+    long long stride;
+    int batch;
+    int b_lo, nb, n4;
+    const int4 *tiles;          // per tile: (input ring, E0, K | chunk flags, offset of its A pair in KB)
+    const int2 *trng;           // per ring group: first tile, tiles
+    const unsigned char *A;     // stored A tiles (TF32 hi, then lo, no-swizzle K-major)
+    const float4 *Z;            // the call's planes: [map][ring - zi0][hi even, hi odd, lo even, lo odd][zrows]
+    int zi0, nz, zrows, pbase;  // first plane ring, plane rings, rows per plane, pixel of row 0
+    int nn, nblk, kmax, nstages;
+    int total;                  // items: groups x maps x pixel blocks
+    int *status;
 };
-bool sk_tc_geometry(int wpm, int emin, int n4, TcGeom *g);
-size_t sk_tc_smem(const TcGeom &g, int wpm);
-cudaError_t sk_launch_belt_tc(const JobsArg &a, const TcGeom &g, int wpm_max, int grid, cudaStream_t st);
+struct TcTileArgs {
+    const int4 *tiles;
+    const int *tile_group;
+    unsigned char *A;
+    const RingDev *rings;
+    const int *pair_off;
+    const PairInfo *pairs;
+    KernParams kp;
+    const float2 *tab;
+    int b_lo, nb, n4;
+};
+// pipeline stages for (kmax, nn) and the launch's shared memory; 0 = does not fit
+int sk_tc_stages(int kmax, int nn, size_t *smem);
+cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st);
+// A tiles of all n_tiles tiles; with `gate`, only if *gate is non-zero
+cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st, const int *gate = nullptr);
+cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
+                                int zrows, int pbase, int n4, float4 *Z, int sms, cudaStream_t st);
 
 // set-up kernels (geometry.cu)
 cudaError_t sk_launch_ring_geom(long long nside, RingDev *rings, double *z, double *rho,
@@ -111,7 +137,6 @@ cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const
 
 // convolution kernels; grid = number of blocks (persistent)
 cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);
-cudaError_t sk_launch_belt_weights(const JobDesc &j, float *w, cudaStream_t st);
 // weight rows of belt ring groups [g0, g1) (the rows of other groups are not written);
 // with `gate`, only if *gate is non-zero
 cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st,

@@ -52,6 +52,25 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// Descriptor of a K-major operand without swizzle: 8-row x 16-byte core matrices
+// (rows 16 bytes apart inside one), `lbo` bytes between core matrices adjacent in K,
+// `sbo` bytes between adjacent 8-row groups; all three 16-byte multiples.  With
+// sbo = 128 the rows of the operand are simply 16 bytes apart, so an operand whose
+// row s + 1 is row s shifted by one 16-byte chunk is a start-address move away.
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                    // version; layout 0 = no swizzle
+    return d;
+}
+// Byte offset of element (r, k) of a 128-row K-major no-swizzle operand whose
+// 4-column chunks are 2048 bytes apart (lbo 2048, sbo 128).
+__host__ __device__ inline uint32_t kmajor128_offset(int r, int k) {
+    return (uint32_t)((k >> 2) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
 // Instruction descriptor of kind::tf32: D fp32, A and B TF32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

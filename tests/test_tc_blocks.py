@@ -1,5 +1,6 @@
 """Tensor-core building blocks (tcgen05 TF32 MMA from swizzled shared memory into
-tensor memory) against a host product, through the C ABI."""
+tensor memory, and the no-swizzle sliding-row operand form of the tensor-core belt)
+against a host product, through the C ABI."""
 import ctypes
 
 import numpy as np
@@ -52,3 +53,46 @@ def test_3xtf32_accuracy(env):
     scale = np.abs(A).astype(np.float64) @ np.abs(B).T.astype(np.float64)
     assert np.max(np.abs(D3 - want) / scale) < 2e-6          # 3xTF32 ~ FP32 accuracy
     assert np.max(np.abs(D1 - want) / scale) > 1e-5          # plain TF32 is visibly coarser
+
+
+def _run_sliding(sk, ctx, torch, A, x, n, off):
+    a = torch.from_numpy(np.ascontiguousarray(A, np.float32)).cuda()
+    xv = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    d = torch.full((128, n), float("nan"), device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = sk.lib()
+    rc = L.sk_selftest_tc_sliding(ctx._h, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(xv.data_ptr()),
+                                  ctypes.c_void_p(d.data_ptr()), n, A.shape[1], off, st)
+    assert rc == 0, L.sk_last_error()
+    torch.cuda.synchronize()
+    assert L.sk_get_status(ctx._h, st) == 0
+    return d.cpu().numpy().astype(np.float64)
+
+
+def _sliding_ref(A, x, n, off):
+    K = A.shape[1]
+    B = np.stack([x[8 * s + off: 8 * s + off + K] for s in range(n)]).astype(np.float64)
+    return A.astype(np.float64) @ B.T
+
+
+@pytest.mark.parametrize("n,k,off", [(256, 40, 0), (256, 40, 4), (16, 8, 4), (128, 64, 0), (64, 24, 4)])
+def test_sliding_rows_exact_on_small_integers(env, n, k, off):
+    sk, ctx, torch = env
+    rng = np.random.default_rng(7 * n + k + off)
+    A = rng.integers(-8, 9, size=(128, k)).astype(np.float32)
+    x = rng.integers(-8, 9, size=8 * (n + k // 8 + 2)).astype(np.float32)
+    D = _run_sliding(sk, ctx, torch, A, x, n, off)
+    assert np.array_equal(D, _sliding_ref(A, x, n, off))
+
+
+def test_sliding_rows_3xtf32_accuracy(env):
+    sk, ctx, torch = env
+    rng = np.random.default_rng(11)
+    n, k = 256, 48
+    A = rng.standard_normal((128, k)).astype(np.float32)
+    x = rng.standard_normal(8 * (n + k // 8 + 2)).astype(np.float32)
+    for off in (0, 4):
+        D = _run_sliding(sk, ctx, torch, A, x, n, off)
+        want = _sliding_ref(A, x, n, off)
+        scale = _sliding_ref(np.abs(A), np.abs(x), n, off)
+        assert np.max(np.abs(D - want) / scale) < 2e-6
