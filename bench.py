@@ -178,6 +178,7 @@ PROFILED_SOURCES = {
     "conv_cap": ["cap.cu", "cap_common.cuh", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
     "conv_capw": ["capw.cu", "cap_common.cuh", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
     "conv_belt": ["belt.cu", "skconv_internal.cuh", "skconv_launch.h"],
+    "conv_belt_tc": ["belt_tc.cu", "skconv_internal.cuh", "skconv_launch.h", "tc.cuh"],
 }
 
 
@@ -314,6 +315,9 @@ def run_ours(args):
     # the same command (e.g. under a profiler, whose serialisation distorts the trials) reuses it
     tune_cache = os.path.join(tempfile.gettempdir(), "skconv_belt_tiles.txt")
     belt_tiles = [o["kern"].autotune(o["x"], out=o["y"], cache_path=tune_cache) for o in ops]
+    tuned = [o["kern"].config() for o in ops]          # belt form, tile width, cap weights kept
+    for o in ops:
+        o["cap_weight_bytes"] = o["kern"].cap_weight_bytes()
 
     if len(ops) == 1:
         o = ops[0]
@@ -351,21 +355,30 @@ def run_ours(args):
     dom = max(prof, key=lambda n: prof[n][0]) if prof else None
     # the pairs each launch sums (sk_count_pairs_by_launch): belt, caps with narrow windows,
     # caps with wide windows (polar rings, side stream), per-pair rings
-    launch_idx = {"conv_belt": 0, "conv_cap": 1, "conv_capw": 1, "conv_cap_polar": 2, "conv_capw_polar": 2,
-                  "conv_general": 3}
+    launch_idx = {"conv_belt": 0, "conv_belt_tc": 0, "conv_cap": 1, "conv_capw": 1, "conv_cap_polar": 2,
+                  "conv_capw_polar": 2, "conv_general": 3}
     roofline = None
     if dom in launch_idx:
         dom_pairs = sum(o["by_launch"][launch_idx[dom]] * o["group"].batch for o in ops)
         launch_ms = prof[dom][0] / prof[dom][1]
         per_launch_pairs = dom_pairs * args.steps / prof[dom][1]
         achieved = FLOP_PER_PAIR * per_launch_pairs / (launch_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                    "traffic": profiled_traffic(dom, args.workload),
-                    "peak_source": "measured on this GPU in this run: FP32 FMA chains (sk_measure_peak), "
-                                   "SM clock %s MHz while it ran" % peaks["ffma2"]["sm_mhz"],
-                    "frac_of_derived": achieved / peaks["fp32_derived_tflops"],
-                    "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
+        if dom == "conv_belt_tc":
+            # 3xTF32: three TF32 MMAs per useful product, so a third of the TF32 peak bounds it
+            tf32 = peaks["tf32_tcgen05"]["tflops"]
+            roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": tf32,
+                        "unit": "TFLOP/s", "frac": achieved / tf32, "frac_of_3xtf32_ceiling": 3 * achieved / tf32,
+                        "traffic": profiled_traffic(dom, args.workload),
+                        "peak_source": "measured on this GPU in this run: tcgen05 TF32 MMA loop (sk_measure_peak)",
+                        "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
+        else:
+            roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                        "traffic": profiled_traffic(dom, args.workload),
+                        "peak_source": "measured on this GPU in this run: FP32 FMA chains (sk_measure_peak), "
+                                       "SM clock %s MHz while it ran" % peaks["ffma2"]["sm_mhz"],
+                        "frac_of_derived": achieved / peaks["fp32_derived_tflops"],
+                        "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -399,7 +412,7 @@ def run_ours(args):
         pb = kb.count_pairs()
         kb.autotune(xb, out=yb, cache_path=os.path.join(tempfile.gettempdir(), "skconv_belt_tiles.txt"))
         batched = {"workload": "n1024x64_batched", "unit": UNIT}
-        for name, path in (("fp32", sk.PATH_AUTO), ("tensor_3xtf32", sk.PATH_TENSOR)):
+        for name, path in (("fp32", sk.PATH_FP32), ("tensor_3xtf32", sk.PATH_TENSOR)):
             msb = time_steps(torch, lambda: sk.convolve(kb, xb, out=yb, path=path), max(3, min(args.steps, 20)), 2,
                              barrier)
             batched[name] = {"value": pb * grp.batch / (msb * 1e-3), "ms_per_map": msb / grp.batch,
@@ -596,7 +609,7 @@ def run_ours(args):
                        "pairs_per_step_per_gpu": pairs_step,
                        "l2": "inputs larger than L2 (map bytes %d > 126 MB)" % int(sum(o["maps"].nbytes for o in ops)),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "belt_tile": belt_tiles},
+                       "belt_tile": belt_tiles, "tuned": tuned},
             "rms_rel_vs_fp64": rms,
             "f_eval": value / world * FLOP_PER_PAIR_EVAL / (fp32_peak * 1e12),
             "f_mac": value / world * FLOP_PER_PAIR / (fp32_peak * 1e12),

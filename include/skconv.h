@@ -58,10 +58,17 @@ extern "C" {
                               /* support, the bias the paper uses for the oscillating kernel  */
 
 /* Path selection for sk_convolve_path / sk_convolve_jobs / sk_graph_capture. */
-#define SK_PATH_AUTO       0   /* belt Toeplitz + symmetric caps where they apply   */
+#define SK_PATH_AUTO       0   /* belt Toeplitz + symmetric caps where they apply; the belt in */
+                               /* the operator's form (sk_kernel_set_belt_form, the autotuner) */
 #define SK_PATH_GENERAL    1   /* per-pair evaluation for every output ring        */
-#define SK_PATH_TENSOR     2   /* as AUTO, with the belt as 3xTF32 tcgen05 contractions over */
-                               /* 32-map blocks (the batched form; caps stay FP32)            */
+#define SK_PATH_TENSOR     2   /* as AUTO, with the belt as 3xTF32 tcgen05 contractions (ring  */
+                               /* group x input ring weight tiles against 8-pixel segments of  */
+                               /* the maps; caps stay FP32) where the operator has that form   */
+#define SK_PATH_FP32       3   /* as AUTO, with the belt on the FP32 CUDA-core kernel          */
+
+/* Belt forms of an operator (sk_kernel_set_belt_form). */
+#define SK_BELT_FP32       0   /* FP32 FMAs, ring-pair weight rows streamed with the strips   */
+#define SK_BELT_TENSOR     1   /* 3xTF32 tcgen05 MMAs (stored weight tiles, per-call map planes) */
 
 typedef struct sk_ctx  sk_ctx;
 typedef struct sk_geom sk_geom;
@@ -371,12 +378,29 @@ int sk_device_info(sk_ctx *ctx, int64_t *out4);
 int sk_kernel_set_tiles(sk_kern *k, int belt_p, int cap_t);
 int sk_kernel_get_tiles(const sk_kern *k, int *belt_p, int *cap_t);
 
-/* Autotuner of the belt tile width: times every candidate P on the caller's
- * maps (d_in -> d_out, `batch` maps), keeps the fastest in k and returns it in
- * *chosen.  If cache_path is not NULL, a text file of "key P" lines keyed by
- * GPU name, Nside, cut, node count, layout and batch is consulted first and
- * appended to after tuning.  Synchronises `stream`.  Not safe while k is used
- * from another thread.  Errors: as sk_convolve. */
+/* Belt form of operator k used by SK_PATH_AUTO: SK_BELT_FP32 (the default) or
+ * SK_BELT_TENSOR.  Choosing the tensor form evaluates its stored weight tiles
+ * (synchronises the device; they follow later table updates).  Not safe while a
+ * launch with k is being issued from another thread.
+ * Errors: SK_EINVAL (bad form, or the operator has no tensor form: no belt, a
+ * ring shorter than 128 pixels, or windows wider than 64 - 7 offsets),
+ * SK_ENOMEM (the tiles do not fit), SK_ECUDA. */
+int sk_kernel_set_belt_form(sk_kern *k, int form);
+
+/* The operator's tuned settings: out4[0] = belt tile width P of the FP32 form,
+ * out4[1] = belt form (SK_BELT_*), out4[2] = 1 if the cap weights are stored,
+ * out4[3] = 1 if the operator has a tensor belt form.  Errors: SK_EINVAL. */
+int sk_kernel_get_config(const sk_kern *k, int64_t *out4);
+
+/* Autotuner: times, on the caller's maps (d_in -> d_out, `batch` maps), every
+ * belt form -- the FP32 kernel with each tile width P and the tensor-core kernel
+ * where the operator has one -- and then stored against evaluated cap weights
+ * where the weights fit; keeps the fastest combination in k (read it back with
+ * sk_kernel_get_config) and returns the FP32 tile width in *chosen.  If
+ * cache_path is not NULL, a text file of "key P form capw" lines keyed by GPU
+ * name, Nside, cut, node count, layout and batch is consulted first and appended
+ * to after tuning.  Synchronises `stream`.  Not safe while k is used from
+ * another thread.  Errors: as sk_convolve. */
 int sk_kernel_autotune(sk_ctx *ctx, sk_kern *k, const float *d_in, float *d_out, int64_t batch,
                        int64_t map_stride, const char *cache_path, void *stream, int *chosen);
 

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libskconv.so")
 
 SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 NODES_UNIFORM, NODES_BIASED = 0, 1
-PATH_AUTO, PATH_GENERAL, PATH_TENSOR = 0, 1, 2
+PATH_AUTO, PATH_GENERAL, PATH_TENSOR, PATH_FP32 = 0, 1, 2, 3
+BELT_FP32, BELT_TENSOR = 0, 1
 PEAK_FFMA, PEAK_FFMA2, PEAK_TF32 = 0, 1, 2
 
 _ERRNAMES = {SK_EINVAL: "SK_EINVAL", SK_ENOMEM: "SK_ENOMEM", SK_ECUDA: "SK_ECUDA",
@@ -104,6 +105,8 @@ def _declare(L):
         "sk_measure_peak": (I, [P, I, D, ctypes.POINTER(D), P]),
         "sk_kernel_set_cap_weights": (I, [P, I]),
         "sk_kernel_cap_weight_bytes": (I, [P, ctypes.POINTER(I64)]),
+        "sk_kernel_set_belt_form": (I, [P, I]),
+        "sk_kernel_get_config": (I, [P, ctypes.POINTER(I64)]),
         "sk_device_info": (I, [P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
@@ -319,7 +322,9 @@ class Kernel:
         return [int(v) for v in a]
 
     def autotune(self, x, out=None, cache_path=None, stream=None) -> int:
-        """Time every belt tile width on maps x and keep the fastest; returns it."""
+        """Time the belt forms (FP32 with every tile width, tensor cores) and stored
+        against evaluated cap weights on maps x, keep the fastest; returns the FP32
+        tile width (the rest: config())."""
         import torch
         x2, b, stride = _map_args(x, self.geom.npix)
         if out is None:
@@ -330,6 +335,18 @@ class Kernel:
                                         ctypes.c_void_p(out.data_ptr()), b, stride, cp, _stream_ptr(stream),
                                         ctypes.byref(p)))
         return p.value
+
+    def set_belt_form(self, form: int):
+        """Belt of PATH_AUTO: BELT_FP32 or BELT_TENSOR (evaluates the tensor form's tiles)."""
+        _check(lib().sk_kernel_set_belt_form(self._h, int(form)))
+
+    def config(self) -> dict:
+        """The operator's settings: FP32 belt tile width, belt form, stored cap weights,
+        whether it has a tensor belt form."""
+        a = (ctypes.c_int64 * 4)()
+        _check(lib().sk_kernel_get_config(self._h, a))
+        return {"belt_p": int(a[0]), "belt_form": "tensor" if a[1] == BELT_TENSOR else "fp32",
+                "cap_weights": "stored" if a[2] else "evaluated", "tensor_form_available": bool(a[3])}
 
     def set_cap_weights(self, stored: bool):
         """Keep the caps' weights stored on the device (True) or evaluate them per call (False)."""

@@ -83,7 +83,6 @@ extern "C" int sk_destroy(sk_ctx *ctx) {
     if (!ctx) return SK_OK;
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
-    if (ctx->tcz) cudaFree(ctx->tcz);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_queue) cudaFree(ctx->d_queue);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
@@ -472,6 +471,36 @@ extern "C" int sk_kernel_set_cap_weights(sk_kern *k, int stored) {
     return SK_OK;
 }
 
+extern "C" int sk_kernel_set_belt_form(sk_kern *k, int form) {
+    if (!k || (form != SK_BELT_FP32 && form != SK_BELT_TENSOR))
+        return sk_fail(SK_EINVAL, "sk_kernel_set_belt_form: bad argument");
+    if (form == SK_BELT_FP32) {
+        k->belt_form = form;
+        return SK_OK;
+    }
+    if (!k->tc_ok) return sk_fail(SK_EINVAL, "sk_kernel_set_belt_form: the operator has no tensor belt form");
+    SK_CU(cudaSetDevice(k->ctx->device));
+    if (!k->d_tca) {
+        int rc = sk_tca_build(k);
+        if (rc) return rc;
+        SK_CU(cudaDeviceSynchronize());
+        if (!k->d_tca)
+            return sk_fail(SK_ENOMEM, "sk_kernel_set_belt_form: %lld KB of weight tiles do not fit",
+                           (long long)k->tca_kb);
+    }
+    k->belt_form = form;
+    return SK_OK;
+}
+
+extern "C" int sk_kernel_get_config(const sk_kern *k, int64_t *out4) {
+    if (!k || !out4) return sk_fail(SK_EINVAL, "sk_kernel_get_config: NULL argument");
+    out4[0] = k->belt_P;
+    out4[1] = k->belt_form;
+    out4[2] = k->d_capw ? 1 : 0;
+    out4[3] = k->tc_ok ? 1 : 0;
+    return SK_OK;
+}
+
 extern "C" int sk_kernel_cap_weight_bytes(const sk_kern *k, int64_t *bytes) {
     if (!k || !bytes) return sk_fail(SK_EINVAL, "sk_kernel_cap_weight_bytes: NULL argument");
     *bytes = k->d_capw ? (int64_t)k->capw_len * 16 : 0;
@@ -576,13 +605,13 @@ extern "C" int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve: NULL context");
     int rc = sk_check_maps("sk_convolve", k, d_in, d_out, batch, map_stride);
     if (rc) return rc;
-    if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL && path != SK_PATH_TENSOR)
+    if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL && path != SK_PATH_TENSOR && path != SK_PATH_FP32)
         return sk_fail(SK_EINVAL, "unknown path %d", path);
     if (batch == 0) return SK_OK;
     SK_CU(cudaSetDevice(ctx->device));
     SkJob jb{k, d_in, d_out, batch, map_stride};
     void *ws = nullptr;
-    size_t need = path != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(&jb, 1) : 0;
+    size_t need = path != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(&jb, 1, path) : 0;
     if (need && (rc = sk_ctx_workspace(ctx, need, &ws))) return rc;
     return sk_run_jobs(ctx, &jb, 1, path, ws, (cudaStream_t)stream);
 }
@@ -754,14 +783,14 @@ static int convert_jobs(const sk_job *jobs, int n, std::vector<SkJob> &out) {
 
 extern "C" int sk_convolve_jobs(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int flags, void *stream) {
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve_jobs: NULL context");
-    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR)
+    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR && flags != SK_PATH_FP32)
         return sk_fail(SK_EINVAL, "unknown flags %d", flags);
     std::vector<SkJob> js;
     int rc = convert_jobs(jobs, n_jobs, js);
     if (rc) return rc;
     SK_CU(cudaSetDevice(ctx->device));
     void *ws = nullptr;
-    size_t need = flags != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(js.data(), n_jobs) : 0;
+    size_t need = flags != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(js.data(), n_jobs, flags) : 0;
     if (need && (rc = sk_ctx_workspace(ctx, need, &ws))) return rc;
     return sk_run_jobs(ctx, js.data(), n_jobs, flags, ws, (cudaStream_t)stream);
 }
@@ -776,7 +805,7 @@ extern "C" int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int
                                 void **graph_exec) {
     if (!ctx || !graph_exec) return sk_fail(SK_EINVAL, "sk_graph_capture: NULL argument");
     *graph_exec = nullptr;
-    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR)
+    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR && flags != SK_PATH_FP32)
         return sk_fail(SK_EINVAL, "unknown flags %d", flags);
     if (!stream) return sk_fail(SK_EINVAL, "sk_graph_capture: capture needs a non-default stream");
     std::vector<SkJob> js;
@@ -785,7 +814,7 @@ extern "C" int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int
     SK_CU(cudaSetDevice(ctx->device));
     sk_graph *g = new sk_graph();
     g->device = ctx->device;
-    size_t need = flags != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(js.data(), n_jobs) : 0;
+    size_t need = flags != SK_PATH_GENERAL ? sk_jobs_workspace_bytes(js.data(), n_jobs, flags) : 0;
     if (need) {
         cudaError_t e = cudaMalloc(&g->ws, need);
         if (e != cudaSuccess) { delete g; return sk_fail(SK_ENOMEM, "graph workspace: %s", cudaGetErrorString(e)); }

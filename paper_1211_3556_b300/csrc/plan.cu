@@ -651,9 +651,23 @@ size_t sk_sym_bytes(const sk_kern *k, long long batch) {
     return ((size_t)batch * (size_t)k->sym_stride * sizeof(float4) + 255) & ~(size_t)255;
 }
 
-size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n) {
+bool sk_job_wants_tc(const SkJob &j, int path) {
+    const sk_kern *k = j.k;
+    const bool want = path == SK_PATH_TENSOR || (path == SK_PATH_AUTO && k->belt_form == SK_BELT_TENSOR);
+    return want && !j.sub && k->plan_ok && k->nb > 0 && k->tc_ok && j.batch > 0;
+}
+
+static size_t tc_plane_bytes(const SkJob &j) {
+    const sk_kern *k = j.k;
+    return ((size_t)j.batch * k->tc_nz * 4 * k->tc_zrows * sizeof(float4) + 255) & ~(size_t)255;
+}
+
+size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path) {
     size_t b = 0;
-    for (int i = 0; i < n; ++i) b += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
+    for (int i = 0; i < n; ++i) {
+        b += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
+        if (sk_job_wants_tc(jobs[i], path)) b += tc_plane_bytes(jobs[i]);
+    }
     return b;
 }
 
@@ -795,37 +809,25 @@ int sk_tca_build(sk_kern *k, cudaStream_t st, const int *gate) {
     return SK_OK;
 }
 
-static int tc_workspace(sk_ctx *ctx, size_t bytes, void **out) {
-    if (bytes > ctx->tcz_bytes) {
-        if (ctx->tcz) cudaFree(ctx->tcz);           // cudaFree waits for work using it
-        ctx->tcz = nullptr;
-        ctx->tcz_bytes = 0;
-        SK_CU(cudaMalloc(&ctx->tcz, bytes));
-        ctx->tcz_bytes = bytes;
-    }
-    *out = ctx->tcz;
-    return SK_OK;
-}
-
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
     // jobs whose belt runs on the tensor cores (their A tiles are built on first use)
+    // (whole operators only: a ring subset runs its belt items on the FP32 kernel)
     std::vector<char> use_tc(n, 0);
-    if (path == SK_PATH_TENSOR)
-        for (int i = 0; i < n; ++i) {
-            sk_kern *k = const_cast<sk_kern *>(jobs[i].k);
-            if (!k->plan_ok || k->nb == 0 || !k->tc_ok || jobs[i].batch == 0) continue;
-            if (!k->d_tca) {
-                int rc = sk_tca_build(k, st);
-                if (rc) return rc;
-            }
-            use_tc[i] = k->d_tca != nullptr;
+    for (int i = 0; i < n; ++i) {
+        sk_kern *k = const_cast<sk_kern *>(jobs[i].k);
+        if (!sk_job_wants_tc(jobs[i], path)) continue;
+        if (!k->d_tca) {
+            int rc = sk_tca_build(k, st);
+            if (rc) return rc;
         }
+        use_tc[i] = k->d_tca != nullptr;
+    }
 
     // belt weight rows of the FP32 belt: stored with the operator, else one pre-pass
     // per job into the workspace, shared by all its maps
     std::vector<float *> wrows(n, nullptr);
     char *wp = (char *)ws;
-    if (path == SK_PATH_AUTO || path == SK_PATH_TENSOR) {
+    if (path != SK_PATH_GENERAL) {
         for (int i = 0; i < n; ++i) {
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
@@ -907,15 +909,21 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         return flush();
     }
 
-    // tensor-core belt: per job, the maps' planes, then one launch over all its maps
-    if (path == SK_PATH_TENSOR) {
+    // tensor-core belt: per job, the maps' planes (in the workspace after the symmetric
+    // copies), then one launch over all its maps
+    {
+        std::vector<void *> zp(n, nullptr);
+        char *p = (char *)ws;
+        for (int i = 0; i < n; ++i) p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
+        for (int i = 0; i < n; ++i)
+            if (sk_job_wants_tc(jobs[i], path)) {
+                zp[i] = p;
+                p += tc_plane_bytes(jobs[i]);
+            }
         for (int i = 0; i < n; ++i) {
             if (!use_tc[i]) continue;
             const sk_kern *k = jobs[i].k;
-            const size_t zbytes = (size_t)jobs[i].batch * k->tc_nz * 4 * k->tc_zrows * sizeof(float4);
-            void *z = nullptr;
-            int rc = tc_workspace(ctx, zbytes, &z);
-            if (rc) return rc;
+            void *z = zp[i];
             cudaEvent_t ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, k->tc_zi0,
                                       k->tc_nz, k->tc_zrows, k->tc_pbase, (int)(4 * k->g->nside), (float4 *)z,

@@ -26,8 +26,6 @@ struct sk_ctx {
     int next_queue = 0;
     void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
     size_t ws_bytes = 0;
-    void *tcz = nullptr;           // workspace of the tensor-core belt's map planes
-    size_t tcz_bytes = 0;
     // side stream for the small launches that overlap the large ones (polar caps,
     // per-pair fallback rings), forked from and joined into the caller's stream
     cudaStream_t aux = nullptr;
@@ -131,6 +129,7 @@ struct sk_kern {
     // the A store (TF32 hi/lo tiles, built on first use and rebuilt with the table);
     // the geometry of the per-call map planes
     bool tc_ok = false;
+    int belt_form = SK_BELT_FP32;          // the belt of SK_PATH_AUTO
     std::vector<int4> h_tct;
     int4 *d_tct = nullptr;
     int *d_tcg = nullptr;
@@ -210,9 +209,12 @@ int sk_plan_bands(sk_kern *k);
 // [nr - hi, nr - lo) (a cap item, which writes a ring and its mirror, taken once).
 int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **out);
 // Launch sequence of the forward operator for a set of jobs.  `ws` must hold
-// sk_jobs_workspace_bytes(jobs) bytes: the belt weight rows of every job, then the
-// symmetric copies of every job's maps for the caps.
-size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n);
+// sk_jobs_workspace_bytes(jobs, n, path) bytes: the belt weight rows of every job,
+// then the symmetric copies of every job's maps for the caps, then the map planes of
+// the jobs whose belt runs on the tensor cores.
+size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path = SK_PATH_AUTO);
+// Whether job j's belt runs on the tensor cores under `path` (given its tiles exist).
+bool sk_job_wants_tc(const SkJob &j, int path);
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st);
 // Table gradient: `acc` is the start of sk_grad_workspace_bytes(k, batch) bytes of
 // workspace (the FP64 bins, then the caps' symmetric copy of x).

@@ -423,9 +423,13 @@ def test_belt_tile_widths_give_identical_results_and_autotune(sk, tmp_path):
             assert torch.equal(y, ref)                 # same summation order for every tile width
     cache = str(tmp_path / "tune.txt")
     p1 = k.autotune(x, cache_path=cache)
+    c1 = k.config()
     p2 = k.autotune(x, cache_path=cache)               # second call is served by the cache
-    assert p1 == p2 and p1 in (5, 7, 9, 11, 13, 15, 17)
-    assert torch.equal(sk.convolve(k, x), ref)
+    assert p1 == p2 and p1 in (5, 7, 9, 11, 13, 15, 17) and k.config() == c1
+    assert torch.equal(sk.convolve(k, x, path=sk.PATH_FP32), ref)
+    # whichever form the tuner kept, PATH_AUTO runs it and meets the bound
+    yo = O.conv_window(nside, V, tc, 0, x[1].cpu().numpy().astype(np.float64))
+    assert rms_rel(sk.convolve(k, x)[1].cpu().numpy(), yo) <= RMS_BOUND
     sk._ctx.status()
 
 
@@ -438,7 +442,7 @@ def test_tensor_path_matches_oracle(sk, nside, tc, batch, layout):
     k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc, layout)
     x = white_noise_maps(nside, batch, 700 + nside)
     y = gpu_conv(sk, k, x, path=sk.PATH_TENSOR)
-    yf = gpu_conv(sk, k, x, path=sk.PATH_AUTO)
+    yf = gpu_conv(sk, k, x, path=sk.PATH_FP32)
     for b in sorted({0, batch // 2, batch - 1}):
         yo = O.conv_window(nside, V, tc, layout, x[b].astype(np.float64))
         assert rms_rel(y[b], yo) <= RMS_BOUND, (b, rms_rel(y[b], yo))
