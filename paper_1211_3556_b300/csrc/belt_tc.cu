@@ -13,10 +13,11 @@
 // to a multiple of 4 and K_i covers the union plus the 7 extra columns of the
 // 8 output pixels (a multiple of 8).  For k-step q the B operand is
 // B_q[s][t] = x_i[j0 + E0 + 8 (s + q) + t]: the input ring read in sliding rows.
-// Staged as planes of 16-byte rows (pixels 8m .. 8m+3, "even", and 8m+4 ..
-// 8m+7, "odd", of the ring), every k-step of both operands is a start address
-// in shared memory (no-swizzle K-major, rows 16 bytes apart), so nothing is
-// rebuilt inside the loop:
+// Staged as two planes of 16-byte rows -- pixels 8m .. 8m+3 and 8m+4 .. 8m+7 of
+// the ring from the tile's first 4-pixel row when that row is even, else the odd
+// rows from it and the even rows one on -- every k-step of both operands is a
+// start address in shared memory (no-swizzle K-major, rows 16 bytes apart, the
+// second plane one plane further), so nothing is rebuilt inside the loop:
 //  * A (TF32 hi and lo parts) is stored per (group, input ring) with the
 //    operator (k_tc_tiles) and rebuilt with its table;
 //  * the maps' planes (hi and lo parts, wrapped around each ring) are written
@@ -52,8 +53,8 @@ constexpr int NEPI = 8;                // epilogue warps
 constexpr int NT = 32 * (2 + NEPI);
 constexpr unsigned long long LIMIT = 2000000000ull;
 
-// One pipeline stage: A (hi then lo, K x 512 bytes each, room for kmax), then three
-// hi and three lo plane slots of `slot` bytes (nn + kmax/8 rows of 16 bytes).
+// One pipeline stage: A (hi then lo, K x 512 bytes each, room for kmax), then two
+// hi and two lo plane slots of `slot` bytes (nn + kmax/8 rows of 16 bytes).
 struct Stage {
     uint32_t a_bytes, slot, bytes;
 };
@@ -61,7 +62,7 @@ __host__ __device__ inline Stage stage_of(int kmax, int nn) {
     Stage s;
     s.a_bytes = 2u * (uint32_t)kmax * 512u;
     s.slot = (uint32_t)(nn + kmax / 8) * 16u;
-    s.bytes = (s.a_bytes + 6u * s.slot + 1023u) & ~1023u;
+    s.bytes = (s.a_bytes + 4u * s.slot + 1023u) & ~1023u;
     return s;
 }
 
@@ -134,13 +135,13 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                     tc::bulk_g2s(tc::smem_u32(sb), T.A + (size_t)tl.w * 1024, (uint32_t)K * 1024u, bar);
                     for (int h = 0; h < 2; ++h) {                 // hi, lo parts
                         const float4 *pe = zr + (size_t)(2 * h) * T.zrows, *po = pe + T.zrows;
-                        const uint32_t sl = tc::smem_u32(sb + L.a_bytes + 3u * (uint32_t)h * L.slot);
+                        const uint32_t sl = tc::smem_u32(sb + L.a_bytes + 2u * (uint32_t)h * L.slot);
                         if (!(u0 & 1)) {                          // k-steps start on an even row
                             tc::bulk_g2s(sl, pe + m0, rbytes, bar);
                             tc::bulk_g2s(sl + L.slot, po + m0, rbytes, bar);
                         } else {                                  // on an odd row: odd, then even one on
-                            tc::bulk_g2s(sl + L.slot, po + m0, rbytes, bar);
-                            tc::bulk_g2s(sl + 2u * L.slot, pe + m0 + 1, rbytes, bar);
+                            tc::bulk_g2s(sl, po + m0, rbytes, bar);
+                            tc::bulk_g2s(sl + L.slot, pe + m0 + 1, rbytes, bar);
                         }
                     }
                 }
@@ -155,9 +156,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
             uint32_t cnt = 0, ccnt = 0;                           // tiles, chunks
             const uint32_t idesc = tc::idesc_tf32(128, T.nn);
             for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
-                const int g = f / per_g, rem = f - g * per_g, pb = rem % T.nblk;
-                const int j0 = pb * 8 * T.nn;
-                const int2 tr = T.trng[g];
+                const int2 tr = T.trng[f / per_g];
                 for (int u = 0; u < tr.y; ++u, ++cnt) {
                     const int4 tl = T.tiles[tr.x + u];
                     const int s = (int)(cnt % (uint32_t)S);
@@ -169,10 +168,9 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                     if (!wait_or_abort(tc::smem_u32(&full_bar[s]), (cnt / S) & 1, abort_flag, T.status)) break;
                     tc::fence_after_sync();
                     const int K = tl.z & SK_TC_K_MASK;
-                    const int u0 = (j0 + tl.y - T.pbase) >> 2;
                     const uint32_t sb = tc::smem_u32(base + (size_t)s * L.bytes);
                     const uint32_t a_hi = sb, a_lo = sb + (uint32_t)K * 512u;
-                    const uint32_t b_hi = sb + L.a_bytes + ((u0 & 1) ? L.slot : 0u), b_lo = b_hi + 3u * L.slot;
+                    const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + 2u * L.slot;
                     const uint32_t d = taddr + 256u * (uint32_t)ab;
                     for (int q = 0; q < K / 8; ++q) {
                         const uint64_t ah = tc::kmajor_desc(a_hi + 4096u * q, 2048, 128);
