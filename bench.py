@@ -182,6 +182,15 @@ PROFILED_SOURCES = {
 }
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on the B300s (MEASURED_PEAKS.json), else the fallback."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        return float(json.load(open(os.path.join(here, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured (copy)"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
 def profiled_traffic(kernel, workload):
     import hashlib
     import re
@@ -379,6 +388,15 @@ def run_ours(args):
                                        "SM clock %s MHz while it ran" % peaks["ffma2"]["sm_mhz"],
                         "frac_of_derived": achieved / peaks["fp32_derived_tflops"],
                         "flop_per_unit": FLOP_PER_PAIR, "unit_of_work": "in-cut pixel pair x map"}
+        if roofline["traffic"]:
+            # the same launch against the HBM roof: DRAM bytes of the committed ncu capture
+            # (cold-cache, per launch) over this run's launch time
+            gbs = roofline["traffic"] / (launch_ms * 1e-3) / 1e9
+            hbm, src = measured_hbm_gbs()
+            roofline["dram_gbs"] = gbs
+            roofline["dram_frac"] = gbs / hbm
+            roofline["dram_peak_gbs"] = hbm
+            roofline["dram_peak_source"] = src
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
