@@ -89,7 +89,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 // zero outside a row's window (or where ring i is not in that output ring's
 // window list) and past 4 nch.  One thread per element.  With `gate`, nothing is
 // written unless *gate is set (the table did not change: the stored rows stand).
-__global__ void k_belt_pairs(const JobDesc J, int g0, int g1, float2 *w, const int *gate) {
+__global__ void k_belt_pairs(const JobDesc J, int g0, int g1, float2 *w, const int *gate, bool w64) {
     constexpr int NW = SK_BELT_WARPS;
     if (gate && !*gate) return;
     const long long base = (long long)g0 * J.smax * NW * J.WPM;
@@ -121,8 +121,13 @@ __global__ void k_belt_pairs(const JobDesc J, int g0, int g1, float2 *w, const i
                 const int s_o = J.rings[ro].s;
                 const int ec = (s_o + 1 - P.s_i) >> 1;
                 if (e < ec - P.W || e > ec + P.W) continue;
-                const float x = (float)((double)(2 * e + P.s_i - s_o) * half_step);
-                v[q] = pair_weight(x, P.A, P.B, J.kp, J.tab);
+                const double xd = (double)(2 * e + P.s_i - s_o) * half_step;
+                if (w64) {
+                    const double2 ab = J.ab64[p];
+                    v[q] = pair_weight64(xd, ab.x, ab.y, J.kp, J.kd, J.V64, J.dOmega);
+                } else {
+                    v[q] = pair_weight((float)xd, P.A, P.B, J.kp, J.tab);
+                }
             }
         }
         w[idx] = make_float2(v[0], v[1]);
@@ -136,8 +141,12 @@ __global__ void k_belt_pairs(const JobDesc J, int g0, int g1, float2 *w, const i
 // last 4-offset chunk reads loaded values), then the eight warps' pair rows of
 // that ring, then their (start, chunks).  Warps meet only at the stage
 // barriers: no block-wide barrier between work items.
-template <int P>
-__global__ void __launch_bounds__(32 * (SK_BELT_WARPS + 1), 3)
+// BLK (operators whose outputs sum thousands of terms): each strip's contribution is
+// summed apart and added to the output's total after the strip, so that the FP32
+// rounding grows with the terms of one input ring and the number of rings, not with
+// their product (two blocks per SM for the extra registers).
+template <int P, bool BLK>
+__global__ void __launch_bounds__(32 * (SK_BELT_WARPS + 1), BLK ? 2 : 3)
 k_conv_belt(const __grid_constant__ JobsArg A) {
     constexpr int NW = SK_BELT_WARPS;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -241,6 +250,9 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
                 const int2 r = reinterpret_cast<const int2 *>(sb + (size_t)slot * 4 + wmax)[warp];
                 const float4 *wr = reinterpret_cast<const float4 *>(sb + (size_t)slot * 4) + warp * (J.WPM / 2);
                 const float *xs = reinterpret_cast<const float *>(sb) + phase + lane * P + r.x;
+                float2 part[BLK ? P : 1];
+#pragma unroll
+                for (int k = 0; k < (BLK ? P : 1); ++k) part[k] = make_float2(0.0f, 0.0f);
                 // Strip values x[m] = xs[m] in a register ring of XB slots (slot m mod XB),
                 // duplicated into both halves of a float2 for the paired FMA.  Chunk c
                 // (offsets 4c .. 4c+3) uses x[4c .. 4c + P + 2]; while it runs, the 4
@@ -278,10 +290,18 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
 #pragma unroll
                             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                                for (int k = 0; k < P; ++k)
-                                    acc[k] = __ffma2_rn(w4[u], xb[(4 * uu + k + u) % XB], acc[k]);
+                                for (int k = 0; k < P; ++k) {
+                                    if constexpr (BLK)
+                                        part[k] = __ffma2_rn(w4[u], xb[(4 * uu + k + u) % XB], part[k]);
+                                    else
+                                        acc[k] = __ffma2_rn(w4[u], xb[(4 * uu + k + u) % XB], acc[k]);
+                                }
                         }
                     }
+                }
+                if constexpr (BLK) {
+#pragma unroll
+                    for (int k = 0; k < P; ++k) acc[k] = make_float2(acc[k].x + part[k].x, acc[k].y + part[k].y);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty0 + 8 * s);
@@ -310,20 +330,48 @@ k_conv_belt(const __grid_constant__ JobsArg A) {
     }
 }
 
-template <int P>
+template <int P, bool BLK>
 cudaError_t launch_p(const JobsArg &a, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_belt<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_belt<P, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_belt<P><<<grid, 32 * (SK_BELT_WARPS + 1), smem, st>>>(a);
+    k_conv_belt<P, BLK><<<grid, 32 * (SK_BELT_WARPS + 1), smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int P>
+template <int P, bool BLK>
 int occupancy_p(size_t smem) {
-    cudaFuncSetAttribute(k_conv_belt<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_conv_belt<P, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_belt<P>, 32 * (SK_BELT_WARPS + 1), smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_belt<P, BLK>, 32 * (SK_BELT_WARPS + 1), smem);
     return nb;
+}
+
+template <bool BLK>
+cudaError_t launch_any(const JobsArg &a, int P, int grid, size_t smem, cudaStream_t st) {
+    switch (P) {
+        case 5: return launch_p<5, BLK>(a, grid, smem, st);
+        case 7: return launch_p<7, BLK>(a, grid, smem, st);
+        case 9: return launch_p<9, BLK>(a, grid, smem, st);
+        case 11: return launch_p<11, BLK>(a, grid, smem, st);
+        case 13: return launch_p<13, BLK>(a, grid, smem, st);
+        case 15: return launch_p<15, BLK>(a, grid, smem, st);
+        case 17: return launch_p<17, BLK>(a, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool BLK>
+int occupancy_any(int P, size_t smem) {
+    switch (P) {
+        case 5: return occupancy_p<5, BLK>(smem);
+        case 7: return occupancy_p<7, BLK>(smem);
+        case 9: return occupancy_p<9, BLK>(smem);
+        case 11: return occupancy_p<11, BLK>(smem);
+        case 13: return occupancy_p<13, BLK>(smem);
+        case 15: return occupancy_p<15, BLK>(smem);
+        case 17: return occupancy_p<17, BLK>(smem);
+        default: return 1;
+    }
 }
 
 size_t stage_bytes(int P, int wpm) {
@@ -343,41 +391,24 @@ size_t belt_smem(const JobsArg &a, int P) {
 
 }  // namespace
 
-cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st, const int *gate) {
+cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st, const int *gate,
+                                 bool w64) {
     const long long n = (long long)(g1 - g0) * j.smax * SK_BELT_WARPS * j.WPM;
     if (n <= 0) return cudaSuccess;
     const long long blocks = (n + 255) / 256;
-    k_belt_pairs<<<(unsigned)std::min<long long>(blocks, 1 << 20), 256, 0, st>>>(j, g0, g1, w, gate);
+    k_belt_pairs<<<(unsigned)std::min<long long>(blocks, 1 << 20), 256, 0, st>>>(j, g0, g1, w, gate, w64);
     return cudaGetLastError();
 }
 
 size_t sk_belt_smem_bytes(int P, int wpm) { return HDR + (size_t)S * stage_bytes(P, wpm); }
 
-cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st) {
+cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, bool blocked, int grid, cudaStream_t st) {
     if (a.total <= 0) return cudaSuccess;
-    size_t smem = belt_smem(a, P);
-    switch (P) {
-        case 5: return launch_p<5>(a, grid, smem, st);
-        case 7: return launch_p<7>(a, grid, smem, st);
-        case 9: return launch_p<9>(a, grid, smem, st);
-        case 11: return launch_p<11>(a, grid, smem, st);
-        case 13: return launch_p<13>(a, grid, smem, st);
-        case 15: return launch_p<15>(a, grid, smem, st);
-        case 17: return launch_p<17>(a, grid, smem, st);
-        default: return cudaErrorInvalidValue;
-    }
+    const size_t smem = belt_smem(a, P);
+    return blocked ? launch_any<true>(a, P, grid, smem, st) : launch_any<false>(a, P, grid, smem, st);
 }
 
-int sk_belt_blocks_per_sm(const JobsArg &a, int P) {
-    size_t smem = belt_smem(a, P);
-    switch (P) {
-        case 5: return occupancy_p<5>(smem);
-        case 7: return occupancy_p<7>(smem);
-        case 9: return occupancy_p<9>(smem);
-        case 11: return occupancy_p<11>(smem);
-        case 13: return occupancy_p<13>(smem);
-        case 15: return occupancy_p<15>(smem);
-        case 17: return occupancy_p<17>(smem);
-        default: return 0;
-    }
+int sk_belt_blocks_per_sm(const JobsArg &a, int P, bool blocked) {
+    const size_t smem = belt_smem(a, P);
+    return blocked ? occupancy_any<true>(P, smem) : occupancy_any<false>(P, smem);
 }

@@ -36,14 +36,16 @@ constexpr int OPT = 4;      // outputs per thread
 static_assert(CT == OPT * NTW, "an item is 256 base outputs");
 // work items per block and strip buffers per item: two buffers (ring p + 1 staged while
 // ring p is summed) where they fit in shared memory
-template <int LS>
-__host__ __device__ constexpr int capw_slots() { return LS <= 288 ? 6 : 2; }
+template <int LS, bool BLK>
+__host__ __device__ constexpr int capw_slots() { return LS <= 288 ? (BLK ? 4 : 6) : 2; }
 template <int LS>
 __host__ __device__ constexpr int capw_bufs() { return LS <= 640 ? 2 : 1; }
 // dynamic shared memory: strips [slots][NB][4][LS] float4, then the full and empty
-// mbarriers of every buffer and the abort flag (16-byte multiple)
+// mbarriers of every buffer and the abort flag (16-byte multiple), then with blocked
+// summation the threads' running totals [64 values][threads] float
 __host__ __device__ constexpr size_t capw_strip_bytes(int ls, int nb, int slots) { return (size_t)slots * nb * 4 * ls * 16; }
 __host__ __device__ constexpr size_t capw_bar_bytes(int nb, int slots) { return ((size_t)2 * slots * nb * 8 + 4 + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t capw_tot_bytes(bool blk, int slots) { return blk ? (size_t)64 * slots * 64 * 4 : 0; }
 // node tables of up to this many nodes are held as (value, slope) pairs, larger ones as
 // values (as in the evaluating kernel, whose weights the builder reproduces)
 constexpr int PAIR_TABLE_NODES = 8192;
@@ -117,13 +119,20 @@ __device__ __forceinline__ void mac16x4(float2 (&acc)[OPT][8], const float4 w, c
 // otherwise.  With one buffer (NB == 1) the item's threads synchronise at every ring.
 // Twelve warps per block at most: the SM's four sub-partitions hold 16K registers each
 // and three warps of the block share one, so a thread gets at most 168 registers.
-template <int LS>
-__global__ void __launch_bounds__(NTW * capw_slots<LS>(), 1)
+// BLK (operators whose outputs sum thousands of terms): the sums of each input ring are
+// added to the thread's running totals, kept in its own slice of shared memory (the
+// registers hold the 64 sums of one ring), so that the FP32 rounding grows with the
+// terms of one ring and the number of rings, not with their product.
+template <int LS, bool BLK>
+__global__ void __launch_bounds__(NTW * capw_slots<LS, BLK>(), 1)
 k_conv_capw(const __grid_constant__ JobsArg A) {
-    constexpr int NB = capw_bufs<LS>(), SLOTS = capw_slots<LS>();
+    constexpr int NB = capw_bufs<LS>(), SLOTS = capw_slots<LS, BLK>();
+    constexpr int NTH = NTW * SLOTS;
     extern __shared__ __align__(16) float4 sx[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(sx) + capw_strip_bytes(LS, NB, SLOTS));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * SLOTS * NB);
+    float *const tot = reinterpret_cast<float *>(reinterpret_cast<char *>(sx) + capw_strip_bytes(LS, NB, SLOTS) +
+                                                 capw_bar_bytes(NB, SLOTS)) + threadIdx.x;   // value i at tot[i NTH]
     if (threadIdx.x == 0) {
         for (int b = 0; b < SLOTS * NB; ++b) {
             tc::mbar_init(tc::smem_u32(bars + b), 1);                  // full: the expect_tx arrival
@@ -206,6 +215,10 @@ k_conv_capw(const __grid_constant__ JobsArg A) {
         for (int k = 0; k < OPT; ++k)
 #pragma unroll
             for (int s = 0; s < 8; ++s) acc[k][s] = make_float2(0.0f, 0.0f);
+        if constexpr (BLK) {
+#pragma unroll
+            for (int i = 0; i < 16 * OPT; ++i) tot[i * NTH] = 0.0f;
+        }
 
         // ring p's strip into buffer b by bulk copies (by the calling warp), unless it
         // wraps the whole ring (then the item's threads copy it when they reach it)
@@ -334,6 +347,18 @@ k_conv_capw(const __grid_constant__ JobsArg A) {
                     for (int q = 0; q < 4; ++q) wc[q] = wn[q];
                     s0 += 4;
                 }
+                if constexpr (BLK) {
+                    // the ring's sums into the running totals
+#pragma unroll
+                    for (int k = 0; k < OPT; ++k)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int i = 2 * (8 * k + e);
+                            tot[i * NTH] += acc[k][e].x;
+                            tot[(i + 1) * NTH] += acc[k][e].y;
+                            acc[k][e] = make_float2(0.0f, 0.0f);
+                        }
+                }
             } else {
                 s0 += 4 * ngroups;
             }
@@ -346,6 +371,15 @@ k_conv_capw(const __grid_constant__ JobsArg A) {
         if (*abort_flag) continue;
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
+        if constexpr (BLK) {
+#pragma unroll
+            for (int k = 0; k < OPT; ++k)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int i = 2 * (8 * k + e);
+                    acc[k][e] = make_float2(tot[i * NTH], tot[(i + 1) * NTH]);
+                }
+        }
 #pragma unroll
         for (int k = 0; k < OPT; ++k) {
             const int j = jt + k;
@@ -442,13 +476,64 @@ k_capw_build(const __grid_constant__ JobsArg A, float4 *__restrict__ W, const in
     }
 }
 
-template <int LS>
+// The same stream evaluated in FP64 (pair_weight64: FP64 chord from the pair's FP64
+// (A, B), node coordinate and interpolation of the FP64 node values, one rounding to
+// FP32), for operators with wide windows, whose outputs sum thousands of weights: there
+// the FP32 evaluation's table-coordinate error (u up to the node count, one FP32 ulp)
+// would otherwise reach 1e-6 of the result.  Same layout and window rules as k_capw_build.
+__global__ void __launch_bounds__(256)
+k_capw_build64(const __grid_constant__ JobsArg A, float4 *__restrict__ W, const int *gate) {
+    if (gate && !*gate) return;                  // table unchanged: the weights stand
+    const JobDesc &J = A.j[0];
+    const int per_block = blockDim.x / NTW;
+    const int t = threadIdx.x % NTW;
+    for (int f = blockIdx.x * per_block + threadIdx.x / NTW; f < J.n_items; f += gridDim.x * per_block) {
+        const int4 it = J.items[f];
+        const int ro = it.x, j0 = it.y;
+        const unsigned mg = (unsigned)it.z;
+        const int sh = it.w;
+        const RingDev R = J.rings[ro];
+        const int T = base_count(R.n >> 2, R.s);
+        const int jt = j0 + OPT * t;
+        if (jt >= T) continue;                       // no outputs: the thread's rows stay unread
+        const longlong2 wr = J.capw_ring[ro];
+        float4 *wp = W + wr.x + (long long)(j0 / CT) * wr.y * NTW + t;
+        long long s0 = 0;
+        for (int p = J.pair_off[ro]; p < J.pair_off[ro + 1]; ++p) {
+            const PairInfo P = J.pairs[p];
+            const double2 ab = J.ab64[p];
+            const double c0 = SK_PI / (2.0 * (double)R.n * (double)P.n_i);
+            int before, cnt;
+            win_shape(P, before, cnt);
+            const int NS = sk_capw_steps(cnt, P.n_i, R.n);
+            const int ct = centre_of(jt, R.n, R.s, P, mg, sh);
+            int lo[OPT];                             // own window of output k in union positions
+#pragma unroll
+            for (int k = 0; k < OPT; ++k) lo[k] = centre_of(jt + k, R.n, R.s, P, mg, sh) - ct;
+            for (int m = 0; m < NS; ++m) {
+                float w[OPT];
+#pragma unroll
+                for (int k = 0; k < OPT; ++k) {
+                    w[k] = 0.0f;
+                    if (jt + k < T && m >= lo[k] && m < lo[k] + cnt) {
+                        const double x = (double)q_of(ct - before + m, jt + k, R.n, R.s, P) * c0;
+                        w[k] = pair_weight64(x, ab.x, ab.y, J.kp, J.kd, J.V64, J.dOmega);
+                    }
+                }
+                wp[(s0 + m) * NTW] = make_float4(w[0], w[1], w[2], w[3]);
+            }
+            s0 += NS;
+        }
+    }
+}
+
+template <int LS, bool BLK>
 cudaError_t launch_conv(const JobsArg &a, int grid, cudaStream_t st) {
-    constexpr int NB = capw_bufs<LS>(), SLOTS = capw_slots<LS>();
-    const size_t smem = capw_strip_bytes(LS, NB, SLOTS) + capw_bar_bytes(NB, SLOTS);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_capw<LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int NB = capw_bufs<LS>(), SLOTS = capw_slots<LS, BLK>();
+    const size_t smem = capw_strip_bytes(LS, NB, SLOTS) + capw_bar_bytes(NB, SLOTS) + capw_tot_bytes(BLK, SLOTS);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_capw<LS, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_conv_capw<LS><<<grid, NTW * SLOTS, smem, st>>>(a);
+    k_conv_capw<LS, BLK><<<grid, NTW * SLOTS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -473,17 +558,26 @@ cudaError_t launch_build_m(const JobsArg &a, float4 *w, int grid, cudaStream_t s
 
 }  // namespace
 
-cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, int grid, cudaStream_t st) {
+cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, bool blocked, int grid, cudaStream_t st) {
     if (a.total <= 0) return cudaSuccess;
     switch (ls) {
-        case SK_CAP_LS[0]: return launch_conv<SK_CAP_LS[0]>(a, grid, st);
-        case SK_CAP_LS[1]: return launch_conv<SK_CAP_LS[1]>(a, grid, st);
-        case SK_CAP_LS[2]: return launch_conv<SK_CAP_LS[2]>(a, grid, st);
+        case SK_CAP_LS[0]:
+            return blocked ? launch_conv<SK_CAP_LS[0], true>(a, grid, st) : launch_conv<SK_CAP_LS[0], false>(a, grid, st);
+        case SK_CAP_LS[1]:
+            return blocked ? launch_conv<SK_CAP_LS[1], true>(a, grid, st) : launch_conv<SK_CAP_LS[1], false>(a, grid, st);
+        case SK_CAP_LS[2]:
+            return blocked ? launch_conv<SK_CAP_LS[2], true>(a, grid, st) : launch_conv<SK_CAP_LS[2], false>(a, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-int sk_capw_items_per_block(int ls) { return ls <= 288 ? 6 : 2; }
+int sk_capw_items_per_block(int ls, bool blocked) { return ls <= 288 ? (blocked ? 4 : 6) : 2; }
+
+cudaError_t sk_launch_capw_build64(const JobsArg &a, float4 *w, int grid, cudaStream_t st, const int *gate) {
+    if (a.j[0].n_items <= 0) return cudaSuccess;
+    k_capw_build64<<<grid, 256, 0, st>>>(a, w, gate);
+    return cudaGetLastError();
+}
 
 cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st,
                                  const int *gate) {

@@ -511,6 +511,14 @@ int sk_plan_build(sk_kern *k) {
     k->h_items_gen = gen;
     int rc = upload(gen, &k->d_items_gen);
     if (rc) return rc;
+    // window pixels of the widest output: the summation mode of the belt and caps
+    k->max_terms = 0;
+    for (int r = 0; r < nr; ++r) {
+        long long t = 0;
+        for (int p = off[r]; p < off[r + 1]; ++p) t += pairs[p].W < 0 ? pairs[p].n_i : 2 * pairs[p].W + 1;
+        k->max_terms = std::max(k->max_terms, t);
+    }
+    k->blocked = k->max_terms > SK_BLOCKED_TERMS;
     k->plan_ok = true;
     return sk_plan_bands(k);
 }
@@ -688,6 +696,8 @@ JobDesc base_desc(const SkJob &jb) {
     d.kp = k->kp;
     d.kd = k->kd;
     d.ab64 = k->d_ab64;
+    d.V64 = k->d_V;
+    d.dOmega = 4.0 * SK_PI / (double)k->g->npix;
     d.nr = k->g->nr;
     d.x = jb.x;
     d.y = jb.y;
@@ -762,7 +772,11 @@ int sk_capw_build(sk_kern *k, bool force, cudaStream_t st, const int *gate) {
             a.n_jobs = 1;
             a.total = n;
             const int mode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
-            SK_CU(sk_launch_capw_build(a, mode, k->d_capw, std::min((n + 3) / 4, 8 * k->ctx->num_sms), st, gate));
+            const int grid = std::min((n + 3) / 4, 8 * k->ctx->num_sms);
+            if (k->blocked)
+                SK_CU(sk_launch_capw_build64(a, k->d_capw, grid, st, gate));
+            else
+                SK_CU(sk_launch_capw_build(a, mode, k->d_capw, grid, st, gate));
         }
     return SK_OK;
 }
@@ -778,7 +792,7 @@ int sk_beltw_build(sk_kern *k, cudaStream_t st, const int *gate) {
         }
     }
     SkJob jb{k, nullptr, nullptr, 1, 0};
-    SK_CU(sk_launch_belt_pairs(belt_desc(jb, nullptr), 0, k->ngroups, k->d_beltw, st, gate));
+    SK_CU(sk_launch_belt_pairs(belt_desc(jb, nullptr), 0, k->ngroups, k->d_beltw, st, gate, k->blocked));
     return SK_OK;
 }
 
@@ -844,11 +858,12 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             // ring pairs: the groups a ring subset runs (one or two ranges), or all
             const SkItems *sub = jobs[i].sub;
             if (!sub || sub->bg[0][1] < 0) {
-                SK_CU(sk_launch_belt_pairs(d, 0, k->ngroups, (float2 *)wrows[i], st));
+                SK_CU(sk_launch_belt_pairs(d, 0, k->ngroups, (float2 *)wrows[i], st, nullptr, k->blocked));
             } else {
                 for (int q = 0; q < 2; ++q)
                     if (sub->bg[q][1] > sub->bg[q][0])
-                        SK_CU(sk_launch_belt_pairs(d, sub->bg[q][0], sub->bg[q][1], (float2 *)wrows[i], st));
+                        SK_CU(sk_launch_belt_pairs(d, sub->bg[q][0], sub->bg[q][1], (float2 *)wrows[i], st, nullptr,
+                                                   k->blocked));
             }
             sk_prof_end(ctx, "belt_weights", ev, st);
         }
@@ -958,16 +973,17 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         }
     }
 
-    // belt: one launch family per tile width P
+    // belt: one launch family per (tile width P, blocked summation)
     const int Ps[] = {5, 7, 9, 11, 13, 15, 17};
+    for (int blk = 0; blk < 2; ++blk)
     for (int P : Ps) {
         Batcher b;
         auto flush = [&]() -> int {
             if (b.a.total > 0) {
                 b.a.status = ctx->d_status;
-                int per = sk_belt_blocks_per_sm(b.a, P);
+                int per = sk_belt_blocks_per_sm(b.a, P, blk != 0);
                 cudaEvent_t ev = sk_prof_begin(ctx, st);
-                SK_CU(sk_launch_conv_belt(b.a, P, grid_for(b.a.total, per, ctx->num_sms), st));
+                SK_CU(sk_launch_conv_belt(b.a, P, blk != 0, grid_for(b.a.total, per, ctx->num_sms), st));
                 sk_prof_end(ctx, "conv_belt", ev, st);
             }
             b.reset();
@@ -975,7 +991,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         };
         for (int i = 0; i < n; ++i) {
             const sk_kern *k = jobs[i].k;
-            if (!k->plan_ok || k->nb == 0 || k->belt_P != P || jobs[i].batch == 0) continue;
+            if (!k->plan_ok || k->nb == 0 || k->belt_P != P || (int)k->blocked != blk || jobs[i].batch == 0)
+                continue;
             if (use_tc[i]) continue;                              // done on the tensor cores
             const SkItems *sub = jobs[i].sub;
             const int4 *items = sub ? sub->belt : k->d_items_belt;
@@ -994,20 +1011,21 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
     SK_CU(cudaEventRecord(ctx->ev_sym, side));
     SK_CU(cudaStreamWaitEvent(st, ctx->ev_sym, 0));
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
-        for (int v = 1; v >= 0; --v) {
+        for (int v = 1; v >= 0; --v)
+        for (int blk = 0; blk < 2; ++blk) {
             Batcher b;
             auto flush = [&]() -> int {
                 if (b.a.total > 0) {
                     b.a.status = ctx->d_status;
                     cudaStream_t cs = v ? st : side;
                     cudaEvent_t ev = sk_prof_begin(ctx, cs);
-                    const int ipb = sk_capw_items_per_block(SK_CAP_LS[c]);
+                    const int ipb = sk_capw_items_per_block(SK_CAP_LS[c], blk != 0);
                     const int blocks = (b.a.total + ipb - 1) / ipb;
                     int *q = ctx->d_queue + ctx->next_queue;
                     ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
                     SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));
                     b.a.queue = q;
-                    SK_CU(sk_launch_conv_capw(b.a, SK_CAP_LS[c], std::min(blocks, ctx->num_sms), cs));
+                    SK_CU(sk_launch_conv_capw(b.a, SK_CAP_LS[c], blk != 0, std::min(blocks, ctx->num_sms), cs));
                     sk_prof_end(ctx, v ? "conv_capw" : "conv_capw_polar", ev, cs);
                 }
                 b.reset();
@@ -1018,7 +1036,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                 const SkItems *sub = jobs[i].sub;
                 const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
                 const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
-                if (!k->plan_ok || !k->d_capw || cn == 0 || jobs[i].batch == 0) continue;
+                if (!k->plan_ok || !k->d_capw || (int)k->blocked != blk || cn == 0 || jobs[i].batch == 0) continue;
                 JobDesc d = base_desc(jobs[i]);
                 d.cap_ls = SK_CAP_LS[c];
                 d.hx = hx[i];

@@ -130,6 +130,10 @@ struct sk_kern {
     // the geometry of the per-call map planes
     bool tc_ok = false;
     int belt_form = SK_BELT_FP32;          // the belt of SK_PATH_AUTO
+    // outputs sum more than SK_BLOCKED_TERMS terms: the FP32 belt and the stored-weight
+    // caps sum each input ring apart and add it to the output's total
+    bool blocked = false;
+    long long max_terms = 0;               // largest number of window pixels of one output
     std::vector<int4> h_tct;
     int4 *d_tct = nullptr;
     int *d_tcg = nullptr;

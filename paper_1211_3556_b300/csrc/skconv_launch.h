@@ -10,6 +10,10 @@
 #include <cuda_runtime.h>
 #include "skconv_internal.cuh"
 
+// Outputs with more window terms than this sum each input ring apart (blocked summation):
+// plain FP32 accumulation of n terms drifts by about 1e-8 sqrt(n) relative, 5e-7 at the
+// few hundred terms of the usual cuts and 1-3e-6 at the 2e4 of a 300' cut.
+constexpr long long SK_BLOCKED_TERMS = 2000;
 constexpr int SK_MAXJ = 16;            // jobs per launch (more: several launches)
 constexpr int SK_MAX_NODES = 16384;    // largest kernel table
 constexpr int SK_BELT_G = 16;          // output rings per belt block (two per consumer warp)
@@ -24,7 +28,9 @@ struct JobDesc {
     const float2 *tab;
     KernParams kp;
     KernParams64 kd;          // table gradient only
-    const double2 *ab64;      // table gradient only: FP64 (A, B) per pair
+    const double2 *ab64;      // FP64 (A, B) per pair (table gradient, FP64-evaluated stored weights)
+    const double *V64;        // FP64 node values and dOmega (FP64-evaluated stored weights)
+    double dOmega;
     int nr;
     // maps
     const float *x;
@@ -139,17 +145,19 @@ cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const
 cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);
 // weight rows of belt ring groups [g0, g1) (the rows of other groups are not written);
 // with `gate`, only if *gate is non-zero
+// (w64: weights evaluated in FP64 -- pair_weight64 -- for operators with wide windows)
 cudaError_t sk_launch_belt_pairs(const JobDesc &j, int g0, int g1, float2 *w, cudaStream_t st,
-                                 const int *gate = nullptr);
+                                 const int *gate = nullptr, bool w64 = false);
 size_t sk_belt_smem_bytes(int P, int wpm);   // dynamic shared memory of a belt block
-cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, int grid, cudaStream_t st);
+// blocked: per-strip partial sums added to each output's total (operators with wide windows)
+cudaError_t sk_launch_conv_belt(const JobsArg &a, int P, bool blocked, int grid, cudaStream_t st);
 // mode bits: 1 sin series valid on every window of the items, 2 theta_cut <= 0.25
 // (asin series), 4 biased node layout
 cudaError_t sk_launch_conv_cap(const JobsArg &a, int ls, int mode, int grid, cudaStream_t st);
 // symmetric copy (hx) of rings [r0, r1) of every map of job j, for the cap kernels, pixels
 // split by residue modulo `split` (2: the evaluating kernel, 4: the stored-weight kernel)
 cudaError_t sk_launch_cap_sym(const JobDesc &j, int r0, int r1, int split, cudaStream_t st);
-int sk_belt_blocks_per_sm(const JobsArg &a, int P);
+int sk_belt_blocks_per_sm(const JobsArg &a, int P, bool blocked);
 int sk_cap_blocks_per_sm(int ls, int mode, int nt);
 constexpr int SK_CAP_LS_CLASSES = 3;
 constexpr int SK_CAP_LS[SK_CAP_LS_CLASSES] = {288, 640, 1280};  // strip positions per row of the cap path (float4)
@@ -162,10 +170,14 @@ __host__ __device__ inline int sk_capw_steps(int cnt, int n_i, int n_o) {
 }
 // stored-weight cap kernel (capw.cu): items of one strip class; the jobs' hx hold the
 // symmetric copies split by residue modulo 4
-cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, int grid, cudaStream_t st);
-int sk_capw_items_per_block(int ls);
+// blocked: each input ring's sums added to running totals (operators with wide windows)
+cudaError_t sk_launch_conv_capw(const JobsArg &a, int ls, bool blocked, int grid, cudaStream_t st);
+int sk_capw_items_per_block(int ls, bool blocked);
 // weight streams of the items of a.j[0] (a kernel's cap items of one list) into w; mode as
 // sk_launch_conv_cap
+// the same stream with every weight evaluated in FP64 (operators with wide windows)
+cudaError_t sk_launch_capw_build64(const JobsArg &a, float4 *w, int grid, cudaStream_t st,
+                                   const int *gate = nullptr);
 cudaError_t sk_launch_capw_build(const JobsArg &a, int mode, float4 *w, int grid, cudaStream_t st,
                                  const int *gate = nullptr);
 int sk_cap_items_per_block(int ls);   // cap work items a block holds at a time (one node table)

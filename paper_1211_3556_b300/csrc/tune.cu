@@ -151,7 +151,9 @@ extern "C" int sk_kernel_autotune(sk_ctx *ctx, sk_kern *k, const float *d_in, fl
         }
         k->belt_form = best.form;
     }
-    if (rc == SK_OK && k->d_capw) {
+    // (operators with wide windows keep their stored weights: those are evaluated in FP64
+    // and summed ring by ring, the evaluating kernel is neither)
+    if (rc == SK_OK && k->d_capw && !k->blocked) {
         if ((rc = sk_kernel_set_cap_weights(k, 0)) == SK_OK && (rc = time_it(&ms)) == SK_OK && ms < best_ms) {
             best_ms = ms;
             best.capw = 0;

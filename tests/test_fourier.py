@@ -119,9 +119,9 @@ def test_fourier_argument_errors(sk):
 
 
 def test_wide_workload_sampled_outputs(sk):
-    # the 300' workload at Nside 1024: zone rings (Fourier form) on sampled outputs against
-    # the oracle; the other rings run the direct sums, whose FP32 accumulation over the
-    # ~2.3e4 neighbours of a pixel at this cut gives a few 1e-6 (bound 5e-6 there)
+    # the 300' workload at Nside 1024: zone rings (Fourier form) and the other rings (the
+    # direct sums, summing each input ring apart over the ~2.4e4 neighbours of a pixel at
+    # this cut) on sampled outputs against the oracle
     import torch
     from inputs import WORKLOADS, make_maps, sample_indices
     grp = WORKLOADS["n1024_wide"].groups[0]
@@ -143,4 +143,4 @@ def test_wide_workload_sampled_outputs(sk):
     other = other[(other < p0) | (other >= p1)][:400]
     xs = x[0].astype(np.float64)
     assert rms_rel(y[zone], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=zone)) <= RMS_BOUND
-    assert rms_rel(y[other], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=other)) <= 5e-6
+    assert rms_rel(y[other], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=other)) <= RMS_BOUND

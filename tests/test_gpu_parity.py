@@ -129,6 +129,8 @@ TINY_CASES = [
     (2, math.pi, 0), (2, math.pi, 1), (2, 0.8, 0),
     (4, math.pi, 0), (4, math.pi, 1), (4, 0.45, 0),
     (8, math.pi, 0), (8, math.pi, 1),
+    # every output sums all 3072 / 12288 pixels: the blocked summation of wide windows
+    (16, math.pi, 0), (32, math.pi, 0),
 ]
 
 
