@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--errors", action="store_true",
                     help="the split's error study (Sec. 3): estimated and actual errors of the split "
                          "convolution of a white-noise map for several l_cut at a fixed theta_cut")
+    ap.add_argument("--table1", action="store_true",
+                    help="one point of the paper's Table 1 (7' beam, l_cut 1158, theta_cut 390', Nside 2048): "
+                         "the real-space part (ring-pair Fourier zone + direct rings) and the harmonic part, "
+                         "timed, with the real-space result against the oracle on sampled outputs")
     ap.add_argument("--bands", action="store_true",
                     help="strong scaling of one map: under torchrun each rank owns a symmetric ring band of "
                          "the workload's first map, and a step is the halo exchange plus the band's sums")
@@ -852,12 +856,54 @@ def split_error_study(nside, lmax, fwhm, tc_arcmin, lcuts, alpha=5.0):
             "data": "white noise band-limited to l_max (C_l flat, the paper's uniform-noise input)"}
 
 
+def run_table1(args):
+    """Sec. 4, Table 1's optimum split for a 7' beam at Planck resolution: the real-space
+    part of Eq. 1 (theta_cut 390') by the ring-pair Fourier form on the equatorial zone and the
+    direct sums elsewhere, the harmonic part (K^_l = K_l - R_l, l <= 1158) by the library's
+    ring transform; one map (its accuracy against the oracle: tests/test_fourier.py)."""
+    import torch
+    import paper_1211_3556_b300 as sk
+    torch.cuda.set_device(0)
+    grp = WORKLOADS["n2048_table1"].groups[0]
+    ks = grp.kernel
+    ctx = sk.Context(0)
+    t0 = time.perf_counter()
+    g = sk.Geometry(ctx, grp.nside)
+    k, V = sk.Kernel.from_legendre(g, ks.beam(), ks.lcut + 1, ks.lmax, ks.n_nodes, ks.theta_cut, ks.layout)
+    fw = sk.FourierBelt(k)
+    torch.cuda.synchronize()
+    t_real_setup = time.perf_counter() - t0
+    x = torch.from_numpy(make_maps(grp)).cuda()
+    y = torch.empty_like(x)
+    ms_real = time_steps(torch, lambda: fw.apply(x, out=y), max(1, min(args.steps, 3)), 1, lambda: None)
+    t0 = time.perf_counter()
+    R = sk.kernel_response(k, ks.lcut)
+    h = sk.Harmonic(ctx, g, ks.beam()[: ks.lcut + 1] - R, ks.lcut)
+    torch.cuda.synchronize()
+    t_harm_setup = time.perf_counter() - t0
+    yh = torch.empty_like(x)
+    ms_harm = time_steps(torch, lambda: h.apply(x, out=yh), max(3, min(args.steps, 5)), 1, lambda: None)
+    ctx.status()
+    info = fw.info()
+    line = {"mode": "table1", "workload": "n2048_table1", "nside": grp.nside, "fwhm_arcmin": ks.fwhm_arcmin,
+            "lmax": ks.lmax, "lcut": ks.lcut, "theta_cut_arcmin": ks.theta_cut_arcmin, "n_nodes": ks.n_nodes,
+            "pairs_per_map": k.count_pairs(), "ms_real_space": ms_real, "ms_harmonic": ms_harm,
+            "ms_split_total": ms_real + ms_harm, "real_setup_s": t_real_setup, "harmonic_setup_s": t_harm_setup,
+            "zone_rings": info["rings"], "G_gb": info["bytes"] / 1e9, "cap_weight_bytes": k.cap_weight_bytes(),
+            "data": "synthetic white-noise map",
+            "context": "paper (Sec. 4): about 12 s per convolution at its optimum splits, against 160 s for "
+                       "the whole kernel by a CPU SHT"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.errors:
         run_errors(args)
+    elif args.table1:
+        run_table1(args)
     elif args.bands:
         run_bands(args)
     else:

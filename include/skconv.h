@@ -244,6 +244,20 @@ int sk_resample(sk_ctx *ctx, const sk_geom *g, const float *d_in, float *d_out, 
                 int64_t map_stride, const double *h_rot, int ring_lo, int ring_hi, int src_ring_hi,
                 void *stream);
 
+/* Plan of a partial-sky field convolved on the polar cap (Sec. 4: a field re-oriented
+ * onto the pole spans few rings).  Writes the rotation M = R_z(phi0) R_y(theta0) that
+ * takes the pole to the field centre (theta0, phi0) (rot9, row-major FP64; resampling by
+ * M moves the field onto the pole, by its transpose back), and four ring indices
+ * (rings4, 0-based, ends exclusive): [0] out_hi -- the cap's output rings [0, out_hi)
+ * reach colatitude radius plus two pixels (every sky pixel of the field has its nearest
+ * rotated centre among them); [1] in_hi -- input rings [0, in_hi) within theta_cut of
+ * those (1e-6 relative margin); [2], [3] sky_lo, sky_hi -- the sky rings that hold the
+ * field (its colatitude band widened by one pixel, clamped to the poles).  With g NULL
+ * only the rotation is written.  Host arithmetic (FP64); no device work.
+ * Errors: SK_EINVAL (rot9 or rings4 NULL, radius <= 0, theta_cut <= 0). */
+int sk_field_plan(const sk_geom *g, double theta0, double phi0, double radius, double theta_cut, double *rot9,
+                  int32_t *rings4);
+
 /* The same resampling planned once: the nearest-centre search depends on the
  * geometry, the rotation and the ring ranges only, so the plan keeps the kept
  * (output, source) pixel pairs (8 bytes each, on the device) and every apply is a

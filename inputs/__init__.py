@@ -115,6 +115,9 @@ WORKLOADS = {
                               (Group(1024, 16, _k(10.0, 1024, 30.0, 4096), 401),)),
     "n8192_plain": Workload("n8192_plain",
                             (Group(8192, 1, _k(2.0, 8192, 5.0, 16384, 16384, 4096), 501),)),
+    # the paper's optimum split for a 7' beam (Sec. 4, Table 1: l_cut 1158, theta_cut 390')
+    # at Planck resolution; ~1.6e5 neighbours per pixel
+    "n2048_table1": Workload("n2048_table1", (Group(2048, 1, KernelSpec(7.0, 4096, 1158, 390.0, 8192), 801),)),
     # wide cut (the ring-pair Fourier form of the belt): 300' windows, ~2.3e4 neighbours per pixel
     "n1024_wide": Workload("n1024_wide", (Group(1024, 1, _k(60.0, 1024, 300.0, 4096), 601),)),
     # a partial-sky field (a disc of FIELD_RADIUS_DEG, ~310 square degrees, the size of the

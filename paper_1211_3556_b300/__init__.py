@@ -106,6 +106,7 @@ def _declare(L):
         "sk_kernel_set_cap_weights": (I, [P, I]),
         "sk_kernel_cap_weight_bytes": (I, [P, ctypes.POINTER(I64)]),
         "sk_kernel_set_belt_form": (I, [P, I]),
+        "sk_field_plan": (I, [P, D, D, D, D, P, P]),
         "sk_kernel_get_config": (I, [P, ctypes.POINTER(I64)]),
         "sk_device_info": (I, [P, ctypes.POINTER(I64)]),
     }
@@ -412,13 +413,19 @@ def convolve_rings(kern: Kernel, x, ring_lo: int, ring_hi: int, out=None, stream
 
 def rotation_to_pole(theta0: float, phi0: float) -> np.ndarray:
     """The rotation M (3x3, FP64) that takes the north pole to the direction (theta0, phi0):
-    M = R_z(phi0) R_y(theta0).  resample(.., M, ..) moves a field centred there onto the
-    pole; resample(.., M.T, ..) moves it back."""
-    ct, st_ = math.cos(theta0), math.sin(theta0)
-    cp, sp = math.cos(phi0), math.sin(phi0)
-    rz = np.array([[cp, -sp, 0.0], [sp, cp, 0.0], [0.0, 0.0, 1.0]])
-    ry = np.array([[ct, 0.0, st_], [0.0, 1.0, 0.0], [-st_, 0.0, ct]])
-    return rz @ ry
+    M = R_z(phi0) R_y(theta0) (sk_field_plan).  resample(.., M, ..) moves a field centred
+    there onto the pole; resample(.., M.T, ..) moves it back."""
+    return field_plan(None, theta0, phi0, 1.0, 1.0)[0]
+
+
+def field_plan(geom, theta0: float, phi0: float, radius: float, theta_cut: float):
+    """(rotation, (out_hi, in_hi, sky_lo, sky_hi)) of a partial-sky field (sk_field_plan);
+    geom None gives the rotation only."""
+    rot = np.empty(9, np.float64)
+    rings = np.zeros(4, np.int32)
+    _check(lib().sk_field_plan(None if geom is None else geom._h, float(theta0), float(phi0), float(radius),
+                               float(theta_cut), rot.ctypes.data, rings.ctypes.data))
+    return rot.reshape(3, 3), tuple(int(v) for v in rings)
 
 
 def resample(geom: Geometry, x, rot, ring_lo: int, ring_hi: int, src_ring_hi: int = None, out=None, stream=None):
@@ -494,29 +501,12 @@ class PolarPatch:
     is radial."""
 
     def __init__(self, kern: Kernel, theta0: float, phi0: float, radius: float):
-        from .bands import ring_table
         self.kern = kern
         g = kern.geom
-        self.rot = rotation_to_pole(theta0, phi0)
-        n, start, theta = ring_table(g.nside)
-        nr = len(n)
-        pix = math.sqrt(4.0 * math.pi / g.npix)
-        # output rings: colatitude up to radius plus two pixels (every sky pixel of the
-        # field has its nearest rotated centre among them)
-        self.out_hi = int(np.searchsorted(theta, radius + 2.0 * pix, side="right"))
-        self.out_hi = max(1, min(self.out_hi, nr))
-        # input rings: within theta_cut of the output rings (margin as for ring bands)
-        reach = theta[self.out_hi - 1] + kern.theta_cut + 1e-6 * max(1.0, kern.theta_cut)
-        self.in_hi = max(self.out_hi, min(nr, int(np.searchsorted(theta, reach, side="right"))))
-        # sky rings that hold the field
-        lo_t, hi_t = theta0 - theta[self.out_hi - 1], theta0 + theta[self.out_hi - 1]
-        self.sky_lo = int(np.searchsorted(theta, lo_t - pix, side="left"))
-        self.sky_hi = int(np.searchsorted(theta, hi_t + pix, side="right"))
-        self.sky_lo, self.sky_hi = max(0, self.sky_lo), min(nr, self.sky_hi)
-        if lo_t <= 0.0:
-            self.sky_lo = 0
-        if hi_t >= math.pi:
-            self.sky_hi = nr
+        # rotation and rings (sk_field_plan): output rings reach the field radius plus two
+        # pixels, input rings theta_cut beyond them, sky rings the field's colatitude band
+        self.rot, (self.out_hi, self.in_hi, self.sky_lo, self.sky_hi) = field_plan(g, theta0, phi0, radius,
+                                                                                   kern.theta_cut)
 
         # the two resamplings, planned once (their searches depend on the geometry only)
         self.to_cap = ResamplePlan(g, self.rot, 0, self.in_hi)

@@ -245,6 +245,16 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         float2 accA[8], accB[8];
 #pragma unroll
         for (int s = 0; s < 8; ++s) { accA[s] = make_float2(0.0f, 0.0f); accB[s] = make_float2(0.0f, 0.0f); }
+        // wide windows (A.ctot): each ring's sums go into the thread's running totals in a
+        // private slice of global scratch (L2-resident; the registers and shared memory are
+        // full), so that the FP32 rounding grows with the terms of one ring and the number of
+        // rings, not with their product
+        const long long ntot = (long long)gridDim.x * blockDim.x;
+        float *const tt = A.ctot ? A.ctot + (long long)blockIdx.x * blockDim.x + threadIdx.x : nullptr;
+        if (tt) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) tt[i * ntot] = 0.0f;
+        }
 
         // ring p's strip into buffer b by bulk copies, unless it wraps; the item's warps
         // take turns (ring p by warp (p - p0) mod 4), and the issuing warp takes lane 0's
@@ -394,6 +404,17 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
                         mac16<LS>(accB, wb, xm, rm, 0);
                     }
                 }
+                if (tt) {
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        tt[(4 * s) * ntot] += accA[s].x;
+                        tt[(4 * s + 1) * ntot] += accA[s].y;
+                        tt[(4 * s + 2) * ntot] += accB[s].x;
+                        tt[(4 * s + 3) * ntot] += accB[s].y;
+                        accA[s] = make_float2(0.0f, 0.0f);
+                        accB[s] = make_float2(0.0f, 0.0f);
+                    }
+                }
             }
         }
         if (NB == 2) {
@@ -406,6 +427,13 @@ k_conv_cap(const __grid_constant__ JobsArg A) {
         if (*abort_flag) continue;
         float *yn = J.y + (long long)map * J.stride + R.start;
         float *ys = J.y + (long long)map * J.stride + J.rings[ro_s].start;
+        if (tt) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                accA[s] = make_float2(tt[(4 * s) * ntot], tt[(4 * s + 1) * ntot]);
+                accB[s] = make_float2(tt[(4 * s + 2) * ntot], tt[(4 * s + 3) * ntot]);
+            }
+        }
         if (actA) store16(yn, ys, jA, jrA, reflA, Qo, accA);
         if (actB) store16(yn, ys, jB, jrB, reflB, Qo, accB);
     }

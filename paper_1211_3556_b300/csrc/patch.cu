@@ -358,3 +358,59 @@ extern "C" int sk_resample_plan_apply(const sk_resample_plan *p, const float *d_
     }
     return SK_OK;
 }
+
+// Colatitude of ring r (0-based) of the RING scheme (Sec. 2's pixelisation), FP64.
+static double ring_theta(long long N, int r) {
+    const long long i = r + 1;
+    double z;
+    if (i < N) z = 1.0 - (double)(i * i) / (3.0 * (double)N * (double)N);
+    else if (i <= 3 * N) z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * (double)N);
+    else {
+        const long long ii = 4 * N - i;
+        z = -(1.0 - (double)(ii * ii) / (3.0 * (double)N * (double)N));
+    }
+    return acos(fmin(1.0, fmax(-1.0, z)));
+}
+
+extern "C" int sk_field_plan(const sk_geom *g, double theta0, double phi0, double radius, double theta_cut,
+                             double *rot9, int32_t *rings4) {
+    if (!rot9 || !rings4) return sk_fail(SK_EINVAL, "sk_field_plan: NULL argument");
+    if (!(radius > 0.0) || !(theta_cut > 0.0)) return sk_fail(SK_EINVAL, "sk_field_plan: radius and theta_cut > 0");
+    const double ct = cos(theta0), st = sin(theta0), cp = cos(phi0), sp = sin(phi0);
+    // R_z(phi0) R_y(theta0)
+    const double m[9] = {cp * ct, -sp, cp * st, sp * ct, cp, sp * st, -st, 0.0, ct};
+    for (int i = 0; i < 9; ++i) rot9[i] = m[i];
+    if (!g) return SK_OK;
+    const int nr = g->nr;
+    const long long N = g->nside;
+    const double pix = sqrt(4.0 * SK_PI / (double)g->npix);
+    // the first ring whose colatitude exceeds t (rings are in increasing colatitude)
+    auto upper = [&](double t) {
+        int lo = 0, hi = nr;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (ring_theta(N, mid) <= t) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    auto lower = [&](double t) {          // the first ring whose colatitude is at least t
+        int lo = 0, hi = nr;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (ring_theta(N, mid) < t) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    int out_hi = std::max(1, std::min(upper(radius + 2.0 * pix), nr));
+    const double reach = ring_theta(N, out_hi - 1) + theta_cut + 1e-6 * std::max(1.0, theta_cut);
+    int in_hi = std::max(out_hi, std::min(nr, upper(reach)));
+    const double lo_t = theta0 - ring_theta(N, out_hi - 1), hi_t = theta0 + ring_theta(N, out_hi - 1);
+    int sky_lo = std::max(0, lower(lo_t - pix)), sky_hi = std::min(nr, upper(hi_t + pix));
+    if (lo_t <= 0.0) sky_lo = 0;
+    if (hi_t >= SK_PI) sky_hi = nr;
+    rings4[0] = out_hi;
+    rings4[1] = in_hi;
+    rings4[2] = sky_lo;
+    rings4[3] = sky_hi;
+    return SK_OK;
+}

@@ -670,13 +670,25 @@ static size_t tc_plane_bytes(const SkJob &j) {
     return ((size_t)j.batch * k->tc_nz * 4 * k->tc_zrows * sizeof(float4) + 255) & ~(size_t)255;
 }
 
+// Running totals of the evaluating cap launches of wide-window jobs: one slice per
+// stream (narrow and polar launches run concurrently), each for up to 2048 threads per SM.
+static size_t ctot_bytes(const SkJob *jobs, int n, int path) {
+    if (path == SK_PATH_GENERAL) return 0;
+    for (int i = 0; i < n; ++i) {
+        const sk_kern *k = jobs[i].k;
+        if (k->plan_ok && k->blocked && !k->d_capw && jobs[i].batch > 0)
+            return (size_t)2 * k->ctx->num_sms * 2048 * 32 * sizeof(float);
+    }
+    return 0;
+}
+
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path) {
     size_t b = 0;
     for (int i = 0; i < n; ++i) {
         b += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
         if (sk_job_wants_tc(jobs[i], path)) b += tc_plane_bytes(jobs[i]);
     }
-    return b;
+    return b + ctot_bytes(jobs, n, path);
 }
 
 // ---------------------------------------------------------------------------
@@ -1049,9 +1061,22 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             int rc = flush();
             if (rc) return rc;
         }
-    // jobs whose caps evaluate their weights: one launch family per (strip class, mode)
+    // jobs whose caps evaluate their weights: one launch family per (strip class, mode,
+    // summation); wide-window jobs sum ring by ring into the running totals at the end of
+    // the workspace (after the tensor planes), one half per stream
+    float *ctot = nullptr;
+    if (ctot_bytes(jobs, n, path)) {
+        char *p = (char *)ws;
+        for (int i = 0; i < n; ++i) {
+            p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
+            if (sk_job_wants_tc(jobs[i], path)) p += tc_plane_bytes(jobs[i]);
+        }
+        ctot = (float *)p;
+    }
+    const long long ctot_half = (long long)ctx->num_sms * 2048 * 32;
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
-        for (int mode = 0; mode < 8; ++mode) {
+        for (int mode = 0; mode < 8; ++mode)
+        for (int blk = 0; blk < 2; ++blk) {
             const int v = mode & 1;
             Batcher b;
             auto flush = [&]() -> int {
@@ -1069,6 +1094,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                     ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
                     SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));
                     b.a.queue = q;
+                    b.a.ctot = blk ? ctot + (v ? 0 : ctot_half) : nullptr;
+                    // at most 2048 threads per SM: the totals' slice holds every thread of the grid
                     SK_CU(sk_launch_conv_cap(b.a, SK_CAP_LS[c], mode, grid_for(blocks, per, ctx->num_sms), cs));
                     sk_prof_end(ctx, v ? "conv_cap" : "conv_cap_polar", ev, cs);
                 }
@@ -1081,6 +1108,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
                 const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
                 const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
                 if (!k->plan_ok || k->d_capw || cn == 0 || jobs[i].batch == 0) continue;
+                if ((int)(k->blocked && ctot) != blk) continue;
                 const int kmode = v | (k->kp.small_angle ? 2 : 0) | (k->layout == SK_NODES_BIASED ? 4 : 0);
                 if (kmode != mode) continue;
                 // one node table per launch (the blocks load it once)

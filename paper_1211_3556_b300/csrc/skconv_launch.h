@@ -71,6 +71,8 @@ struct JobsArg {
     int total;            // flat items over all jobs
     int *status;          // device status word
     int *queue;           // work-queue counter (zero at launch) of kernels that take items dynamically
+    float *ctot;          // evaluating caps of wide-window operators: per-thread running totals,
+                          // [32][gridDim.x blockDim.x] floats (null: plain accumulation)
     JobDesc j[SK_MAXJ];
 };
 

@@ -144,3 +144,23 @@ def test_wide_workload_sampled_outputs(sk):
     xs = x[0].astype(np.float64)
     assert rms_rel(y[zone], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=zone)) <= RMS_BOUND
     assert rms_rel(y[other], O.conv_window(grp.nside, V, ks.theta_cut, 0, xs, outs=other)) <= RMS_BOUND
+
+
+def test_table1_point_sampled_outputs(sk):
+    # Sec. 4, Table 1's optimum split for a 7' beam at Planck resolution (l_cut 1158,
+    # theta_cut 390', Nside 2048): the real-space part by the ring-pair Fourier zone and the
+    # direct sums elsewhere, on sampled outputs against the oracle
+    import torch
+    from inputs import WORKLOADS, make_maps, sample_indices
+    grp = WORKLOADS["n2048_table1"].groups[0]
+    ks = grp.kernel
+    g = sk.Geometry(sk._ctx, grp.nside)
+    k, V = sk.Kernel.from_legendre(g, ks.beam(), ks.lcut + 1, ks.lmax, ks.n_nodes, ks.theta_cut, ks.layout)
+    f = sk.FourierBelt(k)
+    x = make_maps(grp)
+    y = f.apply(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)[0]
+    sk._ctx.status()
+    del f
+    outs = sample_indices(g.npix, 240, 803)
+    yo = O.conv_window(grp.nside, np.asarray(V, np.float64), ks.theta_cut, ks.layout, x[0].astype(np.float64), outs)
+    assert rms_rel(y[outs], yo) <= RMS_BOUND
