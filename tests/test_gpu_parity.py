@@ -510,3 +510,29 @@ def test_pair_counts_by_launch_add_up(sk):
         assert sum(by_launch) == k.count_pairs() == sum(by_path)
         assert by_launch[0] == by_path[0] and by_launch[1] + by_launch[2] == by_path[1]
         assert by_launch[3] == by_path[2]
+
+
+# ------------------------------------------------------------------ non-finite inputs
+
+@pytest.mark.parametrize("path", [0, 2, 3])
+def test_non_finite_input_stays_local(sk, path):
+    # The sums multiply some pixels just outside an output's window by an exact zero (the
+    # union windows of the caps and of the FP32 belt's ring pairs, the tensor belt's
+    # 16-ring tiles), so a NaN input reaches a few outputs beyond its cut -- but no output
+    # farther than theta_cut plus 20 pixel sizes, and every other output is bit-identical
+    # to the run without it
+    import torch
+    nside, tc = 128, 0.03
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 384, 96, tc, 2048)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc)
+    x = white_noise_maps(nside, 1, 1601)
+    vec = O.all_vecs(nside)
+    reach = math.cos(tc + 20.0 * math.sqrt(4.0 * math.pi / x.shape[1]))
+    for p in (5, 12 * nside * nside // 2 + 7, 12 * nside * nside - 3):     # cap, belt, south cap
+        xn = x.copy()
+        xn[0, p] = np.nan
+        y = gpu_conv(sk, k, x, path)
+        yn = gpu_conv(sk, k, xn, path)
+        far = vec @ vec[p] < reach
+        assert np.isnan(yn[0, p])
+        assert np.array_equal(yn[0, far], y[0, far])
