@@ -189,7 +189,9 @@ int sk_count_pairs_by_launch(sk_ctx *ctx, const sk_kern *k, int64_t *out4);
  * d_in, d_out: [batch][map_stride] FP32 device buffers.  batch >= 0 (0 is a
  * no-op).  Inputs should be finite: some sums multiply pixels just outside an
  * output's window by a zero weight, so a NaN or Inf can reach outputs beyond its
- * cut.  Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+ * cut -- within theta_cut plus a few pixels of it (the union windows of the caps and
+ * of the belt's ring pairs, the tensor belt's 16-ring tiles); farther outputs are
+ * unaffected.  Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int sk_convolve(sk_ctx *ctx, const sk_kern *k, const float *d_in, float *d_out,
                 int64_t batch, int64_t map_stride, void *stream);
 
