@@ -65,10 +65,15 @@ extern "C" {
                                /* group x input ring weight tiles against 8-pixel segments of  */
                                /* the maps; caps stay FP32) where the operator has that form   */
 #define SK_PATH_FP32       3   /* as AUTO, with the belt on the FP32 CUDA-core kernel          */
+#define SK_PATH_BF16X3     4   /* as SK_PATH_TENSOR with BF16x3 products (BF16 hi/lo parts,    */
+                               /* three kind::f16 MMAs): ~1e-5 relative, NOT within 1e-6      */
 
 /* Belt forms of an operator (sk_kernel_set_belt_form). */
 #define SK_BELT_FP32       0   /* FP32 FMAs, ring-pair weight rows streamed with the strips   */
 #define SK_BELT_TENSOR     1   /* 3xTF32 tcgen05 MMAs (stored weight tiles, per-call map planes) */
+#define SK_BELT_BF16X3     2   /* the same with BF16x3 products: about twice the MMA rate, ~1e-5 */
+                               /* relative error (outside the 1e-6 bound; never chosen by the    */
+                               /* autotuner)                                                     */
 
 typedef struct sk_ctx  sk_ctx;
 typedef struct sk_geom sk_geom;
@@ -394,18 +399,19 @@ int sk_device_info(sk_ctx *ctx, int64_t *out4);
 int sk_kernel_set_tiles(sk_kern *k, int belt_p, int cap_t);
 int sk_kernel_get_tiles(const sk_kern *k, int *belt_p, int *cap_t);
 
-/* Belt form of operator k used by SK_PATH_AUTO: SK_BELT_FP32 (the default) or
- * SK_BELT_TENSOR.  Choosing the tensor form evaluates its stored weight tiles
- * (synchronises the device; they follow later table updates).  Not safe while a
- * launch with k is being issued from another thread.
- * Errors: SK_EINVAL (bad form, or the operator has no tensor form: no belt, a
- * ring shorter than 128 pixels, or windows wider than 64 - 7 offsets),
+/* Belt form of operator k used by SK_PATH_AUTO: SK_BELT_FP32 (the default),
+ * SK_BELT_TENSOR or SK_BELT_BF16X3.  Choosing a tensor form evaluates its stored
+ * weight tiles (synchronises the device; they follow later table updates).  Not safe
+ * while a launch with k is being issued from another thread.
+ * Errors: SK_EINVAL (bad form, or the operator has no such form: no belt, a ring
+ * shorter than 128 pixels, or windows wider than the form's 64-column tiles allow),
  * SK_ENOMEM (the tiles do not fit), SK_ECUDA. */
 int sk_kernel_set_belt_form(sk_kern *k, int form);
 
 /* The operator's tuned settings: out4[0] = belt tile width P of the FP32 form,
  * out4[1] = belt form (SK_BELT_*), out4[2] = 1 if the cap weights are stored,
- * out4[3] = 1 if the operator has a tensor belt form.  Errors: SK_EINVAL. */
+ * out4[3] = bit 0: the operator has the 3xTF32 tensor form, bit 1: the BF16x3 form.
+ * Errors: SK_EINVAL. */
 int sk_kernel_get_config(const sk_kern *k, int64_t *out4);
 
 /* Autotuner: times, on the caller's maps (d_in -> d_out, `batch` maps), every
@@ -446,6 +452,14 @@ int sk_selftest_tc_gemm(sk_ctx *ctx, const float *d_a, const float *d_b, float *
  * of 8 in [8, 64], off 0 or 4.  Errors: SK_EINVAL, SK_ECUDA. */
 int sk_selftest_tc_sliding(sk_ctx *ctx, const float *d_a, const float *d_x, float *d_d, int n, int k, int off,
                            void *stream);
+
+/* The same product in the BF16x3 form of the tensor-core belt: A and x split into BF16
+ * hi/lo parts, three kind::f16 MMAs of K = 16 per k-step, x read as sliding rows of one
+ * plane of 8-value (16-byte) rows.  D[r][s] = sum_{k < K} A[r][k] x[8 s + k]; x at least
+ * 8 (n + k/8) floats; n a multiple of 16 in [16, 256], k a multiple of 16 in [16, 64].
+ * Errors: SK_EINVAL, SK_ECUDA. */
+int sk_selftest_tc_sliding_bf16(sk_ctx *ctx, const float *d_a, const float *d_x, float *d_d, int n, int k,
+                                void *stream);
 
 /* ---- harmonic half of the split (Sec. 2, Eq. 1: the l <= l_cut part) ----
  *

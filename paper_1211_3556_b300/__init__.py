@@ -24,8 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libskconv.so")
 
 SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 NODES_UNIFORM, NODES_BIASED = 0, 1
-PATH_AUTO, PATH_GENERAL, PATH_TENSOR, PATH_FP32 = 0, 1, 2, 3
-BELT_FP32, BELT_TENSOR = 0, 1
+PATH_AUTO, PATH_GENERAL, PATH_TENSOR, PATH_FP32, PATH_BF16X3 = 0, 1, 2, 3, 4
+BELT_FP32, BELT_TENSOR, BELT_BF16X3 = 0, 1, 2
 PEAK_FFMA, PEAK_FFMA2, PEAK_TF32 = 0, 1, 2
 
 _ERRNAMES = {SK_EINVAL: "SK_EINVAL", SK_ENOMEM: "SK_ENOMEM", SK_ECUDA: "SK_ECUDA",
@@ -90,6 +90,7 @@ def _declare(L):
         "sk_selftest_wait_timeout": (I, [P, D, P]),
         "sk_selftest_tc_gemm": (I, [P, P, P, P, I, I, I, P]),
         "sk_selftest_tc_sliding": (I, [P, P, P, P, I, I, I, P]),
+        "sk_selftest_tc_sliding_bf16": (I, [P, P, P, P, I, I, P]),
         "sk_kernel_get_tiles": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sk_kernel_response": (I, [P, P, I, P]),
         "sk_fit_real_kernel": (I, [P, P, I, I, D, I, I, D, D, P, P]),
@@ -338,7 +339,8 @@ class Kernel:
         return p.value
 
     def set_belt_form(self, form: int):
-        """Belt of PATH_AUTO: BELT_FP32 or BELT_TENSOR (evaluates the tensor form's tiles)."""
+        """Belt of PATH_AUTO: BELT_FP32, BELT_TENSOR (3xTF32) or BELT_BF16X3 (about 1e-5
+        relative: outside the 1e-6 bound); a tensor form evaluates its tiles."""
         _check(lib().sk_kernel_set_belt_form(self._h, int(form)))
 
     def config(self) -> dict:
@@ -346,8 +348,10 @@ class Kernel:
         whether it has a tensor belt form."""
         a = (ctypes.c_int64 * 4)()
         _check(lib().sk_kernel_get_config(self._h, a))
-        return {"belt_p": int(a[0]), "belt_form": "tensor" if a[1] == BELT_TENSOR else "fp32",
-                "cap_weights": "stored" if a[2] else "evaluated", "tensor_form_available": bool(a[3])}
+        return {"belt_p": int(a[0]), "belt_form": {BELT_FP32: "fp32", BELT_TENSOR: "tensor",
+                                                   BELT_BF16X3: "bf16x3"}[int(a[1])],
+                "cap_weights": "stored" if a[2] else "evaluated", "tensor_form_available": bool(a[3] & 1),
+                "bf16x3_form_available": bool(a[3] & 2)}
 
     def set_cap_weights(self, stored: bool):
         """Keep the caps' weights stored on the device (True) or evaluate them per call (False)."""

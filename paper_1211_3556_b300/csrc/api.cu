@@ -425,10 +425,11 @@ extern "C" int sk_kernel_update_values(sk_kern *k, const double *h_values) {
         int rc = sk_beltw_build(k);                 // and the stored belt rows
         if (rc) return rc;
     }
-    if (k->d_tca) {
-        int rc = sk_tca_build(k);                   // and the tensor-core belt's tiles
-        if (rc) return rc;
-    }
+    for (int f = 0; f < 2; ++f)
+        if (k->tcp[f].d_A) {
+            int rc = sk_tca_build(k, f);            // and the tensor-core belt's tiles
+            if (rc) return rc;
+        }
     SK_CU(cudaDeviceSynchronize());
     return SK_OK;
 }
@@ -444,10 +445,11 @@ extern "C" int sk_kernel_update_values_async(sk_kern *k, const double *d_values,
         int rc = sk_beltw_build(k, st, k->d_changed);
         if (rc) return rc;
     }
-    if (k->d_tca) {
-        int rc = sk_tca_build(k, st, k->d_changed);
-        if (rc) return rc;
-    }
+    for (int f = 0; f < 2; ++f)
+        if (k->tcp[f].d_A) {
+            int rc = sk_tca_build(k, f, st, k->d_changed);
+            if (rc) return rc;
+        }
     if (k->d_capw) return sk_capw_build(k, false, st, k->d_changed);
     return SK_OK;
 }
@@ -472,21 +474,22 @@ extern "C" int sk_kernel_set_cap_weights(sk_kern *k, int stored) {
 }
 
 extern "C" int sk_kernel_set_belt_form(sk_kern *k, int form) {
-    if (!k || (form != SK_BELT_FP32 && form != SK_BELT_TENSOR))
+    if (!k || (form != SK_BELT_FP32 && form != SK_BELT_TENSOR && form != SK_BELT_BF16X3))
         return sk_fail(SK_EINVAL, "sk_kernel_set_belt_form: bad argument");
     if (form == SK_BELT_FP32) {
         k->belt_form = form;
         return SK_OK;
     }
-    if (!k->tc_ok) return sk_fail(SK_EINVAL, "sk_kernel_set_belt_form: the operator has no tensor belt form");
+    const int f = form == SK_BELT_BF16X3 ? 1 : 0;
+    TcPlan &T = k->tcp[f];
+    if (!T.ok) return sk_fail(SK_EINVAL, "sk_kernel_set_belt_form: the operator has no such tensor belt form");
     SK_CU(cudaSetDevice(k->ctx->device));
-    if (!k->d_tca) {
-        int rc = sk_tca_build(k);
+    if (!T.d_A) {
+        int rc = sk_tca_build(k, f);
         if (rc) return rc;
         SK_CU(cudaDeviceSynchronize());
-        if (!k->d_tca)
-            return sk_fail(SK_ENOMEM, "sk_kernel_set_belt_form: %lld KB of weight tiles do not fit",
-                           (long long)k->tca_kb);
+        if (!T.d_A)
+            return sk_fail(SK_ENOMEM, "sk_kernel_set_belt_form: %lld KB of weight tiles do not fit", (long long)T.kb);
     }
     k->belt_form = form;
     return SK_OK;
@@ -497,7 +500,7 @@ extern "C" int sk_kernel_get_config(const sk_kern *k, int64_t *out4) {
     out4[0] = k->belt_P;
     out4[1] = k->belt_form;
     out4[2] = k->d_capw ? 1 : 0;
-    out4[3] = k->tc_ok ? 1 : 0;
+    out4[3] = (k->tcp[0].ok ? 1 : 0) | (k->tcp[1].ok ? 2 : 0);
     return SK_OK;
 }
 
@@ -605,7 +608,8 @@ extern "C" int sk_convolve_path(sk_ctx *ctx, const sk_kern *k, const float *d_in
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve: NULL context");
     int rc = sk_check_maps("sk_convolve", k, d_in, d_out, batch, map_stride);
     if (rc) return rc;
-    if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL && path != SK_PATH_TENSOR && path != SK_PATH_FP32)
+    if (path != SK_PATH_AUTO && path != SK_PATH_GENERAL && path != SK_PATH_TENSOR && path != SK_PATH_FP32 &&
+        path != SK_PATH_BF16X3)
         return sk_fail(SK_EINVAL, "unknown path %d", path);
     if (batch == 0) return SK_OK;
     SK_CU(cudaSetDevice(ctx->device));
@@ -783,7 +787,8 @@ static int convert_jobs(const sk_job *jobs, int n, std::vector<SkJob> &out) {
 
 extern "C" int sk_convolve_jobs(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int flags, void *stream) {
     if (!ctx) return sk_fail(SK_EINVAL, "sk_convolve_jobs: NULL context");
-    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR && flags != SK_PATH_FP32)
+    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR && flags != SK_PATH_FP32 &&
+        flags != SK_PATH_BF16X3)
         return sk_fail(SK_EINVAL, "unknown flags %d", flags);
     std::vector<SkJob> js;
     int rc = convert_jobs(jobs, n_jobs, js);
@@ -805,7 +810,8 @@ extern "C" int sk_graph_capture(sk_ctx *ctx, const sk_job *jobs, int n_jobs, int
                                 void **graph_exec) {
     if (!ctx || !graph_exec) return sk_fail(SK_EINVAL, "sk_graph_capture: NULL argument");
     *graph_exec = nullptr;
-    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR && flags != SK_PATH_FP32)
+    if (flags != SK_PATH_AUTO && flags != SK_PATH_GENERAL && flags != SK_PATH_TENSOR && flags != SK_PATH_FP32 &&
+        flags != SK_PATH_BF16X3)
         return sk_fail(SK_EINVAL, "unknown flags %d", flags);
     if (!stream) return sk_fail(SK_EINVAL, "sk_graph_capture: capture needs a non-default stream");
     std::vector<SkJob> js;

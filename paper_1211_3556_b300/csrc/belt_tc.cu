@@ -34,6 +34,10 @@
 // near 1.1e-6 against the FP32 path at Nside 2048, per-tile partial sums 3.6e-7.
 // A chunk also keeps each hand-over of an accumulator longer than its round trip
 // (single tiles at the window's edge are one k-step).
+// The BF16x3 form (SK_BELT_BF16X3) is the same pipeline with BF16 hi/lo parts and
+// kind::f16 MMAs of K = 16: half the MMAs, about 1e-5 relative error (16 significant
+// bits per operand), outside the 1e-6 bound -- reported beside 3xTF32, never chosen by
+// the autotuner.
 // Warp roles: 0 producer (bulk copies), 1 MMA issuer, 2..9 epilogue (tensor
 // memory -> registers -> outputs).  Every wait is bounded and records
 // SK_ETIMEOUT.
@@ -53,16 +57,17 @@ constexpr int NEPI = 8;                // epilogue warps
 constexpr int NT = 32 * (2 + NEPI);
 constexpr unsigned long long LIMIT = 2000000000ull;
 
-// One pipeline stage: A (hi then lo, K x 512 bytes each, room for kmax), then two
-// hi and two lo plane slots of `slot` bytes (nn + kmax/8 rows of 16 bytes).
+// One pipeline stage: A (hi then lo, K x 512 bytes each for TF32, K x 256 for BF16,
+// room for kmax), then the plane slots of `slot` bytes (nn + kmax/8 rows of 16 bytes):
+// two hi and two lo for 3xTF32, one hi and one lo for BF16x3.
 struct Stage {
     uint32_t a_bytes, slot, bytes;
 };
-__host__ __device__ inline Stage stage_of(int kmax, int nn) {
+__host__ __device__ inline Stage stage_of(int kmax, int nn, bool bf) {
     Stage s;
-    s.a_bytes = 2u * (uint32_t)kmax * 512u;
+    s.a_bytes = 2u * (uint32_t)kmax * (bf ? 256u : 512u);
     s.slot = (uint32_t)(nn + kmax / 8) * 16u;
-    s.bytes = (s.a_bytes + 4u * s.slot + 1023u) & ~1023u;
+    s.bytes = (s.a_bytes + (bf ? 2u : 4u) * s.slot + 1023u) & ~1023u;
     return s;
 }
 
@@ -74,6 +79,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
     return false;
 }
 
+// BF: the BF16x3 form -- BF16 hi/lo parts, K = 16 per MMA (kind::f16), one plane of
+// 8-pixel rows per part: B_q[s][t] = rows s + 2q and s + 2q + 1 of the plane, a start
+// address 32 q bytes in with 16 bytes between the two core matrices along K.
+template <bool BF>
 __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArgs T) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -87,8 +96,10 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
     volatile int *abort_flag = &abort_s;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int S = T.nstages;
-    const Stage L = stage_of(T.kmax, T.nn);
+    const Stage L = stage_of(T.kmax, T.nn, BF);
     const int per_g = T.batch * T.nblk;
+    constexpr int NPL = BF ? 2 : 4;                 // planes per map ring
+    constexpr uint32_t APART = BF ? 256u : 512u;    // bytes of one part of A per column
 
     if (warp == 0) tc::tmem_alloc(&tslot, 512);
     if (t == 0) {
@@ -117,7 +128,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                 const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
                 const int j0 = pb * 8 * T.nn;
                 const int2 tr = T.trng[g];
-                const float4 *zb = T.Z + (size_t)b * T.nz * 4 * T.zrows;
+                const float4 *zb = T.Z + (size_t)b * T.nz * NPL * T.zrows;
                 for (int u = 0; u < tr.y; ++u, ++cnt) {
                     const int4 tl = T.tiles[tr.x + u];            // (input ring, E0, K | flags, A offset in KB)
                     const int s = (int)(cnt % (uint32_t)S);
@@ -126,13 +137,22 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                         break;
                     const int K = tl.z & SK_TC_K_MASK;
                     const uint32_t rbytes = (uint32_t)(T.nn + K / 8 - 1) * 16u;
-                    const int u0 = (j0 + tl.y - T.pbase) >> 2;    // 4-pixel row of the first column
-                    const int m0 = u0 >> 1;
-                    const float4 *zr = zb + (size_t)(tl.x - T.zi0) * 4 * T.zrows;
+                    const float4 *zr = zb + (size_t)(tl.x - T.zi0) * NPL * T.zrows;
                     unsigned char *sb = base + (size_t)s * L.bytes;
                     const uint32_t bar = tc::smem_u32(&full_bar[s]);
-                    tc::mbar_expect_tx(bar, (uint32_t)K * 1024u + 4u * rbytes);
-                    tc::bulk_g2s(tc::smem_u32(sb), T.A + (size_t)tl.w * 1024, (uint32_t)K * 1024u, bar);
+                    const uint32_t abytes = 2u * (uint32_t)K * APART;
+                    tc::mbar_expect_tx(bar, abytes + (uint32_t)(NPL * rbytes));
+                    tc::bulk_g2s(tc::smem_u32(sb), T.A + (size_t)tl.w * 1024, abytes, bar);
+                    if constexpr (BF) {
+                        // 8-pixel row of the first column; the hi and lo planes in turn
+                        const int m0 = (j0 + tl.y - T.pbase) >> 3;
+                        const uint32_t sl = tc::smem_u32(sb + L.a_bytes);
+                        tc::bulk_g2s(sl, zr + m0, rbytes, bar);
+                        tc::bulk_g2s(sl + L.slot, zr + T.zrows + m0, rbytes, bar);
+                        continue;
+                    }
+                    const int u0 = (j0 + tl.y - T.pbase) >> 2;    // 4-pixel row of the first column
+                    const int m0 = u0 >> 1;
                     for (int h = 0; h < 2; ++h) {                 // hi, lo parts
                         const float4 *pe = zr + (size_t)(2 * h) * T.zrows, *po = pe + T.zrows;
                         const uint32_t sl = tc::smem_u32(sb + L.a_bytes + 2u * (uint32_t)h * L.slot);
@@ -154,7 +174,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             uint32_t cnt = 0, ccnt = 0;                           // tiles, chunks
-            const uint32_t idesc = tc::idesc_tf32(128, T.nn);
+            const uint32_t idesc = BF ? tc::idesc_bf16(128, T.nn) : tc::idesc_tf32(128, T.nn);
             for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
                 const int2 tr = T.trng[f / per_g];
                 for (int u = 0; u < tr.y; ++u, ++cnt) {
@@ -169,10 +189,22 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                     tc::fence_after_sync();
                     const int K = tl.z & SK_TC_K_MASK;
                     const uint32_t sb = tc::smem_u32(base + (size_t)s * L.bytes);
-                    const uint32_t a_hi = sb, a_lo = sb + (uint32_t)K * 512u;
-                    const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + 2u * L.slot;
+                    const uint32_t a_hi = sb, a_lo = sb + (uint32_t)K * APART;
                     const uint32_t d = taddr + 256u * (uint32_t)ab;
-                    for (int q = 0; q < K / 8; ++q) {
+                    if constexpr (BF) {
+                        const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + L.slot;
+                        for (int q = 0; q < K / 16; ++q) {
+                            const uint64_t ah = tc::kmajor_desc(a_hi + 4096u * q, 2048, 128);
+                            const uint64_t al = tc::kmajor_desc(a_lo + 4096u * q, 2048, 128);
+                            const uint64_t bh = tc::kmajor_desc(b_hi + 32u * q, 16, 128);
+                            const uint64_t bl = tc::kmajor_desc(b_lo + 32u * q, 16, 128);
+                            tc::mma_bf16(d, ah, bh, idesc, (first && q == 0) ? 0 : 1);
+                            tc::mma_bf16(d, ah, bl, idesc, 1);
+                            tc::mma_bf16(d, al, bh, idesc, 1);
+                        }
+                    }
+                    const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + 2u * L.slot;
+                    for (int q = 0; !BF && q < K / 8; ++q) {
                         const uint64_t ah = tc::kmajor_desc(a_hi + 4096u * q, 2048, 128);
                         const uint64_t al = tc::kmajor_desc(a_lo + 4096u * q, 2048, 128);
                         const uint64_t bh = tc::kmajor_desc(b_hi + 16u * q, L.slot, 128);
@@ -260,16 +292,17 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
 }
 
 // One block per tile: A_i[(o, n)][k] = w(o, i, k - n + E0) for the group's rings,
-// zero outside each ring's window, split into TF32 hi and lo parts and written in
-// the no-swizzle K-major image the MMA reads (kmajor128_offset; lo K x 512 bytes
-// after hi).  The weight is the FP32 belt's (pair_weight of the same half-angle).
+// zero outside each ring's window, split into TF32 (or BF16) hi and lo parts and
+// written in the no-swizzle K-major image the MMA reads (kmajor128_offset(_bf16); lo
+// K x 512 (256) bytes after hi).  The weight is the FP32 belt's (pair_weight of the
+// same half-angle).
 __global__ void k_tc_tiles(const __grid_constant__ TcTileArgs T, const int *gate) {
     if (gate && !*gate) return;                      // table unchanged: the tiles stand
     const int tile = blockIdx.x;
     const int4 tl = T.tiles[tile];
     const int g = T.tile_group[tile];
     const int K = tl.z & SK_TC_K_MASK;
-    unsigned char *hi = T.A + (size_t)tl.w * 1024, *lo = hi + (size_t)K * 512;
+    unsigned char *hi = T.A + (size_t)tl.w * 1024, *lo = hi + (size_t)K * (T.bf16 ? 256 : 512);
     const double half_step = SK_PI / (2.0 * (double)T.n4);
     for (int idx = threadIdx.x; idx < 128 * K; idx += blockDim.x) {
         const int row = idx / K, k = idx - row * K;
@@ -290,19 +323,26 @@ __global__ void k_tc_tiles(const __grid_constant__ TcTileArgs T, const int *gate
                 }
             }
         }
-        float h, l;
-        tc::split_tf32(v, h, l);
-        *reinterpret_cast<float *>(hi + tc::kmajor128_offset(row, k)) = h;
-        *reinterpret_cast<float *>(lo + tc::kmajor128_offset(row, k)) = l;
+        if (T.bf16) {
+            uint16_t h, l;
+            tc::split_bf16(v, h, l);
+            *reinterpret_cast<uint16_t *>(hi + tc::kmajor128_offset_bf16(row, k)) = h;
+            *reinterpret_cast<uint16_t *>(lo + tc::kmajor128_offset_bf16(row, k)) = l;
+        } else {
+            float h, l;
+            tc::split_tf32(v, h, l);
+            *reinterpret_cast<float *>(hi + tc::kmajor128_offset(row, k)) = h;
+            *reinterpret_cast<float *>(lo + tc::kmajor128_offset(row, k)) = l;
+        }
     }
 }
 
 // Planes of the maps' belt input rings: for map b, ring zi0 + ri and row m, the
-// pixels pbase + 8m .. + 7 (wrapped around the ring) split into TF32 hi and lo
-// parts, stored as four planes of float4 rows: hi even (first four pixels), hi odd,
-// lo even, lo odd.
+// pixels pbase + 8m .. + 7 (wrapped around the ring) split into hi and lo parts:
+// 3xTF32 four planes of 16-byte rows -- hi even (first four pixels), hi odd, lo even,
+// lo odd; BF16x3 two planes of 16-byte rows (eight BF16 values) -- hi, lo.
 __global__ void k_tc_planes(const float *__restrict__ x, long long stride, const RingDev *__restrict__ rings, int zi0,
-                            int nz, int zrows, int pbase, int n4, long long total, float4 *__restrict__ Z) {
+                            int nz, int zrows, int pbase, int n4, long long total, float4 *__restrict__ Z, bool bf) {
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(idx % zrows);
@@ -318,6 +358,21 @@ __global__ void k_tc_planes(const float *__restrict__ x, long long stride, const
             int q = p + u;
             if (q >= n4) q -= n4;
             v[u] = xr[q];
+        }
+        if (bf) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                uint16_t h0, l0, h1, l1;
+                tc::split_bf16(v[2 * u], h0, l0);
+                tc::split_bf16(v[2 * u + 1], h1, l1);
+                h[u] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                l[u] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+            uint4 *zr = reinterpret_cast<uint4 *>(Z + (size_t)(b * nz + ri) * 2 * zrows);
+            zr[m] = make_uint4(h[0], h[1], h[2], h[3]);
+            zr[zrows + m] = make_uint4(l[0], l[1], l[2], l[3]);
+            continue;
         }
         float4 he, ho, le, lo;
         tc::split_tf32(v[0], he.x, le.x);
@@ -338,8 +393,8 @@ __global__ void k_tc_planes(const float *__restrict__ x, long long stride, const
 
 }  // namespace
 
-int sk_tc_stages(int kmax, int nn, size_t *smem) {
-    const Stage L = stage_of(kmax, nn);
+int sk_tc_stages(int kmax, int nn, bool bf16, size_t *smem) {
+    const Stage L = stage_of(kmax, nn, bf16);
     const size_t avail = (size_t)220 * 1024 - 1024;
     int S = (int)std::min<size_t>(SK_TC_MAX_STAGES, avail / L.bytes);
     if (S < 2) return 0;
@@ -351,10 +406,16 @@ int sk_tc_stages(int kmax, int nn, size_t *smem) {
 cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st) {
     if (a.total <= 0) return cudaSuccess;
     size_t smem = 0;
-    if (sk_tc_stages(a.kmax, a.nn, &smem) != a.nstages) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_belt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_belt_tc<<<grid, NT, smem, st>>>(a);
+    if (sk_tc_stages(a.kmax, a.nn, a.bf16 != 0, &smem) != a.nstages) return cudaErrorInvalidValue;
+    if (a.bf16) {
+        cudaError_t e = cudaFuncSetAttribute(k_belt_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_belt_tc<true><<<grid, NT, smem, st>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_belt_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_belt_tc<false><<<grid, NT, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -365,10 +426,10 @@ cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st
 }
 
 cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
-                                int zrows, int pbase, int n4, float4 *Z, int sms, cudaStream_t st) {
+                                int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms, cudaStream_t st) {
     const long long total = (long long)batch * nz * zrows;
     if (total <= 0) return cudaSuccess;
     const long long blocks = std::min<long long>((total + 255) / 256, (long long)sms * 16);
-    k_tc_planes<<<(unsigned)blocks, 256, 0, st>>>(x, stride, rings, zi0, nz, zrows, pbase, n4, total, Z);
+    k_tc_planes<<<(unsigned)blocks, 256, 0, st>>>(x, stride, rings, zi0, nz, zrows, pbase, n4, total, Z, bf16);
     return cudaGetLastError();
 }

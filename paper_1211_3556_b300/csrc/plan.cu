@@ -90,12 +90,14 @@ void sk_plan_free(sk_kern *k) {
     cudaFree(k->d_bgrp); k->d_bgrp = nullptr;
     cudaFree(k->d_bpr); k->d_bpr = nullptr;
     cudaFree(k->d_items_belt); k->d_items_belt = nullptr;
-    cudaFree(k->d_tct); k->d_tct = nullptr;
-    cudaFree(k->d_tcg); k->d_tcg = nullptr;
-    cudaFree(k->d_tcr); k->d_tcr = nullptr;
-    cudaFree(k->d_tca); k->d_tca = nullptr;
-    k->h_tct.clear();
-    k->tc_ok = false;
+    for (TcPlan &T : k->tcp) {
+        cudaFree(T.d_tiles); T.d_tiles = nullptr;
+        cudaFree(T.d_group); T.d_group = nullptr;
+        cudaFree(T.d_rng); T.d_rng = nullptr;
+        cudaFree(T.d_A); T.d_A = nullptr;
+        T.h_tiles.clear();
+        T.ok = false;
+    }
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
         for (int v = 0; v < 2; ++v) {
             cudaFree(k->d_items_cap[c][v]); k->d_items_cap[c][v] = nullptr;
@@ -235,6 +237,95 @@ int sk_plan_rebuild_belt_items(sk_kern *k) {
     return k->plan_ok ? sk_plan_bands(k) : SK_OK;
 }
 
+// Tiles of a tensor-core belt form: one per (group, input ring) with any window.  3xTF32
+// (bf false): E0 = the union's first offset rounded down to a multiple of 4, K covers the
+// union plus the 7 extra columns of a segment's 8 output pixels, rounded up to 8 (one
+// TF32 k-step); BF16x3: E0 a multiple of 8 (the plane rows hold 8 pixels), K rounded up to
+// 16.  Chunks of consecutive tiles with at least SK_TC_CHUNK_KSTEPS k-steps of 8 columns
+// are accumulated together in tensor memory.
+static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<int2> &ew, int HM, int R2, int n4,
+                   int b_lo, bool bf, TcPlan &T) {
+    const int ealign = bf ? 8 : 4, kalign = bf ? 16 : 8;
+    std::vector<int4> tl;
+    std::vector<int> tg;
+    std::vector<int2> tr(k->ngroups);
+    long long kb = 0;
+    int kmax = 0, e0min = 1 << 30, e0max = -(1 << 30), zi1 = 0;
+    for (int gi = 0; gi < k->ngroups; ++gi) {
+        const int first = (int)tl.size();
+        for (int i = grp[gi].x; i <= grp[gi].y; ++i) {
+            int lo = 1 << 30, hi = -(1 << 30);
+            for (int w = 0; w < SK_BELT_G; ++w) {
+                const int rb = gi * SK_BELT_G + w, d = i - (b_lo + rb);
+                if (rb >= k->nb || d < -HM || d > HM) continue;
+                const int2 e = ew[(size_t)rb * R2 + d + HM];
+                if (e.x > e.y) continue;
+                lo = std::min(lo, e.x);
+                hi = std::max(hi, e.y);
+            }
+            if (lo > hi) continue;
+            const int E0 = lo >= 0 ? (lo / ealign) * ealign : -(((-lo) + ealign - 1) / ealign) * ealign;
+            const int K = (hi - E0 + 8 + kalign - 1) / kalign * kalign;
+            // A bytes: K columns of 128 rows, hi and lo parts (4 or 2 bytes an element) -> KB
+            const int akb = bf ? K / 2 : K;
+            tl.push_back(make_int4(i, E0, K, (int)std::min<long long>(kb, 1 << 30)));
+            tg.push_back(gi);
+            kb += akb;
+            kmax = std::max(kmax, K);
+            e0min = std::min(e0min, E0);
+            e0max = std::max(e0max, E0);
+            zi1 = std::max(zi1, i);
+        }
+        tr[gi] = make_int2(first, (int)tl.size() - first);
+        int ks = 0;
+        for (int u = first; u < (int)tl.size(); ++u) {
+            if (ks == 0) tl[u].z |= SK_TC_FIRST;
+            ks += (tl[u].z & SK_TC_K_MASK) / 8;
+            if (ks >= SK_TC_CHUNK_KSTEPS || u + 1 == (int)tl.size()) {
+                tl[u].z |= SK_TC_LAST;
+                ks = 0;
+            }
+        }
+    }
+    const int nn = std::min(256, (n4 / 8) & ~15);
+    T.ok = false;
+    if (nn < 16 || kmax > 64 || kb >= (1 << 30) || tl.empty()) return SK_OK;
+    T.nn = nn;
+    T.nblk = (n4 + 8 * nn - 1) / (8 * nn);
+    T.kmax = kmax;
+    T.pbase = e0min >= 0 ? (e0min & ~7) : -(((-e0min) + 7) & ~7);
+    T.zi0 = grp[0].x;
+    T.nz = zi1 - grp[0].x + 1;
+    T.zrows = (8 * nn * (T.nblk - 1) + e0max - T.pbase) / 8 + nn + kmax / 8 + 2;
+    T.stages = sk_tc_stages(kmax, nn, bf, nullptr);
+    T.kb = kb;
+    // every plane row an item copies lies inside its ring's planes (rows of 4 pixels in
+    // two planes for 3xTF32, of 8 pixels in one plane for BF16x3)
+    bool rows_ok = true;
+    for (const int4 &t4 : tl)
+        for (int pb = 0; pb < T.nblk; pb += std::max(1, T.nblk - 1)) {
+            const int off = 8 * nn * pb + t4.y - T.pbase;
+            const int Kt = t4.z & SK_TC_K_MASK;
+            int last;
+            if (bf) {
+                last = (off >> 3) + nn + Kt / 8 - 2;
+                if (off < 0 || (off & 7) || last >= T.zrows) rows_ok = false;
+            } else {
+                const int u0 = off >> 2;
+                last = (u0 >> 1) + (u0 & 1) + nn + Kt / 8 - 2;
+                if (u0 < 0 || (off & 3) || last >= T.zrows) rows_ok = false;
+            }
+        }
+    if (T.stages < 2 || !rows_ok) return SK_OK;
+    T.h_tiles = tl;
+    int rc;
+    if ((rc = upload(tl, &T.d_tiles))) return rc;
+    if ((rc = upload(tg, &T.d_group))) return rc;
+    if ((rc = upload(tr, &T.d_rng))) return rc;
+    T.ok = true;
+    return SK_OK;
+}
+
 int sk_plan_build(sk_kern *k) {
     const sk_geom *g = k->g;
     const int nr = g->nr;
@@ -339,79 +430,9 @@ int sk_plan_build(sk_kern *k) {
         if ((rc = upload(pr, &k->d_bpr))) return rc;
         k->belt_P = belt_cost_p(n4);
         if ((rc = sk_plan_rebuild_belt_items(k))) return rc;
-        // tensor-core belt: one tile per (group, input ring) with any window; E0 = the
-        // union's first offset rounded down to a multiple of 4, K covers the union plus
-        // the 7 extra columns of a segment's 8 output pixels, rounded up to 8
-        {
-            std::vector<int4> tl;
-            std::vector<int> tg;
-            std::vector<int2> tr(k->ngroups);
-            long long kb = 0;
-            int kmax = 0, e0min = 1 << 30, e0max = -(1 << 30), zi1 = 0;
-            for (int gi = 0; gi < k->ngroups; ++gi) {
-                const int first = (int)tl.size();
-                for (int i = grp[gi].x; i <= grp[gi].y; ++i) {
-                    int lo = 1 << 30, hi = -(1 << 30);
-                    for (int w = 0; w < SK_BELT_G; ++w) {
-                        const int rb = gi * SK_BELT_G + w, d = i - (b_lo + rb);
-                        if (rb >= k->nb || d < -HM || d > HM) continue;
-                        const int2 e = ew[(size_t)rb * R2 + d + HM];
-                        if (e.x > e.y) continue;
-                        lo = std::min(lo, e.x);
-                        hi = std::max(hi, e.y);
-                    }
-                    if (lo > hi) continue;
-                    const int E0 = lo >= 0 ? (lo & ~3) : -(((-lo) + 3) & ~3);
-                    const int K = (hi - E0 + 8 + 7) & ~7;
-                    tl.push_back(make_int4(i, E0, K, (int)std::min<long long>(kb, 1 << 30)));
-                    tg.push_back(gi);
-                    kb += K;
-                    kmax = std::max(kmax, K);
-                    e0min = std::min(e0min, E0);
-                    e0max = std::max(e0max, E0);
-                    zi1 = std::max(zi1, i);
-                }
-                tr[gi] = make_int2(first, (int)tl.size() - first);
-                // chunks of consecutive tiles accumulated together in tensor memory
-                int ks = 0;
-                for (int u = first; u < (int)tl.size(); ++u) {
-                    if (ks == 0) tl[u].z |= SK_TC_FIRST;
-                    ks += (tl[u].z & SK_TC_K_MASK) / 8;
-                    if (ks >= SK_TC_CHUNK_KSTEPS || u + 1 == (int)tl.size()) {
-                        tl[u].z |= SK_TC_LAST;
-                        ks = 0;
-                    }
-                }
-            }
-            const int nn = std::min(256, (n4 / 8) & ~15);
-            k->tc_ok = false;
-            if (nn >= 16 && kmax <= 64 && kb < (1 << 30) && !tl.empty()) {
-                k->tc_nn = nn;
-                k->tc_nblk = (n4 + 8 * nn - 1) / (8 * nn);
-                k->tc_kmax = kmax;
-                k->tc_pbase = e0min >= 0 ? (e0min & ~7) : -(((-e0min) + 7) & ~7);
-                k->tc_zi0 = grp[0].x;
-                k->tc_nz = zi1 - grp[0].x + 1;
-                k->tc_zrows = (8 * nn * (k->tc_nblk - 1) + e0max - k->tc_pbase) / 8 + nn + kmax / 8 + 2;
-                k->tc_stages = sk_tc_stages(kmax, nn, nullptr);
-                k->tca_kb = kb;
-                // every plane row an item copies lies inside its ring's planes
-                bool rows_ok = true;
-                for (const int4 &t4 : tl)
-                    for (int pb = 0; pb < k->tc_nblk; pb += std::max(1, k->tc_nblk - 1)) {
-                        const int u0 = (8 * nn * pb + t4.y - k->tc_pbase) >> 2;
-                        const int last = (u0 >> 1) + (u0 & 1) + nn + (t4.z & SK_TC_K_MASK) / 8 - 2;
-                        if (u0 < 0 || ((8 * nn * pb + t4.y - k->tc_pbase) & 3) || last >= k->tc_zrows) rows_ok = false;
-                    }
-                if (k->tc_stages >= 2 && rows_ok) {
-                    k->h_tct = tl;
-                    if ((rc = upload(tl, &k->d_tct))) return rc;
-                    if ((rc = upload(tg, &k->d_tcg))) return rc;
-                    if ((rc = upload(tr, &k->d_tcr))) return rc;
-                    k->tc_ok = true;
-                }
-            }
-        }
+        // tensor-core belt forms: 3xTF32 and BF16x3
+        for (int f = 0; f < 2; ++f)
+            if ((rc = plan_tc(k, grp, ew, HM, R2, n4, b_lo, f == 1, k->tcp[f]))) return rc;
     }
 
     // ---- caps: northern rings below the belt (never the equator ring) and mirrors
@@ -659,15 +680,22 @@ size_t sk_sym_bytes(const sk_kern *k, long long batch) {
     return ((size_t)batch * (size_t)k->sym_stride * sizeof(float4) + 255) & ~(size_t)255;
 }
 
-bool sk_job_wants_tc(const SkJob &j, int path) {
+int sk_job_wants_tc(const SkJob &j, int path) {
     const sk_kern *k = j.k;
-    const bool want = path == SK_PATH_TENSOR || (path == SK_PATH_AUTO && k->belt_form == SK_BELT_TENSOR);
-    return want && !j.sub && k->plan_ok && k->nb > 0 && k->tc_ok && j.batch > 0;
+    int f = -1;
+    if (path == SK_PATH_TENSOR) f = 0;
+    else if (path == SK_PATH_BF16X3) f = 1;
+    else if (path == SK_PATH_AUTO && k->belt_form == SK_BELT_TENSOR) f = 0;
+    else if (path == SK_PATH_AUTO && k->belt_form == SK_BELT_BF16X3) f = 1;
+    if (f < 0 || j.sub || !k->plan_ok || k->nb == 0 || !k->tcp[f].ok || j.batch <= 0) return -1;
+    return f;
 }
 
-static size_t tc_plane_bytes(const SkJob &j) {
-    const sk_kern *k = j.k;
-    return ((size_t)j.batch * k->tc_nz * 4 * k->tc_zrows * sizeof(float4) + 255) & ~(size_t)255;
+// Map planes of a tensor form for a job: 3xTF32 four planes of 4-pixel rows (hi/lo x
+// even/odd), BF16x3 two planes of 8-pixel rows (hi/lo); 16-byte rows either way.
+static size_t tc_plane_bytes(const SkJob &j, int f) {
+    const TcPlan &T = j.k->tcp[f];
+    return ((size_t)j.batch * T.nz * (f ? 2 : 4) * T.zrows * sizeof(float4) + 255) & ~(size_t)255;
 }
 
 // Running totals of the evaluating cap launches of wide-window jobs: one slice per
@@ -686,7 +714,8 @@ size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path) {
     size_t b = 0;
     for (int i = 0; i < n; ++i) {
         b += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
-        if (sk_job_wants_tc(jobs[i], path)) b += tc_plane_bytes(jobs[i]);
+        const int f = sk_job_wants_tc(jobs[i], path);
+        if (f >= 0) b += tc_plane_bytes(jobs[i], f);
     }
     return b + ctot_bytes(jobs, n, path);
 }
@@ -808,21 +837,22 @@ int sk_beltw_build(sk_kern *k, cudaStream_t st, const int *gate) {
     return SK_OK;
 }
 
-int sk_tca_build(sk_kern *k, cudaStream_t st, const int *gate) {
-    if (!k->tc_ok) return SK_OK;
-    if (!k->d_tca) {
+int sk_tca_build(sk_kern *k, int form, cudaStream_t st, const int *gate) {
+    TcPlan &T = k->tcp[form];
+    if (!T.ok) return SK_OK;
+    if (!T.d_A) {
         if (gate) return SK_OK;                     // built on first use, from the table then
-        if (cudaMalloc(&k->d_tca, (size_t)k->tca_kb * 1024) != cudaSuccess) {
+        if (cudaMalloc(&T.d_A, (size_t)T.kb * 1024) != cudaSuccess) {
             cudaGetLastError();
-            k->d_tca = nullptr;                     // the tensor path runs the FP32 belt
+            T.d_A = nullptr;                        // that form runs the FP32 belt
             return SK_OK;
         }
     }
     TcTileArgs a;
     memset(&a, 0, sizeof a);
-    a.tiles = k->d_tct;
-    a.tile_group = k->d_tcg;
-    a.A = k->d_tca;
+    a.tiles = T.d_tiles;
+    a.tile_group = T.d_group;
+    a.A = T.d_A;
     a.rings = k->g->d_rings;
     a.pair_off = k->d_pair_off;
     a.pairs = k->d_pairs;
@@ -831,22 +861,24 @@ int sk_tca_build(sk_kern *k, cudaStream_t st, const int *gate) {
     a.b_lo = k->b_lo;
     a.nb = k->nb;
     a.n4 = (int)(4 * k->g->nside);
-    SK_CU(sk_launch_tc_tiles(a, (int)k->h_tct.size(), st, gate));
+    a.bf16 = form;
+    SK_CU(sk_launch_tc_tiles(a, (int)T.h_tiles.size(), st, gate));
     return SK_OK;
 }
 
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
     // jobs whose belt runs on the tensor cores (their A tiles are built on first use)
     // (whole operators only: a ring subset runs its belt items on the FP32 kernel)
-    std::vector<char> use_tc(n, 0);
+    std::vector<int> use_tc(n, -1);            // the form, or -1
     for (int i = 0; i < n; ++i) {
         sk_kern *k = const_cast<sk_kern *>(jobs[i].k);
-        if (!sk_job_wants_tc(jobs[i], path)) continue;
-        if (!k->d_tca) {
-            int rc = sk_tca_build(k, st);
+        const int f = sk_job_wants_tc(jobs[i], path);
+        if (f < 0) continue;
+        if (!k->tcp[f].d_A) {
+            int rc = sk_tca_build(k, f, st);
             if (rc) return rc;
         }
-        use_tc[i] = k->d_tca != nullptr;
+        if (k->tcp[f].d_A) use_tc[i] = f;
     }
 
     // belt weight rows of the FP32 belt: stored with the operator, else one pre-pass
@@ -859,7 +891,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             if (!k->plan_ok || k->nb == 0 || jobs[i].batch == 0) continue;
             wrows[i] = (float *)wp;
             wp += sk_plan_workspace_bytes(k);
-            if (use_tc[i]) continue;
+            if (use_tc[i] >= 0) continue;
             if (k->d_beltw) {
                 wrows[i] = (float *)k->d_beltw;
                 continue;
@@ -942,19 +974,23 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         std::vector<void *> zp(n, nullptr);
         char *p = (char *)ws;
         for (int i = 0; i < n; ++i) p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
-        for (int i = 0; i < n; ++i)
-            if (sk_job_wants_tc(jobs[i], path)) {
-                zp[i] = p;
-                p += tc_plane_bytes(jobs[i]);
-            }
         for (int i = 0; i < n; ++i) {
-            if (!use_tc[i]) continue;
+            const int f = sk_job_wants_tc(jobs[i], path);
+            if (f >= 0) {
+                zp[i] = p;
+                p += tc_plane_bytes(jobs[i], f);
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            const int f = use_tc[i];
+            if (f < 0) continue;
             const sk_kern *k = jobs[i].k;
+            const TcPlan &T = k->tcp[f];
             void *z = zp[i];
             cudaEvent_t ev = sk_prof_begin(ctx, st);
-            SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, k->tc_zi0,
-                                      k->tc_nz, k->tc_zrows, k->tc_pbase, (int)(4 * k->g->nside), (float4 *)z,
-                                      ctx->num_sms, st));
+            SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, T.zi0, T.nz,
+                                      T.zrows, T.pbase, (int)(4 * k->g->nside), (float4 *)z, f == 1, ctx->num_sms,
+                                      st));
             sk_prof_end(ctx, "tc_planes", ev, st);
             TcArgs a;
             memset(&a, 0, sizeof a);
@@ -965,23 +1001,24 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             a.b_lo = k->b_lo;
             a.nb = k->nb;
             a.n4 = (int)(4 * k->g->nside);
-            a.tiles = k->d_tct;
-            a.trng = k->d_tcr;
-            a.A = k->d_tca;
+            a.tiles = T.d_tiles;
+            a.trng = T.d_rng;
+            a.A = T.d_A;
             a.Z = (const float4 *)z;
-            a.zi0 = k->tc_zi0;
-            a.nz = k->tc_nz;
-            a.zrows = k->tc_zrows;
-            a.pbase = k->tc_pbase;
-            a.nn = k->tc_nn;
-            a.nblk = k->tc_nblk;
-            a.kmax = k->tc_kmax;
-            a.nstages = k->tc_stages;
-            a.total = k->ngroups * (int)jobs[i].batch * k->tc_nblk;
+            a.zi0 = T.zi0;
+            a.nz = T.nz;
+            a.zrows = T.zrows;
+            a.pbase = T.pbase;
+            a.nn = T.nn;
+            a.nblk = T.nblk;
+            a.kmax = T.kmax;
+            a.nstages = T.stages;
+            a.bf16 = f;
+            a.total = k->ngroups * (int)jobs[i].batch * T.nblk;
             a.status = ctx->d_status;
             ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_belt_tc(a, std::min(a.total, ctx->num_sms), st));
-            sk_prof_end(ctx, "conv_belt_tc", ev, st);
+            sk_prof_end(ctx, f ? "conv_belt_bf16" : "conv_belt_tc", ev, st);
         }
     }
 
@@ -1005,7 +1042,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             const sk_kern *k = jobs[i].k;
             if (!k->plan_ok || k->nb == 0 || k->belt_P != P || (int)k->blocked != blk || jobs[i].batch == 0)
                 continue;
-            if (use_tc[i]) continue;                              // done on the tensor cores
+            if (use_tc[i] >= 0) continue;                         // done on the tensor cores
             const SkItems *sub = jobs[i].sub;
             const int4 *items = sub ? sub->belt : k->d_items_belt;
             const int n_items = sub ? sub->n_belt : k->n_items_belt;
@@ -1069,7 +1106,10 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         char *p = (char *)ws;
         for (int i = 0; i < n; ++i) {
             p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
-            if (sk_job_wants_tc(jobs[i], path)) p += tc_plane_bytes(jobs[i]);
+                {
+                const int f = sk_job_wants_tc(jobs[i], path);
+                if (f >= 0) p += tc_plane_bytes(jobs[i], f);
+            }
         }
         ctot = (float *)p;
     }

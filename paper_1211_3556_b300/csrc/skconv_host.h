@@ -66,6 +66,21 @@ struct sk_geom {
     std::vector<RingDev> h_rings;
 };
 
+// One tensor-core form of the belt: one tile per (ring group, input ring) with
+// (input ring, E0, K | chunk flags, A offset in KB), its group, and per group (first
+// tile, tiles); the A store (hi/lo tiles, built when the form is first used and rebuilt
+// with the table); the geometry of the per-call map planes.
+struct TcPlan {
+    bool ok = false;
+    std::vector<int4> h_tiles;
+    int4 *d_tiles = nullptr;
+    int *d_group = nullptr;
+    int2 *d_rng = nullptr;
+    long long kb = 0;
+    unsigned char *d_A = nullptr;
+    int kmax = 0, nn = 0, nblk = 0, pbase = 0, zrows = 0, zi0 = 0, nz = 0, stages = 0;
+};
+
 struct sk_kern {
     sk_ctx *ctx = nullptr;
     const sk_geom *g = nullptr;
@@ -124,23 +139,13 @@ struct sk_kern {
     // pair-row pre-pass writes them), rebuilt with the table; null: the pre-pass runs
     // per call into the workspace
     float2 *d_beltw = nullptr;
-    // tensor-core belt (belt_tc.cu): one tile per (ring group, input ring) with
-    // (input ring, E0, K, A offset in KB), its group, and per group (first tile, tiles);
-    // the A store (TF32 hi/lo tiles, built on first use and rebuilt with the table);
-    // the geometry of the per-call map planes
-    bool tc_ok = false;
     int belt_form = SK_BELT_FP32;          // the belt of SK_PATH_AUTO
     // outputs sum more than SK_BLOCKED_TERMS terms: the FP32 belt and the stored-weight
     // caps sum each input ring apart and add it to the output's total
     bool blocked = false;
     long long max_terms = 0;               // largest number of window pixels of one output
-    std::vector<int4> h_tct;
-    int4 *d_tct = nullptr;
-    int *d_tcg = nullptr;
-    int2 *d_tcr = nullptr;
-    long long tca_kb = 0;
-    unsigned char *d_tca = nullptr;
-    int tc_kmax = 0, tc_nn = 0, tc_nblk = 0, tc_pbase = 0, tc_zrows = 0, tc_zi0 = 0, tc_nz = 0, tc_stages = 0;
+    // tensor-core belt forms (belt_tc.cu): [0] 3xTF32, [1] BF16x3
+    TcPlan tcp[2];
     // host copies of the item lists, and their partition into ring bands by distance
     // from the nearest pole (sk_convolve_host overlaps the copies of one band with the
     // sums of another); rebuilt when the belt tile width changes
@@ -189,9 +194,10 @@ void sk_capw_free(sk_kern *k);
 // (same gate and stream rules as sk_capw_build; an allocation that fails leaves the
 // pre-pass per call).
 int sk_beltw_build(sk_kern *k, cudaStream_t st = 0, const int *gate = nullptr);
-// A tiles of the tensor-core belt: allocate (if absent; a failed allocation leaves the
-// tensor path to the FP32 belt) and evaluate them from the current table, gated as above.
-int sk_tca_build(sk_kern *k, cudaStream_t st = 0, const int *gate = nullptr);
+// A tiles of a tensor-core belt form (0 3xTF32, 1 BF16x3): allocate (if absent; a failed
+// allocation leaves that form to the FP32 belt) and evaluate them from the current table,
+// gated as above.
+int sk_tca_build(sk_kern *k, int form, cudaStream_t st = 0, const int *gate = nullptr);
 void sk_plan_free(sk_kern *k);
 int sk_plan_rebuild_belt_items(sk_kern *k);
 size_t sk_plan_workspace_bytes(const sk_kern *k);
@@ -217,8 +223,9 @@ int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **ou
 // then the symmetric copies of every job's maps for the caps, then the map planes of
 // the jobs whose belt runs on the tensor cores.
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path = SK_PATH_AUTO);
-// Whether job j's belt runs on the tensor cores under `path` (given its tiles exist).
-bool sk_job_wants_tc(const SkJob &j, int path);
+// The tensor-core form job j's belt runs under `path` (0 3xTF32, 1 BF16x3; given its
+// tiles exist), or -1.
+int sk_job_wants_tc(const SkJob &j, int path);
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st);
 // Table gradient: `acc` is the start of sk_grad_workspace_bytes(k, batch) bytes of
 // workspace (the FP64 bins, then the caps' symmetric copy of x).

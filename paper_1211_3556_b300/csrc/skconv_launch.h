@@ -102,6 +102,7 @@ struct TcArgs {
     const float4 *Z;            // the call's planes: [map][ring - zi0][hi even, hi odd, lo even, lo odd][zrows]
     int zi0, nz, zrows, pbase;  // first plane ring, plane rings, rows per plane, pixel of row 0
     int nn, nblk, kmax, nstages;
+    int bf16;                   // 0: 3xTF32 (TF32 parts, 4-pixel plane rows), 1: BF16x3 (8-pixel rows)
     int total;                  // items: groups x maps x pixel blocks
     int *status;
 };
@@ -115,14 +116,15 @@ struct TcTileArgs {
     KernParams kp;
     const float2 *tab;
     int b_lo, nb, n4;
+    int bf16;
 };
-// pipeline stages for (kmax, nn) and the launch's shared memory; 0 = does not fit
-int sk_tc_stages(int kmax, int nn, size_t *smem);
+// pipeline stages for (kmax, nn, form) and the launch's shared memory; 0 = does not fit
+int sk_tc_stages(int kmax, int nn, bool bf16, size_t *smem);
 cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st);
 // A tiles of all n_tiles tiles; with `gate`, only if *gate is non-zero
 cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st, const int *gate = nullptr);
 cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
-                                int zrows, int pbase, int n4, float4 *Z, int sms, cudaStream_t st);
+                                int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms, cudaStream_t st);
 
 // set-up kernels (geometry.cu)
 cudaError_t sk_launch_ring_geom(long long nside, RingDev *rings, double *z, double *rho,

@@ -174,7 +174,97 @@ k_tc_sliding(const float *__restrict__ a, const float *__restrict__ x, float *__
     }
 }
 
+// BF16 form: A (128 x K) as 8-column chunks 2048 bytes apart; x in one plane of 16-byte
+// rows of 8 values (x[8m .. 8m+7]); k-step q (16 columns) of B_q[s][t] = x[8 s + 16 q + t]
+// is rows s + 2q (t < 8) and s + 2q + 1 (t >= 8): a start address 32 q bytes into the
+// plane, 16 bytes between the two core matrices along K.  3 passes, two accumulators.
+__global__ void __launch_bounds__(128)
+k_tc_sliding_bf16(const float *__restrict__ a, const float *__restrict__ x, float *__restrict__ d, int N, int K,
+                  int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int R = N + K / 8;                           // rows of the plane
+    const uint32_t slot = (uint32_t)R * 16;
+    unsigned char *b_hi = base, *b_lo = base + slot;
+    unsigned char *a_hi = base + ((2 * slot + 1023) & ~1023u);
+    unsigned char *a_lo = a_hi + (uint32_t)K * 256;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int t = threadIdx.x, warp = t >> 5;
+
+    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (t == 0) {
+        tc::mbar_init(tc::smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = t; i < 128 * K; i += 128) {
+        const int r = i / K, k = i % K;
+        uint16_t hi, lo;
+        tc::split_bf16(a[i], hi, lo);
+        *reinterpret_cast<uint16_t *>(a_hi + tc::kmajor128_offset_bf16(r, k)) = hi;
+        *reinterpret_cast<uint16_t *>(a_lo + tc::kmajor128_offset_bf16(r, k)) = lo;
+    }
+    for (int i = t; i < 8 * R; i += 128) {
+        uint16_t hi, lo;
+        tc::split_bf16(x[i], hi, lo);
+        *reinterpret_cast<uint16_t *>(b_hi + 2 * i) = hi;
+        *reinterpret_cast<uint16_t *>(b_lo + 2 * i) = lo;
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tslot;
+
+    if (t == 0) {
+        const uint32_t idesc = tc::idesc_bf16(128, N);
+        for (int q = 0; q < K / 16; ++q) {
+            const uint64_t ah = tc::kmajor_desc(tc::smem_u32(a_hi + 4096 * q), 2048, 128);
+            const uint64_t al = tc::kmajor_desc(tc::smem_u32(a_lo + 4096 * q), 2048, 128);
+            const uint64_t bh = tc::kmajor_desc(tc::smem_u32(b_hi + 32 * q), 16, 128);
+            const uint64_t bl = tc::kmajor_desc(tc::smem_u32(b_lo + 32 * q), 16, 128);
+            tc::mma_bf16(taddr, ah, bh, idesc, q > 0);
+            tc::mma_bf16(taddr + 256u, ah, bl, idesc, q > 0);
+            tc::mma_bf16(taddr + 256u, al, bh, idesc, 1);
+        }
+        tc::mma_commit(tc::smem_u32(&bar));
+    }
+    const bool ok = tc::mbar_wait(tc::smem_u32(&bar), 0, 1000000000ull);
+    if (!ok && t == 0) atomicCAS(status, 0, SK_ETIMEOUT);
+    tc::fence_after_sync();
+    if (ok) {
+        const int row = warp * 32 + (t & 31);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16], w[16];
+            tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + 256u + (uint32_t)c0, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) d[row * N + c0 + j] = v[j] + w[j];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(taddr, 512);
+    }
+}
+
 }  // namespace
+
+extern "C" int sk_selftest_tc_sliding_bf16(sk_ctx *ctx, const float *d_a, const float *d_x, float *d_d, int n, int k,
+                                           void *stream) {
+    if (!ctx || !d_a || !d_x || !d_d) return sk_fail(SK_EINVAL, "sk_selftest_tc_sliding_bf16: NULL argument");
+    if (n < 16 || n > 256 || n % 16 || k < 16 || k > 64 || k % 16)
+        return sk_fail(SK_EINVAL, "sk_selftest_tc_sliding_bf16: N in 16..256 (x16), K in 16..64 (x16)");
+    // a fixed 200 KB: every operand read stays inside the block's shared memory
+    const size_t smem = 200 * 1024;
+    SK_CU(cudaSetDevice(ctx->device));
+    SK_CU(cudaFuncSetAttribute(k_tc_sliding_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_sliding_bf16<<<1, 128, smem, (cudaStream_t)stream>>>(d_a, d_x, d_d, n, k, ctx->d_status);
+    SK_CU(cudaGetLastError());
+    return SK_OK;
+}
 
 extern "C" int sk_selftest_tc_sliding(sk_ctx *ctx, const float *d_a, const float *d_x, float *d_d, int n, int k,
                                       int off, void *stream) {

@@ -76,6 +76,38 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) of a 128-row K-major no-swizzle BF16 operand whose
+// 8-column chunks are 2048 bytes apart (lbo 2048, sbo 128).
+__host__ __device__ inline uint32_t kmajor128_offset_bf16(int r, int k) {
+    return (uint32_t)((k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, one BF16 MMA of M x N x 16.  Issued by one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t taddr, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         int accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(taddr), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// BF16 split of an fp32 value, both parts rounded to nearest: hi = rn(x), lo = rn(x - hi)
+// (x - hi exact in FP32); hi*hi + hi*lo + lo*hi then misses x*y by about 3 * 2^-18
+// relative.  The parts as raw 16-bit patterns.
+__device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) {
+    uint16_t h, l;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    const float hf = __uint_as_float((uint32_t)h << 16);
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(l) : "f"(x - hf));
+    hi = h;
+    lo = l;
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, one MMA of M x N x 8.  Issued by one thread.
 __device__ __forceinline__ void mma_tf32(uint32_t taddr, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          int accumulate) {

@@ -66,7 +66,7 @@ void cache_store(const char *path, const std::string &key, const Choice &c) {
 int apply(sk_kern *k, const Choice &c) {
     int rc = sk_kernel_set_tiles(k, c.P, 0);
     if (rc) return rc;
-    if (c.form == SK_BELT_TENSOR && k->tc_ok) {
+    if (c.form == SK_BELT_TENSOR && k->tcp[0].ok) {
         if (sk_kernel_set_belt_form(k, SK_BELT_TENSOR) != SK_OK) k->belt_form = SK_BELT_FP32;
     } else {
         k->belt_form = SK_BELT_FP32;
@@ -144,7 +144,8 @@ extern "C" int sk_kernel_autotune(sk_ctx *ctx, sk_kern *k, const float *d_in, fl
         if (ms < best_ms) { best_ms = ms; best.P = P; }
     }
     if (rc == SK_OK) rc = sk_kernel_set_tiles(k, best.P, 0);
-    if (rc == SK_OK && k->tc_ok && sk_kernel_set_belt_form(k, SK_BELT_TENSOR) == SK_OK) {
+    // (the BF16x3 form is outside the accuracy bound and never a candidate)
+    if (rc == SK_OK && k->tcp[0].ok && sk_kernel_set_belt_form(k, SK_BELT_TENSOR) == SK_OK) {
         if ((rc = time_it(&ms)) == SK_OK && ms < best_ms) {
             best_ms = ms;
             best.form = SK_BELT_TENSOR;

@@ -96,3 +96,42 @@ def test_sliding_rows_3xtf32_accuracy(env):
         want = _sliding_ref(A, x, n, off)
         scale = _sliding_ref(np.abs(A), np.abs(x), n, off)
         assert np.max(np.abs(D - want) / scale) < 2e-6
+
+
+def _run_sliding_bf16(sk, ctx, torch, A, x, n):
+    a = torch.from_numpy(np.ascontiguousarray(A, np.float32)).cuda()
+    xv = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    d = torch.full((128, n), float("nan"), device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = sk.lib()
+    rc = L.sk_selftest_tc_sliding_bf16(ctx._h, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(xv.data_ptr()),
+                                       ctypes.c_void_p(d.data_ptr()), n, A.shape[1], st)
+    assert rc == 0, L.sk_last_error()
+    torch.cuda.synchronize()
+    assert L.sk_get_status(ctx._h, st) == 0
+    return d.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n,k", [(256, 32), (16, 16), (128, 64), (64, 48)])
+def test_sliding_rows_bf16_exact_on_small_integers(env, n, k):
+    sk, ctx, torch = env
+    rng = np.random.default_rng(9 * n + k)
+    A = rng.integers(-8, 9, size=(128, k)).astype(np.float32)
+    x = rng.integers(-8, 9, size=8 * (n + k // 8)).astype(np.float32)
+    D = _run_sliding_bf16(sk, ctx, torch, A, x, n)
+    assert np.array_equal(D, _sliding_ref(A, x, n, 0))
+
+
+def test_sliding_rows_bf16x3_accuracy(env):
+    # BF16x3 keeps about 16 significant bits of each operand: ~1e-5 per product, far
+    # coarser than 3xTF32 (the reason it is not the accuracy-bound form)
+    sk, ctx, torch = env
+    rng = np.random.default_rng(12)
+    n, k = 256, 48
+    A = rng.standard_normal((128, k)).astype(np.float32)
+    x = rng.standard_normal(8 * (n + k // 8)).astype(np.float32)
+    D = _run_sliding_bf16(sk, ctx, torch, A, x, n)
+    want = _sliding_ref(A, x, n, 0)
+    scale = _sliding_ref(np.abs(A), np.abs(x), n, 0)
+    err = np.max(np.abs(D - want) / scale)
+    assert 2e-6 < err < 1e-4

@@ -160,3 +160,28 @@ def test_tensor_form_n2048_plain_sampled_outputs(sk):
     outs = sample_indices(x.shape[1], 20000, 207)
     yo = O.conv_window(grp.nside, V, ks.theta_cut, ks.layout, x[0].astype(np.float64), outs)
     assert rms_rel(y[outs], yo) <= RMS_BOUND
+
+
+def test_bf16x3_form_reported_with_its_error(sk):
+    # BF16x3 (BF16 hi/lo parts, three kind::f16 MMAs) keeps about 16 significant bits of
+    # each operand: its error against the oracle is reported, ~1e-5 relative -- outside the
+    # 1e-6 bound the other forms meet (the tuner never picks it)
+    import torch
+    nside, tc = 256, 0.02
+    V = table(2.5 * tc / 3 / ARCMIN, 768, 192, tc, 2048)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc)
+    c = k.config()
+    assert c["bf16x3_form_available"] and c["tensor_form_available"]
+    x = torch.from_numpy(white_noise_maps(nside, 3, 510)).cuda()
+    yb = conv(sk, k, x, sk.PATH_BF16X3)
+    yt = conv(sk, k, x, sk.PATH_TENSOR)
+    k.set_belt_form(sk.BELT_BF16X3)
+    assert k.config()["belt_form"] == "bf16x3"
+    assert torch.equal(conv(sk, k, x), yb)
+    for b in range(3):
+        yo = O.conv_window(nside, V, tc, 0, x[b].cpu().numpy().astype(np.float64))
+        eb = rms_rel(yb[b].cpu().numpy(), yo)
+        et = rms_rel(yt[b].cpu().numpy(), yo)
+        assert et <= RMS_BOUND
+        assert 1e-6 < eb < 5e-5, eb
+    k.set_belt_form(sk.BELT_FP32)
