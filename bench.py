@@ -434,12 +434,21 @@ def run_ours(args):
         pb = kb.count_pairs()
         kb.autotune(xb, out=yb, cache_path=os.path.join(tempfile.gettempdir(), "skconv_belt_tiles.txt"))
         batched = {"workload": "n1024x64_batched", "unit": UNIT}
-        for name, path in (("fp32", sk.PATH_FP32), ("tensor_3xtf32", sk.PATH_TENSOR)):
+        outs_b = {}
+        for name, path in (("fp32", sk.PATH_FP32), ("tensor_3xtf32", sk.PATH_TENSOR),
+                           ("tensor_bf16x3", sk.PATH_BF16X3)):
             msb = time_steps(torch, lambda: sk.convolve(kb, xb, out=yb, path=path), max(3, min(args.steps, 20)), 2,
                              barrier)
             batched[name] = {"value": pb * grp.batch / (msb * 1e-3), "ms_per_map": msb / grp.batch,
                              "ms_per_step": msb}
-        for name in ("fp32", "tensor_3xtf32"):
+            outs_b[name] = yb[:4].clone()
+        # BF16x3 is outside the 1e-6 bound: its deviation from the 3xTF32 form (itself within
+        # 4e-7 of the FP64 oracle in the tests) is reported beside it and flagged
+        ref_b = outs_b["tensor_3xtf32"].double()
+        batched["tensor_bf16x3"]["rms_rel_vs_3xtf32"] = float(torch.linalg.norm(outs_b["tensor_bf16x3"].double() - ref_b)
+                                                              / torch.linalg.norm(ref_b))
+        batched["tensor_bf16x3"]["within_1e-6"] = batched["tensor_bf16x3"]["rms_rel_vs_3xtf32"] <= 1e-6
+        for name in ("fp32", "tensor_3xtf32", "tensor_bf16x3"):
             useful = FLOP_PER_PAIR * batched[name]["value"] / 1e12
             batched[name]["useful_tflops"] = useful
             batched[name]["frac_fp32_peak"] = useful / fp32_peak
@@ -447,7 +456,7 @@ def run_ours(args):
         # MMAs per useful product, so 1/3 is its ceiling)
         batched["tensor_3xtf32"]["frac_tf32_peak"] = (batched["tensor_3xtf32"]["useful_tflops"]
                                                       / peaks["tf32_tcgen05"]["tflops"])
-        batched["value"] = max(batched["fp32"]["value"], batched["tensor_3xtf32"]["value"])
+        batched["value"] = max(batched["fp32"]["value"], batched["tensor_3xtf32"]["value"])   # the 1e-6 forms
         del xb, yb
 
     # the whole split of Eq. 1 beside the real-space step: harmonic part K^_l = K_l - R_l
