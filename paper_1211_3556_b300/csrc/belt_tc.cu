@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
     __shared__ __align__(8) uint64_t tfull_bar[2];                  // a tile's partial sums complete
     __shared__ __align__(8) uint64_t tempty_bar[2];                 // the epilogue has read them
     __shared__ __align__(8) uint64_t drain_bar;                     // teardown
+    __shared__ int4 stile[SK_TC_MAX_STAGES];                        // the tile each stage holds
     __shared__ uint32_t tslot;
     __shared__ int abort_s;
     volatile int *abort_flag = &abort_s;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
             for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
                 const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
                 const int j0 = pb * 8 * T.nn;
-                const int2 tr = T.trng[g];
+                const int4 tr = T.trng[g];
                 const float4 *zb = T.Z + (size_t)b * T.nz * NPL * T.zrows;
                 for (int u = 0; u < tr.y; ++u, ++cnt) {
                     const int4 tl = T.tiles[tr.x + u];            // (input ring, E0, K | flags, A offset in KB)
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                     unsigned char *sb = base + (size_t)s * L.bytes;
                     const uint32_t bar = tc::smem_u32(&full_bar[s]);
                     const uint32_t abytes = 2u * (uint32_t)K * APART;
+                    stile[s] = tl;                                // read by the MMA thread after the barrier
                     tc::mbar_expect_tx(bar, abytes + (uint32_t)(NPL * rbytes));
                     tc::bulk_g2s(tc::smem_u32(sb), T.A + (size_t)tl.w * 1024, abytes, bar);
                     if constexpr (BF) {
@@ -175,43 +177,46 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         if (lane == 0) {
             uint32_t cnt = 0, ccnt = 0;                           // tiles, chunks
             const uint32_t idesc = BF ? tc::idesc_bf16(128, T.nn) : tc::idesc_tf32(128, T.nn);
+            bool need_empty = false;                              // the next tile opens a chunk
             for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
-                const int2 tr = T.trng[f / per_g];
-                for (int u = 0; u < tr.y; ++u, ++cnt) {
-                    const int4 tl = T.tiles[tr.x + u];
+                const int ntile = T.trng[f / per_g].y;
+                for (int u = 0; u < ntile; ++u, ++cnt) {
                     const int s = (int)(cnt % (uint32_t)S);
                     const int ab = (int)(ccnt & 1);               // accumulator of this chunk
-                    const bool first = (tl.z & SK_TC_FIRST) != 0, last = (tl.z & SK_TC_LAST) != 0;
-                    if (first && ccnt >= 2 &&
+                    // a chunk starts at the group's first tile or after a chunk's last one:
+                    // its accumulator must have been read by the epilogue (two chunks ago)
+                    if ((u == 0 || need_empty) && ccnt >= 2 &&
                         !wait_or_abort(tc::smem_u32(&tempty_bar[ab]), ((ccnt >> 1) - 1) & 1, abort_flag, T.status))
                         break;
                     if (!wait_or_abort(tc::smem_u32(&full_bar[s]), (cnt / S) & 1, abort_flag, T.status)) break;
                     tc::fence_after_sync();
+                    const int4 tl = stile[s];
+                    const bool first = (tl.z & SK_TC_FIRST) != 0, last = (tl.z & SK_TC_LAST) != 0;
+                    need_empty = last;
                     const int K = tl.z & SK_TC_K_MASK;
                     const uint32_t sb = tc::smem_u32(base + (size_t)s * L.bytes);
                     const uint32_t a_hi = sb, a_lo = sb + (uint32_t)K * APART;
                     const uint32_t d = taddr + 256u * (uint32_t)ab;
-                    if constexpr (BF) {
-                        const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + L.slot;
-                        for (int q = 0; q < K / 16; ++q) {
-                            const uint64_t ah = tc::kmajor_desc(a_hi + 4096u * q, 2048, 128);
-                            const uint64_t al = tc::kmajor_desc(a_lo + 4096u * q, 2048, 128);
-                            const uint64_t bh = tc::kmajor_desc(b_hi + 32u * q, 16, 128);
-                            const uint64_t bl = tc::kmajor_desc(b_lo + 32u * q, 16, 128);
+                    // descriptors of the k-step's operands: the start address is their low
+                    // field (16-byte units), so a k-step is an add (4096 bytes in A, 32 or 16
+                    // bytes in B); addresses stay below 256 KB, so the field never carries
+                    const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + (BF ? 1u : 2u) * L.slot;
+                    uint64_t ah = tc::kmajor_desc(a_hi, 2048, 128), al = tc::kmajor_desc(a_lo, 2048, 128);
+                    uint64_t bh = tc::kmajor_desc(b_hi, BF ? 16u : L.slot, 128);
+                    uint64_t bl = tc::kmajor_desc(b_lo, BF ? 16u : L.slot, 128);
+                    constexpr uint64_t DA = 4096u >> 4, DB = (BF ? 32u : 16u) >> 4;
+                    const int nq = K / (BF ? 16 : 8);
+                    for (int q = 0; q < nq; ++q) {
+                        if constexpr (BF) {
                             tc::mma_bf16(d, ah, bh, idesc, (first && q == 0) ? 0 : 1);
                             tc::mma_bf16(d, ah, bl, idesc, 1);
                             tc::mma_bf16(d, al, bh, idesc, 1);
+                        } else {
+                            tc::mma_tf32(d, ah, bh, idesc, (first && q == 0) ? 0 : 1);
+                            tc::mma_tf32(d, ah, bl, idesc, 1);
+                            tc::mma_tf32(d, al, bh, idesc, 1);
                         }
-                    }
-                    const uint32_t b_hi = sb + L.a_bytes, b_lo = b_hi + 2u * L.slot;
-                    for (int q = 0; !BF && q < K / 8; ++q) {
-                        const uint64_t ah = tc::kmajor_desc(a_hi + 4096u * q, 2048, 128);
-                        const uint64_t al = tc::kmajor_desc(a_lo + 4096u * q, 2048, 128);
-                        const uint64_t bh = tc::kmajor_desc(b_hi + 16u * q, L.slot, 128);
-                        const uint64_t bl = tc::kmajor_desc(b_lo + 16u * q, L.slot, 128);
-                        tc::mma_tf32(d, ah, bh, idesc, (first && q == 0) ? 0 : 1);
-                        tc::mma_tf32(d, ah, bl, idesc, 1);
-                        tc::mma_tf32(d, al, bh, idesc, 1);
+                        ah += DA; al += DA; bh += DB; bl += DB;
                     }
                     tc::mma_commit(tc::smem_u32(&empty_bar[s]));
                     if (last) {
@@ -236,15 +241,14 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
             const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
             const int j0 = pb * 8 * T.nn;
-            const int2 tr = T.trng[g];
+            const int nchunk = T.trng[g].z;
             float acc[CH][16];
 #pragma unroll
             for (int c = 0; c < CH; ++c)
 #pragma unroll
                 for (int m = 0; m < 16; ++m) acc[c][m] = 0.0f;
             bool ok = true;
-            for (int u = 0; u < tr.y; ++u) {
-                if (!(T.tiles[tr.x + u].z & SK_TC_LAST)) continue;
+            for (int u = 0; u < nchunk; ++u) {
                 const int ab = (int)(ccnt & 1);
                 if (!wait_or_abort(tc::smem_u32(&tfull_bar[ab]), (ccnt >> 1) & 1, abort_flag, T.status)) {
                     ok = false;

@@ -248,7 +248,7 @@ static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<i
     const int ealign = bf ? 8 : 4, kalign = bf ? 16 : 8;
     std::vector<int4> tl;
     std::vector<int> tg;
-    std::vector<int2> tr(k->ngroups);
+    std::vector<int4> tr(k->ngroups);
     long long kb = 0;
     int kmax = 0, e0min = 1 << 30, e0max = -(1 << 30), zi1 = 0;
     for (int gi = 0; gi < k->ngroups; ++gi) {
@@ -276,16 +276,17 @@ static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<i
             e0max = std::max(e0max, E0);
             zi1 = std::max(zi1, i);
         }
-        tr[gi] = make_int2(first, (int)tl.size() - first);
-        int ks = 0;
+        int ks = 0, nchunk = 0;
         for (int u = first; u < (int)tl.size(); ++u) {
             if (ks == 0) tl[u].z |= SK_TC_FIRST;
             ks += (tl[u].z & SK_TC_K_MASK) / 8;
             if (ks >= SK_TC_CHUNK_KSTEPS || u + 1 == (int)tl.size()) {
                 tl[u].z |= SK_TC_LAST;
                 ks = 0;
+                ++nchunk;
             }
         }
+        tr[gi] = make_int4(first, (int)tl.size() - first, nchunk, 0);
     }
     const int nn = std::min(256, (n4 / 8) & ~15);
     T.ok = false;

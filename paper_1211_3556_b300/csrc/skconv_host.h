@@ -75,7 +75,7 @@ struct TcPlan {
     std::vector<int4> h_tiles;
     int4 *d_tiles = nullptr;
     int *d_group = nullptr;
-    int2 *d_rng = nullptr;
+    int4 *d_rng = nullptr;                 // per group: first tile, tiles, chunks, 0
     long long kb = 0;
     unsigned char *d_A = nullptr;
     int kmax = 0, nn = 0, nblk = 0, pbase = 0, zrows = 0, zi0 = 0, nz = 0, stages = 0;

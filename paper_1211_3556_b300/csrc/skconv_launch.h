@@ -97,7 +97,7 @@ struct TcArgs {
     int batch;
     int b_lo, nb, n4;
     const int4 *tiles;          // per tile: (input ring, E0, K | chunk flags, offset of its A pair in KB)
-    const int2 *trng;           // per ring group: first tile, tiles
+    const int4 *trng;           // per ring group: first tile, tiles, chunks, 0
     const unsigned char *A;     // stored A tiles (TF32 hi, then lo, no-swizzle K-major)
     const float4 *Z;            // the call's planes: [map][ring - zi0][hi even, hi odd, lo even, lo odd][zrows]
     int zi0, nz, zrows, pbase;  // first plane ring, plane rings, rows per plane, pixel of row 0
