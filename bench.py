@@ -186,6 +186,22 @@ PROFILED_SOURCES = {
 }
 
 
+def path_costs(prof, by_launch):
+    """Measured cost of one pair on each ring path (0 belt, 1 cap, 2 per-pair, 3 cap with wide
+    windows), ms per pair, from a profiled run's per-kernel times (each path's kernels with
+    their set-up launches: the tensor belt's planes, the caps' symmetric copy)."""
+    def per(names):
+        return sum(prof[n][0] / prof[n][1] for n in names if n in prof)
+    # the polar rings' launch is a few blocks on a side stream, latency-bound and overlapped
+    # with the rest: its time per pair says little about their share, so the caps' pairs
+    # (narrow and wide) and any per-pair rings take the narrow caps' cost
+    belt = per(("conv_belt_tc", "conv_belt_bf16", "conv_belt", "tc_planes", "belt_weights"))
+    cap = per(("conv_capw", "conv_cap", "cap_sym"))
+    cb = belt / by_launch[0] if by_launch[0] else 0.0
+    cc = cap / by_launch[1] if by_launch[1] else cb
+    return [cb if cb > 0 else cc, cc, cc, cc]
+
+
 def measured_hbm_gbs():
     """HBM copy bandwidth measured on the B300s (MEASURED_PEAKS.json), else the fallback."""
     here = os.path.dirname(os.path.abspath(__file__))
@@ -564,23 +580,29 @@ def run_ours(args):
     # a northern range and its mirror, balanced by estimated cost (symmetric_bands)
     bands = None
     if not args.no_bands and args.workload == "n2048_plain" and world == 1:
-        from paper_1211_3556_b300.bands import symmetric_bands
+        from paper_1211_3556_b300.bands import ring_costs, symmetric_bands
         o = ops[0]
         grp = o["group"]
         xb = o["x"][:1]
         yb = torch.empty_like(xb)
         nb_steps = max(3, min(args.steps, 10))
         full = time_steps(torch, lambda: sk.convolve(o["kern"], xb, out=yb), nb_steps, 1, barrier)
-        bands = {"workload": args.workload, "decomposition": "symmetric_bands (cap_cost 2.5)",
+        # bands balanced by each ring's pairs times the measured cost of a pair on its path
+        costs = path_costs(prof, o["by_launch"])
+        rpairs, rpath = o["kern"].pairs_by_ring()
+        rcost = ring_costs(rpairs, rpath, costs)
+        bands = {"workload": args.workload, "decomposition": "symmetric_bands weighted by pairs x measured "
+                 "per-path pair cost", "path_cost_ns_per_pair": [c * 1e6 for c in costs],
                  "ms_full_map": full, "ranks": {}}
         for nrk in (2, 4, 8):
             per = []
-            for b in symmetric_bands(grp.nside, grp.kernel.theta_cut, nrk):
+            for b in symmetric_bands(grp.nside, grp.kernel.theta_cut, nrk, ring_cost=rcost):
                 lo, hi = b.north
                 if hi > lo:
                     per.append(time_steps(torch, lambda: sk.convolve_rings_sym(o["kern"], xb, lo, hi, out=yb),
                                           nb_steps, 1, barrier))
             bands["ranks"][str(nrk)] = {"ms_per_band": per, "ms_slowest": max(per),
+                                        "ms_spread": max(per) - min(per),
                                         "efficiency_bound": full / (nrk * max(per))}
         del xb, yb
 
@@ -722,7 +744,7 @@ def run_bands(args):
     band (strong scaling: the map is the same at every rank count)."""
     import torch
     import paper_1211_3556_b300 as sk
-    from paper_1211_3556_b300.bands import exchange_halo, symmetric_bands
+    from paper_1211_3556_b300.bands import exchange_halo, ring_costs, symmetric_bands
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -742,7 +764,24 @@ def run_bands(args):
     g, k = build_operator(sk, ctx, group)
     maps = make_maps(group, wl.sources[0] if wl.sources else None)[:1]
     npix = maps.shape[1]
-    bands = symmetric_bands(group.nside, ks.theta_cut, world)
+    # band edges from each ring's pairs times the measured cost of a pair on its path, the
+    # costs measured on rank 0 and sent to every rank (all ranks must cut the same bands)
+    x1 = torch.from_numpy(maps).cuda()
+    y1 = torch.empty_like(x1)
+    k.autotune(x1, out=y1, cache_path=os.path.join(tempfile.gettempdir(), "skconv_belt_tiles.txt"))
+    ctx.profile(True)
+    ctx.profile_read()
+    for _ in range(3):
+        sk.convolve(k, x1, out=y1)
+    torch.cuda.synchronize()
+    costs = torch.tensor(path_costs(ctx.profile_read(), k.count_pairs_by_launch()), dtype=torch.float64,
+                         device="cuda")
+    ctx.profile(False)
+    if world > 1:
+        dist.broadcast(costs, src=0)
+    del x1, y1
+    rpairs, rpath = k.pairs_by_ring()
+    bands = symmetric_bands(group.nside, ks.theta_cut, world, ring_cost=ring_costs(rpairs, rpath, costs.cpu().numpy()))
     me = bands[rank]
     own = np.concatenate([maps[:, q0:q1] for q0, q1 in me.out_pix], axis=1) if me.out_pix else maps[:, :0]
     x_own = torch.from_numpy(np.ascontiguousarray(own)).cuda()
@@ -768,7 +807,8 @@ def run_bands(args):
                 "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "nside": [group.nside], "maps_per_step": 1,
                            "theta_cut_arcmin": ks.theta_cut_arcmin, "decomposition": "symmetric ring bands",
-                           "parallelism": f"ring bands x{world}", "pairs_per_step": pairs},
+                           "parallelism": f"ring bands x{world}", "pairs_per_step": pairs,
+                           "band_balance": "pairs x measured per-path pair cost"},
                 "halo_bytes_recv_rank0": stats.get("recv_bytes", 0), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

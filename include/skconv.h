@@ -188,6 +188,12 @@ int sk_count_pairs_by_path(sk_ctx *ctx, const sk_kern *k, int64_t *out3);
  * SK_EUNSUPPORTED (no plan), SK_ECUDA. */
 int sk_count_pairs_by_launch(sk_ctx *ctx, const sk_kern *k, int64_t *out4);
 
+/* In-cut pairs of each output ring (out: rings entries, RING order) and, if path is not
+ * NULL, each ring's path (rings entries: 0 belt, 1 cap, 2 per-pair, 3 cap with wide
+ * windows) -- the costs a ring-band decomposition balances.  Blocks until done.
+ * Errors: SK_EINVAL, SK_EUNSUPPORTED (path asked for without a plan), SK_ECUDA. */
+int sk_count_pairs_by_ring(sk_ctx *ctx, const sk_kern *k, int64_t *out, uint8_t *path);
+
 /* ---- convolution --------------------------------------------------------- */
 
 /* y = A x for `batch` maps (the real-space convolution above).
@@ -323,8 +329,10 @@ int sk_grad_table_noalloc(sk_ctx *ctx, const sk_kern *k, const float *d_x, const
  * ring bands ordered by distance from the poles: the sums of a band start once
  * the bands its windows reach have arrived, and a band's outputs go back once
  * the sums writing them are done, on two copy streams of the context beside
- * `stream`.  Same results, bit for bit, as sk_convolve on device buffers.
- * Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+ * `stream`.  The bands' sums run the FP32 belt whatever the operator's belt form (a
+ * band's few ring groups would underfill the tensor-core form, and the sums hide behind
+ * the copies): the results are bit for bit those of sk_convolve_path with SK_PATH_FP32
+ * on device buffers.  Uses the context workspace.  Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in, float *h_out,
                      int64_t batch, int64_t map_stride, void *stream);
 

@@ -107,6 +107,7 @@ def _declare(L):
         "sk_kernel_set_cap_weights": (I, [P, I]),
         "sk_kernel_cap_weight_bytes": (I, [P, ctypes.POINTER(I64)]),
         "sk_kernel_set_belt_form": (I, [P, I]),
+        "sk_count_pairs_by_ring": (I, [P, P, P, P]),
         "sk_field_plan": (I, [P, D, D, D, D, P, P]),
         "sk_kernel_get_config": (I, [P, ctypes.POINTER(I64)]),
         "sk_device_info": (I, [P, ctypes.POINTER(I64)]),
@@ -322,6 +323,15 @@ class Kernel:
         a = (ctypes.c_int64 * 4)()
         _check(lib().sk_count_pairs_by_launch(self.ctx._h, self._h, a))
         return [int(v) for v in a]
+
+    def pairs_by_ring(self):
+        """(in-cut pairs of each output ring, each ring's path: 0 belt, 1 cap, 2 per-pair,
+        3 cap with wide windows) -- sk_count_pairs_by_ring."""
+        nr = 4 * self.geom.nside - 1
+        pairs = np.zeros(nr, np.int64)
+        path = np.zeros(nr, np.uint8)
+        _check(lib().sk_count_pairs_by_ring(self.ctx._h, self._h, pairs.ctypes.data, path.ctypes.data))
+        return pairs, path
 
     def autotune(self, x, out=None, cache_path=None, stream=None) -> int:
         """Time the belt forms (FP32 with every tile width, tensor cores) and stored

@@ -106,16 +106,31 @@ class SymBand:
     in_pix: tuple
 
 
-def symmetric_bands(nside: int, theta_cut: float, world: int, cap_cost: float = 2.5) -> list:
+def ring_costs(pairs, path, cost_per_pair) -> np.ndarray:
+    """Cost of each output ring: its in-cut pairs (Kernel.pairs_by_ring) times the measured
+    cost of one pair on the ring's path (cost_per_pair[path]: 0 belt, 1 cap, 2 per-pair,
+    3 cap with wide windows)."""
+    c = np.asarray(cost_per_pair, dtype=np.float64)
+    return np.asarray(pairs, dtype=np.float64) * c[np.asarray(path, dtype=np.int64)]
+
+
+def symmetric_bands(nside: int, theta_cut: float, world: int, cap_cost: float = 2.5, ring_cost=None) -> list:
     """Split the northern rings (the equator included) into `world` contiguous ranges of
-    about equal estimated cost, each with its mirror about the equator.  The cost of a
-    northern ring: its pixels, twice (the ring and its mirror; the equator once), times
+    about equal cost, each with its mirror about the equator.  The cost of a northern ring
+    is ring_cost[r] + ring_cost[mirror] (the equator once) when ring_cost (one entry per
+    ring, e.g. ring_costs()) is given; otherwise the model: its pixels, twice, times
     cap_cost on the polar-cap rings (ring index below Nside, 1-based)."""
     n, start, theta = ring_table(nside)
     nr = len(n)
     N = int(nside)
     eq = 2 * N - 1                                    # the equator ring (0-based), its own mirror
-    w = np.array([n[r] * (cap_cost if r < N - 1 else 1.0) * (1.0 if r == eq else 2.0) for r in range(eq + 1)])
+    if ring_cost is not None:
+        rc = np.asarray(ring_cost, dtype=np.float64)
+        if rc.shape != (nr,):
+            raise ValueError("ring_cost needs one entry per ring")
+        w = np.array([rc[r] + (0.0 if r == eq else rc[nr - 1 - r]) for r in range(eq + 1)])
+    else:
+        w = np.array([n[r] * (cap_cost if r < N - 1 else 1.0) * (1.0 if r == eq else 2.0) for r in range(eq + 1)])
     cum = np.cumsum(w)
     world = max(1, min(int(world), eq + 1))
     edges = [0]

@@ -527,6 +527,28 @@ extern "C" int sk_count_pairs(sk_ctx *ctx, const sk_kern *k, int64_t *out) {
     return SK_OK;
 }
 
+extern "C" int sk_count_pairs_by_ring(sk_ctx *ctx, const sk_kern *k, int64_t *out, uint8_t *path) {
+    if (!ctx || !k || !out) return sk_fail(SK_EINVAL, "sk_count_pairs_by_ring: NULL argument");
+    const int nr = k->g->nr;
+    if (path) {
+        if (!k->plan_ok) return sk_fail(SK_EUNSUPPORTED, "sk_count_pairs_by_ring: no plan");
+        for (int r = 0; r < nr; ++r) path[r] = k->h_ring_path[r];
+    }
+    SK_CU(cudaSetDevice(ctx->device));
+    unsigned long long *d_c = nullptr;
+    SK_CU(cudaMalloc(&d_c, sizeof(unsigned long long) * nr));
+    cudaError_t e = cudaMemset(d_c, 0, sizeof(unsigned long long) * nr);
+    if (e == cudaSuccess)
+        e = sk_launch_count_pairs(nr, (int)(4 * k->g->nside), k->g->d_rings, k->d_pair_off, k->d_pairs, k->d_dphimax,
+                                  nullptr, d_c, 0, true);
+    std::vector<unsigned long long> h(nr);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), d_c, sizeof(unsigned long long) * nr, cudaMemcpyDeviceToHost);
+    cudaFree(d_c);
+    if (e != cudaSuccess) return sk_fail(SK_ECUDA, "sk_count_pairs_by_ring: %s", cudaGetErrorString(e));
+    for (int r = 0; r < nr; ++r) out[r] = (int64_t)h[r];
+    return SK_OK;
+}
+
 extern "C" int sk_count_pairs_by_launch(sk_ctx *ctx, const sk_kern *k, int64_t *out4) {
     if (!ctx || !k || !out4) return sk_fail(SK_EINVAL, "sk_count_pairs_by_launch: NULL argument");
     if (!k->plan_ok) return sk_fail(SK_EUNSUPPORTED, "operator has no plan");
@@ -707,7 +729,7 @@ extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in
     SkJob one = jb;
     one.batch = 1;
     void *ws = nullptr;
-    int rc = sk_ctx_workspace(ctx, 2 * half + sk_jobs_workspace_bytes(&one, 1), &ws);
+    int rc = sk_ctx_workspace(ctx, 2 * half + sk_jobs_workspace_bytes(&one, 1, SK_PATH_FP32), &ws);
     if (rc) return rc;
     float *d_in = (float *)ws, *d_out = (float *)((char *)ws + half);
     void *wsj = (char *)ws + 2 * half;
@@ -715,7 +737,7 @@ extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in
         jb.x = d_in;
         jb.y = d_out;
         SK_CU(cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, st));
-        if ((rc = sk_run_jobs(ctx, &jb, 1, SK_PATH_AUTO, wsj, st))) return rc;
+        if ((rc = sk_run_jobs(ctx, &jb, 1, SK_PATH_FP32, wsj, st))) return rc;
         SK_CU(cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st));
         SK_CU(cudaStreamSynchronize(st));
         return SK_OK;
@@ -746,7 +768,9 @@ extern "C" int sk_convolve_host(sk_ctx *ctx, const sk_kern *k, const float *h_in
             SkJob j{k, d_in + mo, d_out + mo, 1, map_stride};
             j.sub = &B.items;
             j.weights = (m == 0 && b == 0);      // the belt weight rows stay in the workspace
-            if ((rc = sk_run_jobs(ctx, &j, 1, SK_PATH_AUTO, wsj, st))) return rc;
+            // the FP32 belt: a band's few ring groups underfill the tensor-core form's one-CTA-
+            // per-SM launch, and the sums hide behind the copies either way
+            if ((rc = sk_run_jobs(ctx, &j, 1, SK_PATH_FP32, wsj, st))) return rc;
             SK_CU(cudaEventRecord(ctx->ev_out[b], st));
             SK_CU(cudaStreamWaitEvent(ctx->d2h, ctx->ev_out[b], 0));
             // every band whose outputs are complete once this band's sums are done

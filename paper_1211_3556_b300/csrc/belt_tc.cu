@@ -71,6 +71,12 @@ __host__ __device__ inline Stage stage_of(int kmax, int nn, bool bf) {
     return s;
 }
 
+// Ring group of the gi-th group a launch runs (two ranges, the second possibly empty).
+__device__ __forceinline__ int group_of(const TcArgs &T, int gi) {
+    const int na = T.ga1 - T.ga0;
+    return gi < na ? T.ga0 + gi : T.gb0 + (gi - na);
+}
+
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status) {
     if (*abort_flag) return false;
     if (tc::mbar_wait(bar, parity, LIMIT)) return true;
@@ -126,9 +132,9 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         if (lane == 0) {
             uint32_t cnt = 0;
             for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
-                const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
+                const int gi = f / per_g, rem = f - gi * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
                 const int j0 = pb * 8 * T.nn;
-                const int4 tr = T.trng[g];
+                const int4 tr = T.trng[group_of(T, gi)];
                 const float4 *zb = T.Z + (size_t)b * T.nz * NPL * T.zrows;
                 for (int u = 0; u < tr.y; ++u, ++cnt) {
                     const int4 tl = T.tiles[tr.x + u];            // (input ring, E0, K | flags, A offset in KB)
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
             const uint32_t idesc = BF ? tc::idesc_bf16(128, T.nn) : tc::idesc_tf32(128, T.nn);
             bool need_empty = false;                              // the next tile opens a chunk
             for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
-                const int ntile = T.trng[f / per_g].y;
+                const int ntile = T.trng[group_of(T, f / per_g)].y;
                 for (int u = 0; u < ntile; ++u, ++cnt) {
                     const int s = (int)(cnt % (uint32_t)S);
                     const int ab = (int)(ccnt & 1);               // accumulator of this chunk
@@ -239,7 +245,8 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         const int nch = (T.nn - 16 * half + 31) / 32;
         uint32_t ccnt = 0;
         for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
-            const int g = f / per_g, rem = f - g * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
+            const int gi = f / per_g, rem = f - gi * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
+            const int g = group_of(T, gi);
             const int j0 = pb * 8 * T.nn;
             const int nchunk = T.trng[g].z;
             float acc[CH][16];
@@ -346,13 +353,14 @@ __global__ void k_tc_tiles(const __grid_constant__ TcTileArgs T, const int *gate
 // 3xTF32 four planes of 16-byte rows -- hi even (first four pixels), hi odd, lo even,
 // lo odd; BF16x3 two planes of 16-byte rows (eight BF16 values) -- hi, lo.
 __global__ void k_tc_planes(const float *__restrict__ x, long long stride, const RingDev *__restrict__ rings, int zi0,
-                            int nz, int zrows, int pbase, int n4, long long total, float4 *__restrict__ Z, bool bf) {
+                            int nz, int ri_lo, int nri, int zrows, int pbase, int n4, long long total,
+                            float4 *__restrict__ Z, bool bf) {
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(idx % zrows);
         const long long rest = idx / zrows;
-        const int ri = (int)(rest % nz);
-        const long long b = rest / nz;
+        const int ri = ri_lo + (int)(rest % nri);
+        const long long b = rest / nri;
         const float *xr = x + b * stride + rings[zi0 + ri].start;
         int p = (pbase + 8 * m) % n4;
         if (p < 0) p += n4;
@@ -430,10 +438,14 @@ cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st
 }
 
 cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
-                                int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms, cudaStream_t st) {
-    const long long total = (long long)batch * nz * zrows;
+                                int ri_lo, int ri_hi, int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms,
+                                cudaStream_t st) {
+    ri_lo = std::max(0, ri_lo);
+    ri_hi = std::min(nz, ri_hi);
+    const long long total = (long long)batch * (ri_hi - ri_lo) * zrows;
     if (total <= 0) return cudaSuccess;
     const long long blocks = std::min<long long>((total + 255) / 256, (long long)sms * 16);
-    k_tc_planes<<<(unsigned)blocks, 256, 0, st>>>(x, stride, rings, zi0, nz, zrows, pbase, n4, total, Z, bf16);
+    k_tc_planes<<<(unsigned)blocks, 256, 0, st>>>(x, stride, rings, zi0, nz, ri_lo, ri_hi - ri_lo, zrows, pbase, n4,
+                                                  total, Z, bf16);
     return cudaGetLastError();
 }

@@ -138,7 +138,8 @@ __global__ void k_make_table(const double *V, int nt, double dOmega, float2 *tab
 // Exact pair count: on ring i the in-cut pixels of output (o, jo) are those with
 // |phi_j - phi_o| <= dphi_max (gamma grows with |dphi|), an integer interval.
 __global__ void k_count_pairs(int nr, const RingDev *rings, const int *off, const PairInfo *pairs,
-                              const double *dphimax, const unsigned char *cls, unsigned long long *total) {
+                              const double *dphimax, const unsigned char *cls, unsigned long long *total,
+                              bool per_ring) {
     int o = blockIdx.y;
     int jo = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long c = 0;
@@ -165,7 +166,7 @@ __global__ void k_count_pairs(int nr, const RingDev *rings, const int *off, cons
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && red[0]) atomicAdd(total + (cls && o < nr ? cls[o] : 0), red[0]);
+    if (threadIdx.x == 0 && red[0]) atomicAdd(total + (per_ring ? o : (cls && o < nr ? cls[o] : 0)), red[0]);
 }
 
 }  // namespace
@@ -220,8 +221,8 @@ cudaError_t sk_launch_update_values(const double *nv, double *V, int nt, int *ch
 
 cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const int *off,
                                   const PairInfo *pairs, const double *dphimax, const unsigned char *cls,
-                                  unsigned long long *total, cudaStream_t st) {
+                                  unsigned long long *total, cudaStream_t st, bool per_ring) {
     dim3 grid((max_n + 255) / 256, nr);
-    k_count_pairs<<<grid, 256, 0, st>>>(nr, rings, off, pairs, dphimax, cls, total);
+    k_count_pairs<<<grid, 256, 0, st>>>(nr, rings, off, pairs, dphimax, cls, total, per_ring);
     return cudaGetLastError();
 }

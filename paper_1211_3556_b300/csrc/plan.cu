@@ -428,6 +428,7 @@ int sk_plan_build(sk_kern *k) {
                 }
         int rc;
         if ((rc = upload(grp, &k->d_bgrp))) return rc;
+        k->h_bgrp = grp;
         if ((rc = upload(pr, &k->d_bpr))) return rc;
         k->belt_P = belt_cost_p(n4);
         if ((rc = sk_plan_rebuild_belt_items(k))) return rc;
@@ -529,6 +530,7 @@ int sk_plan_build(sk_kern *k) {
             for (int j = 0; j < R[r].n; j += 128) gen.push_back(make_int4(r, j, 0, 0));
         }
     if (int rc0 = upload(path, &k->d_ring_path)) return rc0;
+    k->h_ring_path = path;
     k->n_items_gen = (int)gen.size();
     k->h_items_gen = gen;
     int rc = upload(gen, &k->d_items_gen);
@@ -688,8 +690,20 @@ int sk_job_wants_tc(const SkJob &j, int path) {
     else if (path == SK_PATH_BF16X3) f = 1;
     else if (path == SK_PATH_AUTO && k->belt_form == SK_BELT_TENSOR) f = 0;
     else if (path == SK_PATH_AUTO && k->belt_form == SK_BELT_BF16X3) f = 1;
-    if (f < 0 || j.sub || !k->plan_ok || k->nb == 0 || !k->tcp[f].ok || j.batch <= 0) return -1;
+    if (f < 0 || !k->plan_ok || k->nb == 0 || !k->tcp[f].ok || j.batch <= 0) return -1;
     return f;
+}
+
+// The belt ring groups a job runs: [g[0], g[1]) and [g[2], g[3]) (a ring subset's
+// northern groups and their mirror; the whole belt otherwise).
+static void job_groups(const SkJob &j, int g[4]) {
+    const SkItems *sub = j.sub;
+    if (!sub || sub->bg[0][1] < 0) {
+        g[0] = 0; g[1] = j.k->ngroups; g[2] = g[3] = 0;
+        return;
+    }
+    g[0] = sub->bg[0][0]; g[1] = sub->bg[0][1]; g[2] = sub->bg[1][0]; g[3] = sub->bg[1][1];
+    if (sub->n_belt == 0) g[0] = g[1] = g[2] = g[3] = 0;
 }
 
 // Map planes of a tensor form for a job: 3xTF32 four planes of 4-pixel rows (hi/lo x
@@ -988,10 +1002,19 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             const sk_kern *k = jobs[i].k;
             const TcPlan &T = k->tcp[f];
             void *z = zp[i];
+            int gr[4];
+            job_groups(jobs[i], gr);
+            if (gr[1] <= gr[0] && gr[3] <= gr[2]) continue;       // a subset without belt rings
+            // the planes of the input rings the groups read (every belt input ring for the
+            // whole operator)
             cudaEvent_t ev = sk_prof_begin(ctx, st);
-            SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, T.zi0, T.nz,
-                                      T.zrows, T.pbase, (int)(4 * k->g->nside), (float4 *)z, f == 1, ctx->num_sms,
-                                      st));
+            for (int q = 0; q < 2; ++q) {
+                if (gr[2 * q + 1] <= gr[2 * q]) continue;
+                const int r0 = k->h_bgrp[gr[2 * q]].x - T.zi0, r1 = k->h_bgrp[gr[2 * q + 1] - 1].y - T.zi0 + 1;
+                SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, T.zi0, T.nz,
+                                          r0, r1, T.zrows, T.pbase, (int)(4 * k->g->nside), (float4 *)z, f == 1,
+                                          ctx->num_sms, st));
+            }
             sk_prof_end(ctx, "tc_planes", ev, st);
             TcArgs a;
             memset(&a, 0, sizeof a);
@@ -1015,7 +1038,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             a.kmax = T.kmax;
             a.nstages = T.stages;
             a.bf16 = f;
-            a.total = k->ngroups * (int)jobs[i].batch * T.nblk;
+            a.ga0 = gr[0]; a.ga1 = gr[1]; a.gb0 = gr[2]; a.gb1 = gr[3];
+            a.total = ((gr[1] - gr[0]) + (gr[3] - gr[2])) * (int)jobs[i].batch * T.nblk;
             a.status = ctx->d_status;
             ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_belt_tc(a, std::min(a.total, ctx->num_sms), st));

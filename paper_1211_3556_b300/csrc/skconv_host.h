@@ -122,6 +122,7 @@ struct sk_kern {
     // the cap kernel reads the symmetric copy of input rings [0, sym_hi): sym_stride float4 per map
     int sym_hi = 0;
     long long sym_stride = 0;
+    std::vector<unsigned char> h_ring_path;
     unsigned char *d_ring_path = nullptr;  // per output ring: 0 belt, 1 cap (either hemisphere) with
                                            // narrow windows, 3 cap with wide or whole-ring windows,
                                            // 2 general
@@ -150,6 +151,7 @@ struct sk_kern {
     // from the nearest pole (sk_convolve_host overlaps the copies of one band with the
     // sums of another); rebuilt when the belt tile width changes
     std::vector<int4> h_items_belt, h_items_cap[SK_CAP_LS_CLASSES][2], h_items_gen;
+    std::vector<int2> h_bgrp;              // per belt ring group: first and last input ring
     struct Band {
         int n_lo, n_hi, s_lo, s_hi;   // output rings [n_lo, n_hi) and [s_lo, s_hi)
         int need;                     // last band whose input rings the sums read

@@ -103,6 +103,7 @@ struct TcArgs {
     int zi0, nz, zrows, pbase;  // first plane ring, plane rings, rows per plane, pixel of row 0
     int nn, nblk, kmax, nstages;
     int bf16;                   // 0: 3xTF32 (TF32 parts, 4-pixel plane rows), 1: BF16x3 (8-pixel rows)
+    int ga0, ga1, gb0, gb1;     // the ring groups run: [ga0, ga1) then [gb0, gb1)
     int total;                  // items: groups x maps x pixel blocks
     int *status;
 };
@@ -123,8 +124,10 @@ int sk_tc_stages(int kmax, int nn, bool bf16, size_t *smem);
 cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st);
 // A tiles of all n_tiles tiles; with `gate`, only if *gate is non-zero
 cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st, const int *gate = nullptr);
+// planes of the plane rings [ri_lo, ri_hi) (relative to zi0; the layout holds nz rings)
 cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
-                                int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms, cudaStream_t st);
+                                int ri_lo, int ri_hi, int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms,
+                                cudaStream_t st);
 
 // set-up kernels (geometry.cu)
 cudaError_t sk_launch_ring_geom(long long nside, RingDev *rings, double *z, double *rho,
@@ -141,9 +144,10 @@ cudaError_t sk_launch_make_table(const double *V, int nt, double dOmega, float2 
                                  const int *gate = nullptr);
 // V = nv where they differ (one block, nt <= 16384); *changed = 1 if they did, else 0
 cudaError_t sk_launch_update_values(const double *nv, double *V, int nt, int *changed, cudaStream_t st);
+// in-cut pairs summed per class cls[ring] (total[0] if cls is null), or per output ring
 cudaError_t sk_launch_count_pairs(int nr, int max_n, const RingDev *rings, const int *off,
                                   const PairInfo *pairs, const double *dphimax, const unsigned char *cls,
-                                  unsigned long long *total, cudaStream_t st);
+                                  unsigned long long *total, cudaStream_t st, bool per_ring = false);
 
 // convolution kernels; grid = number of blocks (persistent)
 cudaError_t sk_launch_conv_general(const JobsArg &a, int grid, cudaStream_t st);

@@ -77,9 +77,11 @@ def test_bands_stitch_to_the_full_operator(sk, case, outside):
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_symmetric_bands_stitch_to_the_full_operator(sk, case):
+@pytest.mark.parametrize("form", ["fp32", "tensor"])
+def test_symmetric_bands_stitch_to_the_full_operator(sk, case, form):
     # bands of a northern range and its mirror (convolve_rings_sym), from inputs that hold the
-    # halo and noise elsewhere: stitched, bit-identical to the full operator
+    # halo and noise elsewhere: stitched, bit-identical to the full operator -- with the belt
+    # on the CUDA cores or on the tensor cores (the subset's ring groups only)
     import torch
     from paper_1211_3556_b300.bands import symmetric_bands
     nside, fwhm, tcm, lmax, lcut, nt, world, batch = case
@@ -87,6 +89,10 @@ def test_symmetric_bands_stitch_to_the_full_operator(sk, case):
     V = O.tabulate_real_kernel(gaussian_beam(fwhm, lmax), lcut, lmax, tc, nt, 0)
     g = sk.Geometry(sk._ctx, nside)
     k = sk.Kernel(g, V, tc, 0)
+    if form == "tensor":
+        if not k.config()["tensor_form_available"]:
+            pytest.skip("windows too wide for the tensor form")
+        k.set_belt_form(sk.BELT_TENSOR)
     x = white_noise_maps(nside, batch, 1350 + nside)
     y_full = sk.convolve(k, torch.from_numpy(x).cuda()).cpu().numpy()
     stitched = np.full_like(y_full, np.nan)

@@ -226,3 +226,26 @@ def test_symmetric_bands_tile_the_rings_cover_the_windows_and_balance(nside, deg
                         for r in range(lo, hi)))
     ring_max = max(n[r] * 2.5 * 2 for r in range(2 * nside))
     assert max(cost) - min(cost) <= 2 * ring_max + 1e-9
+
+
+@pytest.mark.parametrize("nside,world", [(64, 4), (256, 8)])
+def test_symmetric_bands_balance_given_ring_costs(nside, world):
+    # with per-ring costs (pairs x the measured cost of a pair on the ring's path) every band
+    # carries its share of the total within the cost of one northern ring (ring + mirror)
+    from paper_1211_3556_b300.bands import ring_costs, ring_table, symmetric_bands
+    n, _, _ = ring_table(nside)
+    nr = len(n)
+    rng = np.random.default_rng(nside + world)
+    pairs = (n * rng.uniform(50, 150, nr)).astype(np.int64)
+    path = np.where(np.arange(nr) < nside, 1, 0).astype(np.uint8)
+    path[nr - nside:] = 1
+    rc = ring_costs(pairs, path, [1.0, 4.0, 2.0, 3.0])
+    assert np.allclose(rc[path == 1], 4.0 * pairs[path == 1])
+    bands = symmetric_bands(nside, 0.05, world, ring_cost=rc)
+    eq = 2 * nside - 1
+    w = np.array([rc[r] + (0.0 if r == eq else rc[nr - 1 - r]) for r in range(eq + 1)])
+    cost = [w[b.north[0]:b.north[1]].sum() for b in bands]
+    assert abs(sum(cost) - w.sum()) < 1e-6 * w.sum()
+    assert max(abs(c - w.sum() / world) for c in cost) <= w.max() + 1e-9 * w.sum()
+    with pytest.raises(ValueError):
+        symmetric_bands(nside, 0.05, world, ring_cost=rc[:-1])
