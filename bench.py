@@ -192,13 +192,15 @@ def path_costs(prof, by_launch):
     their set-up launches: the tensor belt's planes, the caps' symmetric copy)."""
     def per(names):
         return sum(prof[n][0] / prof[n][1] for n in names if n in prof)
-    # the polar rings' launch is a few blocks on a side stream, latency-bound and overlapped
-    # with the rest: its time per pair says little about their share, so the caps' pairs
-    # (narrow and wide) and any per-pair rings take the narrow caps' cost
+    # the evaluating kernels' polar launch is a few blocks on a side stream, latency-bound
+    # and overlapped with the rest: its time per pair says little about their share, so
+    # there the caps' pairs (narrow and wide) and any per-pair rings take the narrow caps'
+    # cost; the stored-weight launch sums both kinds of cap rings
     belt = per(("conv_belt_tc", "conv_belt_bf16", "conv_belt", "tc_planes", "belt_weights"))
     cap = per(("conv_capw", "conv_cap", "cap_sym"))
+    cap_pairs = by_launch[1] + (by_launch[2] if "conv_capw" in prof else 0)
     cb = belt / by_launch[0] if by_launch[0] else 0.0
-    cc = cap / by_launch[1] if by_launch[1] else cb
+    cc = cap / cap_pairs if cap_pairs else cb
     return [cb if cb > 0 else cc, cc, cc, cc]
 
 
@@ -382,13 +384,14 @@ def run_ours(args):
 
     # roofline of the dominant kernel: F_mac flops per pair of the outputs it evaluates
     dom = max(prof, key=lambda n: prof[n][0]) if prof else None
-    # the pairs each launch sums (sk_count_pairs_by_launch): belt, caps with narrow windows,
-    # caps with wide windows (polar rings, side stream), per-pair rings
-    launch_idx = {"conv_belt": 0, "conv_belt_tc": 0, "conv_cap": 1, "conv_capw": 1, "conv_cap_polar": 2,
-                  "conv_capw_polar": 2, "conv_general": 3}
+    # the pairs each launch sums (sk_count_pairs_by_launch: belt, caps with narrow windows,
+    # caps with wide windows, per-pair rings); the stored-weight cap launch takes both kinds
+    # of cap rings, the evaluating kernels one launch each (the wide one on a side stream)
+    launch_idx = {"conv_belt": (0,), "conv_belt_tc": (0,), "conv_cap": (1,), "conv_capw": (1, 2),
+                  "conv_cap_polar": (2,), "conv_general": (3,)}
     roofline = None
     if dom in launch_idx:
-        dom_pairs = sum(o["by_launch"][launch_idx[dom]] * o["group"].batch for o in ops)
+        dom_pairs = sum(sum(o["by_launch"][q] for q in launch_idx[dom]) * o["group"].batch for o in ops)
         launch_ms = prof[dom][0] / prof[dom][1]
         per_launch_pairs = dom_pairs * args.steps / prof[dom][1]
         achieved = FLOP_PER_PAIR * per_launch_pairs / (launch_ms * 1e-3) / 1e12

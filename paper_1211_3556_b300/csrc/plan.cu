@@ -1081,30 +1081,32 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
     }
 
     // caps; the launches on `st` wait for the copies.  Jobs with stored weights: one launch
-    // per (strip class, narrow windows or not), any tables together
+    // per strip class, any tables together, on `st`: the items of rings with wide windows
+    // (the polar rings: few items, each a long run of whole-ring strips) first, so that
+    // the work queue hands them out before the many narrow-window items, and no launch
+    // beside the tensor-core belt holds SMs its static schedule is waiting for
     SK_CU(cudaEventRecord(ctx->ev_sym, side));
     SK_CU(cudaStreamWaitEvent(st, ctx->ev_sym, 0));
     for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
-        for (int v = 1; v >= 0; --v)
         for (int blk = 0; blk < 2; ++blk) {
             Batcher b;
             auto flush = [&]() -> int {
                 if (b.a.total > 0) {
                     b.a.status = ctx->d_status;
-                    cudaStream_t cs = v ? st : side;
-                    cudaEvent_t ev = sk_prof_begin(ctx, cs);
+                    cudaEvent_t ev = sk_prof_begin(ctx, st);
                     const int ipb = sk_capw_items_per_block(SK_CAP_LS[c], blk != 0);
                     const int blocks = (b.a.total + ipb - 1) / ipb;
                     int *q = ctx->d_queue + ctx->next_queue;
                     ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
-                    SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));
+                    SK_CU(cudaMemsetAsync(q, 0, sizeof(int), st));
                     b.a.queue = q;
-                    SK_CU(sk_launch_conv_capw(b.a, SK_CAP_LS[c], blk != 0, std::min(blocks, ctx->num_sms), cs));
-                    sk_prof_end(ctx, v ? "conv_capw" : "conv_capw_polar", ev, cs);
+                    SK_CU(sk_launch_conv_capw(b.a, SK_CAP_LS[c], blk != 0, std::min(blocks, ctx->num_sms), st));
+                    sk_prof_end(ctx, "conv_capw", ev, st);
                 }
                 b.reset();
                 return SK_OK;
             };
+            for (int v = 0; v < 2; ++v)
             for (int i = 0; i < n; ++i) {
                 const sk_kern *k = jobs[i].k;
                 const SkItems *sub = jobs[i].sub;

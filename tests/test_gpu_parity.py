@@ -201,14 +201,18 @@ def test_config_n2048_sampled_outputs(sk):
     assert rms_rel(y[outs], yo) <= RMS_BOUND
 
 
-def test_config_n8192_sampled_outputs(sk):
+@pytest.mark.parametrize("form", ["fp32", "tensor"])
+def test_config_n8192_sampled_outputs(sk, form):
     # the largest workload (Nside 8192, 16384 nodes, 3.2 GB per map) in bench.py's
-    # launch configuration, on sampled outputs
+    # launch configuration, on sampled outputs, with each belt form
     grp = WORKLOADS["n8192_plain"].groups[0]
     ks = grp.kernel
     V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
     g = sk.Geometry(sk._ctx, grp.nside)
     k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+    if form == "tensor":
+        assert k.config()["tensor_form_available"]
+        k.set_belt_form(sk.BELT_TENSOR)
     x = white_noise_maps(grp.nside, 1, grp.seed)
     y = gpu_conv(sk, k, x)[0]
     outs = np.concatenate([sample_indices(x.shape[1], 5000, 503), _special_pixels(grp.nside)])
@@ -216,9 +220,10 @@ def test_config_n8192_sampled_outputs(sk):
     assert rms_rel(y[outs], yo) <= RMS_BOUND
 
 
-def test_config_mixed_batch_sampled_outputs(sk):
+@pytest.mark.parametrize("form", ["fp32", "tensor"])
+def test_config_mixed_batch_sampled_outputs(sk, form):
     # the uneven batch (8 x Nside 256, 8 x 512, 4 x 1024, 2 x 2048, four kernels) in one
-    # convolve_jobs call, every map checked on sampled outputs
+    # convolve_jobs call, every map checked on sampled outputs, with each belt form
     import torch
     wl = WORKLOADS["mixed_batch"]
     jobs, keep = [], []
@@ -227,6 +232,9 @@ def test_config_mixed_batch_sampled_outputs(sk):
         V = O.tabulate_real_kernel(ks.beam(), ks.lcut, ks.lmax, ks.theta_cut, ks.n_nodes, ks.layout)
         g = sk.Geometry(sk._ctx, grp.nside)
         k = sk.Kernel(g, V, ks.theta_cut, ks.layout)
+        if form == "tensor":
+            assert k.config()["tensor_form_available"]
+            k.set_belt_form(sk.BELT_TENSOR)
         x = white_noise_maps(grp.nside, grp.batch, grp.seed)
         xt = torch.from_numpy(x).cuda()
         yt = torch.empty_like(xt)
