@@ -204,6 +204,31 @@ def path_costs(prof, by_launch):
     return [cb if cb > 0 else cc, cc, cc, cc]
 
 
+def copy_floor(torch, hx, hy, reps):
+    """The same bytes copied alone between the pinned host buffers and the device: host to
+    device, device to host, and both at once on two streams (the floor an end-to-end call
+    that overlaps its sums with the copies approaches), ms per step."""
+    d = torch.empty(hx.shape, dtype=hx.dtype, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out = {}
+    for name in ("h2d", "d2h", "both"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            if name in ("h2d", "both"):
+                with torch.cuda.stream(s1):
+                    d.copy_(hx, non_blocking=True)
+            if name in ("d2h", "both"):
+                with torch.cuda.stream(s2):
+                    hy.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        out[name] = (time.perf_counter() - t0) / reps * 1e3
+    out["h2d_gbs"] = hx.numel() * hx.element_size() / out["h2d"] * 1e-6
+    out["d2h_gbs"] = hy.numel() * hy.element_size() / out["d2h"] * 1e-6
+    del d
+    return out
+
+
 def measured_hbm_gbs():
     """HBM copy bandwidth measured on the B300s (MEASURED_PEAKS.json), else the fallback."""
     here = os.path.dirname(os.path.abspath(__file__))
@@ -439,7 +464,8 @@ def run_ours(args):
         nbytes = int(o["maps"].nbytes)
         e2e = {"value": aggregate_rate(pairs_step, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
-               "api": "sk_convolve_host (pinned host buffers)"}
+               "api": "sk_convolve_host (pinned host buffers)",
+               "copy_floor_ms": copy_floor(torch, hx, hy, k_e2e)}
         del hx, hy
 
     # the batched forms beside the plain one (64 maps at Nside 1024 sharing one kernel):

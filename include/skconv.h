@@ -70,7 +70,7 @@ extern "C" {
 
 /* Belt forms of an operator (sk_kernel_set_belt_form). */
 #define SK_BELT_FP32       0   /* FP32 FMAs, ring-pair weight rows streamed with the strips   */
-#define SK_BELT_TENSOR     1   /* 3xTF32 tcgen05 MMAs (stored weight tiles, per-call map planes) */
+#define SK_BELT_TENSOR     1   /* 3xTF32 tcgen05 MMAs (stored weight tiles x the maps read in sliding rows) */
 #define SK_BELT_BF16X3     2   /* the same with BF16x3 products: about twice the MMA rate, ~1e-5 */
                                /* relative error (outside the 1e-6 bound; never chosen by the    */
                                /* autotuner)                                                     */

@@ -13,16 +13,17 @@
 // to a multiple of 4 and K_i covers the union plus the 7 extra columns of the
 // 8 output pixels (a multiple of 8).  For k-step q the B operand is
 // B_q[s][t] = x_i[j0 + E0 + 8 (s + q) + t]: the input ring read in sliding rows.
-// Staged as two planes of 16-byte rows -- pixels 8m .. 8m+3 and 8m+4 .. 8m+7 of
-// the ring from the tile's first 4-pixel row when that row is even, else the odd
-// rows from it and the even rows one on -- every k-step of both operands is a
-// start address in shared memory (no-swizzle K-major, rows 16 bytes apart, the
-// second plane one plane further), so nothing is rebuilt inside the loop:
+// Staged as two slots of 16-byte rows -- the 4-pixel rows v = 0, 2, 4, .. and
+// v = 1, 3, 5, .. of the ring from the tile's first column on (pixels j0 + E0 + 4 v
+// .. + 3, wrapped around the ring) -- every k-step of both operands is a start
+// address in shared memory (no-swizzle K-major, rows 16 bytes apart, the second slot
+// one slot further), so nothing is rebuilt inside the loop:
 //  * A (TF32 hi and lo parts) is stored per (group, input ring) with the
 //    operator (k_tc_tiles) and rebuilt with its table;
-//  * the maps' planes (hi and lo parts, wrapped around each ring) are written
-//    by one pass per call (k_tc_planes);
-// one producer thread streams both into shared memory with 1-D bulk copies.
+//  * the map rows are read as they are: one producer thread bulk-copies (1-D TMA)
+//    each tile's A and the raw pixels of its input ring into a pipeline stage, and
+//    two converter warps split the pixels into TF32 hi and lo parts and write them
+//    into the stage's operand slots.
 // 3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation): the tiles of a group are
 // taken in chunks of consecutive input rings with at least SK_TC_CHUNK_KSTEPS
 // k-steps; each chunk is accumulated by the tensor cores in a fresh
@@ -39,8 +40,8 @@
 // bits per operand), outside the 1e-6 bound -- reported beside 3xTF32, never chosen by
 // the autotuner.
 // Warp roles: 0 producer (bulk copies), 1 MMA issuer, 2..9 epilogue (tensor
-// memory -> registers -> outputs).  Every wait is bounded and records
-// SK_ETIMEOUT.
+// memory -> registers -> outputs), 10..11 converters (raw pixels -> operand
+// slots).  Every wait is bounded and records SK_ETIMEOUT.
 #include <string.h>
 
 #include <algorithm>
@@ -54,20 +55,24 @@ constexpr int RG = SK_BELT_G;          // output rings per item
 constexpr int SO = 128 / RG;           // output pixels per ring per segment
 static_assert(RG * SO == 128, "M must be 128");
 constexpr int NEPI = 8;                // epilogue warps
-constexpr int NT = 32 * (2 + NEPI);
+constexpr int NCONV = 2;               // converter warps
+constexpr int NT = 32 * (2 + NEPI + NCONV);
 constexpr unsigned long long LIMIT = 2000000000ull;
 
 // One pipeline stage: A (hi then lo, K x 512 bytes each for TF32, K x 256 for BF16,
-// room for kmax), then the plane slots of `slot` bytes (nn + kmax/8 rows of 16 bytes):
-// two hi and two lo for 3xTF32, one hi and one lo for BF16x3.
+// room for kmax), then the operand slots of `slot` bytes (nn + kmax/8 rows of 16
+// bytes): two hi and two lo for 3xTF32, one hi and one lo for BF16x3; then the raw
+// pixels the slots are made from (8 (nn + kmax/8) floats).
 struct Stage {
-    uint32_t a_bytes, slot, bytes;
+    uint32_t a_bytes, slot, raw, bytes;
 };
 __host__ __device__ inline Stage stage_of(int kmax, int nn, bool bf) {
     Stage s;
     s.a_bytes = 2u * (uint32_t)kmax * (bf ? 256u : 512u);
     s.slot = (uint32_t)(nn + kmax / 8) * 16u;
-    s.bytes = (s.a_bytes + (bf ? 2u : 4u) * s.slot + 1023u) & ~1023u;
+    s.raw = (uint32_t)(nn + kmax / 8) * 32u;
+    // no-swizzle operands and bulk copies need 16-byte alignment; stages on 128 bytes
+    s.bytes = (s.a_bytes + (bf ? 2u : 4u) * s.slot + s.raw + 127u) & ~127u;
     return s;
 }
 
@@ -91,8 +96,9 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 template <bool BF>
 __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArgs T) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     __shared__ __align__(8) uint64_t full_bar[SK_TC_MAX_STAGES];    // copies of a stage landed
+    __shared__ __align__(8) uint64_t conv_bar[SK_TC_MAX_STAGES];    // its operand slots written
     __shared__ __align__(8) uint64_t empty_bar[SK_TC_MAX_STAGES];   // MMAs reading a stage done
     __shared__ __align__(8) uint64_t tfull_bar[2];                  // a tile's partial sums complete
     __shared__ __align__(8) uint64_t tempty_bar[2];                 // the epilogue has read them
@@ -105,13 +111,14 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
     const int S = T.nstages;
     const Stage L = stage_of(T.kmax, T.nn, BF);
     const int per_g = T.batch * T.nblk;
-    constexpr int NPL = BF ? 2 : 4;                 // planes per map ring
+    constexpr int NPL = BF ? 2 : 4;                 // operand slots per stage
     constexpr uint32_t APART = BF ? 256u : 512u;    // bytes of one part of A per column
 
     if (warp == 0) tc::tmem_alloc(&tslot, 512);
     if (t == 0) {
         for (int s = 0; s < S; ++s) {
             tc::mbar_init(tc::smem_u32(&full_bar[s]), 1);
+            tc::mbar_init(tc::smem_u32(&conv_bar[s]), NCONV);
             tc::mbar_init(tc::smem_u32(&empty_bar[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                 const int gi = f / per_g, rem = f - gi * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
                 const int j0 = pb * 8 * T.nn;
                 const int4 tr = T.trng[group_of(T, gi)];
-                const float4 *zb = T.Z + (size_t)b * T.nz * NPL * T.zrows;
+                const float *xb = T.x + (long long)b * T.stride;
                 for (int u = 0; u < tr.y; ++u, ++cnt) {
                     const int4 tl = T.tiles[tr.x + u];            // (input ring, E0, K | flags, A offset in KB)
                     const int s = (int)(cnt % (uint32_t)S);
@@ -143,34 +150,25 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                         !wait_or_abort(tc::smem_u32(&empty_bar[s]), ((cnt / S) - 1) & 1, abort_flag, T.status))
                         break;
                     const int K = tl.z & SK_TC_K_MASK;
-                    const uint32_t rbytes = (uint32_t)(T.nn + K / 8 - 1) * 16u;
-                    const float4 *zr = zb + (size_t)(tl.x - T.zi0) * NPL * T.zrows;
+                    const int npix = 8 * (T.nn + K / 8 - 1);      // pixels j0 + E0 .. of the input ring
                     unsigned char *sb = base + (size_t)s * L.bytes;
                     const uint32_t bar = tc::smem_u32(&full_bar[s]);
                     const uint32_t abytes = 2u * (uint32_t)K * APART;
-                    stile[s] = tl;                                // read by the MMA thread after the barrier
-                    tc::mbar_expect_tx(bar, abytes + (uint32_t)(NPL * rbytes));
+                    stile[s] = tl;                                // read after the barrier
+                    tc::mbar_expect_tx(bar, abytes + 4u * (uint32_t)npix);
                     tc::bulk_g2s(tc::smem_u32(sb), T.A + (size_t)tl.w * 1024, abytes, bar);
-                    if constexpr (BF) {
-                        // 8-pixel row of the first column; the hi and lo planes in turn
-                        const int m0 = (j0 + tl.y - T.pbase) >> 3;
-                        const uint32_t sl = tc::smem_u32(sb + L.a_bytes);
-                        tc::bulk_g2s(sl, zr + m0, rbytes, bar);
-                        tc::bulk_g2s(sl + L.slot, zr + T.zrows + m0, rbytes, bar);
-                        continue;
-                    }
-                    const int u0 = (j0 + tl.y - T.pbase) >> 2;    // 4-pixel row of the first column
-                    const int m0 = u0 >> 1;
-                    for (int h = 0; h < 2; ++h) {                 // hi, lo parts
-                        const float4 *pe = zr + (size_t)(2 * h) * T.zrows, *po = pe + T.zrows;
-                        const uint32_t sl = tc::smem_u32(sb + L.a_bytes + 2u * (uint32_t)h * L.slot);
-                        if (!(u0 & 1)) {                          // k-steps start on an even row
-                            tc::bulk_g2s(sl, pe + m0, rbytes, bar);
-                            tc::bulk_g2s(sl + L.slot, po + m0, rbytes, bar);
-                        } else {                                  // on an odd row: odd, then even one on
-                            tc::bulk_g2s(sl, po + m0, rbytes, bar);
-                            tc::bulk_g2s(sl + L.slot, pe + m0 + 1, rbytes, bar);
-                        }
+                    // the raw pixels, wrapped around the ring: pieces start on 4-pixel
+                    // boundaries (E0, j0 and the ring length are multiples of 4)
+                    const float *xr = xb + T.rings[tl.x].start;
+                    int p = (j0 + tl.y) % T.n4;
+                    if (p < 0) p += T.n4;
+                    uint32_t dst = tc::smem_u32(sb + L.a_bytes + NPL * L.slot);
+                    for (int rem = npix; rem > 0;) {
+                        const int c = min(rem, T.n4 - p);
+                        tc::bulk_g2s(dst, xr + p, 4u * (uint32_t)c, bar);
+                        dst += 4u * (uint32_t)c;
+                        rem -= c;
+                        p = 0;
                     }
                 }
             }
@@ -195,6 +193,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                         !wait_or_abort(tc::smem_u32(&tempty_bar[ab]), ((ccnt >> 1) - 1) & 1, abort_flag, T.status))
                         break;
                     if (!wait_or_abort(tc::smem_u32(&full_bar[s]), (cnt / S) & 1, abort_flag, T.status)) break;
+                    if (!wait_or_abort(tc::smem_u32(&conv_bar[s]), (cnt / S) & 1, abort_flag, T.status)) break;
                     tc::fence_after_sync();
                     const int4 tl = stile[s];
                     const bool first = (tl.z & SK_TC_FIRST) != 0, last = (tl.z & SK_TC_LAST) != 0;
@@ -235,7 +234,7 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
             tc::mma_commit(tc::smem_u32(&drain_bar));
             tc::mbar_wait(tc::smem_u32(&drain_bar), 0, LIMIT);
         }
-    } else {
+    } else if (warp < 2 + NEPI) {
         // ---------------- epilogue ----------------
         // warp w reads lane quadrant w % 4 (rows 32 (w % 4) ..) and the 16-column chunks
         // 16 half, 16 half + 32, ...: up to eight chunks of partial sums held in registers
@@ -293,6 +292,65 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
                 }
             }
         }
+    } else {
+        // ---------------- converters ----------------
+        // the stage's raw pixels into its operand slots: 3xTF32 4-pixel row v to slot
+        // v & 1 (row v >> 1) of the hi and lo parts, BF16x3 8-pixel row v to row v of
+        // the hi and lo slots; then the writes are made visible to the tensor cores
+        const int c = warp - 2 - NEPI;
+        uint32_t cnt = 0;
+        for (int f = blockIdx.x; f < T.total; f += gridDim.x) {
+            if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;     // the same in every lane
+            const int ntile = T.trng[group_of(T, f / per_g)].y;
+            bool ok = true;
+            for (int u = 0; u < ntile; ++u, ++cnt) {
+                const int s = (int)(cnt % (uint32_t)S);
+                ok = wait_or_abort(tc::smem_u32(&full_bar[s]), (cnt / S) & 1, abort_flag, T.status);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                const int4 tl = stile[s];
+                const int R = T.nn + (tl.z & SK_TC_K_MASK) / 8 - 1;     // rows per slot
+                unsigned char *sb = base + (size_t)s * L.bytes;
+                const float4 *raw = reinterpret_cast<const float4 *>(sb + L.a_bytes + NPL * L.slot);
+                if constexpr (BF) {
+                    uint4 *hs = reinterpret_cast<uint4 *>(sb + L.a_bytes);
+                    uint4 *ls = reinterpret_cast<uint4 *>(sb + L.a_bytes + L.slot);
+                    for (int v = 32 * c + lane; v < R; v += 32 * NCONV) {
+                        const float4 x0 = raw[2 * v], x1 = raw[2 * v + 1];
+                        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                        uint32_t h[4], l[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            uint16_t h0, l0, h1, l1;
+                            tc::split_bf16(xv[2 * e], h0, l0);
+                            tc::split_bf16(xv[2 * e + 1], h1, l1);
+                            h[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            l[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                        }
+                        hs[v] = make_uint4(h[0], h[1], h[2], h[3]);
+                        ls[v] = make_uint4(l[0], l[1], l[2], l[3]);
+                    }
+                } else {
+                    for (int v = 32 * c + lane; v < 2 * R; v += 32 * NCONV) {
+                        const float4 xv = raw[v];
+                        float4 h, l;
+                        tc::split_tf32(xv.x, h.x, l.x);
+                        tc::split_tf32(xv.y, h.y, l.y);
+                        tc::split_tf32(xv.z, h.z, l.z);
+                        tc::split_tf32(xv.w, h.w, l.w);
+                        const uint32_t o = (uint32_t)(v & 1) * L.slot + 16u * (uint32_t)(v >> 1);
+                        *reinterpret_cast<float4 *>(sb + L.a_bytes + o) = h;
+                        *reinterpret_cast<float4 *>(sb + L.a_bytes + 2u * L.slot + o) = l;
+                    }
+                }
+                tc::fence_smem_to_async();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive1(tc::smem_u32(&conv_bar[s]));
+            }
+            if (!ok) break;
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -348,70 +406,17 @@ __global__ void k_tc_tiles(const __grid_constant__ TcTileArgs T, const int *gate
     }
 }
 
-// Planes of the maps' belt input rings: for map b, ring zi0 + ri and row m, the
-// pixels pbase + 8m .. + 7 (wrapped around the ring) split into hi and lo parts:
-// 3xTF32 four planes of 16-byte rows -- hi even (first four pixels), hi odd, lo even,
-// lo odd; BF16x3 two planes of 16-byte rows (eight BF16 values) -- hi, lo.
-__global__ void k_tc_planes(const float *__restrict__ x, long long stride, const RingDev *__restrict__ rings, int zi0,
-                            int nz, int ri_lo, int nri, int zrows, int pbase, int n4, long long total,
-                            float4 *__restrict__ Z, bool bf) {
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(idx % zrows);
-        const long long rest = idx / zrows;
-        const int ri = ri_lo + (int)(rest % nri);
-        const long long b = rest / nri;
-        const float *xr = x + b * stride + rings[zi0 + ri].start;
-        int p = (pbase + 8 * m) % n4;
-        if (p < 0) p += n4;
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            int q = p + u;
-            if (q >= n4) q -= n4;
-            v[u] = xr[q];
-        }
-        if (bf) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                uint16_t h0, l0, h1, l1;
-                tc::split_bf16(v[2 * u], h0, l0);
-                tc::split_bf16(v[2 * u + 1], h1, l1);
-                h[u] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                l[u] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-            }
-            uint4 *zr = reinterpret_cast<uint4 *>(Z + (size_t)(b * nz + ri) * 2 * zrows);
-            zr[m] = make_uint4(h[0], h[1], h[2], h[3]);
-            zr[zrows + m] = make_uint4(l[0], l[1], l[2], l[3]);
-            continue;
-        }
-        float4 he, ho, le, lo;
-        tc::split_tf32(v[0], he.x, le.x);
-        tc::split_tf32(v[1], he.y, le.y);
-        tc::split_tf32(v[2], he.z, le.z);
-        tc::split_tf32(v[3], he.w, le.w);
-        tc::split_tf32(v[4], ho.x, lo.x);
-        tc::split_tf32(v[5], ho.y, lo.y);
-        tc::split_tf32(v[6], ho.z, lo.z);
-        tc::split_tf32(v[7], ho.w, lo.w);
-        float4 *zr = Z + (size_t)(b * nz + ri) * 4 * zrows;
-        zr[m] = he;
-        zr[zrows + m] = ho;
-        zr[2 * (size_t)zrows + m] = le;
-        zr[3 * (size_t)zrows + m] = lo;
-    }
-}
-
 }  // namespace
 
 int sk_tc_stages(int kmax, int nn, bool bf16, size_t *smem) {
     const Stage L = stage_of(kmax, nn, bf16);
-    const size_t avail = (size_t)220 * 1024 - 1024;
+    // the opt-in maximum of dynamic shared memory per block (227 KB) less the static
+    // barriers and the base alignment
+    const size_t avail = (size_t)227 * 1024 - 1024 - 128;
     int S = (int)std::min<size_t>(SK_TC_MAX_STAGES, avail / L.bytes);
     if (S < 2) return 0;
     // at least 120 KB so that one block holds an SM (it allocates all 512 tensor-memory columns)
-    if (smem) *smem = std::max((size_t)1024 + (size_t)S * L.bytes, (size_t)120 * 1024);
+    if (smem) *smem = std::max((size_t)128 + (size_t)S * L.bytes, (size_t)120 * 1024);
     return S;
 }
 
@@ -434,18 +439,5 @@ cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st) {
 cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st, const int *gate) {
     if (n_tiles <= 0) return cudaSuccess;
     k_tc_tiles<<<n_tiles, 256, 0, st>>>(a, gate);
-    return cudaGetLastError();
-}
-
-cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
-                                int ri_lo, int ri_hi, int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms,
-                                cudaStream_t st) {
-    ri_lo = std::max(0, ri_lo);
-    ri_hi = std::min(nz, ri_hi);
-    const long long total = (long long)batch * (ri_hi - ri_lo) * zrows;
-    if (total <= 0) return cudaSuccess;
-    const long long blocks = std::min<long long>((total + 255) / 256, (long long)sms * 16);
-    k_tc_planes<<<(unsigned)blocks, 256, 0, st>>>(x, stride, rings, zi0, nz, ri_lo, ri_hi - ri_lo, zrows, pbase, n4,
-                                                  total, Z, bf16);
     return cudaGetLastError();
 }

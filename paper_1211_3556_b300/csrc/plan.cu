@@ -250,7 +250,7 @@ static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<i
     std::vector<int> tg;
     std::vector<int4> tr(k->ngroups);
     long long kb = 0;
-    int kmax = 0, e0min = 1 << 30, e0max = -(1 << 30), zi1 = 0;
+    int kmax = 0;
     for (int gi = 0; gi < k->ngroups; ++gi) {
         const int first = (int)tl.size();
         for (int i = grp[gi].x; i <= grp[gi].y; ++i) {
@@ -272,9 +272,6 @@ static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<i
             tg.push_back(gi);
             kb += akb;
             kmax = std::max(kmax, K);
-            e0min = std::min(e0min, E0);
-            e0max = std::max(e0max, E0);
-            zi1 = std::max(zi1, i);
         }
         int ks = 0, nchunk = 0;
         for (int u = first; u < (int)tl.size(); ++u) {
@@ -294,30 +291,9 @@ static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<i
     T.nn = nn;
     T.nblk = (n4 + 8 * nn - 1) / (8 * nn);
     T.kmax = kmax;
-    T.pbase = e0min >= 0 ? (e0min & ~7) : -(((-e0min) + 7) & ~7);
-    T.zi0 = grp[0].x;
-    T.nz = zi1 - grp[0].x + 1;
-    T.zrows = (8 * nn * (T.nblk - 1) + e0max - T.pbase) / 8 + nn + kmax / 8 + 2;
     T.stages = sk_tc_stages(kmax, nn, bf, nullptr);
     T.kb = kb;
-    // every plane row an item copies lies inside its ring's planes (rows of 4 pixels in
-    // two planes for 3xTF32, of 8 pixels in one plane for BF16x3)
-    bool rows_ok = true;
-    for (const int4 &t4 : tl)
-        for (int pb = 0; pb < T.nblk; pb += std::max(1, T.nblk - 1)) {
-            const int off = 8 * nn * pb + t4.y - T.pbase;
-            const int Kt = t4.z & SK_TC_K_MASK;
-            int last;
-            if (bf) {
-                last = (off >> 3) + nn + Kt / 8 - 2;
-                if (off < 0 || (off & 7) || last >= T.zrows) rows_ok = false;
-            } else {
-                const int u0 = off >> 2;
-                last = (u0 >> 1) + (u0 & 1) + nn + Kt / 8 - 2;
-                if (u0 < 0 || (off & 3) || last >= T.zrows) rows_ok = false;
-            }
-        }
-    if (T.stages < 2 || !rows_ok) return SK_OK;
+    if (T.stages < 2) return SK_OK;
     T.h_tiles = tl;
     int rc;
     if ((rc = upload(tl, &T.d_tiles))) return rc;
@@ -706,13 +682,6 @@ static void job_groups(const SkJob &j, int g[4]) {
     if (sub->n_belt == 0) g[0] = g[1] = g[2] = g[3] = 0;
 }
 
-// Map planes of a tensor form for a job: 3xTF32 four planes of 4-pixel rows (hi/lo x
-// even/odd), BF16x3 two planes of 8-pixel rows (hi/lo); 16-byte rows either way.
-static size_t tc_plane_bytes(const SkJob &j, int f) {
-    const TcPlan &T = j.k->tcp[f];
-    return ((size_t)j.batch * T.nz * (f ? 2 : 4) * T.zrows * sizeof(float4) + 255) & ~(size_t)255;
-}
-
 // Running totals of the evaluating cap launches of wide-window jobs: one slice per
 // stream (narrow and polar launches run concurrently), each for up to 2048 threads per SM.
 static size_t ctot_bytes(const SkJob *jobs, int n, int path) {
@@ -729,8 +698,6 @@ size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path) {
     size_t b = 0;
     for (int i = 0; i < n; ++i) {
         b += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
-        const int f = sk_job_wants_tc(jobs[i], path);
-        if (f >= 0) b += tc_plane_bytes(jobs[i], f);
     }
     return b + ctot_bytes(jobs, n, path);
 }
@@ -882,8 +849,8 @@ int sk_tca_build(sk_kern *k, int form, cudaStream_t st, const int *gate) {
 }
 
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st) {
-    // jobs whose belt runs on the tensor cores (their A tiles are built on first use)
-    // (whole operators only: a ring subset runs its belt items on the FP32 kernel)
+    // jobs whose belt runs on the tensor cores (their A tiles are built on first use; a
+    // ring subset runs the tile groups of its belt rings)
     std::vector<int> use_tc(n, -1);            // the form, or -1
     for (int i = 0; i < n; ++i) {
         sk_kern *k = const_cast<sk_kern *>(jobs[i].k);
@@ -928,13 +895,19 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         }
     }
 
-    // The polar cap rings and any per-pair rings are small launches: run them on the
-    // context's side stream, forked from `st` here (after the belt weight rows, so that
-    // the belt is launched before the polar caps take SMs) and joined back at the end.
-    // The symmetric copies of the maps' cap input rings (in the workspace after the belt
-    // rows of all jobs) go first on the side stream, beside the belt (a band run of the
-    // host-buffer path builds its band's rings).
+    // The polar cap rings of the evaluating kernels and any per-pair rings are small
+    // launches: run them on the context's side stream, forked from `st` here (after the
+    // belt weight rows, so that the belt is launched before the polar caps take SMs) and
+    // joined back at the end.  The symmetric copies of the maps' cap input rings (in the
+    // workspace after the belt rows of all jobs) go first: on the side stream, beside the
+    // FP32 belt (whose blocks take work from a grid-stride loop), or on `st` before the
+    // tensor-core belt, whose one CTA per SM runs a fixed share of the items and would
+    // wait for SMs the copies hold (a band run of the host-buffer path builds its band's
+    // rings).
     cudaStream_t side = ctx->aux;
+    bool any_tc = false;
+    for (int i = 0; i < n; ++i) any_tc = any_tc || use_tc[i] >= 0;
+    cudaStream_t sym_st = any_tc ? st : side;
     std::vector<float4 *> hx(n, nullptr);
     auto sym = [&](int i, int r0, int r1, cudaStream_t s) -> int {
         if (r1 <= r0) return SK_OK;
@@ -957,8 +930,8 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             hx[i] = (float4 *)hp;
             hp += bytes;
             const SkItems *sub = jobs[i].sub;
-            int rc = sub ? sym(i, sub->sym[0][0], sub->sym[0][1], side) : sym(i, 0, jobs[i].k->sym_hi, side);
-            if (!rc && sub) rc = sym(i, sub->sym[1][0], sub->sym[1][1], side);
+            int rc = sub ? sym(i, sub->sym[0][0], sub->sym[0][1], sym_st) : sym(i, 0, jobs[i].k->sym_hi, sym_st);
+            if (!rc && sub) rc = sym(i, sub->sym[1][0], sub->sym[1][1], sym_st);
             if (rc) return rc;
         }
     }
@@ -983,39 +956,16 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         return flush();
     }
 
-    // tensor-core belt: per job, the maps' planes (in the workspace after the symmetric
-    // copies), then one launch over all its maps
+    // tensor-core belt: one launch per job over all its maps, reading the maps directly
     {
-        std::vector<void *> zp(n, nullptr);
-        char *p = (char *)ws;
-        for (int i = 0; i < n; ++i) p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
-        for (int i = 0; i < n; ++i) {
-            const int f = sk_job_wants_tc(jobs[i], path);
-            if (f >= 0) {
-                zp[i] = p;
-                p += tc_plane_bytes(jobs[i], f);
-            }
-        }
         for (int i = 0; i < n; ++i) {
             const int f = use_tc[i];
             if (f < 0) continue;
             const sk_kern *k = jobs[i].k;
             const TcPlan &T = k->tcp[f];
-            void *z = zp[i];
             int gr[4];
             job_groups(jobs[i], gr);
             if (gr[1] <= gr[0] && gr[3] <= gr[2]) continue;       // a subset without belt rings
-            // the planes of the input rings the groups read (every belt input ring for the
-            // whole operator)
-            cudaEvent_t ev = sk_prof_begin(ctx, st);
-            for (int q = 0; q < 2; ++q) {
-                if (gr[2 * q + 1] <= gr[2 * q]) continue;
-                const int r0 = k->h_bgrp[gr[2 * q]].x - T.zi0, r1 = k->h_bgrp[gr[2 * q + 1] - 1].y - T.zi0 + 1;
-                SK_CU(sk_launch_tc_planes(jobs[i].x, jobs[i].stride, (int)jobs[i].batch, k->g->d_rings, T.zi0, T.nz,
-                                          r0, r1, T.zrows, T.pbase, (int)(4 * k->g->nside), (float4 *)z, f == 1,
-                                          ctx->num_sms, st));
-            }
-            sk_prof_end(ctx, "tc_planes", ev, st);
             TcArgs a;
             memset(&a, 0, sizeof a);
             a.rings = k->g->d_rings;
@@ -1028,11 +978,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             a.tiles = T.d_tiles;
             a.trng = T.d_rng;
             a.A = T.d_A;
-            a.Z = (const float4 *)z;
-            a.zi0 = T.zi0;
-            a.nz = T.nz;
-            a.zrows = T.zrows;
-            a.pbase = T.pbase;
+            a.x = jobs[i].x;
             a.nn = T.nn;
             a.nblk = T.nblk;
             a.kmax = T.kmax;
@@ -1041,7 +987,7 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             a.ga0 = gr[0]; a.ga1 = gr[1]; a.gb0 = gr[2]; a.gb1 = gr[3];
             a.total = ((gr[1] - gr[0]) + (gr[3] - gr[2])) * (int)jobs[i].batch * T.nblk;
             a.status = ctx->d_status;
-            ev = sk_prof_begin(ctx, st);
+            cudaEvent_t ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_belt_tc(a, std::min(a.total, ctx->num_sms), st));
             sk_prof_end(ctx, f ? "conv_belt_bf16" : "conv_belt_tc", ev, st);
         }
@@ -1127,17 +1073,11 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         }
     // jobs whose caps evaluate their weights: one launch family per (strip class, mode,
     // summation); wide-window jobs sum ring by ring into the running totals at the end of
-    // the workspace (after the tensor planes), one half per stream
+    // the workspace (after the symmetric copies), one half per stream
     float *ctot = nullptr;
     if (ctot_bytes(jobs, n, path)) {
         char *p = (char *)ws;
-        for (int i = 0; i < n; ++i) {
-            p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
-                {
-                const int f = sk_job_wants_tc(jobs[i], path);
-                if (f >= 0) p += tc_plane_bytes(jobs[i], f);
-            }
-        }
+        for (int i = 0; i < n; ++i) p += sk_plan_workspace_bytes(jobs[i].k) + sk_sym_bytes(jobs[i].k, jobs[i].batch);
         ctot = (float *)p;
     }
     const long long ctot_half = (long long)ctx->num_sms * 2048 * 32;

@@ -69,7 +69,7 @@ struct sk_geom {
 // One tensor-core form of the belt: one tile per (ring group, input ring) with
 // (input ring, E0, K | chunk flags, A offset in KB), its group, and per group (first
 // tile, tiles); the A store (hi/lo tiles, built when the form is first used and rebuilt
-// with the table); the geometry of the per-call map planes.
+// with the table); the operand-row block (nn segments of 8 pixels) and its stages.
 struct TcPlan {
     bool ok = false;
     std::vector<int4> h_tiles;
@@ -78,7 +78,7 @@ struct TcPlan {
     int4 *d_rng = nullptr;                 // per group: first tile, tiles, chunks, 0
     long long kb = 0;
     unsigned char *d_A = nullptr;
-    int kmax = 0, nn = 0, nblk = 0, pbase = 0, zrows = 0, zi0 = 0, nz = 0, stages = 0;
+    int kmax = 0, nn = 0, nblk = 0, stages = 0;
 };
 
 struct sk_kern {
@@ -222,8 +222,8 @@ int sk_plan_bands(sk_kern *k);
 int sk_plan_ring_subset(sk_kern *k, int lo, int hi, bool sym, const SkItems **out);
 // Launch sequence of the forward operator for a set of jobs.  `ws` must hold
 // sk_jobs_workspace_bytes(jobs, n, path) bytes: the belt weight rows of every job,
-// then the symmetric copies of every job's maps for the caps, then the map planes of
-// the jobs whose belt runs on the tensor cores.
+// then the symmetric copies of every job's maps for the caps, then (wide-window jobs
+// whose caps evaluate their weights) the running totals of those launches.
 size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path = SK_PATH_AUTO);
 // The tensor-core form job j's belt runs under `path` (0 3xTF32, 1 BF16x3; given its
 // tiles exist), or -1.

@@ -99,10 +99,9 @@ struct TcArgs {
     const int4 *tiles;          // per tile: (input ring, E0, K | chunk flags, offset of its A pair in KB)
     const int4 *trng;           // per ring group: first tile, tiles, chunks, 0
     const unsigned char *A;     // stored A tiles (TF32 hi, then lo, no-swizzle K-major)
-    const float4 *Z;            // the call's planes: [map][ring - zi0][hi even, hi odd, lo even, lo odd][zrows]
-    int zi0, nz, zrows, pbase;  // first plane ring, plane rings, rows per plane, pixel of row 0
+    const float *x;             // the maps (map b at x + b stride, rings as `rings` gives)
     int nn, nblk, kmax, nstages;
-    int bf16;                   // 0: 3xTF32 (TF32 parts, 4-pixel plane rows), 1: BF16x3 (8-pixel rows)
+    int bf16;                   // 0: 3xTF32 (TF32 parts, 4-pixel operand rows), 1: BF16x3 (8-pixel rows)
     int ga0, ga1, gb0, gb1;     // the ring groups run: [ga0, ga1) then [gb0, gb1)
     int total;                  // items: groups x maps x pixel blocks
     int *status;
@@ -124,10 +123,6 @@ int sk_tc_stages(int kmax, int nn, bool bf16, size_t *smem);
 cudaError_t sk_launch_belt_tc(const TcArgs &a, int grid, cudaStream_t st);
 // A tiles of all n_tiles tiles; with `gate`, only if *gate is non-zero
 cudaError_t sk_launch_tc_tiles(const TcTileArgs &a, int n_tiles, cudaStream_t st, const int *gate = nullptr);
-// planes of the plane rings [ri_lo, ri_hi) (relative to zi0; the layout holds nz rings)
-cudaError_t sk_launch_tc_planes(const float *x, long long stride, int batch, const RingDev *rings, int zi0, int nz,
-                                int ri_lo, int ri_hi, int zrows, int pbase, int n4, float4 *Z, bool bf16, int sms,
-                                cudaStream_t st);
 
 // set-up kernels (geometry.cu)
 cudaError_t sk_launch_ring_geom(long long nside, RingDev *rings, double *z, double *rho,
