@@ -1026,51 +1026,70 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
         if (rc) return rc;
     }
 
-    // caps; the launches on `st` wait for the copies.  Jobs with stored weights: one launch
-    // per strip class, any tables together, on `st`: the items of rings with wide windows
-    // (the polar rings: few items, each a long run of whole-ring strips) first, so that
-    // the work queue hands them out before the many narrow-window items, and no launch
-    // beside the tensor-core belt holds SMs its static schedule is waiting for
+    // caps; the launches wait for the copies.  Jobs with stored weights: one launch per
+    // strip class, any tables together, the items of rings with wide windows (the polar
+    // rings: few items, each a long run of whole-ring strips) first, so that the work queue
+    // hands them out before the many narrow-window items.  The launch with the most items
+    // runs on `st`; the others (a wide cut's short strip classes: a few blocks, some of them
+    // one long item) go first, on the side stream, so that their blocks run beside it
+    // rather than before it with most of the GPU idle -- the big launch's blocks take items
+    // from its queue, so those that start late take fewer.  With one launch, no launch
+    // beside the tensor-core belt holds SMs its static schedule is waiting for.
     SK_CU(cudaEventRecord(ctx->ev_sym, side));
     SK_CU(cudaStreamWaitEvent(st, ctx->ev_sym, 0));
-    for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
-        for (int blk = 0; blk < 2; ++blk) {
-            Batcher b;
-            auto flush = [&]() -> int {
-                if (b.a.total > 0) {
-                    b.a.status = ctx->d_status;
-                    cudaEvent_t ev = sk_prof_begin(ctx, st);
-                    const int ipb = sk_capw_items_per_block(SK_CAP_LS[c], blk != 0);
-                    const int blocks = (b.a.total + ipb - 1) / ipb;
-                    int *q = ctx->d_queue + ctx->next_queue;
-                    ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
-                    SK_CU(cudaMemsetAsync(q, 0, sizeof(int), st));
-                    b.a.queue = q;
-                    SK_CU(sk_launch_conv_capw(b.a, SK_CAP_LS[c], blk != 0, std::min(blocks, ctx->num_sms), st));
-                    sk_prof_end(ctx, "conv_capw", ev, st);
+    {
+        struct CapwLaunch { JobsArg a; int c, blk; };
+        std::vector<CapwLaunch> cl;
+        for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+            for (int blk = 0; blk < 2; ++blk) {
+                Batcher b;
+                auto flush = [&]() {
+                    if (b.a.total > 0) cl.push_back(CapwLaunch{b.a, c, blk});
+                    b.reset();
+                };
+                for (int v = 0; v < 2; ++v)
+                for (int i = 0; i < n; ++i) {
+                    const sk_kern *k = jobs[i].k;
+                    const SkItems *sub = jobs[i].sub;
+                    const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
+                    const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
+                    if (!k->plan_ok || !k->d_capw || (int)k->blocked != blk || cn == 0 || jobs[i].batch == 0)
+                        continue;
+                    JobDesc d = base_desc(jobs[i]);
+                    d.cap_ls = SK_CAP_LS[c];
+                    d.hx = hx[i];
+                    d.hstride = k->sym_stride;
+                    d.capw = k->d_capw;
+                    d.capw_ring = k->d_capw_ring;
+                    b.add(d, citems, cn);
+                    if (b.full()) flush();
                 }
-                b.reset();
-                return SK_OK;
-            };
-            for (int v = 0; v < 2; ++v)
-            for (int i = 0; i < n; ++i) {
-                const sk_kern *k = jobs[i].k;
-                const SkItems *sub = jobs[i].sub;
-                const int4 *citems = sub ? sub->cap[c][v] : k->d_items_cap[c][v];
-                const int cn = sub ? sub->n_cap[c][v] : k->n_items_cap[c][v];
-                if (!k->plan_ok || !k->d_capw || (int)k->blocked != blk || cn == 0 || jobs[i].batch == 0) continue;
-                JobDesc d = base_desc(jobs[i]);
-                d.cap_ls = SK_CAP_LS[c];
-                d.hx = hx[i];
-                d.hstride = k->sym_stride;
-                d.capw = k->d_capw;
-                d.capw_ring = k->d_capw_ring;
-                b.add(d, citems, cn);
-                if (b.full()) { int rc = flush(); if (rc) return rc; }
+                flush();
             }
-            int rc = flush();
-            if (rc) return rc;
+        size_t main_l = 0;
+        for (size_t l = 1; l < cl.size(); ++l)
+            if (cl[l].a.total > cl[main_l].a.total) main_l = l;
+        if (cl.size() > 1 && sym_st == st) {          // the side stream waits for the copies too
+            SK_CU(cudaEventRecord(ctx->ev_sym, st));
+            SK_CU(cudaStreamWaitEvent(side, ctx->ev_sym, 0));
         }
+        auto launch = [&](CapwLaunch &L, cudaStream_t cs) -> int {
+            L.a.status = ctx->d_status;
+            cudaEvent_t ev = sk_prof_begin(ctx, cs);
+            const int ipb = sk_capw_items_per_block(SK_CAP_LS[L.c], L.blk != 0);
+            const int blocks = (L.a.total + ipb - 1) / ipb;
+            int *q = ctx->d_queue + ctx->next_queue;
+            ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
+            SK_CU(cudaMemsetAsync(q, 0, sizeof(int), cs));
+            L.a.queue = q;
+            SK_CU(sk_launch_conv_capw(L.a, SK_CAP_LS[L.c], L.blk != 0, std::min(blocks, ctx->num_sms), cs));
+            sk_prof_end(ctx, "conv_capw", ev, cs);
+            return SK_OK;
+        };
+        for (size_t l = 0; l < cl.size(); ++l)
+            if (l != main_l) { int rc = launch(cl[l], side); if (rc) return rc; }
+        if (!cl.empty()) { int rc = launch(cl[main_l], st); if (rc) return rc; }
+    }
     // jobs whose caps evaluate their weights: one launch family per (strip class, mode,
     // summation); wide-window jobs sum ring by ring into the running totals at the end of
     // the workspace (after the symmetric copies), one half per stream
