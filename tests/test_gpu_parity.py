@@ -376,6 +376,39 @@ def test_graph_replay_equals_eager(sk):
     gr.close()
 
 
+def test_graph_with_side_stream_cap_launches_equals_eager(sk):
+    # an operator whose cap rings fall into several strip classes (wide windows, blocked
+    # summation): its stored-weight cap launches run side by side, the smaller ones forked
+    # onto the context's side stream and joined back -- inside a captured graph too
+    import torch
+    nside, tc, nt = 64, 0.6, 1024
+    th = O.node_thetas(nt, tc, 0)
+    V = (1.0 + 0.5 * np.cos(3.0 * th) - 0.2 * th) * O.taper(th, tc)
+    k = sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc)
+    assert k.config()["cap_weights"] == "stored"
+    x = torch.from_numpy(white_noise_maps(nside, 2, 1201)).cuda()
+    sk._ctx.profile(True)
+    sk._ctx.profile_read()
+    ref = sk.convolve(k, x)
+    torch.cuda.synchronize()
+    prof = sk._ctx.profile_read()
+    sk._ctx.profile(False)
+    assert prof["conv_capw"][1] >= 2
+    y = torch.zeros_like(x)
+    gr = sk.Graph(sk._ctx, [(k, x, y)])
+    for _ in range(2):
+        y.zero_()
+        gr.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
+    gr.close()
+    sk._ctx.status()
+    for b in range(2):
+        outs = sample_indices(x.shape[1], 400, 1210 + b)
+        yo = O.conv_window(nside, V, tc, 0, x[b].cpu().numpy().astype(np.float64), outs)
+        assert rms_rel(ref[b].cpu().numpy()[outs], yo) <= RMS_BOUND
+
+
 # ------------------------------------------------------------------ errors
 
 def test_argument_errors(sk):
