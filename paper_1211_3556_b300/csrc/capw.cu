@@ -175,9 +175,12 @@ k_conv_capw(const __grid_constant__ JobsArg A) {
         const bool pref = NB == 2 && s_pref[slot] != 0;
         if (f >= A.total) break;
         const JobDesc &J = A.j[sk_find_job(A, f)];
+        // the maps of a job's batch are the innermost index of its work: one item's maps
+        // are taken one after another, so its weights come from HBM once and from L2 for
+        // the other maps (queued map by map, a batch re-read the whole stream per map)
         const int local = f - J.flat_base;
-        const int map = local / J.n_items;
-        const int4 it = J.items[local - map * J.n_items];
+        const int item = local / J.batch, map = local - item * J.batch;
+        const int4 it = J.items[item];
         const int ro = it.x, j0 = it.y;
         const unsigned mg = (unsigned)it.z;            // division by 2 n_o (centre_of)
         const int sh = it.w;
@@ -239,8 +242,8 @@ k_conv_capw(const __grid_constant__ JobsArg A) {
         auto stage_first = [&](int fn, int b) -> int {
             const JobDesc &Jn = A.j[sk_find_job(A, fn)];
             const int ln = fn - Jn.flat_base;
-            const int mn = ln / Jn.n_items;
-            const int4 itn = Jn.items[ln - mn * Jn.n_items];
+            const int itm = ln / Jn.batch, mn = ln - itm * Jn.batch;
+            const int4 itn = Jn.items[itm];
             const RingDev Rn = Jn.rings[itn.x];
             const int jln = min(itn.y + CT - 1, base_count(Rn.n >> 2, Rn.s) - 1);
             const PairInfo Pn = Jn.pairs[Jn.pair_off[itn.x]];
