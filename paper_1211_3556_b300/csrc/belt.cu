@@ -30,7 +30,7 @@
 
 namespace {
 
-constexpr int G = SK_BELT_G;
+// G below: SK_BELT_G, the output rings of a group
 constexpr int S = SK_BELT_STAGES;
 // Shared-memory header: full[S], empty[S] and the weight barrier (8 bytes each),
 // then the abort flag; the weight rows start at HDR (a multiple of 128 bytes).
