@@ -189,14 +189,14 @@ PROFILED_SOURCES = {
 def path_costs(prof, by_launch):
     """Measured cost of one pair on each ring path (0 belt, 1 cap, 2 per-pair, 3 cap with wide
     windows), ms per pair, from a profiled run's per-kernel times (each path's kernels with
-    their set-up launches: the tensor belt's planes, the caps' symmetric copy)."""
+    their set-up launches: the caps' symmetric copy)."""
     def per(names):
         return sum(prof[n][0] / prof[n][1] for n in names if n in prof)
     # the evaluating kernels' polar launch is a few blocks on a side stream, latency-bound
     # and overlapped with the rest: its time per pair says little about their share, so
     # there the caps' pairs (narrow and wide) and any per-pair rings take the narrow caps'
     # cost; the stored-weight launch sums both kinds of cap rings
-    belt = per(("conv_belt_tc", "conv_belt_bf16", "conv_belt", "tc_planes", "belt_weights"))
+    belt = per(("conv_belt_tc", "conv_belt_bf16", "conv_belt", "belt_weights"))
     cap = per(("conv_capw", "conv_cap", "cap_sym"))
     cap_pairs = by_launch[1] + (by_launch[2] if "conv_capw" in prof else 0)
     cb = belt / by_launch[0] if by_launch[0] else 0.0

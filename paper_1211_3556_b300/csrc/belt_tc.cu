@@ -90,8 +90,8 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
     return false;
 }
 
-// BF: the BF16x3 form -- BF16 hi/lo parts, K = 16 per MMA (kind::f16), one plane of
-// 8-pixel rows per part: B_q[s][t] = rows s + 2q and s + 2q + 1 of the plane, a start
+// BF: the BF16x3 form -- BF16 hi/lo parts, K = 16 per MMA (kind::f16), one slot of
+// 8-pixel rows per part: B_q[s][t] = rows s + 2q and s + 2q + 1 of the slot, a start
 // address 32 q bytes in with 16 bytes between the two core matrices along K.
 template <bool BF>
 __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArgs T) {

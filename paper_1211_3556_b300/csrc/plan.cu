@@ -240,7 +240,7 @@ int sk_plan_rebuild_belt_items(sk_kern *k) {
 // Tiles of a tensor-core belt form: one per (group, input ring) with any window.  3xTF32
 // (bf false): E0 = the union's first offset rounded down to a multiple of 4, K covers the
 // union plus the 7 extra columns of a segment's 8 output pixels, rounded up to 8 (one
-// TF32 k-step); BF16x3: E0 a multiple of 8 (the plane rows hold 8 pixels), K rounded up to
+// TF32 k-step); BF16x3: E0 a multiple of 8 (the operand rows hold 8 pixels), K rounded up to
 // 16.  Chunks of consecutive tiles with at least SK_TC_CHUNK_KSTEPS k-steps of 8 columns
 // are accumulated together in tensor memory.
 static int plan_tc(sk_kern *k, const std::vector<int2> &grp, const std::vector<int2> &ew, int HM, int R2, int n4,

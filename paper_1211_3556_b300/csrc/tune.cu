@@ -5,7 +5,7 @@
 // thread along a ring -- trades the per-chunk strip reloads, P + 3 values per 4P
 // FFMAs, against the tail of the last segment of each ring, 4 Nside pixels in
 // segments of 32 P; or the 3xTF32 tensor-core kernel, whose extra work is the
-// padding of its weight tiles and the per-call planes of the maps) and whether
+// padding of its weight tiles and the split of the maps' rows in each stage) and whether
 // the caps stream stored weights or evaluate them.  The planner starts from a
 // cost model; sk_kernel_autotune times the candidates on the caller's maps and
 // keeps the fastest, optionally remembering the choice in a small text cache
