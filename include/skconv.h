@@ -87,6 +87,16 @@ typedef struct sk_kern sk_kern;
 int sk_create(sk_ctx **out, int device);
 int sk_destroy(sk_ctx *ctx);
 
+/* Cap the context's workspace (the scratch memory that sk_convolve, sk_convolve_jobs,
+ * sk_convolve_host, sk_grad_table and the ring-band calls grow on demand) at `bytes`;
+ * 0 removes the cap (the default).  A call whose workspace would have to grow past the
+ * cap fails with SK_ENOMEM before launching any kernel, and the context stays usable (a
+ * later call under a higher cap, or no cap, succeeds).  The cap does not shrink a
+ * workspace already allocated, and it does not cover the operator's own stored tables
+ * (cap weights, tensor tiles), which fall back to their evaluated forms when they do
+ * not fit.  Errors: SK_EINVAL (NULL context, bytes < 0). */
+int sk_set_workspace_limit(sk_ctx *ctx, int64_t bytes);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char *sk_last_error(void);
 

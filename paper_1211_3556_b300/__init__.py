@@ -67,6 +67,7 @@ def _declare(L):
         "sk_count_pairs_by_path": (I, [P, P, ctypes.POINTER(I64)]),
         "sk_count_pairs_by_launch": (I, [P, P, ctypes.POINTER(I64)]),
         "sk_profile_enable": (I, [P, I]),
+        "sk_set_workspace_limit": (I, [P, I64]),
         "sk_profile_read": (I, [P, I, P, P, P, ctypes.POINTER(I)]),
         "sk_convolve": (I, [P, P, P, P, I64, I64, P]),
         "sk_convolve_path": (I, [P, P, P, P, I64, I64, I, P]),
@@ -191,6 +192,11 @@ class Context:
         a = (ctypes.c_int64 * 4)()
         _check(lib().sk_device_info(self._h, a))
         return {"sms": int(a[0]), "sm_clock_khz": int(a[1]), "smem_per_block": int(a[2]), "l2_bytes": int(a[3])}
+
+    def set_workspace_limit(self, nbytes: int):
+        """Cap the context's on-demand workspace at nbytes (0: no cap); a call that would
+        need more fails with SkError(SK_ENOMEM) before launching any kernel."""
+        _check(lib().sk_set_workspace_limit(self._h, int(nbytes)))
 
     def profile(self, on: bool):
         _check(lib().sk_profile_enable(self._h, 1 if on else 0))

@@ -34,15 +34,26 @@ extern "C" const char *sk_last_error(void) { return g_last_error.c_str(); }
 // ---------------------------------------------------------------------------
 
 int sk_ctx_workspace(sk_ctx *ctx, size_t bytes, void **out) {
+    if (bytes > ctx->ws_bytes && ctx->ws_limit && bytes > ctx->ws_limit)
+        return sk_fail(SK_ENOMEM, "workspace of %zu bytes over the context's limit of %zu bytes", bytes,
+                       ctx->ws_limit);
     if (bytes > ctx->ws_bytes) {
         if (ctx->ws) cudaFree(ctx->ws);          // cudaFree waits for work using it
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
         size_t b = std::max(bytes, (size_t)1 << 20);
+        if (ctx->ws_limit) b = std::min(b, std::max(bytes, ctx->ws_limit));
         SK_CU(cudaMalloc(&ctx->ws, b));
         ctx->ws_bytes = b;
     }
     *out = ctx->ws;
+    return SK_OK;
+}
+
+extern "C" int sk_set_workspace_limit(sk_ctx *ctx, int64_t bytes) {
+    if (!ctx) return sk_fail(SK_EINVAL, "sk_set_workspace_limit: NULL context");
+    if (bytes < 0) return sk_fail(SK_EINVAL, "sk_set_workspace_limit: bytes %lld < 0", (long long)bytes);
+    ctx->ws_limit = (size_t)bytes;
     return SK_OK;
 }
 

@@ -26,6 +26,7 @@ struct sk_ctx {
     int next_queue = 0;
     void *ws = nullptr;            // reusable workspace (maps of sk_convolve_host, belt weights, grad bins)
     size_t ws_bytes = 0;
+    size_t ws_limit = 0;           // cap on ws_bytes (sk_set_workspace_limit); 0: none
     // side stream for the small launches that overlap the large ones (polar caps,
     // per-pair fallback rings), forked from and joined into the caller's stream
     cudaStream_t aux = nullptr;

@@ -62,3 +62,4 @@ def test_null_handles_are_rejected():
     assert L.sk_grad_table(None, None, None, None, 1, 12, None, None) == sk.SK_EINVAL
     assert L.sk_destroy(None) == 0 and L.sk_kernel_destroy(None) == 0
     assert L.sk_graph_launch(None, None) == sk.SK_EINVAL
+    assert L.sk_set_workspace_limit(None, 0) == sk.SK_EINVAL

@@ -411,6 +411,30 @@ def test_graph_with_side_stream_cap_launches_equals_eager(sk):
 
 # ------------------------------------------------------------------ errors
 
+def test_workspace_limit_fails_cleanly_and_the_context_survives(sk):
+    # out-of-memory emulated by a capped workspace: the call fails with SK_ENOMEM before
+    # launching anything, nothing is written, and the same context then runs the call
+    import torch
+    nside, tc = 256, 0.02
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, 1024)
+    ctx = sk.Context(0)
+    k = sk.Kernel(sk.Geometry(ctx, nside), V, tc)
+    x = torch.from_numpy(white_noise_maps(nside, 2, 1301)).cuda()
+    y = torch.full_like(x, 7.0)
+    ctx.set_workspace_limit(64 << 10)
+    with pytest.raises(sk.SkError) as ei:
+        sk.convolve(k, x, out=y)
+    assert ei.value.code == sk.SK_ENOMEM
+    torch.cuda.synchronize()
+    assert bool((y == 7.0).all())
+    ctx.status()
+    ctx.set_workspace_limit(0)
+    sk.convolve(k, x, out=y)
+    torch.cuda.synchronize()
+    ctx.status()
+    assert torch.equal(y, sk.convolve(sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc), x))
+
+
 def test_argument_errors(sk):
     import torch
     g = sk.Geometry(sk._ctx, 16)
