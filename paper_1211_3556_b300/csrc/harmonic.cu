@@ -576,7 +576,10 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
         e = cudaGetLastError();
     }
     // chirp-z classes of the cap rings r = 1 .. N-1: FFT length P = the smallest 2^a or 3 2^a
-    // that holds n + K - 1 (n = 4r, K = min(n, L+1)); rows north then south per class
+    // that holds n + K - 1 (n = 4r, K = min(n, L+1)), but at least 2048 (or the largest
+    // ring's P when that is smaller): the small rings then share one class, one batched FFT
+    // each way instead of a dozen launches of a few microseconds; rows north then south per
+    // class
     std::vector<CzRow> rows;
     if (e == cudaSuccess && N > 1) {
         auto fft_len = [](long long need) {
@@ -585,11 +588,14 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
             const long long p3 = 3 * (p >> 2);           // 3 2^(a-2) between p/2 and p
             return (int)(p3 >= need ? p3 : p);
         };
+        const int nlast = 4 * ((int)N - 1);
+        const int pmin = std::min(2048, fft_len(nlast + std::min(nlast, L + 1) - 1));
+        auto ring_len = [&](int r) { return std::max(pmin, fft_len(4 * r + std::min(4 * r, L + 1) - 1)); };
         long long woff = 0, foff = 0;
         for (int r = 1; r < N;) {
-            const int n = 4 * r, P = fft_len(n + std::min(n, L + 1) - 1);
+            const int P = ring_len(r);
             int r1 = r;
-            while (r1 + 1 < N && fft_len(4 * (r1 + 1) + std::min(4 * (r1 + 1), L + 1) - 1) == P) ++r1;
+            while (r1 + 1 < N && ring_len(r1 + 1) == P) ++r1;
             sk_harm::CzClass c{P, r, r1 - r + 1, woff, 0};
             for (int hh = 0; hh < 2; ++hh)
                 for (int i = 0; i < c.cnt; ++i)
