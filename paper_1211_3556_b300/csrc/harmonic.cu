@@ -49,6 +49,12 @@ struct sk_harm {
     long long *d_moff = nullptr; // start of block m in d_lam
     long long *d_aoff = nullptr; // start of block m in a (l = m..L)
     long long lam_n = 0, a_n = 0;
+    // where the table rows matter: lambda_lm(theta) decays fast towards the pole below the
+    // turning point sin(theta) ~ m / (l + 1/2), and values below LAM_EPS are not read --
+    // per row (m, l) the first float4 of rings the analysis reads (d_q0, indexed like a_lm),
+    // per (m, 32 float4 of rings) the first l the synthesis reads (d_l0w, [m][n4 / 32])
+    int *d_q0 = nullptr;
+    int *d_l0w = nullptr;
     // per-call buffers (sized for `cap_batch` maps, grown on demand)
     long long cap_batch = 0;
     float2 *d_F = nullptr;       // [batch][nr][L + 1] ring coefficients F, then G
@@ -126,6 +132,54 @@ __global__ void k_lambda(const double *theta, const double *lg2c, const long lon
         }
         out[(long long)(l - m) * nrh] = (float)ldexp(v, -E);
     }
+}
+
+// Rows of the table whose leading rings are below LAM_EPS in magnitude: their products
+// with the ring coefficients (|F| up to ~sqrt(4 Nside) times the map's rms) sit far below
+// the FP32 rounding of the sums, so those rings are not read.  One warp per row (m, l):
+// q0 = (first ring with |lambda| >= LAM_EPS) / 4, or n4 when none.
+constexpr float LAM_EPS = 1e-12f;
+__global__ void k_lam_q0(const float *lam, const long long *moff, const long long *aoff, int L, int nrh,
+                         int *q0) {
+    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    // row index = aoff[m] + (l - m): find m by a scan of aoff (rows of block m: L - m + 1)
+    const long long a_n = aoff[L] + 1;
+    if (warp >= a_n) return;
+    int lo = 0, hi = L;
+    while (lo < hi) {                                    // largest m with aoff[m] <= warp
+        const int mid = (lo + hi + 1) >> 1;
+        if (aoff[mid] <= warp) lo = mid; else hi = mid - 1;
+    }
+    const int m = lo, l = m + (int)(warp - aoff[m]);
+    const float *row = lam + moff[m] + (long long)(l - m) * nrh;
+    int first = nrh;
+    for (int r0 = 0; r0 < nrh; r0 += 32) {
+        const int r = r0 + lane;
+        const bool big = r < nrh && fabsf(row[r]) >= LAM_EPS;
+        const unsigned bal = __ballot_sync(0xffffffffu, big);
+        if (bal) {
+            first = r0 + __ffs(bal) - 1;
+            break;
+        }
+    }
+    if (lane == 0) q0[warp] = first >> 2;
+}
+
+// Per (m, group of 32 float4 of rings): the first l whose row matters to any ring of the
+// group, i.e. the smallest l with q0(m, l) <= the group's last float4 (every earlier row is
+// negligible on all the group's rings).  One thread per m.
+__global__ void k_lam_l0(const int *q0, const long long *aoff, int L, int n4, int *l0w) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > L) return;
+    const int nw = (n4 + 31) / 32;
+    int *out = l0w + (long long)m * nw;
+    int wl = nw;                                         // groups wl .. nw - 1 have their start
+    int cur = n4;
+    for (int l = m; l <= L && wl > 0; ++l) {
+        cur = min(cur, q0[aoff[m] + (l - m)]);
+        while (wl > 0 && min(32 * (wl - 1) + 31, n4 - 1) >= cur) out[--wl] = l;
+    }
+    while (wl > 0) out[--wl] = L + 1;                   // nothing matters: no row is read
 }
 
 // Twiddle and phase tables of the ring DFTs (FP64 sincospi, stored FP32).
@@ -276,8 +330,8 @@ __global__ void k_zone_in(const RingDev *rings, int nside, const float2 *X, int 
 
 // Legendre analysis: a_lm = dOmega sum_r lambda_lm(theta_r) (E_r or O_r), one
 // block per (m, map), a warp per l, lanes along r, warp sum.
-__global__ void k_leg_analysis(const float *lam, const long long *moff, const long long *aoff, const float2 *F,
-                               int L, int nr, int nrh, long long a_n, float domega, float2 *a) {
+__global__ void k_leg_analysis(const float *lam, const long long *moff, const long long *aoff, const int *q0s,
+                               const float2 *F, int L, int nr, int nrh, long long a_n, float domega, float2 *a) {
     extern __shared__ float2 sEO[];                  // [nrh] E, then [nrh] O
     const int m = blockIdx.x, b = blockIdx.y;
     const float2 *Fb = F + (long long)b * nr * (L + 1);
@@ -301,7 +355,7 @@ __global__ void k_leg_analysis(const float *lam, const long long *moff, const lo
         const float4 *row = reinterpret_cast<const float4 *>(lm + (long long)(l - m) * nrh);
         const float4 *S = reinterpret_cast<const float4 *>(sEO + (((l + m) & 1) ? nrh : 0));
         float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;
-        int q = lane;
+        int q = q0s[aoff[m] + (l - m)] + lane;       // the row's leading rings are negligible
         for (; q + 32 < n4; q += 64) {               // two 16-byte loads in flight per lane
             const float4 w = row[q], v = row[q + 32];
             const float4 s0 = S[2 * q], s1 = S[2 * q + 1], t0 = S[2 * (q + 32)], t1 = S[2 * (q + 32) + 1];
@@ -331,8 +385,9 @@ __global__ void k_leg_analysis(const float *lam, const long long *moff, const lo
         if (lane == 0) a[(long long)b * a_n + aoff[m] + (l - m)] = make_float2(domega * re, domega * im);
     }
 }
-__global__ void k_leg_synthesis(const float *lam, const long long *moff, const long long *aoff, const double *kl,
-                                const float2 *a, int L, int nr, int nrh, long long a_n, float2 *G) {
+__global__ void k_leg_synthesis(const float *lam, const long long *moff, const long long *aoff, const int *l0w,
+                                const double *kl, const float2 *a, int L, int nr, int nrh, long long a_n,
+                                float2 *G) {
     extern __shared__ float2 sb[];                   // b_l = K^_l a_lm, l = m..L
     const int m = blockIdx.x, b = blockIdx.y;
     for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
@@ -346,7 +401,10 @@ __global__ void k_leg_synthesis(const float *lam, const long long *moff, const l
     const int n4 = nrh >> 2;                          // rings in fours: one 16-byte load per l
     for (int q = threadIdx.x; q < n4; q += blockDim.x) {
         float er[4] = {}, ei[4] = {}, orr[4] = {}, oi[4] = {};
-        int l = m;
+        // the rows before the group's first one that matters are skipped (the start is
+        // rounded down to an even l - m, keeping the pairs' parity)
+        const int l0 = l0w[(long long)m * ((n4 + 31) / 32) + (q >> 5)];
+        int l = m + ((max(l0, m) - m) & ~1);
         for (; l + 1 <= L; l += 2) {                 // l - m even (l + m even), then odd
             const float4 w0 = reinterpret_cast<const float4 *>(lm + (long long)(l - m) * nrh)[q];
             const float4 w1 = reinterpret_cast<const float4 *>(lm + (long long)(l + 1 - m) * nrh)[q];
@@ -518,6 +576,7 @@ void free_harm(sk_harm *h) {
     cudaFree(h->d_kl); cudaFree(h->d_lam); cudaFree(h->d_moff); cudaFree(h->d_aoff);
     cudaFree(h->d_F); cudaFree(h->d_a); cudaFree(h->d_X); cudaFree(h->d_tmp);
     cudaFree(h->d_zph);
+    cudaFree(h->d_q0); cudaFree(h->d_l0w);
     for (auto &c : h->cz)
         if (c.plan) cufftDestroy(c.plan);
     cudaFree(h->d_czrow); cudaFree(h->d_czf); cudaFree(h->d_czw);
@@ -625,6 +684,19 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
         k_lambda<<<(unsigned)((nthr + HT - 1) / HT), HT>>>(g->d_theta, d_lg2c, h->d_moff, L, nrh, h->d_lam);
         e = cudaGetLastError();
     }
+    // where the rows matter (rings in float4 groups of four: nq of them)
+    const int nq = nrh / 4;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_q0, sizeof(int) * (size_t)atot);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_l0w, sizeof(int) * (size_t)(L + 1) * ((nq + 31) / 32));
+    if (e == cudaSuccess) {
+        const long long threads = 32LL * atot;
+        k_lam_q0<<<(unsigned)((threads + HT - 1) / HT), HT>>>(h->d_lam, h->d_moff, h->d_aoff, L, nrh, h->d_q0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_lam_l0<<<(L + HT) / HT, HT>>>(h->d_q0, h->d_aoff, L, nq, h->d_l0w);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_lg2c);
     if (e != cudaSuccess) {
@@ -729,8 +801,8 @@ static int harm_analysis(sk_ctx *ctx, sk_harm *h, const float *d_in, int64_t bat
     // Legendre analysis and synthesis
     const size_t sm_a = sizeof(float2) * 2 * nrh;
     SK_CU(cudaFuncSetAttribute(k_leg_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_a));
-    k_leg_analysis<<<dim3(L + 1, (unsigned)batch), HT, sm_a, st>>>(h->d_lam, h->d_moff, h->d_aoff, h->d_F, L, nr,
-                                                                    nrh, h->a_n, domega, h->d_a);
+    k_leg_analysis<<<dim3(L + 1, (unsigned)batch), HT, sm_a, st>>>(h->d_lam, h->d_moff, h->d_aoff, h->d_q0, h->d_F,
+                                                                    L, nr, nrh, h->a_n, domega, h->d_a);
     SK_CU(cudaGetLastError());
     return SK_OK;
 }
@@ -745,7 +817,7 @@ static int harm_synthesis(sk_ctx *ctx, sk_harm *h, float *d_out, int64_t batch, 
     const int ncap = 2 * (N - 1);
     (void)ctx;
     k_leg_synthesis<<<dim3(L + 1, (unsigned)batch), HT, sizeof(float2) * (L + 1), st>>>(
-        h->d_lam, h->d_moff, h->d_aoff, h->d_kl, h->d_a, L, nr, nrh, h->a_n, h->d_F);
+        h->d_lam, h->d_moff, h->d_aoff, h->d_l0w, h->d_kl, h->d_a, L, nr, nrh, h->a_n, h->d_F);
     SK_CU(cudaGetLastError());
     // inverse ring DFTs
     if (ncap > 0) {
