@@ -85,6 +85,9 @@ typedef struct sk_kern sk_kern;
  * The context owns a device status word and a reusable workspace.
  * Errors: SK_EINVAL (bad device), SK_ENOMEM, SK_ECUDA. */
 int sk_create(sk_ctx **out, int device);
+/* Release a context.  The handles made with it (geometries, operators, Fourier belts,
+ * harmonic handles, resampling plans, graphs) may be destroyed before or after it --
+ * each records its device -- but every other call on such a handle needs its context. */
 int sk_destroy(sk_ctx *ctx);
 
 /* Cap the context's workspace (the scratch memory that sk_convolve, sk_convolve_jobs,

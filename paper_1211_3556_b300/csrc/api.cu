@@ -185,7 +185,7 @@ extern "C" int64_t sk_npix(int64_t nside) { return valid_nside(nside) ? 12 * nsi
 
 extern "C" int sk_geometry_destroy(sk_geom *g) {
     if (!g) return SK_OK;
-    cudaSetDevice(g->ctx->device);
+    cudaSetDevice(g->device);
     cudaFree(g->d_rings); cudaFree(g->d_z); cudaFree(g->d_rho); cudaFree(g->d_theta);
     delete g;
     return SK_OK;
@@ -198,6 +198,7 @@ extern "C" int sk_geometry_create(sk_ctx *ctx, int64_t nside, sk_geom **out) {
     SK_CU(cudaSetDevice(ctx->device));
     sk_geom *g = new sk_geom();
     g->ctx = ctx;
+    g->device = ctx->device;
     g->nside = nside;
     g->npix = 12 * nside * nside;
     g->nr = (int)(4 * nside - 1);
@@ -249,7 +250,7 @@ static void free_kern(sk_kern *k) {
 
 extern "C" int sk_kernel_destroy(sk_kern *k) {
     if (!k) return SK_OK;
-    cudaSetDevice(k->ctx->device);
+    cudaSetDevice(k->device);
     free_kern(k);
     return SK_OK;
 }
@@ -363,6 +364,7 @@ static int finish_kernel(sk_kern *k) {
 static sk_kern *new_kernel(sk_ctx *ctx, const sk_geom *g, int64_t n_nodes, double tc, int layout) {
     sk_kern *k = new sk_kern();
     k->ctx = ctx;
+    k->device = ctx->device;
     k->g = g;
     k->nt = (int)n_nodes;
     k->tc = tc;

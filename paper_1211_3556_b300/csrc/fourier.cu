@@ -38,6 +38,7 @@
 
 struct sk_fourier {
     sk_ctx *ctx = nullptr;
+    int device = 0;                 // the context's device (the handle may outlive the context)
     const sk_kern *k = nullptr;
     int n = 0, M = 0;               // ring length 4 Nside, modes 0 .. n/2
     int f_lo = 0, f_nb = 0;         // output rings [f_lo, f_lo + f_nb) (0-based)
@@ -174,6 +175,7 @@ extern "C" int sk_fourier_create(sk_ctx *ctx, const sk_kern *k, sk_fourier **out
     const int z0 = N - 1, z1 = 3 * N - 1;                 // rings of 4N pixels (0-based)
     sk_fourier *f = new sk_fourier();
     f->ctx = ctx;
+    f->device = ctx->device;
     f->k = k;
     f->n = 4 * N;
     f->M = 2 * N + 1;
@@ -297,7 +299,7 @@ extern "C" int sk_fourier_create(sk_ctx *ctx, const sk_kern *k, sk_fourier **out
 
 extern "C" int sk_fourier_destroy(sk_fourier *f) {
     if (!f) return SK_OK;
-    cudaSetDevice(f->ctx->device);
+    cudaSetDevice(f->device);
     free_fourier(f);
     return SK_OK;
 }

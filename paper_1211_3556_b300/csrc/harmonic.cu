@@ -41,6 +41,7 @@
 
 struct sk_harm {
     sk_ctx *ctx = nullptr;
+    int device = 0;              // the context's device (the handle may outlive the context)
     const sk_geom *g = nullptr;
     int L = 0;
     int nrh = 0;                 // northern rings and the equator: 0-based rings 0 .. 2N - 1
@@ -600,6 +601,7 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
     SK_CU(cudaSetDevice(ctx->device));
     sk_harm *h = new sk_harm();
     h->ctx = ctx;
+    h->device = ctx->device;
     h->g = g;
     h->L = lmax;
     h->nrh = (int)(2 * N);
@@ -727,7 +729,7 @@ extern "C" int sk_harmonic_create(sk_ctx *ctx, const sk_geom *g, const double *k
 
 extern "C" int sk_harmonic_destroy(sk_harm *h) {
     if (!h) return SK_OK;
-    cudaSetDevice(h->ctx->device);
+    cudaSetDevice(h->device);
     free_harm(h);
     return SK_OK;
 }

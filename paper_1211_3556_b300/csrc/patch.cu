@@ -264,6 +264,7 @@ extern "C" int sk_resample(sk_ctx *ctx, const sk_geom *g, const float *d_in, flo
 
 struct sk_resample_plan {
     sk_ctx *ctx = nullptr;
+    int device = 0;                 // the context's device (the handle may outlive the context)
     const sk_geom *g = nullptr;
     int ring_lo = 0, ring_hi = 0;
     long long p0 = 0, p1 = 0;       // pixel range of the output rings
@@ -281,6 +282,7 @@ extern "C" int sk_resample_plan_create(sk_ctx *ctx, const sk_geom *g, const doub
     SK_CU(cudaSetDevice(ctx->device));
     sk_resample_plan *p = new sk_resample_plan();
     p->ctx = ctx;
+    p->device = ctx->device;
     p->g = g;
     p->ring_lo = ring_lo;
     p->ring_hi = ring_hi;
@@ -319,7 +321,7 @@ extern "C" int sk_resample_plan_create(sk_ctx *ctx, const sk_geom *g, const doub
 
 extern "C" int sk_resample_plan_destroy(sk_resample_plan *p) {
     if (!p) return SK_OK;
-    cudaSetDevice(p->ctx->device);
+    cudaSetDevice(p->device);
     cudaFree(p->d_pairs);
     delete p;
     return SK_OK;

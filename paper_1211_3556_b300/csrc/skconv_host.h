@@ -60,6 +60,7 @@ struct SkItems {
 
 struct sk_geom {
     sk_ctx *ctx = nullptr;
+    int device = 0;                        // the context's device (the handle may outlive the context)
     long long nside = 0, npix = 0;
     int nr = 0;
     RingDev *d_rings = nullptr;
@@ -84,6 +85,7 @@ struct TcPlan {
 
 struct sk_kern {
     sk_ctx *ctx = nullptr;
+    int device = 0;                        // the context's device (the handle may outlive the context)
     const sk_geom *g = nullptr;
     int nt = 0, layout = 0;
     double tc = 0.0;

@@ -411,6 +411,27 @@ def test_graph_with_side_stream_cap_launches_equals_eager(sk):
 
 # ------------------------------------------------------------------ errors
 
+def test_handles_released_after_their_context(sk):
+    # a context released before the handles made with it, as a garbage collector may order
+    # it: their release uses only their own device, not the freed context
+    import torch
+    nside, tc = 32, 0.1
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, 512)
+    ctx = sk.Context(0)
+    g = sk.Geometry(ctx, nside)
+    k = sk.Kernel(g, V, tc)
+    ctx.close()
+    k.close()
+    g.close()
+    torch.cuda.synchronize()
+    x = torch.from_numpy(white_noise_maps(nside, 1, 5)).cuda()
+    y = sk.convolve(sk.Kernel(sk.Geometry(sk._ctx, nside), V, tc), x)
+    torch.cuda.synchronize()
+    sk._ctx.status()
+    yo = O.conv_window(nside, V, tc, 0, x[0].cpu().numpy().astype(np.float64))
+    assert rms_rel(y[0].cpu().numpy(), yo) <= RMS_BOUND
+
+
 def test_workspace_limit_fails_cleanly_and_the_context_survives(sk):
     # out-of-memory emulated by a capped workspace: the call fails with SK_ENOMEM before
     # launching anything, nothing is written, and the same context then runs the call
