@@ -209,6 +209,20 @@ def test_harmonic_matches_ring_oracle_above_nside_32(sk, nside, lmax):
     assert rms_rel(y, ref) <= HARM_BOUND
 
 
+def test_harmonic_at_the_split_workloads_nside(sk):
+    # Nside 2048, the split workload's geometry -- 2047 cap rings through chirp-z transforms
+    # in several FFT-length classes, the 4097 zone rings through 8192-point FFTs, the lambda
+    # table's row starts -- at a band limit the oracle's FP64 ring transform finishes in
+    # seconds (the workload's l_cut of 1024 would take it minutes)
+    nside, lmax = 2048, 160
+    kl = np.exp(-np.arange(lmax + 1) / (0.4 * lmax)) * (1.0 + 0.3 * np.cos(np.arange(lmax + 1) / 5.0))
+    x = white_noise_maps(nside, 1, 740)[0]
+    y = run_harm(sk, nside, kl, lmax, x)[0]
+    a = O.sht_analysis_rings(nside, x.astype(np.float64), lmax)
+    ref = O.sht_synthesis_rings(nside, a, lmax, kl)
+    assert rms_rel(y, ref) <= HARM_BOUND
+
+
 @pytest.mark.parametrize("nside,lmax", [(32, 63), (128, 255)])
 def test_power_spectrum_matches_oracle(sk, nside, lmax):
     import torch
