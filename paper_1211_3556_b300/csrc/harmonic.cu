@@ -357,7 +357,9 @@ __global__ void k_leg_analysis(const float *lam, const long long *moff, const lo
         const float4 *S = reinterpret_cast<const float4 *>(sEO + (((l + m) & 1) ? nrh : 0));
         float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;
         int q = q0s[aoff[m] + (l - m)] + lane;       // the row's leading rings are negligible
-        for (; q + 32 < n4; q += 64) {               // two 16-byte loads in flight per lane
+#pragma unroll 2
+        for (; q + 32 < n4; q += 64) {               // four 16-byte loads in flight per lane (unrolled
+                                                     // twice: 3.86 -> 3.74 ms at Nside 2048; four times 3.91)
             const float4 w = row[q], v = row[q + 32];
             const float4 s0 = S[2 * q], s1 = S[2 * q + 1], t0 = S[2 * (q + 32)], t1 = S[2 * (q + 32) + 1];
             re0 = fmaf(w.x, s0.x, re0); im0 = fmaf(w.x, s0.y, im0);
