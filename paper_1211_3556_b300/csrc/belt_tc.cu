@@ -41,7 +41,11 @@
 // the autotuner.
 // Warp roles: 0 producer (bulk copies), 1 MMA issuer, 2..9 epilogue (tensor
 // memory -> registers -> outputs), 10..11 converters (raw pixels -> operand
-// slots).  Every wait is bounded and records SK_ETIMEOUT.
+// slots).  The producer takes items (group, map, pixel block) from an atomic
+// queue and hands their indices to the other roles through a small ring of
+// shared-memory slots (items differ in tile count: against a fixed share per
+// CTA, 0.387 -> 0.382 ms at Nside 2048, 4.63 -> 4.47 ms for 64 maps at Nside
+// 1024).  Every wait is bounded and records SK_ETIMEOUT.
 #include <string.h>
 
 #include <algorithm>
@@ -90,6 +94,22 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
     return false;
 }
 
+// Items: the producer takes each from the launch's queue (an atomic counter, so CTAs that
+// start late -- beside another launch -- take fewer) and writes it to slot ic mod NITEM;
+// every other role reads the slots in the same order.  take_item: the ic-th item (T.total
+// when there are none left or after an abort); `arrive` for one thread of each reading unit
+// (the MMA thread, each epilogue and converter warp), after its lanes have read the slot.
+constexpr int NITEM = 4;
+__device__ __forceinline__ int take_item(const int *sitem, uint64_t *ifull, uint64_t *iempty, uint32_t ic,
+                                         volatile int *abort_flag, int *status, bool arrive) {
+    const int si = (int)(ic % NITEM);
+    int f = 1 << 30;
+    if (wait_or_abort(tc::smem_u32(&ifull[si]), (ic / NITEM) & 1, abort_flag, status)) f = sitem[si];
+    __syncwarp(__activemask());
+    if (arrive) tc::mbar_arrive1(tc::smem_u32(&iempty[si]));
+    return f;
+}
+
 // BF: the BF16x3 form -- BF16 hi/lo parts, K = 16 per MMA (kind::f16), one slot of
 // 8-pixel rows per part: B_q[s][t] = rows s + 2q and s + 2q + 1 of the slot, a start
 // address 32 q bytes in with 16 bytes between the two core matrices along K.
@@ -104,6 +124,10 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
     __shared__ __align__(8) uint64_t tempty_bar[2];                 // the epilogue has read them
     __shared__ __align__(8) uint64_t drain_bar;                     // teardown
     __shared__ int4 stile[SK_TC_MAX_STAGES];                        // the tile each stage holds
+    // the items the producer takes from the launch's queue, handed to the other roles
+    __shared__ int sitem[NITEM];
+    __shared__ __align__(8) uint64_t ifull_bar[NITEM];              // an item index written
+    __shared__ __align__(8) uint64_t iempty_bar[NITEM];             // every role has read it
     __shared__ uint32_t tslot;
     __shared__ int abort_s;
     volatile int *abort_flag = &abort_s;
@@ -125,6 +149,10 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
             tc::mbar_init(tc::smem_u32(&tfull_bar[a]), 1);
             tc::mbar_init(tc::smem_u32(&tempty_bar[a]), NEPI);
         }
+        for (int i = 0; i < NITEM; ++i) {
+            tc::mbar_init(tc::smem_u32(&ifull_bar[i]), 1);
+            tc::mbar_init(tc::smem_u32(&iempty_bar[i]), 1 + NEPI + NCONV);
+        }
         tc::mbar_init(tc::smem_u32(&drain_bar), 1);
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -138,7 +166,16 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         // ---------------- producer ----------------
         if (lane == 0) {
             uint32_t cnt = 0;
-            for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
+            for (uint32_t ic = 0;; ++ic) {
+                // the next item from the queue (T.total: none left), handed to the other roles
+                const int f = *abort_flag ? T.total : min(atomicAdd(T.queue, 1), T.total);
+                const int si = (int)(ic % NITEM);
+                if (ic >= NITEM && !wait_or_abort(tc::smem_u32(&iempty_bar[si]), ((ic / NITEM) - 1) & 1,
+                                                  abort_flag, T.status))
+                    break;
+                sitem[si] = f;
+                tc::mbar_arrive1(tc::smem_u32(&ifull_bar[si]));
+                if (f >= T.total) break;
                 const int gi = f / per_g, rem = f - gi * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
                 const int j0 = pb * 8 * T.nn;
                 const int4 tr = T.trng[group_of(T, gi)];
@@ -182,7 +219,9 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
             uint32_t cnt = 0, ccnt = 0;                           // tiles, chunks
             const uint32_t idesc = BF ? tc::idesc_bf16(128, T.nn) : tc::idesc_tf32(128, T.nn);
             bool need_empty = false;                              // the next tile opens a chunk
-            for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
+            for (uint32_t ic = 0;; ++ic) {
+                const int f = take_item(sitem, ifull_bar, iempty_bar, ic, abort_flag, T.status, true);
+                if (f >= T.total) break;
                 const int ntile = T.trng[group_of(T, f / per_g)].y;
                 for (int u = 0; u < ntile; ++u, ++cnt) {
                     const int s = (int)(cnt % (uint32_t)S);
@@ -243,7 +282,9 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         const int row = quad * 32 + lane, r = row / SO, n = row - r * SO;
         const int nch = (T.nn - 16 * half + 31) / 32;
         uint32_t ccnt = 0;
-        for (int f = blockIdx.x; f < T.total && !*abort_flag; f += gridDim.x) {
+        for (uint32_t ic = 0;; ++ic) {
+            const int f = take_item(sitem, ifull_bar, iempty_bar, ic, abort_flag, T.status, lane == 0);
+            if (f >= T.total) break;
             const int gi = f / per_g, rem = f - gi * per_g, b = rem / T.nblk, pb = rem - b * T.nblk;
             const int g = group_of(T, gi);
             const int j0 = pb * 8 * T.nn;
@@ -299,8 +340,10 @@ __global__ void __launch_bounds__(NT, 1) k_belt_tc(const __grid_constant__ TcArg
         // the hi and lo slots; then the writes are made visible to the tensor cores
         const int c = warp - 2 - NEPI;
         uint32_t cnt = 0;
-        for (int f = blockIdx.x; f < T.total; f += gridDim.x) {
-            if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;     // the same in every lane
+        for (uint32_t ic = 0;; ++ic) {
+            const int f = __shfl_sync(0xffffffffu, take_item(sitem, ifull_bar, iempty_bar, ic, abort_flag,
+                                                             T.status, lane == 0), 0);
+            if (f >= T.total || __shfl_sync(0xffffffffu, *abort_flag, 0)) break;   // the same in every lane
             const int ntile = T.trng[group_of(T, f / per_g)].y;
             bool ok = true;
             for (int u = 0; u < ntile; ++u, ++cnt) {

@@ -987,6 +987,9 @@ int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaS
             a.ga0 = gr[0]; a.ga1 = gr[1]; a.gb0 = gr[2]; a.gb1 = gr[3];
             a.total = ((gr[1] - gr[0]) + (gr[3] - gr[2])) * (int)jobs[i].batch * T.nblk;
             a.status = ctx->d_status;
+            a.queue = ctx->d_queue + ctx->next_queue;
+            ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
+            SK_CU(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
             cudaEvent_t ev = sk_prof_begin(ctx, st);
             SK_CU(sk_launch_belt_tc(a, std::min(a.total, ctx->num_sms), st));
             sk_prof_end(ctx, f ? "conv_belt_bf16" : "conv_belt_tc", ev, st);

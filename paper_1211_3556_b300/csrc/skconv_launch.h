@@ -104,6 +104,7 @@ struct TcArgs {
     int bf16;                   // 0: 3xTF32 (TF32 parts, 4-pixel operand rows), 1: BF16x3 (8-pixel rows)
     int ga0, ga1, gb0, gb1;     // the ring groups run: [ga0, ga1) then [gb0, gb1)
     int total;                  // items: groups x maps x pixel blocks
+    int *queue;                 // the launch's item counter (zero at launch)
     int *status;
 };
 struct TcTileArgs {
