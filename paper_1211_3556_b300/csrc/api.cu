@@ -704,7 +704,7 @@ extern "C" int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, co
     if (rc) return rc;
     SK_CU(cudaSetDevice(ctx->device));
     void *ws = nullptr;
-    if ((rc = sk_ctx_workspace(ctx, sk_grad_workspace_bytes(k, batch), &ws))) return rc;
+    if ((rc = sk_ctx_workspace(ctx, sk_grad_workspace_bytes(k, batch, ctx->num_sms), &ws))) return rc;
     return sk_run_grad(ctx, k, d_x, d_gy, batch, map_stride, d_gtable, (double *)ws, (cudaStream_t)stream);
 }
 

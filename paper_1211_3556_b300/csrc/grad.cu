@@ -14,7 +14,9 @@
 //  * cap rings: a base pair and its 16 symmetric images share (k, f), so one FP64
 //    evaluation serves 16 products per map (k_grad_cap, inputs from the caps'
 //    symmetric copy, four maps per pass; the node coordinate in double-float FP32 where
-//    the cut is small, FP64 otherwise);
+//    the cut is small, FP64 otherwise, evaluated on the first pass and cached for the
+//    others; each lane starts its window walk at its own position so that a warp's bin
+//    updates spread over the table);
 //  * the remaining rings: one thread per output pixel walks its window
 //    (k_grad_general).
 // Each block adds its bins (FP32 in shared memory, or FP64 directly for the belt's
@@ -329,9 +331,10 @@ __device__ __forceinline__ float dot4(const float *g, float4 h) {
 // the input pixel a come from the symmetric copy H (H[a], H[a + n/4], and the reflection
 // b = n/4 - s - a: H[b], H[b + n/4]), in the pairing the forward kernel uses; one (k, f)
 // per base pair and four maps (double-float, or FP64).
-constexpr int GC = 4;           // maps per pass of the cap gradient
-__global__ void __launch_bounds__(256)
-k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, double *acc) {
+constexpr int GC = SK_GRAD_CAP_MAPS;     // maps per pass of the cap gradient
+__global__ void __launch_bounds__(SK_GRAD_CAP_THREADS, 2)
+k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, double *acc, int2 *__restrict__ kfc,
+           int kf_steps) {
     extern __shared__ float bins[];
     const JobDesc &J = A.j[0];
     const int nt = J.kp.nt;
@@ -344,6 +347,11 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
     // items' order (heaviest first): no lane waits on a short ring's item, no warp on a
     // block's last item
     const int lane = threadIdx.x & 31;
+    // this warp's cache of (k, f), one entry per step of a lane's walk over its windows
+    // (kf_steps of them): the first pass over the maps writes it, the others read it
+    int2 *const kw = kf_steps > 0
+                         ? kfc + ((long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kf_steps) * 32 + lane
+                         : nullptr;
     for (;;) {
         int task = 0;
         if (lane == 0) task = atomicAdd(A.queue, 1);
@@ -381,6 +389,7 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
                     g[u][8 * r + 7] = o2 * yb[ss + j + 3 * Qo];
                 }
             }
+            int s = 0;          // step of the walk
             for (int p = J.pair_off[ro]; p < J.pair_off[ro + 1]; ++p) {
                 const PairInfo P = J.pairs[p];
                 const double2 ab = J.ab64[p];
@@ -390,27 +399,49 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
                 const float4 *h0 = J.hx + (long long)b0 * J.hstride + J.rings[P.ri].start;
                 int jlo, cnt;
                 pair_window(jo, R.n, R.s, P, jlo, cnt);
-                long long q = pair_q(jlo, jo, R.n, R.s, P);
-                // pixels a = jlo + m, a + n/4 (rising) and their reflections n/4 - s - a,
-                // + n/4 (falling), kept reduced mod n
-                const int n_i = P.n_i, hn = n_i >> 1;
-                int pa = jlo % n_i; if (pa < 0) pa += n_i;
+                // Each lane walks its window from its own position (lane mod cnt) and wraps
+                // to the window's start: the lanes' outputs are neighbours, so at one position
+                // of their windows their pairs mostly fall in one node interval, and the bin
+                // updates of a warp would all hit the same two addresses.
+                const int r0 = lane % cnt, js = jlo + r0, wrap = cnt - r0;
+                long long q = pair_q(js, jo, R.n, R.s, P);
+                // pixels a (rising from js, back to jlo after the wrap), a + n/4 and their
+                // reflections n/4 - s - a, + n/4 (falling), kept reduced mod n
+                const int n_i = P.n_i, hn = n_i >> 1, cm = cnt % n_i;
+                int pa = js % n_i; if (pa < 0) pa += n_i;
                 int pb = pa + Qi; if (pb >= n_i) pb -= n_i;
-                int pc = (Qi - P.s_i - jlo) % n_i; if (pc < 0) pc += n_i;
+                int pc = (Qi - P.s_i - js) % n_i; if (pc < 0) pc += n_i;
                 int pd = pc + Qi; if (pd >= n_i) pd -= n_i;
-                for (int m = 0; m < cnt; ++m, q += 2 * R.n) {
+                for (int m = 0; m < cnt; ++m, ++s, q += 2 * R.n) {
+                    if (m == wrap) {        // back to the window's first pixel
+                        q -= 2LL * R.n * cnt;
+                        pa -= cm; if (pa < 0) pa += n_i;
+                        pb -= cm; if (pb < 0) pb += n_i;
+                        pc += cm; if (pc >= n_i) pc -= n_i;
+                        pd += cm; if (pd >= n_i) pd -= n_i;
+                    }
                     const int ia = (pa & 1) * hn + (pa >> 1), ib = (pb & 1) * hn + (pb >> 1);
                     const int ic = (pc & 1) * hn + (pc >> 1), id = (pd & 1) * hn + (pd >> 1);
                     pa = pa + 1 == n_i ? 0 : pa + 1;
                     pb = pb + 1 == n_i ? 0 : pb + 1;
                     pc = pc == 0 ? n_i - 1 : pc - 1;
                     pd = pd == 0 ? n_i - 1 : pd - 1;
-                    int k;
-                    float fr;
-                    // |q| < 2^24 on the cap windows (checked when the plan was built): exact in FP32
-                    const int in = dfpath ? pair_kf_df((float)q, PD, KD, J.kp, k, fr) : -1;
-                    if (in == 0) continue;
-                    if (in < 0 && !pair_kf64((double)q * c0, ab.x, ab.y, J.kp, J.kd, k, fr)) continue;
+                    int k = -1;
+                    float fr = 0.0f;
+                    bool hit;
+                    if (b0 > 0 && s < kf_steps) {
+                        const int2 c = __ldcg(kw + (long long)s * 32);
+                        k = c.x;
+                        fr = __int_as_float(c.y);
+                        hit = k >= 0;
+                    } else {
+                        // |q| < 2^24 on the cap windows (checked when the plan was built): exact in FP32
+                        const int in = dfpath ? pair_kf_df((float)q, PD, KD, J.kp, k, fr) : -1;
+                        hit = in > 0 || (in < 0 && pair_kf64((double)q * c0, ab.x, ab.y, J.kp, J.kd, k, fr));
+                        if (b0 == 0 && s < kf_steps)
+                            __stcg(kw + (long long)s * 32, make_int2(hit ? k : -1, __float_as_int(hit ? fr : 0.0f)));
+                    }
+                    if (!hit) continue;
                     float v = 0.0f;
 #pragma unroll
                     for (int u = 0; u < GC; ++u) {
@@ -504,13 +535,15 @@ cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, dou
     return cudaGetLastError();
 }
 
-cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, cudaStream_t st) {
+cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, int2 *kfc, int kf_steps,
+                               cudaStream_t st) {
     if (a.n_jobs <= 0 || a.j[0].batch <= 0 || a.j[0].n_items <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.j[0].kp.nt * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_grad_cap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!a.queue) return cudaErrorInvalidValue;       // the task queue (zeroed by the caller)
-    k_grad_cap<<<grid, 256, smem, st>>>(a, gy, acc);
+    if (kf_steps > 0 && !kfc) return cudaErrorInvalidValue;
+    k_grad_cap<<<grid, SK_GRAD_CAP_THREADS, smem, st>>>(a, gy, acc, kfc, kf_steps);
     return cudaGetLastError();
 }
 

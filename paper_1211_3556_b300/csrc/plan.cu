@@ -103,6 +103,9 @@ void sk_plan_free(sk_kern *k) {
             cudaFree(k->d_items_cap[c][v]); k->d_items_cap[c][v] = nullptr;
             k->h_items_cap[c][v].clear();
         }
+    cudaFree(k->d_items_gcap); k->d_items_gcap = nullptr;
+    k->n_items_gcap = 0;
+    k->gcap_walk = 0;
     k->h_items_belt.clear();
     k->h_items_gen.clear();
     cudaFree(k->d_band_items); k->d_band_items = nullptr;
@@ -467,6 +470,25 @@ int sk_plan_build(sk_kern *k) {
             int rc = upload(cap_items[c][v], &k->d_items_cap[c][v]);
             if (rc) return rc;
         }
+    // the table gradient's cap items: one list, longest window walks first (a walk's steps,
+    // the window pixels of all the ring's window rings, set a gradient task's length)
+    {
+        std::vector<long long> walk(nr, 0);
+        std::vector<int4> all;
+        for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
+            for (int v = 0; v < 2; ++v)
+                for (const int4 &it : cap_items[c][v]) {
+                    if (walk[it.x] == 0)
+                        for (int p = off[it.x]; p < off[it.x + 1]; ++p)
+                            walk[it.x] += pairs[p].W < 0 ? pairs[p].n_i : 2 * pairs[p].W + 1;
+                    k->gcap_walk = std::max(k->gcap_walk, walk[it.x]);
+                    all.push_back(it);
+                }
+        std::stable_sort(all.begin(), all.end(),
+                         [&](const int4 &a, const int4 &b) { return walk[a.x] > walk[b.x]; });
+        k->n_items_gcap = (int)all.size();
+        if (int rc = upload(all, &k->d_items_gcap)) return rc;
+    }
     // layout of the stored cap weights: the items of a ring share its step count (the sum
     // over its window rings of the union steps), rings one after another
     {
@@ -1191,8 +1213,21 @@ static size_t grad_belt_bytes(const sk_kern *k) {
     if (!k->plan_ok || k->nb == 0) return 0;
     return (sizeof(float) * (size_t)k->nb * (2 * k->HM + 1) * k->WPM + 255) & ~(size_t)255;
 }
-size_t sk_grad_workspace_bytes(const sk_kern *k, long long batch) {
-    return grad_bins_bytes(k) + sk_sym_bytes(k, batch) + grad_belt_bytes(k);
+// The caps' (k, f) cache: with more maps than one pass of the cap gradient takes, each of
+// its warps (two blocks per SM) keeps the (k, f) of its walk's steps over an output's windows,
+// at most the longest walk of a cap ring and KF_MAX_STEPS.
+constexpr int KF_MAX_STEPS = 2048;
+static int grad_kf_steps(const sk_kern *k, long long batch) {
+    if (!k->plan_ok || k->n_items_gcap == 0 || batch <= SK_GRAD_CAP_MAPS) return 0;
+    return (int)std::min<long long>(k->gcap_walk, KF_MAX_STEPS);
+}
+static int grad_cap_grid(int num_sms) { return 2 * num_sms; }     // persistent: two blocks per SM
+static size_t grad_kf_bytes(const sk_kern *k, long long batch, int num_sms) {
+    return sizeof(int2) * 32 * (size_t)grad_kf_steps(k, batch) * grad_cap_grid(num_sms) *
+           (SK_GRAD_CAP_THREADS / 32);
+}
+size_t sk_grad_workspace_bytes(const sk_kern *k, long long batch, int num_sms) {
+    return grad_bins_bytes(k) + sk_sym_bytes(k, batch) + grad_belt_bytes(k) + grad_kf_bytes(k, batch, num_sms);
 }
 
 int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,
@@ -1232,29 +1267,34 @@ int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, 
             if (k->sym_hi > 0) {
                 JobDesc d = base_desc(jb);
                 d.hx = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + grad_bins_bytes(k));
+                const int kf_steps = grad_kf_steps(k, batch);
+                int2 *kfc = kf_steps > 0 ? reinterpret_cast<int2 *>(reinterpret_cast<char *>(acc) + grad_bins_bytes(k) +
+                                                                     sk_sym_bytes(k, batch) + grad_belt_bytes(k))
+                                         : nullptr;
                 d.hstride = k->sym_stride;
                 cudaEvent_t ev = sk_prof_begin(ctx, st);
                 SK_CU(sk_launch_cap_sym(d, 0, k->sym_hi, 2, st));
                 sk_prof_end(ctx, "cap_sym", ev, st);
-                for (int c = 0; c < SK_CAP_LS_CLASSES; ++c)
-                    for (int v = 0; v < 2; ++v) {
-                        if (k->n_items_cap[c][v] == 0) continue;
-                        JobsArg a;
-                        memset(&a, 0, sizeof a);
-                        a.j[0] = d;
-                        a.j[0].items = k->d_items_cap[c][v];
-                        a.j[0].n_items = k->n_items_cap[c][v];
-                        a.n_jobs = 1;
-                        a.total = k->n_items_cap[c][v];
-                        a.status = ctx->d_status;
-                        a.queue = ctx->d_queue + ctx->next_queue;
-                        ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
-                        SK_CU(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
-                        ev = sk_prof_begin(ctx, st);
-                        // persistent blocks (two per SM: 256 threads of 128 registers)
-                        SK_CU(sk_launch_grad_cap(a, gy, acc, std::min(8 * a.total, 2 * ctx->num_sms), st));
-                        sk_prof_end(ctx, "grad_cap", ev, st);
-                    }
+                // every strip class's items in one launch, the longest walks first, so that the
+                // polar rings' long tasks run beside the others rather than in a launch of their own
+                if (k->n_items_gcap > 0) {
+                    JobsArg a;
+                    memset(&a, 0, sizeof a);
+                    a.j[0] = d;
+                    a.j[0].items = k->d_items_gcap;
+                    a.j[0].n_items = k->n_items_gcap;
+                    a.n_jobs = 1;
+                    a.total = k->n_items_gcap;
+                    a.status = ctx->d_status;
+                    a.queue = ctx->d_queue + ctx->next_queue;
+                    ctx->next_queue = (ctx->next_queue + 1) % sk_ctx::NQUEUE;
+                    SK_CU(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
+                    ev = sk_prof_begin(ctx, st);
+                    // persistent blocks (two per SM: 256 threads of 128 registers)
+                    SK_CU(sk_launch_grad_cap(a, gy, acc, std::min(8 * a.total, grad_cap_grid(ctx->num_sms)), kfc,
+                                             kf_steps, st));
+                    sk_prof_end(ctx, "grad_cap", ev, st);
+                }
             }
             // the other rings: per pixel
             if (int rc = general(k->d_items_gen, k->n_items_gen)) return rc;

@@ -121,6 +121,11 @@ struct sk_kern {
     // [strip class][sin series valid]
     int4 *d_items_cap[SK_CAP_LS_CLASSES][2] = {};
     int n_items_cap[SK_CAP_LS_CLASSES][2] = {};
+    // the table gradient's cap items: every class in one list, the longest window walks
+    // (window pixels summed over the ring's window rings) first; the longest walk
+    int4 *d_items_gcap = nullptr;
+    int n_items_gcap = 0;
+    long long gcap_walk = 0;
     int n_cap_rings = 0;
     // the cap kernel reads the symmetric copy of input rings [0, sym_hi): sym_stride float4 per map
     int sym_hi = 0;
@@ -232,9 +237,10 @@ size_t sk_jobs_workspace_bytes(const SkJob *jobs, int n, int path = SK_PATH_AUTO
 // tiles exist), or -1.
 int sk_job_wants_tc(const SkJob &j, int path);
 int sk_run_jobs(sk_ctx *ctx, const SkJob *jobs, int n, int path, void *ws, cudaStream_t st);
-// Table gradient: `acc` is the start of sk_grad_workspace_bytes(k, batch) bytes of
-// workspace (the FP64 bins, then the caps' symmetric copy of x).
-size_t sk_grad_workspace_bytes(const sk_kern *k, long long batch);
+// Table gradient: `acc` is the start of sk_grad_workspace_bytes(k, batch, num_sms) bytes of
+// workspace (the FP64 bins, the caps' symmetric copy of x, the belt's ring-pair sums, the
+// caps' (k, f) cache).
+size_t sk_grad_workspace_bytes(const sk_kern *k, long long batch, int num_sms);
 int sk_run_grad(sk_ctx *ctx, const sk_kern *k, const float *x, const float *gy, long long batch,
                 long long stride, float *out, double *acc, cudaStream_t st);
 

@@ -198,4 +198,11 @@ size_t sk_grad_belt_floats(const JobDesc &j);
 cudaError_t sk_launch_grad_belt(const JobDesc &j, const float *gy, float *C, double *acc, const int *h_lo,
                                 const int *h_np, cudaStream_t st);
 // cap rings by symmetric base pairs (a.j[0]: the cap items, x's symmetric copy in hx)
-cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, cudaStream_t st);
+// The caps' table gradient: GC = SK_GRAD_CAP_MAPS maps per pass over a warp's windows, blocks of
+// SK_GRAD_CAP_THREADS; with more maps than one pass takes, each warp caches the (k, f) of the
+// first kf_steps steps of its walk in kfc ([grid x warps per block][kf_steps][32] int2; null
+// with kf_steps 0: no cache).
+constexpr int SK_GRAD_CAP_MAPS = 4;
+constexpr int SK_GRAD_CAP_THREADS = 256;
+cudaError_t sk_launch_grad_cap(const JobsArg &a, const float *gy, double *acc, int grid, int2 *kfc, int kf_steps,
+                               cudaStream_t st);

@@ -337,6 +337,28 @@ def test_grad_table_matches_oracle(sk, nside, tc, layout, nt):
     assert np.abs(got - go).max() <= 1e-5 * np.abs(go).max()
 
 
+@pytest.mark.parametrize("nside,tc,layout,nt", [(32, 0.1, 1, 64), (32, 0.12, 0, 512), (64, 0.05, 0, 4096)])
+def test_grad_table_many_maps_matches_oracle(sk, nside, tc, layout, nt):
+    """Nine maps: the cap gradient's later passes over the maps (four per pass, the last one
+    partial) take the node interval and fraction of each pair from the first pass's cache."""
+    import torch
+    V = oracle_table(nside, 2.5 * tc / 3 / ARCMIN, 3 * nside, nside, tc, nt, layout)
+    g = sk.Geometry(sk._ctx, nside)
+    k = sk.Kernel(g, V, tc, layout)
+    x = white_noise_maps(nside, 9, 23)
+    gy = white_noise_maps(nside, 9, 24)
+    gt = sk.grad_table(k, torch.from_numpy(x).cuda(), torch.from_numpy(gy).cuda())
+    torch.cuda.synchronize()
+    go = sum(O.grad_table(nside, nt, tc, layout, x[b].astype(np.float64), gy[b].astype(np.float64))
+             for b in range(9))
+    got = gt.cpu().numpy().astype(np.float64)
+    assert np.abs(got - go).max() <= 1e-5 * np.abs(go).max()
+    # the same bins from one map at a time (no cache: one pass each)
+    one = sum(sk.grad_table(k, torch.from_numpy(x[b:b + 1]).cuda(), torch.from_numpy(gy[b:b + 1]).cuda())
+              .cpu().numpy().astype(np.float64) for b in range(9))
+    assert np.abs(got - one).max() <= 1e-6 * np.abs(go).max()
+
+
 # ------------------------------------------------------------------ jobs and graphs
 
 def _mixed_jobs(sk):
