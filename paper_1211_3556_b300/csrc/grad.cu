@@ -392,13 +392,19 @@ k_grad_cap(const __grid_constant__ JobsArg A, const float *__restrict__ gy, doub
             int s = 0;          // step of the walk
             for (int p = J.pair_off[ro]; p < J.pair_off[ro + 1]; ++p) {
                 const PairInfo P = J.pairs[p];
-                const double2 ab = J.ab64[p];
-                const double c0 = SK_PI / (2.0 * (double)P.n_i * (double)R.n);
-                const PairDF PD{df_from(c0), df_from(ab.x), df_from(ab.y)};
                 const int Qi = P.n_i >> 2;
                 const float4 *h0 = J.hx + (long long)b0 * J.hstride + J.rings[P.ri].start;
                 int jlo, cnt;
                 pair_window(jo, R.n, R.s, P, jlo, cnt);
+                // the pair's FP64 constants, unless every step of its walk is in the cache
+                double2 ab = make_double2(0.0, 0.0);
+                double c0 = 0.0;
+                PairDF PD{};
+                if (!(b0 > 0 && s + cnt <= kf_steps)) {
+                    ab = J.ab64[p];
+                    c0 = SK_PI / (2.0 * (double)P.n_i * (double)R.n);
+                    PD = PairDF{df_from(c0), df_from(ab.x), df_from(ab.y)};
+                }
                 // Each lane walks its window from its own position (lane mod cnt) and wraps
                 // to the window's start: the lanes' outputs are neighbours, so at one position
                 // of their windows their pairs mostly fall in one node interval, and the bin
