@@ -311,7 +311,11 @@ int sk_convolve_adjoint(sk_ctx *ctx, const sk_kern *k, const float *d_gy, float 
  * and dL/dy:  d_gtable[n] = dOmega sum_b sum_o gy_bo sum_{i in cut} x_bi dK_lin/dV_n,
  * dK_lin/dV_k = 1 - f, dK_lin/dV_{k+1} = f (linear interpolation, Sec. 3).
  * d_gtable: n_nodes FP32 device buffer (overwritten).  Partial sums are FP32
- * per block and reduced in FP64.  Uses the context workspace.
+ * per block and reduced in FP64.  Uses the context workspace: the FP64 bins, the
+ * caps' input rings in their symmetric layout (16 bytes per pixel and map), the
+ * belt's ring-pair sums and, with more than four maps, a per-warp cache of the cap
+ * pairs' node intervals (8 bytes per step of the longest cap walk, at most 2048
+ * steps, x 32 lanes x 16 warps per SM; about 150 MB at Nside 1024, 30').
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int sk_grad_table(sk_ctx *ctx, const sk_kern *k, const float *d_x, const float *d_gy,
                   int64_t batch, int64_t map_stride, float *d_gtable, void *stream);
